@@ -1,0 +1,279 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds no arithmetic of the preconditioner: it only builds problem
+matrices (CSR, full symmetric pattern), partitions of the unknowns into
+non-overlapping subdomains, and right-hand sides.  Everything is deterministic
+for a given seed (numpy PCG64 streams).
+
+Problem shapes follow the paper's experiments where they are stated: a sparse
+SPD matrix A and a graph partition into N disjoint sets (Sec. 2.1); the 3D
+diffusion generator mimics the high-contrast coefficient of Fig. 2a
+(coefficient extruded in one direction, contrast up to 1e6).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class CSR:
+    """Square sparse matrix in CSR form: int64 row pointers, int32 column
+    indices (ascending within each row), float64 values."""
+
+    n: int
+    rowptr: np.ndarray
+    colind: np.ndarray
+    val: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+
+def _csr_from_coo(n, rows, cols, vals) -> CSR:
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    key = rows * n + cols
+    order = np.argsort(key, kind="stable")
+    key, vals = key[order], vals[order]
+    uniq, start = np.unique(key, return_index=True)
+    summed = np.add.reduceat(vals, start) if len(vals) else vals
+    r = (uniq // n).astype(np.int64)
+    c = (uniq % n).astype(np.int32)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    rowptr = np.cumsum(rowptr).astype(np.int64)
+    return CSR(n, rowptr, c, summed.astype(np.float64))
+
+
+def laplace2d(m: int) -> CSR:
+    """5-point Dirichlet Laplacian on an m x m grid of interior nodes.
+
+    Node (x, y) has index y*m + x; the stencil is [4, -1, -1, -1, -1] with the
+    boundary eliminated.  Its eigenvalues are 4 - 2cos(j pi/(m+1)) -
+    2cos(k pi/(m+1)), j, k = 1..m.
+    """
+    n = m * m
+    idx = np.arange(n).reshape(m, m)  # [y, x]
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [np.full(n, 4.0)]
+    for dy, dx in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+        ys, xs = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+        ny, nx = ys + dy, xs + dx
+        ok = (ny >= 0) & (ny < m) & (nx >= 0) & (nx < m)
+        rows.append(idx[ys[ok], xs[ok]])
+        cols.append(idx[ny[ok], nx[ok]])
+        vals.append(np.full(int(ok.sum()), -1.0))
+    return _csr_from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def box_partition_2d(m: int, box: int) -> np.ndarray:
+    """Partition of the m x m grid of laplace2d into (m/box)^2 square boxes,
+    numbered row-major; returns part[node] in [0, N)."""
+    assert m % box == 0
+    nb = m // box
+    ys, xs = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    return ((ys // box) * nb + xs // box).ravel().astype(np.int32)
+
+
+def _gaussian_field(shape, corr: float, rng) -> np.ndarray:
+    """Unit-variance Gaussian random field: white noise convolved with a
+    separable Gaussian kernel of correlation length `corr` (truncated at
+    3*corr), periodic wrap, then renormalised."""
+    g = rng.standard_normal(shape)
+    half = int(np.ceil(3 * corr))
+    t = np.arange(-half, half + 1, dtype=np.float64)
+    k = np.exp(-0.5 * (t / corr) ** 2)
+    k /= k.sum()
+    for ax in range(len(shape)):
+        acc = np.zeros_like(g)
+        for off, w in zip(t.astype(int), k):
+            acc += w * np.roll(g, off, axis=ax)
+        g = acc
+    g -= g.mean()
+    g /= g.std()
+    return g
+
+
+def diffusion_coefficient_3d(m: int, sigma: float, corr: float, n_channels: int,
+                             seed: int, channel_value: float = 1e6) -> np.ndarray:
+    """Cell coefficient kappa[z, y, x] = exp(sigma * g) with g a unit-variance
+    correlated Gaussian field, plus `n_channels` straight one-cell channels of
+    value `channel_value` along x at seeded (y, z) positions."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    kappa = np.exp(sigma * _gaussian_field((m, m, m), corr, rng))
+    if n_channels:
+        pos = rng.choice(m * m, size=min(n_channels, m * m), replace=False)
+        for p in pos:
+            kappa[p // m, p % m, :] = channel_value
+    return kappa
+
+
+def diffusion3d(m: int, sigma: float = 2.0, corr: float = 8.0, n_channels: int = 16,
+                seed: int = 0, channel_value: float = 1e6) -> CSR:
+    """7-point cell-centred finite-volume diffusion on an m^3 grid (h = 1) with
+    homogeneous Dirichlet boundary.  Interior face coefficient: harmonic mean
+    of the two cell coefficients; boundary face: 2*kappa_cell (half-cell
+    distance).  Cell (x, y, z) has index (z*m + y)*m + x."""
+    kappa = diffusion_coefficient_3d(m, sigma, corr, n_channels, seed, channel_value)
+    n = m ** 3
+    idx = np.arange(n).reshape(m, m, m)
+    diag = np.zeros((m, m, m))
+    rows, cols, vals = [], [], []
+    for ax in range(3):
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, m - 1)
+        hi[ax] = slice(1, m)
+        ka, kb = kappa[tuple(lo)], kappa[tuple(hi)]
+        t = 2.0 * ka * kb / (ka + kb)
+        diag[tuple(lo)] += t
+        diag[tuple(hi)] += t
+        ia, ib = idx[tuple(lo)].ravel(), idx[tuple(hi)].ravel()
+        rows += [ia, ib]
+        cols += [ib, ia]
+        vals += [-t.ravel(), -t.ravel()]
+        for face in (0, m - 1):
+            sl = [slice(None)] * 3
+            sl[ax] = slice(face, face + 1)
+            diag[tuple(sl)] += 2.0 * kappa[tuple(sl)]
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    vals.append(diag.ravel())
+    return _csr_from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def _neighbors(A: CSR, v: int) -> np.ndarray:
+    return A.colind[A.rowptr[v]:A.rowptr[v + 1]]
+
+
+def bfs_partition(A: CSR, N: int, seed: int, min_size: int, max_size: int) -> np.ndarray:
+    """Seeded multi-source BFS region growing on the graph of A.
+
+    N distinct random seeds; regions grow in round-robin order, one frontier
+    node at a time, claiming unclaimed neighbours in random order, and stop at
+    max_size.  Nodes left over join an adjacent region.  Regions smaller than
+    min_size are merged into their smallest adjacent region; regions larger
+    than max_size are split by BFS from their farthest node.  Returns part
+    with values in [0, N') (N' may differ from N after merges/splits)."""
+    n = A.n
+    rng = np.random.Generator(np.random.PCG64(seed))
+    part = np.full(n, -1, dtype=np.int64)
+    seeds = rng.choice(n, size=N, replace=False)
+    frontiers = [[int(s)] for s in seeds]
+    heads = [0] * N
+    sizes = np.ones(N, dtype=np.int64)
+    for r, s in enumerate(seeds):
+        part[s] = r
+    active = True
+    while active:
+        active = False
+        for r in range(N):
+            if sizes[r] >= max_size or heads[r] >= len(frontiers[r]):
+                continue
+            v = frontiers[r][heads[r]]
+            heads[r] += 1
+            nb = _neighbors(A, v)
+            nb = nb[part[nb] < 0]
+            rng.shuffle(nb)
+            for u in nb:
+                if sizes[r] >= max_size:
+                    break
+                if part[u] < 0:
+                    part[u] = r
+                    sizes[r] += 1
+                    frontiers[r].append(int(u))
+            active = True
+    # leftovers: attach to any claimed neighbour (repeat until none left)
+    while (part < 0).any():
+        for v in np.flatnonzero(part < 0):
+            nb = _neighbors(A, v)
+            claimed = nb[part[nb] >= 0]
+            if len(claimed):
+                part[v] = part[claimed[0]]
+    part = _merge_small(A, part, min_size)
+    part = _split_large(A, part, max_size)
+    # renumber densely
+    _, part = np.unique(part, return_inverse=True)
+    return part.astype(np.int32)
+
+
+def _region_adjacency(A: CSR, part: np.ndarray, r: int) -> np.ndarray:
+    nodes = np.flatnonzero(part == r)
+    nb = np.concatenate([_neighbors(A, v) for v in nodes]) if len(nodes) else np.zeros(0, np.int64)
+    other = np.unique(part[nb])
+    return other[other != r]
+
+
+def _merge_small(A: CSR, part: np.ndarray, min_size: int) -> np.ndarray:
+    part = part.copy()
+    while True:
+        labels, counts = np.unique(part, return_counts=True)
+        small = labels[counts < min_size]
+        if len(small) == 0 or len(labels) == 1:
+            return part
+        r = int(small[np.argmin(counts[counts < min_size])])
+        adj = _region_adjacency(A, part, r)
+        if len(adj) == 0:
+            return part
+        sz = np.array([np.sum(part == a) for a in adj])
+        part[part == r] = adj[int(np.argmin(sz))]
+
+
+def _split_large(A: CSR, part: np.ndarray, max_size: int) -> np.ndarray:
+    part = part.copy()
+    next_label = int(part.max()) + 1
+    changed = True
+    while changed:
+        changed = False
+        labels, counts = np.unique(part, return_counts=True)
+        for r, c in zip(labels, counts):
+            if c <= max_size:
+                continue
+            nodes = np.flatnonzero(part == r)
+            inside = np.zeros(A.n, dtype=bool)
+            inside[nodes] = True
+            # farthest node from the first node by BFS inside the region
+            far = _bfs_order(A, int(nodes[0]), inside)[-1]
+            order = _bfs_order(A, far, inside)
+            take = np.array(order[: c // 2], dtype=np.int64)
+            part[take] = next_label
+            next_label += 1
+            changed = True
+    return part
+
+
+def _bfs_order(A: CSR, start: int, inside: np.ndarray) -> list:
+    seen = {start}
+    order = [start]
+    head = 0
+    while head < len(order):
+        v = order[head]
+        head += 1
+        for u in _neighbors(A, v):
+            u = int(u)
+            if inside[u] and u not in seen:
+                seen.add(u)
+                order.append(u)
+    return order
+
+
+def rhs(n: int, seed: int, nrhs: int = 1) -> np.ndarray:
+    """Right-hand side(s) with entries uniform in [-1, 1]; shape (n,) or
+    (nrhs, n) (row k is right-hand side k, seed + k)."""
+    out = np.empty((nrhs, n))
+    for k in range(nrhs):
+        rng = np.random.Generator(np.random.PCG64(seed + k))
+        out[k] = rng.uniform(-1.0, 1.0, n)
+    return out[0] if nrhs == 1 else out
+
+
+# Named workloads (sizes as stated with the paper's experiments' shapes).
+def workload_c1():
+    """2D 5-point Laplacian, 64x64 interior nodes (n = 4096), 16 boxes of
+    16x16, overlap 1, tau = 50, b uniform[-1, 1] with seed 0."""
+    m = 64
+    return dict(A=laplace2d(m), part=box_partition_2d(m, 16), N=16, overlap=1, tau=50.0,
+                b=rhs(m * m, 0), name="laplace2d_64x64_16box_ov1_tau50")
