@@ -31,8 +31,8 @@ Readings where the paper is silent (each listed in the design notes):
     pencil is obtained by eliminating u on Omega_Gi from eq. (Zi) (textbook
     deflation of the kernel of D_i A_ii D_i, no approximation).  The
     eigenpairs are then those of the symmetric-definite pencil
-    (S_i, A_II) with S_i the Schur complement of tilde A_ii onto Omega_Ii and
-    mu = 1/lambda;
+    (S_i, A_II) with S_i the Schur complement of tilde A_ii onto Omega_Ii
+    (= that of Abar_ii onto Omega_Ii, quotient property) and mu = 1/lambda;
   * stopping test ||r_k||_2 <= rtol ||b||_2 on the recursively updated
     residual, x0 = 0.
 """
@@ -120,26 +120,33 @@ def schur_overlap(Abar: np.ndarray, n_i: int) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Eq. (Zi): local generalized eigenproblem and selection
 # --------------------------------------------------------------------------
-def local_eigenproblem(Aii: np.ndarray, tA: np.ndarray, nI: int, tau: float):
-    """Eigenpairs of D_i A_ii D_i u = lambda tilde A_ii u with D_i Boolean (1 on
-    Omega_Ii, 0 on Omega_Gi).  The kernel of D_i A_ii D_i (lambda = 0) is
-    eliminated: with u = [u_I; u_G], the Omega_Gi rows give
-    u_G = -tA_GG^{-1} tA_GI u_I and the Omega_Ii rows give
-    A_II u_I = lambda S u_I, S = tA_II - tA_IG tA_GG^{-1} tA_GI.
-    Solved as the symmetric-definite pencil S u = mu A_II u (mu = 1/lambda).
+def local_eigenproblem(Aii: np.ndarray, Abar: np.ndarray, nI: int, tau: float):
+    """Eigenpairs of eq. (Zi), D_i A_ii D_i u = lambda tilde A_ii u, with D_i
+    Boolean (1 on Omega_Ii, 0 on Omega_Gi).
 
-    Returns (lam, U, keep): all non-zero eigenvalues lambda descending, the
-    matching full eigenvectors u (n_i x nI, columns, A_II-orthonormal on their
-    Omega_Ii part) and the boolean mask lambda > 1/tau."""
+    The kernel of D_i A_ii D_i (lambda = 0, u supported on Omega_Gi) is never
+    selected.  Eliminating u_G from eq. (Zi) leaves A_II u_I = lambda S u_I
+    with S the Schur complement of tilde A_ii onto Omega_Ii.  By the quotient
+    property of Schur complements, S is also the Schur complement of Abar_ii
+    onto Omega_Ii (eliminating Omega_Gi and Omega_Di at once), which is how it
+    is formed here: S = Abar_II - Abar_IR Abar_RR^{-1} Abar_RI, R = [G, D].
+    Abar_RR^{-1} is applied through its Cholesky factor (Abar_RR >= delta I
+    with delta = s1 eps, the shift of Remark 3.2, so the factor exists).  The
+    symmetric-definite pencil S u = mu A_II u is then solved with
+    mu = 1/lambda.
+
+    Returns (lam, U, keep): all nI non-zero eigenvalues lambda descending, the
+    matching eigenvectors u on Omega_i (n_i x nI columns; the Omega_Ii part is
+    A_II-orthonormal, the Omega_Gi part is the minimising extension) and the
+    mask lambda > 1/tau."""
     n_i = Aii.shape[0]
     AII = Aii[:nI, :nI]
-    tII, tIG = tA[:nI, :nI], tA[:nI, nI:]
-    tGI, tGG = tA[nI:, :nI], tA[nI:, nI:]
-    if n_i > nI:
-        c = sla.cho_factor(tGG, lower=True)
-        S = tII - tIG @ sla.cho_solve(c, tGI)
+    BII, BIR, BRI, BRR = Abar[:nI, :nI], Abar[:nI, nI:], Abar[nI:, :nI], Abar[nI:, nI:]
+    if BRR.shape[0]:
+        c = sla.cho_factor(BRR, lower=True)
+        S = BII - BIR @ sla.cho_solve(c, BRI)
     else:
-        S = tII.copy()
+        S = BII.copy()
     S = 0.5 * (S + S.T)
     mu, uI = sla.eigh(S, AII)            # ascending mu  <=>  descending lambda
     # S is positive definite in exact arithmetic (shifted splitting), so every
@@ -149,8 +156,9 @@ def local_eigenproblem(Aii: np.ndarray, tA: np.ndarray, nI: int, tau: float):
         lam = np.where(mu > 0.0, 1.0 / np.where(mu > 0.0, mu, 1.0), np.inf)
     U = np.zeros((n_i, nI))
     U[:nI] = uI
-    if n_i > nI:
-        U[nI:] = -sla.cho_solve(c, tGI @ uI)
+    if BRR.shape[0]:
+        ext = -sla.cho_solve(c, BRI @ uI)
+        U[nI:] = ext[: n_i - nI]
     keep = lam > 1.0 / tau
     return lam, U, keep
 
@@ -206,8 +214,7 @@ def setup(A, part, N: int, overlap: int, tau: float, eps: float = EPS) -> Setup:
         I, G, D = subdomain_sets(As, part, i, overlap)
         Aii, X = local_matrices(As, I, G, D)
         Abar, s = splitting_root(X, eps)
-        tA = schur_overlap(Abar, len(I) + len(G))
-        lam, U, keep = local_eigenproblem(Aii, tA, len(I), tau)
+        lam, U, keep = local_eigenproblem(Aii, Abar, len(I), tau)
         chol = sla.cho_factor(Aii, lower=True)
         subs.append(Subdomain(I, G, D, Aii, chol, lam, keep, U[:, keep], s))
     W = coarse_basis(subs, n)

@@ -137,6 +137,25 @@ def test_all_nonzero_eigenvalues_at_least_one():
             assert len(s.lam) == len(s.I)
 
 
+def test_schur_quotient_property():
+    """Eliminating Omega_Gi from eq. (tildeA)'s tilde A_ii gives the same pencil
+    as eliminating Omega_Gi and Omega_Di from Abar_ii at once (quotient
+    property); checked on eigenvalues of eq. (Zi) below the eps-cluster."""
+    A, part, N = _small_2d()
+    As = O.to_scipy(A)
+    for i in range(N):
+        I, G, D = O.subdomain_sets(As, part, i, 1)
+        Aii, X = O.local_matrices(As, I, G, D)
+        Abar, sg = O.splitting_root(X)
+        tA = O.schur_overlap(Abar, len(I) + len(G))
+        nI = len(I)
+        S1 = tA[:nI, :nI] - tA[:nI, nI:] @ np.linalg.solve(tA[nI:, nI:], tA[nI:, :nI])
+        mu1 = sla.eigh(0.5 * (S1 + S1.T), Aii[:nI, :nI], eigvals_only=True)
+        lam, _, _ = O.local_eigenproblem(Aii, Abar, nI, 1.0)
+        lam1 = np.sort(1.0 / mu1[mu1 > 1e-8])
+        assert np.allclose(np.sort(lam[lam < 1e8]), lam1, rtol=1e-10)
+
+
 # --------------------------------------- eq. (Zi) by brute force in extended precision
 def _bruteforce_zi(X, Aii, nI, dps=40):
     """Eq. (invAii) and eq. (Zi) exactly as printed, in mpmath at `dps`
@@ -184,10 +203,9 @@ def test_eigenproblem_matches_extended_precision_bruteforce():
     for i in (0, 1):
         I, G, D = O.subdomain_sets(A, part, i, 1)
         Aii, X = O.local_matrices(A, I, G, D)
-        Abar, _ = O.splitting_root(X)
-        tA = O.schur_overlap(Abar, len(I) + len(G))
+        Abar, sg = O.splitting_root(X)
         for tau in (0.5, 50.0):
-            lam, U, keep = O.local_eigenproblem(Aii, tA, len(I), tau)
+            lam, U, keep = O.local_eigenproblem(Aii, Abar, len(I), tau)
             blam, bvec = _bruteforce_zi(X, Aii, len(I))
             assert len(blam) == len(lam) == len(I)
             order = np.argsort(-blam)
@@ -367,8 +385,8 @@ def test_planted_reversed_selection_is_caught(monkeypatch):
     count against the extended-precision evaluation of eq. (Zi)."""
     orig = O.local_eigenproblem
 
-    def wrong(Aii, tA, nI, tau):
-        lam, U, keep = orig(Aii, tA, nI, tau)
+    def wrong(Aii, Abar, nI, tau):
+        lam, U, keep = orig(Aii, Abar, nI, tau)
         return lam, U, ~keep
     monkeypatch.setattr(O, "local_eigenproblem", wrong)
     with pytest.raises(AssertionError):
