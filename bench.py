@@ -1,0 +1,324 @@
+"""Benchmark: time to a 1e-8 relative residual (setup + PCG solve) of the
+two-level algebraic Schwarz preconditioner on one GB300.
+
+Workload: 2D 5-point Laplacian on 64 x 64 interior nodes (n = 4096), 16 boxes
+of 16 x 16, overlap 1, tau = 50, b uniform[-1, 1] (seed 0): the
+configuration of the paper-shaped suite that fits one GPU (see the design
+notes for why the 2M-unknown diffusion configurations do not).
+
+One step = amdd_setup + amdd_pcg_solve (rtol 1e-8) on device-resident inputs,
+timed with CUDA events on the library's stream; L2 is flushed before each
+step.  `e2e` repeats the step through the C ABI from pinned host buffers with
+the host->device copies of A, the partition and b and the device->host copy of
+x inside the timed region.  `roofline` describes the kernel class with the
+largest device time, measured with CUDA events around each of its launches
+(the library's profiling mode) during the timed steps.  `cpu_baseline` is the
+FP64 CPU oracle on the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amdd|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 residual (setup+solve), learned/mixed vs plain FP64, same GB300"
+WORKLOAD = "laplace2d_64x64_16box_ov1_tau50"
+RTOL = 1e-8
+FP64_PEAK_GFLOPS = 1250.0    # GB300 FP64 (profiling recipe's table); no FP64 figure is measured by the driver
+ALU_CLASSES = {"jacobi_svd", "jacobi_eig", "gemm_tiles", "chol_diag", "chol_panel", "trtri_diag", "e_offdiag"}
+
+
+def _workload():
+    import synth
+    w = synth.workload_c1()
+    return w
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, max_seconds=30.0):
+    """The FP64 CPU oracle, as it stands, on the same workload (setup + PCG)."""
+    from oracle import amdd_oracle as O
+    times, its = [], None
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        S = O.setup(w["A"], w["part"], w["N"], w["overlap"], w["tau"])
+        _, its, _ = O.pcg(S.A, w["b"], lambda r: O.apply(S, r), rtol=RTOL)
+        times.append((time.perf_counter() - t0) * 1e3)
+        if time.perf_counter() - t_all > max_seconds / 2 or len(times) >= 3:
+            break
+    cores = os.cpu_count()
+    return {"value": statistics.median(times), "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": f"full workload ({WORKLOAD}), {len(times)} solve(s), numpy/scipy FP64 with the default "
+                      f"BLAS threading on {cores} host cores; {its} PCG iterations"}, its
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = _workload()
+    from oracle import amdd_oracle as O
+    budget = 150.0
+    t_start = time.perf_counter()
+    for _ in range(min(args.warmup, 1)):
+        S = O.setup(w["A"], w["part"], w["N"], w["overlap"], w["tau"])
+        O.pcg(S.A, w["b"], lambda r: O.apply(S, r), rtol=RTOL)
+    times, its = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        S = O.setup(w["A"], w["part"], w["N"], w["overlap"], w["tau"])
+        _, its, _ = O.pcg(S.A, w["b"], lambda r: O.apply(S, r), rtol=RTOL)
+        times.append((time.perf_counter() - t0) * 1e3)
+        if time.perf_counter() - t_start > budget:
+            break
+    v = sum(times) / len(times)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": w["A"].n, "N": w["N"], "overlap": w["overlap"],
+                       "tau": w["tau"], "rtol": RTOL},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": f"full workload per step, {len(times)} of {args.steps} steps run "
+                                       f"(bounded to {budget:.0f} s), {its} PCG iterations"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_amdd(args):
+    import numpy as np
+    import torch
+
+    from paper_2109_05908_gb300 import amdd as A
+    from paper_2109_05908_gb300.device import DeviceMatrix
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    w = _workload()
+    M, part_h, b_h = w["A"], np.asarray(w["part"], np.int32), w["b"]
+    dA = DeviceMatrix(M, device=dev)
+    part = torch.from_numpy(part_h).to(dev)
+    b = torch.from_numpy(b_h).to(dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    opts = A.opts_default()
+    opts.profile = 1
+
+    def one_step(profile_acc=None):
+        x.zero_()
+        h = A.setup(dA.csr, part.data_ptr(), w["N"], w["overlap"], w["tau"], opts, sp)
+        st = A.pcg_solve(h, b.data_ptr(), x.data_ptr(), 1, RTOL, 1000)
+        if profile_acc is not None:
+            for c in A.get_profile(h):
+                a = profile_acc.setdefault(c["name"], {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+                for k in ("launches", "ms", "flops", "bytes"):
+                    a[k] += c[k]
+        info = A.get_info(h)
+        A.destroy(h)
+        return st, info
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    prof = {}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    its = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        st, info = one_step(prof)
+        ev[k][1].record(stream)
+        its.append(st.iterations)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(bb) for a, bb in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end from pinned host buffers through the C ABI
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    h_rowptr, h_col, h_val = pin(M.rowptr.astype(np.int64)), pin(M.colind.astype(np.int32)), pin(M.val)
+    h_part, h_b = pin(part_h), pin(b_h)
+    h_x = torch.empty_like(h_b).pin_memory()
+    d_rowptr, d_col, d_val = torch.empty_like(dA.rowptr), torch.empty_like(dA.colind), torch.empty_like(dA.val)
+    d_part, d_b, d_x = torch.empty_like(part), torch.empty_like(b), torch.empty_like(b)
+    csr2 = A.make_csr(M.n, dA.nnz, d_rowptr.data_ptr(), d_col.data_ptr(), d_val.data_ptr())
+    h2d = sum(t.numel() * t.element_size() for t in (h_rowptr, h_col, h_val, h_part, h_b))
+    d2h = h_x.numel() * h_x.element_size()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for dst, src in ((d_rowptr, h_rowptr), (d_col, h_col), (d_val, h_val), (d_part, h_part), (d_b, h_b)):
+            dst.copy_(src, non_blocking=True)
+        d_x.zero_()
+        h = A.setup(csr2, d_part.data_ptr(), w["N"], w["overlap"], w["tau"], None, sp)
+        A.pcg_solve(h, d_b.data_ptr(), d_x.data_ptr(), 1, RTOL, 1000)
+        h_x.copy_(d_x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        A.destroy(h)
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e = sum(e2e_ms) / len(e2e_ms)
+    xs = h_x.numpy()
+    res = np.linalg.norm(M_mv(M, xs) - b_h) / np.linalg.norm(b_h)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_src = _peaks()
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, c = top
+    per_launch_ms = c["ms"] / max(c["launches"], 1)
+    if name in ALU_CLASSES:
+        achieved = c["flops"] / (c["ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3,
+                "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
+                "launches_per_step": c["launches"] / args.steps, "ms_per_launch": per_launch_ms,
+                "peak_source": "FP64 1.25 TFLOP/s nominal (recipe table); no measured FP64 figure"}
+    else:
+        achieved = c["bytes"] / (c["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "launches_per_step": c["launches"] / args.steps, "ms_per_launch": per_launch_ms,
+                "peak_source": f"hbm_gbs ({peak_src})"}
+    launches = int(sum(v["launches"] for v in prof.values()) / args.steps)
+    base, base_its = cpu_baseline(w) if world == 1 or rank == 0 else (None, None)
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": M.n, "nnz": int(M.rowptr[-1]), "N": w["N"], "overlap": w["overlap"],
+                   "tau": w["tau"], "rtol": RTOL, "n_C": info.n_C, "pcg_iterations": its[-1],
+                   "oracle_pcg_iterations": base_its, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "true_rel_residual": float(res)},
+        "gpu_launches": launches * args.steps,
+        "roofline": roof,
+        "cpu_baseline": base,
+        "clocks": clk,
+        "profile_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in
+                                sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def M_mv(M, x):
+    import numpy as np
+    rows = np.repeat(np.arange(M.n), np.diff(M.rowptr))
+    y = np.zeros(M.n)
+    np.add.at(y, rows, M.val * x[M.colind])
+    return y
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="amdd", choices=["amdd", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_amdd(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,204 @@
+/*
+ * amdd.h -- C ABI of a GB300 (sm_103a) implementation of the fully algebraic
+ * two-level overlapping Schwarz preconditioner for sparse SPD systems of
+ * Al Daas & Jolivet, "A robust algebraic multilevel domain decomposition
+ * preconditioner for sparse symmetric positive definite matrices"
+ * (arXiv 2109.05908).
+ *
+ * Problem (Sec. 1): solve A x = b, A n x n sparse SPD.
+ * Setup (Sec. 2.1, Eq. (Xi), Sec. 3.2, Eq. (tildeA), Eq. (Zi)): for each of
+ * the N non-overlapping subdomains Omega_Ii given by `part`, build the
+ * overlap Omega_Gi (graph distance 1..overlap), the extension Omega_Di
+ * (distance overlap+1), the local block row X_i = R_i A tilde R_i^T, its
+ * regularised square root Abar_ii, the local eigenproblem
+ * D_i A_ii D_i u = lambda tilde A_ii u with Boolean D_i, and keep the
+ * eigenvectors with lambda > 1/tau as the coarse block Z_i.  Then assemble
+ * and factor the coarse matrix E = R_0 A R_0^T, R_0^T = [R_i^T D_i Z_i].
+ * Apply (Eq. (two_level_schwarz)):
+ *     z = R_0^T E^{-1} R_0 r + sum_i R_i^T A_ii^{-1} R_i r.
+ * Solve: preconditioned conjugate gradient with that z.
+ *
+ * Conventions for every entry point:
+ *   - Pointers documented as "device" must be CUDA device pointers valid on
+ *     the current device; "host" pointers are ordinary host memory.
+ *   - The caller owns every buffer it passes; the library never frees or
+ *     retains caller memory past the call.  A handle owns every device and
+ *     host buffer it allocates, released by amdd_destroy.
+ *   - All GPU work of a handle is issued on the CUDA stream given to
+ *     amdd_setup (NULL = legacy default stream).  Calls return after the work
+ *     they issued has completed (they synchronise that stream), so results in
+ *     caller buffers are ready on return.
+ *   - Every call returns a status and never aborts the process.  Device-side
+ *     errors (a non-positive Cholesky pivot, an eigensolver that did not
+ *     converge) are latched and returned by the call that detects them.
+ *   - Not thread-safe per handle: one host thread at a time per handle.
+ */
+#ifndef AMDD_H
+#define AMDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AMDD_OK = 0,
+    AMDD_ERR_INVALID = 1,     /* bad argument, size or partition                  */
+    AMDD_ERR_NOT_SPD = 2,     /* a Cholesky pivot <= 0 (A_ii or E not SPD)         */
+    AMDD_ERR_NOCONV = 3,      /* PCG reached maxit before the tolerance            */
+    AMDD_ERR_OOM = 4,         /* a device or host allocation failed                */
+    AMDD_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up           */
+    AMDD_ERR_CUDA = 6,        /* any other CUDA runtime error                      */
+    AMDD_ERR_EIG_NOCONV = 7   /* a Jacobi eigensolver hit its sweep limit          */
+} amdd_status;
+
+typedef struct amdd_handle amdd_handle;
+
+/* Square sparse matrix in CSR form, full symmetric pattern, DEVICE pointers.
+ * rowptr[n+1] (int64), colind[nnz] (int32, ascending in each row), val[nnz]. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* rowptr;
+    const int32_t* colind;
+    const double* val;
+} amdd_csr;
+
+typedef struct {
+    double eps;           /* shift of Remark 3.2 / Sec. 3.2: Abar += sigma_1*eps*I; default 2^-52 */
+    int32_t max_sweeps;   /* sweep limit of the one-sided Jacobi solvers; default 60               */
+    int32_t profile;      /* 1: time every kernel launch of the handle with CUDA events (see
+                             amdd_get_profile); default 0                                           */
+    int32_t reserved[6];  /* must be zero                                                          */
+} amdd_opts;
+
+typedef struct {
+    int32_t iterations;         /* PCG iterations performed (first right-hand side)          */
+    int32_t converged;          /* 1 if ||r_k|| <= rtol ||b|| was reached                    */
+    double rel_residual;        /* recursive residual ||r_k|| / ||b|| at exit                */
+    double true_rel_residual;   /* ||b - A x|| / ||b|| recomputed at exit                    */
+    double solve_ms;            /* wall time of the call                                     */
+} amdd_stats;
+
+typedef struct {
+    int64_t n;             /* order of A                                   */
+    int32_t N;             /* number of subdomains                         */
+    int32_t overlap;       /* overlap layers                               */
+    double tau;            /* prescribed bound parameter of eq. (Zi)       */
+    int64_t n_C;           /* coarse dimension sum_i p_i                   */
+    int64_t sum_ni;        /* sum of |Omega_i|                             */
+    int64_t sum_nti;       /* sum of |tilde Omega_i|                       */
+    int32_t max_ni;        /* largest |Omega_i|                            */
+    int32_t max_nti;       /* largest |tilde Omega_i|                      */
+    int32_t sweeps_svd;    /* largest Jacobi sweep count for the SVD of X_i */
+    int32_t sweeps_eig;    /* largest Jacobi sweep count for eq. (Zi)      */
+    double setup_ms;       /* wall time of amdd_setup                      */
+} amdd_info;
+
+/* Fill `o` with the defaults (eps = 2^-52, max_sweeps = 60). */
+amdd_status amdd_opts_default(amdd_opts* o);
+
+/* y = A x (Sec. 1: the operator of A x = b).  A, x (length n) and y
+ * (length n) are device pointers; y must not alias x.  Work is issued on
+ * `stream` (cudaStream_t, may be NULL) and completed before return. */
+amdd_status amdd_spmv(const amdd_csr* A, const double* x, double* y, void* stream);
+
+/* Sec. 2.1 on the host, no GPU involved: the sets of subdomain i from a HOST
+ * CSR graph (n, rowptr[n+1], colind[rowptr[n]]) and a HOST partition
+ * part[n].  Omega_Ii = {j : part[j] == i}; Omega_Gi = unknowns at graph
+ * distance 1..overlap from Omega_Ii; Omega_Di = unknowns at distance
+ * overlap+1.  Each set is written ascending into the caller's host arrays
+ * I[capI], G[capG], D[capD] (any may be NULL to query sizes only); the sizes
+ * always go to *nI, *nG, *nD.  AMDD_ERR_INVALID if an array is too small or
+ * the graph is malformed.  amdd_setup builds its sets with the same code. */
+amdd_status amdd_overlap_sets(int64_t n, const int64_t* rowptr, const int32_t* colind, const int32_t* part,
+                              int32_t i, int32_t overlap, int32_t* I, int32_t capI, int32_t* G, int32_t capG,
+                              int32_t* D, int32_t capD, int32_t* nI, int32_t* nG, int32_t* nD);
+
+/* Build the two-level preconditioner (Sec. 2.1, Eq. (Xi), Sec. 3.2,
+ * Eq. (tildeA), Eq. (Zi), Eq. (two_level_schwarz)).
+ *   A        device CSR of the SPD matrix (copied; the caller may free it after).
+ *   part     device int32[n], part[j] in [0, N): the non-overlapping subdomain
+ *            Omega_Ij of unknown j.  Every subdomain must be non-empty.
+ *   N        number of subdomains (>= 1).
+ *   overlap  number of overlap layers (>= 1).
+ *   tau      > 0; the eigenvectors of eq. (Zi) with lambda > 1/tau are kept.
+ *   opts     NULL for defaults.
+ *   stream   cudaStream_t on which all work of the handle runs (NULL allowed).
+ *   out      receives the handle (NULL on failure).
+ * Errors: AMDD_ERR_INVALID (sizes, empty subdomain, part out of range),
+ * AMDD_ERR_NOT_SPD (non-positive pivot in a local or the coarse Cholesky),
+ * AMDD_ERR_EIG_NOCONV, AMDD_ERR_OOM, AMDD_ERR_CUDA. */
+amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_t overlap,
+                       double tau, const amdd_opts* opts, void* stream, amdd_handle** out);
+
+/* z = M^{-1} r, Eq. (two_level_schwarz), for `nrhs` vectors.  r and z are
+ * device pointers to nrhs contiguous vectors of length n (vector k at
+ * offset k*n); z must not alias r. */
+amdd_status amdd_apply(amdd_handle* h, const double* r, double* z, int32_t nrhs);
+
+/* Preconditioned conjugate gradient on A x = b with M^{-1} of
+ * Eq. (two_level_schwarz), for `nrhs` right-hand sides solved one after the
+ * other.  b and x are device pointers (nrhs contiguous vectors of length n);
+ * x holds the initial guess on entry and the solution on return.  Stops when
+ * ||r_k||_2 <= rtol ||b||_2 (recursive residual) or after maxit iterations
+ * (AMDD_ERR_NOCONV).  `stats` (host, may be NULL) describes the first
+ * right-hand side. */
+amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t nrhs,
+                           double rtol, int32_t maxit, amdd_stats* stats);
+
+/* Sizes and counters of a handle (host struct). */
+amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info);
+
+/* Sizes of subdomain i: |Omega_Ii|, |Omega_Gi|, |Omega_Di| and p_i (host out). */
+amdd_status amdd_get_subdomain(const amdd_handle* h, int32_t i, int32_t* nI, int32_t* nG,
+                               int32_t* nD, int32_t* p);
+
+/* The |Omega_Ii| non-zero eigenvalues of eq. (Zi) of subdomain i, descending,
+ * into the host array lam[cap]; +inf marks an eps-cluster eigenvalue whose
+ * computed reciprocal was not positive.  *count receives |Omega_Ii|. */
+amdd_status amdd_get_eigenvalues(const amdd_handle* h, int32_t i, double* lam, int32_t cap,
+                                 int32_t* count);
+
+/* The |Omega_i| singular values of X_i (Eq. (Xi)) of subdomain i, descending,
+ * into the host array sigma[cap]; *count receives |Omega_i|. */
+amdd_status amdd_get_singular_values(const amdd_handle* h, int32_t i, double* sigma, int32_t cap,
+                                     int32_t* count);
+
+/* The selected eigenvectors of subdomain i restricted to Omega_Ii (that is
+ * D_i Z_i on its support), as a host row-major p x nI array (row k = vector
+ * k, entries in ascending global order of Omega_Ii, A_II-orthonormal),
+ * ordered by descending lambda.  Needs cap >= p*nI. */
+amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, int64_t cap,
+                                  int32_t* p, int32_t* nI);
+
+/* Kernel-class profile of a handle created with opts.profile = 1: for class
+ * k in [0, AMDD_PROF_CLASSES) (one class per kernel; the two Jacobi solvers
+ * are separate classes), its static name, number of launches, summed device
+ * time in ms (CUDA events recorded on the handle's stream around each
+ * launch), and the algorithmic FP64 flops and DRAM bytes of those launches
+ * (flops from the operation counts of the launched work; bytes for the
+ * bandwidth-bound classes, 0 where not meaningful).  Counts accumulate over
+ * amdd_setup, amdd_apply and amdd_pcg_solve until amdd_reset_profile.
+ * Synchronises the handle's stream.  AMDD_ERR_INVALID if profiling is off or
+ * k is out of range. */
+#define AMDD_PROF_CLASSES 13
+amdd_status amdd_get_profile(amdd_handle* h, int32_t k, const char** name, int64_t* launches, double* ms,
+                             double* flops, double* bytes);
+
+/* Clear the accumulated profile (keeps profiling on). */
+amdd_status amdd_reset_profile(amdd_handle* h);
+
+/* Release every resource of the handle (NULL is a no-op). */
+void amdd_destroy(amdd_handle* h);
+
+/* Static description of a status code. */
+const char* amdd_status_str(amdd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMDD_H */

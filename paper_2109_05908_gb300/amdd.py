@@ -1,0 +1,220 @@
+"""Thin ctypes binding of libamdd (include/amdd.h): argument marshalling only.
+
+Every numerical step runs inside the CUDA library.  Device buffers are passed
+as raw pointers (for example `tensor.data_ptr()` of CUDA torch tensors, which
+is how the tests and the benchmark provide device memory and streams).  The
+library must be built (`build.build()`); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamdd.so")
+
+AMDD_OK = 0
+STATUS_NAMES = {0: "AMDD_OK", 1: "AMDD_ERR_INVALID", 2: "AMDD_ERR_NOT_SPD", 3: "AMDD_ERR_NOCONV",
+                4: "AMDD_ERR_OOM", 5: "AMDD_ERR_TIMEOUT", 6: "AMDD_ERR_CUDA", 7: "AMDD_ERR_EIG_NOCONV"}
+
+
+class amdd_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+class amdd_opts(C.Structure):
+    _fields_ = [("eps", C.c_double), ("max_sweeps", C.c_int32), ("profile", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
+
+
+class amdd_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
+                ("true_rel_residual", C.c_double), ("solve_ms", C.c_double)]
+
+
+class amdd_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("N", C.c_int32), ("overlap", C.c_int32), ("tau", C.c_double),
+                ("n_C", C.c_int64), ("sum_ni", C.c_int64), ("sum_nti", C.c_int64), ("max_ni", C.c_int32),
+                ("max_nti", C.c_int32), ("sweeps_svd", C.c_int32), ("sweeps_eig", C.c_int32),
+                ("setup_ms", C.c_double)]
+
+
+class AmddError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({status_str(status)})")
+        self.status = status
+
+
+_lib = None
+
+# exported symbol -> (restype, argtypes)
+SIGNATURES = {
+    "amdd_opts_default": (C.c_int, [C.POINTER(amdd_opts)]),
+    "amdd_spmv": (C.c_int, [C.POINTER(amdd_csr), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "amdd_setup": (C.c_int, [C.POINTER(amdd_csr), C.c_void_p, C.c_int32, C.c_int32, C.c_double,
+                             C.POINTER(amdd_opts), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "amdd_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "amdd_pcg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32,
+                                 C.POINTER(amdd_stats)]),
+    "amdd_get_info": (C.c_int, [C.c_void_p, C.POINTER(amdd_info)]),
+    "amdd_get_subdomain": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "amdd_get_eigenvalues": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "amdd_get_singular_values": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
+                                           C.POINTER(C.c_int32)]),
+    "amdd_get_coarse_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int32)]),
+    "amdd_overlap_sets": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                    C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "amdd_get_profile": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "amdd_reset_profile": (C.c_int, [C.c_void_p]),
+    "amdd_destroy": (None, [C.c_void_p]),
+    "amdd_status_str": (C.c_char_p, [C.c_int]),
+}
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libamdd.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_str(st: int) -> str:
+    return lib().amdd_status_str(int(st)).decode()
+
+
+def _check(st: int, where: str, allow=()):
+    if st != AMDD_OK and st not in allow:
+        raise AmddError(st, where)
+    return st
+
+
+def opts_default() -> amdd_opts:
+    o = amdd_opts()
+    _check(lib().amdd_opts_default(C.byref(o)), "amdd_opts_default")
+    return o
+
+
+def make_csr(n: int, nnz: int, rowptr_ptr: int, colind_ptr: int, val_ptr: int) -> amdd_csr:
+    return amdd_csr(n, nnz, rowptr_ptr, colind_ptr, val_ptr)
+
+
+def spmv(A: amdd_csr, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    _check(lib().amdd_spmv(C.byref(A), x_ptr, y_ptr, stream), "amdd_spmv")
+
+
+def setup(A: amdd_csr, part_ptr: int, N: int, overlap: int, tau: float, opts: amdd_opts | None = None,
+          stream: int = 0) -> int:
+    h = C.c_void_p()
+    st = lib().amdd_setup(C.byref(A), part_ptr, N, overlap, float(tau), C.byref(opts) if opts else None,
+                          stream, C.byref(h))
+    _check(st, "amdd_setup")
+    return h.value
+
+
+def apply(h: int, r_ptr: int, z_ptr: int, nrhs: int = 1) -> None:
+    _check(lib().amdd_apply(h, r_ptr, z_ptr, nrhs), "amdd_apply")
+
+
+def pcg_solve(h: int, b_ptr: int, x_ptr: int, nrhs: int = 1, rtol: float = 1e-8, maxit: int = 1000,
+              allow_noconv: bool = False) -> amdd_stats:
+    s = amdd_stats()
+    _check(lib().amdd_pcg_solve(h, b_ptr, x_ptr, nrhs, float(rtol), maxit, C.byref(s)), "amdd_pcg_solve",
+           allow=(3,) if allow_noconv else ())
+    return s
+
+
+def get_info(h: int) -> amdd_info:
+    info = amdd_info()
+    _check(lib().amdd_get_info(h, C.byref(info)), "amdd_get_info")
+    return info
+
+
+def get_subdomain(h: int, i: int):
+    a, b, c, p = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().amdd_get_subdomain(h, i, C.byref(a), C.byref(b), C.byref(c), C.byref(p)), "amdd_get_subdomain")
+    return a.value, b.value, c.value, p.value
+
+
+def get_eigenvalues(h: int, i: int):
+    import numpy as np
+    cnt = C.c_int32()
+    _check(lib().amdd_get_eigenvalues(h, i, None, 0, C.byref(cnt)), "amdd_get_eigenvalues")
+    out = np.empty(cnt.value, dtype=np.float64)
+    _check(lib().amdd_get_eigenvalues(h, i, out.ctypes.data, cnt.value, C.byref(cnt)), "amdd_get_eigenvalues")
+    return out
+
+
+def get_singular_values(h: int, i: int):
+    import numpy as np
+    cnt = C.c_int32()
+    _check(lib().amdd_get_singular_values(h, i, None, 0, C.byref(cnt)), "amdd_get_singular_values")
+    out = np.empty(cnt.value, dtype=np.float64)
+    _check(lib().amdd_get_singular_values(h, i, out.ctypes.data, cnt.value, C.byref(cnt)),
+           "amdd_get_singular_values")
+    return out
+
+
+def get_coarse_block(h: int, i: int):
+    import numpy as np
+    p, nI = C.c_int32(), C.c_int32()
+    _check(lib().amdd_get_coarse_block(h, i, None, 0, C.byref(p), C.byref(nI)), "amdd_get_coarse_block")
+    out = np.empty((p.value, nI.value), dtype=np.float64)
+    if out.size:
+        _check(lib().amdd_get_coarse_block(h, i, out.ctypes.data, out.size, C.byref(p), C.byref(nI)),
+               "amdd_get_coarse_block")
+    return out
+
+
+def overlap_sets(n, rowptr, colind, part, i: int, overlap: int):
+    """Host-only Sec. 2.1 sets of subdomain i from host numpy arrays
+    (rowptr int64, colind int32, part int32); returns (I, G, D)."""
+    import numpy as np
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    args = (n, rowptr.ctypes.data, colind.ctypes.data, part.ctypes.data, i, overlap)
+    _check(lib().amdd_overlap_sets(*args, None, 0, None, 0, None, 0, C.byref(a), C.byref(b), C.byref(c)),
+           "amdd_overlap_sets")
+    I = np.empty(a.value, np.int32)
+    G = np.empty(b.value, np.int32)
+    D = np.empty(c.value, np.int32)
+    _check(lib().amdd_overlap_sets(*args, I.ctypes.data, a.value, G.ctypes.data, b.value, D.ctypes.data, c.value,
+                                   C.byref(a), C.byref(b), C.byref(c)), "amdd_overlap_sets")
+    return I, G, D
+
+
+PROF_CLASSES = 13
+
+
+def get_profile(h: int):
+    """List of dicts (name, launches, ms, flops, bytes), one per kernel class."""
+    out = []
+    for k in range(PROF_CLASSES):
+        name, n, ms, fl, by = C.c_char_p(), C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+        _check(lib().amdd_get_profile(h, k, C.byref(name), C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)),
+               "amdd_get_profile")
+        out.append(dict(name=name.value.decode(), launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value))
+    return out
+
+
+def reset_profile(h: int) -> None:
+    _check(lib().amdd_reset_profile(h), "amdd_reset_profile")
+
+
+def destroy(h: int) -> None:
+    if h:
+        lib().amdd_destroy(h)

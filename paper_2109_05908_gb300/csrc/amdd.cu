@@ -1,0 +1,1308 @@
+// Host side of libamdd: the C ABI declared in amdd.h, the integer part of the
+// setup (subdomain sets of Sec. 2.1 and the gather plans), the orchestration
+// of the batched setup kernels (Eq. (Xi), Sec. 3.2, Eq. (tildeA), Eq. (Zi),
+// Eq. (two_level_schwarz)) and the preconditioned conjugate gradient.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "amdd.h"
+#include "amdd_internal.h"
+
+using namespace amdd;
+
+namespace {
+
+struct Fail {
+    amdd_status st;
+};
+
+inline void ck(cudaError_t e) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Fail{e == cudaErrorMemoryAllocation ? AMDD_ERR_OOM : AMDD_ERR_CUDA};
+    }
+}
+
+inline void require(bool ok) {
+    if (!ok) throw Fail{AMDD_ERR_INVALID};
+}
+
+}  // namespace
+
+// Kernel classes of the profile (one per kernel; the Jacobi solver split by use).
+enum ProfK {
+    PK_GATHER,
+    PK_CHOL_DIAG,
+    PK_CHOL_PANEL,
+    PK_GEMM,
+    PK_TRTRI,
+    PK_JAC_SVD,
+    PK_JAC_EIG,
+    PK_SMALL,
+    PK_E_ASM,
+    PK_SPMV,
+    PK_GEMV,
+    PK_GATHER_SCATTER,
+    PK_PCG_VEC,
+    PK_COUNT
+};
+static_assert(PK_COUNT == AMDD_PROF_CLASSES, "profile classes");
+static const char* const kProfNames[PK_COUNT] = {
+    "gather_values", "chol_diag", "chol_panel", "gemm_tiles", "trtri_diag", "jacobi_svd", "jacobi_eig",
+    "small_dense", "e_offdiag", "spmv", "gemv_rows", "gather_scatter", "pcg_vectors"};
+
+struct ProfState {
+    bool on = false;
+    int64_t launches[PK_COUNT] = {};
+    double flops[PK_COUNT] = {};
+    double bytes[PK_COUNT] = {};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PK_COUNT];
+    void clear() {
+        for (int k = 0; k < PK_COUNT; ++k) {
+            for (auto& e : ev[k]) {
+                cudaEventDestroy(e.first);
+                cudaEventDestroy(e.second);
+            }
+            ev[k].clear();
+            launches[k] = 0;
+            flops[k] = 0.0;
+            bytes[k] = 0.0;
+        }
+    }
+};
+
+struct amdd_handle {
+    cudaStream_t s = nullptr;
+    ProfState prof;
+    int64_t n = 0, nnz = 0;
+    int N = 0, overlap = 0;
+    double tau = 0.0, eps = 0.0;
+    int max_sweeps = 60;
+    int spmv_group = 4;
+    // copy of A
+    int64_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    // per-subdomain sizes
+    std::vector<int32_t> nI, nG, nD, ni, nt, p;
+    std::vector<int64_t> off_om, off_sq, off_zt, off_I, coff;
+    int64_t sum_ni = 0, sum_sq = 0, sum_nI = 0, sum_nt = 0, nC = 0, sum_zt = 0;
+    int max_ni = 0, max_nt = 0;
+    int64_t apply_tri_elems = 0;  // sum_i ni (ni + 1): elements read by the two local triangular products
+    // persistent device data of the apply
+    int32_t* d_omega = nullptr;
+    double* d_Y = nullptr;
+    double* d_Yt = nullptr;
+    double* d_Zt = nullptr;
+    double* d_YE = nullptr;
+    double* d_YEt = nullptr;
+    GemvDesc* d_gv_l1 = nullptr;
+    GemvDesc* d_gv_l2 = nullptr;
+    GemvDesc* d_gv_c = nullptr;
+    GemvDesc* d_gv_e1 = nullptr;
+    GemvDesc* d_gv_e2 = nullptr;
+    int32_t *d_rd_loc = nullptr, *d_rl_loc = nullptr, *d_rd_c = nullptr, *d_rl_c = nullptr;
+    int32_t *d_rd_e = nullptr, *d_rl_e = nullptr;
+    int32_t *d_order_g = nullptr, *d_own_sub = nullptr, *d_own_a = nullptr, *d_sc_idx = nullptr;
+    int32_t *d_nI = nullptr, *d_p = nullptr;
+    int64_t *d_sc_ptr = nullptr, *d_zt_off = nullptr, *d_coff = nullptr;
+    double *d_rloc = nullptr, *d_tloc = nullptr, *d_yloc = nullptr;
+    double *d_c = nullptr, *d_ct = nullptr, *d_e = nullptr;
+    // PCG work vectors
+    double *d_r = nullptr, *d_z = nullptr, *d_pv = nullptr, *d_q = nullptr, *d_part = nullptr;
+    PcgScal* d_sc = nullptr;
+    int* d_err = nullptr;
+    // host results
+    std::vector<double> sigma_h;  // singular values of X_i, descending, at off_om
+    std::vector<double> lam_h;    // eigenvalues of eq. (Zi), descending, at off_I
+    int sweeps_svd = 0, sweeps_eig = 0;
+    double setup_ms = 0.0;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+// Stream-ordered allocation owned by the handle (freed by amdd_destroy).
+template <class T>
+T* dnew(amdd_handle* h, size_t count) {
+    void* p = nullptr;
+    ck(cudaMallocAsync(&p, std::max<size_t>(count, 1) * sizeof(T), h->s));
+    h->allocs.push_back(p);
+    return static_cast<T*>(p);
+}
+
+// Records CUDA events around one launch of kernel class k on the handle's
+// stream when profiling is on, and accounts its algorithmic flops / bytes.
+struct PScope {
+    amdd_handle* h;
+    int k;
+    cudaEvent_t b = nullptr;
+    PScope(amdd_handle* hh, int kk, double flops = 0.0, double bytes = 0.0) : h(hh), k(kk) {
+        if (!h->prof.on) return;
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            b = nullptr;
+            return;
+        }
+        cudaEventRecord(b, h->s);
+        h->prof.launches[k] += 1;
+        h->prof.flops[k] += flops;
+        h->prof.bytes[k] += bytes;
+    }
+    ~PScope() {
+        if (!b) return;
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaEventDestroy(b);
+            return;
+        }
+        cudaEventRecord(e, h->s);
+        h->prof.ev[k].push_back({b, e});
+    }
+};
+
+// Setup-lifetime context: temporary device buffers and the host arrays that
+// back asynchronous uploads are kept until the final synchronisation.
+struct Ctx {
+    amdd_handle* h;
+    std::vector<void*> temps;
+    std::vector<std::shared_ptr<void>> keep;
+    explicit Ctx(amdd_handle* hh) : h(hh) {}
+    ~Ctx() {
+        for (void* p : temps) cudaFreeAsync(p, h->s);
+    }
+    template <class T>
+    T* tnew(size_t count) {
+        void* p = nullptr;
+        ck(cudaMallocAsync(&p, std::max<size_t>(count, 1) * sizeof(T), h->s));
+        temps.push_back(p);
+        return static_cast<T*>(p);
+    }
+    template <class T>
+    T* up(const std::vector<T>& v, bool persistent = false) {
+        T* d = persistent ? dnew<T>(h, v.size()) : tnew<T>(v.size());
+        if (!v.empty()) {
+            auto copy = std::make_shared<std::vector<T>>(v);
+            ck(cudaMemcpyAsync(d, copy->data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->s));
+            keep.push_back(copy);
+        }
+        return d;
+    }
+};
+
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+void gemm(Ctx& C, const std::vector<GemmDesc>& ds) {
+    std::vector<TileRef> tiles;
+    for (int d = 0; d < (int)ds.size(); ++d) {
+        const GemmDesc& g = ds[d];
+        if (g.m <= 0 || g.n <= 0) continue;
+        const int tm = cdiv(g.m, GEMM_T), tn = cdiv(g.n, GEMM_T);
+        for (int a = 0; a < tm; ++a)
+            for (int b = 0; b < tn; ++b) {
+                if (g.lower && b > a) continue;
+                tiles.push_back({d, a, b});
+            }
+    }
+    if (tiles.empty()) return;
+    double fl = 0.0;
+    for (const GemmDesc& g : ds) {
+        if (g.m <= 0 || g.n <= 0) continue;
+        const double m = g.m, n = g.n;
+        const double outs = g.lower ? (n <= m ? m * n - n * (n - 1) / 2 : m * (m + 1) / 2) : m * n;
+        fl += 2.0 * outs * g.k;
+    }
+    const GemmDesc* dd = C.up(ds);
+    const TileRef* dt = C.up(tiles);
+    PScope ps(C.h, PK_GEMM, fl);
+    launch_gemm(dd, dt, (int)tiles.size(), C.h->s);
+}
+
+GemmDesc gd(const double* A, int lda, int ta, const double* B, int ldb, int tb, double* Cm, int ldc, int m, int n,
+            int k, double alpha, double beta, int lower) {
+    GemmDesc g;
+    g.A = A;
+    g.B = B;
+    g.C = Cm;
+    g.m = m;
+    g.n = n;
+    g.k = k;
+    g.lda = lda;
+    g.ldb = ldb;
+    g.ldc = ldc;
+    g.ta = ta;
+    g.tb = tb;
+    g.lower = lower;
+    g.kfrom_row = 0;
+    g.alpha = alpha;
+    g.beta = beta;
+    return g;
+}
+
+// Blocked right-looking Cholesky of a batch of matrices (lower triangles),
+// each stopped at its own column `stop` (the trailing block then holds the
+// Schur complement of the factored leading block).
+void chol_batched(Ctx& C, const std::vector<CholDesc>& ds) {
+    if (ds.empty()) return;
+    amdd_handle* h = C.h;
+    CholDesc* dd = C.up(ds);
+    int maxstop = 0;
+    for (const auto& d : ds) maxstop = std::max(maxstop, d.stop);
+    for (int k0 = 0; k0 < maxstop; k0 += CHOL_NB) {
+        {
+            double fl = 0.0;
+            for (const auto& c : ds)
+                if (k0 < c.stop) {
+                    const double kb = std::min(k0 + CHOL_NB, c.stop) - k0;
+                    fl += 2.0 * kb * kb * kb / 3.0;
+                }
+            PScope ps(h, PK_CHOL_DIAG, fl);
+            launch_chol_diag(dd, (int)ds.size(), k0, h->d_err, h->s);
+        }
+        std::vector<PanelRef> pt;
+        double pfl = 0.0;
+        std::vector<GemmDesc> g;
+        for (int d = 0; d < (int)ds.size(); ++d) {
+            const CholDesc& c = ds[d];
+            if (k0 >= c.stop) continue;
+            const int kend = std::min(k0 + CHOL_NB, c.stop);
+            const int rows = c.n - kend;
+            if (rows <= 0) continue;
+            for (int rt = 0; rt * 64 < rows; ++rt) pt.push_back({d, rt});
+            pfl += (double)rows * (kend - k0) * (kend - k0 + 1);
+            double* panel = c.A + (size_t)kend * c.ld + k0;
+            g.push_back(gd(panel, c.ld, 0, panel, c.ld, 1, c.A + (size_t)kend * c.ld + kend, c.ld, rows, rows,
+                           kend - k0, -1.0, 1.0, 1));
+        }
+        if (!pt.empty()) {
+            const PanelRef* dpt = C.up(pt);
+            PScope ps(h, PK_CHOL_PANEL, pfl);
+            launch_chol_panel(dd, dpt, (int)pt.size(), k0, h->s);
+        }
+        gemm(C, g);
+    }
+}
+
+// Y = L^{-1} (lower triangular) for a batch, from the factors and the
+// diagonal-block inverses left by chol_batched.
+void trtri_batched(Ctx& C, const std::vector<TrtriDesc>& ds) {
+    if (ds.empty()) return;
+    amdd_handle* h = C.h;
+    TrtriDesc* dd = C.up(ds);
+    int maxn = 0;
+    for (const auto& d : ds) maxn = std::max(maxn, d.n);
+    {
+        PScope ps(h, PK_SMALL);
+        launch_set_identity(dd, (int)ds.size(), maxn, h->s);
+    }
+    for (int k0 = 0; k0 < maxn; k0 += CHOL_NB) {
+        std::vector<ChunkRef> ch;
+        std::vector<GemmDesc> g;
+        double fl = 0.0;
+        for (int d = 0; d < (int)ds.size(); ++d) {
+            const TrtriDesc& t = ds[d];
+            if (k0 >= t.n) continue;
+            const int kend = std::min(k0 + CHOL_NB, t.n);
+            for (int ct = 0; ct * 64 < kend; ++ct) ch.push_back({d, ct});
+            fl += (double)kend * (kend - k0) * (kend - k0 + 1);
+            if (kend < t.n)
+                g.push_back(gd(t.L + (size_t)kend * t.ld + k0, t.ld, 0, t.Y + (size_t)k0 * t.ldy, t.ldy, 0,
+                               t.Y + (size_t)kend * t.ldy, t.ldy, t.n - kend, kend, kend - k0, -1.0, 1.0, 0));
+        }
+        {
+            const ChunkRef* dch = C.up(ch);
+            PScope ps(h, PK_TRTRI, fl);
+            launch_trtri_diag(dd, dch, (int)ch.size(), k0, h->s);
+        }
+        gemm(C, g);
+    }
+}
+
+void transpose_batched(Ctx& C, const std::vector<const double*>& src, const std::vector<double*>& dst,
+                       const std::vector<int>& n, const std::vector<int>& lds, const std::vector<int>& ldd) {
+    if (src.empty()) return;
+    int maxn = *std::max_element(n.begin(), n.end());
+    auto a = C.up(src);
+    auto b = C.up(dst);
+    auto c = C.up(n);
+    auto d = C.up(lds);
+    auto e = C.up(ldd);
+    PScope ps(C.h, PK_SMALL);
+    launch_transpose(a, b, c, d, e, (int)src.size(), maxn, C.h->s);
+}
+
+int read_err(amdd_handle* h) {
+    int e = 0;
+    ck(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    ck(cudaStreamSynchronize(h->s));
+    return e;
+}
+
+amdd_status err_status(int e) {
+    if (e & DERR_NOT_SPD) return AMDD_ERR_NOT_SPD;
+    if (e & DERR_EIG_NOCONV) return AMDD_ERR_EIG_NOCONV;
+    if (e) return AMDD_ERR_CUDA;
+    return AMDD_OK;
+}
+
+// Sec. 2.1: Omega_Gi = nodes at graph distance 1..ov from Omega_Ii (ascending)
+// and Omega_Di = nodes at distance ov+1 (ascending), by breadth-first layers
+// on the CSR graph.  `mark` (length n) is a scratch stamp array: entries equal
+// to `stamp` are treated as already reached; on return every node of
+// Omega_Ii, Omega_Gi and Omega_Di carries `stamp`.
+void overlap_layers(const int64_t* rp, const int32_t* ci, const std::vector<int32_t>& I, int ov, int32_t stamp,
+                    int32_t* mark, std::vector<int32_t>& G, std::vector<int32_t>& D) {
+    for (int32_t g : I) mark[g] = stamp;
+    std::vector<int32_t> frontier = I;
+    G.clear();
+    D.clear();
+    for (int d = 1; d <= ov + 1; ++d) {
+        std::vector<int32_t> nw;
+        for (int32_t v : frontier)
+            for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+                const int32_t c = ci[k];
+                if (mark[c] != stamp) {
+                    mark[c] = stamp;
+                    nw.push_back(c);
+                }
+            }
+        std::sort(nw.begin(), nw.end());
+        if (d <= ov)
+            G.insert(G.end(), nw.begin(), nw.end());
+        else
+            D = nw;
+        frontier.swap(nw);
+    }
+    std::sort(G.begin(), G.end());
+}
+
+// ---------------------------------------------------------------------------
+// Setup
+// ---------------------------------------------------------------------------
+void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
+    const int64_t n = A->n, nnz = A->nnz;
+    const int N = h->N, ov = h->overlap;
+    cudaStream_t s = h->s;
+    Ctx C(h);
+
+    h->d_err = dnew<int>(h, 1);
+    ck(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+    h->rowptr = dnew<int64_t>(h, n + 1);
+    h->col = dnew<int32_t>(h, nnz);
+    h->val = dnew<double>(h, nnz);
+    ck(cudaMemcpyAsync(h->rowptr, A->rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    ck(cudaMemcpyAsync(h->col, A->colind, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    ck(cudaMemcpyAsync(h->val, A->val, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+
+    // ---- host copies of the graph and the partition (integer setup, Sec. 2.1)
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int32_t> ci(nnz), part(n);
+    ck(cudaMemcpyAsync(rp.data(), A->rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(ci.data(), A->colind, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(part.data(), d_part, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    require(rp[0] == 0 && rp[n] == nnz);
+    for (int64_t r = 0; r < n; ++r) require(rp[r] <= rp[r + 1]);
+    for (int64_t k = 0; k < nnz; ++k) require(ci[k] >= 0 && ci[k] < n);
+    std::vector<std::vector<int32_t>> Il(N);
+    for (int64_t g = 0; g < n; ++g) {
+        require(part[g] >= 0 && part[g] < N);
+        Il[part[g]].push_back((int32_t)g);
+    }
+    for (int i = 0; i < N; ++i) require(!Il[i].empty());
+    h->spmv_group = (nnz / std::max<int64_t>(n, 1) <= 8) ? 4 : (nnz / std::max<int64_t>(n, 1) <= 24 ? 8 : 32);
+
+    // ---- overlap Omega_Gi (distance 1..ov) and extension Omega_Di (ov+1)
+    std::vector<std::vector<int32_t>> Gl(N), Dl(N);
+    {
+        std::vector<int32_t> mark(n, -1);
+        for (int i = 0; i < N; ++i) overlap_layers(rp.data(), ci.data(), Il[i], ov, i, mark.data(), Gl[i], Dl[i]);
+    }
+
+    // ---- sizes and offsets
+    h->nI.resize(N);
+    h->nG.resize(N);
+    h->nD.resize(N);
+    h->ni.resize(N);
+    h->nt.resize(N);
+    h->off_om.assign(N + 1, 0);
+    h->off_sq.assign(N + 1, 0);
+    h->off_I.assign(N + 1, 0);
+    std::vector<int64_t> off_x(N + 1, 0), off_m(N + 1, 0), off_ti(N + 1, 0), off_P(N + 1, 0), off_la(N + 1, 0),
+        off_lm(N + 1, 0);
+    for (int i = 0; i < N; ++i) {
+        const int a = (int)Il[i].size(), b = (int)Gl[i].size(), c = (int)Dl[i].size();
+        h->nI[i] = a;
+        h->nG[i] = b;
+        h->nD[i] = c;
+        h->ni[i] = a + b;
+        h->nt[i] = a + b + c;
+        const int64_t ni = a + b, nt = a + b + c, nR = b + c;
+        h->off_om[i + 1] = h->off_om[i] + ni;
+        h->off_sq[i + 1] = h->off_sq[i] + ni * ni;
+        h->off_I[i + 1] = h->off_I[i] + a;
+        off_x[i + 1] = off_x[i] + ni * nt;
+        off_m[i + 1] = off_m[i] + nt * nt;
+        off_ti[i + 1] = off_ti[i] + (int64_t)a * 2 * a;
+        off_P[i + 1] = off_P[i] + (int64_t)a * a;
+        off_la[i + 1] = off_la[i] + (int64_t)cdiv(ni, CHOL_NB) * CHOL_NB * CHOL_NB;
+        off_lm[i + 1] = off_lm[i] + (int64_t)cdiv(nR, CHOL_NB) * CHOL_NB * CHOL_NB;
+        h->max_ni = std::max<int>(h->max_ni, (int)ni);
+        h->max_nt = std::max<int>(h->max_nt, (int)nt);
+    }
+    h->sum_ni = h->off_om[N];
+    h->sum_sq = h->off_sq[N];
+    h->sum_nI = h->off_I[N];
+    h->sum_nt = 0;
+    for (int i = 0; i < N; ++i) {
+        h->sum_nt += h->nt[i];
+        h->apply_tri_elems += (int64_t)h->ni[i] * (h->ni[i] + 1);
+    }
+
+    // ---- gather plans for A_ii = R_i A R_i^T (order [I, G]) and for
+    // X_i = R_i A tilde R_i^T with columns ordered [G, D, I] (Eq. (Xi)).
+    std::vector<int32_t> omega(h->sum_ni);
+    std::vector<int64_t> pa_src, pa_dst, px_src, px_dst;
+    {
+        std::vector<int32_t> stamp(n, -1), posA(n, -1), posX(n, -1);
+        for (int i = 0; i < N; ++i) {
+            const int nIi = h->nI[i], nGi = h->nG[i], ni = h->ni[i], nt = h->nt[i];
+            const int nR = nGi + h->nD[i];
+            int32_t* om = omega.data() + h->off_om[i];
+            for (int a = 0; a < nIi; ++a) {
+                const int32_t g = Il[i][a];
+                om[a] = g;
+                stamp[g] = i;
+                posA[g] = a;
+                posX[g] = nR + a;
+            }
+            for (int b = 0; b < nGi; ++b) {
+                const int32_t g = Gl[i][b];
+                om[nIi + b] = g;
+                stamp[g] = i;
+                posA[g] = nIi + b;
+                posX[g] = b;
+            }
+            for (int c = 0; c < h->nD[i]; ++c) {
+                const int32_t g = Dl[i][c];
+                stamp[g] = i;
+                posA[g] = -1;
+                posX[g] = nGi + c;
+            }
+            for (int a = 0; a < ni; ++a) {
+                const int32_t g = om[a];
+                for (int64_t k = rp[g]; k < rp[g + 1]; ++k) {
+                    const int32_t c = ci[k];
+                    require(stamp[c] == i);  // every column of a row of Omega_i lies in tilde Omega_i
+                    if (posA[c] >= 0) {
+                        pa_src.push_back(k);
+                        pa_dst.push_back(h->off_sq[i] + (int64_t)a * ni + posA[c]);
+                    }
+                    px_src.push_back(k);
+                    px_dst.push_back(off_x[i] + (int64_t)a * nt + posX[c]);
+                }
+            }
+        }
+    }
+
+    // ---- device buffers
+    h->d_omega = C.up(omega, true);
+    double* Araw = C.tnew<double>(h->sum_sq);
+    double* Lb = C.tnew<double>(h->sum_sq);
+    double* Xp = C.tnew<double>(off_x[N]);
+    double* M = C.tnew<double>(off_m[N]);
+    double* TI = C.tnew<double>(off_ti[N]);
+    double* Pb = C.tnew<double>(off_P[N]);
+    double* sig = C.tnew<double>(h->sum_ni);
+    double* mu = C.tnew<double>(h->sum_nI);
+    double* delta = C.tnew<double>(N);
+    double* linvA = C.tnew<double>(off_la[N]);
+    double* linvM = C.tnew<double>(off_lm[N]);
+    int* sweeps = C.tnew<int>(2 * N);
+    unsigned long long* rots = C.tnew<unsigned long long>(2 * N);
+    ck(cudaMemsetAsync(rots, 0, 2 * N * sizeof(unsigned long long), s));
+    h->d_Y = dnew<double>(h, h->sum_sq);
+    h->d_Yt = dnew<double>(h, h->sum_sq);
+    ck(cudaMemsetAsync(Araw, 0, h->sum_sq * sizeof(double), s));
+    ck(cudaMemsetAsync(Xp, 0, off_x[N] * sizeof(double), s));
+    {
+        const int64_t* sa = C.up(pa_src);
+        const int64_t* da = C.up(pa_dst);
+        const int64_t* sx = C.up(px_src);
+        const int64_t* dx = C.up(px_dst);
+        {
+            PScope ps(h, PK_GATHER, 0.0, 32.0 * pa_src.size());
+            launch_gather_values(sa, da, (int64_t)pa_src.size(), h->val, Araw, s);
+        }
+        {
+            PScope ps(h, PK_GATHER, 0.0, 32.0 * px_src.size());
+            launch_gather_values(sx, dx, (int64_t)px_src.size(), h->val, Xp, s);
+        }
+    }
+    ck(cudaMemcpyAsync(Lb, Araw, h->sum_sq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+
+    // ---- (1) exact Cholesky of A_ii (local solver) and its inverse factor
+    {
+        std::vector<CholDesc> cd(N);
+        std::vector<TrtriDesc> td(N);
+        std::vector<const double*> src(N);
+        std::vector<double*> dst(N);
+        std::vector<int> nn(N), ld(N);
+        for (int i = 0; i < N; ++i) {
+            const int ni = h->ni[i];
+            cd[i] = {Lb + h->off_sq[i], ni, ni, ni, nullptr, linvA + off_la[i]};
+            td[i] = {Lb + h->off_sq[i], h->d_Y + h->off_sq[i], linvA + off_la[i], ni, ni, ni};
+            src[i] = h->d_Y + h->off_sq[i];
+            dst[i] = h->d_Yt + h->off_sq[i];
+            nn[i] = ni;
+            ld[i] = ni;
+        }
+        chol_batched(C, cd);
+        trtri_batched(C, td);
+        transpose_batched(C, src, dst, nn, ld, ld);
+    }
+
+    // ---- (2) SVD of X_i by one-sided Jacobi on its rows (Sec. 3.2): rows
+    // become sigma_j v_j^T; sigma_j = row norms; rows scaled by sigma_j^{-1/2}.
+    const double eps = h->eps;
+    {
+        std::vector<JacobiDesc> jd(N);
+        std::vector<double*> sp(N);
+        int maxc = 1;
+        for (int i = 0; i < N; ++i) {
+            jd[i] = {Xp + off_x[i], h->ni[i], h->nt[i], h->nt[i], h->nt[i]};
+            sp[i] = sig + h->off_om[i];
+            maxc = std::max(maxc, h->nt[i]);
+        }
+        JacobiDesc* djd = C.up(jd);
+        double* const* dsp = C.up(sp);
+        {
+            PScope ps(h, PK_JAC_SVD);
+            launch_jacobi(djd, N, h->max_sweeps, std::numeric_limits<double>::epsilon() * maxc, sweeps, rots,
+                          h->d_err, s);
+        }
+        PScope ps(h, PK_SMALL);
+        launch_rownorms(djd, N, dsp, delta, eps, 1, s);
+    }
+
+    // ---- (3) Abar_ii = C^T diag(1/sigma) C + sigma_1 eps I, ordered [G, D, I]
+    {
+        std::vector<GemmDesc> g(N);
+        std::vector<double*> mats(N);
+        std::vector<int> nn(N), ld(N);
+        for (int i = 0; i < N; ++i) {
+            const int ni = h->ni[i], nt = h->nt[i];
+            double* Xi = Xp + off_x[i];
+            g[i] = gd(Xi, nt, 1, Xi, nt, 0, M + off_m[i], nt, nt, nt, ni, 1.0, 0.0, 1);
+            mats[i] = M + off_m[i];
+            nn[i] = nt;
+            ld[i] = nt;
+        }
+        gemm(C, g);
+        auto a = C.up(mats);
+        auto b = C.up(nn);
+        auto c = C.up(ld);
+        PScope ps(h, PK_SMALL);
+        launch_add_diag(a, b, c, delta, N, h->max_nt, s);
+    }
+
+    // ---- (4) Schur complement of Abar_ii onto Omega_Ii: Cholesky of the
+    // leading [G, D] block (pivot floor sigma_1 eps, the shift of Remark 3.2).
+    {
+        std::vector<CholDesc> cd(N);
+        for (int i = 0; i < N; ++i) {
+            const int nt = h->nt[i], nR = h->nG[i] + h->nD[i];
+            cd[i] = {M + off_m[i], nt, nt, nR, delta + i, linvM + off_lm[i]};
+        }
+        chol_batched(C, cd);
+    }
+
+    // ---- (5) T = L_A^{-1} S L_A^{-T} (L_A = Cholesky factor of A_II, the
+    // leading block of that of A_ii), appended identity for the rotations.
+    {
+        std::vector<double*> mats(N);
+        std::vector<int> nn(N), ld(N);
+        std::vector<GemmDesc> g1(N), g2(N);
+        std::vector<TrtriDesc> idd(N);
+        for (int i = 0; i < N; ++i) {
+            const int nIi = h->nI[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], ni = h->ni[i];
+            double* S = M + off_m[i] + (size_t)nR * nt + nR;
+            mats[i] = S;
+            nn[i] = nIi;
+            ld[i] = nt;
+            const double* Y = h->d_Y + h->off_sq[i];
+            g1[i] = gd(Y, ni, 0, S, nt, 0, Pb + off_P[i], nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
+            g2[i] = gd(Pb + off_P[i], nIi, 0, Y, ni, 1, TI + off_ti[i], 2 * nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
+            idd[i] = {nullptr, TI + off_ti[i] + nIi, nullptr, nIi, 0, 2 * nIi};
+        }
+        {
+            auto a = C.up(mats);
+            auto b = C.up(nn);
+            auto c = C.up(ld);
+            PScope ps(h, PK_SMALL);
+            launch_mirror_lower(a, b, c, N, h->max_nt, s);
+        }
+        gemm(C, g1);
+        gemm(C, g2);
+        auto di = C.up(idd);
+        PScope ps(h, PK_SMALL);
+        launch_set_identity(di, N, h->max_nt, s);
+    }
+
+    // ---- (6) eigenvalues mu = 1/lambda of eq. (Zi) by one-sided Jacobi on
+    // the rows of [T | I]: rows of the left half become mu_j w_j^T, the right
+    // half accumulates the eigenvectors w_j.
+    {
+        std::vector<JacobiDesc> jd(N);
+        std::vector<double*> mp(N);
+        int maxc = 1;
+        for (int i = 0; i < N; ++i) {
+            const int nIi = h->nI[i];
+            jd[i] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi};
+            mp[i] = mu + h->off_I[i];
+            maxc = std::max(maxc, nIi);
+        }
+        JacobiDesc* djd = C.up(jd);
+        double* const* dmp = C.up(mp);
+        {
+            PScope ps(h, PK_JAC_EIG);
+            launch_jacobi(djd, N, h->max_sweeps, std::numeric_limits<double>::epsilon() * maxc, sweeps + N,
+                          rots + N, h->d_err, s);
+        }
+        PScope ps(h, PK_SMALL);
+        launch_rownorms(djd, N, dmp, nullptr, 0.0, 0, s);
+    }
+
+    // ---- (7) selection lambda > 1/tau on the host
+    std::vector<double> mu_h(h->sum_nI);
+    std::vector<int> sw(2 * N);
+    std::vector<unsigned long long> rot_h(2 * N);
+    h->sigma_h.resize(h->sum_ni);
+    ck(cudaMemcpyAsync(rot_h.data(), rots, 2 * N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(mu_h.data(), mu, h->sum_nI * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(h->sigma_h.data(), sig, h->sum_ni * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(sw.data(), sweeps, 2 * N * sizeof(int), cudaMemcpyDeviceToHost, s));
+    {
+        const int e = read_err(h);
+        if (e) throw Fail{err_status(e)};
+    }
+    for (int i = 0; i < N; ++i) {
+        h->sweeps_svd = std::max(h->sweeps_svd, sw[i]);
+        h->sweeps_eig = std::max(h->sweeps_eig, sw[N + i]);
+        if (h->prof.on) {
+            // inner products of every pair in every sweep, plus the rotations performed
+            const double ni = h->ni[i], nt = h->nt[i], nIi = h->nI[i];
+            h->prof.flops[PK_JAC_SVD] += sw[i] * ni * (ni - 1) / 2 * 6.0 * nt + rot_h[i] * 6.0 * nt;
+            h->prof.flops[PK_JAC_EIG] += sw[N + i] * nIi * (nIi - 1) / 2 * 6.0 * nIi + rot_h[N + i] * 12.0 * nIi;
+        }
+        std::sort(h->sigma_h.begin() + h->off_om[i], h->sigma_h.begin() + h->off_om[i + 1], std::greater<double>());
+    }
+    h->lam_h.resize(h->sum_nI);
+    h->p.assign(N, 0);
+    h->coff.assign(N + 1, 0);
+    h->off_zt.assign(N + 1, 0);
+    std::vector<int64_t> wsrc, wdst;
+    std::vector<int32_t> wlen;
+    for (int i = 0; i < N; ++i) {
+        const int nIi = h->nI[i];
+        std::vector<double> lam(nIi);
+        for (int j = 0; j < nIi; ++j) {
+            const double m = mu_h[h->off_I[i] + j];
+            lam[j] = (m > 0.0) ? 1.0 / m : std::numeric_limits<double>::infinity();
+        }
+        std::vector<int> order(nIi);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] > lam[b]; });
+        int pi = 0;
+        for (int k = 0; k < nIi; ++k) {
+            const int j = order[k];
+            h->lam_h[h->off_I[i] + k] = lam[j];
+            if (lam[j] > 1.0 / h->tau) {
+                wsrc.push_back(off_ti[i] + (int64_t)j * 2 * nIi + nIi);
+                wdst.push_back(h->off_zt[i] + (int64_t)pi * nIi);
+                wlen.push_back(nIi);
+                ++pi;
+            }
+        }
+        h->p[i] = pi;
+        h->coff[i + 1] = h->coff[i] + pi;
+        h->off_zt[i + 1] = h->off_zt[i] + (int64_t)pi * nIi;
+    }
+    h->nC = h->coff[N];
+    h->sum_zt = h->off_zt[N];
+
+    // ---- (8) coarse block Z_i on Omega_Ii: u_k = L_A^{-T} w_k, stored as rows
+    h->d_Zt = dnew<double>(h, h->sum_zt);
+    if (h->nC > 0) {
+        double* Wsel = C.tnew<double>(h->sum_zt);
+        {
+            auto a = C.up(wsrc);
+            auto b = C.up(wdst);
+            auto c = C.up(wlen);
+            PScope ps(h, PK_SMALL);
+            launch_gather_rows(TI, a, Wsel, b, c, (int64_t)wsrc.size(), s);
+        }
+        std::vector<GemmDesc> g;
+        for (int i = 0; i < N; ++i)
+            if (h->p[i] > 0)
+                g.push_back(gd(Wsel + h->off_zt[i], h->nI[i], 0, h->d_Y + h->off_sq[i], h->ni[i], 0,
+                               h->d_Zt + h->off_zt[i], h->nI[i], h->p[i], h->nI[i], h->nI[i], 1.0, 0.0, 0));
+        gemm(C, g);
+    }
+
+    // ---- (9) coarse matrix E = R_0 A R_0^T (Eq. (two_level_schwarz)), its
+    // Cholesky factor and inverse factor
+    const int64_t nC = h->nC;
+    if (nC > 0) {
+        std::vector<int64_t> off_az(N + 1, 0);
+        for (int i = 0; i < N; ++i) off_az[i + 1] = off_az[i] + (int64_t)h->ni[i] * h->p[i];
+        double* AZ = C.tnew<double>(off_az[N]);
+        double* E = C.tnew<double>((size_t)nC * nC);
+        ck(cudaMemsetAsync(E, 0, (size_t)nC * nC * sizeof(double), s));
+        std::vector<GemmDesc> g1, g2;
+        for (int i = 0; i < N; ++i) {
+            if (h->p[i] == 0) continue;
+            const int ni = h->ni[i], nIi = h->nI[i], pi = h->p[i];
+            // AZ_i = A(Omega_i, Omega_Ii) Z_i   (ni x p_i)
+            g1.push_back(gd(Araw + h->off_sq[i], ni, 0, h->d_Zt + h->off_zt[i], nIi, 1, AZ + off_az[i], pi, ni, pi,
+                            nIi, 1.0, 0.0, 0));
+            // E_ii = Z_i^T A_II Z_i
+            g2.push_back(gd(h->d_Zt + h->off_zt[i], nIi, 0, AZ + off_az[i], pi, 0,
+                            E + (size_t)h->coff[i] * nC + h->coff[i], (int)nC, pi, pi, nIi, 1.0, 0.0, 1));
+        }
+        gemm(C, g1);
+        gemm(C, g2);
+        // E_ij (i > j) = sum over g in Omega_Ii cap Omega_j of Z_i[g]^T (A Z_j)[g]
+        std::vector<int32_t> posI(n, -1);
+        for (int i = 0; i < N; ++i)
+            for (int a = 0; a < h->nI[i]; ++a) posI[Il[i][a]] = a;
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> lists;  // per pair
+        std::vector<std::pair<int, int>> pairs;
+        {
+            std::vector<int> slot(N, -1);
+            for (int j = 0; j < N; ++j) {
+                if (h->p[j] == 0) continue;
+                std::fill(slot.begin(), slot.end(), -1);
+                std::vector<int> touched;
+                const int32_t* om = omega.data() + h->off_om[j];
+                for (int ps = 0; ps < h->ni[j]; ++ps) {
+                    const int32_t g = om[ps];
+                    const int i = part[g];
+                    if (i <= j || h->p[i] == 0) continue;
+                    if (slot[i] < 0) {
+                        slot[i] = (int)pairs.size();
+                        pairs.push_back({i, j});
+                        lists.emplace_back();
+                    }
+                    lists[slot[i]].push_back({posI[g], ps});
+                }
+            }
+        }
+        std::vector<int32_t> la, lpos;
+        std::vector<EPairRef> et;
+        for (size_t q = 0; q < pairs.size(); ++q) {
+            const int i = pairs[q].first, j = pairs[q].second;
+            const int64_t lo = (int64_t)la.size();
+            for (auto& e : lists[q]) {
+                la.push_back(e.first);
+                lpos.push_back(e.second);
+            }
+            for (int tr = 0; tr * 32 < h->p[i]; ++tr)
+                for (int tc = 0; tc * 32 < h->p[j]; ++tc) {
+                    EPairRef t;
+                    t.i = i;
+                    t.j = j;
+                    t.list_off = lo;
+                    t.list_len = (int)lists[q].size();
+                    t.tr = tr;
+                    t.tc = tc;
+                    et.push_back(t);
+                }
+        }
+        std::vector<int32_t> nIv(h->nI.begin(), h->nI.end()), pv(h->p.begin(), h->p.end());
+        h->d_zt_off = C.up(std::vector<int64_t>(h->off_zt.begin(), h->off_zt.end() - 1), true);
+        h->d_nI = C.up(nIv, true);
+        h->d_p = C.up(pv, true);
+        h->d_coff = C.up(std::vector<int64_t>(h->coff.begin(), h->coff.end() - 1), true);
+        if (!et.empty()) {
+            auto a = C.up(et);
+            auto b = C.up(la);
+            auto c = C.up(lpos);
+            auto d = C.up(std::vector<int64_t>(off_az.begin(), off_az.end() - 1));
+            double fl = 0.0;
+            for (size_t q = 0; q < pairs.size(); ++q)
+                fl += 2.0 * h->p[pairs[q].first] * h->p[pairs[q].second] * lists[q].size();
+            PScope ps(h, PK_E_ASM, fl);
+            launch_e_offdiag(a, (int)et.size(), b, c, h->d_Zt, h->d_zt_off, h->d_nI, AZ, d, h->d_p, h->d_coff, E, nC,
+                             s);
+        }
+        double* linvE = C.tnew<double>((size_t)cdiv(nC, CHOL_NB) * CHOL_NB * CHOL_NB);
+        h->d_YE = dnew<double>(h, (size_t)nC * nC);
+        h->d_YEt = dnew<double>(h, (size_t)nC * nC);
+        chol_batched(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}});
+        trtri_batched(C, {TrtriDesc{E, h->d_YE, linvE, (int)nC, (int)nC, (int)nC}});
+        transpose_batched(C, {h->d_YE}, {h->d_YEt}, {(int)nC}, {(int)nC}, {(int)nC});
+    } else {
+        h->d_zt_off = C.up(std::vector<int64_t>(h->off_zt.begin(), h->off_zt.end() - 1), true);
+        h->d_nI = C.up(std::vector<int32_t>(h->nI.begin(), h->nI.end()), true);
+        h->d_p = C.up(std::vector<int32_t>(h->p.begin(), h->p.end()), true);
+        h->d_coff = C.up(std::vector<int64_t>(h->coff.begin(), h->coff.end() - 1), true);
+    }
+
+    // ---- (10) apply plan
+    {
+        std::vector<GemvDesc> l1(N), l2(N), cr(N);
+        h->d_rloc = dnew<double>(h, h->sum_ni);
+        h->d_tloc = dnew<double>(h, h->sum_ni);
+        h->d_yloc = dnew<double>(h, h->sum_ni);
+        h->d_c = dnew<double>(h, nC);
+        h->d_ct = dnew<double>(h, nC);
+        h->d_e = dnew<double>(h, nC);
+        std::vector<int32_t> rd, rl, rdc, rlc;
+        rd.reserve(h->sum_ni);
+        rl.reserve(h->sum_ni);
+        for (int i = 0; i < N; ++i) {
+            const int ni = h->ni[i];
+            l1[i] = {h->d_Y + h->off_sq[i], ni, ni, ni, 1, h->d_rloc + h->off_om[i], h->d_tloc + h->off_om[i]};
+            l2[i] = {h->d_Yt + h->off_sq[i], ni, ni, ni, 2, h->d_tloc + h->off_om[i], h->d_yloc + h->off_om[i]};
+            cr[i] = {h->d_Zt + h->off_zt[i], h->p[i], h->nI[i], h->nI[i], 0, h->d_rloc + h->off_om[i],
+                     h->d_c + h->coff[i]};
+            for (int a = 0; a < ni; ++a) {
+                rd.push_back(i);
+                rl.push_back(a);
+            }
+            for (int k = 0; k < h->p[i]; ++k) {
+                rdc.push_back(i);
+                rlc.push_back(k);
+            }
+        }
+        h->d_gv_l1 = C.up(l1, true);
+        h->d_gv_l2 = C.up(l2, true);
+        h->d_gv_c = C.up(cr, true);
+        h->d_rd_loc = C.up(rd, true);
+        h->d_rl_loc = C.up(rl, true);
+        h->d_rd_c = C.up(rdc, true);
+        h->d_rl_c = C.up(rlc, true);
+        std::vector<GemvDesc> e1{{h->d_YE, (int)nC, (int)nC, (int)nC, 1, h->d_c, h->d_ct}};
+        std::vector<GemvDesc> e2{{h->d_YEt, (int)nC, (int)nC, (int)nC, 2, h->d_ct, h->d_e}};
+        h->d_gv_e1 = C.up(e1, true);
+        h->d_gv_e2 = C.up(e2, true);
+        std::vector<int32_t> rde(nC, 0), rle(nC);
+        std::iota(rle.begin(), rle.end(), 0);
+        h->d_rd_e = C.up(rde, true);
+        h->d_rl_e = C.up(rle, true);
+        // prolongation: copies of each unknown in subdomain order, owners
+        std::vector<int64_t> scp(n + 1, 0);
+        for (int64_t t = 0; t < h->sum_ni; ++t) scp[omega[t] + 1]++;
+        for (int64_t g = 0; g < n; ++g) scp[g + 1] += scp[g];
+        std::vector<int32_t> sci(h->sum_ni);
+        std::vector<int64_t> fill(scp.begin(), scp.end() - 1);
+        for (int64_t t = 0; t < h->sum_ni; ++t) sci[fill[omega[t]]++] = (int32_t)t;
+        std::vector<int32_t> og, osub, oa;
+        og.reserve(n);
+        osub.reserve(n);
+        oa.reserve(n);
+        for (int i = 0; i < N; ++i)
+            for (int a = 0; a < h->nI[i]; ++a) {
+                og.push_back(Il[i][a]);
+                osub.push_back(i);
+                oa.push_back(a);
+            }
+        h->d_sc_ptr = C.up(scp, true);
+        h->d_sc_idx = C.up(sci, true);
+        h->d_order_g = C.up(og, true);
+        h->d_own_sub = C.up(osub, true);
+        h->d_own_a = C.up(oa, true);
+        // PCG vectors
+        h->d_r = dnew<double>(h, n);
+        h->d_z = dnew<double>(h, n);
+        h->d_pv = dnew<double>(h, n);
+        h->d_q = dnew<double>(h, n);
+        h->d_part = dnew<double>(h, DOT_BLOCKS);
+        h->d_sc = dnew<PcgScal>(h, 1);
+    }
+    ck(cudaGetLastError());
+    const int e = read_err(h);
+    if (e) throw Fail{err_status(e)};
+}
+
+void apply_one(amdd_handle* h, const double* r, double* z) {
+    cudaStream_t s = h->s;
+    const double tri = (double)h->apply_tri_elems;  // elements of the lower + upper local factors
+    {
+        PScope ps(h, PK_GATHER_SCATTER, 0.0, 20.0 * h->sum_ni);
+        launch_gather_vec(h->d_omega, h->sum_ni, r, h->d_rloc, s);
+    }
+    {
+        PScope ps(h, PK_GEMV, tri, 8.0 * tri / 2 + 24.0 * h->sum_ni);
+        launch_gemv_rows(h->d_gv_l1, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+    }
+    {
+        PScope ps(h, PK_GEMV, tri, 8.0 * tri / 2 + 24.0 * h->sum_ni);
+        launch_gemv_rows(h->d_gv_l2, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+    }
+    if (h->nC > 0) {
+        const double zt = (double)h->sum_zt, et = (double)h->nC * (h->nC + 1) / 2;
+        {
+            PScope ps(h, PK_GEMV, 2.0 * zt, 8.0 * zt + 8.0 * h->sum_ni + 16.0 * h->nC);
+            launch_gemv_rows(h->d_gv_c, h->d_rd_c, h->d_rl_c, h->nC, s);
+        }
+        {
+            PScope ps(h, PK_GEMV, 2.0 * et, 8.0 * et + 24.0 * h->nC);
+            launch_gemv_rows(h->d_gv_e1, h->d_rd_e, h->d_rl_e, h->nC, s);
+        }
+        {
+            PScope ps(h, PK_GEMV, 2.0 * et, 8.0 * et + 24.0 * h->nC);
+            launch_gemv_rows(h->d_gv_e2, h->d_rd_e, h->d_rl_e, h->nC, s);
+        }
+    }
+    PScope ps(h, PK_GATHER_SCATTER, 2.0 * h->sum_zt, 8.0 * h->sum_zt + 12.0 * h->sum_ni + 24.0 * h->n);
+    launch_scatter_prolong(h->n, h->d_order_g, h->d_own_sub, h->d_own_a, h->d_sc_ptr, h->d_sc_idx, h->d_yloc,
+                           h->d_zt_off, h->d_nI, h->d_p, h->d_coff, h->d_Zt, h->nC > 0 ? h->d_e : nullptr, z, s);
+}
+
+// Launch wrappers of the PCG loop with their profile accounting.
+void spmv_h(amdd_handle* h, const double* x, double* y) {
+    PScope ps(h, PK_SPMV, 2.0 * h->nnz, 12.0 * h->nnz + 8.0 * (h->n + 1) + 16.0 * h->n);
+    launch_spmv(h->n, h->rowptr, h->col, h->val, x, y, h->spmv_group, h->s);
+}
+void dot_h(amdd_handle* h, const double* x, const double* y, int which, double tol2) {
+    {
+        PScope ps(h, PK_PCG_VEC, 2.0 * h->n, 16.0 * h->n);
+        launch_dot_partials(h->n, x, y, h->d_part, h->s);
+    }
+    PScope ps(h, PK_PCG_VEC);
+    launch_dot_finalize(h->d_part, h->d_sc, which, tol2, h->s);
+}
+
+amdd_status guard_exc() {
+    try {
+        throw;
+    } catch (const Fail& f) {
+        return f.st;
+    } catch (const std::bad_alloc&) {
+        return AMDD_ERR_OOM;
+    } catch (...) {
+        return AMDD_ERR_CUDA;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+amdd_status amdd_opts_default(amdd_opts* o) {
+    if (!o) return AMDD_ERR_INVALID;
+    std::memset(o, 0, sizeof(*o));
+    o->eps = std::ldexp(1.0, -52);
+    o->max_sweeps = 60;
+    return AMDD_OK;
+}
+
+amdd_status amdd_spmv(const amdd_csr* A, const double* x, double* y, void* stream) {
+    if (!A || A->n < 0 || A->nnz < 0 || (A->n > 0 && (!A->rowptr || !x || !y)) || (A->nnz > 0 && (!A->colind || !A->val)))
+        return AMDD_ERR_INVALID;
+    if (A->n > INT32_MAX) return AMDD_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t per = A->n ? A->nnz / A->n : 0;
+    launch_spmv(A->n, A->rowptr, A->colind, A->val, x, y, per <= 8 ? 4 : (per <= 24 ? 8 : 32), s);
+    if (cudaGetLastError() != cudaSuccess) return AMDD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return AMDD_ERR_CUDA;
+    return AMDD_OK;
+}
+
+amdd_status amdd_overlap_sets(int64_t n, const int64_t* rowptr, const int32_t* colind, const int32_t* part,
+                              int32_t i, int32_t overlap, int32_t* I, int32_t capI, int32_t* G, int32_t capG,
+                              int32_t* D, int32_t capD, int32_t* nI, int32_t* nG, int32_t* nD) {
+    if (n < 1 || n > INT32_MAX || !rowptr || !colind || !part || i < 0 || overlap < 0) return AMDD_ERR_INVALID;
+    try {
+        const int64_t nnz = rowptr[n];
+        if (rowptr[0] != 0 || nnz < 0) return AMDD_ERR_INVALID;
+        for (int64_t r = 0; r < n; ++r)
+            if (rowptr[r] > rowptr[r + 1]) return AMDD_ERR_INVALID;
+        for (int64_t k = 0; k < nnz; ++k)
+            if (colind[k] < 0 || colind[k] >= n) return AMDD_ERR_INVALID;
+        std::vector<int32_t> Iv;
+        for (int64_t g = 0; g < n; ++g)
+            if (part[g] == i) Iv.push_back((int32_t)g);
+        std::vector<int32_t> mark(n, -1), Gv, Dv;
+        overlap_layers(rowptr, colind, Iv, overlap, i, mark.data(), Gv, Dv);
+        if (nI) *nI = (int32_t)Iv.size();
+        if (nG) *nG = (int32_t)Gv.size();
+        if (nD) *nD = (int32_t)Dv.size();
+        if ((I && capI < (int64_t)Iv.size()) || (G && capG < (int64_t)Gv.size()) || (D && capD < (int64_t)Dv.size()))
+            return AMDD_ERR_INVALID;
+        if (I) std::copy(Iv.begin(), Iv.end(), I);
+        if (G) std::copy(Gv.begin(), Gv.end(), G);
+        if (D) std::copy(Dv.begin(), Dv.end(), D);
+    } catch (...) {
+        return guard_exc();
+    }
+    return AMDD_OK;
+}
+
+amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_t overlap, double tau,
+                       const amdd_opts* opts, void* stream, amdd_handle** out) {
+    if (!out) return AMDD_ERR_INVALID;
+    *out = nullptr;
+    if (!A || !part || N < 1 || overlap < 1 || !(tau > 0.0) || A->n < 1 || A->nnz < A->n || !A->rowptr ||
+        !A->colind || !A->val || N > A->n || A->n > INT32_MAX)
+        return AMDD_ERR_INVALID;
+    amdd_opts o;
+    amdd_opts_default(&o);
+    if (opts) {
+        o = *opts;
+        if (!(o.eps > 0.0) || o.max_sweeps < 1) return AMDD_ERR_INVALID;
+        for (int k = 0; k < 6; ++k)
+            if (o.reserved[k] != 0) return AMDD_ERR_INVALID;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    amdd_handle* h = nullptr;
+    try {
+        h = new amdd_handle();
+        h->s = static_cast<cudaStream_t>(stream);
+        h->n = A->n;
+        h->nnz = A->nnz;
+        h->N = N;
+        h->overlap = overlap;
+        h->tau = tau;
+        h->eps = o.eps;
+        h->max_sweeps = o.max_sweeps;
+        h->prof.on = o.profile != 0;
+        do_setup(h, A, part);
+        ck(cudaStreamSynchronize(h->s));
+    } catch (...) {
+        const amdd_status st = guard_exc();
+        if (h) {
+            cudaStreamSynchronize(h->s);
+            amdd_destroy(h);
+        }
+        return st;
+    }
+    h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return AMDD_OK;
+}
+
+amdd_status amdd_apply(amdd_handle* h, const double* r, double* z, int32_t nrhs) {
+    if (!h || !r || !z || nrhs < 0 || r == z) return AMDD_ERR_INVALID;
+    try {
+        for (int k = 0; k < nrhs; ++k) apply_one(h, r + (size_t)k * h->n, z + (size_t)k * h->n);
+        ck(cudaGetLastError());
+        ck(cudaStreamSynchronize(h->s));
+    } catch (...) {
+        return guard_exc();
+    }
+    return AMDD_OK;
+}
+
+amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t nrhs, double rtol, int32_t maxit,
+                           amdd_stats* stats) {
+    if (!h || !b || !x || nrhs < 0 || !(rtol >= 0.0) || maxit < 0) return AMDD_ERR_INVALID;
+    const auto t0 = std::chrono::steady_clock::now();
+    amdd_status result = AMDD_OK;
+    try {
+        cudaStream_t s = h->s;
+        const int64_t n = h->n;
+        const double tol2 = rtol * rtol;
+        for (int k = 0; k < nrhs; ++k) {
+            const double* bk = b + (size_t)k * n;
+            double* xk = x + (size_t)k * n;
+            PcgScal sc0{};
+            ck(cudaMemcpyAsync(h->d_sc, &sc0, sizeof(PcgScal), cudaMemcpyHostToDevice, s));
+            // r = b - A x0
+            spmv_h(h, xk, h->d_q);
+            {
+                PScope ps(h, PK_PCG_VEC, 2.0 * n, 24.0 * n);
+                launch_axpby(n, 1.0, bk, -1.0, h->d_q, h->d_r, s);
+            }
+            dot_h(h, bk, bk, 3, tol2);
+            dot_h(h, h->d_r, h->d_r, 5, tol2);
+            PcgScal sc{};
+            ck(cudaMemcpyAsync(&sc, h->d_sc, sizeof(PcgScal), cudaMemcpyDeviceToHost, s));
+            ck(cudaStreamSynchronize(s));
+            int its = 0;
+            bool conv = sc.bb == 0.0 || sc.conv;
+            if (sc.bb == 0.0) {
+                ck(cudaMemsetAsync(xk, 0, n * sizeof(double), s));
+                sc.rr = 0.0;
+            }
+            if (!conv) {
+                apply_one(h, h->d_r, h->d_z);
+                dot_h(h, h->d_r, h->d_z, 4, tol2);
+                ck(cudaMemcpyAsync(h->d_pv, h->d_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                for (its = 1; its <= maxit; ++its) {
+                    spmv_h(h, h->d_pv, h->d_q);
+                    dot_h(h, h->d_pv, h->d_q, 0, tol2);
+                    {
+                        PScope ps(h, PK_PCG_VEC, 6.0 * n, 48.0 * n);
+                        launch_pcg_update_xr(n, xk, h->d_r, h->d_pv, h->d_q, h->d_sc, h->d_part, s);
+                    }
+                    {
+                        PScope ps(h, PK_PCG_VEC);
+                        launch_dot_finalize(h->d_part, h->d_sc, 2, tol2, s);
+                    }
+                    ck(cudaMemcpyAsync(&sc, h->d_sc, sizeof(PcgScal), cudaMemcpyDeviceToHost, s));
+                    ck(cudaStreamSynchronize(s));
+                    if (sc.conv) {
+                        conv = true;
+                        break;
+                    }
+                    if (its == maxit) break;
+                    apply_one(h, h->d_r, h->d_z);
+                    dot_h(h, h->d_r, h->d_z, 1, tol2);
+                    PScope ps(h, PK_PCG_VEC, 2.0 * n, 24.0 * n);
+                    launch_pcg_update_p(n, h->d_pv, h->d_z, h->d_sc, s);
+                }
+                if (its > maxit) its = maxit;
+            }
+            if (!conv) result = AMDD_ERR_NOCONV;
+            if (k == 0 && stats) {
+                // true residual b - A x
+                spmv_h(h, xk, h->d_q);
+                launch_axpby(n, 1.0, bk, -1.0, h->d_q, h->d_z, s);
+                dot_h(h, h->d_z, h->d_z, 5, tol2);
+                PcgScal st{};
+                ck(cudaMemcpyAsync(&st, h->d_sc, sizeof(PcgScal), cudaMemcpyDeviceToHost, s));
+                ck(cudaStreamSynchronize(s));
+                stats->iterations = its;
+                stats->converged = conv ? 1 : 0;
+                stats->rel_residual = sc.bb > 0.0 ? std::sqrt(sc.rr / sc.bb) : 0.0;
+                stats->true_rel_residual = sc.bb > 0.0 ? std::sqrt(st.rr / sc.bb) : 0.0;
+            }
+        }
+        ck(cudaGetLastError());
+        ck(cudaStreamSynchronize(s));
+    } catch (...) {
+        return guard_exc();
+    }
+    if (stats)
+        stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return result;
+}
+
+amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
+    if (!h || !info) return AMDD_ERR_INVALID;
+    std::memset(info, 0, sizeof(*info));
+    info->n = h->n;
+    info->N = h->N;
+    info->overlap = h->overlap;
+    info->tau = h->tau;
+    info->n_C = h->nC;
+    info->sum_ni = h->sum_ni;
+    info->sum_nti = h->sum_nt;
+    info->max_ni = h->max_ni;
+    info->max_nti = h->max_nt;
+    info->sweeps_svd = h->sweeps_svd;
+    info->sweeps_eig = h->sweeps_eig;
+    info->setup_ms = h->setup_ms;
+    return AMDD_OK;
+}
+
+amdd_status amdd_get_subdomain(const amdd_handle* h, int32_t i, int32_t* nI, int32_t* nG, int32_t* nD, int32_t* p) {
+    if (!h || i < 0 || i >= h->N) return AMDD_ERR_INVALID;
+    if (nI) *nI = h->nI[i];
+    if (nG) *nG = h->nG[i];
+    if (nD) *nD = h->nD[i];
+    if (p) *p = h->p[i];
+    return AMDD_OK;
+}
+
+amdd_status amdd_get_eigenvalues(const amdd_handle* h, int32_t i, double* lam, int32_t cap, int32_t* count) {
+    if (!h || i < 0 || i >= h->N) return AMDD_ERR_INVALID;
+    const int c = h->nI[i];
+    if (count) *count = c;
+    if (lam) {
+        if (cap < c) return AMDD_ERR_INVALID;
+        std::memcpy(lam, h->lam_h.data() + h->off_I[i], c * sizeof(double));
+    }
+    return AMDD_OK;
+}
+
+amdd_status amdd_get_singular_values(const amdd_handle* h, int32_t i, double* sigma, int32_t cap, int32_t* count) {
+    if (!h || i < 0 || i >= h->N) return AMDD_ERR_INVALID;
+    const int c = h->ni[i];
+    if (count) *count = c;
+    if (sigma) {
+        if (cap < c) return AMDD_ERR_INVALID;
+        std::memcpy(sigma, h->sigma_h.data() + h->off_om[i], c * sizeof(double));
+    }
+    return AMDD_OK;
+}
+
+amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, int64_t cap, int32_t* p,
+                                  int32_t* nI) {
+    if (!h || i < 0 || i >= h->N) return AMDD_ERR_INVALID;
+    const int64_t cnt = (int64_t)h->p[i] * h->nI[i];
+    if (p) *p = h->p[i];
+    if (nI) *nI = h->nI[i];
+    if (Zt && cnt > 0) {
+        if (cap < cnt) return AMDD_ERR_INVALID;
+        if (cudaMemcpyAsync(Zt, h->d_Zt + h->off_zt[i], cnt * sizeof(double), cudaMemcpyDeviceToHost, h->s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(h->s) != cudaSuccess)
+            return AMDD_ERR_CUDA;
+    }
+    return AMDD_OK;
+}
+
+amdd_status amdd_get_profile(amdd_handle* h, int32_t k, const char** name, int64_t* launches, double* ms,
+                             double* flops, double* bytes) {
+    if (!h || !h->prof.on || k < 0 || k >= PK_COUNT) return AMDD_ERR_INVALID;
+    if (cudaStreamSynchronize(h->s) != cudaSuccess) return AMDD_ERR_CUDA;
+    double t = 0.0;
+    for (auto& e : h->prof.ev[k]) {
+        float x = 0.0f;
+        if (cudaEventElapsedTime(&x, e.first, e.second) != cudaSuccess) return AMDD_ERR_CUDA;
+        t += x;
+    }
+    if (name) *name = kProfNames[k];
+    if (launches) *launches = h->prof.launches[k];
+    if (ms) *ms = t;
+    if (flops) *flops = h->prof.flops[k];
+    if (bytes) *bytes = h->prof.bytes[k];
+    return AMDD_OK;
+}
+
+amdd_status amdd_reset_profile(amdd_handle* h) {
+    if (!h || !h->prof.on) return AMDD_ERR_INVALID;
+    if (cudaStreamSynchronize(h->s) != cudaSuccess) return AMDD_ERR_CUDA;
+    h->prof.clear();
+    return AMDD_OK;
+}
+
+void amdd_destroy(amdd_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->s);
+    h->prof.clear();
+    for (void* p : h->allocs) cudaFreeAsync(p, h->s);
+    cudaStreamSynchronize(h->s);
+    delete h;
+}
+
+const char* amdd_status_str(amdd_status s) {
+    switch (s) {
+        case AMDD_OK: return "ok";
+        case AMDD_ERR_INVALID: return "invalid argument";
+        case AMDD_ERR_NOT_SPD: return "matrix not SPD (Cholesky pivot <= 0)";
+        case AMDD_ERR_NOCONV: return "PCG did not converge within maxit";
+        case AMDD_ERR_OOM: return "out of memory";
+        case AMDD_ERR_TIMEOUT: return "device wait timed out";
+        case AMDD_ERR_CUDA: return "CUDA runtime error";
+        case AMDD_ERR_EIG_NOCONV: return "Jacobi eigensolver did not converge";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Internal declarations shared by the translation units of libamdd.
+// Dense matrices are row-major: element (r, c) of a matrix with leading
+// dimension ld sits at p[r * ld + c].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace amdd {
+
+// Bits of the device error word.
+enum : int {
+    DERR_NOT_SPD = 1,        // Cholesky pivot <= 0 (or NaN) without clamping
+    DERR_EIG_NOCONV = 2,     // Jacobi sweep limit reached
+    DERR_BOUNDS = 4,         // an index check failed
+};
+
+constexpr int CHOL_NB = 32;     // diagonal block of the blocked Cholesky / inverse
+constexpr int GEMM_T = 64;      // GEMM output tile
+constexpr int JAC_CLUSTER = 8;  // CTAs per matrix in the Jacobi solvers
+
+// ---------------------------------------------------------------- dense
+// C = alpha * op(A) * op(B) + beta * C for m x n outputs, inner dimension k.
+// ta = 0: A is m x k (A[r*lda + kk]); ta = 1: A is stored k x m (A[kk*lda + r]).
+// tb = 0: B is k x n (B[kk*ldb + c]); tb = 1: B is stored n x k (B[c*ldb + kk]).
+// lower = 1: only elements with r >= c are written (tiles above skipped).
+// kfrom_row = 1: the k loop starts at the tile's first row (for products whose
+// A operand is zero for kk < r, e.g. a lower-triangular Y read transposed).
+// beta == 0 means C is not read.
+struct GemmDesc {
+    const double* A;
+    const double* B;
+    double* C;
+    int m, n, k;
+    int lda, ldb, ldc;
+    int ta, tb, lower, kfrom_row;
+    double alpha, beta;
+};
+
+struct TileRef {
+    int desc, tm, tn;
+};
+
+// Blocked Cholesky / inverse-factor descriptors (one per matrix).
+struct CholDesc {
+    double* A;            // n x n, lower triangle used and overwritten with L
+    int n, ld;
+    int stop;             // factor columns [0, stop); stop < n leaves the Schur complement
+    const double* clamp;  // per-matrix pivot floor (pivots below are raised to it); NULL = SPD check
+    double* Linv;         // ceil(stop/NB) * NB*NB doubles: inverses of the diagonal blocks
+};
+
+struct PanelRef {
+    int desc, rt;  // row tile index (64 rows) below the diagonal block
+};
+
+struct TrtriDesc {
+    const double* L;      // n x n lower Cholesky factor (ld)
+    double* Y;            // n x n output L^{-1} (ldy), lower triangular
+    const double* Linv;   // diagonal-block inverses from the Cholesky
+    int n, ld, ldy;
+};
+
+struct ChunkRef {
+    int desc, ct;  // column chunk (64 columns)
+};
+
+struct JacobiDesc {
+    double* A;        // rows x ld, rows orthogonalised in place
+    int rows, ld;
+    int ncols_dot;    // columns entering the inner products
+    int ncols_rot;    // columns rotated (>= ncols_dot)
+};
+
+// Row GEMV descriptors: y[row] = sum_{c in [c0(row), c1(row))} M[row][c] x[c].
+// mode 0: full row [0, ncols); mode 1: lower [0, row]; mode 2: upper [row, ncols).
+struct GemvDesc {
+    const double* M;
+    int rows, ncols, ld, mode;
+    const double* x;
+    double* y;
+};
+
+void launch_gemm(const GemmDesc* d_descs, const TileRef* d_tiles, int ntiles, cudaStream_t s);
+void launch_chol_diag(const CholDesc* d, int nmat, int k0, int* err, cudaStream_t s);
+void launch_chol_panel(const CholDesc* d, const PanelRef* tiles, int ntiles, int k0, cudaStream_t s);
+void launch_trtri_diag(const TrtriDesc* d, const ChunkRef* tiles, int ntiles, int k0, cudaStream_t s);
+void launch_set_identity(const TrtriDesc* d, int nmat, int maxn, cudaStream_t s);
+void launch_jacobi(const JacobiDesc* d, int nmat, int max_sweeps, double tol, int* sweeps, unsigned long long* rots,
+                   int* err, cudaStream_t s);
+// sigma[j] = ||row j|| over ncols_dot; delta[mat] = eps * max_j sigma[j]; optionally
+// scale row j by 1/sqrt(sigma[j]).
+void launch_rownorms(const JacobiDesc* d, int nmat, double* const* sigma_ptrs, double* delta, double eps,
+                     int scale_rows, cudaStream_t s);
+void launch_add_diag(double* const* mats, const int* n, const int* ld, const double* delta, int nmat,
+                     int maxn, cudaStream_t s);
+void launch_mirror_lower(double* const* mats, const int* n, const int* ld, int nmat, int maxn,
+                         cudaStream_t s);
+void launch_transpose(const double* const* src, double* const* dst, const int* n, const int* lds,
+                      const int* ldd, int nmat, int maxn, cudaStream_t s);
+void launch_gemv_rows(const GemvDesc* d, const int* row_desc, const int* row_local, int64_t nrows,
+                      cudaStream_t s);
+
+// ---------------------------------------------------------------- sparse / vectors
+void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
+                 double* y, int group, cudaStream_t s);
+void launch_gather_values(const int64_t* src, const int64_t* dst, int64_t cnt, const double* val, double* out,
+                          cudaStream_t s);
+void launch_gather_vec(const int32_t* idx, int64_t cnt, const double* x, double* out, cudaStream_t s);
+void launch_gather_rows(const double* src, const int64_t* src_off, double* dst, const int64_t* dst_off,
+                        const int32_t* len, int64_t nrows, cudaStream_t s);
+void launch_scatter_prolong(int64_t n, const int32_t* order_g, const int32_t* own_sub, const int32_t* own_a,
+                            const int64_t* sc_ptr, const int32_t* sc_idx, const double* yloc,
+                            const int64_t* zt_off, const int32_t* nI, const int32_t* p, const int64_t* coff,
+                            const double* Zt, const double* e, double* z, cudaStream_t s);
+struct EPairRef {
+    int i, j;          // block E_ij, i > j
+    int64_t list_off;  // entries [list_off, list_off + list_len)
+    int list_len;
+    int tr, tc;        // 32x32 tile of the p_i x p_j block
+};
+void launch_e_offdiag(const EPairRef* tiles, int ntiles, const int32_t* la, const int32_t* lpos,
+                      const double* Zt, const int64_t* zt_off, const int32_t* nI, const double* AZ,
+                      const int64_t* az_off, const int32_t* p, const int64_t* coff, double* E, int64_t ldE,
+                      cudaStream_t s);
+
+// Deterministic dot products: fixed grid of DOT_BLOCKS partial sums reduced in
+// a fixed order by one block.
+constexpr int DOT_BLOCKS = 264;
+struct PcgScal {
+    double rz, pq, rr, bb, alpha, beta, rz_new;
+    int conv, iters;
+};
+void launch_dot_partials(int64_t n, const double* x, const double* y, double* partials, cudaStream_t s);
+// which: 0 -> pq (alpha = rz/pq), 1 -> rz_new (beta = rz_new/rz, rz = rz_new),
+// 2 -> rr (conv = rr <= tol2 * bb), 3 -> bb, 4 -> rz (initial)
+void launch_dot_finalize(const double* partials, PcgScal* sc, int which, double tol2, cudaStream_t s);
+void launch_pcg_update_xr(int64_t n, double* x, double* r, const double* p, const double* q, const PcgScal* sc,
+                          double* partials, cudaStream_t s);
+void launch_pcg_update_p(int64_t n, double* p, const double* z, const PcgScal* sc, cudaStream_t s);
+void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
+
+}  // namespace amdd

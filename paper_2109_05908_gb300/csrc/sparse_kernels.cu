@@ -1,0 +1,292 @@
+// Sparse and vector kernels: CSR SpMV (Sec. 1, the operator of A x = b),
+// restriction / prolongation of the additive Schwarz apply
+// (Eq. (two_level_schwarz)), coarse-matrix blocks E_ij = Z_i^T A_{I_i I_j} Z_j,
+// and the deterministic reductions and updates of PCG.
+#include "amdd_internal.h"
+
+namespace amdd {
+
+// ------------------------------------------------------------------ SpMV
+// G lanes per row (G in {4, 8, 32}); rows are assigned to lane groups in a
+// grid-stride loop.
+template <int G>
+__global__ void __launch_bounds__(256) spmv_kernel(int64_t n, const int64_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                   const double* __restrict__ x, double* __restrict__ y) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = threadIdx.x & (G - 1);
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    // every lane of the grid runs the same number of iterations, so the full
+    // warp takes part in each shuffle
+    const int64_t nround = ((n + groups - 1) / groups) * groups;
+    for (int64_t row = gid / G; row < nround; row += groups) {
+        double s = 0.0;
+        if (row < n) {
+            const int64_t b = rowptr[row], e = rowptr[row + 1];
+            for (int64_t k = b + sub; k < e; k += G) s = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (row < n && sub == 0) y[row] = s;
+    }
+}
+
+void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
+                 double* y, int group, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t want = (n * group + 255) / 256;
+    const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+    if (group <= 4)
+        spmv_kernel<4><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
+    else if (group <= 8)
+        spmv_kernel<8><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
+    else
+        spmv_kernel<32><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
+}
+
+// ------------------------------------------------------------------ gathers
+__global__ void gather_values_kernel(const int64_t* __restrict__ src, const int64_t* __restrict__ dst, int64_t cnt,
+                                     const double* __restrict__ val, double* __restrict__ out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        out[dst[t]] = val[src[t]];
+}
+
+void launch_gather_values(const int64_t* src, const int64_t* dst, int64_t cnt, const double* val, double* out,
+                          cudaStream_t s) {
+    if (cnt <= 0) return;
+    const int64_t want = (cnt + 255) / 256;
+    gather_values_kernel<<<(unsigned)(want < 152 * 32 ? want : 152 * 32), 256, 0, s>>>(src, dst, cnt, val, out);
+}
+
+__global__ void gather_vec_kernel(const int32_t* __restrict__ idx, int64_t cnt, const double* __restrict__ x,
+                                  double* __restrict__ out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = x[idx[t]];
+}
+
+void launch_gather_vec(const int32_t* idx, int64_t cnt, const double* x, double* out, cudaStream_t s) {
+    if (cnt <= 0) return;
+    const int64_t want = (cnt + 255) / 256;
+    gather_vec_kernel<<<(unsigned)(want < 152 * 32 ? want : 152 * 32), 256, 0, s>>>(idx, cnt, x, out);
+}
+
+// dst[dst_off[r] + c] = src[src_off[r] + c] for c < len[r]: copies rows of
+// matrices with different leading dimensions.
+__global__ void gather_rows_kernel(const double* __restrict__ src, const int64_t* __restrict__ src_off,
+                                   double* __restrict__ dst, const int64_t* __restrict__ dst_off,
+                                   const int32_t* __restrict__ len, int64_t nrows) {
+    for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const double* s = src + src_off[r];
+        double* d = dst + dst_off[r];
+        for (int c = threadIdx.x; c < len[r]; c += blockDim.x) d[c] = s[c];
+    }
+}
+
+void launch_gather_rows(const double* src, const int64_t* src_off, double* dst, const int64_t* dst_off,
+                        const int32_t* len, int64_t nrows, cudaStream_t s) {
+    if (nrows <= 0) return;
+    gather_rows_kernel<<<(unsigned)(nrows < 65535 ? nrows : 65535), 128, 0, s>>>(src, src_off, dst, dst_off, len,
+                                                                                  nrows);
+}
+
+// ------------------------------------------------------------------ prolongation
+// z[g] = sum over the copies of g in the local vectors (fixed subdomain order)
+//      + sum_k Zt_i[k][a] e[coff_i + k]   (i owns g, a = position of g in Omega_Ii).
+// Threads run in owner order so that consecutive threads read consecutive
+// columns of Zt_i.
+__global__ void __launch_bounds__(256) scatter_prolong_kernel(
+    int64_t n, const int32_t* __restrict__ order_g, const int32_t* __restrict__ own_sub,
+    const int32_t* __restrict__ own_a, const int64_t* __restrict__ sc_ptr, const int32_t* __restrict__ sc_idx,
+    const double* __restrict__ yloc, const int64_t* __restrict__ zt_off, const int32_t* __restrict__ nI,
+    const int32_t* __restrict__ p, const int64_t* __restrict__ coff, const double* __restrict__ Zt,
+    const double* __restrict__ e, double* __restrict__ z) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int g = order_g[t];
+        double s = 0.0;
+        for (int64_t k = sc_ptr[g]; k < sc_ptr[g + 1]; ++k) s += yloc[sc_idx[k]];
+        if (e) {
+            const int i = own_sub[t], a = own_a[t];
+            const int pi = p[i], ni = nI[i];
+            const double* zt = Zt + zt_off[i] + a;
+            const double* ei = e + coff[i];
+            double c = 0.0;
+            for (int k = 0; k < pi; ++k) c = fma(zt[(size_t)k * ni], ei[k], c);
+            s += c;
+        }
+        z[g] = s;
+    }
+}
+
+void launch_scatter_prolong(int64_t n, const int32_t* order_g, const int32_t* own_sub, const int32_t* own_a,
+                            const int64_t* sc_ptr, const int32_t* sc_idx, const double* yloc, const int64_t* zt_off,
+                            const int32_t* nI, const int32_t* p, const int64_t* coff, const double* Zt,
+                            const double* e, double* z, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t want = (n + 255) / 256;
+    scatter_prolong_kernel<<<(unsigned)(want < 152 * 32 ? want : 152 * 32), 256, 0, s>>>(
+        n, order_g, own_sub, own_a, sc_ptr, sc_idx, yloc, zt_off, nI, p, coff, Zt, e, z);
+}
+
+// ------------------------------------------------------------------ coarse blocks
+// E[coff_i + r][coff_j + c] = sum_l Zt_i[r][la[l]] * AZ_j[lpos[l]][c], 32 x 32
+// tile per CTA (i > j: strictly lower blocks of E).
+__global__ void __launch_bounds__(256) e_offdiag_kernel(const EPairRef* __restrict__ tiles,
+                                                         const int32_t* __restrict__ la,
+                                                         const int32_t* __restrict__ lpos,
+                                                         const double* __restrict__ Zt,
+                                                         const int64_t* __restrict__ zt_off,
+                                                         const int32_t* __restrict__ nI,
+                                                         const double* __restrict__ AZ,
+                                                         const int64_t* __restrict__ az_off,
+                                                         const int32_t* __restrict__ p,
+                                                         const int64_t* __restrict__ coff, double* __restrict__ E,
+                                                         int64_t ldE) {
+    const EPairRef t = tiles[blockIdx.x];
+    const int pi = p[t.i], pj = p[t.j];
+    const int ni = nI[t.i];
+    const double* zt = Zt + zt_off[t.i];
+    const double* az = AZ + az_off[t.j];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    const int c = t.tc * 32 + tx;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l = 0; l < t.list_len; ++l) {
+        const int a = la[t.list_off + l], ps = lpos[t.list_off + l];
+        const double bv = (c < pj) ? az[(size_t)ps * pj + c] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = t.tr * 32 + ty + 8 * q;
+            if (r < pi) acc[q] = fma(zt[(size_t)r * ni + a], bv, acc[q]);
+        }
+    }
+    if (c < pj) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = t.tr * 32 + ty + 8 * q;
+            if (r < pi) E[(size_t)(coff[t.i] + r) * ldE + (coff[t.j] + c)] = acc[q];
+        }
+    }
+}
+
+void launch_e_offdiag(const EPairRef* tiles, int ntiles, const int32_t* la, const int32_t* lpos, const double* Zt,
+                      const int64_t* zt_off, const int32_t* nI, const double* AZ, const int64_t* az_off,
+                      const int32_t* p, const int64_t* coff, double* E, int64_t ldE, cudaStream_t s) {
+    if (ntiles > 0)
+        e_offdiag_kernel<<<ntiles, 256, 0, s>>>(tiles, la, lpos, Zt, zt_off, nI, AZ, az_off, p, coff, E, ldE);
+}
+
+// ------------------------------------------------------------------ reductions
+// Fixed grid (DOT_BLOCKS x 256) and fixed per-thread strides, then a fixed
+// tree in shared memory: the result is bitwise reproducible for a given n.
+__device__ __forceinline__ double block_sum_256(double v) {
+    __shared__ double red[256];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) dot_partials_kernel(int64_t n, const double* __restrict__ x,
+                                                            const double* __restrict__ y,
+                                                            double* __restrict__ partials) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)DOT_BLOCKS * 256)
+        s = fma(x[i], y[i], s);
+    s = block_sum_256(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+void launch_dot_partials(int64_t n, const double* x, const double* y, double* partials, cudaStream_t s) {
+    dot_partials_kernel<<<DOT_BLOCKS, 256, 0, s>>>(n, x, y, partials);
+}
+
+__global__ void __launch_bounds__(256) dot_finalize_kernel(const double* __restrict__ partials, PcgScal* sc,
+                                                            int which, double tol2) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < DOT_BLOCKS; i += 256) v += partials[i];
+    v = block_sum_256(v);
+    if (threadIdx.x == 0) {
+        switch (which) {
+            case 0:
+                sc->pq = v;
+                sc->alpha = sc->rz / v;
+                break;
+            case 1:
+                sc->rz_new = v;
+                sc->beta = v / sc->rz;
+                sc->rz = v;
+                break;
+            case 2:
+                sc->rr = v;
+                sc->iters += 1;
+                sc->conv = (v <= tol2 * sc->bb) ? 1 : 0;
+                break;
+            case 3:
+                sc->bb = v;
+                break;
+            case 4:
+                sc->rz = v;
+                break;
+            default:
+                sc->rr = v;
+                sc->conv = (v <= tol2 * sc->bb) ? 1 : 0;
+                break;
+        }
+    }
+}
+
+void launch_dot_finalize(const double* partials, PcgScal* sc, int which, double tol2, cudaStream_t s) {
+    dot_finalize_kernel<<<1, 256, 0, s>>>(partials, sc, which, tol2);
+}
+
+// x += alpha p; r -= alpha q; partial sums of r.r
+__global__ void __launch_bounds__(256) pcg_update_xr_kernel(int64_t n, double* __restrict__ x,
+                                                             double* __restrict__ r, const double* __restrict__ p,
+                                                             const double* __restrict__ q,
+                                                             const PcgScal* __restrict__ sc,
+                                                             double* __restrict__ partials) {
+    const double a = sc->alpha;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)DOT_BLOCKS * 256) {
+        x[i] = fma(a, p[i], x[i]);
+        const double ri = fma(-a, q[i], r[i]);
+        r[i] = ri;
+        s = fma(ri, ri, s);
+    }
+    s = block_sum_256(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+void launch_pcg_update_xr(int64_t n, double* x, double* r, const double* p, const double* q, const PcgScal* sc,
+                          double* partials, cudaStream_t s) {
+    pcg_update_xr_kernel<<<DOT_BLOCKS, 256, 0, s>>>(n, x, r, p, q, sc, partials);
+}
+
+// p = z + beta p
+__global__ void pcg_update_p_kernel(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                                    const PcgScal* __restrict__ sc) {
+    const double b = sc->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fma(b, p[i], z[i]);
+}
+
+void launch_pcg_update_p(int64_t n, double* p, const double* z, const PcgScal* sc, cudaStream_t s) {
+    pcg_update_p_kernel<<<DOT_BLOCKS, 256, 0, s>>>(n, p, z, sc);
+}
+
+// out = a x + b y
+__global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, double b,
+                             const double* __restrict__ y, double* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = fma(a, x[i], b * y[i]);
+}
+
+void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
+    if (n > 0) axpby_kernel<<<DOT_BLOCKS, 256, 0, s>>>(n, a, x, b, y, out);
+}
+
+}  // namespace amdd
