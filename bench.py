@@ -35,7 +35,7 @@ METRIC = "time-to-1e-8 residual (setup+solve), learned/mixed vs plain FP64, same
 WORKLOAD = "laplace2d_64x64_16box_ov1_tau50"
 RTOL = 1e-8
 FP64_PEAK_GFLOPS = 1250.0    # GB300 FP64 (profiling recipe's table); no FP64 figure is measured by the driver
-ALU_CLASSES = {"jacobi_svd", "jacobi_eig", "gemm_tiles", "chol_diag", "chol_panel", "trtri_diag", "e_offdiag"}
+ALU_CLASSES = {"jacobi_svd", "jacobi_eig", "jacobi_f32", "gemm_tiles", "chol_diag", "chol_panel", "trtri_diag", "e_offdiag"}
 
 
 def _workload():
@@ -283,6 +283,9 @@ def run_amdd(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": M.n, "nnz": int(M.rowptr[-1]), "N": w["N"], "overlap": w["overlap"],
                    "tau": w["tau"], "rtol": RTOL, "n_C": info.n_C, "pcg_iterations": its[-1],
+                   "jacobi": {"sweeps_svd": info.sweeps_svd, "sweeps_eig": info.sweeps_eig,
+                              "sweeps_svd_fp32": info.sweeps_svd32, "sweeps_eig_fp32": info.sweeps_eig32,
+                              "rotations_svd": info.rotations_svd, "rotations_eig": info.rotations_eig},
                    "oracle_pcg_iterations": base_its, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

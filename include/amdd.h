@@ -95,6 +95,10 @@ typedef struct {
     int32_t sweeps_svd;    /* largest Jacobi sweep count for the SVD of X_i */
     int32_t sweeps_eig;    /* largest Jacobi sweep count for eq. (Zi)      */
     double setup_ms;       /* wall time of amdd_setup                      */
+    int64_t rotations_svd; /* plane rotations applied by the SVD solver    */
+    int64_t rotations_eig; /* plane rotations applied by the eq. (Zi) solver */
+    int32_t sweeps_svd32;  /* sweeps of the FP32 preconditioning stage (SVD) */
+    int32_t sweeps_eig32;  /* sweeps of the FP32 preconditioning stage (eq. (Zi)) */
 } amdd_info;
 
 /* Fill `o` with the defaults (eps = 2^-52, max_sweeps = 60). */
@@ -184,7 +188,7 @@ amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, i
  * amdd_setup, amdd_apply and amdd_pcg_solve until amdd_reset_profile.
  * Synchronises the handle's stream.  AMDD_ERR_INVALID if profiling is off or
  * k is out of range. */
-#define AMDD_PROF_CLASSES 13
+#define AMDD_PROF_CLASSES 14
 amdd_status amdd_get_profile(amdd_handle* h, int32_t k, const char** name, int64_t* launches, double* ms,
                              double* flops, double* bytes);
 

@@ -37,7 +37,8 @@ class amdd_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("N", C.c_int32), ("overlap", C.c_int32), ("tau", C.c_double),
                 ("n_C", C.c_int64), ("sum_ni", C.c_int64), ("sum_nti", C.c_int64), ("max_ni", C.c_int32),
                 ("max_nti", C.c_int32), ("sweeps_svd", C.c_int32), ("sweeps_eig", C.c_int32),
-                ("setup_ms", C.c_double)]
+                ("setup_ms", C.c_double), ("rotations_svd", C.c_int64), ("rotations_eig", C.c_int64),
+                ("sweeps_svd32", C.c_int32), ("sweeps_eig32", C.c_int32)]
 
 
 class AmddError(RuntimeError):
@@ -197,7 +198,7 @@ def overlap_sets(n, rowptr, colind, part, i: int, overlap: int):
     return I, G, D
 
 
-PROF_CLASSES = 13
+PROF_CLASSES = 14
 
 
 def get_profile(h: int):

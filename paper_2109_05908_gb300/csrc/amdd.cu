@@ -47,6 +47,7 @@ enum ProfK {
     PK_TRTRI,
     PK_JAC_SVD,
     PK_JAC_EIG,
+    PK_JAC_F32,
     PK_SMALL,
     PK_E_ASM,
     PK_SPMV,
@@ -57,7 +58,7 @@ enum ProfK {
 };
 static_assert(PK_COUNT == AMDD_PROF_CLASSES, "profile classes");
 static const char* const kProfNames[PK_COUNT] = {
-    "gather_values", "chol_diag", "chol_panel", "gemm_tiles", "trtri_diag", "jacobi_svd", "jacobi_eig",
+    "gather_values", "chol_diag", "chol_panel", "gemm_tiles", "trtri_diag", "jacobi_svd", "jacobi_eig", "jacobi_f32",
     "small_dense", "e_offdiag", "spmv", "gemv_rows", "gather_scatter", "pcg_vectors"};
 
 struct ProfState {
@@ -124,7 +125,8 @@ struct amdd_handle {
     // host results
     std::vector<double> sigma_h;  // singular values of X_i, descending, at off_om
     std::vector<double> lam_h;    // eigenvalues of eq. (Zi), descending, at off_I
-    int sweeps_svd = 0, sweeps_eig = 0;
+    int sweeps_svd = 0, sweeps_eig = 0, sweeps_svd32 = 0, sweeps_eig32 = 0;
+    int64_t rot_svd = 0, rot_eig = 0;
     double setup_ms = 0.0;
     std::vector<void*> allocs;
 };
@@ -339,6 +341,89 @@ void transpose_batched(Ctx& C, const std::vector<const double*>& src, const std:
     launch_transpose(a, b, c, d, e, (int)src.size(), maxn, C.h->s);
 }
 
+// FP32 stage of the Jacobi solvers.  For each R x L matrix A_b (FP64, lda),
+// an FP32 one-sided Jacobi on the rows of [float(A_b) | I] accumulates
+// rotations Q32 with Q32 A_b nearly row-orthogonal (to FP32 accuracy); Q32 is
+// then made orthogonal to FP64 accuracy by Cholesky-QR (G = Q Q^T = L L^T,
+// Q <- L^{-1} Q).  The caller applies Q in FP64 and finishes with FP64 sweeps,
+// which then start from pairs that are orthogonal to ~1e-5 and converge in a
+// few sweeps.  `floor` adds the absolute rotation floor eps32 * max row norm^2
+// (used where only absolute accuracy of the rows is needed).
+struct PrecondJob {
+    const double* A;
+    int R, L, lda;
+    double* Q;  // R x R output
+};
+
+void fp32_precondition(Ctx& C, const std::vector<PrecondJob>& jobs, bool floor, int max_sweeps32, int* sweeps32,
+                       unsigned long long* rots32) {
+    amdd_handle* h = C.h;
+    const int nb = (int)jobs.size();
+    if (nb == 0) return;
+    std::vector<int64_t> o32(nb + 1, 0), oR(nb + 1, 0), oQ(nb + 1, 0), oL(nb + 1, 0);
+    int maxR = 1, maxL = 1;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t R = jobs[b].R, L = jobs[b].L;
+        o32[b + 1] = o32[b] + R * (L + R);
+        oR[b + 1] = oR[b] + R;
+        oQ[b + 1] = oQ[b] + R * R;
+        oL[b + 1] = oL[b] + (int64_t)cdiv(R, CHOL_NB) * CHOL_NB * CHOL_NB;
+        maxR = std::max<int>(maxR, (int)R);
+        maxL = std::max<int>(maxL, (int)L);
+    }
+    float* m32 = C.tnew<float>(o32[nb]);
+    float* n32 = C.tnew<float>(oR[nb]);
+    float* f32 = C.tnew<float>(nb);
+    double* Qraw = C.tnew<double>(oQ[nb]);
+    double* G = C.tnew<double>(oQ[nb]);
+    double* Y = C.tnew<double>(oQ[nb]);
+    double* linv = C.tnew<double>(oL[nb]);
+    std::vector<CvtDesc> cd(nb);
+    std::vector<JacobiDescT<float>> jd(nb);
+    for (int b = 0; b < nb; ++b) {
+        const PrecondJob& j = jobs[b];
+        cd[b] = {j.A, j.R, j.L, j.lda, m32 + o32[b], Qraw + oQ[b]};
+        jd[b] = {m32 + o32[b], j.R, j.L + j.R, j.L, j.L + j.R, n32 + oR[b], floor ? f32 + b : nullptr};
+    }
+    const CvtDesc* dcd = C.up(cd);
+    const JacobiDescT<float>* djd = C.up(jd);
+    {
+        PScope ps(h, PK_SMALL);
+        launch_to_f32_with_identity(dcd, nb, maxR, h->s);
+    }
+    if (floor) {
+        PScope ps(h, PK_SMALL);
+        launch_row_maxnorm2<float>(djd, nb, std::numeric_limits<float>::epsilon(), f32, h->s);
+    }
+    {
+        double fl = 0.0;  // one sweep's inner products (rotations add more; counted for the FP64 stage only)
+        for (const auto& j : jobs) fl += (double)j.R * (j.R - 1) / 2 * 2.0 * j.L;
+        PScope ps(h, PK_JAC_F32, fl);
+        const float tol32 = 8.0f * std::sqrt((float)maxL) * std::numeric_limits<float>::epsilon();
+        launch_jacobi_t<float>(djd, nb, max_sweeps32, tol32, sweeps32, rots32, h->d_err, 0, h->s);
+    }
+    {
+        PScope ps(h, PK_SMALL);
+        launch_extract_q(dcd, nb, maxR, h->s);
+    }
+    // Cholesky-QR re-orthogonalisation in FP64
+    std::vector<GemmDesc> g1, g2;
+    std::vector<CholDesc> ch;
+    std::vector<TrtriDesc> tr;
+    for (int b = 0; b < nb; ++b) {
+        const int R = jobs[b].R;
+        double* q = Qraw + oQ[b];
+        g1.push_back(gd(q, R, 0, q, R, 1, G + oQ[b], R, R, R, R, 1.0, 0.0, 1));
+        ch.push_back({G + oQ[b], R, R, R, nullptr, linv + oL[b]});
+        tr.push_back({G + oQ[b], Y + oQ[b], linv + oL[b], R, R, R});
+        g2.push_back(gd(Y + oQ[b], R, 0, q, R, 0, jobs[b].Q, R, R, R, R, 1.0, 0.0, 0));
+    }
+    gemm(C, g1);
+    chol_batched(C, ch);
+    trtri_batched(C, tr);
+    gemm(C, g2);
+}
+
 int read_err(amdd_handle* h) {
     int e = 0;
     ck(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
@@ -526,9 +611,12 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     double* delta = C.tnew<double>(N);
     double* linvA = C.tnew<double>(off_la[N]);
     double* linvM = C.tnew<double>(off_lm[N]);
-    int* sweeps = C.tnew<int>(2 * N);
-    unsigned long long* rots = C.tnew<unsigned long long>(2 * N);
-    ck(cudaMemsetAsync(rots, 0, 2 * N * sizeof(unsigned long long), s));
+    // sweeps / rotations: [FP64 SVD, FP64 eig, FP32 SVD, FP32 eig] x N
+    int* sweeps = C.tnew<int>(4 * N);
+    unsigned long long* rots = C.tnew<unsigned long long>(4 * N);
+    ck(cudaMemsetAsync(rots, 0, 4 * N * sizeof(unsigned long long), s));
+    double* nrm64 = C.tnew<double>(h->sum_ni);
+    double* absf64 = C.tnew<double>(N);
     h->d_Y = dnew<double>(h, h->sum_sq);
     h->d_Yt = dnew<double>(h, h->sum_sq);
     ck(cudaMemsetAsync(Araw, 0, h->sum_sq * sizeof(double), s));
@@ -570,15 +658,31 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         transpose_batched(C, src, dst, nn, ld, ld);
     }
 
-    // ---- (2) SVD of X_i by one-sided Jacobi on its rows (Sec. 3.2): rows
-    // become sigma_j v_j^T; sigma_j = row norms; rows scaled by sigma_j^{-1/2}.
+    // ---- (2) SVD of X_i (Sec. 3.2) by one-sided Jacobi on its rows: an
+    // FP32-preconditioned rotation Q_i (orthogonal to FP64 accuracy) is applied
+    // in FP64, X1_i = Q_i X_i, then FP64 sweeps make the rows of X1_i exactly
+    // orthogonal: rows become sigma_j v_j^T, sigma_j = row norms; rows are then
+    // scaled by sigma_j^{-1/2}.
     const double eps = h->eps;
+    double* X1 = C.tnew<double>(off_x[N]);
     {
+        std::vector<int64_t> oq(N + 1, 0);
+        for (int i = 0; i < N; ++i) oq[i + 1] = oq[i] + (int64_t)h->ni[i] * h->ni[i];
+        double* Q = C.tnew<double>(oq[N]);
+        std::vector<PrecondJob> pj(N);
+        std::vector<GemmDesc> g(N);
+        for (int i = 0; i < N; ++i) {
+            pj[i] = {Xp + off_x[i], h->ni[i], h->nt[i], h->nt[i], Q + oq[i]};
+            g[i] = gd(Q + oq[i], h->ni[i], 0, Xp + off_x[i], h->nt[i], 0, X1 + off_x[i], h->nt[i], h->ni[i],
+                      h->nt[i], h->ni[i], 1.0, 0.0, 0);
+        }
+        fp32_precondition(C, pj, false, 40, sweeps + 2 * N, rots + 2 * N);
+        gemm(C, g);
         std::vector<JacobiDesc> jd(N);
         std::vector<double*> sp(N);
         int maxc = 1;
         for (int i = 0; i < N; ++i) {
-            jd[i] = {Xp + off_x[i], h->ni[i], h->nt[i], h->nt[i], h->nt[i]};
+            jd[i] = {X1 + off_x[i], h->ni[i], h->nt[i], h->nt[i], h->nt[i], nrm64 + h->off_om[i], nullptr};
             sp[i] = sig + h->off_om[i];
             maxc = std::max(maxc, h->nt[i]);
         }
@@ -586,8 +690,8 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         double* const* dsp = C.up(sp);
         {
             PScope ps(h, PK_JAC_SVD);
-            launch_jacobi(djd, N, h->max_sweeps, std::numeric_limits<double>::epsilon() * maxc, sweeps, rots,
-                          h->d_err, s);
+            launch_jacobi_t<double>(djd, N, h->max_sweeps, std::numeric_limits<double>::epsilon() * maxc, sweeps,
+                                    rots, h->d_err, 1, s);
         }
         PScope ps(h, PK_SMALL);
         launch_rownorms(djd, N, dsp, delta, eps, 1, s);
@@ -600,7 +704,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         std::vector<int> nn(N), ld(N);
         for (int i = 0; i < N; ++i) {
             const int ni = h->ni[i], nt = h->nt[i];
-            double* Xi = Xp + off_x[i];
+            double* Xi = X1 + off_x[i];
             g[i] = gd(Xi, nt, 1, Xi, nt, 0, M + off_m[i], nt, nt, nt, ni, 1.0, 0.0, 1);
             mats[i] = M + off_m[i];
             nn[i] = nt;
@@ -658,24 +762,53 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     }
 
     // ---- (6) eigenvalues mu = 1/lambda of eq. (Zi) by one-sided Jacobi on
-    // the rows of [T | I]: rows of the left half become mu_j w_j^T, the right
-    // half accumulates the eigenvectors w_j.
+    // the rows of [T | I]: an FP32-preconditioned orthogonal Q_i (FP64
+    // accurate) gives T1 = Q T Q^T, nearly diagonal, and FP64 sweeps on the
+    // rows of [T1 | Q] finish: rows of the left half become mu_j w_j^T, the
+    // right half holds the eigenvectors w_j.  Only absolute accuracy of mu is
+    // needed (mu near 0 is the eps-cluster, selected for any tau), so pairs
+    // with |<p,q>| below eps * max row norm^2 are not rotated.
     {
+        double* Q = C.tnew<double>(off_P[N]);
+        std::vector<PrecondJob> pj(N);
+        std::vector<GemmDesc> g1(N), g2(N);
+        for (int i = 0; i < N; ++i) {
+            const int nIi = h->nI[i];
+            pj[i] = {TI + off_ti[i], nIi, nIi, 2 * nIi, Q + off_P[i]};
+            // P = Q T, T1 = P Q^T
+            g1[i] = gd(Q + off_P[i], nIi, 0, TI + off_ti[i], 2 * nIi, 0, Pb + off_P[i], nIi, nIi, nIi, nIi, 1.0,
+                       0.0, 0);
+            g2[i] = gd(Pb + off_P[i], nIi, 0, Q + off_P[i], nIi, 1, TI + off_ti[i], 2 * nIi, nIi, nIi, nIi, 1.0,
+                       0.0, 0);
+        }
+        fp32_precondition(C, pj, true, 40, sweeps + 3 * N, rots + 3 * N);
+        gemm(C, g1);
+        gemm(C, g2);
+        for (int i = 0; i < N; ++i) {
+            const int nIi = h->nI[i];
+            if (nIi == 0) continue;
+            ck(cudaMemcpy2DAsync(TI + off_ti[i] + nIi, 2 * nIi * sizeof(double), Q + off_P[i], nIi * sizeof(double),
+                                 nIi * sizeof(double), nIi, cudaMemcpyDeviceToDevice, s));
+        }
         std::vector<JacobiDesc> jd(N);
         std::vector<double*> mp(N);
         int maxc = 1;
         for (int i = 0; i < N; ++i) {
             const int nIi = h->nI[i];
-            jd[i] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi};
+            jd[i] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrm64 + h->off_om[i], absf64 + i};
             mp[i] = mu + h->off_I[i];
             maxc = std::max(maxc, nIi);
         }
         JacobiDesc* djd = C.up(jd);
         double* const* dmp = C.up(mp);
         {
+            PScope ps(h, PK_SMALL);
+            launch_row_maxnorm2<double>(djd, N, std::numeric_limits<double>::epsilon(), absf64, s);
+        }
+        {
             PScope ps(h, PK_JAC_EIG);
-            launch_jacobi(djd, N, h->max_sweeps, std::numeric_limits<double>::epsilon() * maxc, sweeps + N,
-                          rots + N, h->d_err, s);
+            launch_jacobi_t<double>(djd, N, h->max_sweeps, std::numeric_limits<double>::epsilon() * maxc,
+                                    sweeps + N, rots + N, h->d_err, 1, s);
         }
         PScope ps(h, PK_SMALL);
         launch_rownorms(djd, N, dmp, nullptr, 0.0, 0, s);
@@ -683,13 +816,13 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
 
     // ---- (7) selection lambda > 1/tau on the host
     std::vector<double> mu_h(h->sum_nI);
-    std::vector<int> sw(2 * N);
-    std::vector<unsigned long long> rot_h(2 * N);
+    std::vector<int> sw(4 * N);
+    std::vector<unsigned long long> rot_h(4 * N);
     h->sigma_h.resize(h->sum_ni);
-    ck(cudaMemcpyAsync(rot_h.data(), rots, 2 * N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(rot_h.data(), rots, 4 * N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     ck(cudaMemcpyAsync(mu_h.data(), mu, h->sum_nI * sizeof(double), cudaMemcpyDeviceToHost, s));
     ck(cudaMemcpyAsync(h->sigma_h.data(), sig, h->sum_ni * sizeof(double), cudaMemcpyDeviceToHost, s));
-    ck(cudaMemcpyAsync(sw.data(), sweeps, 2 * N * sizeof(int), cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(sw.data(), sweeps, 4 * N * sizeof(int), cudaMemcpyDeviceToHost, s));
     {
         const int e = read_err(h);
         if (e) throw Fail{err_status(e)};
@@ -697,11 +830,16 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     for (int i = 0; i < N; ++i) {
         h->sweeps_svd = std::max(h->sweeps_svd, sw[i]);
         h->sweeps_eig = std::max(h->sweeps_eig, sw[N + i]);
+        h->sweeps_svd32 = std::max(h->sweeps_svd32, sw[2 * N + i]);
+        h->sweeps_eig32 = std::max(h->sweeps_eig32, sw[3 * N + i]);
+        h->rot_svd += (int64_t)rot_h[i];
+        h->rot_eig += (int64_t)rot_h[N + i];
         if (h->prof.on) {
-            // inner products of every pair in every sweep, plus the rotations performed
+            // per sweep: row norms and one inner product per pair; plus the rotations performed
             const double ni = h->ni[i], nt = h->nt[i], nIi = h->nI[i];
-            h->prof.flops[PK_JAC_SVD] += sw[i] * ni * (ni - 1) / 2 * 6.0 * nt + rot_h[i] * 6.0 * nt;
-            h->prof.flops[PK_JAC_EIG] += sw[N + i] * nIi * (nIi - 1) / 2 * 6.0 * nIi + rot_h[N + i] * 12.0 * nIi;
+            h->prof.flops[PK_JAC_SVD] += sw[i] * (ni * 2.0 * nt + ni * (ni - 1) / 2 * 2.0 * nt) + rot_h[i] * 6.0 * nt;
+            h->prof.flops[PK_JAC_EIG] +=
+                sw[N + i] * (nIi * 2.0 * nIi + nIi * (nIi - 1) / 2 * 2.0 * nIi) + rot_h[N + i] * 12.0 * nIi;
         }
         std::sort(h->sigma_h.begin() + h->off_om[i], h->sigma_h.begin() + h->off_om[i + 1], std::greater<double>());
     }
@@ -1207,6 +1345,10 @@ amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
     info->sweeps_svd = h->sweeps_svd;
     info->sweeps_eig = h->sweeps_eig;
     info->setup_ms = h->setup_ms;
+    info->rotations_svd = h->rot_svd;
+    info->rotations_eig = h->rot_eig;
+    info->sweeps_svd32 = h->sweeps_svd32;
+    info->sweeps_eig32 = h->sweeps_eig32;
     return AMDD_OK;
 }
 

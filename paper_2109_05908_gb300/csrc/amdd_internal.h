@@ -67,11 +67,23 @@ struct ChunkRef {
     int desc, ct;  // column chunk (64 columns)
 };
 
-struct JacobiDesc {
-    double* A;        // rows x ld, rows orthogonalised in place
+template <typename T>
+struct JacobiDescT {
+    T* A;               // rows x ld, rows orthogonalised in place
     int rows, ld;
-    int ncols_dot;    // columns entering the inner products
-    int ncols_rot;    // columns rotated (>= ncols_dot)
+    int ncols_dot;      // columns entering the inner products
+    int ncols_rot;      // columns rotated (>= ncols_dot)
+    T* nrm2;            // rows scratch entries (squared row norms)
+    const T* absfloor;  // optional absolute floor on |<p,q>| below which no rotation is made
+};
+using JacobiDesc = JacobiDescT<double>;
+
+// Conversion descriptors of the FP32 preconditioning stage of the Jacobi solvers.
+struct CvtDesc {
+    const double* A;  // rows x L (lda)
+    int rows, L, lda;
+    float* out32;     // rows x (L + rows)
+    double* Q;        // rows x rows
 };
 
 // Row GEMV descriptors: y[row] = sum_{c in [c0(row), c1(row))} M[row][c] x[c].
@@ -88,8 +100,13 @@ void launch_chol_diag(const CholDesc* d, int nmat, int k0, int* err, cudaStream_
 void launch_chol_panel(const CholDesc* d, const PanelRef* tiles, int ntiles, int k0, cudaStream_t s);
 void launch_trtri_diag(const TrtriDesc* d, const ChunkRef* tiles, int ntiles, int k0, cudaStream_t s);
 void launch_set_identity(const TrtriDesc* d, int nmat, int maxn, cudaStream_t s);
-void launch_jacobi(const JacobiDesc* d, int nmat, int max_sweeps, double tol, int* sweeps, unsigned long long* rots,
-                   int* err, cudaStream_t s);
+template <typename T>
+void launch_jacobi_t(const JacobiDescT<T>* d, int nmat, int max_sweeps, T tol, int* sweeps, unsigned long long* rots,
+                     int* err, int report_noconv, cudaStream_t s);
+template <typename T>
+void launch_row_maxnorm2(const JacobiDescT<T>* d, int nmat, T eps, T* out, cudaStream_t s);
+void launch_to_f32_with_identity(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s);
+void launch_extract_q(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s);
 // sigma[j] = ||row j|| over ncols_dot; delta[mat] = eps * max_j sigma[j]; optionally
 // scale row j by 1/sqrt(sigma[j]).
 void launch_rownorms(const JacobiDesc* d, int nmat, double* const* sigma_ptrs, double* delta, double eps,

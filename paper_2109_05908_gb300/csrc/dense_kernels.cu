@@ -239,23 +239,33 @@ void launch_set_identity(const TrtriDesc* d, int nmat, int maxn, cudaStream_t s)
 }
 
 // ------------------------------------------------------------------ Jacobi
-// One-sided (Hestenes) Jacobi on the rows of each matrix: rotate row pairs
-// until every pair is orthogonal to tol relative to the row norms, over the
-// first ncols_dot columns; rotations are applied to ncols_rot columns (so an
-// identity appended on the right accumulates the rotations).  A cluster of
-// JAC_CLUSTER CTAs works on one matrix; each round of the round-robin
-// (circle) schedule holds rows/2 disjoint pairs, one warp per pair, and the
-// cluster barrier separates rounds.  Every thread of the cluster runs the same
-// number of barriers: the sweep loop ends on a value all threads compute
-// identically from the CTAs' shared flags (read through distributed shared
-// memory), and is bounded by max_sweeps.
+// One-sided (Hestenes) Jacobi on the rows of each matrix, in T = float or
+// double: rotate row pairs until every pair is orthogonal over the first
+// ncols_dot columns to tol relative to the row norms (and, when a floor is
+// given, above that absolute floor on |<p,q>|); rotations are applied to
+// ncols_rot columns (so an identity appended on the right accumulates them).
+// Row norms^2 are recomputed at the start of each sweep and updated exactly
+// after each rotation (a' = a - t g, b' = b + t g), so a pair that needs no
+// rotation costs one inner product.  A cluster of JAC_CLUSTER CTAs works on
+// one matrix; each round of the round-robin (circle) schedule holds rows/2
+// disjoint pairs, one warp per pair, and the cluster barrier separates
+// rounds.  Every thread of the cluster runs the same number of barriers: the
+// sweep loop ends on a value all threads compute identically from the CTAs'
+// shared flags (read through distributed shared memory), and is bounded by
+// max_sweeps.
+template <typename T>
+__device__ __forceinline__ T ldcg_t(const T* p) {
+    return __ldcg(p);
+}
+
+template <typename T>
 __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
-    jacobi_rows_kernel(const JacobiDesc* __restrict__ descs, int max_sweeps, double tol, int* __restrict__ sweeps,
-                       unsigned long long* __restrict__ rots, int* __restrict__ err) {
+    jacobi_rows_kernel(const JacobiDescT<T>* __restrict__ descs, int max_sweeps, T tol, int* __restrict__ sweeps,
+                       unsigned long long* __restrict__ rots, int* __restrict__ err, int report_noconv) {
     cg::cluster_group cluster = cg::this_cluster();
     const int mat = blockIdx.x / JAC_CLUSTER;
     const int crank = (int)cluster.block_rank();
-    const JacobiDesc d = descs[mat];
+    const JacobiDescT<T> d = descs[mat];
     __shared__ int rotated;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpc = blockDim.x >> 5;
@@ -263,10 +273,24 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
     const int m = d.rows + (d.rows & 1);
     const int npairs = m / 2;
     const int nrounds = m - 1;
+    const T absf = d.absfloor ? *d.absfloor : T(0);
     int sweep = 0;
     bool done = false;
     for (; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) rotated = 0;
+        // row norms^2 at the start of the sweep
+        for (int r = gw; r < d.rows; r += nw) {
+            const T* x = d.A + (size_t)r * d.ld;
+            T a = T(0);
+            for (int c = lane; c < d.ncols_dot; c += 32) {
+                const T u = ldcg_t(x + c);
+                a = fma(u, u, a);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) d.nrm2[r] = a;
+        }
+        __threadfence();
         cluster.sync();
         for (int r = 0; r < nrounds; ++r) {
             for (int k = gw; k < npairs; k += nw) {
@@ -279,32 +303,26 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
                     q = (r - k + (m - 1)) % (m - 1);
                 }
                 if (p >= d.rows || q >= d.rows) continue;
-                double* xp = d.A + (size_t)p * d.ld;
-                double* xq = d.A + (size_t)q * d.ld;
-                double a = 0.0, b = 0.0, g = 0.0;
-                for (int c = lane; c < d.ncols_dot; c += 32) {
-                    const double u = __ldcg(xp + c), v = __ldcg(xq + c);
-                    a = fma(u, u, a);
-                    b = fma(v, v, b);
-                    g = fma(u, v, g);
-                }
+                T* xp = d.A + (size_t)p * d.ld;
+                T* xq = d.A + (size_t)q * d.ld;
+                T g = T(0);
+                for (int c = lane; c < d.ncols_dot; c += 32) g = fma(ldcg_t(xp + c), ldcg_t(xq + c), g);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    b += __shfl_xor_sync(0xffffffffu, b, o);
-                    g += __shfl_xor_sync(0xffffffffu, g, o);
-                }
-                if (g != 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b)) {
-                    const double zeta = (b - a) / (2.0 * g);
-                    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-                    const double cs = 1.0 / sqrt(fma(t, t, 1.0));
-                    const double sn = cs * t;
+                for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+                const T a = ldcg_t(d.nrm2 + p), b = ldcg_t(d.nrm2 + q);
+                if (g != T(0) && fabs(g) > tol * sqrt(a) * sqrt(b) && fabs(g) > absf) {
+                    const T zeta = (b - a) / (T(2) * g);
+                    const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
+                    const T cs = T(1) / sqrt(fma(t, t, T(1)));
+                    const T sn = cs * t;
                     for (int c = lane; c < d.ncols_rot; c += 32) {
-                        const double u = __ldcg(xp + c), v = __ldcg(xq + c);
+                        const T u = ldcg_t(xp + c), v = ldcg_t(xq + c);
                         xp[c] = fma(cs, u, -sn * v);
                         xq[c] = fma(sn, u, cs * v);
                     }
                     if (lane == 0) {
+                        d.nrm2[p] = fma(-t, g, a);
+                        d.nrm2[q] = fma(t, g, b);
                         rotated = 1;
                         atomicAdd(rots + mat, 1ull);
                     }
@@ -324,13 +342,85 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
     }
     if (crank == 0 && threadIdx.x == 0) {
         sweeps[mat] = done ? sweep + 1 : sweep;
-        if (!done) atomicOr(err, DERR_EIG_NOCONV);
+        if (!done && report_noconv) atomicOr(err, DERR_EIG_NOCONV);
     }
 }
 
-void launch_jacobi(const JacobiDesc* d, int nmat, int max_sweeps, double tol, int* sweeps, unsigned long long* rots,
-                   int* err, cudaStream_t s) {
-    if (nmat > 0) jacobi_rows_kernel<<<nmat * JAC_CLUSTER, 256, 0, s>>>(d, max_sweeps, tol, sweeps, rots, err);
+template <typename T>
+void launch_jacobi_t(const JacobiDescT<T>* d, int nmat, int max_sweeps, T tol, int* sweeps, unsigned long long* rots,
+                     int* err, int report_noconv, cudaStream_t s) {
+    if (nmat > 0)
+        jacobi_rows_kernel<T><<<nmat * JAC_CLUSTER, 256, 0, s>>>(d, max_sweeps, tol, sweeps, rots, err, report_noconv);
+}
+template void launch_jacobi_t<float>(const JacobiDescT<float>*, int, int, float, int*, unsigned long long*, int*, int,
+                                     cudaStream_t);
+template void launch_jacobi_t<double>(const JacobiDescT<double>*, int, int, double, int*, unsigned long long*, int*,
+                                      int, cudaStream_t);
+
+// absfloor[mat] = eps * max_r ||row r||^2 over ncols_dot (one CTA per matrix).
+template <typename T>
+__global__ void __launch_bounds__(256) row_maxnorm2_kernel(const JacobiDescT<T>* __restrict__ descs, T eps,
+                                                            T* __restrict__ out) {
+    const JacobiDescT<T> d = descs[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ T wmax[8];
+    T mx = T(0);
+    for (int r = warp; r < d.rows; r += 8) {
+        const T* x = d.A + (size_t)r * d.ld;
+        T a = T(0);
+        for (int c = lane; c < d.ncols_dot; c += 32) a = fma(x[c], x[c], a);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        mx = a > mx ? a : mx;
+    }
+    if (lane == 0) wmax[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T m = T(0);
+        for (int w = 0; w < 8; ++w) m = wmax[w] > m ? wmax[w] : m;
+        out[blockIdx.x] = eps * m;
+    }
+}
+
+template <typename T>
+void launch_row_maxnorm2(const JacobiDescT<T>* d, int nmat, T eps, T* out, cudaStream_t s) {
+    if (nmat > 0) row_maxnorm2_kernel<T><<<nmat, 256, 0, s>>>(d, eps, out);
+}
+template void launch_row_maxnorm2<float>(const JacobiDescT<float>*, int, float, float*, cudaStream_t);
+template void launch_row_maxnorm2<double>(const JacobiDescT<double>*, int, double, double*, cudaStream_t);
+
+// out32 (rows x (L + rows), ld L + rows) = [float(A) | I] for A rows x L (lda).
+__global__ void to_f32_with_identity_kernel(const CvtDesc* __restrict__ descs) {
+    const CvtDesc d = descs[blockIdx.y];
+    const int w = d.L + d.rows;
+    for (int r = blockIdx.x; r < d.rows; r += gridDim.x) {
+        const double* a = d.A + (size_t)r * d.lda;
+        float* o = d.out32 + (size_t)r * w;
+        for (int c = threadIdx.x; c < w; c += blockDim.x) o[c] = (c < d.L) ? (float)a[c] : (c - d.L == r ? 1.f : 0.f);
+    }
+}
+
+void launch_to_f32_with_identity(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s) {
+    if (nmat <= 0 || maxrows <= 0) return;
+    dim3 grid(min(maxrows, 1024), nmat);
+    to_f32_with_identity_kernel<<<grid, 256, 0, s>>>(d);
+}
+
+// Q64 (rows x rows) = double(right block of out32).
+__global__ void extract_q_kernel(const CvtDesc* __restrict__ descs) {
+    const CvtDesc d = descs[blockIdx.y];
+    const int w = d.L + d.rows;
+    for (int r = blockIdx.x; r < d.rows; r += gridDim.x) {
+        const float* o = d.out32 + (size_t)r * w + d.L;
+        double* q = d.Q + (size_t)r * d.rows;
+        for (int c = threadIdx.x; c < d.rows; c += blockDim.x) q[c] = (double)o[c];
+    }
+}
+
+void launch_extract_q(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s) {
+    if (nmat <= 0 || maxrows <= 0) return;
+    dim3 grid(min(maxrows, 1024), nmat);
+    extract_q_kernel<<<grid, 256, 0, s>>>(d);
 }
 
 // Row norms over ncols_dot, delta = eps * max norm, optional row scaling by
