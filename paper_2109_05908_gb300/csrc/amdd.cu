@@ -616,7 +616,6 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     unsigned long long* rots = C.tnew<unsigned long long>(4 * N);
     ck(cudaMemsetAsync(rots, 0, 4 * N * sizeof(unsigned long long), s));
     double* nrm64 = C.tnew<double>(h->sum_ni);
-    double* absf64 = C.tnew<double>(N);
     h->d_Y = dnew<double>(h, h->sum_sq);
     h->d_Yt = dnew<double>(h, h->sum_sq);
     ck(cudaMemsetAsync(Araw, 0, h->sum_sq * sizeof(double), s));
@@ -690,8 +689,9 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         double* const* dsp = C.up(sp);
         {
             PScope ps(h, PK_JAC_SVD);
-            launch_jacobi_t<double>(djd, N, h->max_sweeps, std::numeric_limits<double>::epsilon() * maxc, sweeps,
-                                    rots, h->d_err, 1, s);
+            launch_jacobi_t<double>(djd, N, h->max_sweeps,
+                                    2.0 * std::sqrt((double)maxc) * std::numeric_limits<double>::epsilon(), sweeps, rots,
+                                    h->d_err, 1, s);
         }
         PScope ps(h, PK_SMALL);
         launch_rownorms(djd, N, dsp, delta, eps, 1, s);
@@ -762,52 +762,26 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     }
 
     // ---- (6) eigenvalues mu = 1/lambda of eq. (Zi) by one-sided Jacobi on
-    // the rows of [T | I]: an FP32-preconditioned orthogonal Q_i (FP64
-    // accurate) gives T1 = Q T Q^T, nearly diagonal, and FP64 sweeps on the
-    // rows of [T1 | Q] finish: rows of the left half become mu_j w_j^T, the
-    // right half holds the eigenvectors w_j.  Only absolute accuracy of mu is
-    // needed (mu near 0 is the eps-cluster, selected for any tau), so pairs
-    // with |<p,q>| below eps * max row norm^2 are not rotated.
+    // the rows of [T | I] in FP64: rows of the left half become mu_j w_j^T,
+    // the right half accumulates the eigenvectors w_j.  The criterion is
+    // relative to the rows' own norms (no absolute floor), so small mu keep
+    // their accuracy.  (An FP32 preconditioning stage does not pay here: the
+    // spectrum near mu = 1 is denser than FP32 can resolve.)
     {
-        double* Q = C.tnew<double>(off_P[N]);
-        std::vector<PrecondJob> pj(N);
-        std::vector<GemmDesc> g1(N), g2(N);
-        for (int i = 0; i < N; ++i) {
-            const int nIi = h->nI[i];
-            pj[i] = {TI + off_ti[i], nIi, nIi, 2 * nIi, Q + off_P[i]};
-            // P = Q T, T1 = P Q^T
-            g1[i] = gd(Q + off_P[i], nIi, 0, TI + off_ti[i], 2 * nIi, 0, Pb + off_P[i], nIi, nIi, nIi, nIi, 1.0,
-                       0.0, 0);
-            g2[i] = gd(Pb + off_P[i], nIi, 0, Q + off_P[i], nIi, 1, TI + off_ti[i], 2 * nIi, nIi, nIi, nIi, 1.0,
-                       0.0, 0);
-        }
-        fp32_precondition(C, pj, true, 40, sweeps + 3 * N, rots + 3 * N);
-        gemm(C, g1);
-        gemm(C, g2);
-        for (int i = 0; i < N; ++i) {
-            const int nIi = h->nI[i];
-            if (nIi == 0) continue;
-            ck(cudaMemcpy2DAsync(TI + off_ti[i] + nIi, 2 * nIi * sizeof(double), Q + off_P[i], nIi * sizeof(double),
-                                 nIi * sizeof(double), nIi, cudaMemcpyDeviceToDevice, s));
-        }
         std::vector<JacobiDesc> jd(N);
         std::vector<double*> mp(N);
         int maxc = 1;
         for (int i = 0; i < N; ++i) {
             const int nIi = h->nI[i];
-            jd[i] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrm64 + h->off_om[i], absf64 + i};
+            jd[i] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrm64 + h->off_om[i], nullptr};
             mp[i] = mu + h->off_I[i];
             maxc = std::max(maxc, nIi);
         }
         JacobiDesc* djd = C.up(jd);
         double* const* dmp = C.up(mp);
         {
-            PScope ps(h, PK_SMALL);
-            launch_row_maxnorm2<double>(djd, N, std::numeric_limits<double>::epsilon(), absf64, s);
-        }
-        {
             PScope ps(h, PK_JAC_EIG);
-            launch_jacobi_t<double>(djd, N, h->max_sweeps, std::numeric_limits<double>::epsilon() * maxc,
+            launch_jacobi_t<double>(djd, N, h->max_sweeps, 2.0 * std::sqrt((double)maxc) * std::numeric_limits<double>::epsilon(),
                                     sweeps + N, rots + N, h->d_err, 1, s);
         }
         PScope ps(h, PK_SMALL);
