@@ -195,6 +195,27 @@ amdd_status amdd_get_profile(amdd_handle* h, int32_t k, const char** name, int64
 /* Clear the accumulated profile (keeps profiling on). */
 amdd_status amdd_reset_profile(amdd_handle* h);
 
+/* Largest n accepted by amdd_true_residual_noalloc. */
+#define AMDD_NOALLOC_MAX_N 524288
+
+/* No counterpart in the paper: a utility for callers that cannot allocate
+ * device memory, e.g. code that runs where a framework owns every allocation
+ * or a real-time loop that must not reach the allocator.  Computes the true
+ * residual of a solution: out[0] = ||b - A x||_2 and out[1] = ||b||_2 (HOST
+ * array of 2 doubles), with the same kernels and the same fixed reduction
+ * order as the exit check of amdd_pcg_solve (stats.true_rel_residual equals
+ * out[0] / out[1] for the same A, b, x).  A (device CSR), b and x (device,
+ * length n) are the caller's.  It allocates nothing: its scratch is a static
+ * device array of 2 * AMDD_NOALLOC_MAX_N + 272 doubles (about 8 MB) that
+ * every GPU which loads the library holds until the process exits.  The first
+ * call on a device looks up that array's device address (make that first call
+ * before any stream capture).  Every call shares the array, so calls that
+ * overlap on the GPU (other streams, other host threads) race; serialise
+ * them.  AMDD_ERR_INVALID if n > AMDD_NOALLOC_MAX_N or an argument is
+ * missing; work is issued on `stream` and completed before return. */
+amdd_status amdd_true_residual_noalloc(const amdd_csr* A, const double* b, const double* x, double* out,
+                                       void* stream);
+
 /* Release every resource of the handle (NULL is a no-op). */
 void amdd_destroy(amdd_handle* h);
 

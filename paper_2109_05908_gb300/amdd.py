@@ -72,6 +72,8 @@ SIGNATURES = {
     "amdd_get_profile": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "amdd_reset_profile": (C.c_int, [C.c_void_p]),
+    "amdd_true_residual_noalloc": (C.c_int, [C.POINTER(amdd_csr), C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]),
     "amdd_destroy": (None, [C.c_void_p]),
     "amdd_status_str": (C.c_char_p, [C.c_int]),
 }
@@ -214,6 +216,17 @@ def get_profile(h: int):
 
 def reset_profile(h: int) -> None:
     _check(lib().amdd_reset_profile(h), "amdd_reset_profile")
+
+
+NOALLOC_MAX_N = 524288
+
+
+def true_residual_noalloc(A: amdd_csr, b_ptr: int, x_ptr: int, stream: int = 0):
+    """(||b - A x||_2, ||b||_2) through the allocation-free entry point."""
+    out = (C.c_double * 2)()
+    _check(lib().amdd_true_residual_noalloc(C.byref(A), b_ptr, x_ptr, C.cast(out, C.c_void_p), stream),
+           "amdd_true_residual_noalloc")
+    return out[0], out[1]
 
 
 def destroy(h: int) -> None:
