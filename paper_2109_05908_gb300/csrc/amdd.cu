@@ -341,6 +341,19 @@ void transpose_batched(Ctx& C, const std::vector<const double*>& src, const std:
     launch_transpose(a, b, c, d, e, (int)src.size(), maxn, C.h->s);
 }
 
+// One-sided Jacobi on the rows of a batch: the shared-memory-resident block
+// kernel when the two row blocks of the largest matrix fit, else the kernel
+// that keeps the rows in global memory.
+template <typename T>
+void run_jacobi(amdd_handle* h, const std::vector<JacobiDescT<T>>& jd, const JacobiDescT<T>* djd, int max_sweeps, T tol,
+                int* sweeps, unsigned long long* rots, int report_noconv) {
+    size_t smem = 0;
+    for (const auto& j : jd) smem = std::max(smem, jacobi_block_smem<T>(j.rows, j.ncols_rot));
+    if (!launch_jacobi_block<T>(djd, (int)jd.size(), smem, max_sweeps, tol, sweeps, rots, h->d_err, report_noconv,
+                                h->s))
+        launch_jacobi_t<T>(djd, (int)jd.size(), max_sweeps, tol, sweeps, rots, h->d_err, report_noconv, h->s);
+}
+
 // FP32 stage of the Jacobi solvers.  For each R x L matrix A_b (FP64, lda),
 // an FP32 one-sided Jacobi on the rows of [float(A_b) | I] accumulates
 // rotations Q32 with Q32 A_b nearly row-orthogonal (to FP32 accuracy); Q32 is
@@ -400,7 +413,7 @@ void fp32_precondition(Ctx& C, const std::vector<PrecondJob>& jobs, bool floor, 
         for (const auto& j : jobs) fl += (double)j.R * (j.R - 1) / 2 * 2.0 * j.L;
         PScope ps(h, PK_JAC_F32, fl);
         const float tol32 = 8.0f * std::sqrt((float)maxL) * std::numeric_limits<float>::epsilon();
-        launch_jacobi_t<float>(djd, nb, max_sweeps32, tol32, sweeps32, rots32, h->d_err, 0, h->s);
+        run_jacobi<float>(h, jd, djd, max_sweeps32, tol32, sweeps32, rots32, 0);
     }
     {
         PScope ps(h, PK_SMALL);
@@ -689,9 +702,8 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         double* const* dsp = C.up(sp);
         {
             PScope ps(h, PK_JAC_SVD);
-            launch_jacobi_t<double>(djd, N, h->max_sweeps,
-                                    2.0 * std::sqrt((double)maxc) * std::numeric_limits<double>::epsilon(), sweeps, rots,
-                                    h->d_err, 1, s);
+            run_jacobi<double>(h, jd, djd, h->max_sweeps,
+                               2.0 * std::sqrt((double)maxc) * std::numeric_limits<double>::epsilon(), sweeps, rots, 1);
         }
         PScope ps(h, PK_SMALL);
         launch_rownorms(djd, N, dsp, delta, eps, 1, s);
@@ -781,8 +793,9 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         double* const* dmp = C.up(mp);
         {
             PScope ps(h, PK_JAC_EIG);
-            launch_jacobi_t<double>(djd, N, h->max_sweeps, 2.0 * std::sqrt((double)maxc) * std::numeric_limits<double>::epsilon(),
-                                    sweeps + N, rots + N, h->d_err, 1, s);
+            run_jacobi<double>(h, jd, djd, h->max_sweeps,
+                               2.0 * std::sqrt((double)maxc) * std::numeric_limits<double>::epsilon(), sweeps + N,
+                               rots + N, 1);
         }
         PScope ps(h, PK_SMALL);
         launch_rownorms(djd, N, dmp, nullptr, 0.0, 0, s);

@@ -86,6 +86,17 @@ struct CvtDesc {
     double* Q;        // rows x rows
 };
 
+// Symmetric tridiagonal reduction and bisection (eigenvalues only).
+struct TridiagDesc {
+    double* A;  // n x n symmetric, full storage (ld); destroyed
+    int n, ld;
+    double* d;  // n
+    double* e;  // n (e[i] = T[i][i-1], e[0] = 0)
+};
+void launch_tridiag(const TridiagDesc* d, int nmat, int maxn, cudaStream_t s);
+void launch_bisect(const TridiagDesc* d, const int* eig_mat, const int* eig_idx, int64_t total, double* const* out,
+                   cudaStream_t s);
+
 // Row GEMV descriptors: y[row] = sum_{c in [c0(row), c1(row))} M[row][c] x[c].
 // mode 0: full row [0, ncols); mode 1: lower [0, row]; mode 2: upper [row, ncols).
 struct GemvDesc {
@@ -103,6 +114,14 @@ void launch_set_identity(const TrtriDesc* d, int nmat, int maxn, cudaStream_t s)
 template <typename T>
 void launch_jacobi_t(const JacobiDescT<T>* d, int nmat, int max_sweeps, T tol, int* sweeps, unsigned long long* rots,
                      int* err, int report_noconv, cudaStream_t s);
+// Shared-memory-resident block variant; returns false (nothing launched) when
+// the two row blocks of the largest matrix do not fit in shared memory.
+constexpr size_t JAC_BLOCK_SMEM_MAX = 220 * 1024;
+template <typename T>
+size_t jacobi_block_smem(int rows, int ncols_rot);
+template <typename T>
+bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem, int max_sweeps, T tol, int* sweeps,
+                         unsigned long long* rots, int* err, int report_noconv, cudaStream_t s);
 template <typename T>
 void launch_row_maxnorm2(const JacobiDescT<T>* d, int nmat, T eps, T* out, cudaStream_t s);
 void launch_to_f32_with_identity(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s);

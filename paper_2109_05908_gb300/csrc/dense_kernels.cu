@@ -258,6 +258,23 @@ __device__ __forceinline__ T ldcg_t(const T* p) {
     return __ldcg(p);
 }
 
+// Rotation that makes rows p, q (Gram [[a, g], [g, b]]) orthogonal:
+// t = tan(theta) is the smaller root of t^2 + 2 zeta t - 1 = 0, zeta =
+// (b - a) / (2 g), written as t = sign(b - a) 2 g / (|b - a| + sqrt((b - a)^2 +
+// 4 g^2)) so that one square root, one division and one reciprocal square
+// root suffice; cs = 1/sqrt(1 + t^2), sn = cs t.
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ void jac_rotation(T a, T b, T g, T& cs, T& sn, T& t) {
+    const T dd = b - a;
+    const T g2 = g + g;
+    t = copysign(T(1), dd) * g2 / (fabs(dd) + sqrt(fma(dd, dd, g2 * g2)));
+    cs = rsqrt_t(fma(t, t, T(1)));
+    sn = cs * t;
+}
+
 template <typename T>
 __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
     jacobi_rows_kernel(const JacobiDescT<T>* __restrict__ descs, int max_sweeps, T tol, int* __restrict__ sweeps,
@@ -305,16 +322,20 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
                 if (p >= d.rows || q >= d.rows) continue;
                 T* xp = d.A + (size_t)p * d.ld;
                 T* xq = d.A + (size_t)q * d.ld;
-                T g = T(0);
-                for (int c = lane; c < d.ncols_dot; c += 32) g = fma(ldcg_t(xp + c), ldcg_t(xq + c), g);
+                T g0 = T(0), g1 = T(0);
+                int c = lane;
+                for (; c + 32 < d.ncols_dot; c += 64) {
+                    g0 = fma(ldcg_t(xp + c), ldcg_t(xq + c), g0);
+                    g1 = fma(ldcg_t(xp + c + 32), ldcg_t(xq + c + 32), g1);
+                }
+                if (c < d.ncols_dot) g0 = fma(ldcg_t(xp + c), ldcg_t(xq + c), g0);
+                T g = g0 + g1;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
                 const T a = ldcg_t(d.nrm2 + p), b = ldcg_t(d.nrm2 + q);
-                if (g != T(0) && fabs(g) > tol * sqrt(a) * sqrt(b) && fabs(g) > absf) {
-                    const T zeta = (b - a) / (T(2) * g);
-                    const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
-                    const T cs = T(1) / sqrt(fma(t, t, T(1)));
-                    const T sn = cs * t;
+                if (g != T(0) && g * g > tol * tol * a * b && fabs(g) > absf) {
+                    T cs, sn, t;
+                    jac_rotation(a, b, g, cs, sn, t);
                     for (int c = lane; c < d.ncols_rot; c += 32) {
                         const T u = ldcg_t(xp + c), v = ldcg_t(xq + c);
                         xp[c] = fma(cs, u, -sn * v);
@@ -356,6 +377,188 @@ template void launch_jacobi_t<float>(const JacobiDescT<float>*, int, int, float,
                                      cudaStream_t);
 template void launch_jacobi_t<double>(const JacobiDescT<double>*, int, int, double, int*, unsigned long long*, int*,
                                       int, cudaStream_t);
+
+// ------------------------------------------------------------------ block Jacobi
+// The same one-sided Jacobi with the rows resident in shared memory: the
+// matrix is cut into 2 * JAC_CLUSTER row blocks of hb rows; in each block
+// round every CTA of the cluster loads two blocks (P, Q) from global memory,
+// performs all row pairs between them (hb sub-rounds of hb disjoint pairs,
+// one warp per pair, __syncthreads between sub-rounds), and in the first
+// block round also the pairs inside each block; it then writes the blocks
+// back.  The blocks meet in a round-robin (circle) schedule, so one sweep
+// visits every row pair once, with one cluster barrier per block round
+// (2 * JAC_CLUSTER - 1 per sweep).  Row norms^2 are recomputed when a block is
+// loaded and updated exactly after each rotation.
+template <typename T>
+__device__ __forceinline__ bool jac_pair(T* __restrict__ xp, T* __restrict__ xq, T* __restrict__ ap,
+                                         T* __restrict__ aq, int D, int W, T tol, int lane) {
+    T g0 = T(0), g1 = T(0);
+    int c = lane;
+    for (; c + 32 < D; c += 64) {
+        g0 = fma(xp[c], xq[c], g0);
+        g1 = fma(xp[c + 32], xq[c + 32], g1);
+    }
+    if (c < D) g0 = fma(xp[c], xq[c], g0);
+    T g = g0 + g1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    const T a = *ap, b = *aq;
+    if (!(g != T(0) && g * g > tol * tol * a * b)) return false;
+    T cs, sn, t;
+    jac_rotation(a, b, g, cs, sn, t);
+    for (int c = lane; c < W; c += 32) {
+        const T u = xp[c], v = xq[c];
+        xp[c] = fma(cs, u, -sn * v);
+        xq[c] = fma(sn, u, cs * v);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        *ap = fma(-t, g, a);
+        *aq = fma(t, g, b);
+    }
+    __syncwarp();
+    return true;
+}
+
+template <typename T>
+__global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
+    jacobi_block_kernel(const JacobiDescT<T>* __restrict__ descs, int max_sweeps, T tol, int* __restrict__ sweeps,
+                        unsigned long long* __restrict__ rots, int* __restrict__ err, int report_noconv) {
+    extern __shared__ __align__(16) unsigned char jac_smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int mat = blockIdx.x / JAC_CLUSTER;
+    const int crank = (int)cluster.block_rank();
+    const JacobiDescT<T> d = descs[mat];
+    constexpr int NBLK = 2 * JAC_CLUSTER;
+    const int hb = (d.rows + NBLK - 1) / NBLK;
+    const int W = d.ncols_rot, D = d.ncols_dot;
+    T* blk = reinterpret_cast<T*>(jac_smem);  // [2][hb][W]
+    T* nrm = blk + (size_t)2 * hb * W;        // [2][hb]
+    __shared__ int rotated;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int hbe = hb + (hb & 1);
+    unsigned long long my_rots = 0;
+    int sweep = 0;
+    bool done = false;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
+        for (int br = 0; br < NBLK - 1; ++br) {
+            int P, Q;
+            if (crank == 0) {
+                P = NBLK - 1;
+                Q = br;
+            } else {
+                P = (br + crank) % (NBLK - 1);
+                Q = (br - crank + NBLK - 1) % (NBLK - 1);
+            }
+            const int r0[2] = {P * hb, Q * hb};
+            int nr[2];
+            for (int k = 0; k < 2; ++k) nr[k] = max(0, min(hb, d.rows - r0[k]));
+            for (int k = 0; k < 2; ++k)
+                for (int r = warp; r < nr[k]; r += nwarps) {
+                    const T* src = d.A + (size_t)(r0[k] + r) * d.ld;
+                    T* dst = blk + ((size_t)k * hb + r) * W;
+                    T a = T(0);
+                    for (int c = lane; c < W; c += 32) {
+                        const T v = __ldcg(src + c);
+                        dst[c] = v;
+                        if (c < D) a = fma(v, v, a);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                    if (lane == 0) nrm[k * hb + r] = a;
+                }
+            __syncthreads();
+            if (br == 0) {
+                // pairs inside each of the two blocks (circle schedule on hbe)
+                for (int sr = 0; sr < hbe - 1; ++sr) {
+                    for (int k = warp; k < hbe; k += nwarps) {
+                        const int which = k / (hbe / 2), kk = k % (hbe / 2);
+                        int a, b;
+                        if (kk == 0) {
+                            a = hbe - 1;
+                            b = sr;
+                        } else {
+                            a = (sr + kk) % (hbe - 1);
+                            b = (sr - kk + (hbe - 1)) % (hbe - 1);
+                        }
+                        if (a >= nr[which] || b >= nr[which]) continue;
+                        T* base = blk + (size_t)which * hb * W;
+                        if (jac_pair<T>(base + (size_t)a * W, base + (size_t)b * W, nrm + which * hb + a,
+                                        nrm + which * hb + b, D, W, tol, lane) &&
+                            lane == 0) {
+                            ++my_rots;
+                            rotated = 1;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            // pairs between the two blocks
+            for (int sr = 0; sr < hb; ++sr) {
+                for (int a = warp; a < hb; a += nwarps) {
+                    const int b = (a + sr) % hb;
+                    if (a >= nr[0] || b >= nr[1]) continue;
+                    if (jac_pair<T>(blk + (size_t)a * W, blk + ((size_t)hb + b) * W, nrm + a, nrm + hb + b, D, W, tol,
+                                    lane) &&
+                        lane == 0) {
+                        ++my_rots;
+                        rotated = 1;
+                    }
+                }
+                __syncthreads();
+            }
+            for (int k = 0; k < 2; ++k)
+                for (int r = warp; r < nr[k]; r += nwarps) {
+                    T* dst = d.A + (size_t)(r0[k] + r) * d.ld;
+                    const T* src = blk + ((size_t)k * hb + r) * W;
+                    for (int c = lane; c < W; c += 32) dst[c] = src[c];
+                }
+            __threadfence();
+            cluster.sync();
+        }
+        int any = 0;
+#pragma unroll
+        for (int rr = 0; rr < JAC_CLUSTER; ++rr) any |= *cluster.map_shared_rank(&rotated, rr);
+        cluster.sync();
+        if (!any) {
+            done = true;
+            break;
+        }
+    }
+    if (lane == 0 && my_rots) atomicAdd(rots + mat, my_rots);
+    if (crank == 0 && threadIdx.x == 0) {
+        sweeps[mat] = done ? sweep + 1 : sweep;
+        if (!done && report_noconv) atomicOr(err, DERR_EIG_NOCONV);
+    }
+}
+
+template <typename T>
+size_t jacobi_block_smem(int rows, int ncols_rot) {
+    const size_t hb = (size_t)(rows + 2 * JAC_CLUSTER - 1) / (2 * JAC_CLUSTER);
+    return (2 * hb * (size_t)ncols_rot + 2 * hb) * sizeof(T);
+}
+template size_t jacobi_block_smem<float>(int, int);
+template size_t jacobi_block_smem<double>(int, int);
+
+template <typename T>
+bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem, int max_sweeps, T tol, int* sweeps,
+                         unsigned long long* rots, int* err, int report_noconv, cudaStream_t s) {
+    if (nmat <= 0) return true;
+    if (smem > JAC_BLOCK_SMEM_MAX) return false;
+    if (cudaFuncSetAttribute(jacobi_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    jacobi_block_kernel<T><<<nmat * JAC_CLUSTER, 256, smem, s>>>(d, max_sweeps, tol, sweeps, rots, err, report_noconv);
+    return true;
+}
+template bool launch_jacobi_block<float>(const JacobiDescT<float>*, int, size_t, int, float, int*,
+                                         unsigned long long*, int*, int, cudaStream_t);
+template bool launch_jacobi_block<double>(const JacobiDescT<double>*, int, size_t, int, double, int*,
+                                          unsigned long long*, int*, int, cudaStream_t);
 
 // absfloor[mat] = eps * max_r ||row r||^2 over ncols_dot (one CTA per matrix).
 template <typename T>
@@ -523,6 +726,149 @@ void launch_transpose(const double* const* src, double* const* dst, const int* n
     const int nt = (maxn + 31) / 32;
     dim3 grid(min(nt * nt, 4096), 1, nmat);
     transpose_kernel<<<grid, 256, 0, s>>>(src, dst, n, lds, ldd);
+}
+
+// ------------------------------------------------------------------ tridiagonal eigenvalues
+// Householder reduction of a symmetric n x n matrix (full storage, updated in
+// place) to tridiagonal form T = Q^T A Q, one CTA per matrix: at step k the
+// reflector H = I - beta v v^T maps A[k+1:, k] onto alpha e_1, and the trailing
+// block becomes H A22 H = A22 - v w^T - w v^T with p = beta A22 v,
+// w = p - (beta/2)(p^T v) v.  Output: diagonal d[0..n) and sub-diagonal
+// e[1..n) (e[0] = 0).
+__device__ __forceinline__ double block_sum_1024(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) r += red[w];
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) tridiag_kernel(const TridiagDesc* __restrict__ descs) {
+    const TridiagDesc t = descs[blockIdx.x];
+    const int n = t.n;
+    extern __shared__ double tri_smem[];
+    double* v = tri_smem;      // n
+    double* p = v + n;         // n
+    __shared__ double red[32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    double* A = t.A;
+    if (tid == 0) t.e[0] = 0.0;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;  // length of v
+        double sl = 0.0;
+        for (int i = tid; i < m; i += blockDim.x) {
+            const double x = A[(size_t)(k + 1 + i) * t.ld + k];
+            sl = fma(x, x, sl);
+        }
+        const double s2 = block_sum_1024(sl, red);
+        const double x0 = A[(size_t)(k + 1) * t.ld + k];
+        const double tail = s2 - x0 * x0;
+        if (tid == 0) t.d[k] = A[(size_t)k * t.ld + k];
+        if (!(tail > 0.0)) {  // column already in tridiagonal form
+            if (tid == 0) t.e[k + 1] = x0;
+            __syncthreads();
+            continue;
+        }
+        const double alpha = -copysign(sqrt(s2), x0);
+        const double v0 = x0 - alpha;
+        const double beta = 2.0 / fma(v0, v0, tail);
+        for (int i = tid; i < m; i += blockDim.x) v[i] = (i == 0) ? v0 : A[(size_t)(k + 1 + i) * t.ld + k];
+        __syncthreads();
+        // p = beta A22 v (one warp per row)
+        for (int i = warp; i < m; i += nw) {
+            const double* row = A + (size_t)(k + 1 + i) * t.ld + (k + 1);
+            double acc0 = 0.0, acc1 = 0.0;
+            int j = lane;
+            for (; j + 32 < m; j += 64) {
+                acc0 = fma(row[j], v[j], acc0);
+                acc1 = fma(row[j + 32], v[j + 32], acc1);
+            }
+            if (j < m) acc0 = fma(row[j], v[j], acc0);
+            double acc = acc0 + acc1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) p[i] = beta * acc;
+        }
+        __syncthreads();
+        double kl = 0.0;
+        for (int i = tid; i < m; i += blockDim.x) kl = fma(p[i], v[i], kl);
+        const double K = 0.5 * beta * block_sum_1024(kl, red);
+        for (int i = tid; i < m; i += blockDim.x) p[i] = fma(-K, v[i], p[i]);  // w
+        __syncthreads();
+        for (int i = warp; i < m; i += nw) {
+            double* row = A + (size_t)(k + 1 + i) * t.ld + (k + 1);
+            const double vi = v[i], wi = p[i];
+            for (int j = lane; j < m; j += 32) row[j] = fma(-vi, p[j], fma(-wi, v[j], row[j]));
+        }
+        if (tid == 0) t.e[k + 1] = alpha;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (n >= 2) {
+            t.d[n - 2] = A[(size_t)(n - 2) * t.ld + (n - 2)];
+            t.e[n - 1] = A[(size_t)(n - 1) * t.ld + (n - 2)];
+        }
+        if (n >= 1) t.d[n - 1] = A[(size_t)(n - 1) * t.ld + (n - 1)];
+    }
+}
+
+void launch_tridiag(const TridiagDesc* d, int nmat, int maxn, cudaStream_t s) {
+    if (nmat <= 0 || maxn <= 0) return;
+    const size_t smem = 2 * (size_t)maxn * sizeof(double);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tridiag_kernel<<<nmat, 1024, smem, s>>>(d);
+}
+
+// All eigenvalues of symmetric tridiagonal matrices by bisection with Sturm
+// counts (number of negative pivots of T - x I), one thread per eigenvalue:
+// eigenvalue j (ascending) is the x where the count passes j.  The interval
+// starts from the Gershgorin bounds and is halved until it is no wider than
+// 2 eps (|lo| + |hi|) or stops shrinking.
+__global__ void bisect_kernel(const TridiagDesc* __restrict__ descs, const int* __restrict__ eig_mat,
+                              const int* __restrict__ eig_idx, int64_t total, double* const* __restrict__ out) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const TridiagDesc t = descs[eig_mat[gid]];
+    const int j = eig_idx[gid];
+    const int n = t.n;
+    double lo = 0.0, hi = 0.0, emax2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? fabs(t.e[i]) : 0.0) + (i + 1 < n ? fabs(t.e[i + 1]) : 0.0);
+        lo = (i == 0) ? t.d[i] - r : fmin(lo, t.d[i] - r);
+        hi = (i == 0) ? t.d[i] + r : fmax(hi, t.d[i] + r);
+        if (i > 0) emax2 = fmax(emax2, t.e[i] * t.e[i]);
+    }
+    const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax2);
+    const double eps = 2.220446049250313e-16;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi) || (hi - lo) <= 2.0 * eps * (fabs(lo) + fabs(hi))) break;
+        int cnt = 0;
+        double q = t.d[0] - mid;
+        if (fabs(q) < pivmin) q = -pivmin;
+        cnt += (q < 0.0);
+        for (int i = 1; i < n; ++i) {
+            q = (t.d[i] - mid) - t.e[i] * t.e[i] / q;
+            if (fabs(q) < pivmin) q = -pivmin;
+            cnt += (q < 0.0);
+        }
+        if (cnt > j)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    out[eig_mat[gid]][j] = 0.5 * (lo + hi);
+}
+
+void launch_bisect(const TridiagDesc* d, const int* eig_mat, const int* eig_idx, int64_t total, double* const* out,
+                   cudaStream_t s) {
+    if (total <= 0) return;
+    bisect_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(d, eig_mat, eig_idx, total, out);
 }
 
 // ------------------------------------------------------------------ row GEMV
