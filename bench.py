@@ -35,7 +35,7 @@ METRIC = "time-to-1e-8 residual (setup+solve), learned/mixed vs plain FP64, same
 WORKLOAD = "laplace2d_64x64_16box_ov1_tau50"
 RTOL = 1e-8
 FP64_PEAK_GFLOPS = 1250.0    # GB300 FP64 (profiling recipe's table); no FP64 figure is measured by the driver
-ALU_CLASSES = {"jacobi_svd", "jacobi_eig", "jacobi_f32", "gemm_tiles", "chol_diag", "chol_panel", "trtri_diag", "e_offdiag"}
+ALU_CLASSES = {"jacobi_svd", "jacobi_eig", "jacobi_f32", "tridiag", "bisect", "gemm_tiles", "chol_diag", "chol_panel", "trtri_diag", "e_offdiag"}
 
 
 def _workload():

@@ -171,10 +171,13 @@ amdd_status amdd_get_eigenvalues(const amdd_handle* h, int32_t i, double* lam, i
 amdd_status amdd_get_singular_values(const amdd_handle* h, int32_t i, double* sigma, int32_t cap,
                                      int32_t* count);
 
-/* The selected eigenvectors of subdomain i restricted to Omega_Ii (that is
- * D_i Z_i on its support), as a host row-major p x nI array (row k = vector
- * k, entries in ascending global order of Omega_Ii, A_II-orthonormal),
- * ordered by descending lambda.  Needs cap >= p*nI. */
+/* The coarse block of subdomain i restricted to Omega_Ii (D_i Z_i on its
+ * support) as a host row-major p x nI array: p A_II-orthonormal rows spanning
+ * the selected eigenvectors of eq. (Zi), entries in ascending global order of
+ * Omega_Ii.  When the selection is partial the rows are the eigenvectors, by
+ * descending lambda; when every eigenvalue is selected the span is all of
+ * R^nI and the rows are those of L_A^{-1} (A_II = L_A L_A^T).  Needs
+ * cap >= p*nI. */
 amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, int64_t cap,
                                   int32_t* p, int32_t* nI);
 
@@ -188,7 +191,7 @@ amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, i
  * amdd_setup, amdd_apply and amdd_pcg_solve until amdd_reset_profile.
  * Synchronises the handle's stream.  AMDD_ERR_INVALID if profiling is off or
  * k is out of range. */
-#define AMDD_PROF_CLASSES 14
+#define AMDD_PROF_CLASSES 16
 amdd_status amdd_get_profile(amdd_handle* h, int32_t k, const char** name, int64_t* launches, double* ms,
                              double* flops, double* bytes);
 

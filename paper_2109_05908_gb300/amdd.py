@@ -200,7 +200,7 @@ def overlap_sets(n, rowptr, colind, part, i: int, overlap: int):
     return I, G, D
 
 
-PROF_CLASSES = 14
+PROF_CLASSES = 16
 
 
 def get_profile(h: int):

@@ -48,6 +48,8 @@ enum ProfK {
     PK_JAC_SVD,
     PK_JAC_EIG,
     PK_JAC_F32,
+    PK_TRIDIAG,
+    PK_BISECT,
     PK_SMALL,
     PK_E_ASM,
     PK_SPMV,
@@ -58,7 +60,7 @@ enum ProfK {
 };
 static_assert(PK_COUNT == AMDD_PROF_CLASSES, "profile classes");
 static const char* const kProfNames[PK_COUNT] = {
-    "gather_values", "chol_diag", "chol_panel", "gemm_tiles", "trtri_diag", "jacobi_svd", "jacobi_eig", "jacobi_f32",
+    "gather_values", "chol_diag", "chol_panel", "gemm_tiles", "trtri_diag", "jacobi_svd", "jacobi_eig", "jacobi_f32", "tridiag", "bisect",
     "small_dense", "e_offdiag", "spmv", "gemv_rows", "gather_scatter", "pcg_vectors"};
 
 struct ProfState {
@@ -773,32 +775,44 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         launch_set_identity(di, N, h->max_nt, s);
     }
 
-    // ---- (6) eigenvalues mu = 1/lambda of eq. (Zi) by one-sided Jacobi on
-    // the rows of [T | I] in FP64: rows of the left half become mu_j w_j^T,
-    // the right half accumulates the eigenvectors w_j.  The criterion is
-    // relative to the rows' own norms (no absolute floor), so small mu keep
-    // their accuracy.  (An FP32 preconditioning stage does not pay here: the
-    // spectrum near mu = 1 is denser than FP32 can resolve.)
+    // ---- (6) eigenvalues mu = 1/lambda of eq. (Zi): Householder reduction of
+    // each T_i to tridiagonal form and bisection with Sturm counts (absolute
+    // accuracy O(eps ||T||), like a dense symmetric eigensolver).
     {
-        std::vector<JacobiDesc> jd(N);
-        std::vector<double*> mp(N);
-        int maxc = 1;
+        double* TD = C.tnew<double>(off_P[N]);
+        double* dd = C.tnew<double>(h->sum_nI);
+        double* ee = C.tnew<double>(h->sum_nI);
+        std::vector<TridiagDesc> td(N);
+        std::vector<double*> outp(N);
+        std::vector<int> em, ej;
+        em.reserve(h->sum_nI);
+        ej.reserve(h->sum_nI);
+        int maxn = 1;
         for (int i = 0; i < N; ++i) {
             const int nIi = h->nI[i];
-            jd[i] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrm64 + h->off_om[i], nullptr};
-            mp[i] = mu + h->off_I[i];
-            maxc = std::max(maxc, nIi);
+            if (nIi > 0)
+                ck(cudaMemcpy2DAsync(TD + off_P[i], nIi * sizeof(double), TI + off_ti[i], 2 * nIi * sizeof(double),
+                                     nIi * sizeof(double), nIi, cudaMemcpyDeviceToDevice, s));
+            td[i] = {TD + off_P[i], nIi, nIi, dd + h->off_I[i], ee + h->off_I[i]};
+            outp[i] = mu + h->off_I[i];
+            for (int j = 0; j < nIi; ++j) {
+                em.push_back(i);
+                ej.push_back(j);
+            }
+            maxn = std::max(maxn, nIi);
         }
-        JacobiDesc* djd = C.up(jd);
-        double* const* dmp = C.up(mp);
+        const TridiagDesc* dtd = C.up(td);
+        auto dem = C.up(em);
+        auto dej = C.up(ej);
+        auto dout = C.up(outp);
         {
-            PScope ps(h, PK_JAC_EIG);
-            run_jacobi<double>(h, jd, djd, h->max_sweeps,
-                               2.0 * std::sqrt((double)maxc) * std::numeric_limits<double>::epsilon(), sweeps + N,
-                               rots + N, 1);
+            double fl = 0.0;
+            for (int i = 0; i < N; ++i) fl += 8.0 / 3.0 * std::pow((double)h->nI[i], 3);
+            PScope ps(h, PK_TRIDIAG, fl);
+            launch_tridiag(dtd, N, maxn, s);
         }
-        PScope ps(h, PK_SMALL);
-        launch_rownorms(djd, N, dmp, nullptr, 0.0, 0, s);
+        PScope ps(h, PK_BISECT);
+        launch_bisect(dtd, dem, dej, (int64_t)em.size(), dout, s);
     }
 
     // ---- (7) selection lambda > 1/tau on the host
@@ -816,17 +830,12 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     }
     for (int i = 0; i < N; ++i) {
         h->sweeps_svd = std::max(h->sweeps_svd, sw[i]);
-        h->sweeps_eig = std::max(h->sweeps_eig, sw[N + i]);
         h->sweeps_svd32 = std::max(h->sweeps_svd32, sw[2 * N + i]);
-        h->sweeps_eig32 = std::max(h->sweeps_eig32, sw[3 * N + i]);
         h->rot_svd += (int64_t)rot_h[i];
-        h->rot_eig += (int64_t)rot_h[N + i];
         if (h->prof.on) {
             // per sweep: row norms and one inner product per pair; plus the rotations performed
-            const double ni = h->ni[i], nt = h->nt[i], nIi = h->nI[i];
+            const double ni = h->ni[i], nt = h->nt[i];
             h->prof.flops[PK_JAC_SVD] += sw[i] * (ni * 2.0 * nt + ni * (ni - 1) / 2 * 2.0 * nt) + rot_h[i] * 6.0 * nt;
-            h->prof.flops[PK_JAC_EIG] +=
-                sw[N + i] * (nIi * 2.0 * nIi + nIi * (nIi - 1) / 2 * 2.0 * nIi) + rot_h[N + i] * 12.0 * nIi;
         }
         std::sort(h->sigma_h.begin() + h->off_om[i], h->sigma_h.begin() + h->off_om[i + 1], std::greater<double>());
     }
@@ -834,53 +843,115 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     h->p.assign(N, 0);
     h->coff.assign(N + 1, 0);
     h->off_zt.assign(N + 1, 0);
-    std::vector<int64_t> wsrc, wdst;
-    std::vector<int32_t> wlen;
+    std::vector<int> partial;  // subdomains whose selection is neither empty nor everything
     for (int i = 0; i < N; ++i) {
         const int nIi = h->nI[i];
-        std::vector<double> lam(nIi);
-        for (int j = 0; j < nIi; ++j) {
-            const double m = mu_h[h->off_I[i] + j];
-            lam[j] = (m > 0.0) ? 1.0 / m : std::numeric_limits<double>::infinity();
-        }
-        std::vector<int> order(nIi);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] > lam[b]; });
         int pi = 0;
-        for (int k = 0; k < nIi; ++k) {
-            const int j = order[k];
-            h->lam_h[h->off_I[i] + k] = lam[j];
-            if (lam[j] > 1.0 / h->tau) {
-                wsrc.push_back(off_ti[i] + (int64_t)j * 2 * nIi + nIi);
-                wdst.push_back(h->off_zt[i] + (int64_t)pi * nIi);
-                wlen.push_back(nIi);
-                ++pi;
-            }
+        for (int j = 0; j < nIi; ++j) {  // mu ascending -> lambda descending
+            const double m = mu_h[h->off_I[i] + j];
+            const double lam = (m > 0.0) ? 1.0 / m : std::numeric_limits<double>::infinity();
+            h->lam_h[h->off_I[i] + j] = lam;
+            if (lam > 1.0 / h->tau) ++pi;
         }
         h->p[i] = pi;
+        if (pi > 0 && pi < nIi) partial.push_back(i);
         h->coff[i + 1] = h->coff[i] + pi;
         h->off_zt[i + 1] = h->off_zt[i] + (int64_t)pi * nIi;
     }
     h->nC = h->coff[N];
     h->sum_zt = h->off_zt[N];
 
-    // ---- (8) coarse block Z_i on Omega_Ii: u_k = L_A^{-T} w_k, stored as rows
+    // ---- (8) coarse block Z_i on Omega_Ii as A_II-orthonormal rows.  When
+    // every eigenvalue is selected, span(Z_i) = R^{|Omega_Ii|} and any
+    // A_II-orthonormal basis serves: the rows of L_A^{-1}.  When the selection
+    // is partial, the eigenvectors are needed: one-sided Jacobi on the rows of
+    // [T | I] (FP64, relative criterion) gives the eigenvectors w_j as the
+    // right half and mu_j as the left-half row norms; the p_i rows with the
+    // smallest mu give u = L_A^{-T} w.
     h->d_Zt = dnew<double>(h, h->sum_zt);
     if (h->nC > 0) {
-        double* Wsel = C.tnew<double>(h->sum_zt);
-        {
-            auto a = C.up(wsrc);
-            auto b = C.up(wdst);
-            auto c = C.up(wlen);
-            PScope ps(h, PK_SMALL);
-            launch_gather_rows(TI, a, Wsel, b, c, (int64_t)wsrc.size(), s);
+        std::vector<int64_t> ysrc, ydst;
+        std::vector<int32_t> ylen;
+        for (int i = 0; i < N; ++i) {
+            if (h->p[i] != h->nI[i] || h->p[i] == 0) continue;
+            for (int k = 0; k < h->nI[i]; ++k) {
+                ysrc.push_back(h->off_sq[i] + (int64_t)k * h->ni[i]);
+                ydst.push_back(h->off_zt[i] + (int64_t)k * h->nI[i]);
+                ylen.push_back(h->nI[i]);
+            }
         }
-        std::vector<GemmDesc> g;
-        for (int i = 0; i < N; ++i)
-            if (h->p[i] > 0)
+        if (!ysrc.empty()) {
+            auto a = C.up(ysrc);
+            auto b = C.up(ydst);
+            auto c = C.up(ylen);
+            PScope ps(h, PK_SMALL);
+            launch_gather_rows(h->d_Y, a, h->d_Zt, b, c, (int64_t)ysrc.size(), s);
+        }
+        if (!partial.empty()) {
+            const int np = (int)partial.size();
+            std::vector<JacobiDesc> jd(np);
+            std::vector<double*> mp(np);
+            double* mu_j = C.tnew<double>(h->sum_nI);
+            int maxc = 1;
+            for (int q = 0; q < np; ++q) {
+                const int i = partial[q], nIi = h->nI[i];
+                jd[q] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrm64 + h->off_om[i], nullptr};
+                mp[q] = mu_j + h->off_I[i];
+                maxc = std::max(maxc, nIi);
+            }
+            JacobiDesc* djd = C.up(jd);
+            double* const* dmp = C.up(mp);
+            {
+                PScope ps(h, PK_JAC_EIG);
+                run_jacobi<double>(h, jd, djd, h->max_sweeps,
+                                   2.0 * std::sqrt((double)maxc) * std::numeric_limits<double>::epsilon(), sweeps + N,
+                                   rots + N, 1);
+            }
+            {
+                PScope ps(h, PK_SMALL);
+                launch_rownorms(djd, np, dmp, nullptr, 0.0, 0, s);
+            }
+            std::vector<double> muj(h->sum_nI);
+            ck(cudaMemcpyAsync(muj.data(), mu_j, h->sum_nI * sizeof(double), cudaMemcpyDeviceToHost, s));
+            ck(cudaMemcpyAsync(sw.data() + N, sweeps + N, N * sizeof(int), cudaMemcpyDeviceToHost, s));
+            ck(cudaMemcpyAsync(rot_h.data() + N, rots + N, N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            {
+                const int e = read_err(h);
+                if (e) throw Fail{err_status(e)};
+            }
+            std::vector<int64_t> wsrc, wdst;
+            std::vector<int32_t> wlen;
+            for (int q = 0; q < np; ++q) {
+                const int i = partial[q], nIi = h->nI[i];
+                h->sweeps_eig = std::max(h->sweeps_eig, sw[N + q]);
+                h->rot_eig += (int64_t)rot_h[N + q];
+                if (h->prof.on)
+                    h->prof.flops[PK_JAC_EIG] +=
+                        sw[N + q] * (nIi * 2.0 * nIi + nIi * (nIi - 1) / 2.0 * 2.0 * nIi) + rot_h[N + q] * 12.0 * nIi;
+                std::vector<int> order(nIi);
+                std::iota(order.begin(), order.end(), 0);
+                const double* m = muj.data() + h->off_I[i];
+                std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return m[x] < m[y]; });
+                for (int k = 0; k < h->p[i]; ++k) {
+                    wsrc.push_back(off_ti[i] + (int64_t)order[k] * 2 * nIi + nIi);
+                    wdst.push_back(h->off_zt[i] + (int64_t)k * nIi);
+                    wlen.push_back(nIi);
+                }
+            }
+            double* Wsel = C.tnew<double>(h->sum_zt);
+            {
+                auto a = C.up(wsrc);
+                auto b = C.up(wdst);
+                auto c = C.up(wlen);
+                PScope ps(h, PK_SMALL);
+                launch_gather_rows(TI, a, Wsel, b, c, (int64_t)wsrc.size(), s);
+            }
+            std::vector<GemmDesc> g;
+            for (int i : partial)
                 g.push_back(gd(Wsel + h->off_zt[i], h->nI[i], 0, h->d_Y + h->off_sq[i], h->ni[i], 0,
                                h->d_Zt + h->off_zt[i], h->nI[i], h->p[i], h->nI[i], h->nI[i], 1.0, 0.0, 0));
-        gemm(C, g);
+            gemm(C, g);
+        }
     }
 
     // ---- (9) coarse matrix E = R_0 A R_0^T (Eq. (two_level_schwarz)), its
