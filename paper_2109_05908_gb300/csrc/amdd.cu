@@ -119,7 +119,19 @@ struct amdd_handle {
     int32_t *d_nI = nullptr, *d_p = nullptr;
     int64_t *d_sc_ptr = nullptr, *d_zt_off = nullptr, *d_coff = nullptr;
     double *d_rloc = nullptr, *d_tloc = nullptr, *d_yloc = nullptr;
-    double *d_c = nullptr, *d_ct = nullptr, *d_e = nullptr;
+    double *d_c = nullptr, *d_ct = nullptr, *d_e = nullptr, *d_ctmp = nullptr;
+    // coarse solve: L_E (d_YE), L_E^T (d_YEt), inverses of its diagonal blocks
+    double *d_Yd = nullptr, *d_Ydt = nullptr;
+    int cSB = 0, cK = 0;
+    struct CStep {
+        int rows;
+        double flops, bytes;
+    };
+    std::vector<CStep> csteps;
+    std::vector<int> env_row;     // first non-zero column of each row of E (and L_E)
+    std::vector<int> env_colend;  // one past the last non-zero row of each column of L_E
+    int* d_env_row = nullptr;
+    int* d_env_colend = nullptr;
     // PCG work vectors
     double *d_r = nullptr, *d_z = nullptr, *d_pv = nullptr, *d_q = nullptr, *d_part = nullptr;
     PcgScal* d_sc = nullptr;
@@ -254,7 +266,12 @@ GemmDesc gd(const double* A, int lda, int ta, const double* B, int ldb, int tb, 
 // Blocked right-looking Cholesky of a batch of matrices (lower triangles),
 // each stopped at its own column `stop` (the trailing block then holds the
 // Schur complement of the factored leading block).
-void chol_batched(Ctx& C, const std::vector<CholDesc>& ds) {
+//
+// `env` (optional, one entry per matrix, may be null) gives each row's first
+// non-zero column (the envelope).  The Cholesky factor keeps the envelope of
+// the matrix, so panel row tiles and trailing-update tiles whose rows have no
+// entries in the current block column are zero throughout and are skipped.
+void chol_batched(Ctx& C, const std::vector<CholDesc>& ds, const std::vector<const std::vector<int>*>& env = {}) {
     if (ds.empty()) return;
     amdd_handle* h = C.h;
     CholDesc* dd = C.up(ds);
@@ -272,26 +289,53 @@ void chol_batched(Ctx& C, const std::vector<CholDesc>& ds) {
             launch_chol_diag(dd, (int)ds.size(), k0, h->d_err, h->s);
         }
         std::vector<PanelRef> pt;
-        double pfl = 0.0;
+        double pfl = 0.0, gfl = 0.0;
         std::vector<GemmDesc> g;
+        std::vector<TileRef> gt;
         for (int d = 0; d < (int)ds.size(); ++d) {
             const CholDesc& c = ds[d];
             if (k0 >= c.stop) continue;
             const int kend = std::min(k0 + CHOL_NB, c.stop);
             const int rows = c.n - kend;
             if (rows <= 0) continue;
-            for (int rt = 0; rt * 64 < rows; ++rt) pt.push_back({d, rt});
-            pfl += (double)rows * (kend - k0) * (kend - k0 + 1);
+            const int ntile = cdiv(rows, 64);
+            std::vector<char> act(ntile, 1);
+            const std::vector<int>* e = (d < (int)env.size()) ? env[d] : nullptr;
+            if (e) {
+                for (int t = 0; t < ntile; ++t) {
+                    int mn = INT32_MAX;
+                    for (int r = kend + 64 * t; r < std::min(c.n, kend + 64 * t + 64); ++r) mn = std::min(mn, (*e)[r]);
+                    act[t] = mn < kend;
+                }
+            }
+            const int kb = kend - k0;
+            for (int rt = 0; rt < ntile; ++rt)
+                if (act[rt]) {
+                    pt.push_back({d, rt});
+                    pfl += (double)std::min(64, rows - 64 * rt) * kb * (kb + 1);
+                }
             double* panel = c.A + (size_t)kend * c.ld + k0;
-            g.push_back(gd(panel, c.ld, 0, panel, c.ld, 1, c.A + (size_t)kend * c.ld + kend, c.ld, rows, rows,
-                           kend - k0, -1.0, 1.0, 1));
+            const int gi = (int)g.size();
+            g.push_back(gd(panel, c.ld, 0, panel, c.ld, 1, c.A + (size_t)kend * c.ld + kend, c.ld, rows, rows, kb, -1.0,
+                           1.0, 1));
+            for (int a = 0; a < ntile; ++a)
+                for (int b = 0; b <= a; ++b)
+                    if (act[a] && act[b]) {
+                        gt.push_back({gi, a, b});
+                        gfl += 2.0 * 64 * 64 * kb;
+                    }
         }
         if (!pt.empty()) {
             const PanelRef* dpt = C.up(pt);
             PScope ps(h, PK_CHOL_PANEL, pfl);
             launch_chol_panel(dd, dpt, (int)pt.size(), k0, h->s);
         }
-        gemm(C, g);
+        if (!gt.empty()) {
+            const GemmDesc* dg = C.up(g);
+            const TileRef* dt = C.up(gt);
+            PScope ps(h, PK_GEMM, gfl);
+            launch_gemm(dg, dt, (int)gt.size(), h->s);
+        }
     }
 }
 
@@ -350,9 +394,13 @@ template <typename T>
 void run_jacobi(amdd_handle* h, const std::vector<JacobiDescT<T>>& jd, const JacobiDescT<T>* djd, int max_sweeps, T tol,
                 int* sweeps, unsigned long long* rots, int report_noconv) {
     size_t smem = 0;
-    for (const auto& j : jd) smem = std::max(smem, jacobi_block_smem<T>(j.rows, j.ncols_rot));
-    if (!launch_jacobi_block<T>(djd, (int)jd.size(), smem, max_sweeps, tol, sweeps, rots, h->d_err, report_noconv,
-                                h->s))
+    int maxr = 0;
+    for (const auto& j : jd) {
+        smem = std::max(smem, jacobi_block_smem<T>(j.rows, j.ncols_rot));
+        maxr = std::max(maxr, j.rows);
+    }
+    if (!launch_jacobi_block<T>(djd, (int)jd.size(), smem, maxr, max_sweeps, tol, sweeps, rots, h->d_err,
+                                report_noconv, h->s))
         launch_jacobi_t<T>(djd, (int)jd.size(), max_sweeps, tol, sweeps, rots, h->d_err, report_noconv, h->s);
 }
 
@@ -961,7 +1009,8 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         std::vector<int64_t> off_az(N + 1, 0);
         for (int i = 0; i < N; ++i) off_az[i + 1] = off_az[i] + (int64_t)h->ni[i] * h->p[i];
         double* AZ = C.tnew<double>(off_az[N]);
-        double* E = C.tnew<double>((size_t)nC * nC);
+        h->d_YE = dnew<double>(h, (size_t)nC * nC);  // E, then its Cholesky factor L_E (lower)
+        double* E = h->d_YE;
         ck(cudaMemsetAsync(E, 0, (size_t)nC * nC * sizeof(double), s));
         std::vector<GemmDesc> g1, g2;
         for (int i = 0; i < N; ++i) {
@@ -1041,11 +1090,49 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                              s);
         }
         double* linvE = C.tnew<double>((size_t)cdiv(nC, CHOL_NB) * CHOL_NB * CHOL_NB);
-        h->d_YE = dnew<double>(h, (size_t)nC * nC);
+        // envelope of E: block row i starts at the first subdomain j <= i coupled
+        // to i.  The factor keeps that row envelope but fills it in, so column c
+        // of L_E reaches every row whose envelope starts at or before c: block
+        // column j ends after the last block row i with lowj[i] <= j.
+        std::vector<int> lowj(N), highi(N);
+        for (int i = 0; i < N; ++i) lowj[i] = highi[i] = i;
+        for (const auto& pr : pairs) lowj[pr.first] = std::min(lowj[pr.first], pr.second);
+        for (int i = 0; i < N; ++i)
+            for (int j = lowj[i]; j <= i; ++j) highi[j] = std::max(highi[j], i);
+        h->env_row.assign(nC, 0);
+        h->env_colend.assign(nC, 0);
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < h->p[i]; ++k) {
+                h->env_row[h->coff[i] + k] = (int)h->coff[lowj[i]];
+                h->env_colend[h->coff[i] + k] = (int)h->coff[highi[i] + 1];
+            }
         h->d_YEt = dnew<double>(h, (size_t)nC * nC);
-        chol_batched(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}});
-        trtri_batched(C, {TrtriDesc{E, h->d_YE, linvE, (int)nC, (int)nC, (int)nC}});
-        transpose_batched(C, {h->d_YE}, {h->d_YEt}, {(int)nC}, {(int)nC}, {(int)nC});
+        chol_batched(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}}, {&h->env_row});
+        // Inverses of the diagonal blocks of L_E (block size cSB): the coarse
+        // solve is then a blocked forward / backward substitution with L_E and
+        // L_E^T (row GEMVs), with no inverse of the whole factor.
+        const int SB = std::max<int>(CHOL_NB, cdiv(cdiv(nC, 8), CHOL_NB) * CHOL_NB);
+        const int K = cdiv(nC, SB);
+        h->cSB = SB;
+        h->cK = K;
+        h->d_Yd = dnew<double>(h, (size_t)K * SB * SB);
+        h->d_Ydt = dnew<double>(h, (size_t)K * SB * SB);
+        std::vector<TrtriDesc> tj;
+        std::vector<const double*> ts;
+        std::vector<double*> tdst;
+        std::vector<int> tn, tl;
+        for (int k = 0; k < K; ++k) {
+            const int r0 = k * SB, sb = (int)std::min<int64_t>(SB, nC - r0);
+            tj.push_back({E + (size_t)r0 * nC + r0, h->d_Yd + (size_t)k * SB * SB,
+                          linvE + (size_t)(r0 / CHOL_NB) * CHOL_NB * CHOL_NB, sb, (int)nC, SB});
+            ts.push_back(h->d_Yd + (size_t)k * SB * SB);
+            tdst.push_back(h->d_Ydt + (size_t)k * SB * SB);
+            tn.push_back(sb);
+            tl.push_back(SB);
+        }
+        trtri_batched(C, tj);
+        transpose_batched(C, ts, tdst, tn, tl, tl);
+        transpose_batched(C, {E}, {h->d_YEt}, {(int)nC}, {(int)nC}, {(int)nC});
     } else {
         h->d_zt_off = C.up(std::vector<int64_t>(h->off_zt.begin(), h->off_zt.end() - 1), true);
         h->d_nI = C.up(std::vector<int32_t>(h->nI.begin(), h->nI.end()), true);
@@ -1087,14 +1174,53 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         h->d_rl_loc = C.up(rl, true);
         h->d_rd_c = C.up(rdc, true);
         h->d_rl_c = C.up(rlc, true);
-        std::vector<GemvDesc> e1{{h->d_YE, (int)nC, (int)nC, (int)nC, 1, h->d_c, h->d_ct}};
-        std::vector<GemvDesc> e2{{h->d_YEt, (int)nC, (int)nC, (int)nC, 2, h->d_ct, h->d_e}};
-        h->d_gv_e1 = C.up(e1, true);
-        h->d_gv_e2 = C.up(e2, true);
-        std::vector<int32_t> rde(nC, 0), rle(nC);
-        std::iota(rle.begin(), rle.end(), 0);
-        h->d_rd_e = C.up(rde, true);
-        h->d_rl_e = C.up(rle, true);
+        // coarse solve L_E L_E^T e = c: forward steps (t_k = c_k - L_{k,<k} y_<k,
+        // y_k = Y_kk t_k), then backward steps (t_k = y_k - (L^T)_{k,>k} e_>k,
+        // e_k = Y_kk^T t_k), one row-GEMV launch each.
+        if (nC > 0) {
+            h->d_ctmp = dnew<double>(h, nC);
+            h->d_env_row = C.up(h->env_row, true);
+            h->d_env_colend = C.up(h->env_colend, true);
+            const int SB = h->cSB, K = h->cK;
+            std::vector<GemvDesc> cd;
+            h->csteps.clear();
+            auto add = [&](GemvDesc g, double fl, double by) {
+                cd.push_back(g);
+                h->csteps.push_back({g.rows, fl, by});
+            };
+            for (int k = 0; k < K; ++k) {
+                const int r0 = k * SB, sb = (int)std::min<int64_t>(SB, nC - r0);
+                GemvDesc f1{h->d_YE + (size_t)r0 * nC, sb, r0, (int)nC, 0, h->d_ct, h->d_ctmp + r0};
+                f1.b = h->d_c + r0;
+                f1.alpha = -1.0;
+                f1.cstart = h->d_env_row + r0;
+                double el = 0.0;
+                for (int r = r0; r < r0 + sb; ++r) el += std::max(0, r0 - h->env_row[r]);
+                add(f1, 2.0 * el, 8.0 * el);
+                GemvDesc f2{h->d_Yd + (size_t)k * SB * SB, sb, sb, SB, 1, h->d_ctmp + r0, h->d_ct + r0};
+                add(f2, 1.0 * sb * (sb + 1), 4.0 * sb * (sb + 1));
+            }
+            for (int k = K - 1; k >= 0; --k) {
+                const int r0 = k * SB, sb = (int)std::min<int64_t>(SB, nC - r0);
+                const int rest = (int)(nC - r0 - sb);
+                GemvDesc b1{h->d_YEt + (size_t)r0 * nC + r0 + sb, sb, rest, (int)nC, 0, h->d_e + r0 + sb,
+                            h->d_ctmp + r0};
+                b1.b = h->d_ct + r0;
+                b1.alpha = -1.0;
+                b1.cend = h->d_env_colend + r0;
+                b1.coff = r0 + sb;
+                double el = 0.0;
+                for (int r = r0; r < r0 + sb; ++r) el += std::max(0, h->env_colend[r] - (r0 + sb));
+                add(b1, 2.0 * el, 8.0 * el);
+                GemvDesc b2{h->d_Ydt + (size_t)k * SB * SB, sb, sb, SB, 2, h->d_ctmp + r0, h->d_e + r0};
+                add(b2, 1.0 * sb * (sb + 1), 4.0 * sb * (sb + 1));
+            }
+            h->d_gv_e1 = C.up(cd, true);
+            std::vector<int32_t> rde(SB, 0), rle(SB);
+            std::iota(rle.begin(), rle.end(), 0);
+            h->d_rd_e = C.up(rde, true);
+            h->d_rl_e = C.up(rle, true);
+        }
         // prolongation: copies of each unknown in subdomain order, owners
         std::vector<int64_t> scp(n + 1, 0);
         for (int64_t t = 0; t < h->sum_ni; ++t) scp[omega[t] + 1]++;
@@ -1146,18 +1272,15 @@ void apply_one(amdd_handle* h, const double* r, double* z) {
         launch_gemv_rows(h->d_gv_l2, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
     }
     if (h->nC > 0) {
-        const double zt = (double)h->sum_zt, et = (double)h->nC * (h->nC + 1) / 2;
+        const double zt = (double)h->sum_zt;
         {
             PScope ps(h, PK_GEMV, 2.0 * zt, 8.0 * zt + 8.0 * h->sum_ni + 16.0 * h->nC);
             launch_gemv_rows(h->d_gv_c, h->d_rd_c, h->d_rl_c, h->nC, s);
         }
-        {
-            PScope ps(h, PK_GEMV, 2.0 * et, 8.0 * et + 24.0 * h->nC);
-            launch_gemv_rows(h->d_gv_e1, h->d_rd_e, h->d_rl_e, h->nC, s);
-        }
-        {
-            PScope ps(h, PK_GEMV, 2.0 * et, 8.0 * et + 24.0 * h->nC);
-            launch_gemv_rows(h->d_gv_e2, h->d_rd_e, h->d_rl_e, h->nC, s);
+        for (size_t j = 0; j < h->csteps.size(); ++j) {
+            const auto& st = h->csteps[j];
+            PScope ps(h, PK_GEMV, st.flops, st.bytes);
+            launch_gemv_rows(h->d_gv_e1 + j, h->d_rd_e, h->d_rl_e, st.rows, s);
         }
     }
     PScope ps(h, PK_GATHER_SCATTER, 2.0 * h->sum_zt, 8.0 * h->sum_zt + 12.0 * h->sum_ni + 24.0 * h->n);

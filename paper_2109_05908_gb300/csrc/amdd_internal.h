@@ -97,13 +97,18 @@ void launch_tridiag(const TridiagDesc* d, int nmat, int maxn, cudaStream_t s);
 void launch_bisect(const TridiagDesc* d, const int* eig_mat, const int* eig_idx, int64_t total, double* const* out,
                    cudaStream_t s);
 
-// Row GEMV descriptors: y[row] = sum_{c in [c0(row), c1(row))} M[row][c] x[c].
+// Row GEMV descriptors: y[row] = (b ? b[row] : 0) + alpha * sum_{c in [c0(row), c1(row))} M[row][c] x[c].
 // mode 0: full row [0, ncols); mode 1: lower [0, row]; mode 2: upper [row, ncols).
 struct GemvDesc {
     const double* M;
     int rows, ncols, ld, mode;
     const double* x;
     double* y;
+    const double* b = nullptr;  // y[row] = b[row] + alpha * (M x)[row] when b is given
+    double alpha = 1.0;
+    const int* cstart = nullptr;  // optional per-row first column (absolute, minus coff)
+    const int* cend = nullptr;    // optional per-row end column (absolute, minus coff)
+    int coff = 0;
 };
 
 void launch_gemm(const GemmDesc* d_descs, const TileRef* d_tiles, int ntiles, cudaStream_t s);
@@ -120,8 +125,8 @@ constexpr size_t JAC_BLOCK_SMEM_MAX = 220 * 1024;
 template <typename T>
 size_t jacobi_block_smem(int rows, int ncols_rot);
 template <typename T>
-bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem, int max_sweeps, T tol, int* sweeps,
-                         unsigned long long* rots, int* err, int report_noconv, cudaStream_t s);
+bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem, int max_rows, int max_sweeps, T tol,
+                         int* sweeps, unsigned long long* rots, int* err, int report_noconv, cudaStream_t s);
 template <typename T>
 void launch_row_maxnorm2(const JacobiDescT<T>* d, int nmat, T eps, T* out, cudaStream_t s);
 void launch_to_f32_with_identity(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s);

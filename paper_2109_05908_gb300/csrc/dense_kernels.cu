@@ -421,7 +421,7 @@ __device__ __forceinline__ bool jac_pair(T* __restrict__ xp, T* __restrict__ xq,
 }
 
 template <typename T>
-__global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
+__global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
     jacobi_block_kernel(const JacobiDescT<T>* __restrict__ descs, int max_sweeps, T tol, int* __restrict__ sweeps,
                         unsigned long long* __restrict__ rots, int* __restrict__ err, int report_noconv) {
     extern __shared__ __align__(16) unsigned char jac_smem[];
@@ -543,8 +543,8 @@ template size_t jacobi_block_smem<float>(int, int);
 template size_t jacobi_block_smem<double>(int, int);
 
 template <typename T>
-bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem, int max_sweeps, T tol, int* sweeps,
-                         unsigned long long* rots, int* err, int report_noconv, cudaStream_t s) {
+bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem, int max_rows, int max_sweeps, T tol,
+                         int* sweeps, unsigned long long* rots, int* err, int report_noconv, cudaStream_t s) {
     if (nmat <= 0) return true;
     if (smem > JAC_BLOCK_SMEM_MAX) return false;
     if (cudaFuncSetAttribute(jacobi_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -552,12 +552,16 @@ bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem, int max
         cudaGetLastError();
         return false;
     }
-    jacobi_block_kernel<T><<<nmat * JAC_CLUSTER, 256, smem, s>>>(d, max_sweeps, tol, sweeps, rots, err, report_noconv);
+    // one warp per pair of a sub-round (hb pairs), 8 to 32 warps
+    const int hb = (max_rows + 2 * JAC_CLUSTER - 1) / (2 * JAC_CLUSTER);
+    const int warps = hb < 8 ? 8 : (hb > 32 ? 32 : hb);
+    jacobi_block_kernel<T><<<nmat * JAC_CLUSTER, 32 * warps, smem, s>>>(d, max_sweeps, tol, sweeps, rots, err,
+                                                                        report_noconv);
     return true;
 }
-template bool launch_jacobi_block<float>(const JacobiDescT<float>*, int, size_t, int, float, int*,
+template bool launch_jacobi_block<float>(const JacobiDescT<float>*, int, size_t, int, int, float, int*,
                                          unsigned long long*, int*, int, cudaStream_t);
-template bool launch_jacobi_block<double>(const JacobiDescT<double>*, int, size_t, int, double, int*,
+template bool launch_jacobi_block<double>(const JacobiDescT<double>*, int, size_t, int, int, double, int*,
                                           unsigned long long*, int*, int, cudaStream_t);
 
 // absfloor[mat] = eps * max_r ||row r||^2 over ncols_dot (one CTA per matrix).
@@ -824,51 +828,74 @@ void launch_tridiag(const TridiagDesc* d, int nmat, int maxn, cudaStream_t s) {
     tridiag_kernel<<<nmat, 1024, smem, s>>>(d);
 }
 
-// All eigenvalues of symmetric tridiagonal matrices by bisection with Sturm
-// counts (number of negative pivots of T - x I), one thread per eigenvalue:
-// eigenvalue j (ascending) is the x where the count passes j.  The interval
-// starts from the Gershgorin bounds and is halved until it is no wider than
-// 2 eps (|lo| + |hi|) or stops shrinking.
-__global__ void bisect_kernel(const TridiagDesc* __restrict__ descs, const int* __restrict__ eig_mat,
-                              const int* __restrict__ eig_idx, int64_t total, double* const* __restrict__ out) {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= total) return;
-    const TridiagDesc t = descs[eig_mat[gid]];
-    const int j = eig_idx[gid];
+// All eigenvalues of symmetric tridiagonal matrices by multisection with
+// Sturm counts (number of negative pivots of T - x I), one warp per
+// eigenvalue: eigenvalue j (ascending) is the x where the count passes j.
+// Each step, the 32 lanes count at 32 interior points of [lo, hi] and the
+// interval shrinks to the sub-interval where the count passes j (a factor 33
+// per step).  The interval starts from the Gershgorin bounds and stops when
+// it is no wider than 2 eps (|lo| + |hi|) or stops shrinking.
+__global__ void __launch_bounds__(256) bisect_kernel(const TridiagDesc* __restrict__ descs,
+                                                      const int* __restrict__ eig_mat,
+                                                      const int* __restrict__ eig_idx, int64_t total,
+                                                      double* const* __restrict__ out) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= total) return;
+    const TridiagDesc t = descs[eig_mat[w]];
+    const int j = eig_idx[w];
     const int n = t.n;
     double lo = 0.0, hi = 0.0, emax2 = 0.0;
-    for (int i = 0; i < n; ++i) {
+    for (int i = lane; i < n; i += 32) {
         const double r = (i > 0 ? fabs(t.e[i]) : 0.0) + (i + 1 < n ? fabs(t.e[i + 1]) : 0.0);
-        lo = (i == 0) ? t.d[i] - r : fmin(lo, t.d[i] - r);
-        hi = (i == 0) ? t.d[i] + r : fmax(hi, t.d[i] + r);
+        const double l = t.d[i] - r, u = t.d[i] + r;
+        lo = (i == lane) ? l : fmin(lo, l);
+        hi = (i == lane) ? u : fmax(hi, u);
         if (i > 0) emax2 = fmax(emax2, t.e[i] * t.e[i]);
+    }
+    if (lane >= n) {
+        lo = t.d[0];
+        hi = t.d[0];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
     }
     const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax2);
     const double eps = 2.220446049250313e-16;
-    for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (!(mid > lo && mid < hi) || (hi - lo) <= 2.0 * eps * (fabs(lo) + fabs(hi))) break;
+    for (int it = 0; it < 64; ++it) {
+        if ((hi - lo) <= 2.0 * eps * (fabs(lo) + fabs(hi))) break;
+        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
         int cnt = 0;
-        double q = t.d[0] - mid;
+        double q = t.d[0] - x;
         if (fabs(q) < pivmin) q = -pivmin;
         cnt += (q < 0.0);
         for (int i = 1; i < n; ++i) {
-            q = (t.d[i] - mid) - t.e[i] * t.e[i] / q;
+            q = (t.d[i] - x) - t.e[i] * t.e[i] / q;
             if (fabs(q) < pivmin) q = -pivmin;
             cnt += (q < 0.0);
         }
-        if (cnt > j)
-            hi = mid;
-        else
-            lo = mid;
+        // first lane whose count exceeds j bounds the eigenvalue from above
+        const unsigned above = __ballot_sync(0xffffffffu, cnt > j && x > lo && x < hi);
+        const unsigned below = __ballot_sync(0xffffffffu, cnt <= j && x > lo && x < hi);
+        const int first_above = above ? __ffs(above) - 1 : 32;
+        const int last_below = below ? 31 - __clz(below) : -1;
+        const double nlo = (last_below >= 0) ? __shfl_sync(0xffffffffu, x, last_below) : lo;
+        const double nhi = (first_above < 32) ? __shfl_sync(0xffffffffu, x, first_above) : hi;
+        if (!(nhi - nlo < hi - lo)) break;
+        lo = nlo;
+        hi = nhi;
     }
-    out[eig_mat[gid]][j] = 0.5 * (lo + hi);
+    if (lane == 0) out[eig_mat[w]][j] = 0.5 * (lo + hi);
 }
 
 void launch_bisect(const TridiagDesc* d, const int* eig_mat, const int* eig_idx, int64_t total, double* const* out,
                    cudaStream_t s) {
     if (total <= 0) return;
-    bisect_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(d, eig_mat, eig_idx, total, out);
+    const int64_t threads = total * 32;
+    bisect_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(d, eig_mat, eig_idx, total, out);
 }
 
 // ------------------------------------------------------------------ row GEMV
@@ -884,12 +911,20 @@ __global__ void __launch_bounds__(256) gemv_rows_kernel(const GemvDesc* __restri
     int c0 = 0, c1 = d.ncols;
     if (d.mode == 1) c1 = min(r + 1, d.ncols);
     if (d.mode == 2) c0 = r;
+    if (d.cstart) c0 = max(c0, d.cstart[r] - d.coff);
+    if (d.cend) c1 = min(c1, d.cend[r] - d.coff);
     const double* row = d.M + (size_t)r * d.ld;
-    double s = 0.0;
-    for (int c = c0 + lane; c < c1; c += 32) s = fma(row[c], d.x[c], s);
+    double s0 = 0.0, s1 = 0.0;
+    int c = c0 + lane;
+    for (; c + 32 < c1; c += 64) {
+        s0 = fma(row[c], d.x[c], s0);
+        s1 = fma(row[c + 32], d.x[c + 32], s1);
+    }
+    if (c < c1) s0 = fma(row[c], d.x[c], s0);
+    double s = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) d.y[r] = s;
+    if (lane == 0) d.y[r] = d.b ? fma(d.alpha, s, d.b[r]) : d.alpha * s;
 }
 
 void launch_gemv_rows(const GemvDesc* d, const int* row_desc, const int* row_local, int64_t nrows, cudaStream_t s) {
