@@ -69,17 +69,31 @@ struct ProfState {
     double flops[PK_COUNT] = {};
     double bytes[PK_COUNT] = {};
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PK_COUNT];
-    void clear() {
+    // events are created once and reused, so a profiled launch costs two
+    // cudaEventRecord calls on the host
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    cudaEvent_t take() {
+        if (used == pool.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void clear() {  // forget the records, keep the events
         for (int k = 0; k < PK_COUNT; ++k) {
-            for (auto& e : ev[k]) {
-                cudaEventDestroy(e.first);
-                cudaEventDestroy(e.second);
-            }
             ev[k].clear();
             launches[k] = 0;
             flops[k] = 0.0;
             bytes[k] = 0.0;
         }
+        used = 0;
+    }
+    void release() {
+        clear();
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+        pool.clear();
     }
 };
 
@@ -164,10 +178,8 @@ struct PScope {
     cudaEvent_t b = nullptr;
     PScope(amdd_handle* hh, int kk, double flops = 0.0, double bytes = 0.0) : h(hh), k(kk) {
         if (!h->prof.on) return;
-        if (cudaEventCreate(&b) != cudaSuccess) {
-            b = nullptr;
-            return;
-        }
+        b = h->prof.take();
+        if (!b) return;
         cudaEventRecord(b, h->s);
         h->prof.launches[k] += 1;
         h->prof.flops[k] += flops;
@@ -175,11 +187,8 @@ struct PScope {
     }
     ~PScope() {
         if (!b) return;
-        cudaEvent_t e = nullptr;
-        if (cudaEventCreate(&e) != cudaSuccess) {
-            cudaEventDestroy(b);
-            return;
-        }
+        cudaEvent_t e = h->prof.take();
+        if (!e) return;
         cudaEventRecord(e, h->s);
         h->prof.ev[k].push_back({b, e});
     }
@@ -830,6 +839,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         double* TD = C.tnew<double>(off_P[N]);
         double* dd = C.tnew<double>(h->sum_nI);
         double* ee = C.tnew<double>(h->sum_nI);
+        double* pp = C.tnew<double>(h->sum_nI);
         std::vector<TridiagDesc> td(N);
         std::vector<double*> outp(N);
         std::vector<int> em, ej;
@@ -841,7 +851,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             if (nIi > 0)
                 ck(cudaMemcpy2DAsync(TD + off_P[i], nIi * sizeof(double), TI + off_ti[i], 2 * nIi * sizeof(double),
                                      nIi * sizeof(double), nIi, cudaMemcpyDeviceToDevice, s));
-            td[i] = {TD + off_P[i], nIi, nIi, dd + h->off_I[i], ee + h->off_I[i]};
+            td[i] = {TD + off_P[i], nIi, nIi, dd + h->off_I[i], ee + h->off_I[i], pp + h->off_I[i]};
             outp[i] = mu + h->off_I[i];
             for (int j = 0; j < nIi; ++j) {
                 em.push_back(i);
@@ -860,7 +870,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             launch_tridiag(dtd, N, maxn, s);
         }
         PScope ps(h, PK_BISECT);
-        launch_bisect(dtd, dem, dej, (int64_t)em.size(), dout, s);
+        launch_bisect(dtd, N, dem, dej, (int64_t)em.size(), dout, s);
     }
 
     // ---- (7) selection lambda > 1/tau on the host
@@ -1608,7 +1618,7 @@ amdd_status amdd_reset_profile(amdd_handle* h) {
 void amdd_destroy(amdd_handle* h) {
     if (!h) return;
     cudaStreamSynchronize(h->s);
-    h->prof.clear();
+    h->prof.release();
     for (void* p : h->allocs) cudaFreeAsync(p, h->s);
     cudaStreamSynchronize(h->s);
     delete h;

@@ -20,6 +20,7 @@ enum : int {
 constexpr int CHOL_NB = 32;     // diagonal block of the blocked Cholesky / inverse
 constexpr int GEMM_T = 64;      // GEMM output tile
 constexpr int JAC_CLUSTER = 8;  // CTAs per matrix in the Jacobi solvers
+constexpr int JAC_MAX_PAIRS = 64;  // largest sub-round of the shared-memory block Jacobi
 
 // ---------------------------------------------------------------- dense
 // C = alpha * op(A) * op(B) + beta * C for m x n outputs, inner dimension k.
@@ -92,10 +93,11 @@ struct TridiagDesc {
     int n, ld;
     double* d;  // n
     double* e;  // n (e[i] = T[i][i-1], e[0] = 0)
+    double* p;  // n scratch
 };
 void launch_tridiag(const TridiagDesc* d, int nmat, int maxn, cudaStream_t s);
-void launch_bisect(const TridiagDesc* d, const int* eig_mat, const int* eig_idx, int64_t total, double* const* out,
-                   cudaStream_t s);
+void launch_bisect(const TridiagDesc* d, int nmat, const int* eig_mat, const int* eig_idx, int64_t total,
+                   double* const* out, cudaStream_t s);
 
 // Row GEMV descriptors: y[row] = (b ? b[row] : 0) + alpha * sum_{c in [c0(row), c1(row))} M[row][c] x[c].
 // mode 0: full row [0, ncols); mode 1: lower [0, row]; mode 2: upper [row, ncols).

@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const CholDesc* __restri
     const int kb = kend - k0;
     __shared__ double L[CHOL_NB][CHOL_NB + 1];
     __shared__ double Li[CHOL_NB][CHOL_NB + 1];
+    __shared__ double dinv[CHOL_NB];  // 1 / L[j][j]
     const int tid = threadIdx.x;
     for (int e = tid; e < CHOL_NB * CHOL_NB; e += blockDim.x) {
         const int r = e / CHOL_NB, c = e % CHOL_NB;
@@ -120,10 +121,13 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const CholDesc* __restri
                 atomicOr(err, DERR_NOT_SPD);
                 piv = 1.0;
             }
-            L[j][j] = sqrt(piv);
+            // one reciprocal square root per pivot: L_jj = piv / sqrt(piv)
+            const double r = rsqrt(piv);
+            L[j][j] = piv * r;
+            dinv[j] = r;
         }
         __syncthreads();
-        if (tid > j && tid < kb) L[tid][j] /= L[j][j];
+        if (tid > j && tid < kb) L[tid][j] *= dinv[j];
         __syncthreads();
         for (int e = tid; e < CHOL_NB * CHOL_NB; e += blockDim.x) {
             const int r = e / CHOL_NB, c = e % CHOL_NB;
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const CholDesc* __restri
         for (int r = c; r < kb; ++r) {
             double s = (r == c) ? 1.0 : 0.0;
             for (int k = c; k < r; ++k) s = fma(-L[r][k], Li[k][c], s);
-            Li[r][c] = s / L[r][r];
+            Li[r][c] = s * dinv[r];
         }
     }
     __syncthreads();
@@ -390,37 +394,6 @@ template void launch_jacobi_t<double>(const JacobiDescT<double>*, int, int, doub
 // (2 * JAC_CLUSTER - 1 per sweep).  Row norms^2 are recomputed when a block is
 // loaded and updated exactly after each rotation.
 template <typename T>
-__device__ __forceinline__ bool jac_pair(T* __restrict__ xp, T* __restrict__ xq, T* __restrict__ ap,
-                                         T* __restrict__ aq, int D, int W, T tol, int lane) {
-    T g0 = T(0), g1 = T(0);
-    int c = lane;
-    for (; c + 32 < D; c += 64) {
-        g0 = fma(xp[c], xq[c], g0);
-        g1 = fma(xp[c + 32], xq[c + 32], g1);
-    }
-    if (c < D) g0 = fma(xp[c], xq[c], g0);
-    T g = g0 + g1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-    const T a = *ap, b = *aq;
-    if (!(g != T(0) && g * g > tol * tol * a * b)) return false;
-    T cs, sn, t;
-    jac_rotation(a, b, g, cs, sn, t);
-    for (int c = lane; c < W; c += 32) {
-        const T u = xp[c], v = xq[c];
-        xp[c] = fma(cs, u, -sn * v);
-        xq[c] = fma(sn, u, cs * v);
-    }
-    __syncwarp();
-    if (lane == 0) {
-        *ap = fma(-t, g, a);
-        *aq = fma(t, g, b);
-    }
-    __syncwarp();
-    return true;
-}
-
-template <typename T>
 __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
     jacobi_block_kernel(const JacobiDescT<T>* __restrict__ descs, int max_sweeps, T tol, int* __restrict__ sweeps,
                         unsigned long long* __restrict__ rots, int* __restrict__ err, int report_noconv) {
@@ -435,6 +408,8 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
     T* blk = reinterpret_cast<T*>(jac_smem);  // [2][hb][W]
     T* nrm = blk + (size_t)2 * hb * W;        // [2][hb]
     __shared__ int rotated;
+    __shared__ T jg[JAC_MAX_PAIRS], jcs[JAC_MAX_PAIRS], jsn[JAC_MAX_PAIRS];
+    __shared__ int jflag[JAC_MAX_PAIRS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     const int hbe = hb + (hb & 1);
@@ -470,10 +445,68 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
                     if (lane == 0) nrm[k * hb + r] = a;
                 }
             __syncthreads();
+            // One sub-round in three phases: inner products (one warp per pair),
+            // rotation parameters and norm updates (one thread per pair), then
+            // the rotations (one warp per pair).  The scalar rotation math runs
+            // once per pair instead of on every lane.
+            auto subround = [&](int npairs, auto&& pair_of) {
+                for (int k = warp; k < npairs; k += nwarps) {
+                    int sa, sb;
+                    if (!pair_of(k, sa, sb)) continue;
+                    const T* xp = blk + (size_t)sa * W;
+                    const T* xq = blk + (size_t)sb * W;
+                    T g0 = T(0), g1 = T(0);
+                    int c = lane;
+                    for (; c + 32 < D; c += 64) {
+                        g0 = fma(xp[c], xq[c], g0);
+                        g1 = fma(xp[c + 32], xq[c + 32], g1);
+                    }
+                    if (c < D) g0 = fma(xp[c], xq[c], g0);
+                    T g = g0 + g1;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+                    if (lane == 0) jg[k] = g;
+                }
+                __syncthreads();
+                if ((int)threadIdx.x < npairs) {
+                    const int k = threadIdx.x;
+                    int sa, sb;
+                    jflag[k] = 0;
+                    if (pair_of(k, sa, sb)) {
+                        const T g = jg[k], a = nrm[sa], b = nrm[sb];
+                        if (g != T(0) && g * g > tol * tol * a * b) {
+                            T cs, sn, t;
+                            jac_rotation(a, b, g, cs, sn, t);
+                            jcs[k] = cs;
+                            jsn[k] = sn;
+                            jflag[k] = 1;
+                            nrm[sa] = fma(-t, g, a);
+                            nrm[sb] = fma(t, g, b);
+                            ++my_rots;
+                            rotated = 1;
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int k = warp; k < npairs; k += nwarps) {
+                    if (!jflag[k]) continue;
+                    int sa, sb;
+                    pair_of(k, sa, sb);
+                    T* xp = blk + (size_t)sa * W;
+                    T* xq = blk + (size_t)sb * W;
+                    const T cs = jcs[k], sn = jsn[k];
+                    for (int c = lane; c < W; c += 32) {
+                        const T u = xp[c], v = xq[c];
+                        xp[c] = fma(cs, u, -sn * v);
+                        xq[c] = fma(sn, u, cs * v);
+                    }
+                }
+                __syncthreads();
+            };
             if (br == 0) {
                 // pairs inside each of the two blocks (circle schedule on hbe)
-                for (int sr = 0; sr < hbe - 1; ++sr) {
-                    for (int k = warp; k < hbe; k += nwarps) {
+                for (int sr = 0; sr < hbe - 1; ++sr)
+                    subround(hbe, [&](int k, int& sa, int& sb) {
                         const int which = k / (hbe / 2), kk = k % (hbe / 2);
                         int a, b;
                         if (kk == 0) {
@@ -483,32 +516,19 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
                             a = (sr + kk) % (hbe - 1);
                             b = (sr - kk + (hbe - 1)) % (hbe - 1);
                         }
-                        if (a >= nr[which] || b >= nr[which]) continue;
-                        T* base = blk + (size_t)which * hb * W;
-                        if (jac_pair<T>(base + (size_t)a * W, base + (size_t)b * W, nrm + which * hb + a,
-                                        nrm + which * hb + b, D, W, tol, lane) &&
-                            lane == 0) {
-                            ++my_rots;
-                            rotated = 1;
-                        }
-                    }
-                    __syncthreads();
-                }
+                        sa = which * hb + a;
+                        sb = which * hb + b;
+                        return a < nr[which] && b < nr[which];
+                    });
             }
             // pairs between the two blocks
-            for (int sr = 0; sr < hb; ++sr) {
-                for (int a = warp; a < hb; a += nwarps) {
+            for (int sr = 0; sr < hb; ++sr)
+                subround(hb, [&](int a, int& sa, int& sb) {
                     const int b = (a + sr) % hb;
-                    if (a >= nr[0] || b >= nr[1]) continue;
-                    if (jac_pair<T>(blk + (size_t)a * W, blk + ((size_t)hb + b) * W, nrm + a, nrm + hb + b, D, W, tol,
-                                    lane) &&
-                        lane == 0) {
-                        ++my_rots;
-                        rotated = 1;
-                    }
-                }
-                __syncthreads();
-            }
+                    sa = a;
+                    sb = hb + b;
+                    return a < nr[0] && b < nr[1];
+                });
             for (int k = 0; k < 2; ++k)
                 for (int r = warp; r < nr[k]; r += nwarps) {
                     T* dst = d.A + (size_t)(r0[k] + r) * d.ld;
@@ -527,7 +547,7 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
             break;
         }
     }
-    if (lane == 0 && my_rots) atomicAdd(rots + mat, my_rots);
+    if (my_rots) atomicAdd(rots + mat, my_rots);
     if (crank == 0 && threadIdx.x == 0) {
         sweeps[mat] = done ? sweep + 1 : sweep;
         if (!done && report_noconv) atomicOr(err, DERR_EIG_NOCONV);
@@ -554,6 +574,7 @@ bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem, int max
     }
     // one warp per pair of a sub-round (hb pairs), 8 to 32 warps
     const int hb = (max_rows + 2 * JAC_CLUSTER - 1) / (2 * JAC_CLUSTER);
+    if (hb + 2 > JAC_MAX_PAIRS) return false;
     const int warps = hb < 8 ? 8 : (hb > 32 ? 32 : hb);
     jacobi_block_kernel<T><<<nmat * JAC_CLUSTER, 32 * warps, smem, s>>>(d, max_sweeps, tol, sweeps, rots, err,
                                                                         report_noconv);
@@ -739,85 +760,114 @@ void launch_transpose(const double* const* src, double* const* dst, const int* n
 // block becomes H A22 H = A22 - v w^T - w v^T with p = beta A22 v,
 // w = p - (beta/2)(p^T v) v.  Output: diagonal d[0..n) and sub-diagonal
 // e[1..n) (e[0] = 0).
-__device__ __forceinline__ double block_sum_1024(double v, double* red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double r = 0.0;
-    const int nw = blockDim.x >> 5;
-    for (int w = 0; w < nw; ++w) r += red[w];
-    return r;
-}
-
-__global__ void __launch_bounds__(1024) tridiag_kernel(const TridiagDesc* __restrict__ descs) {
-    const TridiagDesc t = descs[blockIdx.x];
+// A cluster of JAC_CLUSTER CTAs reduces one matrix; row r of the matrix
+// belongs to CTA r mod JAC_CLUSTER.  Per step: partial sums of the column norm
+// (cluster barrier 1, partials read through distributed shared memory), the
+// owned entries of p = beta A22 v written to a global buffer with partial sums
+// of p^T v (barrier 2), the full w = p - K v rebuilt in shared memory and the
+// owned rows updated (barrier 3).  All CTAs compute the same reflector from the
+// same partials in the same order, so every barrier is reached by every
+// thread.
+__global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
+    tridiag_kernel(const TridiagDesc* __restrict__ descs) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int mat = blockIdx.x / JAC_CLUSTER;
+    const int crank = (int)cluster.block_rank();
+    const TridiagDesc t = descs[mat];
     const int n = t.n;
     extern __shared__ double tri_smem[];
-    double* v = tri_smem;      // n
-    double* p = v + n;         // n
-    __shared__ double red[32];
+    double* v = tri_smem;  // n
+    double* w = v + n;     // n
+    __shared__ double part[2];
+    __shared__ double red[8];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
     double* A = t.A;
-    if (tid == 0) t.e[0] = 0.0;
+    if (crank == 0 && tid == 0) t.e[0] = 0.0;
     for (int k = 0; k + 2 < n; ++k) {
-        const int m = n - k - 1;  // length of v
+        const int m = n - k - 1;
+        // owned rows of the trailing block: global rows r = k+1+i with r % CS == crank
+        const int first = (k + 1) + ((crank - (k + 1)) % JAC_CLUSTER + JAC_CLUSTER) % JAC_CLUSTER;
         double sl = 0.0;
-        for (int i = tid; i < m; i += blockDim.x) {
-            const double x = A[(size_t)(k + 1 + i) * t.ld + k];
+        for (int r = first + JAC_CLUSTER * tid; r < n; r += JAC_CLUSTER * blockDim.x) {
+            const double x = __ldcg(A + (size_t)r * t.ld + k);
             sl = fma(x, x, sl);
         }
-        const double s2 = block_sum_1024(sl, red);
-        const double x0 = A[(size_t)(k + 1) * t.ld + k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sl += __shfl_xor_sync(0xffffffffu, sl, o);
+        if (lane == 0) red[warp] = sl;
+        __syncthreads();
+        if (tid == 0) {
+            double q = 0.0;
+            for (int ww = 0; ww < nw; ++ww) q += red[ww];
+            part[0] = q;
+        }
+        cluster.sync();  // 1
+        double s2 = 0.0;
+        for (int rr = 0; rr < JAC_CLUSTER; ++rr) s2 += *cluster.map_shared_rank(&part[0], rr);
+        const double x0 = __ldcg(A + (size_t)(k + 1) * t.ld + k);
         const double tail = s2 - x0 * x0;
-        if (tid == 0) t.d[k] = A[(size_t)k * t.ld + k];
-        if (!(tail > 0.0)) {  // column already in tridiagonal form
-            if (tid == 0) t.e[k + 1] = x0;
-            __syncthreads();
+        if (crank == 0 && tid == 0) t.d[k] = __ldcg(A + (size_t)k * t.ld + k);
+        if (!(tail > 0.0)) {
+            if (crank == 0 && tid == 0) t.e[k + 1] = x0;
+            cluster.sync();  // 2
+            cluster.sync();  // 3
             continue;
         }
         const double alpha = -copysign(sqrt(s2), x0);
         const double v0 = x0 - alpha;
         const double beta = 2.0 / fma(v0, v0, tail);
-        for (int i = tid; i < m; i += blockDim.x) v[i] = (i == 0) ? v0 : A[(size_t)(k + 1 + i) * t.ld + k];
+        for (int i = tid; i < m; i += blockDim.x) v[i] = (i == 0) ? v0 : __ldcg(A + (size_t)(k + 1 + i) * t.ld + k);
         __syncthreads();
-        // p = beta A22 v (one warp per row)
-        for (int i = warp; i < m; i += nw) {
-            const double* row = A + (size_t)(k + 1 + i) * t.ld + (k + 1);
+        // p = beta A22 v for owned rows
+        double kl = 0.0;
+        for (int r = first + JAC_CLUSTER * warp; r < n; r += JAC_CLUSTER * nw) {
+            const double* row = A + (size_t)r * t.ld + (k + 1);
             double acc0 = 0.0, acc1 = 0.0;
             int j = lane;
             for (; j + 32 < m; j += 64) {
-                acc0 = fma(row[j], v[j], acc0);
-                acc1 = fma(row[j + 32], v[j + 32], acc1);
+                acc0 = fma(__ldcg(row + j), v[j], acc0);
+                acc1 = fma(__ldcg(row + j + 32), v[j + 32], acc1);
             }
-            if (j < m) acc0 = fma(row[j], v[j], acc0);
+            if (j < m) acc0 = fma(__ldcg(row + j), v[j], acc0);
             double acc = acc0 + acc1;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) p[i] = beta * acc;
+            const int i = r - (k + 1);
+            if (lane == 0) {
+                t.p[i] = beta * acc;
+                kl = fma(beta * acc, v[i], kl);
+            }
         }
+        if (lane == 0) red[warp] = kl;
         __syncthreads();
-        double kl = 0.0;
-        for (int i = tid; i < m; i += blockDim.x) kl = fma(p[i], v[i], kl);
-        const double K = 0.5 * beta * block_sum_1024(kl, red);
-        for (int i = tid; i < m; i += blockDim.x) p[i] = fma(-K, v[i], p[i]);  // w
-        __syncthreads();
-        for (int i = warp; i < m; i += nw) {
-            double* row = A + (size_t)(k + 1 + i) * t.ld + (k + 1);
-            const double vi = v[i], wi = p[i];
-            for (int j = lane; j < m; j += 32) row[j] = fma(-vi, p[j], fma(-wi, v[j], row[j]));
+        if (tid == 0) {
+            double q = 0.0;
+            for (int ww = 0; ww < nw; ++ww) q += red[ww];
+            part[1] = q;
         }
-        if (tid == 0) t.e[k + 1] = alpha;
+        __threadfence();
+        cluster.sync();  // 2
+        double ks = 0.0;
+        for (int rr = 0; rr < JAC_CLUSTER; ++rr) ks += *cluster.map_shared_rank(&part[1], rr);
+        const double K = 0.5 * beta * ks;
+        for (int i = tid; i < m; i += blockDim.x) w[i] = fma(-K, v[i], __ldcg(t.p + i));
         __syncthreads();
+        for (int r = first + JAC_CLUSTER * warp; r < n; r += JAC_CLUSTER * nw) {
+            double* row = A + (size_t)r * t.ld + (k + 1);
+            const int i = r - (k + 1);
+            const double vi = v[i], wi = w[i];
+            for (int j = lane; j < m; j += 32) row[j] = fma(-vi, w[j], fma(-wi, v[j], __ldcg(row + j)));
+        }
+        if (crank == 0 && tid == 0) t.e[k + 1] = alpha;
+        __threadfence();
+        cluster.sync();  // 3
     }
-    if (tid == 0) {
+    if (crank == 0 && tid == 0) {
         if (n >= 2) {
-            t.d[n - 2] = A[(size_t)(n - 2) * t.ld + (n - 2)];
-            t.e[n - 1] = A[(size_t)(n - 1) * t.ld + (n - 2)];
+            t.d[n - 2] = __ldcg(A + (size_t)(n - 2) * t.ld + (n - 2));
+            t.e[n - 1] = __ldcg(A + (size_t)(n - 1) * t.ld + (n - 2));
         }
-        if (n >= 1) t.d[n - 1] = A[(size_t)(n - 1) * t.ld + (n - 1)];
+        if (n >= 1) t.d[n - 1] = __ldcg(A + (size_t)(n - 1) * t.ld + (n - 1));
     }
 }
 
@@ -825,77 +875,90 @@ void launch_tridiag(const TridiagDesc* d, int nmat, int maxn, cudaStream_t s) {
     if (nmat <= 0 || maxn <= 0) return;
     const size_t smem = 2 * (size_t)maxn * sizeof(double);
     if (smem > 48 * 1024) cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    tridiag_kernel<<<nmat, 1024, smem, s>>>(d);
+    tridiag_kernel<<<nmat * JAC_CLUSTER, 256, smem, s>>>(d);
 }
 
-// All eigenvalues of symmetric tridiagonal matrices by multisection with
-// Sturm counts (number of negative pivots of T - x I), one warp per
-// eigenvalue: eigenvalue j (ascending) is the x where the count passes j.
-// Each step, the 32 lanes count at 32 interior points of [lo, hi] and the
-// interval shrinks to the sub-interval where the count passes j (a factor 33
-// per step).  The interval starts from the Gershgorin bounds and stops when
-// it is no wider than 2 eps (|lo| + |hi|) or stops shrinking.
-__global__ void __launch_bounds__(256) bisect_kernel(const TridiagDesc* __restrict__ descs,
+// All eigenvalues of symmetric tridiagonal matrices by bisection, one thread
+// per eigenvalue j (ascending): eigenvalue j is the x where the Sturm count
+// (number of eigenvalues below x = number of negative pivots of T - x I)
+// passes j.  The count uses the leading principal minors
+// p_i = (d_i - x) p_{i-1} - e_i^2 p_{i-2} (a pivot p_i / p_{i-1} is negative
+// when consecutive minors differ in sign), which needs no division; minors are
+// rescaled by powers of two to stay in range, and an exact zero minor is
+// replaced by a tiny value of the opposite sign (the pivot counts as
+// negative).  The interval starts from the Gershgorin bounds and is halved
+// until it is no wider than 2 eps (|lo| + |hi|) or stops shrinking.
+__device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int n,
+                                           double x) {
+    // signs and magnitudes are read from the bit patterns (integer pipe); the
+    // FP64 work per step is one subtraction, one multiplication and one FMA
+    double p2 = 1.0, p1 = d[0] - x;
+    if (p1 == 0.0) p1 = -0x1p-1000;
+    long long b1 = __double_as_longlong(p1);
+    int cnt = (b1 < 0);
+    for (int i = 1; i < n; ++i) {
+        double p = fma(d[i] - x, p1, -e2[i] * p2);
+        long long b = __double_as_longlong(p);
+        if ((b & 0x7fffffffffffffffLL) == 0) {  // exact zero: opposite sign to p1, tiny magnitude
+            p = (b1 < 0) ? 0x1p-1000 : -0x1p-1000;
+            b = __double_as_longlong(p);
+        }
+        cnt += ((b ^ b1) < 0);
+        const int ex = (int)((b >> 52) & 0x7ff);
+        if (ex > 1023 + 400) {
+            p *= 0x1p-400;
+            p1 *= 0x1p-400;
+        } else if (ex < 1023 - 400) {
+            p *= 0x1p+400;
+            p1 *= 0x1p+400;
+        }
+        p2 = p1;
+        p1 = p;
+        b1 = __double_as_longlong(p1);
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(32) bisect_kernel(const TridiagDesc* __restrict__ descs,
                                                       const int* __restrict__ eig_mat,
                                                       const int* __restrict__ eig_idx, int64_t total,
                                                       double* const* __restrict__ out) {
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= total) return;
-    const TridiagDesc t = descs[eig_mat[w]];
-    const int j = eig_idx[w];
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const TridiagDesc t = descs[eig_mat[gid]];
+    const int j = eig_idx[gid];
     const int n = t.n;
-    double lo = 0.0, hi = 0.0, emax2 = 0.0;
-    for (int i = lane; i < n; i += 32) {
-        const double r = (i > 0 ? fabs(t.e[i]) : 0.0) + (i + 1 < n ? fabs(t.e[i + 1]) : 0.0);
-        const double l = t.d[i] - r, u = t.d[i] + r;
-        lo = (i == lane) ? l : fmin(lo, l);
-        hi = (i == lane) ? u : fmax(hi, u);
-        if (i > 0) emax2 = fmax(emax2, t.e[i] * t.e[i]);
+    double* e2 = t.e;  // squared in place by bisect_prepare_kernel
+    double lo = 0.0, hi = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? sqrt(e2[i]) : 0.0) + (i + 1 < n ? sqrt(e2[i + 1]) : 0.0);
+        lo = (i == 0) ? t.d[i] - r : fmin(lo, t.d[i] - r);
+        hi = (i == 0) ? t.d[i] + r : fmax(hi, t.d[i] + r);
     }
-    if (lane >= n) {
-        lo = t.d[0];
-        hi = t.d[0];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-        emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
-    }
-    const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax2);
     const double eps = 2.220446049250313e-16;
-    for (int it = 0; it < 64; ++it) {
-        if ((hi - lo) <= 2.0 * eps * (fabs(lo) + fabs(hi))) break;
-        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-        int cnt = 0;
-        double q = t.d[0] - x;
-        if (fabs(q) < pivmin) q = -pivmin;
-        cnt += (q < 0.0);
-        for (int i = 1; i < n; ++i) {
-            q = (t.d[i] - x) - t.e[i] * t.e[i] / q;
-            if (fabs(q) < pivmin) q = -pivmin;
-            cnt += (q < 0.0);
-        }
-        // first lane whose count exceeds j bounds the eigenvalue from above
-        const unsigned above = __ballot_sync(0xffffffffu, cnt > j && x > lo && x < hi);
-        const unsigned below = __ballot_sync(0xffffffffu, cnt <= j && x > lo && x < hi);
-        const int first_above = above ? __ffs(above) - 1 : 32;
-        const int last_below = below ? 31 - __clz(below) : -1;
-        const double nlo = (last_below >= 0) ? __shfl_sync(0xffffffffu, x, last_below) : lo;
-        const double nhi = (first_above < 32) ? __shfl_sync(0xffffffffu, x, first_above) : hi;
-        if (!(nhi - nlo < hi - lo)) break;
-        lo = nlo;
-        hi = nhi;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi) || (hi - lo) <= 2.0 * eps * (fabs(lo) + fabs(hi))) break;
+        if (sturm_count(t.d, e2, n, mid) > j)
+            hi = mid;
+        else
+            lo = mid;
     }
-    if (lane == 0) out[eig_mat[w]][j] = 0.5 * (lo + hi);
+    out[eig_mat[gid]][j] = 0.5 * (lo + hi);
 }
 
-void launch_bisect(const TridiagDesc* d, const int* eig_mat, const int* eig_idx, int64_t total, double* const* out,
-                   cudaStream_t s) {
+// e[i] <- e[i]^2 for every matrix (the bisection only needs the squares).
+__global__ void bisect_prepare_kernel(const TridiagDesc* __restrict__ descs) {
+    const TridiagDesc t = descs[blockIdx.x];
+    for (int i = threadIdx.x; i < t.n; i += blockDim.x) t.e[i] = t.e[i] * t.e[i];
+}
+
+void launch_bisect(const TridiagDesc* d, int nmat, const int* eig_mat, const int* eig_idx, int64_t total,
+                   double* const* out, cudaStream_t s) {
     if (total <= 0) return;
-    const int64_t threads = total * 32;
-    bisect_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(d, eig_mat, eig_idx, total, out);
+    bisect_prepare_kernel<<<nmat, 256, 0, s>>>(d);
+    // one warp per block so that the eigenvalues spread over every SM
+    bisect_kernel<<<(unsigned)((total + 31) / 32), 32, 0, s>>>(d, eig_mat, eig_idx, total, out);
 }
 
 // ------------------------------------------------------------------ row GEMV
