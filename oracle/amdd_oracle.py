@@ -195,6 +195,7 @@ class Setup:
     E: np.ndarray               # R_0 A R_0^T
     E_chol: tuple
     tau: float
+    eps: float = EPS
     extra: dict = field(default_factory=dict)
 
     @property
@@ -221,7 +222,7 @@ def setup(A, part, N: int, overlap: int, tau: float, eps: float = EPS) -> Setup:
     E = (W.T @ (As @ W)).toarray()
     E = 0.5 * (E + E.T)
     E_chol = sla.cho_factor(E, lower=True) if E.shape[0] else None
-    return Setup(As, subs, W, E, E_chol, tau)
+    return Setup(As, subs, W, E, E_chol, tau, eps)
 
 
 def coarse_basis(subs, n: int) -> sp.csr_matrix:
@@ -272,10 +273,12 @@ def apply(S: Setup, r: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------
 # PCG
 # --------------------------------------------------------------------------
-def pcg(As, b: np.ndarray, prec, rtol: float = 1e-8, maxit: int = 1000):
+def pcg(As, b: np.ndarray, prec, rtol: float = 1e-8, maxit: int = 1000, coeffs=None):
     """Preconditioned conjugate gradient (Hestenes-Stiefel), x0 = 0; stops when
     ||r_k||_2 <= rtol ||b||_2 (recursive residual).  Returns (x, iterations,
-    relative residual history)."""
+    relative residual history).  If `coeffs` is a list, the step lengths
+    alpha_k and the ratios beta_k = (r_{k}, z_{k}) / (r_{k-1}, z_{k-1}) are
+    appended to it as ("a", alpha) and ("b", beta) in the order computed."""
     x = np.zeros_like(b)
     r = b.copy()
     nb = np.linalg.norm(b)
@@ -288,6 +291,8 @@ def pcg(As, b: np.ndarray, prec, rtol: float = 1e-8, maxit: int = 1000):
     for k in range(1, maxit + 1):
         q = As @ p
         alpha = rz / (p @ q)
+        if coeffs is not None:
+            coeffs.append(("a", alpha))
         x += alpha * p
         r -= alpha * q
         hist.append(np.linalg.norm(r) / nb)
@@ -295,9 +300,79 @@ def pcg(As, b: np.ndarray, prec, rtol: float = 1e-8, maxit: int = 1000):
             return x, k, hist
         z = prec(r)
         rz_new = r @ z
+        if coeffs is not None:
+            coeffs.append(("b", rz_new / rz))
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, maxit, hist
+
+
+def lanczos_extremes(coeffs):
+    """Extreme eigenvalues of the Lanczos tridiagonal that k steps of PCG
+    build implicitly (the CG-Lanczos relation, e.g. Saad, Iterative Methods
+    for Sparse Linear Systems, Sec. 6.7.3): with step lengths alpha_j and
+    ratios beta_j,
+        T_11 = 1/alpha_1,  T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+        T_{j,j+1} = sqrt(beta_j)/alpha_j.
+    Its eigenvalues are Ritz values of M^{-1} A, inside [lambda_min,
+    lambda_max]; lambda_max(T)/lambda_min(T) is the condition estimate that
+    the bound of Sec. 3.2 is checked against.  Returns (lambda_min,
+    lambda_max), or (nan, nan) without a step."""
+    al = [v for t, v in coeffs if t == "a"]
+    be = [v for t, v in coeffs if t == "b"]
+    k = len(al)
+    if k == 0:
+        return float("nan"), float("nan")
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / al[j] + (be[j - 1] / al[j - 1] if j > 0 else 0.0)
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(be[j]) / al[j]
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[0]), float(ev[-1])
+
+
+def colouring_number(S) -> int:
+    """k_c of Sec. 3.2: colours of a greedy colouring of the subdomain graph
+    (i ~ j iff R_i A R_j^T != 0); any valid colouring gives a valid bound."""
+    N = len(S.subs)
+    A = S.A
+    masks = []
+    for s in S.subs:
+        v = np.zeros(A.shape[0], dtype=bool)
+        v[s.omega] = True
+        masks.append(v)
+    adj = np.zeros((N, N), dtype=bool)
+    for i in range(N):
+        reach = (abs(A) @ masks[i].astype(float)) > 0
+        for j in range(N):
+            adj[i, j] = i != j and bool((reach & masks[j]).any())
+    col = -np.ones(N, dtype=int)
+    for i in range(N):
+        used = {col[j] for j in range(N) if adj[i, j] and col[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        col[i] = c
+    return int(col.max() + 1)
+
+
+def splitting_constant(S) -> float:
+    """k_m of Sec. 3.2: lambda_max(sum_i R_i^T tilde A_ii R_i, A) by a dense
+    generalized eigenproblem (tiny inputs only)."""
+    n = S.A.shape[0]
+    Ad = S.A.toarray()
+    T = np.zeros((n, n))
+    for s in S.subs:
+        Aii, X = local_matrices(S.A, s.I, s.G, s.D)
+        Abar, _ = splitting_root(X, S.eps)
+        T[np.ix_(s.omega, s.omega)] += schur_overlap(Abar, len(s.omega))
+    return float(sla.eigh(T, Ad, eigvals_only=True).max())
+
+
+def condition_bound(kc: int, km: float, tau: float) -> float:
+    """Sec. 3.2: kappa(M^{-1} A) <= (k_c + 1)(2 + (2 k_c + 1) k_m / tau)."""
+    return (kc + 1) * (2 + (2 * kc + 1) * km / tau)
 
 
 def solve(A, part, N, overlap, tau, b, rtol=1e-8, maxit=1000):

@@ -249,43 +249,6 @@ def test_single_subdomain_is_twice_exact_inverse():
     assert np.allclose(x, np.linalg.solve(Ad, b), atol=1e-10)
 
 
-def _colours(S):
-    """Greedy colouring of the subdomain graph (i ~ j iff R_i A R_j^T != 0)."""
-    N = len(S.subs)
-    A = S.A
-    masks = []
-    for s in S.subs:
-        v = np.zeros(A.shape[0], dtype=bool)
-        v[s.omega] = True
-        masks.append(v)
-    adj = np.zeros((N, N), dtype=bool)
-    for i in range(N):
-        reach = (abs(A) @ masks[i].astype(float)) > 0
-        for j in range(N):
-            adj[i, j] = i != j and bool((reach & masks[j]).any())
-    col = -np.ones(N, dtype=int)
-    for i in range(N):
-        used = {col[j] for j in range(N) if adj[i, j] and col[j] >= 0}
-        c = 0
-        while c in used:
-            c += 1
-        col[i] = c
-    return col.max() + 1
-
-
-def _km(S):
-    """k_m = lambda_max(sum_i R_i^T tilde A_ii R_i, A) (dense GEVP)."""
-    n = S.A.shape[0]
-    Ad = S.A.toarray()
-    T = np.zeros((n, n))
-    for s in S.subs:
-        Aii, X = O.local_matrices(S.A, s.I, s.G, s.D)
-        Abar, _ = O.splitting_root(X)
-        tA = O.schur_overlap(Abar, len(s.omega))
-        T[np.ix_(s.omega, s.omega)] += tA
-    return sla.eigh(T, Ad, eigvals_only=True).max()
-
-
 @pytest.mark.parametrize("maker,tau", [(_small_2d, 0.5), (_small_2d, 50.0), (_small_3d, 0.5),
                                        (_small_3d, 0.05), (_small_3d, 100.0)])
 def test_condition_bound(maker, tau):
@@ -296,11 +259,52 @@ def test_condition_bound(maker, tau):
     Ad = S.A.toarray()
     Minv = _dense_minv(S)
     ev = np.sort(np.linalg.eigvals(Minv @ Ad).real)
-    kc, km = _colours(S), _km(S)
+    kc, km = O.colouring_number(S), O.splitting_constant(S)
     assert km <= N + 1e-8
     assert ev[-1] <= kc + 1 + 1e-8
     assert ev[0] >= 1.0 / (2 + (2 * kc + 1) * km / tau) - 1e-10
-    assert ev[-1] / ev[0] <= (kc + 1) * (2 + (2 * kc + 1) * km / tau) * (1 + 1e-10)
+    assert ev[-1] / ev[0] <= O.condition_bound(kc, km, tau) * (1 + 1e-10)
+
+
+@pytest.mark.parametrize("maker,tau", [(_small_2d, 0.5), (_small_3d, 0.5), (_small_3d, 100.0)])
+def test_lanczos_estimate_against_dense_spectrum(maker, tau):
+    """The CG-Lanczos tridiagonal (Saad, Sec. 6.7.3) built from the PCG
+    coefficients has Ritz values inside the dense spectrum of M^{-1} A, and
+    run to a tight tolerance its extremes reach the extreme eigenvalues."""
+    A, part, N = maker()
+    S = O.setup(A, part, N, 1, tau)
+    ev = np.sort(np.linalg.eigvals(_dense_minv(S) @ S.A.toarray()).real)
+    b = synth.rhs(A.n, 3)
+    co = []
+    O.pcg(S.A, b, lambda r: O.apply(S, r), rtol=1e-8, coeffs=co)
+    lo, hi = O.lanczos_extremes(co)
+    assert ev[0] * (1 - 1e-9) <= lo and hi <= ev[-1] * (1 + 1e-9)
+    assert hi / lo <= ev[-1] / ev[0] * (1 + 1e-9)
+    co = []
+    O.pcg(S.A, b, lambda r: O.apply(S, r), rtol=1e-13, coeffs=co)
+    lo, hi = O.lanczos_extremes(co)
+    assert abs(hi - ev[-1]) <= 1e-6 * ev[-1]
+    assert abs(lo - ev[0]) <= 2e-3 * ev[0]
+
+
+def test_lanczos_estimate_first_step():
+    """Closed forms on a diagonal system with M = I: after one step T =
+    [1/alpha_1] = (b, A b)/(b, b), the mean of the diagonal for b = 1; after
+    n steps on n distinct eigenvalues T is similar to A, so its extremes are
+    those of A."""
+    d = np.array([1.0, 2.0, 5.0])
+    As = sp.diags(d).tocsr()
+    b = np.array([1.0, 1.0, 1.0])
+    co = []
+    O.pcg(As, b, lambda r: r.copy(), rtol=1e-30, maxit=1, coeffs=co)
+    lo, hi = O.lanczos_extremes(co)
+    # z = b, alpha = (b,b)/(b,Ab) -> Ritz value (b,Ab)/(b,b) = mean(d)
+    assert lo == pytest.approx(d.mean(), rel=1e-14) and hi == lo
+    co = []
+    O.pcg(As, b, lambda r: r.copy(), rtol=1e-30, maxit=3, coeffs=co)
+    lo, hi = O.lanczos_extremes(co)
+    # three steps on a 3x3 system with distinct eigenvalues: T is similar to diag(d)
+    assert lo == pytest.approx(1.0, rel=1e-12) and hi == pytest.approx(5.0, rel=1e-12)
 
 
 def test_preconditioner_symmetric_positive_definite():
