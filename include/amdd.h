@@ -71,7 +71,14 @@ typedef struct {
     int32_t max_sweeps;   /* sweep limit of the one-sided Jacobi solvers; default 60               */
     int32_t profile;      /* 1: time every kernel launch of the handle with CUDA events (see
                              amdd_get_profile); default 0                                           */
-    int32_t reserved[6];  /* must be zero                                                          */
+    int32_t precision;    /* 0: plain FP64 (default).  1: mixed form: the local work (local
+                             Cholesky factors and solves, SVD of X_i, splitting, eq. (Zi)) in FP32
+                             with FP32 accumulation; E, its factor, the coarse solve and PCG in FP64.
+                             Sec. 3.2 takes eps as the machine precision of the arithmetic, so the
+                             FP32 stage uses max(eps, 2^-23) (amdd_info.eps reports it)             */
+    uint32_t profile_classes; /* with profile = 1: bit k set times kernel class k only (classes as
+                             numbered by amdd_get_profile); 0 times every class; default 0         */
+    int32_t reserved[4];  /* must be zero                                                          */
 } amdd_opts;
 
 typedef struct {
@@ -80,6 +87,11 @@ typedef struct {
     double rel_residual;        /* recursive residual ||r_k|| / ||b|| at exit                */
     double true_rel_residual;   /* ||b - A x|| / ||b|| recomputed at exit                    */
     double solve_ms;            /* wall time of the call                                     */
+    double ritz_min;            /* extreme eigenvalues of the Lanczos tridiagonal built from  */
+    double ritz_max;            /* the PCG step lengths alpha_k and ratios beta_k (first     */
+    double cond_est;            /* right-hand side): Ritz values of M^{-1} A, inside its     */
+                                /* spectrum; cond_est = ritz_max / ritz_min, the estimate    */
+                                /* checked against the bound of Sec. 3.2 (NaN: no step)      */
 } amdd_stats;
 
 typedef struct {
@@ -99,6 +111,8 @@ typedef struct {
     int64_t rotations_eig; /* plane rotations applied by the eq. (Zi) solver */
     int32_t sweeps_svd32;  /* sweeps of the FP32 preconditioning stage (SVD) */
     int32_t sweeps_eig32;  /* sweeps of the FP32 preconditioning stage (eq. (Zi)) */
+    int32_t precision;     /* 0 plain FP64, 1 mixed (see amdd_opts)          */
+    double eps;            /* the eps of the splitting actually used       */
 } amdd_info;
 
 /* Fill `o` with the defaults (eps = 2^-52, max_sweeps = 60). */
@@ -153,6 +167,16 @@ amdd_status amdd_apply(amdd_handle* h, const double* r, double* z, int32_t nrhs)
 amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t nrhs,
                            double rtol, int32_t maxit, amdd_stats* stats);
 
+/* Host-only, no GPU involved: the extreme eigenvalues of the Lanczos
+ * tridiagonal of k PCG steps (the CG-Lanczos relation; Sec. 1 gives the CG
+ * bound these Ritz values feed): T_11 = 1/alpha_1, T_jj = 1/alpha_j +
+ * beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j, from the HOST
+ * arrays alpha[k] (> 0) and beta[k-1] (>= 0; may be NULL for k <= 1).  Writes
+ * *lo, *hi (NaN for k = 0).  AMDD_ERR_INVALID on a negative k or a
+ * non-positive alpha / negative beta.  amdd_pcg_solve reports the same
+ * values in amdd_stats. */
+amdd_status amdd_lanczos_extremes(const double* alpha, const double* beta, int32_t k, double* lo, double* hi);
+
 /* Sizes and counters of a handle (host struct). */
 amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info);
 
@@ -191,7 +215,7 @@ amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, i
  * amdd_setup, amdd_apply and amdd_pcg_solve until amdd_reset_profile.
  * Synchronises the handle's stream.  AMDD_ERR_INVALID if profiling is off or
  * k is out of range. */
-#define AMDD_PROF_CLASSES 16
+#define AMDD_PROF_CLASSES 23
 amdd_status amdd_get_profile(amdd_handle* h, int32_t k, const char** name, int64_t* launches, double* ms,
                              double* flops, double* bytes);
 

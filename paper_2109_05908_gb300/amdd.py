@@ -25,12 +25,13 @@ class amdd_csr(C.Structure):
 
 class amdd_opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("max_sweeps", C.c_int32), ("profile", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("precision", C.c_int32), ("profile_classes", C.c_uint32), ("reserved", C.c_int32 * 4)]
 
 
 class amdd_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
-                ("true_rel_residual", C.c_double), ("solve_ms", C.c_double)]
+                ("true_rel_residual", C.c_double), ("solve_ms", C.c_double), ("ritz_min", C.c_double),
+                ("ritz_max", C.c_double), ("cond_est", C.c_double)]
 
 
 class amdd_info(C.Structure):
@@ -38,7 +39,8 @@ class amdd_info(C.Structure):
                 ("n_C", C.c_int64), ("sum_ni", C.c_int64), ("sum_nti", C.c_int64), ("max_ni", C.c_int32),
                 ("max_nti", C.c_int32), ("sweeps_svd", C.c_int32), ("sweeps_eig", C.c_int32),
                 ("setup_ms", C.c_double), ("rotations_svd", C.c_int64), ("rotations_eig", C.c_int64),
-                ("sweeps_svd32", C.c_int32), ("sweeps_eig32", C.c_int32)]
+                ("sweeps_svd32", C.c_int32), ("sweeps_eig32", C.c_int32), ("precision", C.c_int32),
+                ("eps", C.c_double)]
 
 
 class AmddError(RuntimeError):
@@ -59,6 +61,8 @@ SIGNATURES = {
     "amdd_pcg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32,
                                  C.POINTER(amdd_stats)]),
     "amdd_get_info": (C.c_int, [C.c_void_p, C.POINTER(amdd_info)]),
+    "amdd_lanczos_extremes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]),
     "amdd_get_subdomain": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "amdd_get_eigenvalues": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
@@ -200,7 +204,19 @@ def overlap_sets(n, rowptr, colind, part, i: int, overlap: int):
     return I, G, D
 
 
-PROF_CLASSES = 16
+def lanczos_extremes(alpha, beta):
+    """Host-only extreme eigenvalues of the PCG Lanczos tridiagonal from the
+    step lengths alpha[k] and ratios beta[k-1]; returns (lo, hi)."""
+    import numpy as np
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    lo, hi = C.c_double(), C.c_double()
+    _check(lib().amdd_lanczos_extremes(a.ctypes.data if a.size else None, b.ctypes.data if b.size else None,
+                                       int(a.size), C.byref(lo), C.byref(hi)), "amdd_lanczos_extremes")
+    return lo.value, hi.value
+
+
+PROF_CLASSES = 23
 
 
 def get_profile(h: int):

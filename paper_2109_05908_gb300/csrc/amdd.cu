@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -56,15 +57,32 @@ enum ProfK {
     PK_GEMV,
     PK_GATHER_SCATTER,
     PK_PCG_VEC,
+    // FP32 variants (mixed form)
+    PK_GEMM_F32,
+    PK_CHOL_DIAG_F32,
+    PK_CHOL_PANEL_F32,
+    PK_TRTRI_F32,
+    PK_TRIDIAG_F32,
+    PK_BISECT_F32,
+    PK_GEMV_F32,
     PK_COUNT
 };
 static_assert(PK_COUNT == AMDD_PROF_CLASSES, "profile classes");
 static const char* const kProfNames[PK_COUNT] = {
     "gather_values", "chol_diag", "chol_panel", "gemm_tiles", "trtri_diag", "jacobi_svd", "jacobi_eig", "jacobi_f32", "tridiag", "bisect",
-    "small_dense", "e_offdiag", "spmv", "gemv_rows", "gather_scatter", "pcg_vectors"};
+    "small_dense", "e_offdiag", "spmv", "gemv_rows", "gather_scatter", "pcg_vectors",
+    "gemm_tiles_f32", "chol_diag_f32", "chol_panel_f32", "trtri_diag_f32", "tridiag_f32", "bisect_f32",
+    "gemv_rows_f32"};
+
+// class of a kernel in element type T (FP32 variants have their own classes)
+template <typename T>
+constexpr int pk(int k64, int k32) {
+    return std::is_same<T, float>::value ? k32 : k64;
+}
 
 struct ProfState {
     bool on = false;
+    uint32_t mask = ~0u;  // classes timed
     int64_t launches[PK_COUNT] = {};
     double flops[PK_COUNT] = {};
     double bytes[PK_COUNT] = {};
@@ -133,6 +151,12 @@ struct amdd_handle {
     int32_t *d_nI = nullptr, *d_p = nullptr;
     int64_t *d_sc_ptr = nullptr, *d_zt_off = nullptr, *d_coff = nullptr;
     double *d_rloc = nullptr, *d_tloc = nullptr, *d_yloc = nullptr;
+    // mixed form: FP32 local factors and local work vectors
+    int precision = 0;
+    float *d_Y32 = nullptr, *d_Yt32 = nullptr;
+    float *d_rloc32 = nullptr, *d_tloc32 = nullptr, *d_yloc32 = nullptr;
+    GemvDescT<float>* d_gv_l1_32 = nullptr;
+    GemvDescT<float>* d_gv_l2_32 = nullptr;
     double *d_c = nullptr, *d_ct = nullptr, *d_e = nullptr, *d_ctmp = nullptr;
     // coarse solve: L_E (d_YE), L_E^T (d_YEt), inverses of its diagonal blocks
     double *d_Yd = nullptr, *d_Ydt = nullptr;
@@ -177,7 +201,7 @@ struct PScope {
     int k;
     cudaEvent_t b = nullptr;
     PScope(amdd_handle* hh, int kk, double flops = 0.0, double bytes = 0.0) : h(hh), k(kk) {
-        if (!h->prof.on) return;
+        if (!h->prof.on || !((h->prof.mask >> k) & 1u)) return;
         b = h->prof.take();
         if (!b) return;
         cudaEventRecord(b, h->s);
@@ -225,10 +249,11 @@ struct Ctx {
 
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
-void gemm(Ctx& C, const std::vector<GemmDesc>& ds) {
+template <typename T>
+void gemm(Ctx& C, const std::vector<GemmDescT<T>>& ds) {
     std::vector<TileRef> tiles;
     for (int d = 0; d < (int)ds.size(); ++d) {
-        const GemmDesc& g = ds[d];
+        const GemmDescT<T>& g = ds[d];
         if (g.m <= 0 || g.n <= 0) continue;
         const int tm = cdiv(g.m, GEMM_T), tn = cdiv(g.n, GEMM_T);
         for (int a = 0; a < tm; ++a)
@@ -239,21 +264,22 @@ void gemm(Ctx& C, const std::vector<GemmDesc>& ds) {
     }
     if (tiles.empty()) return;
     double fl = 0.0;
-    for (const GemmDesc& g : ds) {
+    for (const GemmDescT<T>& g : ds) {
         if (g.m <= 0 || g.n <= 0) continue;
         const double m = g.m, n = g.n;
         const double outs = g.lower ? (n <= m ? m * n - n * (n - 1) / 2 : m * (m + 1) / 2) : m * n;
         fl += 2.0 * outs * g.k;
     }
-    const GemmDesc* dd = C.up(ds);
+    const GemmDescT<T>* dd = C.up(ds);
     const TileRef* dt = C.up(tiles);
-    PScope ps(C.h, PK_GEMM, fl);
-    launch_gemm(dd, dt, (int)tiles.size(), C.h->s);
+    PScope ps(C.h, pk<T>(PK_GEMM, PK_GEMM_F32), fl);
+    launch_gemm<T>(dd, dt, (int)tiles.size(), C.h->s);
 }
 
-GemmDesc gd(const double* A, int lda, int ta, const double* B, int ldb, int tb, double* Cm, int ldc, int m, int n,
-            int k, double alpha, double beta, int lower) {
-    GemmDesc g;
+template <typename T>
+GemmDescT<T> gd(const T* A, int lda, int ta, const T* B, int ldb, int tb, T* Cm, int ldc, int m, int n, int k,
+                double alpha, double beta, int lower) {
+    GemmDescT<T> g;
     g.A = A;
     g.B = B;
     g.C = Cm;
@@ -267,8 +293,8 @@ GemmDesc gd(const double* A, int lda, int ta, const double* B, int ldb, int tb, 
     g.tb = tb;
     g.lower = lower;
     g.kfrom_row = 0;
-    g.alpha = alpha;
-    g.beta = beta;
+    g.alpha = (T)alpha;
+    g.beta = (T)beta;
     return g;
 }
 
@@ -280,10 +306,11 @@ GemmDesc gd(const double* A, int lda, int ta, const double* B, int ldb, int tb, 
 // non-zero column (the envelope).  The Cholesky factor keeps the envelope of
 // the matrix, so panel row tiles and trailing-update tiles whose rows have no
 // entries in the current block column are zero throughout and are skipped.
-void chol_batched(Ctx& C, const std::vector<CholDesc>& ds, const std::vector<const std::vector<int>*>& env = {}) {
+template <typename T>
+void chol_batched(Ctx& C, const std::vector<CholDescT<T>>& ds, const std::vector<const std::vector<int>*>& env = {}) {
     if (ds.empty()) return;
     amdd_handle* h = C.h;
-    CholDesc* dd = C.up(ds);
+    CholDescT<T>* dd = C.up(ds);
     int maxstop = 0;
     for (const auto& d : ds) maxstop = std::max(maxstop, d.stop);
     for (int k0 = 0; k0 < maxstop; k0 += CHOL_NB) {
@@ -294,15 +321,15 @@ void chol_batched(Ctx& C, const std::vector<CholDesc>& ds, const std::vector<con
                     const double kb = std::min(k0 + CHOL_NB, c.stop) - k0;
                     fl += 2.0 * kb * kb * kb / 3.0;
                 }
-            PScope ps(h, PK_CHOL_DIAG, fl);
-            launch_chol_diag(dd, (int)ds.size(), k0, h->d_err, h->s);
+            PScope ps(h, pk<T>(PK_CHOL_DIAG, PK_CHOL_DIAG_F32), fl);
+            launch_chol_diag<T>(dd, (int)ds.size(), k0, h->d_err, h->s);
         }
         std::vector<PanelRef> pt;
         double pfl = 0.0, gfl = 0.0;
-        std::vector<GemmDesc> g;
+        std::vector<GemmDescT<T>> g;
         std::vector<TileRef> gt;
         for (int d = 0; d < (int)ds.size(); ++d) {
-            const CholDesc& c = ds[d];
+            const CholDescT<T>& c = ds[d];
             if (k0 >= c.stop) continue;
             const int kend = std::min(k0 + CHOL_NB, c.stop);
             const int rows = c.n - kend;
@@ -323,7 +350,7 @@ void chol_batched(Ctx& C, const std::vector<CholDesc>& ds, const std::vector<con
                     pt.push_back({d, rt});
                     pfl += (double)std::min(64, rows - 64 * rt) * kb * (kb + 1);
                 }
-            double* panel = c.A + (size_t)kend * c.ld + k0;
+            T* panel = c.A + (size_t)kend * c.ld + k0;
             const int gi = (int)g.size();
             g.push_back(gd(panel, c.ld, 0, panel, c.ld, 1, c.A + (size_t)kend * c.ld + kend, c.ld, rows, rows, kb, -1.0,
                            1.0, 1));
@@ -336,36 +363,37 @@ void chol_batched(Ctx& C, const std::vector<CholDesc>& ds, const std::vector<con
         }
         if (!pt.empty()) {
             const PanelRef* dpt = C.up(pt);
-            PScope ps(h, PK_CHOL_PANEL, pfl);
-            launch_chol_panel(dd, dpt, (int)pt.size(), k0, h->s);
+            PScope ps(h, pk<T>(PK_CHOL_PANEL, PK_CHOL_PANEL_F32), pfl);
+            launch_chol_panel<T>(dd, dpt, (int)pt.size(), k0, h->s);
         }
         if (!gt.empty()) {
-            const GemmDesc* dg = C.up(g);
+            const GemmDescT<T>* dg = C.up(g);
             const TileRef* dt = C.up(gt);
-            PScope ps(h, PK_GEMM, gfl);
-            launch_gemm(dg, dt, (int)gt.size(), h->s);
+            PScope ps(h, pk<T>(PK_GEMM, PK_GEMM_F32), gfl);
+            launch_gemm<T>(dg, dt, (int)gt.size(), h->s);
         }
     }
 }
 
 // Y = L^{-1} (lower triangular) for a batch, from the factors and the
 // diagonal-block inverses left by chol_batched.
-void trtri_batched(Ctx& C, const std::vector<TrtriDesc>& ds) {
+template <typename T>
+void trtri_batched(Ctx& C, const std::vector<TrtriDescT<T>>& ds) {
     if (ds.empty()) return;
     amdd_handle* h = C.h;
-    TrtriDesc* dd = C.up(ds);
+    TrtriDescT<T>* dd = C.up(ds);
     int maxn = 0;
     for (const auto& d : ds) maxn = std::max(maxn, d.n);
     {
         PScope ps(h, PK_SMALL);
-        launch_set_identity(dd, (int)ds.size(), maxn, h->s);
+        launch_set_identity<T>(dd, (int)ds.size(), maxn, h->s);
     }
     for (int k0 = 0; k0 < maxn; k0 += CHOL_NB) {
         std::vector<ChunkRef> ch;
-        std::vector<GemmDesc> g;
+        std::vector<GemmDescT<T>> g;
         double fl = 0.0;
         for (int d = 0; d < (int)ds.size(); ++d) {
-            const TrtriDesc& t = ds[d];
+            const TrtriDescT<T>& t = ds[d];
             if (k0 >= t.n) continue;
             const int kend = std::min(k0 + CHOL_NB, t.n);
             for (int ct = 0; ct * 64 < kend; ++ct) ch.push_back({d, ct});
@@ -376,14 +404,15 @@ void trtri_batched(Ctx& C, const std::vector<TrtriDesc>& ds) {
         }
         {
             const ChunkRef* dch = C.up(ch);
-            PScope ps(h, PK_TRTRI, fl);
-            launch_trtri_diag(dd, dch, (int)ch.size(), k0, h->s);
+            PScope ps(h, pk<T>(PK_TRTRI, PK_TRTRI_F32), fl);
+            launch_trtri_diag<T>(dd, dch, (int)ch.size(), k0, h->s);
         }
         gemm(C, g);
     }
 }
 
-void transpose_batched(Ctx& C, const std::vector<const double*>& src, const std::vector<double*>& dst,
+template <typename T>
+void transpose_batched(Ctx& C, const std::vector<const T*>& src, const std::vector<T*>& dst,
                        const std::vector<int>& n, const std::vector<int>& lds, const std::vector<int>& ldd) {
     if (src.empty()) return;
     int maxn = *std::max_element(n.begin(), n.end());
@@ -393,7 +422,7 @@ void transpose_batched(Ctx& C, const std::vector<const double*>& src, const std:
     auto d = C.up(lds);
     auto e = C.up(ldd);
     PScope ps(C.h, PK_SMALL);
-    launch_transpose(a, b, c, d, e, (int)src.size(), maxn, C.h->s);
+    launch_transpose<T>(a, b, c, d, e, (int)src.size(), maxn, C.h->s);
 }
 
 // One-sided Jacobi on the rows of a batch: the shared-memory-resident block
@@ -544,7 +573,13 @@ void overlap_layers(const int64_t* rp, const int32_t* ci, const std::vector<int3
 // ---------------------------------------------------------------------------
 // Setup
 // ---------------------------------------------------------------------------
+// T is the precision of the local work (sets aside): double for the plain
+// FP64 form, float for the mixed form (local factors, local solves, the SVD
+// of X_i, the splitting and the eigensolve in FP32; E, its factor and PCG in
+// FP64).
+template <typename T>
 void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
+    constexpr bool f64 = std::is_same<T, double>::value;
     const int64_t n = A->n, nnz = A->nnz;
     const int N = h->N, ov = h->overlap;
     cudaStream_t s = h->s;
@@ -673,23 +708,30 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     // ---- device buffers
     h->d_omega = C.up(omega, true);
     double* Araw = C.tnew<double>(h->sum_sq);
-    double* Lb = C.tnew<double>(h->sum_sq);
+    T* Lb = C.tnew<T>(h->sum_sq);
     double* Xp = C.tnew<double>(off_x[N]);
-    double* M = C.tnew<double>(off_m[N]);
-    double* TI = C.tnew<double>(off_ti[N]);
-    double* Pb = C.tnew<double>(off_P[N]);
+    T* M = C.tnew<T>(off_m[N]);
+    T* TI = C.tnew<T>(off_ti[N]);
+    T* Pb = C.tnew<T>(off_P[N]);
     double* sig = C.tnew<double>(h->sum_ni);
     double* mu = C.tnew<double>(h->sum_nI);
-    double* delta = C.tnew<double>(N);
-    double* linvA = C.tnew<double>(off_la[N]);
-    double* linvM = C.tnew<double>(off_lm[N]);
+    T* delta = C.tnew<T>(N);
+    T* linvA = C.tnew<T>(off_la[N]);
+    T* linvM = C.tnew<T>(off_lm[N]);
     // sweeps / rotations: [FP64 SVD, FP64 eig, FP32 SVD, FP32 eig] x N
     int* sweeps = C.tnew<int>(4 * N);
     unsigned long long* rots = C.tnew<unsigned long long>(4 * N);
     ck(cudaMemsetAsync(rots, 0, 4 * N * sizeof(unsigned long long), s));
-    double* nrm64 = C.tnew<double>(h->sum_ni);
-    h->d_Y = dnew<double>(h, h->sum_sq);
-    h->d_Yt = dnew<double>(h, h->sum_sq);
+    T* nrmT = C.tnew<T>(h->sum_ni);
+    T* Yl = dnew<T>(h, h->sum_sq);   // L_i^{-1}
+    T* Ylt = dnew<T>(h, h->sum_sq);  // L_i^{-T}
+    if constexpr (f64) {
+        h->d_Y = Yl;
+        h->d_Yt = Ylt;
+    } else {
+        h->d_Y32 = Yl;
+        h->d_Yt32 = Ylt;
+    }
     ck(cudaMemsetAsync(Araw, 0, h->sum_sq * sizeof(double), s));
     ck(cudaMemsetAsync(Xp, 0, off_x[N] * sizeof(double), s));
     {
@@ -706,21 +748,24 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             launch_gather_values(sx, dx, (int64_t)px_src.size(), h->val, Xp, s);
         }
     }
-    ck(cudaMemcpyAsync(Lb, Araw, h->sum_sq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if constexpr (f64)
+        ck(cudaMemcpyAsync(Lb, Araw, h->sum_sq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else
+        launch_convert<double, float>(Araw, Lb, h->sum_sq, s);
 
     // ---- (1) exact Cholesky of A_ii (local solver) and its inverse factor
     {
-        std::vector<CholDesc> cd(N);
-        std::vector<TrtriDesc> td(N);
-        std::vector<const double*> src(N);
-        std::vector<double*> dst(N);
+        std::vector<CholDescT<T>> cd(N);
+        std::vector<TrtriDescT<T>> td(N);
+        std::vector<const T*> src(N);
+        std::vector<T*> dst(N);
         std::vector<int> nn(N), ld(N);
         for (int i = 0; i < N; ++i) {
             const int ni = h->ni[i];
             cd[i] = {Lb + h->off_sq[i], ni, ni, ni, nullptr, linvA + off_la[i]};
-            td[i] = {Lb + h->off_sq[i], h->d_Y + h->off_sq[i], linvA + off_la[i], ni, ni, ni};
-            src[i] = h->d_Y + h->off_sq[i];
-            dst[i] = h->d_Yt + h->off_sq[i];
+            td[i] = {Lb + h->off_sq[i], Yl + h->off_sq[i], linvA + off_la[i], ni, ni, ni};
+            src[i] = Yl + h->off_sq[i];
+            dst[i] = Ylt + h->off_sq[i];
             nn[i] = ni;
             ld[i] = ni;
         }
@@ -734,9 +779,12 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     // in FP64, X1_i = Q_i X_i, then FP64 sweeps make the rows of X1_i exactly
     // orthogonal: rows become sigma_j v_j^T, sigma_j = row norms; rows are then
     // scaled by sigma_j^{-1/2}.
+    // eps is the machine precision of the arithmetic (Sec. 3.2): the FP32
+    // stage shifts by at least sigma_1 * 2^-23, above its own rounding.
+    if constexpr (!f64) h->eps = std::max(h->eps, (double)std::numeric_limits<float>::epsilon());
     const double eps = h->eps;
-    double* X1 = C.tnew<double>(off_x[N]);
-    {
+    T* X1 = C.tnew<T>(off_x[N]);
+    if constexpr (f64) {
         std::vector<int64_t> oq(N + 1, 0);
         for (int i = 0; i < N; ++i) oq[i + 1] = oq[i] + (int64_t)h->ni[i] * h->ni[i];
         double* Q = C.tnew<double>(oq[N]);
@@ -753,7 +801,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         std::vector<double*> sp(N);
         int maxc = 1;
         for (int i = 0; i < N; ++i) {
-            jd[i] = {X1 + off_x[i], h->ni[i], h->nt[i], h->nt[i], h->nt[i], nrm64 + h->off_om[i], nullptr};
+            jd[i] = {X1 + off_x[i], h->ni[i], h->nt[i], h->nt[i], h->nt[i], nrmT + h->off_om[i], nullptr};
             sp[i] = sig + h->off_om[i];
             maxc = std::max(maxc, h->nt[i]);
         }
@@ -768,14 +816,36 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         launch_rownorms(djd, N, dsp, delta, eps, 1, s);
     }
 
+    else {
+        // mixed form: FP32 one-sided Jacobi on the rows of X_i alone
+        launch_convert<double, float>(Xp, X1, off_x[N], s);
+        std::vector<JacobiDescT<float>> jd(N);
+        std::vector<double*> sp(N);
+        int maxc = 1;
+        for (int i = 0; i < N; ++i) {
+            jd[i] = {X1 + off_x[i], h->ni[i], h->nt[i], h->nt[i], h->nt[i], nrmT + h->off_om[i], nullptr};
+            sp[i] = sig + h->off_om[i];
+            maxc = std::max(maxc, h->nt[i]);
+        }
+        JacobiDescT<float>* djd = C.up(jd);
+        double* const* dsp = C.up(sp);
+        {
+            PScope ps(h, PK_JAC_F32);
+            run_jacobi<float>(h, jd, djd, h->max_sweeps,
+                              8.0f * std::sqrt((float)maxc) * std::numeric_limits<float>::epsilon(), sweeps, rots, 0);
+        }
+        PScope ps(h, PK_SMALL);
+        launch_rownorms<float>(djd, N, dsp, delta, eps, 1, s);
+    }
+
     // ---- (3) Abar_ii = C^T diag(1/sigma) C + sigma_1 eps I, ordered [G, D, I]
     {
-        std::vector<GemmDesc> g(N);
-        std::vector<double*> mats(N);
+        std::vector<GemmDescT<T>> g(N);
+        std::vector<T*> mats(N);
         std::vector<int> nn(N), ld(N);
         for (int i = 0; i < N; ++i) {
             const int ni = h->ni[i], nt = h->nt[i];
-            double* Xi = X1 + off_x[i];
+            T* Xi = X1 + off_x[i];
             g[i] = gd(Xi, nt, 1, Xi, nt, 0, M + off_m[i], nt, nt, nt, ni, 1.0, 0.0, 1);
             mats[i] = M + off_m[i];
             nn[i] = nt;
@@ -786,13 +856,13 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         auto b = C.up(nn);
         auto c = C.up(ld);
         PScope ps(h, PK_SMALL);
-        launch_add_diag(a, b, c, delta, N, h->max_nt, s);
+        launch_add_diag<T>(a, b, c, delta, N, h->max_nt, s);
     }
 
     // ---- (4) Schur complement of Abar_ii onto Omega_Ii: Cholesky of the
     // leading [G, D] block (pivot floor sigma_1 eps, the shift of Remark 3.2).
     {
-        std::vector<CholDesc> cd(N);
+        std::vector<CholDescT<T>> cd(N);
         for (int i = 0; i < N; ++i) {
             const int nt = h->nt[i], nR = h->nG[i] + h->nD[i];
             cd[i] = {M + off_m[i], nt, nt, nR, delta + i, linvM + off_lm[i]};
@@ -803,17 +873,17 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     // ---- (5) T = L_A^{-1} S L_A^{-T} (L_A = Cholesky factor of A_II, the
     // leading block of that of A_ii), appended identity for the rotations.
     {
-        std::vector<double*> mats(N);
+        std::vector<T*> mats(N);
         std::vector<int> nn(N), ld(N);
-        std::vector<GemmDesc> g1(N), g2(N);
-        std::vector<TrtriDesc> idd(N);
+        std::vector<GemmDescT<T>> g1(N), g2(N);
+        std::vector<TrtriDescT<T>> idd(N);
         for (int i = 0; i < N; ++i) {
             const int nIi = h->nI[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], ni = h->ni[i];
-            double* S = M + off_m[i] + (size_t)nR * nt + nR;
+            T* S = M + off_m[i] + (size_t)nR * nt + nR;
             mats[i] = S;
             nn[i] = nIi;
             ld[i] = nt;
-            const double* Y = h->d_Y + h->off_sq[i];
+            const T* Y = Yl + h->off_sq[i];
             g1[i] = gd(Y, ni, 0, S, nt, 0, Pb + off_P[i], nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
             g2[i] = gd(Pb + off_P[i], nIi, 0, Y, ni, 1, TI + off_ti[i], 2 * nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
             idd[i] = {nullptr, TI + off_ti[i] + nIi, nullptr, nIi, 0, 2 * nIi};
@@ -823,24 +893,24 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             auto b = C.up(nn);
             auto c = C.up(ld);
             PScope ps(h, PK_SMALL);
-            launch_mirror_lower(a, b, c, N, h->max_nt, s);
+            launch_mirror_lower<T>(a, b, c, N, h->max_nt, s);
         }
         gemm(C, g1);
         gemm(C, g2);
         auto di = C.up(idd);
         PScope ps(h, PK_SMALL);
-        launch_set_identity(di, N, h->max_nt, s);
+        launch_set_identity<T>(di, N, h->max_nt, s);
     }
 
     // ---- (6) eigenvalues mu = 1/lambda of eq. (Zi): Householder reduction of
     // each T_i to tridiagonal form and bisection with Sturm counts (absolute
     // accuracy O(eps ||T||), like a dense symmetric eigensolver).
     {
-        double* TD = C.tnew<double>(off_P[N]);
-        double* dd = C.tnew<double>(h->sum_nI);
-        double* ee = C.tnew<double>(h->sum_nI);
-        double* pp = C.tnew<double>(h->sum_nI);
-        std::vector<TridiagDesc> td(N);
+        T* TD = C.tnew<T>(off_P[N]);
+        T* dd = C.tnew<T>(h->sum_nI);
+        T* ee = C.tnew<T>(h->sum_nI);
+        T* pp = C.tnew<T>(h->sum_nI);
+        std::vector<TridiagDescT<T>> td(N);
         std::vector<double*> outp(N);
         std::vector<int> em, ej;
         em.reserve(h->sum_nI);
@@ -849,8 +919,8 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         for (int i = 0; i < N; ++i) {
             const int nIi = h->nI[i];
             if (nIi > 0)
-                ck(cudaMemcpy2DAsync(TD + off_P[i], nIi * sizeof(double), TI + off_ti[i], 2 * nIi * sizeof(double),
-                                     nIi * sizeof(double), nIi, cudaMemcpyDeviceToDevice, s));
+                ck(cudaMemcpy2DAsync(TD + off_P[i], nIi * sizeof(T), TI + off_ti[i], 2 * nIi * sizeof(T),
+                                     nIi * sizeof(T), nIi, cudaMemcpyDeviceToDevice, s));
             td[i] = {TD + off_P[i], nIi, nIi, dd + h->off_I[i], ee + h->off_I[i], pp + h->off_I[i]};
             outp[i] = mu + h->off_I[i];
             for (int j = 0; j < nIi; ++j) {
@@ -859,18 +929,18 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             }
             maxn = std::max(maxn, nIi);
         }
-        const TridiagDesc* dtd = C.up(td);
+        const TridiagDescT<T>* dtd = C.up(td);
         auto dem = C.up(em);
         auto dej = C.up(ej);
         auto dout = C.up(outp);
         {
             double fl = 0.0;
             for (int i = 0; i < N; ++i) fl += 8.0 / 3.0 * std::pow((double)h->nI[i], 3);
-            PScope ps(h, PK_TRIDIAG, fl);
-            launch_tridiag(dtd, N, maxn, s);
+            PScope ps(h, pk<T>(PK_TRIDIAG, PK_TRIDIAG_F32), fl);
+            launch_tridiag<T>(dtd, N, maxn, s);
         }
-        PScope ps(h, PK_BISECT);
-        launch_bisect(dtd, N, dem, dej, (int64_t)em.size(), dout, s);
+        PScope ps(h, pk<T>(PK_BISECT, PK_BISECT_F32));
+        launch_bisect<T>(dtd, N, dem, dej, (int64_t)em.size(), dout, s);
     }
 
     // ---- (7) selection lambda > 1/tau on the host
@@ -927,6 +997,11 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     // right half and mu_j as the left-half row norms; the p_i rows with the
     // smallest mu give u = L_A^{-T} w.
     h->d_Zt = dnew<double>(h, h->sum_zt);
+    T* ZtT = nullptr;
+    if constexpr (f64)
+        ZtT = h->d_Zt;
+    else
+        ZtT = C.tnew<T>(h->sum_zt);
     if (h->nC > 0) {
         std::vector<int64_t> ysrc, ydst;
         std::vector<int32_t> ylen;
@@ -943,31 +1018,30 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             auto b = C.up(ydst);
             auto c = C.up(ylen);
             PScope ps(h, PK_SMALL);
-            launch_gather_rows(h->d_Y, a, h->d_Zt, b, c, (int64_t)ysrc.size(), s);
+            launch_gather_rows<T>(Yl, a, ZtT, b, c, (int64_t)ysrc.size(), s);
         }
         if (!partial.empty()) {
             const int np = (int)partial.size();
-            std::vector<JacobiDesc> jd(np);
+            std::vector<JacobiDescT<T>> jd(np);
             std::vector<double*> mp(np);
             double* mu_j = C.tnew<double>(h->sum_nI);
             int maxc = 1;
             for (int q = 0; q < np; ++q) {
                 const int i = partial[q], nIi = h->nI[i];
-                jd[q] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrm64 + h->off_om[i], nullptr};
+                jd[q] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrmT + h->off_om[i], nullptr};
                 mp[q] = mu_j + h->off_I[i];
                 maxc = std::max(maxc, nIi);
             }
-            JacobiDesc* djd = C.up(jd);
+            JacobiDescT<T>* djd = C.up(jd);
             double* const* dmp = C.up(mp);
             {
                 PScope ps(h, PK_JAC_EIG);
-                run_jacobi<double>(h, jd, djd, h->max_sweeps,
-                                   2.0 * std::sqrt((double)maxc) * std::numeric_limits<double>::epsilon(), sweeps + N,
-                                   rots + N, 1);
+                const T tol = (f64 ? T(2) : T(8)) * std::sqrt((T)maxc) * std::numeric_limits<T>::epsilon();
+                run_jacobi<T>(h, jd, djd, h->max_sweeps, tol, sweeps + N, rots + N, f64 ? 1 : 0);
             }
             {
                 PScope ps(h, PK_SMALL);
-                launch_rownorms(djd, np, dmp, nullptr, 0.0, 0, s);
+                launch_rownorms<T>(djd, np, dmp, (T*)nullptr, 0.0, 0, s);
             }
             std::vector<double> muj(h->sum_nI);
             ck(cudaMemcpyAsync(muj.data(), mu_j, h->sum_nI * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -996,20 +1070,22 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                     wlen.push_back(nIi);
                 }
             }
-            double* Wsel = C.tnew<double>(h->sum_zt);
+            T* Wsel = C.tnew<T>(h->sum_zt);
             {
                 auto a = C.up(wsrc);
                 auto b = C.up(wdst);
                 auto c = C.up(wlen);
                 PScope ps(h, PK_SMALL);
-                launch_gather_rows(TI, a, Wsel, b, c, (int64_t)wsrc.size(), s);
+                launch_gather_rows<T>(TI, a, Wsel, b, c, (int64_t)wsrc.size(), s);
             }
-            std::vector<GemmDesc> g;
+            std::vector<GemmDescT<T>> g;
             for (int i : partial)
-                g.push_back(gd(Wsel + h->off_zt[i], h->nI[i], 0, h->d_Y + h->off_sq[i], h->ni[i], 0,
-                               h->d_Zt + h->off_zt[i], h->nI[i], h->p[i], h->nI[i], h->nI[i], 1.0, 0.0, 0));
+                g.push_back(gd<T>(Wsel + h->off_zt[i], h->nI[i], 0, Yl + h->off_sq[i], h->ni[i], 0,
+                                  ZtT + h->off_zt[i], h->nI[i], h->p[i], h->nI[i], h->nI[i], 1.0, 0.0, 0));
             gemm(C, g);
         }
+        // the coarse part is FP64: Z_i rounded to FP64 once, used for E and the apply
+        if constexpr (!f64) launch_convert<float, double>(ZtT, h->d_Zt, h->sum_zt, s);
     }
 
     // ---- (9) coarse matrix E = R_0 A R_0^T (Eq. (two_level_schwarz)), its
@@ -1117,7 +1193,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                 h->env_colend[h->coff[i] + k] = (int)h->coff[highi[i] + 1];
             }
         h->d_YEt = dnew<double>(h, (size_t)nC * nC);
-        chol_batched(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}}, {&h->env_row});
+        chol_batched<double>(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}}, {&h->env_row});
         // Inverses of the diagonal blocks of L_E (block size cSB): the coarse
         // solve is then a blocked forward / backward substitution with L_E and
         // L_E^T (row GEMVs), with no inverse of the whole factor.
@@ -1142,7 +1218,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         }
         trtri_batched(C, tj);
         transpose_batched(C, ts, tdst, tn, tl, tl);
-        transpose_batched(C, {E}, {h->d_YEt}, {(int)nC}, {(int)nC}, {(int)nC});
+        transpose_batched<double>(C, {E}, {h->d_YEt}, {(int)nC}, {(int)nC}, {(int)nC});
     } else {
         h->d_zt_off = C.up(std::vector<int64_t>(h->off_zt.begin(), h->off_zt.end() - 1), true);
         h->d_nI = C.up(std::vector<int32_t>(h->nI.begin(), h->nI.end()), true);
@@ -1152,10 +1228,20 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
 
     // ---- (10) apply plan
     {
-        std::vector<GemvDesc> l1(N), l2(N), cr(N);
+        std::vector<GemvDescT<T>> l1(N), l2(N);
+        std::vector<GemvDesc> cr(N);
         h->d_rloc = dnew<double>(h, h->sum_ni);
-        h->d_tloc = dnew<double>(h, h->sum_ni);
-        h->d_yloc = dnew<double>(h, h->sum_ni);
+        T* rlocT = f64 ? (T*)h->d_rloc : dnew<T>(h, h->sum_ni);
+        T* tlocT = dnew<T>(h, h->sum_ni);
+        T* ylocT = dnew<T>(h, h->sum_ni);
+        if constexpr (f64) {
+            h->d_tloc = tlocT;
+            h->d_yloc = ylocT;
+        } else {
+            h->d_rloc32 = rlocT;
+            h->d_tloc32 = tlocT;
+            h->d_yloc32 = ylocT;
+        }
         h->d_c = dnew<double>(h, nC);
         h->d_ct = dnew<double>(h, nC);
         h->d_e = dnew<double>(h, nC);
@@ -1164,8 +1250,8 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         rl.reserve(h->sum_ni);
         for (int i = 0; i < N; ++i) {
             const int ni = h->ni[i];
-            l1[i] = {h->d_Y + h->off_sq[i], ni, ni, ni, 1, h->d_rloc + h->off_om[i], h->d_tloc + h->off_om[i]};
-            l2[i] = {h->d_Yt + h->off_sq[i], ni, ni, ni, 2, h->d_tloc + h->off_om[i], h->d_yloc + h->off_om[i]};
+            l1[i] = {Yl + h->off_sq[i], ni, ni, ni, 1, rlocT + h->off_om[i], tlocT + h->off_om[i]};
+            l2[i] = {Ylt + h->off_sq[i], ni, ni, ni, 2, tlocT + h->off_om[i], ylocT + h->off_om[i]};
             cr[i] = {h->d_Zt + h->off_zt[i], h->p[i], h->nI[i], h->nI[i], 0, h->d_rloc + h->off_om[i],
                      h->d_c + h->coff[i]};
             for (int a = 0; a < ni; ++a) {
@@ -1177,8 +1263,13 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                 rlc.push_back(k);
             }
         }
-        h->d_gv_l1 = C.up(l1, true);
-        h->d_gv_l2 = C.up(l2, true);
+        if constexpr (f64) {
+            h->d_gv_l1 = C.up(l1, true);
+            h->d_gv_l2 = C.up(l2, true);
+        } else {
+            h->d_gv_l1_32 = C.up(l1, true);
+            h->d_gv_l2_32 = C.up(l2, true);
+        }
         h->d_gv_c = C.up(cr, true);
         h->d_rd_loc = C.up(rd, true);
         h->d_rl_loc = C.up(rl, true);
@@ -1273,29 +1364,51 @@ void apply_one(amdd_handle* h, const double* r, double* z) {
         PScope ps(h, PK_GATHER_SCATTER, 0.0, 20.0 * h->sum_ni);
         launch_gather_vec(h->d_omega, h->sum_ni, r, h->d_rloc, s);
     }
-    {
-        PScope ps(h, PK_GEMV, tri, 8.0 * tri / 2 + 24.0 * h->sum_ni);
-        launch_gemv_rows(h->d_gv_l1, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
-    }
-    {
-        PScope ps(h, PK_GEMV, tri, 8.0 * tri / 2 + 24.0 * h->sum_ni);
-        launch_gemv_rows(h->d_gv_l2, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+    if (h->precision == 0) {
+        {
+            PScope ps(h, PK_GEMV, tri, 8.0 * tri / 2 + 24.0 * h->sum_ni);
+            launch_gemv_rows<double>(h->d_gv_l1, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+        }
+        {
+            PScope ps(h, PK_GEMV, tri, 8.0 * tri / 2 + 24.0 * h->sum_ni);
+            launch_gemv_rows<double>(h->d_gv_l2, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+        }
+    } else {
+        // mixed form: local solves in FP32 (FP32 factors, FP32 accumulation)
+        {
+            PScope ps(h, PK_GATHER_SCATTER, 0.0, 12.0 * h->sum_ni);
+            launch_convert<double, float>(h->d_rloc, h->d_rloc32, h->sum_ni, s);
+        }
+        {
+            PScope ps(h, PK_GEMV_F32, tri, 4.0 * tri / 2 + 12.0 * h->sum_ni);
+            launch_gemv_rows<float>(h->d_gv_l1_32, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+        }
+        {
+            PScope ps(h, PK_GEMV_F32, tri, 4.0 * tri / 2 + 12.0 * h->sum_ni);
+            launch_gemv_rows<float>(h->d_gv_l2_32, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+        }
     }
     if (h->nC > 0) {
         const double zt = (double)h->sum_zt;
         {
             PScope ps(h, PK_GEMV, 2.0 * zt, 8.0 * zt + 8.0 * h->sum_ni + 16.0 * h->nC);
-            launch_gemv_rows(h->d_gv_c, h->d_rd_c, h->d_rl_c, h->nC, s);
+            launch_gemv_rows<double>(h->d_gv_c, h->d_rd_c, h->d_rl_c, h->nC, s);
         }
         for (size_t j = 0; j < h->csteps.size(); ++j) {
             const auto& st = h->csteps[j];
             PScope ps(h, PK_GEMV, st.flops, st.bytes);
-            launch_gemv_rows(h->d_gv_e1 + j, h->d_rd_e, h->d_rl_e, st.rows, s);
+            launch_gemv_rows<double>(h->d_gv_e1 + j, h->d_rd_e, h->d_rl_e, st.rows, s);
         }
     }
     PScope ps(h, PK_GATHER_SCATTER, 2.0 * h->sum_zt, 8.0 * h->sum_zt + 12.0 * h->sum_ni + 24.0 * h->n);
-    launch_scatter_prolong(h->n, h->d_order_g, h->d_own_sub, h->d_own_a, h->d_sc_ptr, h->d_sc_idx, h->d_yloc,
-                           h->d_zt_off, h->d_nI, h->d_p, h->d_coff, h->d_Zt, h->nC > 0 ? h->d_e : nullptr, z, s);
+    if (h->precision == 0)
+        launch_scatter_prolong<double>(h->n, h->d_order_g, h->d_own_sub, h->d_own_a, h->d_sc_ptr, h->d_sc_idx,
+                                       h->d_yloc, h->d_zt_off, h->d_nI, h->d_p, h->d_coff, h->d_Zt,
+                                       h->nC > 0 ? h->d_e : nullptr, z, s);
+    else
+        launch_scatter_prolong<float>(h->n, h->d_order_g, h->d_own_sub, h->d_own_a, h->d_sc_ptr, h->d_sc_idx,
+                                      h->d_yloc32, h->d_zt_off, h->d_nI, h->d_p, h->d_coff, h->d_Zt,
+                                      h->nC > 0 ? h->d_e : nullptr, z, s);
 }
 
 // Launch wrappers of the PCG loop with their profile accounting.
@@ -1392,9 +1505,10 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
     amdd_opts_default(&o);
     if (opts) {
         o = *opts;
-        if (!(o.eps > 0.0) || o.max_sweeps < 1) return AMDD_ERR_INVALID;
-        for (int k = 0; k < 6; ++k)
+        if (!(o.eps > 0.0) || o.max_sweeps < 1 || (o.precision != 0 && o.precision != 1)) return AMDD_ERR_INVALID;
+        for (int k = 0; k < 4; ++k)
             if (o.reserved[k] != 0) return AMDD_ERR_INVALID;
+        if (o.profile_classes >> PK_COUNT) return AMDD_ERR_INVALID;
     }
     const auto t0 = std::chrono::steady_clock::now();
     amdd_handle* h = nullptr;
@@ -1409,7 +1523,12 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         h->eps = o.eps;
         h->max_sweeps = o.max_sweeps;
         h->prof.on = o.profile != 0;
-        do_setup(h, A, part);
+        h->prof.mask = o.profile_classes ? o.profile_classes : ~0u;
+        h->precision = o.precision;
+        if (o.precision == 0)
+            do_setup<double>(h, A, part);
+        else
+            do_setup<float>(h, A, part);
         ck(cudaStreamSynchronize(h->s));
     } catch (...) {
         const amdd_status st = guard_exc();
@@ -1430,6 +1549,78 @@ amdd_status amdd_apply(amdd_handle* h, const double* r, double* z, int32_t nrhs)
         for (int k = 0; k < nrhs; ++k) apply_one(h, r + (size_t)k * h->n, z + (size_t)k * h->n);
         ck(cudaGetLastError());
         ck(cudaStreamSynchronize(h->s));
+    } catch (...) {
+        return guard_exc();
+    }
+    return AMDD_OK;
+}
+
+namespace {
+
+// Number of eigenvalues below x of the symmetric tridiagonal (d, e) by the
+// signs of the LDL^T pivots (Sturm sequence), with a tiny pivot replaced by a
+// signed floor so the recurrence never divides by zero.
+int tri_count_below(const std::vector<double>& d, const std::vector<double>& e, double x, double floor) {
+    int c = 0;
+    double q = d[0] - x;
+    if (std::fabs(q) < floor) q = -floor;
+    if (q < 0.0) ++c;
+    for (size_t j = 1; j < d.size(); ++j) {
+        q = d[j] - x - e[j - 1] * e[j - 1] / q;
+        if (std::fabs(q) < floor) q = -floor;
+        if (q < 0.0) ++c;
+    }
+    return c;
+}
+
+// Smallest and largest eigenvalue of the Lanczos tridiagonal of PCG (the
+// CG-Lanczos relation): T_11 = 1/alpha_1, T_jj = 1/alpha_j +
+// beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j; bisection inside
+// the Gershgorin interval to a relative width of 1e-15.
+void lanczos_extremes(const std::vector<double>& al, const std::vector<double>& be, double* lo, double* hi) {
+    const size_t k = al.size();
+    if (k == 0) {
+        *lo = *hi = std::numeric_limits<double>::quiet_NaN();
+        return;
+    }
+    std::vector<double> d(k), e(k > 1 ? k - 1 : 1, 0.0);
+    for (size_t j = 0; j < k; ++j) d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    for (size_t j = 0; j + 1 < k; ++j) e[j] = std::sqrt(std::max(be[j], 0.0)) / al[j];
+    double gl = d[0], gu = d[0];
+    for (size_t j = 0; j < k; ++j) {
+        const double r = (j > 0 ? std::fabs(e[j - 1]) : 0.0) + (j + 1 < k ? std::fabs(e[j]) : 0.0);
+        gl = std::min(gl, d[j] - r);
+        gu = std::max(gu, d[j] + r);
+    }
+    const double scale = std::max(std::fabs(gl), std::fabs(gu));
+    const double floor = 1e-300 * std::max(1.0, scale);
+    auto kth = [&](int target) {  // smallest x with count_below(x) > target
+        double a = gl, b = gu;
+        for (int it = 0; it < 200 && b - a > 1e-15 * std::max(std::fabs(a), std::fabs(b)); ++it) {
+            const double m = 0.5 * (a + b);
+            if (tri_count_below(d, e, m, floor) > target)
+                b = m;
+            else
+                a = m;
+        }
+        return 0.5 * (a + b);
+    };
+    *lo = kth(0);
+    *hi = kth((int)k - 1);
+}
+
+}  // namespace
+
+amdd_status amdd_lanczos_extremes(const double* alpha, const double* beta, int32_t k, double* lo, double* hi) {
+    if (k < 0 || !lo || !hi || (k > 0 && !alpha) || (k > 1 && !beta)) return AMDD_ERR_INVALID;
+    try {
+        std::vector<double> al(alpha, alpha + k), be;
+        if (k > 1) be.assign(beta, beta + (k - 1));
+        for (int j = 0; j < k; ++j)
+            if (!(al[j] > 0.0)) return AMDD_ERR_INVALID;
+        for (int j = 0; j + 1 < k; ++j)
+            if (!(be[j] >= 0.0)) return AMDD_ERR_INVALID;
+        lanczos_extremes(al, be, lo, hi);
     } catch (...) {
         return guard_exc();
     }
@@ -1462,6 +1653,7 @@ amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t n
             ck(cudaMemcpyAsync(&sc, h->d_sc, sizeof(PcgScal), cudaMemcpyDeviceToHost, s));
             ck(cudaStreamSynchronize(s));
             int its = 0;
+            std::vector<double> al, be;  // PCG step lengths and ratios (condition estimate)
             bool conv = sc.bb == 0.0 || sc.conv;
             if (sc.bb == 0.0) {
                 ck(cudaMemsetAsync(xk, 0, n * sizeof(double), s));
@@ -1484,6 +1676,10 @@ amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t n
                     }
                     ck(cudaMemcpyAsync(&sc, h->d_sc, sizeof(PcgScal), cudaMemcpyDeviceToHost, s));
                     ck(cudaStreamSynchronize(s));
+                    if (k == 0) {
+                        if (its > 1) be.push_back(sc.beta);
+                        al.push_back(sc.alpha);
+                    }
                     if (sc.conv) {
                         conv = true;
                         break;
@@ -1509,6 +1705,8 @@ amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t n
                 stats->converged = conv ? 1 : 0;
                 stats->rel_residual = sc.bb > 0.0 ? std::sqrt(sc.rr / sc.bb) : 0.0;
                 stats->true_rel_residual = sc.bb > 0.0 ? std::sqrt(st.rr / sc.bb) : 0.0;
+                lanczos_extremes(al, be, &stats->ritz_min, &stats->ritz_max);
+                stats->cond_est = stats->ritz_max / stats->ritz_min;
             }
         }
         ck(cudaGetLastError());
@@ -1540,6 +1738,8 @@ amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
     info->rotations_eig = h->rot_eig;
     info->sweeps_svd32 = h->sweeps_svd32;
     info->sweeps_eig32 = h->sweeps_eig32;
+    info->precision = h->precision;
+    info->eps = h->eps;
     return AMDD_OK;
 }
 

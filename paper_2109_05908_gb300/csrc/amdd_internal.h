@@ -30,39 +30,45 @@ constexpr int JAC_MAX_PAIRS = 64;  // largest sub-round of the shared-memory blo
 // kfrom_row = 1: the k loop starts at the tile's first row (for products whose
 // A operand is zero for kk < r, e.g. a lower-triangular Y read transposed).
 // beta == 0 means C is not read.
-struct GemmDesc {
-    const double* A;
-    const double* B;
-    double* C;
+template <typename T>
+struct GemmDescT {
+    const T* A;
+    const T* B;
+    T* C;
     int m, n, k;
     int lda, ldb, ldc;
     int ta, tb, lower, kfrom_row;
-    double alpha, beta;
+    T alpha, beta;
 };
+using GemmDesc = GemmDescT<double>;
 
 struct TileRef {
     int desc, tm, tn;
 };
 
 // Blocked Cholesky / inverse-factor descriptors (one per matrix).
-struct CholDesc {
-    double* A;            // n x n, lower triangle used and overwritten with L
+template <typename T>
+struct CholDescT {
+    T* A;            // n x n, lower triangle used and overwritten with L
     int n, ld;
-    int stop;             // factor columns [0, stop); stop < n leaves the Schur complement
-    const double* clamp;  // per-matrix pivot floor (pivots below are raised to it); NULL = SPD check
-    double* Linv;         // ceil(stop/NB) * NB*NB doubles: inverses of the diagonal blocks
+    int stop;        // factor columns [0, stop); stop < n leaves the Schur complement
+    const T* clamp;  // per-matrix pivot floor (pivots below are raised to it); NULL = SPD check
+    T* Linv;         // ceil(stop/NB) * NB*NB entries: inverses of the diagonal blocks
 };
+using CholDesc = CholDescT<double>;
 
 struct PanelRef {
     int desc, rt;  // row tile index (64 rows) below the diagonal block
 };
 
-struct TrtriDesc {
-    const double* L;      // n x n lower Cholesky factor (ld)
-    double* Y;            // n x n output L^{-1} (ldy), lower triangular
-    const double* Linv;   // diagonal-block inverses from the Cholesky
+template <typename T>
+struct TrtriDescT {
+    const T* L;     // n x n lower Cholesky factor (ld)
+    T* Y;           // n x n output L^{-1} (ldy), lower triangular
+    const T* Linv;  // diagonal-block inverses from the Cholesky
     int n, ld, ldy;
 };
+using TrtriDesc = TrtriDescT<double>;
 
 struct ChunkRef {
     int desc, ct;  // column chunk (64 columns)
@@ -88,36 +94,42 @@ struct CvtDesc {
 };
 
 // Symmetric tridiagonal reduction and bisection (eigenvalues only).
-struct TridiagDesc {
-    double* A;  // n x n symmetric, full storage (ld); destroyed
+template <typename T>
+struct TridiagDescT {
+    T* A;  // n x n symmetric, full storage (ld); destroyed
     int n, ld;
-    double* d;  // n
-    double* e;  // n (e[i] = T[i][i-1], e[0] = 0)
-    double* p;  // n scratch
+    T* d;  // n
+    T* e;  // n (e[i] = T[i][i-1], e[0] = 0)
+    T* p;  // n scratch
 };
-void launch_tridiag(const TridiagDesc* d, int nmat, int maxn, cudaStream_t s);
-void launch_bisect(const TridiagDesc* d, int nmat, const int* eig_mat, const int* eig_idx, int64_t total,
-                   double* const* out, cudaStream_t s);
+using TridiagDesc = TridiagDescT<double>;
 
 // Row GEMV descriptors: y[row] = (b ? b[row] : 0) + alpha * sum_{c in [c0(row), c1(row))} M[row][c] x[c].
 // mode 0: full row [0, ncols); mode 1: lower [0, row]; mode 2: upper [row, ncols).
-struct GemvDesc {
-    const double* M;
+template <typename T>
+struct GemvDescT {
+    const T* M;
     int rows, ncols, ld, mode;
-    const double* x;
-    double* y;
-    const double* b = nullptr;  // y[row] = b[row] + alpha * (M x)[row] when b is given
-    double alpha = 1.0;
+    const T* x;
+    T* y;
+    const T* b = nullptr;  // y[row] = b[row] + alpha * (M x)[row] when b is given
+    T alpha = T(1);
     const int* cstart = nullptr;  // optional per-row first column (absolute, minus coff)
     const int* cend = nullptr;    // optional per-row end column (absolute, minus coff)
     int coff = 0;
 };
+using GemvDesc = GemvDescT<double>;
 
-void launch_gemm(const GemmDesc* d_descs, const TileRef* d_tiles, int ntiles, cudaStream_t s);
-void launch_chol_diag(const CholDesc* d, int nmat, int k0, int* err, cudaStream_t s);
-void launch_chol_panel(const CholDesc* d, const PanelRef* tiles, int ntiles, int k0, cudaStream_t s);
-void launch_trtri_diag(const TrtriDesc* d, const ChunkRef* tiles, int ntiles, int k0, cudaStream_t s);
-void launch_set_identity(const TrtriDesc* d, int nmat, int maxn, cudaStream_t s);
+template <typename T>
+void launch_gemm(const GemmDescT<T>* d_descs, const TileRef* d_tiles, int ntiles, cudaStream_t s);
+template <typename T>
+void launch_chol_diag(const CholDescT<T>* d, int nmat, int k0, int* err, cudaStream_t s);
+template <typename T>
+void launch_chol_panel(const CholDescT<T>* d, const PanelRef* tiles, int ntiles, int k0, cudaStream_t s);
+template <typename T>
+void launch_trtri_diag(const TrtriDescT<T>* d, const ChunkRef* tiles, int ntiles, int k0, cudaStream_t s);
+template <typename T>
+void launch_set_identity(const TrtriDescT<T>* d, int nmat, int maxn, cudaStream_t s);
 template <typename T>
 void launch_jacobi_t(const JacobiDescT<T>* d, int nmat, int max_sweeps, T tol, int* sweeps, unsigned long long* rots,
                      int* err, int report_noconv, cudaStream_t s);
@@ -133,18 +145,29 @@ template <typename T>
 void launch_row_maxnorm2(const JacobiDescT<T>* d, int nmat, T eps, T* out, cudaStream_t s);
 void launch_to_f32_with_identity(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s);
 void launch_extract_q(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s);
-// sigma[j] = ||row j|| over ncols_dot; delta[mat] = eps * max_j sigma[j]; optionally
-// scale row j by 1/sqrt(sigma[j]).
-void launch_rownorms(const JacobiDesc* d, int nmat, double* const* sigma_ptrs, double* delta, double eps,
+// sigma[j] = ||row j|| over ncols_dot (as double); delta[mat] = eps * max_j sigma[j];
+// optionally scale row j by 1/sqrt(sigma[j]).
+template <typename T>
+void launch_rownorms(const JacobiDescT<T>* d, int nmat, double* const* sigma_ptrs, T* delta, double eps,
                      int scale_rows, cudaStream_t s);
-void launch_add_diag(double* const* mats, const int* n, const int* ld, const double* delta, int nmat,
-                     int maxn, cudaStream_t s);
-void launch_mirror_lower(double* const* mats, const int* n, const int* ld, int nmat, int maxn,
-                         cudaStream_t s);
-void launch_transpose(const double* const* src, double* const* dst, const int* n, const int* lds,
-                      const int* ldd, int nmat, int maxn, cudaStream_t s);
-void launch_gemv_rows(const GemvDesc* d, const int* row_desc, const int* row_local, int64_t nrows,
+template <typename T>
+void launch_add_diag(T* const* mats, const int* n, const int* ld, const T* delta, int nmat, int maxn, cudaStream_t s);
+template <typename T>
+void launch_mirror_lower(T* const* mats, const int* n, const int* ld, int nmat, int maxn, cudaStream_t s);
+template <typename T>
+void launch_transpose(const T* const* src, T* const* dst, const int* n, const int* lds, const int* ldd, int nmat,
+                      int maxn, cudaStream_t s);
+template <typename T>
+void launch_gemv_rows(const GemvDescT<T>* d, const int* row_desc, const int* row_local, int64_t nrows,
                       cudaStream_t s);
+template <typename T>
+void launch_tridiag(const TridiagDescT<T>* d, int nmat, int maxn, cudaStream_t s);
+template <typename T>
+void launch_bisect(const TridiagDescT<T>* d, int nmat, const int* eig_mat, const int* eig_idx, int64_t total,
+                   double* const* out, cudaStream_t s);
+// dst[i] = (To)src[i]
+template <typename Ti, typename To>
+void launch_convert(const Ti* src, To* dst, int64_t n, cudaStream_t s);
 
 // ---------------------------------------------------------------- sparse / vectors
 void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
@@ -152,10 +175,12 @@ void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
 void launch_gather_values(const int64_t* src, const int64_t* dst, int64_t cnt, const double* val, double* out,
                           cudaStream_t s);
 void launch_gather_vec(const int32_t* idx, int64_t cnt, const double* x, double* out, cudaStream_t s);
-void launch_gather_rows(const double* src, const int64_t* src_off, double* dst, const int64_t* dst_off,
-                        const int32_t* len, int64_t nrows, cudaStream_t s);
+template <typename T>
+void launch_gather_rows(const T* src, const int64_t* src_off, T* dst, const int64_t* dst_off, const int32_t* len,
+                        int64_t nrows, cudaStream_t s);
+template <typename TY>
 void launch_scatter_prolong(int64_t n, const int32_t* order_g, const int32_t* own_sub, const int32_t* own_a,
-                            const int64_t* sc_ptr, const int32_t* sc_idx, const double* yloc,
+                            const int64_t* sc_ptr, const int32_t* sc_idx, const TY* yloc,
                             const int64_t* zt_off, const int32_t* nI, const int32_t* p, const int64_t* coff,
                             const double* Zt, const double* e, double* z, cudaStream_t s);
 struct EPairRef {

@@ -1,4 +1,5 @@
-// Batched dense FP64 kernels for the subdomain blocks of the setup:
+// Batched dense kernels (FP64, and FP32 for the mixed-precision form) for the
+// subdomain blocks of the setup:
 // tiled GEMM, blocked Cholesky (full or stopped early to leave a Schur
 // complement), blocked inverse of the Cholesky factor, one-sided Jacobi row
 // orthogonalisation (SVD of X_i, Sec. 3.2, and the symmetric eigensolve of
@@ -12,27 +13,31 @@ namespace cg = cooperative_groups;
 
 namespace amdd {
 
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+
 // ------------------------------------------------------------------ GEMM
 // 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread, k
-// staged through shared memory 16 at a time.  FP64 FMA throughout.
+// staged through shared memory 16 at a time, FMA in the element type.
 constexpr int GK = 16;
 
-__global__ void __launch_bounds__(256) gemm_tiles_kernel(const GemmDesc* __restrict__ descs,
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_tiles_kernel(const GemmDescT<T>* __restrict__ descs,
                                                           const TileRef* __restrict__ tiles, int ntiles) {
     const int t = blockIdx.x;
     if (t >= ntiles) return;
     const TileRef tr = tiles[t];
-    const GemmDesc d = descs[tr.desc];
-    __shared__ double As[GK][GEMM_T + 1];
-    __shared__ double Bs[GK][GEMM_T + 1];
+    const GemmDescT<T> d = descs[tr.desc];
+    __shared__ T As[GK][GEMM_T + 1];
+    __shared__ T Bs[GK][GEMM_T + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int row0 = tr.tm * GEMM_T, col0 = tr.tn * GEMM_T;
-    double acc[4][4];
+    T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
     int kbeg = 0;
     if (d.kfrom_row) kbeg = (row0 / GK) * GK;
     for (int k0 = kbeg; k0 < d.k; k0 += GK) {
@@ -40,7 +45,7 @@ __global__ void __launch_bounds__(256) gemm_tiles_kernel(const GemmDesc* __restr
             int r, kk;
             if (!d.ta) { r = e / GK; kk = e % GK; } else { kk = e / GEMM_T; r = e % GEMM_T; }
             const int gr = row0 + r, gk = k0 + kk;
-            double v = 0.0;
+            T v = T(0);
             if (gr < d.m && gk < d.k)
                 v = d.ta ? d.A[(size_t)gk * d.lda + gr] : d.A[(size_t)gr * d.lda + gk];
             As[kk][r] = v;
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(256) gemm_tiles_kernel(const GemmDesc* __restr
             int c, kk;
             if (!d.tb) { kk = e / GEMM_T; c = e % GEMM_T; } else { c = e / GK; kk = e % GK; }
             const int gc = col0 + c, gk = k0 + kk;
-            double v = 0.0;
+            T v = T(0);
             if (gc < d.n && gk < d.k)
                 v = d.tb ? d.B[(size_t)gc * d.ldb + gk] : d.B[(size_t)gk * d.ldb + gc];
             Bs[kk][c] = v;
@@ -57,7 +62,7 @@ __global__ void __launch_bounds__(256) gemm_tiles_kernel(const GemmDesc* __restr
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            double a[4], b[4];
+            T a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -77,16 +82,19 @@ __global__ void __launch_bounds__(256) gemm_tiles_kernel(const GemmDesc* __restr
         for (int j = 0; j < 4; ++j) {
             const int c = col0 + tx + 16 * j;
             if (c >= d.n || (d.lower && c > r)) continue;
-            double* cp = d.C + (size_t)r * d.ldc + c;
-            const double v = d.alpha * acc[i][j];
-            *cp = (d.beta != 0.0) ? fma(d.beta, *cp, v) : v;
+            T* cp = d.C + (size_t)r * d.ldc + c;
+            const T v = d.alpha * acc[i][j];
+            *cp = (d.beta != T(0)) ? fma(d.beta, *cp, v) : v;
         }
     }
 }
 
-void launch_gemm(const GemmDesc* d_descs, const TileRef* d_tiles, int ntiles, cudaStream_t s) {
-    if (ntiles > 0) gemm_tiles_kernel<<<ntiles, 256, 0, s>>>(d_descs, d_tiles, ntiles);
+template <typename T>
+void launch_gemm(const GemmDescT<T>* d_descs, const TileRef* d_tiles, int ntiles, cudaStream_t s) {
+    if (ntiles > 0) gemm_tiles_kernel<T><<<ntiles, 256, 0, s>>>(d_descs, d_tiles, ntiles);
 }
+template void launch_gemm<float>(const GemmDescT<float>*, const TileRef*, int, cudaStream_t);
+template void launch_gemm<double>(const GemmDescT<double>*, const TileRef*, int, cudaStream_t);
 
 // ------------------------------------------------------------------ Cholesky
 // Factor the NB x NB diagonal block [k0, k0+kb) of each matrix in shared
@@ -95,34 +103,35 @@ void launch_gemm(const GemmDesc* d_descs, const TileRef* d_tiles, int ntiles, cu
 // factor.  With a pivot floor (clamp) a pivot below it is raised to it;
 // without, a pivot <= 0 (or NaN) latches DERR_NOT_SPD and is replaced by 1 so
 // the factorisation finishes with finite numbers.
-__global__ void __launch_bounds__(256) chol_diag_kernel(const CholDesc* __restrict__ descs, int k0,
+template <typename T>
+__global__ void __launch_bounds__(256) chol_diag_kernel(const CholDescT<T>* __restrict__ descs, int k0,
                                                          int* __restrict__ err) {
-    const CholDesc d = descs[blockIdx.x];
+    const CholDescT<T> d = descs[blockIdx.x];
     const int kend = min(k0 + CHOL_NB, d.stop);
     if (k0 >= kend) return;
     const int kb = kend - k0;
-    __shared__ double L[CHOL_NB][CHOL_NB + 1];
-    __shared__ double Li[CHOL_NB][CHOL_NB + 1];
-    __shared__ double dinv[CHOL_NB];  // 1 / L[j][j]
+    __shared__ T L[CHOL_NB][CHOL_NB + 1];
+    __shared__ T Li[CHOL_NB][CHOL_NB + 1];
+    __shared__ T dinv[CHOL_NB];  // 1 / L[j][j]
     const int tid = threadIdx.x;
     for (int e = tid; e < CHOL_NB * CHOL_NB; e += blockDim.x) {
         const int r = e / CHOL_NB, c = e % CHOL_NB;
-        L[r][c] = (r < kb && c <= r) ? d.A[(size_t)(k0 + r) * d.ld + (k0 + c)] : 0.0;
-        Li[r][c] = 0.0;
+        L[r][c] = (r < kb && c <= r) ? d.A[(size_t)(k0 + r) * d.ld + (k0 + c)] : T(0);
+        Li[r][c] = T(0);
     }
     __syncthreads();
-    const double floor_v = d.clamp ? *d.clamp : 0.0;
+    const T floor_v = d.clamp ? *d.clamp : T(0);
     for (int j = 0; j < kb; ++j) {
         if (tid == 0) {
-            double piv = L[j][j];
+            T piv = L[j][j];
             if (d.clamp) {
                 if (!(piv >= floor_v)) piv = floor_v;
-            } else if (!(piv > 0.0)) {
+            } else if (!(piv > T(0))) {
                 atomicOr(err, DERR_NOT_SPD);
-                piv = 1.0;
+                piv = T(1);
             }
             // one reciprocal square root per pivot: L_jj = piv / sqrt(piv)
-            const double r = rsqrt(piv);
+            const T r = rsqrt_t(piv);
             L[j][j] = piv * r;
             dinv[j] = r;
         }
@@ -139,108 +148,123 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const CholDesc* __restri
     if (tid < kb) {
         const int c = tid;
         for (int r = c; r < kb; ++r) {
-            double s = (r == c) ? 1.0 : 0.0;
+            T s = (r == c) ? T(1) : T(0);
             for (int k = c; k < r; ++k) s = fma(-L[r][k], Li[k][c], s);
             Li[r][c] = s * dinv[r];
         }
     }
     __syncthreads();
-    double* linv = d.Linv + (size_t)(k0 / CHOL_NB) * CHOL_NB * CHOL_NB;
+    T* linv = d.Linv + (size_t)(k0 / CHOL_NB) * CHOL_NB * CHOL_NB;
     for (int e = tid; e < CHOL_NB * CHOL_NB; e += blockDim.x) {
         const int r = e / CHOL_NB, c = e % CHOL_NB;
         if (r < kb && c <= r) d.A[(size_t)(k0 + r) * d.ld + (k0 + c)] = L[r][c];
-        linv[e] = (r < kb && c < kb) ? Li[r][c] : 0.0;
+        linv[e] = (r < kb && c < kb) ? Li[r][c] : T(0);
     }
 }
 
-void launch_chol_diag(const CholDesc* d, int nmat, int k0, int* err, cudaStream_t s) {
-    if (nmat > 0) chol_diag_kernel<<<nmat, 256, 0, s>>>(d, k0, err);
+template <typename T>
+void launch_chol_diag(const CholDescT<T>* d, int nmat, int k0, int* err, cudaStream_t s) {
+    if (nmat > 0) chol_diag_kernel<T><<<nmat, 256, 0, s>>>(d, k0, err);
 }
+template void launch_chol_diag<float>(const CholDescT<float>*, int, int, int*, cudaStream_t);
+template void launch_chol_diag<double>(const CholDescT<double>*, int, int, int*, cudaStream_t);
 
 // Panel below the diagonal block: A[r, k0:k0+kb] <- A[r, k0:k0+kb] * Linv^T
 // for 64 rows per CTA.
-__global__ void __launch_bounds__(256) chol_panel_kernel(const CholDesc* __restrict__ descs,
+template <typename T>
+__global__ void __launch_bounds__(256) chol_panel_kernel(const CholDescT<T>* __restrict__ descs,
                                                           const PanelRef* __restrict__ tiles, int k0) {
     const PanelRef t = tiles[blockIdx.x];
-    const CholDesc d = descs[t.desc];
+    const CholDescT<T> d = descs[t.desc];
     const int kend = min(k0 + CHOL_NB, d.stop);
     const int kb = kend - k0;
     const int r0 = kend + t.rt * 64;
-    __shared__ double Li[CHOL_NB][CHOL_NB + 1];
-    __shared__ double P[64][CHOL_NB + 1];
-    const double* linv = d.Linv + (size_t)(k0 / CHOL_NB) * CHOL_NB * CHOL_NB;
+    __shared__ T Li[CHOL_NB][CHOL_NB + 1];
+    __shared__ T P[64][CHOL_NB + 1];
+    const T* linv = d.Linv + (size_t)(k0 / CHOL_NB) * CHOL_NB * CHOL_NB;
     const int tid = threadIdx.x;
     for (int e = tid; e < CHOL_NB * CHOL_NB; e += 256) Li[e / CHOL_NB][e % CHOL_NB] = linv[e];
     for (int e = tid; e < 64 * CHOL_NB; e += 256) {
         const int r = e / CHOL_NB, c = e % CHOL_NB;
         const int gr = r0 + r;
-        P[r][c] = (gr < d.n && c < kb) ? d.A[(size_t)gr * d.ld + (k0 + c)] : 0.0;
+        P[r][c] = (gr < d.n && c < kb) ? d.A[(size_t)gr * d.ld + (k0 + c)] : T(0);
     }
     __syncthreads();
     for (int e = tid; e < 64 * CHOL_NB; e += 256) {
         const int r = e / CHOL_NB, c = e % CHOL_NB;
         const int gr = r0 + r;
         if (c < kb && gr < d.n) {
-            double s = 0.0;
+            T s = T(0);
             for (int k = 0; k <= c; ++k) s = fma(P[r][k], Li[c][k], s);
             d.A[(size_t)gr * d.ld + (k0 + c)] = s;
         }
     }
 }
 
-void launch_chol_panel(const CholDesc* d, const PanelRef* tiles, int ntiles, int k0, cudaStream_t s) {
-    if (ntiles > 0) chol_panel_kernel<<<ntiles, 256, 0, s>>>(d, tiles, k0);
+template <typename T>
+void launch_chol_panel(const CholDescT<T>* d, const PanelRef* tiles, int ntiles, int k0, cudaStream_t s) {
+    if (ntiles > 0) chol_panel_kernel<T><<<ntiles, 256, 0, s>>>(d, tiles, k0);
 }
+template void launch_chol_panel<float>(const CholDescT<float>*, const PanelRef*, int, int, cudaStream_t);
+template void launch_chol_panel<double>(const CholDescT<double>*, const PanelRef*, int, int, cudaStream_t);
 
 // ------------------------------------------------------------------ inverse factor
 // Y = L^{-1} by blocked forward substitution on the identity: for each
 // diagonal block k, Y[k-rows, 0:kend] <- Linv_k * Y[k-rows, 0:kend]; the
 // trailing update Y[kend:, 0:kend] -= L[kend:, k-cols] * Y[k-rows, 0:kend]
 // is a GEMM issued by the host.
-__global__ void __launch_bounds__(256) trtri_diag_kernel(const TrtriDesc* __restrict__ descs,
+template <typename T>
+__global__ void __launch_bounds__(256) trtri_diag_kernel(const TrtriDescT<T>* __restrict__ descs,
                                                           const ChunkRef* __restrict__ tiles, int k0) {
     const ChunkRef t = tiles[blockIdx.x];
-    const TrtriDesc d = descs[t.desc];
+    const TrtriDescT<T> d = descs[t.desc];
     const int kend = min(k0 + CHOL_NB, d.n);
     const int kb = kend - k0;
     const int c0 = t.ct * 64;
-    __shared__ double Li[CHOL_NB][CHOL_NB + 1];
-    __shared__ double B[CHOL_NB][64 + 1];
-    const double* linv = d.Linv + (size_t)(k0 / CHOL_NB) * CHOL_NB * CHOL_NB;
+    __shared__ T Li[CHOL_NB][CHOL_NB + 1];
+    __shared__ T B[CHOL_NB][64 + 1];
+    const T* linv = d.Linv + (size_t)(k0 / CHOL_NB) * CHOL_NB * CHOL_NB;
     const int tid = threadIdx.x;
     for (int e = tid; e < CHOL_NB * CHOL_NB; e += 256) Li[e / CHOL_NB][e % CHOL_NB] = linv[e];
     for (int e = tid; e < CHOL_NB * 64; e += 256) {
         const int r = e / 64, c = e % 64;
-        B[r][c] = (r < kb && c0 + c < kend) ? d.Y[(size_t)(k0 + r) * d.ldy + (c0 + c)] : 0.0;
+        B[r][c] = (r < kb && c0 + c < kend) ? d.Y[(size_t)(k0 + r) * d.ldy + (c0 + c)] : T(0);
     }
     __syncthreads();
     for (int e = tid; e < CHOL_NB * 64; e += 256) {
         const int r = e / 64, c = e % 64;
         if (r < kb && c0 + c < kend) {
-            double s = 0.0;
+            T s = T(0);
             for (int k = 0; k <= r; ++k) s = fma(Li[r][k], B[k][c], s);
             d.Y[(size_t)(k0 + r) * d.ldy + (c0 + c)] = s;
         }
     }
 }
 
-void launch_trtri_diag(const TrtriDesc* d, const ChunkRef* tiles, int ntiles, int k0, cudaStream_t s) {
-    if (ntiles > 0) trtri_diag_kernel<<<ntiles, 256, 0, s>>>(d, tiles, k0);
+template <typename T>
+void launch_trtri_diag(const TrtriDescT<T>* d, const ChunkRef* tiles, int ntiles, int k0, cudaStream_t s) {
+    if (ntiles > 0) trtri_diag_kernel<T><<<ntiles, 256, 0, s>>>(d, tiles, k0);
 }
+template void launch_trtri_diag<float>(const TrtriDescT<float>*, const ChunkRef*, int, int, cudaStream_t);
+template void launch_trtri_diag<double>(const TrtriDescT<double>*, const ChunkRef*, int, int, cudaStream_t);
 
-__global__ void set_identity_kernel(const TrtriDesc* __restrict__ descs) {
-    const TrtriDesc d = descs[blockIdx.y];
+template <typename T>
+__global__ void set_identity_kernel(const TrtriDescT<T>* __restrict__ descs) {
+    const TrtriDescT<T> d = descs[blockIdx.y];
     for (int r = blockIdx.x; r < d.n; r += gridDim.x) {
-        double* row = d.Y + (size_t)r * d.ldy;
-        for (int c = threadIdx.x; c < d.n; c += blockDim.x) row[c] = (r == c) ? 1.0 : 0.0;
+        T* row = d.Y + (size_t)r * d.ldy;
+        for (int c = threadIdx.x; c < d.n; c += blockDim.x) row[c] = (r == c) ? T(1) : T(0);
     }
 }
 
-void launch_set_identity(const TrtriDesc* d, int nmat, int maxn, cudaStream_t s) {
+template <typename T>
+void launch_set_identity(const TrtriDescT<T>* d, int nmat, int maxn, cudaStream_t s) {
     if (nmat <= 0 || maxn <= 0) return;
     dim3 grid(min(maxn, 1024), nmat);
-    set_identity_kernel<<<grid, 256, 0, s>>>(d);
+    set_identity_kernel<T><<<grid, 256, 0, s>>>(d);
 }
+template void launch_set_identity<float>(const TrtriDescT<float>*, int, int, cudaStream_t);
+template void launch_set_identity<double>(const TrtriDescT<double>*, int, int, cudaStream_t);
 
 // ------------------------------------------------------------------ Jacobi
 // One-sided (Hestenes) Jacobi on the rows of each matrix, in T = float or
@@ -267,8 +291,6 @@ __device__ __forceinline__ T ldcg_t(const T* p) {
 // (b - a) / (2 g), written as t = sign(b - a) 2 g / (|b - a| + sqrt((b - a)^2 +
 // 4 g^2)) so that one square root, one division and one reciprocal square
 // root suffice; cs = 1/sqrt(1 + t^2), sn = cs t.
-__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
 template <typename T>
 __device__ __forceinline__ void jac_rotation(T a, T b, T g, T& cs, T& sn, T& t) {
@@ -651,89 +673,105 @@ void launch_extract_q(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s) {
     extract_q_kernel<<<grid, 256, 0, s>>>(d);
 }
 
-// Row norms over ncols_dot, delta = eps * max norm, optional row scaling by
-// 1/sqrt(norm) over ncols_rot.  One CTA per matrix, one warp per row.
-__global__ void __launch_bounds__(256) rownorms_kernel(const JacobiDesc* __restrict__ descs,
-                                                        double* const* __restrict__ sig, double* __restrict__ delta,
+// Row norms over ncols_dot (written as double), delta = eps * max norm,
+// optional row scaling by 1/sqrt(norm) over ncols_rot.  One CTA per matrix,
+// one warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) rownorms_kernel(const JacobiDescT<T>* __restrict__ descs,
+                                                        double* const* __restrict__ sig, T* __restrict__ delta,
                                                         double eps, int scale_rows) {
-    const JacobiDesc d = descs[blockIdx.x];
+    const JacobiDescT<T> d = descs[blockIdx.x];
     double* out = sig[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ double wmax[8];
-    double mx = 0.0;
+    __shared__ T wmax[8];
+    T mx = T(0);
     for (int r = warp; r < d.rows; r += 8) {
-        double* row = d.A + (size_t)r * d.ld;
-        double s = 0.0;
+        T* row = d.A + (size_t)r * d.ld;
+        T s = T(0);
         for (int c = lane; c < d.ncols_dot; c += 32) s = fma(row[c], row[c], s);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        const double nrm = sqrt(s);
-        if (lane == 0) out[r] = nrm;
+        const T nrm = sqrt(s);
+        if (lane == 0) out[r] = (double)nrm;
         mx = fmax(mx, nrm);
-        if (scale_rows && nrm > 0.0) {
-            const double f = 1.0 / sqrt(nrm);
+        if (scale_rows && nrm > T(0)) {
+            const T f = rsqrt_t(nrm);
             for (int c = lane; c < d.ncols_rot; c += 32) row[c] *= f;
         }
     }
     if (lane == 0) wmax[warp] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = 0.0;
+        T m = T(0);
         for (int w = 0; w < 8; ++w) m = fmax(m, wmax[w]);
-        if (delta) delta[blockIdx.x] = eps * m;
+        if (delta) delta[blockIdx.x] = (T)(eps * (double)m);
     }
 }
 
-void launch_rownorms(const JacobiDesc* d, int nmat, double* const* sigma_ptrs, double* delta, double eps,
+template <typename T>
+void launch_rownorms(const JacobiDescT<T>* d, int nmat, double* const* sigma_ptrs, T* delta, double eps,
                      int scale_rows, cudaStream_t s) {
-    if (nmat > 0) rownorms_kernel<<<nmat, 256, 0, s>>>(d, sigma_ptrs, delta, eps, scale_rows);
+    if (nmat > 0) rownorms_kernel<T><<<nmat, 256, 0, s>>>(d, sigma_ptrs, delta, eps, scale_rows);
 }
+template void launch_rownorms<float>(const JacobiDescT<float>*, int, double* const*, float*, double, int,
+                                     cudaStream_t);
+template void launch_rownorms<double>(const JacobiDescT<double>*, int, double* const*, double*, double, int,
+                                      cudaStream_t);
 
-__global__ void add_diag_kernel(double* const* __restrict__ mats, const int* __restrict__ n,
-                                const int* __restrict__ ld, const double* __restrict__ delta) {
+template <typename T>
+__global__ void add_diag_kernel(T* const* __restrict__ mats, const int* __restrict__ n, const int* __restrict__ ld,
+                                const T* __restrict__ delta) {
     const int b = blockIdx.y;
-    double* M = mats[b];
-    const double dv = delta[b];
+    T* M = mats[b];
+    const T dv = delta[b];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n[b]; j += gridDim.x * blockDim.x)
         M[(size_t)j * ld[b] + j] += dv;
 }
 
-void launch_add_diag(double* const* mats, const int* n, const int* ld, const double* delta, int nmat, int maxn,
-                     cudaStream_t s) {
+template <typename T>
+void launch_add_diag(T* const* mats, const int* n, const int* ld, const T* delta, int nmat, int maxn, cudaStream_t s) {
     if (nmat <= 0 || maxn <= 0) return;
     dim3 grid((maxn + 255) / 256, nmat);
-    add_diag_kernel<<<grid, 256, 0, s>>>(mats, n, ld, delta);
+    add_diag_kernel<T><<<grid, 256, 0, s>>>(mats, n, ld, delta);
 }
+template void launch_add_diag<float>(float* const*, const int*, const int*, const float*, int, int, cudaStream_t);
+template void launch_add_diag<double>(double* const*, const int*, const int*, const double*, int, int,
+                                      cudaStream_t);
 
-__global__ void mirror_lower_kernel(double* const* __restrict__ mats, const int* __restrict__ n,
+template <typename T>
+__global__ void mirror_lower_kernel(T* const* __restrict__ mats, const int* __restrict__ n,
                                     const int* __restrict__ ld) {
     const int b = blockIdx.y;
-    double* M = mats[b];
+    T* M = mats[b];
     const int nn = n[b], l = ld[b];
     for (int r = blockIdx.x; r < nn; r += gridDim.x)
         for (int c = r + 1 + threadIdx.x; c < nn; c += blockDim.x) M[(size_t)r * l + c] = M[(size_t)c * l + r];
 }
 
-void launch_mirror_lower(double* const* mats, const int* n, const int* ld, int nmat, int maxn, cudaStream_t s) {
+template <typename T>
+void launch_mirror_lower(T* const* mats, const int* n, const int* ld, int nmat, int maxn, cudaStream_t s) {
     if (nmat <= 0 || maxn <= 0) return;
     dim3 grid(min(maxn, 1024), nmat);
-    mirror_lower_kernel<<<grid, 128, 0, s>>>(mats, n, ld);
+    mirror_lower_kernel<T><<<grid, 128, 0, s>>>(mats, n, ld);
 }
+template void launch_mirror_lower<float>(float* const*, const int*, const int*, int, int, cudaStream_t);
+template void launch_mirror_lower<double>(double* const*, const int*, const int*, int, int, cudaStream_t);
 
 // dst = src^T for square n x n matrices, 32 x 32 tiles through shared memory.
-__global__ void transpose_kernel(const double* const* __restrict__ src, double* const* __restrict__ dst,
+template <typename T>
+__global__ void transpose_kernel(const T* const* __restrict__ src, T* const* __restrict__ dst,
                                  const int* __restrict__ n, const int* __restrict__ lds,
                                  const int* __restrict__ ldd) {
     const int b = blockIdx.z;
     const int nn = n[b];
     const int nt = (nn + 31) / 32;
-    __shared__ double tile[32][33];
+    __shared__ T tile[32][33];
     for (int t = blockIdx.x; t < nt * nt; t += gridDim.x) {
         const int tr = t / nt, tc = t % nt;
         for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
             const int r = e / 32, c = e % 32;
             const int gr = tr * 32 + r, gc = tc * 32 + c;
-            tile[r][c] = (gr < nn && gc < nn) ? src[b][(size_t)gr * lds[b] + gc] : 0.0;
+            tile[r][c] = (gr < nn && gc < nn) ? src[b][(size_t)gr * lds[b] + gc] : T(0);
         }
         __syncthreads();
         for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
@@ -745,13 +783,34 @@ __global__ void transpose_kernel(const double* const* __restrict__ src, double* 
     }
 }
 
-void launch_transpose(const double* const* src, double* const* dst, const int* n, const int* lds, const int* ldd,
-                      int nmat, int maxn, cudaStream_t s) {
+template <typename T>
+void launch_transpose(const T* const* src, T* const* dst, const int* n, const int* lds, const int* ldd, int nmat,
+                      int maxn, cudaStream_t s) {
     if (nmat <= 0 || maxn <= 0) return;
     const int nt = (maxn + 31) / 32;
     dim3 grid(min(nt * nt, 4096), 1, nmat);
-    transpose_kernel<<<grid, 256, 0, s>>>(src, dst, n, lds, ldd);
+    transpose_kernel<T><<<grid, 256, 0, s>>>(src, dst, n, lds, ldd);
 }
+template void launch_transpose<float>(const float* const*, float* const*, const int*, const int*, const int*, int,
+                                      int, cudaStream_t);
+template void launch_transpose<double>(const double* const*, double* const*, const int*, const int*, const int*,
+                                       int, int, cudaStream_t);
+
+// dst[i] = (To) src[i]
+template <typename Ti, typename To>
+__global__ void convert_kernel(const Ti* __restrict__ src, To* __restrict__ dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (To)src[i];
+}
+
+template <typename Ti, typename To>
+void launch_convert(const Ti* src, To* dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t want = (n + 255) / 256;
+    convert_kernel<Ti, To><<<(unsigned)(want < 152 * 32 ? want : 152 * 32), 256, 0, s>>>(src, dst, n);
+}
+template void launch_convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
 
 // ------------------------------------------------------------------ tridiagonal eigenvalues
 // Householder reduction of a symmetric n x n matrix (full storage, updated in
@@ -768,28 +827,29 @@ void launch_transpose(const double* const* src, double* const* dst, const int* n
 // owned rows updated (barrier 3).  All CTAs compute the same reflector from the
 // same partials in the same order, so every barrier is reached by every
 // thread.
+template <typename T>
 __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
-    tridiag_kernel(const TridiagDesc* __restrict__ descs) {
+    tridiag_kernel(const TridiagDescT<T>* __restrict__ descs) {
     cg::cluster_group cluster = cg::this_cluster();
     const int mat = blockIdx.x / JAC_CLUSTER;
     const int crank = (int)cluster.block_rank();
-    const TridiagDesc t = descs[mat];
+    const TridiagDescT<T> t = descs[mat];
     const int n = t.n;
-    extern __shared__ double tri_smem[];
-    double* v = tri_smem;  // n
-    double* w = v + n;     // n
-    __shared__ double part[2];
-    __shared__ double red[8];
+    extern __shared__ __align__(16) unsigned char tri_smem_raw[];
+    T* v = reinterpret_cast<T*>(tri_smem_raw);  // n
+    T* w = v + n;     // n
+    __shared__ T part[2];
+    __shared__ T red[8];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-    double* A = t.A;
-    if (crank == 0 && tid == 0) t.e[0] = 0.0;
+    T* A = t.A;
+    if (crank == 0 && tid == 0) t.e[0] = T(0);
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
         // owned rows of the trailing block: global rows r = k+1+i with r % CS == crank
         const int first = (k + 1) + ((crank - (k + 1)) % JAC_CLUSTER + JAC_CLUSTER) % JAC_CLUSTER;
-        double sl = 0.0;
+        T sl = T(0);
         for (int r = first + JAC_CLUSTER * tid; r < n; r += JAC_CLUSTER * blockDim.x) {
-            const double x = __ldcg(A + (size_t)r * t.ld + k);
+            const T x = __ldcg(A + (size_t)r * t.ld + k);
             sl = fma(x, x, sl);
         }
 #pragma unroll
@@ -797,39 +857,39 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
         if (lane == 0) red[warp] = sl;
         __syncthreads();
         if (tid == 0) {
-            double q = 0.0;
+            T q = T(0);
             for (int ww = 0; ww < nw; ++ww) q += red[ww];
             part[0] = q;
         }
         cluster.sync();  // 1
-        double s2 = 0.0;
+        T s2 = T(0);
         for (int rr = 0; rr < JAC_CLUSTER; ++rr) s2 += *cluster.map_shared_rank(&part[0], rr);
-        const double x0 = __ldcg(A + (size_t)(k + 1) * t.ld + k);
-        const double tail = s2 - x0 * x0;
+        const T x0 = __ldcg(A + (size_t)(k + 1) * t.ld + k);
+        const T tail = s2 - x0 * x0;
         if (crank == 0 && tid == 0) t.d[k] = __ldcg(A + (size_t)k * t.ld + k);
-        if (!(tail > 0.0)) {
+        if (!(tail > T(0))) {
             if (crank == 0 && tid == 0) t.e[k + 1] = x0;
             cluster.sync();  // 2
             cluster.sync();  // 3
             continue;
         }
-        const double alpha = -copysign(sqrt(s2), x0);
-        const double v0 = x0 - alpha;
-        const double beta = 2.0 / fma(v0, v0, tail);
+        const T alpha = -copysign(sqrt(s2), x0);
+        const T v0 = x0 - alpha;
+        const T beta = T(2) / fma(v0, v0, tail);
         for (int i = tid; i < m; i += blockDim.x) v[i] = (i == 0) ? v0 : __ldcg(A + (size_t)(k + 1 + i) * t.ld + k);
         __syncthreads();
         // p = beta A22 v for owned rows
-        double kl = 0.0;
+        T kl = T(0);
         for (int r = first + JAC_CLUSTER * warp; r < n; r += JAC_CLUSTER * nw) {
-            const double* row = A + (size_t)r * t.ld + (k + 1);
-            double acc0 = 0.0, acc1 = 0.0;
+            const T* row = A + (size_t)r * t.ld + (k + 1);
+            T acc0 = T(0), acc1 = T(0);
             int j = lane;
             for (; j + 32 < m; j += 64) {
                 acc0 = fma(__ldcg(row + j), v[j], acc0);
                 acc1 = fma(__ldcg(row + j + 32), v[j + 32], acc1);
             }
             if (j < m) acc0 = fma(__ldcg(row + j), v[j], acc0);
-            double acc = acc0 + acc1;
+            T acc = acc0 + acc1;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             const int i = r - (k + 1);
@@ -841,21 +901,21 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
         if (lane == 0) red[warp] = kl;
         __syncthreads();
         if (tid == 0) {
-            double q = 0.0;
+            T q = T(0);
             for (int ww = 0; ww < nw; ++ww) q += red[ww];
             part[1] = q;
         }
         __threadfence();
         cluster.sync();  // 2
-        double ks = 0.0;
+        T ks = T(0);
         for (int rr = 0; rr < JAC_CLUSTER; ++rr) ks += *cluster.map_shared_rank(&part[1], rr);
-        const double K = 0.5 * beta * ks;
+        const T K = T(0.5) * beta * ks;
         for (int i = tid; i < m; i += blockDim.x) w[i] = fma(-K, v[i], __ldcg(t.p + i));
         __syncthreads();
         for (int r = first + JAC_CLUSTER * warp; r < n; r += JAC_CLUSTER * nw) {
-            double* row = A + (size_t)r * t.ld + (k + 1);
+            T* row = A + (size_t)r * t.ld + (k + 1);
             const int i = r - (k + 1);
-            const double vi = v[i], wi = w[i];
+            const T vi = v[i], wi = w[i];
             for (int j = lane; j < m; j += 32) row[j] = fma(-vi, w[j], fma(-wi, v[j], __ldcg(row + j)));
         }
         if (crank == 0 && tid == 0) t.e[k + 1] = alpha;
@@ -871,12 +931,16 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
     }
 }
 
-void launch_tridiag(const TridiagDesc* d, int nmat, int maxn, cudaStream_t s) {
+template <typename T>
+void launch_tridiag(const TridiagDescT<T>* d, int nmat, int maxn, cudaStream_t s) {
     if (nmat <= 0 || maxn <= 0) return;
-    const size_t smem = 2 * (size_t)maxn * sizeof(double);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    tridiag_kernel<<<nmat * JAC_CLUSTER, 256, smem, s>>>(d);
+    const size_t smem = 2 * (size_t)maxn * sizeof(T);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(tridiag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tridiag_kernel<T><<<nmat * JAC_CLUSTER, 256, smem, s>>>(d);
 }
+template void launch_tridiag<float>(const TridiagDescT<float>*, int, int, cudaStream_t);
+template void launch_tridiag<double>(const TridiagDescT<double>*, int, int, cudaStream_t);
 
 // All eigenvalues of symmetric tridiagonal matrices by bisection, one thread
 // per eigenvalue j (ascending): eigenvalue j is the x where the Sturm count
@@ -888,113 +952,152 @@ void launch_tridiag(const TridiagDesc* d, int nmat, int maxn, cudaStream_t s) {
 // replaced by a tiny value of the opposite sign (the pivot counts as
 // negative).  The interval starts from the Gershgorin bounds and is halved
 // until it is no wider than 2 eps (|lo| + |hi|) or stops shrinking.
-__device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int n,
-                                           double x) {
+// Bit-level helpers of the Sturm count: sign, biased exponent and the range
+// kept for the minors, per element type.
+template <typename T>
+struct SturmBits;
+template <>
+struct SturmBits<double> {
+    using I = long long;
+    static __device__ __forceinline__ I bits(double x) { return __double_as_longlong(x); }
+    static __device__ __forceinline__ int expo(I b) { return (int)((b >> 52) & 0x7ff) - 1023; }
+    static __device__ __forceinline__ bool is_zero(I b) { return (b & 0x7fffffffffffffffLL) == 0; }
+    static constexpr int R = 400;
+    static constexpr double up = 0x1p+400, down = 0x1p-400, tiny = 0x1p-1000;
+    static constexpr double eps = 2.220446049250313e-16;
+};
+template <>
+struct SturmBits<float> {
+    using I = int;
+    static __device__ __forceinline__ I bits(float x) { return __float_as_int(x); }
+    static __device__ __forceinline__ int expo(I b) { return ((b >> 23) & 0xff) - 127; }
+    static __device__ __forceinline__ bool is_zero(I b) { return (b & 0x7fffffff) == 0; }
+    static constexpr int R = 40;
+    static constexpr float up = 0x1p+40f, down = 0x1p-40f, tiny = 0x1p-120f;
+    static constexpr float eps = 1.1920929e-07f;
+};
+
+template <typename T>
+__device__ __forceinline__ int sturm_count(const T* __restrict__ d, const T* __restrict__ e2, int n, T x) {
     // signs and magnitudes are read from the bit patterns (integer pipe); the
-    // FP64 work per step is one subtraction, one multiplication and one FMA
-    double p2 = 1.0, p1 = d[0] - x;
-    if (p1 == 0.0) p1 = -0x1p-1000;
-    long long b1 = __double_as_longlong(p1);
+    // floating-point work per step is one subtraction, one multiplication and
+    // one FMA
+    using B = SturmBits<T>;
+    T p2 = T(1), p1 = d[0] - x;
+    if (p1 == T(0)) p1 = -B::tiny;
+    typename B::I b1 = B::bits(p1);
     int cnt = (b1 < 0);
     for (int i = 1; i < n; ++i) {
-        double p = fma(d[i] - x, p1, -e2[i] * p2);
-        long long b = __double_as_longlong(p);
-        if ((b & 0x7fffffffffffffffLL) == 0) {  // exact zero: opposite sign to p1, tiny magnitude
-            p = (b1 < 0) ? 0x1p-1000 : -0x1p-1000;
-            b = __double_as_longlong(p);
+        T p = fma(d[i] - x, p1, -e2[i] * p2);
+        typename B::I b = B::bits(p);
+        if (B::is_zero(b)) {  // exact zero: opposite sign to p1, tiny magnitude
+            p = (b1 < 0) ? B::tiny : -B::tiny;
+            b = B::bits(p);
         }
         cnt += ((b ^ b1) < 0);
-        const int ex = (int)((b >> 52) & 0x7ff);
-        if (ex > 1023 + 400) {
-            p *= 0x1p-400;
-            p1 *= 0x1p-400;
-        } else if (ex < 1023 - 400) {
-            p *= 0x1p+400;
-            p1 *= 0x1p+400;
+        const int ex = B::expo(b);
+        if (ex > B::R) {
+            p *= B::down;
+            p1 *= B::down;
+        } else if (ex < -B::R) {
+            p *= B::up;
+            p1 *= B::up;
         }
         p2 = p1;
         p1 = p;
-        b1 = __double_as_longlong(p1);
+        b1 = B::bits(p1);
     }
     return cnt;
 }
 
-__global__ void __launch_bounds__(32) bisect_kernel(const TridiagDesc* __restrict__ descs,
-                                                      const int* __restrict__ eig_mat,
-                                                      const int* __restrict__ eig_idx, int64_t total,
-                                                      double* const* __restrict__ out) {
+template <typename T>
+__global__ void __launch_bounds__(32) bisect_kernel(const TridiagDescT<T>* __restrict__ descs,
+                                                     const int* __restrict__ eig_mat,
+                                                     const int* __restrict__ eig_idx, int64_t total,
+                                                     double* const* __restrict__ out) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= total) return;
-    const TridiagDesc t = descs[eig_mat[gid]];
+    const TridiagDescT<T> t = descs[eig_mat[gid]];
     const int j = eig_idx[gid];
     const int n = t.n;
-    double* e2 = t.e;  // squared in place by bisect_prepare_kernel
-    double lo = 0.0, hi = 0.0;
+    const T* e2 = t.e;  // squared in place by bisect_prepare_kernel
+    T lo = T(0), hi = T(0);
     for (int i = 0; i < n; ++i) {
-        const double r = (i > 0 ? sqrt(e2[i]) : 0.0) + (i + 1 < n ? sqrt(e2[i + 1]) : 0.0);
+        const T r = (i > 0 ? sqrt(e2[i]) : T(0)) + (i + 1 < n ? sqrt(e2[i + 1]) : T(0));
         lo = (i == 0) ? t.d[i] - r : fmin(lo, t.d[i] - r);
         hi = (i == 0) ? t.d[i] + r : fmax(hi, t.d[i] + r);
     }
-    const double eps = 2.220446049250313e-16;
+    const T eps = SturmBits<T>::eps;
     for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (!(mid > lo && mid < hi) || (hi - lo) <= 2.0 * eps * (fabs(lo) + fabs(hi))) break;
-        if (sturm_count(t.d, e2, n, mid) > j)
+        const T mid = T(0.5) * (lo + hi);
+        if (!(mid > lo && mid < hi) || (hi - lo) <= T(2) * eps * (fabs(lo) + fabs(hi))) break;
+        if (sturm_count<T>(t.d, e2, n, mid) > j)
             hi = mid;
         else
             lo = mid;
     }
-    out[eig_mat[gid]][j] = 0.5 * (lo + hi);
+    out[eig_mat[gid]][j] = (double)(T(0.5) * (lo + hi));
 }
 
 // e[i] <- e[i]^2 for every matrix (the bisection only needs the squares).
-__global__ void bisect_prepare_kernel(const TridiagDesc* __restrict__ descs) {
-    const TridiagDesc t = descs[blockIdx.x];
+template <typename T>
+__global__ void bisect_prepare_kernel(const TridiagDescT<T>* __restrict__ descs) {
+    const TridiagDescT<T> t = descs[blockIdx.x];
     for (int i = threadIdx.x; i < t.n; i += blockDim.x) t.e[i] = t.e[i] * t.e[i];
 }
 
-void launch_bisect(const TridiagDesc* d, int nmat, const int* eig_mat, const int* eig_idx, int64_t total,
+template <typename T>
+void launch_bisect(const TridiagDescT<T>* d, int nmat, const int* eig_mat, const int* eig_idx, int64_t total,
                    double* const* out, cudaStream_t s) {
     if (total <= 0) return;
-    bisect_prepare_kernel<<<nmat, 256, 0, s>>>(d);
+    bisect_prepare_kernel<T><<<nmat, 256, 0, s>>>(d);
     // one warp per block so that the eigenvalues spread over every SM
-    bisect_kernel<<<(unsigned)((total + 31) / 32), 32, 0, s>>>(d, eig_mat, eig_idx, total, out);
+    bisect_kernel<T><<<(unsigned)((total + 31) / 32), 32, 0, s>>>(d, eig_mat, eig_idx, total, out);
 }
+template void launch_bisect<float>(const TridiagDescT<float>*, int, const int*, const int*, int64_t, double* const*,
+                                   cudaStream_t);
+template void launch_bisect<double>(const TridiagDescT<double>*, int, const int*, const int*, int64_t,
+                                    double* const*, cudaStream_t);
 
 // ------------------------------------------------------------------ row GEMV
 // One warp per output row, rows of all matrices in one flat list.
-__global__ void __launch_bounds__(256) gemv_rows_kernel(const GemvDesc* __restrict__ descs,
+template <typename T>
+__global__ void __launch_bounds__(256) gemv_rows_kernel(const GemvDescT<T>* __restrict__ descs,
                                                          const int* __restrict__ row_desc,
                                                          const int* __restrict__ row_local, int64_t nrows) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nrows) return;
-    const GemvDesc d = descs[row_desc[w]];
+    const GemvDescT<T> d = descs[row_desc[w]];
     const int r = row_local[w];
     int c0 = 0, c1 = d.ncols;
     if (d.mode == 1) c1 = min(r + 1, d.ncols);
     if (d.mode == 2) c0 = r;
     if (d.cstart) c0 = max(c0, d.cstart[r] - d.coff);
     if (d.cend) c1 = min(c1, d.cend[r] - d.coff);
-    const double* row = d.M + (size_t)r * d.ld;
-    double s0 = 0.0, s1 = 0.0;
+    const T* row = d.M + (size_t)r * d.ld;
+    T s0 = T(0), s1 = T(0);
     int c = c0 + lane;
     for (; c + 32 < c1; c += 64) {
         s0 = fma(row[c], d.x[c], s0);
         s1 = fma(row[c + 32], d.x[c + 32], s1);
     }
     if (c < c1) s0 = fma(row[c], d.x[c], s0);
-    double s = s0 + s1;
+    T s = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) d.y[r] = d.b ? fma(d.alpha, s, d.b[r]) : d.alpha * s;
 }
 
-void launch_gemv_rows(const GemvDesc* d, const int* row_desc, const int* row_local, int64_t nrows, cudaStream_t s) {
+template <typename T>
+void launch_gemv_rows(const GemvDescT<T>* d, const int* row_desc, const int* row_local, int64_t nrows,
+                      cudaStream_t s) {
     if (nrows <= 0) return;
     const int64_t threads = nrows * 32;
     const int64_t blocks = (threads + 255) / 256;
-    gemv_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, row_desc, row_local, nrows);
+    gemv_rows_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, row_desc, row_local, nrows);
 }
+template void launch_gemv_rows<float>(const GemvDescT<float>*, const int*, const int*, int64_t, cudaStream_t);
+template void launch_gemv_rows<double>(const GemvDescT<double>*, const int*, const int*, int64_t, cudaStream_t);
 
 }  // namespace amdd

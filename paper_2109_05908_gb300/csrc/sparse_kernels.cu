@@ -72,38 +72,45 @@ void launch_gather_vec(const int32_t* idx, int64_t cnt, const double* x, double*
 
 // dst[dst_off[r] + c] = src[src_off[r] + c] for c < len[r]: copies rows of
 // matrices with different leading dimensions.
-__global__ void gather_rows_kernel(const double* __restrict__ src, const int64_t* __restrict__ src_off,
-                                   double* __restrict__ dst, const int64_t* __restrict__ dst_off,
+template <typename T>
+__global__ void gather_rows_kernel(const T* __restrict__ src, const int64_t* __restrict__ src_off,
+                                   T* __restrict__ dst, const int64_t* __restrict__ dst_off,
                                    const int32_t* __restrict__ len, int64_t nrows) {
     for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
-        const double* s = src + src_off[r];
-        double* d = dst + dst_off[r];
+        const T* s = src + src_off[r];
+        T* d = dst + dst_off[r];
         for (int c = threadIdx.x; c < len[r]; c += blockDim.x) d[c] = s[c];
     }
 }
 
-void launch_gather_rows(const double* src, const int64_t* src_off, double* dst, const int64_t* dst_off,
-                        const int32_t* len, int64_t nrows, cudaStream_t s) {
+template <typename T>
+void launch_gather_rows(const T* src, const int64_t* src_off, T* dst, const int64_t* dst_off, const int32_t* len,
+                        int64_t nrows, cudaStream_t s) {
     if (nrows <= 0) return;
-    gather_rows_kernel<<<(unsigned)(nrows < 65535 ? nrows : 65535), 128, 0, s>>>(src, src_off, dst, dst_off, len,
-                                                                                  nrows);
+    gather_rows_kernel<T><<<(unsigned)(nrows < 65535 ? nrows : 65535), 128, 0, s>>>(src, src_off, dst, dst_off, len,
+                                                                                     nrows);
 }
+template void launch_gather_rows<float>(const float*, const int64_t*, float*, const int64_t*, const int32_t*, int64_t,
+                                        cudaStream_t);
+template void launch_gather_rows<double>(const double*, const int64_t*, double*, const int64_t*, const int32_t*,
+                                         int64_t, cudaStream_t);
 
 // ------------------------------------------------------------------ prolongation
 // z[g] = sum over the copies of g in the local vectors (fixed subdomain order)
 //      + sum_k Zt_i[k][a] e[coff_i + k]   (i owns g, a = position of g in Omega_Ii).
 // Threads run in owner order so that consecutive threads read consecutive
 // columns of Zt_i.
+template <typename TY>
 __global__ void __launch_bounds__(256) scatter_prolong_kernel(
     int64_t n, const int32_t* __restrict__ order_g, const int32_t* __restrict__ own_sub,
     const int32_t* __restrict__ own_a, const int64_t* __restrict__ sc_ptr, const int32_t* __restrict__ sc_idx,
-    const double* __restrict__ yloc, const int64_t* __restrict__ zt_off, const int32_t* __restrict__ nI,
+    const TY* __restrict__ yloc, const int64_t* __restrict__ zt_off, const int32_t* __restrict__ nI,
     const int32_t* __restrict__ p, const int64_t* __restrict__ coff, const double* __restrict__ Zt,
     const double* __restrict__ e, double* __restrict__ z) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const int g = order_g[t];
         double s = 0.0;
-        for (int64_t k = sc_ptr[g]; k < sc_ptr[g + 1]; ++k) s += yloc[sc_idx[k]];
+        for (int64_t k = sc_ptr[g]; k < sc_ptr[g + 1]; ++k) s += (double)yloc[sc_idx[k]];
         if (e) {
             const int i = own_sub[t], a = own_a[t];
             const int pi = p[i], ni = nI[i];
@@ -117,15 +124,24 @@ __global__ void __launch_bounds__(256) scatter_prolong_kernel(
     }
 }
 
+template <typename TY>
 void launch_scatter_prolong(int64_t n, const int32_t* order_g, const int32_t* own_sub, const int32_t* own_a,
-                            const int64_t* sc_ptr, const int32_t* sc_idx, const double* yloc, const int64_t* zt_off,
+                            const int64_t* sc_ptr, const int32_t* sc_idx, const TY* yloc, const int64_t* zt_off,
                             const int32_t* nI, const int32_t* p, const int64_t* coff, const double* Zt,
                             const double* e, double* z, cudaStream_t s) {
     if (n <= 0) return;
     const int64_t want = (n + 255) / 256;
-    scatter_prolong_kernel<<<(unsigned)(want < 152 * 32 ? want : 152 * 32), 256, 0, s>>>(
+    scatter_prolong_kernel<TY><<<(unsigned)(want < 152 * 32 ? want : 152 * 32), 256, 0, s>>>(
         n, order_g, own_sub, own_a, sc_ptr, sc_idx, yloc, zt_off, nI, p, coff, Zt, e, z);
 }
+template void launch_scatter_prolong<float>(int64_t, const int32_t*, const int32_t*, const int32_t*, const int64_t*,
+                                            const int32_t*, const float*, const int64_t*, const int32_t*,
+                                            const int32_t*, const int64_t*, const double*, const double*, double*,
+                                            cudaStream_t);
+template void launch_scatter_prolong<double>(int64_t, const int32_t*, const int32_t*, const int32_t*, const int64_t*,
+                                             const int32_t*, const double*, const int64_t*, const int32_t*,
+                                             const int32_t*, const int64_t*, const double*, const double*, double*,
+                                             cudaStream_t);
 
 // ------------------------------------------------------------------ coarse blocks
 // E[coff_i + r][coff_j + c] = sum_l Zt_i[r][la[l]] * AZ_j[lpos[l]][c], 32 x 32

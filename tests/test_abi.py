@@ -70,3 +70,32 @@ def test_host_overlap_sets_rejects_bad_graph(A):
     bad[3] = 99
     with pytest.raises(A.AmddError):
         A.overlap_sets(M.n, M.rowptr, bad, synth.box_partition_2d(4, 2), 0, 1)
+
+
+@pytest.mark.parametrize("tau", [0.5, 100.0])
+def test_host_lanczos_extremes_match_oracle(A, tau):
+    """The library's Lanczos condition estimate (host code) on the oracle's
+    own PCG coefficients equals the oracle's dense tridiagonal eigenvalues."""
+    M = synth.diffusion3d(8, sigma=1.0, corr=2.0, n_channels=2, seed=1, channel_value=1e3)
+    part = synth.bfs_partition(M, 6, seed=1, min_size=40, max_size=160)
+    S = O.setup(M, part, int(part.max()) + 1, 1, tau)
+    co = []
+    O.pcg(S.A, synth.rhs(M.n, 0), lambda r: O.apply(S, r), rtol=1e-8, coeffs=co)
+    al = [v for t, v in co if t == "a"]
+    be = [v for t, v in co if t == "b"][: len(al) - 1]
+    lo, hi = A.lanczos_extremes(al, be)
+    olo, ohi = O.lanczos_extremes(co)
+    assert lo == pytest.approx(olo, rel=1e-12) and hi == pytest.approx(ohi, rel=1e-12)
+    for k in (1, 2, 3):
+        lo, hi = A.lanczos_extremes(al[:k], be[: k - 1])
+        olo, ohi = O.lanczos_extremes([("a", a) for a in al[:k]] + [("b", b) for b in be[: k - 1]])
+        assert lo == pytest.approx(olo, rel=1e-12) and hi == pytest.approx(ohi, rel=1e-12)
+
+
+def test_host_lanczos_extremes_rejects_bad_input(A):
+    with pytest.raises(A.AmddError):
+        A.lanczos_extremes([1.0, -2.0], [0.5])
+    with pytest.raises(A.AmddError):
+        A.lanczos_extremes([1.0, 2.0], [-0.5])
+    lo, hi = A.lanczos_extremes([], [])
+    assert np.isnan(lo) and np.isnan(hi)

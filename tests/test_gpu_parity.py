@@ -184,6 +184,28 @@ def test_pcg_matches_oracle(name):
     assert torch.equal(xd2, xd3), "PCG is not bitwise reproducible"
 
 
+@pytest.mark.parametrize("name", ["lap16_box4_tau0.5", "diff8_bfs_ov1_tau0.5", "diff9_bfs_ov2_tau100"])
+def test_condition_estimate(name):
+    """The Lanczos condition estimate of the GPU PCG equals the oracle's on the
+    same iterations (1e-6), lies inside the dense spectrum of M^{-1} A and
+    under the bound of Sec. 3.2."""
+    M, part, N, ov, tau, S, dA, dpart, P = _case(name)
+    b = synth.rhs(M.n, 0)
+    co = []
+    _, its_o, _ = O.pcg(S.A, b, lambda r: O.apply(S, r), rtol=1e-8, coeffs=co)
+    bd = to_device(b)
+    xd = torch.zeros_like(bd)
+    st = P.solve(bd, xd, rtol=1e-8)
+    lo, hi = O.lanczos_extremes(co)
+    if st.iterations == its_o:
+        assert st.ritz_min == pytest.approx(lo, rel=1e-6) and st.ritz_max == pytest.approx(hi, rel=1e-6)
+    Minv = np.column_stack([O.apply(S, e) for e in np.eye(M.n)])
+    ev = np.sort(np.linalg.eigvals(Minv @ S.A.toarray()).real)
+    assert ev[0] * (1 - 1e-8) <= st.ritz_min and st.ritz_max <= ev[-1] * (1 + 1e-8)
+    bound = O.condition_bound(O.colouring_number(S), O.splitting_constant(S), tau)
+    assert st.cond_est == pytest.approx(st.ritz_max / st.ritz_min) and st.cond_est <= bound
+
+
 def test_pcg_initial_guess_and_zero_rhs():
     M, part, N, ov, tau, S, dA, dpart, P = _case("lap16_box4_tau0.5")
     b = synth.rhs(M.n, 2)
