@@ -126,6 +126,79 @@ def cpu_baseline(w, max_seconds=30.0):
                       f"BLAS threading on {cores} host cores; {its} PCG iterations"}, its
 
 
+APPLY_SCALE = {"m": 1024, "box": 16, "overlap": 1, "tau": 1e-12}
+APPLY_CLASSES = ("gemv_rows_f32", "gemv_rows", "gather_scatter", "coarse_solve")
+
+
+def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20):
+    """SpMV and the two-level apply at scale: 2D Laplacian 1024 x 1024 (n = 1M),
+    4096 boxes of 16 x 16, overlap 1, mixed form.  With tau = 1e-12 only
+    eigenvalues above 1e12 enter the coarse space, so the apply is the
+    bandwidth-bound part (restriction, the local triangular products with
+    ~1.7 GB of FP32 factors, prolongation).  Each timed call is bracketed by
+    CUDA events on the library's stream, with L2 flushed before it; bytes are
+    the algorithmic counts of the library's profile."""
+    import synth
+    from paper_2109_05908_gb300.device import DeviceMatrix
+    c = APPLY_SCALE
+    M = synth.laplace2d(c["m"])
+    part_h = synth.box_partition_2d(c["m"], c["box"])
+    N = int(part_h.max()) + 1
+    dA = DeviceMatrix(M, device=dev)
+    part = torch.from_numpy(part_h).to(dev)
+    o = A.opts_default()
+    o.precision = 1
+    o.profile = 1
+    t0 = time.perf_counter()
+    h = A.setup(dA.csr, part.data_ptr(), N, c["overlap"], c["tau"], o, sp)
+    setup_s = time.perf_counter() - t0
+    info = A.get_info(h)
+    stream = torch.cuda.current_stream(dev)
+    r = torch.from_numpy(synth.rhs(M.n, 3)).to(dev)
+    z = torch.empty_like(r)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        out = []
+        for k in range(reps + 3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 3:
+                out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    spmv_ms = timed(lambda: A.spmv(dA.csr, r.data_ptr(), z.data_ptr(), sp))
+    spmv_bytes = 12.0 * dA.nnz + 8.0 * (M.n + 1) + 16.0 * M.n
+    A.apply(h, r.data_ptr(), z.data_ptr(), 1)
+    A.reset_profile(h)
+    apply_ms = timed(lambda: A.apply(h, r.data_ptr(), z.data_ptr(), 1))
+    prof = {p["name"]: p for p in A.get_profile(h)}
+    n_calls = reps + 3
+    apply_bytes = sum(prof[k]["bytes"] for k in APPLY_CLASSES if k in prof) / n_calls
+    kernels = {}
+    for k in APPLY_CLASSES:
+        p = prof.get(k)
+        if p and p["launches"] and p["ms"] > 0:
+            gbs = p["bytes"] / (p["ms"] * 1e-3) / 1e9
+            kernels[k] = {"launches_per_apply": p["launches"] / n_calls, "ms_per_apply": p["ms"] / n_calls,
+                          "GB/s": gbs, "frac": gbs / hbm_gbs}
+    A.destroy(h)
+    spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    apply_gbs = apply_bytes / (apply_ms * 1e-3) / 1e9
+    return {
+        "workload": f"laplace2d_{c['m']}x{c['m']}_{N}box_ov{c['overlap']}_tau{c['tau']:g}, mixed form",
+        "n": M.n, "N": N, "n_C": info.n_C, "setup_s": setup_s, "l2": "flushed before every timed call",
+        "spmv": {"ms": spmv_ms, "bytes": spmv_bytes, "GB/s": spmv_gbs, "frac": spmv_gbs / hbm_gbs},
+        "apply": {"ms": apply_ms, "bytes": apply_bytes, "GB/s": apply_gbs, "frac": apply_gbs / hbm_gbs,
+                  "note": "whole amdd_apply call between events (launch gaps included)"},
+        "apply_kernels": kernels,
+    }
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -296,6 +369,7 @@ def run_amdd(args):
                 "launches_per_step": c["launches"] / args.steps, "ms_per_launch": per_launch_ms,
                 "peak_source": f"hbm_gbs ({peak_src})"}
     launches = int(sum(v["launches"] for v in prof.values()) / args.steps)
+    scale = apply_at_scale(A, torch, np, dev, sp, peaks["hbm_gbs"]) if not args.no_scale else None
     base, base_its = cpu_baseline(w) if world == 1 or rank == 0 else (None, None)
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -310,8 +384,7 @@ def run_amdd(args):
                               "rotations_svd": info.rotations_svd, "rotations_eig": info.rotations_eig},
                    "oracle_pcg_iterations": base_its, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "form": "plain FP64" if args.precision == 0 else
-                           "mixed: FP32 local factors/solves/SVD/splitting/eigensolve, FP64 E and PCG",
+                   "form": FORMS[args.precision],
                    "profiling_events_in_timed_region": "dominant kernel class only"},
         "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "true_rel_residual": float(res)},
@@ -319,6 +392,7 @@ def run_amdd(args):
         "roofline": roof,
         "cpu_baseline": base,
         "clocks": clk,
+        "apply_scale": scale,
         "profile_ms_warmup_step": {k: round(v["ms"], 4) for k, v in
                                    sorted(warm_prof.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
     }
@@ -336,14 +410,22 @@ def M_mv(M, x):
     return y
 
 
+FORMS = {0: "plain FP64",
+         1: "mixed: FP32 local factors/solves/SVD/splitting/eigensolve (eps 2^-23), FP64 E and PCG",
+         2: "mixed: FP64 SVD/splitting (eps 2^-52), FP32 local factors/solves/eigensolve, FP64 E and PCG"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="amdd", choices=["amdd", "reference"])
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
-                    help="0: plain FP64 form; 1: mixed form (FP32 local work, FP64 coarse and PCG)")
+    ap.add_argument("--no-scale", action="store_true",
+                    help="skip the SpMV / apply bandwidth measurement on the 1M-unknown problem")
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
+                    help="0: plain FP64 form; 1: mixed form (FP32 local work, FP64 coarse and PCG); "
+                         "2: mixed form with an FP64 splitting")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -71,11 +71,15 @@ typedef struct {
     int32_t max_sweeps;   /* sweep limit of the one-sided Jacobi solvers; default 60               */
     int32_t profile;      /* 1: time every kernel launch of the handle with CUDA events (see
                              amdd_get_profile); default 0                                           */
-    int32_t precision;    /* 0: plain FP64 (default).  1: mixed form: the local work (local
-                             Cholesky factors and solves, SVD of X_i, splitting, eq. (Zi)) in FP32
-                             with FP32 accumulation; E, its factor, the coarse solve and PCG in FP64.
-                             Sec. 3.2 takes eps as the machine precision of the arithmetic, so the
-                             FP32 stage uses max(eps, 2^-23) (amdd_info.eps reports it)             */
+    int32_t precision;    /* 0: plain FP64 (default).
+                             1: mixed form: the local work (local Cholesky factors and solves, SVD
+                             of X_i, splitting, eq. (Zi)) in FP32 with FP32 accumulation; E, its
+                             factor, the coarse solve and PCG in FP64.  Sec. 3.2 takes eps as the
+                             machine precision of the arithmetic, so the FP32 stage uses
+                             max(eps, 2^-23) (amdd_info.eps reports it).
+                             2: mixed form with an FP64 splitting: the SVD of X_i, Abar_ii and its
+                             Schur complement in FP64 with eps as given; the local factors and
+                             solves, T and the eigensolve of eq. (Zi) in FP32; E and PCG in FP64 */
     uint32_t profile_classes; /* with profile = 1: bit k set times kernel class k only (classes as
                              numbered by amdd_get_profile); 0 times every class; default 0         */
     int32_t reserved[4];  /* must be zero                                                          */
@@ -111,7 +115,7 @@ typedef struct {
     int64_t rotations_eig; /* plane rotations applied by the eq. (Zi) solver */
     int32_t sweeps_svd32;  /* sweeps of the FP32 preconditioning stage (SVD) */
     int32_t sweeps_eig32;  /* sweeps of the FP32 preconditioning stage (eq. (Zi)) */
-    int32_t precision;     /* 0 plain FP64, 1 mixed (see amdd_opts)          */
+    int32_t precision;     /* 0 plain FP64, 1 or 2 mixed (see amdd_opts)     */
     double eps;            /* the eps of the splitting actually used       */
 } amdd_info;
 
@@ -208,14 +212,14 @@ amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, i
 /* Kernel-class profile of a handle created with opts.profile = 1: for class
  * k in [0, AMDD_PROF_CLASSES) (one class per kernel; the two Jacobi solvers
  * are separate classes), its static name, number of launches, summed device
- * time in ms (CUDA events recorded on the handle's stream around each
- * launch), and the algorithmic FP64 flops and DRAM bytes of those launches
+ * time in ms (CUDA events recorded around each launch on the stream it
+ * runs on), and the algorithmic FP64 flops and DRAM bytes of those launches
  * (flops from the operation counts of the launched work; bytes for the
  * bandwidth-bound classes, 0 where not meaningful).  Counts accumulate over
  * amdd_setup, amdd_apply and amdd_pcg_solve until amdd_reset_profile.
  * Synchronises the handle's stream.  AMDD_ERR_INVALID if profiling is off or
  * k is out of range. */
-#define AMDD_PROF_CLASSES 23
+#define AMDD_PROF_CLASSES 24
 amdd_status amdd_get_profile(amdd_handle* h, int32_t k, const char** name, int64_t* launches, double* ms,
                              double* flops, double* bytes);
 

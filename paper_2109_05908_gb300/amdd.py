@@ -216,7 +216,7 @@ def lanczos_extremes(alpha, beta):
     return lo.value, hi.value
 
 
-PROF_CLASSES = 23
+PROF_CLASSES = 24
 
 
 def get_profile(h: int):

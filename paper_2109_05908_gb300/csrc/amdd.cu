@@ -65,6 +65,7 @@ enum ProfK {
     PK_TRIDIAG_F32,
     PK_BISECT_F32,
     PK_GEMV_F32,
+    PK_CSOLVE,
     PK_COUNT
 };
 static_assert(PK_COUNT == AMDD_PROF_CLASSES, "profile classes");
@@ -72,7 +73,7 @@ static const char* const kProfNames[PK_COUNT] = {
     "gather_values", "chol_diag", "chol_panel", "gemm_tiles", "trtri_diag", "jacobi_svd", "jacobi_eig", "jacobi_f32", "tridiag", "bisect",
     "small_dense", "e_offdiag", "spmv", "gemv_rows", "gather_scatter", "pcg_vectors",
     "gemm_tiles_f32", "chol_diag_f32", "chol_panel_f32", "trtri_diag_f32", "tridiag_f32", "bisect_f32",
-    "gemv_rows_f32"};
+    "gemv_rows_f32", "coarse_solve"};
 
 // class of a kernel in element type T (FP32 variants have their own classes)
 template <typename T>
@@ -117,6 +118,8 @@ struct ProfState {
 
 struct amdd_handle {
     cudaStream_t s = nullptr;
+    cudaStream_t s2 = nullptr;  // second stream of the setup (look-ahead of the blocked Cholesky)
+    cudaEvent_t ev_panel = nullptr, ev_far = nullptr;
     ProfState prof;
     int64_t n = 0, nnz = 0;
     int N = 0, overlap = 0;
@@ -143,10 +146,7 @@ struct amdd_handle {
     GemvDesc* d_gv_l1 = nullptr;
     GemvDesc* d_gv_l2 = nullptr;
     GemvDesc* d_gv_c = nullptr;
-    GemvDesc* d_gv_e1 = nullptr;
-    GemvDesc* d_gv_e2 = nullptr;
     int32_t *d_rd_loc = nullptr, *d_rl_loc = nullptr, *d_rd_c = nullptr, *d_rl_c = nullptr;
-    int32_t *d_rd_e = nullptr, *d_rl_e = nullptr;
     int32_t *d_order_g = nullptr, *d_own_sub = nullptr, *d_own_a = nullptr, *d_sc_idx = nullptr;
     int32_t *d_nI = nullptr, *d_p = nullptr;
     int64_t *d_sc_ptr = nullptr, *d_zt_off = nullptr, *d_coff = nullptr;
@@ -157,15 +157,11 @@ struct amdd_handle {
     float *d_rloc32 = nullptr, *d_tloc32 = nullptr, *d_yloc32 = nullptr;
     GemvDescT<float>* d_gv_l1_32 = nullptr;
     GemvDescT<float>* d_gv_l2_32 = nullptr;
-    double *d_c = nullptr, *d_ct = nullptr, *d_e = nullptr, *d_ctmp = nullptr;
+    double *d_c = nullptr, *d_e = nullptr, *d_ctmp = nullptr;
     // coarse solve: L_E (d_YE), L_E^T (d_YEt), inverses of its diagonal blocks
     double *d_Yd = nullptr, *d_Ydt = nullptr;
-    int cSB = 0, cK = 0;
-    struct CStep {
-        int rows;
-        double flops, bytes;
-    };
-    std::vector<CStep> csteps;
+    int cSB = 0, cK = 0, coop_blocks = 0;
+    double csolve_flops = 0.0, csolve_bytes = 0.0;
     std::vector<int> env_row;     // first non-zero column of each row of E (and L_E)
     std::vector<int> env_colend;  // one past the last non-zero row of each column of L_E
     int* d_env_row = nullptr;
@@ -199,12 +195,14 @@ T* dnew(amdd_handle* h, size_t count) {
 struct PScope {
     amdd_handle* h;
     int k;
+    cudaStream_t st;
     cudaEvent_t b = nullptr;
-    PScope(amdd_handle* hh, int kk, double flops = 0.0, double bytes = 0.0) : h(hh), k(kk) {
+    PScope(amdd_handle* hh, int kk, double flops = 0.0, double bytes = 0.0, cudaStream_t stream = nullptr)
+        : h(hh), k(kk), st(stream ? stream : hh->s) {
         if (!h->prof.on || !((h->prof.mask >> k) & 1u)) return;
         b = h->prof.take();
         if (!b) return;
-        cudaEventRecord(b, h->s);
+        cudaEventRecord(b, st);
         h->prof.launches[k] += 1;
         h->prof.flops[k] += flops;
         h->prof.bytes[k] += bytes;
@@ -213,7 +211,7 @@ struct PScope {
         if (!b) return;
         cudaEvent_t e = h->prof.take();
         if (!e) return;
-        cudaEventRecord(e, h->s);
+        cudaEventRecord(e, st);
         h->prof.ev[k].push_back({b, e});
     }
 };
@@ -226,6 +224,8 @@ struct Ctx {
     std::vector<std::shared_ptr<void>> keep;
     explicit Ctx(amdd_handle* hh) : h(hh) {}
     ~Ctx() {
+        // work on the second stream may still read temporaries (after an error)
+        if (h->s2) cudaStreamSynchronize(h->s2);
         for (void* p : temps) cudaFreeAsync(p, h->s);
     }
     template <class T>
@@ -249,20 +249,35 @@ struct Ctx {
 
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Output tiles of a batch of GEMMs for tile size `tile`.
 template <typename T>
-void gemm(Ctx& C, const std::vector<GemmDescT<T>>& ds) {
+std::vector<TileRef> gemm_tiles(const std::vector<GemmDescT<T>>& ds, int tile) {
     std::vector<TileRef> tiles;
     for (int d = 0; d < (int)ds.size(); ++d) {
         const GemmDescT<T>& g = ds[d];
         if (g.m <= 0 || g.n <= 0) continue;
-        const int tm = cdiv(g.m, GEMM_T), tn = cdiv(g.n, GEMM_T);
+        const int tm = cdiv(g.m, tile), tn = cdiv(g.n, tile);
         for (int a = 0; a < tm; ++a)
             for (int b = 0; b < tn; ++b) {
                 if (g.lower && b > a) continue;
                 tiles.push_back({d, a, b});
             }
     }
+    return tiles;
+}
+
+// 64 x 64 tiles unless that leaves fewer than two CTAs per SM; then 32 x 32.
+constexpr int SMALL_LAUNCH_TILES = 2 * 152;
+
+template <typename T>
+void gemm(Ctx& C, const std::vector<GemmDescT<T>>& ds) {
+    int tile = GEMM_T;
+    std::vector<TileRef> tiles = gemm_tiles(ds, tile);
     if (tiles.empty()) return;
+    if ((int)tiles.size() < SMALL_LAUNCH_TILES) {
+        tile = 32;
+        tiles = gemm_tiles(ds, tile);
+    }
     double fl = 0.0;
     for (const GemmDescT<T>& g : ds) {
         if (g.m <= 0 || g.n <= 0) continue;
@@ -273,7 +288,7 @@ void gemm(Ctx& C, const std::vector<GemmDescT<T>>& ds) {
     const GemmDescT<T>* dd = C.up(ds);
     const TileRef* dt = C.up(tiles);
     PScope ps(C.h, pk<T>(PK_GEMM, PK_GEMM_F32), fl);
-    launch_gemm<T>(dd, dt, (int)tiles.size(), C.h->s);
+    launch_gemm<T>(dd, dt, (int)tiles.size(), tile, C.h->s);
 }
 
 template <typename T>
@@ -306,13 +321,47 @@ GemmDescT<T> gd(const T* A, int lda, int ta, const T* B, int ldb, int tb, T* Cm,
 // non-zero column (the envelope).  The Cholesky factor keeps the envelope of
 // the matrix, so panel row tiles and trailing-update tiles whose rows have no
 // entries in the current block column are zero throughout and are skipped.
+//
+// Look-ahead: the trailing update of step k is split into the next block
+// column ("near", on the handle's stream, right after the panel) and the rest
+// ("far", on a second stream).  The far update of step k runs while the
+// diagonal block and panel of step k+1 are factored; the near update of step
+// k+1 waits for it, since both write block column k+2.  The order of the
+// updates of every entry is fixed, so results do not depend on timing.
 template <typename T>
 void chol_batched(Ctx& C, const std::vector<CholDescT<T>>& ds, const std::vector<const std::vector<int>*>& env = {}) {
     if (ds.empty()) return;
     amdd_handle* h = C.h;
+    cudaStream_t sm = h->s, ss = h->s2;
     CholDescT<T>* dd = C.up(ds);
     int maxstop = 0;
     for (const auto& d : ds) maxstop = std::max(maxstop, d.stop);
+    bool far_pending = false;  // a far update was issued on ss and not yet joined
+    auto active_rows = [&](int d, int r_begin, int r_end, int kend) {
+        const std::vector<int>* e = (d < (int)env.size()) ? env[d] : nullptr;
+        if (!e) return true;
+        for (int r = r_begin; r < r_end; ++r)
+            if ((*e)[r] < kend) return true;
+        return false;
+    };
+    // tiles of one GEMM descriptor whose row and column blocks are both active
+    auto update_tiles = [&](int gi, const GemmDescT<T>& g, int d, int row_base, int col_base, int kend, int tile,
+                            std::vector<TileRef>& out, double& fl) {
+        const int tm = cdiv(g.m, tile), tn = cdiv(g.n, tile);
+        std::vector<char> ar(tm), ac(tn);
+        for (int a = 0; a < tm; ++a)
+            ar[a] = active_rows(d, row_base + a * tile, std::min(row_base + (a + 1) * tile, row_base + g.m), kend);
+        for (int b = 0; b < tn; ++b)
+            ac[b] = active_rows(d, col_base + b * tile, std::min(col_base + (b + 1) * tile, col_base + g.n), kend);
+        for (int a = 0; a < tm; ++a)
+            for (int b = 0; b < tn; ++b)
+                if (ar[a] && ac[b] && !(g.lower && b > a)) {
+                    out.push_back({gi, a, b});
+                    const double ri = std::min(tile, g.m - a * tile), ci = std::min(tile, g.n - b * tile);
+                    const double outs = (g.lower && a == b) ? ri * (ri + 1) / 2 : ri * ci;
+                    fl += 2.0 * outs * g.k;
+                }
+    };
     for (int k0 = 0; k0 < maxstop; k0 += CHOL_NB) {
         {
             double fl = 0.0;
@@ -322,57 +371,84 @@ void chol_batched(Ctx& C, const std::vector<CholDescT<T>>& ds, const std::vector
                     fl += 2.0 * kb * kb * kb / 3.0;
                 }
             PScope ps(h, pk<T>(PK_CHOL_DIAG, PK_CHOL_DIAG_F32), fl);
-            launch_chol_diag<T>(dd, (int)ds.size(), k0, h->d_err, h->s);
+            launch_chol_diag<T>(dd, (int)ds.size(), k0, h->d_err, sm);
         }
         std::vector<PanelRef> pt;
-        double pfl = 0.0, gfl = 0.0;
-        std::vector<GemmDescT<T>> g;
-        std::vector<TileRef> gt;
+        double pfl = 0.0;
+        std::vector<GemmDescT<T>> gn, gf;  // near / far updates
+        std::vector<int> gn_d, gf_d, gn_kend, gf_kend;
+        int tiles64 = 0;
         for (int d = 0; d < (int)ds.size(); ++d) {
             const CholDescT<T>& c = ds[d];
             if (k0 >= c.stop) continue;
             const int kend = std::min(k0 + CHOL_NB, c.stop);
             const int rows = c.n - kend;
             if (rows <= 0) continue;
-            const int ntile = cdiv(rows, 64);
-            std::vector<char> act(ntile, 1);
-            const std::vector<int>* e = (d < (int)env.size()) ? env[d] : nullptr;
-            if (e) {
-                for (int t = 0; t < ntile; ++t) {
-                    int mn = INT32_MAX;
-                    for (int r = kend + 64 * t; r < std::min(c.n, kend + 64 * t + 64); ++r) mn = std::min(mn, (*e)[r]);
-                    act[t] = mn < kend;
-                }
-            }
             const int kb = kend - k0;
-            for (int rt = 0; rt < ntile; ++rt)
-                if (act[rt]) {
+            for (int rt = 0; rt < cdiv(rows, PANEL_ROWS); ++rt)
+                if (active_rows(d, kend + rt * PANEL_ROWS, std::min(c.n, kend + (rt + 1) * PANEL_ROWS), kend)) {
                     pt.push_back({d, rt});
-                    pfl += (double)std::min(64, rows - 64 * rt) * kb * (kb + 1);
+                    pfl += (double)std::min(PANEL_ROWS, rows - PANEL_ROWS * rt) * kb * (kb + 1);
                 }
-            T* panel = c.A + (size_t)kend * c.ld + k0;
-            const int gi = (int)g.size();
-            g.push_back(gd(panel, c.ld, 0, panel, c.ld, 1, c.A + (size_t)kend * c.ld + kend, c.ld, rows, rows, kb, -1.0,
-                           1.0, 1));
-            for (int a = 0; a < ntile; ++a)
-                for (int b = 0; b <= a; ++b)
-                    if (act[a] && act[b]) {
-                        gt.push_back({gi, a, b});
-                        gfl += 2.0 * 64 * 64 * kb;
-                    }
+            const T* P = c.A + (size_t)kend * c.ld + k0;  // panel rows [kend, n)
+            const int w = std::max(0, std::min(CHOL_NB, c.stop - kend));  // next block column
+            if (w > 0) {
+                gn.push_back(gd(P, c.ld, 0, P, c.ld, 1, c.A + (size_t)kend * c.ld + kend, c.ld, rows, w, kb, -1.0, 1.0,
+                                1));
+                gn_d.push_back(d);
+                gn_kend.push_back(kend);
+            }
+            if (rows - w > 0) {
+                const T* Pf = P + (size_t)w * c.ld;
+                gf.push_back(gd(Pf, c.ld, 0, Pf, c.ld, 1, c.A + (size_t)(kend + w) * c.ld + kend + w, c.ld, rows - w,
+                                rows - w, kb, -1.0, 1.0, 1));
+                gf_d.push_back(d);
+                gf_kend.push_back(kend);
+                tiles64 += cdiv(rows - w, 64) * (cdiv(rows - w, 64) + 1) / 2;
+            }
         }
         if (!pt.empty()) {
             const PanelRef* dpt = C.up(pt);
             PScope ps(h, pk<T>(PK_CHOL_PANEL, PK_CHOL_PANEL_F32), pfl);
-            launch_chol_panel<T>(dd, dpt, (int)pt.size(), k0, h->s);
+            launch_chol_panel<T>(dd, dpt, (int)pt.size(), k0, sm);
         }
-        if (!gt.empty()) {
-            const GemmDescT<T>* dg = C.up(g);
-            const TileRef* dt = C.up(gt);
-            PScope ps(h, pk<T>(PK_GEMM, PK_GEMM_F32), gfl);
-            launch_gemm<T>(dg, dt, (int)gt.size(), h->s);
+        // far update on the second stream, after this panel
+        const int tile = tiles64 < SMALL_LAUNCH_TILES ? 32 : 64;
+        std::vector<TileRef> tf, tn;
+        double ffl = 0.0, nfl = 0.0;
+        for (int q = 0; q < (int)gf.size(); ++q) {
+            const int kend = gf_kend[q];
+            const int w = (int)(ds[gf_d[q]].n - kend) - gf[q].m;
+            update_tiles(q, gf[q], gf_d[q], kend + w, kend + w, kend, tile, tf, ffl);
+        }
+        for (int q = 0; q < (int)gn.size(); ++q)
+            update_tiles(q, gn[q], gn_d[q], gn_kend[q], gn_kend[q], gn_kend[q], 32, tn, nfl);
+        const GemmDescT<T>* dgf = tf.empty() ? nullptr : C.up(gf);
+        const TileRef* dtf = tf.empty() ? nullptr : C.up(tf);
+        const GemmDescT<T>* dgn = tn.empty() ? nullptr : C.up(gn);
+        const TileRef* dtn = tn.empty() ? nullptr : C.up(tn);
+        // the near update of this step writes block column k+1, which the far
+        // update of the previous step also writes: join it first
+        if (far_pending) {
+            ck(cudaStreamWaitEvent(sm, h->ev_far, 0));
+            far_pending = false;
+        }
+        if (!tf.empty()) {
+            ck(cudaEventRecord(h->ev_panel, sm));
+            ck(cudaStreamWaitEvent(ss, h->ev_panel, 0));
+            {
+                PScope ps(h, pk<T>(PK_GEMM, PK_GEMM_F32), ffl, 0.0, ss);
+                launch_gemm<T>(dgf, dtf, (int)tf.size(), tile, ss);
+            }
+            ck(cudaEventRecord(h->ev_far, ss));
+            far_pending = true;
+        }
+        if (!tn.empty()) {
+            PScope ps(h, pk<T>(PK_GEMM, PK_GEMM_F32), nfl);
+            launch_gemm<T>(dgn, dtn, (int)tn.size(), 32, sm);
         }
     }
+    if (far_pending) ck(cudaStreamWaitEvent(sm, h->ev_far, 0));
 }
 
 // Y = L^{-1} (lower triangular) for a batch, from the factors and the
@@ -577,9 +653,13 @@ void overlap_layers(const int64_t* rp, const int32_t* ci, const std::vector<int3
 // FP64 form, float for the mixed form (local factors, local solves, the SVD
 // of X_i, the splitting and the eigensolve in FP32; E, its factor and PCG in
 // FP64).
-template <typename T>
+// T: type of the local work (factors of A_ii, T = L_A^{-1} S L_A^{-T}, its
+// eigensolve, Z_i).  TS: type of the splitting (SVD of X_i, Abar_ii and its
+// Schur complement S).
+template <typename T, typename TS>
 void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     constexpr bool f64 = std::is_same<T, double>::value;
+    constexpr bool s64 = std::is_same<TS, double>::value;
     const int64_t n = A->n, nnz = A->nnz;
     const int N = h->N, ov = h->overlap;
     cudaStream_t s = h->s;
@@ -710,19 +790,19 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     double* Araw = C.tnew<double>(h->sum_sq);
     T* Lb = C.tnew<T>(h->sum_sq);
     double* Xp = C.tnew<double>(off_x[N]);
-    T* M = C.tnew<T>(off_m[N]);
+    TS* M = C.tnew<TS>(off_m[N]);
     T* TI = C.tnew<T>(off_ti[N]);
     T* Pb = C.tnew<T>(off_P[N]);
     double* sig = C.tnew<double>(h->sum_ni);
     double* mu = C.tnew<double>(h->sum_nI);
-    T* delta = C.tnew<T>(N);
+    TS* delta = C.tnew<TS>(N);
     T* linvA = C.tnew<T>(off_la[N]);
-    T* linvM = C.tnew<T>(off_lm[N]);
+    TS* linvM = C.tnew<TS>(off_lm[N]);
     // sweeps / rotations: [FP64 SVD, FP64 eig, FP32 SVD, FP32 eig] x N
     int* sweeps = C.tnew<int>(4 * N);
     unsigned long long* rots = C.tnew<unsigned long long>(4 * N);
     ck(cudaMemsetAsync(rots, 0, 4 * N * sizeof(unsigned long long), s));
-    T* nrmT = C.tnew<T>(h->sum_ni);
+    TS* nrmT = C.tnew<TS>(h->sum_ni);
     T* Yl = dnew<T>(h, h->sum_sq);   // L_i^{-1}
     T* Ylt = dnew<T>(h, h->sum_sq);  // L_i^{-T}
     if constexpr (f64) {
@@ -781,10 +861,10 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     // scaled by sigma_j^{-1/2}.
     // eps is the machine precision of the arithmetic (Sec. 3.2): the FP32
     // stage shifts by at least sigma_1 * 2^-23, above its own rounding.
-    if constexpr (!f64) h->eps = std::max(h->eps, (double)std::numeric_limits<float>::epsilon());
+    if constexpr (!s64) h->eps = std::max(h->eps, (double)std::numeric_limits<float>::epsilon());
     const double eps = h->eps;
-    T* X1 = C.tnew<T>(off_x[N]);
-    if constexpr (f64) {
+    TS* X1 = C.tnew<TS>(off_x[N]);
+    if constexpr (s64) {
         std::vector<int64_t> oq(N + 1, 0);
         for (int i = 0; i < N; ++i) oq[i + 1] = oq[i] + (int64_t)h->ni[i] * h->ni[i];
         double* Q = C.tnew<double>(oq[N]);
@@ -817,7 +897,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     }
 
     else {
-        // mixed form: FP32 one-sided Jacobi on the rows of X_i alone
+        // FP32 splitting: one-sided Jacobi on the rows of X_i alone
         launch_convert<double, float>(Xp, X1, off_x[N], s);
         std::vector<JacobiDescT<float>> jd(N);
         std::vector<double*> sp(N);
@@ -840,12 +920,12 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
 
     // ---- (3) Abar_ii = C^T diag(1/sigma) C + sigma_1 eps I, ordered [G, D, I]
     {
-        std::vector<GemmDescT<T>> g(N);
-        std::vector<T*> mats(N);
+        std::vector<GemmDescT<TS>> g(N);
+        std::vector<TS*> mats(N);
         std::vector<int> nn(N), ld(N);
         for (int i = 0; i < N; ++i) {
             const int ni = h->ni[i], nt = h->nt[i];
-            T* Xi = X1 + off_x[i];
+            TS* Xi = X1 + off_x[i];
             g[i] = gd(Xi, nt, 1, Xi, nt, 0, M + off_m[i], nt, nt, nt, ni, 1.0, 0.0, 1);
             mats[i] = M + off_m[i];
             nn[i] = nt;
@@ -856,13 +936,13 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         auto b = C.up(nn);
         auto c = C.up(ld);
         PScope ps(h, PK_SMALL);
-        launch_add_diag<T>(a, b, c, delta, N, h->max_nt, s);
+        launch_add_diag<TS>(a, b, c, delta, N, h->max_nt, s);
     }
 
     // ---- (4) Schur complement of Abar_ii onto Omega_Ii: Cholesky of the
     // leading [G, D] block (pivot floor sigma_1 eps, the shift of Remark 3.2).
     {
-        std::vector<CholDescT<T>> cd(N);
+        std::vector<CholDescT<TS>> cd(N);
         for (int i = 0; i < N; ++i) {
             const int nt = h->nt[i], nR = h->nG[i] + h->nD[i];
             cd[i] = {M + off_m[i], nt, nt, nR, delta + i, linvM + off_lm[i]};
@@ -872,19 +952,38 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
 
     // ---- (5) T = L_A^{-1} S L_A^{-T} (L_A = Cholesky factor of A_II, the
     // leading block of that of A_ii), appended identity for the rotations.
+    // With an FP64 splitting and FP32 local work, S is rounded to FP32 first.
     {
-        std::vector<T*> mats(N);
+        std::vector<TS*> mats(N);
         std::vector<int> nn(N), ld(N);
         std::vector<GemmDescT<T>> g1(N), g2(N);
         std::vector<TrtriDescT<T>> idd(N);
+        T* Sc = nullptr;
+        if constexpr (!std::is_same<T, TS>::value) Sc = C.tnew<T>(off_P[N]);
+        std::vector<const TS*> csrc(N);
+        std::vector<T*> cdst(N);
+        std::vector<int> cls(N), cld(N);
         for (int i = 0; i < N; ++i) {
             const int nIi = h->nI[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], ni = h->ni[i];
-            T* S = M + off_m[i] + (size_t)nR * nt + nR;
+            TS* S = M + off_m[i] + (size_t)nR * nt + nR;
             mats[i] = S;
             nn[i] = nIi;
             ld[i] = nt;
             const T* Y = Yl + h->off_sq[i];
-            g1[i] = gd(Y, ni, 0, S, nt, 0, Pb + off_P[i], nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
+            const T* Sl;
+            int lds;
+            if constexpr (std::is_same<T, TS>::value) {
+                Sl = S;
+                lds = nt;
+            } else {
+                Sl = Sc + off_P[i];
+                lds = nIi;
+            }
+            csrc[i] = S;
+            cdst[i] = Sc ? Sc + off_P[i] : nullptr;
+            cls[i] = nt;
+            cld[i] = nIi;
+            g1[i] = gd(Y, ni, 0, Sl, lds, 0, Pb + off_P[i], nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
             g2[i] = gd(Pb + off_P[i], nIi, 0, Y, ni, 1, TI + off_ti[i], 2 * nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
             idd[i] = {nullptr, TI + off_ti[i] + nIi, nullptr, nIi, 0, 2 * nIi};
         }
@@ -893,7 +992,16 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             auto b = C.up(nn);
             auto c = C.up(ld);
             PScope ps(h, PK_SMALL);
-            launch_mirror_lower<T>(a, b, c, N, h->max_nt, s);
+            launch_mirror_lower<TS>(a, b, c, N, h->max_nt, s);
+        }
+        if constexpr (!std::is_same<T, TS>::value) {
+            auto a = C.up(csrc);
+            auto b = C.up(cls);
+            auto c = C.up(cdst);
+            auto d = C.up(cld);
+            auto e = C.up(nn);
+            PScope ps(h, PK_SMALL);
+            launch_convert_blocks<TS, T>(a, b, c, d, e, N, h->max_nt, s);
         }
         gemm(C, g1);
         gemm(C, g2);
@@ -1025,10 +1133,11 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             std::vector<JacobiDescT<T>> jd(np);
             std::vector<double*> mp(np);
             double* mu_j = C.tnew<double>(h->sum_nI);
+            T* nrmE = C.tnew<T>(h->sum_nI);  // row norms of the eigen-Jacobi
             int maxc = 1;
             for (int q = 0; q < np; ++q) {
                 const int i = partial[q], nIi = h->nI[i];
-                jd[q] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrmT + h->off_om[i], nullptr};
+                jd[q] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrmE + h->off_I[i], nullptr};
                 mp[q] = mu_j + h->off_I[i];
                 maxc = std::max(maxc, nIi);
             }
@@ -1243,7 +1352,6 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             h->d_yloc32 = ylocT;
         }
         h->d_c = dnew<double>(h, nC);
-        h->d_ct = dnew<double>(h, nC);
         h->d_e = dnew<double>(h, nC);
         std::vector<int32_t> rd, rl, rdc, rlc;
         rd.reserve(h->sum_ni);
@@ -1275,52 +1383,25 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         h->d_rl_loc = C.up(rl, true);
         h->d_rd_c = C.up(rdc, true);
         h->d_rl_c = C.up(rlc, true);
-        // coarse solve L_E L_E^T e = c: forward steps (t_k = c_k - L_{k,<k} y_<k,
-        // y_k = Y_kk t_k), then backward steps (t_k = y_k - (L^T)_{k,>k} e_>k,
-        // e_k = Y_kk^T t_k), one row-GEMV launch each.
+        // coarse solve L_E L_E^T e = c: blocked forward / backward substitution
+        // with the stored inverses of the diagonal blocks, one cooperative
+        // launch (profile figures: the envelope of L_E and L_E^T, the diagonal
+        // inverses, once each)
         if (nC > 0) {
             h->d_ctmp = dnew<double>(h, nC);
             h->d_env_row = C.up(h->env_row, true);
             h->d_env_colend = C.up(h->env_colend, true);
+            h->coop_blocks = coarse_solve_blocks();
+            if (h->coop_blocks <= 0) throw Fail{AMDD_ERR_CUDA};
             const int SB = h->cSB, K = h->cK;
-            std::vector<GemvDesc> cd;
-            h->csteps.clear();
-            auto add = [&](GemvDesc g, double fl, double by) {
-                cd.push_back(g);
-                h->csteps.push_back({g.rows, fl, by});
-            };
+            double el = 0.0, dl = 0.0;
+            for (int64_t r = 0; r < nC; ++r) el += (double)(r - h->env_row[r]) + (double)(h->env_colend[r] - 1 - r);
             for (int k = 0; k < K; ++k) {
-                const int r0 = k * SB, sb = (int)std::min<int64_t>(SB, nC - r0);
-                GemvDesc f1{h->d_YE + (size_t)r0 * nC, sb, r0, (int)nC, 0, h->d_ct, h->d_ctmp + r0};
-                f1.b = h->d_c + r0;
-                f1.alpha = -1.0;
-                f1.cstart = h->d_env_row + r0;
-                double el = 0.0;
-                for (int r = r0; r < r0 + sb; ++r) el += std::max(0, r0 - h->env_row[r]);
-                add(f1, 2.0 * el, 8.0 * el);
-                GemvDesc f2{h->d_Yd + (size_t)k * SB * SB, sb, sb, SB, 1, h->d_ctmp + r0, h->d_ct + r0};
-                add(f2, 1.0 * sb * (sb + 1), 4.0 * sb * (sb + 1));
+                const double sb = (double)std::min<int64_t>(SB, nC - (int64_t)k * SB);
+                dl += sb * (sb + 1);
             }
-            for (int k = K - 1; k >= 0; --k) {
-                const int r0 = k * SB, sb = (int)std::min<int64_t>(SB, nC - r0);
-                const int rest = (int)(nC - r0 - sb);
-                GemvDesc b1{h->d_YEt + (size_t)r0 * nC + r0 + sb, sb, rest, (int)nC, 0, h->d_e + r0 + sb,
-                            h->d_ctmp + r0};
-                b1.b = h->d_ct + r0;
-                b1.alpha = -1.0;
-                b1.cend = h->d_env_colend + r0;
-                b1.coff = r0 + sb;
-                double el = 0.0;
-                for (int r = r0; r < r0 + sb; ++r) el += std::max(0, h->env_colend[r] - (r0 + sb));
-                add(b1, 2.0 * el, 8.0 * el);
-                GemvDesc b2{h->d_Ydt + (size_t)k * SB * SB, sb, sb, SB, 2, h->d_ctmp + r0, h->d_e + r0};
-                add(b2, 1.0 * sb * (sb + 1), 4.0 * sb * (sb + 1));
-            }
-            h->d_gv_e1 = C.up(cd, true);
-            std::vector<int32_t> rde(SB, 0), rle(SB);
-            std::iota(rle.begin(), rle.end(), 0);
-            h->d_rd_e = C.up(rde, true);
-            h->d_rl_e = C.up(rle, true);
+            h->csolve_flops = 2.0 * el + 2.0 * dl;
+            h->csolve_bytes = 8.0 * el + 8.0 * dl + 8.0 * 6.0 * nC;
         }
         // prolongation: copies of each unknown in subdomain order, owners
         std::vector<int64_t> scp(n + 1, 0);
@@ -1394,10 +1475,11 @@ void apply_one(amdd_handle* h, const double* r, double* z) {
             PScope ps(h, PK_GEMV, 2.0 * zt, 8.0 * zt + 8.0 * h->sum_ni + 16.0 * h->nC);
             launch_gemv_rows<double>(h->d_gv_c, h->d_rd_c, h->d_rl_c, h->nC, s);
         }
-        for (size_t j = 0; j < h->csteps.size(); ++j) {
-            const auto& st = h->csteps[j];
-            PScope ps(h, PK_GEMV, st.flops, st.bytes);
-            launch_gemv_rows<double>(h->d_gv_e1 + j, h->d_rd_e, h->d_rl_e, st.rows, s);
+        {
+            CoarseSolveArgs a{h->d_YE, h->d_YEt, h->d_Yd, h->d_Ydt, h->d_env_row, h->d_env_colend,
+                              h->d_c, h->d_ctmp, h->d_e, (int)h->nC, (int)h->nC, h->cSB, h->cK};
+            PScope ps(h, PK_CSOLVE, h->csolve_flops, h->csolve_bytes);
+            ck(launch_coarse_solve(a, h->coop_blocks, s));
         }
     }
     PScope ps(h, PK_GATHER_SCATTER, 2.0 * h->sum_zt, 8.0 * h->sum_zt + 12.0 * h->sum_ni + 24.0 * h->n);
@@ -1505,7 +1587,7 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
     amdd_opts_default(&o);
     if (opts) {
         o = *opts;
-        if (!(o.eps > 0.0) || o.max_sweeps < 1 || (o.precision != 0 && o.precision != 1)) return AMDD_ERR_INVALID;
+        if (!(o.eps > 0.0) || o.max_sweeps < 1 || o.precision < 0 || o.precision > 2) return AMDD_ERR_INVALID;
         for (int k = 0; k < 4; ++k)
             if (o.reserved[k] != 0) return AMDD_ERR_INVALID;
         if (o.profile_classes >> PK_COUNT) return AMDD_ERR_INVALID;
@@ -1515,6 +1597,9 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
     try {
         h = new amdd_handle();
         h->s = static_cast<cudaStream_t>(stream);
+        ck(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
+        ck(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
+        ck(cudaEventCreateWithFlags(&h->ev_far, cudaEventDisableTiming));
         h->n = A->n;
         h->nnz = A->nnz;
         h->N = N;
@@ -1526,9 +1611,11 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         h->prof.mask = o.profile_classes ? o.profile_classes : ~0u;
         h->precision = o.precision;
         if (o.precision == 0)
-            do_setup<double>(h, A, part);
+            do_setup<double, double>(h, A, part);
+        else if (o.precision == 1)
+            do_setup<float, float>(h, A, part);
         else
-            do_setup<float>(h, A, part);
+            do_setup<float, double>(h, A, part);
         ck(cudaStreamSynchronize(h->s));
     } catch (...) {
         const amdd_status st = guard_exc();
@@ -1817,7 +1904,11 @@ amdd_status amdd_reset_profile(amdd_handle* h) {
 
 void amdd_destroy(amdd_handle* h) {
     if (!h) return;
+    if (h->s2) cudaStreamSynchronize(h->s2);
     cudaStreamSynchronize(h->s);
+    if (h->ev_panel) cudaEventDestroy(h->ev_panel);
+    if (h->ev_far) cudaEventDestroy(h->ev_far);
+    if (h->s2) cudaStreamDestroy(h->s2);
     h->prof.release();
     for (void* p : h->allocs) cudaFreeAsync(p, h->s);
     cudaStreamSynchronize(h->s);

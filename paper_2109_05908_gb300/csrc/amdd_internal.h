@@ -19,6 +19,7 @@ enum : int {
 
 constexpr int CHOL_NB = 32;     // diagonal block of the blocked Cholesky / inverse
 constexpr int GEMM_T = 64;      // GEMM output tile
+constexpr int PANEL_ROWS = 16;  // rows per CTA of the Cholesky panel solve
 constexpr int JAC_CLUSTER = 8;  // CTAs per matrix in the Jacobi solvers
 constexpr int JAC_MAX_PAIRS = 64;  // largest sub-round of the shared-memory block Jacobi
 
@@ -58,7 +59,7 @@ struct CholDescT {
 using CholDesc = CholDescT<double>;
 
 struct PanelRef {
-    int desc, rt;  // row tile index (64 rows) below the diagonal block
+    int desc, rt;  // row tile index (PANEL_ROWS rows) below the diagonal block
 };
 
 template <typename T>
@@ -121,7 +122,7 @@ struct GemvDescT {
 using GemvDesc = GemvDescT<double>;
 
 template <typename T>
-void launch_gemm(const GemmDescT<T>* d_descs, const TileRef* d_tiles, int ntiles, cudaStream_t s);
+void launch_gemm(const GemmDescT<T>* d_descs, const TileRef* d_tiles, int ntiles, int tile, cudaStream_t s);
 template <typename T>
 void launch_chol_diag(const CholDescT<T>* d, int nmat, int k0, int* err, cudaStream_t s);
 template <typename T>
@@ -168,6 +169,9 @@ void launch_bisect(const TridiagDescT<T>* d, int nmat, const int* eig_mat, const
 // dst[i] = (To)src[i]
 template <typename Ti, typename To>
 void launch_convert(const Ti* src, To* dst, int64_t n, cudaStream_t s);
+template <typename Ti, typename To>
+void launch_convert_blocks(const Ti* const* src, const int* lds, To* const* dst, const int* ldd, const int* n,
+                           int nmat, int maxn, cudaStream_t s);
 
 // ---------------------------------------------------------------- sparse / vectors
 void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
@@ -197,6 +201,22 @@ void launch_e_offdiag(const EPairRef* tiles, int ntiles, const int32_t* la, cons
 // Deterministic dot products: fixed grid of DOT_BLOCKS partial sums reduced in
 // a fixed order by one block.
 constexpr int DOT_BLOCKS = 264;
+// Coarse solve L_E L_E^T e = c (one cooperative launch; c is overwritten).
+struct CoarseSolveArgs {
+    const double* L;       // factor, n x n row-major (lower), leading dimension ld
+    const double* Lt;      // its transpose, row-major
+    const double* Yd;      // K inverses of the SB x SB diagonal blocks (lower), SB x SB each
+    const double* Ydt;     // their transposes
+    const int* env_row;    // first non-zero column of row r of L
+    const int* env_colend; // one past the last non-zero row of column r of L
+    double* c;             // right-hand side, overwritten
+    double* y;             // work (n)
+    double* e;             // solution (n)
+    int n, ld, SB, K;
+};
+int coarse_solve_blocks();  // cooperative grid size for this device (0 on error)
+cudaError_t launch_coarse_solve(const CoarseSolveArgs& a, int blocks, cudaStream_t s);
+
 struct PcgScal {
     double rz, pq, rr, bb, alpha, beta, rz_new;
     int conv, iters;

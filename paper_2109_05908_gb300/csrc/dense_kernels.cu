@@ -17,42 +17,50 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
 // ------------------------------------------------------------------ GEMM
-// 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread, k
-// staged through shared memory 16 at a time, FMA in the element type.
+// TILE x TILE output tile per CTA, RM x 4 outputs per thread (threads =
+// TILE/RM x TILE/4), k staged through shared memory 16 at a time, FMA in the
+// element type.  TILE = 64 (4 x 4 per thread, 256 threads) for wide batches;
+// TILE = 32 (2 x 4 per thread, 128 threads) gives four times as many CTAs
+// when one launch would not fill the SMs (the coarse factorisation), with
+// four warps per CTA so each SM sub-partition has one to issue from.
 constexpr int GK = 16;
 
-template <typename T>
-__global__ void __launch_bounds__(256) gemm_tiles_kernel(const GemmDescT<T>* __restrict__ descs,
-                                                          const TileRef* __restrict__ tiles, int ntiles) {
+template <typename T, int TILE, int RM>
+__global__ void __launch_bounds__((TILE / RM) * (TILE / 4)) gemm_tiles_kernel(const GemmDescT<T>* __restrict__ descs,
+                                                                              const TileRef* __restrict__ tiles,
+                                                                              int ntiles) {
+    constexpr int TX = TILE / 4;   // threads along a tile row (4 columns each)
+    constexpr int TY = TILE / RM;  // threads along a tile column (RM rows each)
+    constexpr int NT = TX * TY;
     const int t = blockIdx.x;
     if (t >= ntiles) return;
     const TileRef tr = tiles[t];
     const GemmDescT<T> d = descs[tr.desc];
-    __shared__ T As[GK][GEMM_T + 1];
-    __shared__ T Bs[GK][GEMM_T + 1];
+    __shared__ T As[GK][TILE + 1];
+    __shared__ T Bs[GK][TILE + 1];
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
-    const int row0 = tr.tm * GEMM_T, col0 = tr.tn * GEMM_T;
-    T acc[4][4];
+    const int tx = tid % TX, ty = tid / TX;
+    const int row0 = tr.tm * TILE, col0 = tr.tn * TILE;
+    T acc[RM][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
     int kbeg = 0;
     if (d.kfrom_row) kbeg = (row0 / GK) * GK;
     for (int k0 = kbeg; k0 < d.k; k0 += GK) {
-        for (int e = tid; e < GEMM_T * GK; e += 256) {
+        for (int e = tid; e < TILE * GK; e += NT) {
             int r, kk;
-            if (!d.ta) { r = e / GK; kk = e % GK; } else { kk = e / GEMM_T; r = e % GEMM_T; }
+            if (!d.ta) { r = e / GK; kk = e % GK; } else { kk = e / TILE; r = e % TILE; }
             const int gr = row0 + r, gk = k0 + kk;
             T v = T(0);
             if (gr < d.m && gk < d.k)
                 v = d.ta ? d.A[(size_t)gk * d.lda + gr] : d.A[(size_t)gr * d.lda + gk];
             As[kk][r] = v;
         }
-        for (int e = tid; e < GEMM_T * GK; e += 256) {
+        for (int e = tid; e < TILE * GK; e += NT) {
             int c, kk;
-            if (!d.tb) { kk = e / GEMM_T; c = e % GEMM_T; } else { c = e / GK; kk = e % GK; }
+            if (!d.tb) { kk = e / TILE; c = e % TILE; } else { c = e / GK; kk = e % GK; }
             const int gc = col0 + c, gk = k0 + kk;
             T v = T(0);
             if (gc < d.n && gk < d.k)
@@ -62,25 +70,25 @@ __global__ void __launch_bounds__(256) gemm_tiles_kernel(const GemmDescT<T>* __r
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            T a[4], b[4];
+            T a[RM], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + TY * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + TX * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RM; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = row0 + ty + 16 * i;
+    for (int i = 0; i < RM; ++i) {
+        const int r = row0 + ty + TY * i;
         if (r >= d.m) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int c = col0 + tx + 16 * j;
+            const int c = col0 + tx + TX * j;
             if (c >= d.n || (d.lower && c > r)) continue;
             T* cp = d.C + (size_t)r * d.ldc + c;
             const T v = d.alpha * acc[i][j];
@@ -90,11 +98,15 @@ __global__ void __launch_bounds__(256) gemm_tiles_kernel(const GemmDescT<T>* __r
 }
 
 template <typename T>
-void launch_gemm(const GemmDescT<T>* d_descs, const TileRef* d_tiles, int ntiles, cudaStream_t s) {
-    if (ntiles > 0) gemm_tiles_kernel<T><<<ntiles, 256, 0, s>>>(d_descs, d_tiles, ntiles);
+void launch_gemm(const GemmDescT<T>* d_descs, const TileRef* d_tiles, int ntiles, int tile, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    if (tile == 32)
+        gemm_tiles_kernel<T, 32, 2><<<ntiles, 128, 0, s>>>(d_descs, d_tiles, ntiles);
+    else
+        gemm_tiles_kernel<T, 64, 4><<<ntiles, 256, 0, s>>>(d_descs, d_tiles, ntiles);
 }
-template void launch_gemm<float>(const GemmDescT<float>*, const TileRef*, int, cudaStream_t);
-template void launch_gemm<double>(const GemmDescT<double>*, const TileRef*, int, cudaStream_t);
+template void launch_gemm<float>(const GemmDescT<float>*, const TileRef*, int, int, cudaStream_t);
+template void launch_gemm<double>(const GemmDescT<double>*, const TileRef*, int, int, cudaStream_t);
 
 // ------------------------------------------------------------------ Cholesky
 // Factor the NB x NB diagonal block [k0, k0+kb) of each matrix in shared
@@ -103,59 +115,114 @@ template void launch_gemm<double>(const GemmDescT<double>*, const TileRef*, int,
 // factor.  With a pivot floor (clamp) a pivot below it is raised to it;
 // without, a pivot <= 0 (or NaN) latches DERR_NOT_SPD and is replaced by 1 so
 // the factorisation finishes with finite numbers.
+//
+// Column j keeps its unscaled entries a_rj; the update of step j is
+// a_rc -= a_rj a_cj / d_j over the active lower triangle j < c <= r, listed
+// by a table whose active part is a prefix at every step (columns in
+// descending order).  The thread that updates the next pivot also takes its
+// reciprocal square root, so one barrier per column suffices.  The inverse of
+// the factor is formed blockwise: four 8 x 8 diagonal inverses, then two
+// levels of [A 0; B C]^{-1} = [A^{-1} 0; -C^{-1} B A^{-1}  C^{-1}].
+constexpr int DIAG_THREADS = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(256) chol_diag_kernel(const CholDescT<T>* __restrict__ descs, int k0,
-                                                         int* __restrict__ err) {
+__global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(const CholDescT<T>* __restrict__ descs, int k0,
+                                                                  int* __restrict__ err) {
     const CholDescT<T> d = descs[blockIdx.x];
     const int kend = min(k0 + CHOL_NB, d.stop);
     if (k0 >= kend) return;
     const int kb = kend - k0;
-    __shared__ T L[CHOL_NB][CHOL_NB + 1];
-    __shared__ T Li[CHOL_NB][CHOL_NB + 1];
-    __shared__ T dinv[CHOL_NB];  // 1 / L[j][j]
+    __shared__ T L[CHOL_NB][CHOL_NB + 1];   // working entries; the factor F overwrites column j after step j
+    __shared__ T Li[CHOL_NB][CHOL_NB + 1];  // inverse of the factor
+    __shared__ T Xs[CHOL_NB][CHOL_NB + 1];  // products of the blocked inverse
+    __shared__ T piv[CHOL_NB];              // pivot d_j (after clamping)
+    __shared__ T rinv[CHOL_NB];             // 1 / sqrt(d_j)
+    __shared__ unsigned short tab[CHOL_NB * (CHOL_NB + 1) / 2];
     const int tid = threadIdx.x;
-    for (int e = tid; e < CHOL_NB * CHOL_NB; e += blockDim.x) {
-        const int r = e / CHOL_NB, c = e % CHOL_NB;
-        L[r][c] = (r < kb && c <= r) ? d.A[(size_t)(k0 + r) * d.ld + (k0 + c)] : T(0);
-        Li[r][c] = T(0);
-    }
-    __syncthreads();
     const T floor_v = d.clamp ? *d.clamp : T(0);
-    for (int j = 0; j < kb; ++j) {
-        if (tid == 0) {
-            T piv = L[j][j];
-            if (d.clamp) {
-                if (!(piv >= floor_v)) piv = floor_v;
-            } else if (!(piv > T(0))) {
-                atomicOr(err, DERR_NOT_SPD);
-                piv = T(1);
-            }
-            // one reciprocal square root per pivot: L_jj = piv / sqrt(piv)
-            const T r = rsqrt_t(piv);
-            L[j][j] = piv * r;
-            dinv[j] = r;
-        }
-        __syncthreads();
-        if (tid > j && tid < kb) L[tid][j] *= dinv[j];
-        __syncthreads();
-        for (int e = tid; e < CHOL_NB * CHOL_NB; e += blockDim.x) {
-            const int r = e / CHOL_NB, c = e % CHOL_NB;
-            if (c > j && r >= c && r < kb) L[r][c] = fma(-L[r][j], L[c][j], L[r][c]);
-        }
-        __syncthreads();
-    }
-    // inverse of the lower-triangular block, one column per thread
-    if (tid < kb) {
-        const int c = tid;
-        for (int r = c; r < kb; ++r) {
-            T s = (r == c) ? T(1) : T(0);
-            for (int k = c; k < r; ++k) s = fma(-L[r][k], Li[k][c], s);
-            Li[r][c] = s * dinv[r];
+    // padded to NB: rows / columns >= kb are the identity
+    for (int e = tid; e < CHOL_NB * CHOL_NB; e += DIAG_THREADS) {
+        const int r = e / CHOL_NB, c = e % CHOL_NB;
+        T v = T(0);
+        if (r < kb && c <= r) v = d.A[(size_t)(k0 + r) * d.ld + (k0 + c)];
+        else if (r == c) v = T(1);
+        L[r][c] = v;
+        if (c <= r && r < kb) {
+            const int q = kb - 1 - c;
+            tab[q * (q + 1) / 2 + (r - c)] = (unsigned short)((r << 8) | c);
         }
     }
     __syncthreads();
+    auto take_pivot = [&](int j, T a) {
+        T p = a;
+        if (d.clamp) {
+            if (!(p >= floor_v)) p = floor_v;
+        } else if (!(p > T(0))) {
+            atomicOr(err, DERR_NOT_SPD);
+            p = T(1);
+        }
+        piv[j] = p;
+        rinv[j] = rsqrt_t(p);
+    };
+    if (tid == 0) take_pivot(0, L[0][0]);
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        const T rj = rinv[j];
+        const T s = rj * rj;
+        const int m = (kb - 1 - j) * (kb - j) / 2;
+        for (int e = tid; e < m; e += DIAG_THREADS) {
+            const int rc = tab[e];
+            const int r = rc >> 8, c = rc & 255;
+            const T v = fma(-(L[r][j] * s), L[c][j], L[r][c]);
+            L[r][c] = v;
+            if (r == j + 1 && c == j + 1) take_pivot(j + 1, v);
+        }
+        __syncthreads();
+        // column j of the factor (entries below the diagonal are not read again)
+        if (tid < kb - j) {
+            const int r = j + tid;
+            L[r][j] = (r == j) ? piv[j] * rj : L[r][j] * rj;
+        }
+    }
+    for (int r = kb + tid; r < CHOL_NB; r += DIAG_THREADS) rinv[r] = T(1);
+    __syncthreads();
+    // ---- inverse of the factor, blockwise
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < CHOL_NB * CHOL_NB; e += DIAG_THREADS) Li[e / CHOL_NB][e % CHOL_NB] = T(0);
+    __syncthreads();
+    if (lane < 8) {  // warp w inverts the 8 x 8 diagonal block w, one column per lane
+        const int b0 = warp * 8, c = b0 + lane;
+        for (int r = c; r < b0 + 8; ++r) {
+            T acc = (r == c) ? T(1) : T(0);
+            for (int k = c; k < r; ++k) acc = fma(-L[r][k], Li[k][c], acc);
+            Li[r][c] = acc * rinv[r];
+        }
+    }
+    __syncthreads();
+    for (int w = 8; w < CHOL_NB; w *= 2) {
+        // pairs of w x w diagonal blocks [A 0; B C] at offsets o = 0, 2w, ...
+        const int npairs = CHOL_NB / (2 * w);
+        // X = B A^{-1}  (w x w per pair)
+        for (int e = tid; e < npairs * w * w; e += DIAG_THREADS) {
+            const int pr = e / (w * w), rr = (e / w) % w, cc = e % w;
+            const int o = pr * 2 * w;
+            T acc = T(0);
+            for (int k = cc; k < w; ++k) acc = fma(L[o + w + rr][o + k], Li[o + k][o + cc], acc);
+            Xs[o + w + rr][o + cc] = acc;
+        }
+        __syncthreads();
+        // lower-left block = -C^{-1} X
+        for (int e = tid; e < npairs * w * w; e += DIAG_THREADS) {
+            const int pr = e / (w * w), rr = (e / w) % w, cc = e % w;
+            const int o = pr * 2 * w;
+            T acc = T(0);
+            for (int k = 0; k <= rr; ++k) acc = fma(Li[o + w + rr][o + w + k], Xs[o + w + k][o + cc], acc);
+            Li[o + w + rr][o + cc] = -acc;
+        }
+        __syncthreads();
+    }
     T* linv = d.Linv + (size_t)(k0 / CHOL_NB) * CHOL_NB * CHOL_NB;
-    for (int e = tid; e < CHOL_NB * CHOL_NB; e += blockDim.x) {
+    for (int e = tid; e < CHOL_NB * CHOL_NB; e += DIAG_THREADS) {
         const int r = e / CHOL_NB, c = e % CHOL_NB;
         if (r < kb && c <= r) d.A[(size_t)(k0 + r) * d.ld + (k0 + c)] = L[r][c];
         linv[e] = (r < kb && c < kb) ? Li[r][c] : T(0);
@@ -164,13 +231,13 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(const CholDescT<T>* __re
 
 template <typename T>
 void launch_chol_diag(const CholDescT<T>* d, int nmat, int k0, int* err, cudaStream_t s) {
-    if (nmat > 0) chol_diag_kernel<T><<<nmat, 256, 0, s>>>(d, k0, err);
+    if (nmat > 0) chol_diag_kernel<T><<<nmat, DIAG_THREADS, 0, s>>>(d, k0, err);
 }
 template void launch_chol_diag<float>(const CholDescT<float>*, int, int, int*, cudaStream_t);
 template void launch_chol_diag<double>(const CholDescT<double>*, int, int, int*, cudaStream_t);
 
 // Panel below the diagonal block: A[r, k0:k0+kb] <- A[r, k0:k0+kb] * Linv^T
-// for 64 rows per CTA.
+// for PANEL_ROWS rows per CTA.
 template <typename T>
 __global__ void __launch_bounds__(256) chol_panel_kernel(const CholDescT<T>* __restrict__ descs,
                                                           const PanelRef* __restrict__ tiles, int k0) {
@@ -178,20 +245,21 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(const CholDescT<T>* __r
     const CholDescT<T> d = descs[t.desc];
     const int kend = min(k0 + CHOL_NB, d.stop);
     const int kb = kend - k0;
-    const int r0 = kend + t.rt * 64;
+    const int r0 = kend + t.rt * PANEL_ROWS;
     __shared__ T Li[CHOL_NB][CHOL_NB + 1];
-    __shared__ T P[64][CHOL_NB + 1];
+    __shared__ T P[PANEL_ROWS][CHOL_NB + 1];
     const T* linv = d.Linv + (size_t)(k0 / CHOL_NB) * CHOL_NB * CHOL_NB;
     const int tid = threadIdx.x;
     for (int e = tid; e < CHOL_NB * CHOL_NB; e += 256) Li[e / CHOL_NB][e % CHOL_NB] = linv[e];
-    for (int e = tid; e < 64 * CHOL_NB; e += 256) {
+    for (int e = tid; e < PANEL_ROWS * CHOL_NB; e += 256) {
         const int r = e / CHOL_NB, c = e % CHOL_NB;
         const int gr = r0 + r;
         P[r][c] = (gr < d.n && c < kb) ? d.A[(size_t)gr * d.ld + (k0 + c)] : T(0);
     }
     __syncthreads();
-    for (int e = tid; e < 64 * CHOL_NB; e += 256) {
-        const int r = e / CHOL_NB, c = e % CHOL_NB;
+    // lanes run over rows so the loop length (c + 1) is uniform in a warp
+    for (int e = tid; e < PANEL_ROWS * CHOL_NB; e += 256) {
+        const int c = e / PANEL_ROWS, r = e % PANEL_ROWS;
         const int gr = r0 + r;
         if (c < kb && gr < d.n) {
             T s = T(0);
@@ -812,6 +880,29 @@ void launch_convert(const Ti* src, To* dst, int64_t n, cudaStream_t s) {
 template void launch_convert<float, double>(const float*, double*, int64_t, cudaStream_t);
 template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
 
+// dst_b[r * ldd_b + c] = (To) src_b[r * lds_b + c] for r, c < n_b (batch b = blockIdx.y)
+template <typename Ti, typename To>
+__global__ void convert_blocks_kernel(const Ti* const* __restrict__ src, const int* __restrict__ lds,
+                                      To* const* __restrict__ dst, const int* __restrict__ ldd,
+                                      const int* __restrict__ n) {
+    const int b = blockIdx.y;
+    const int nn = n[b];
+    const Ti* S = src[b];
+    To* D = dst[b];
+    for (int r = blockIdx.x; r < nn; r += gridDim.x)
+        for (int c = threadIdx.x; c < nn; c += blockDim.x) D[(size_t)r * ldd[b] + c] = (To)S[(size_t)r * lds[b] + c];
+}
+
+template <typename Ti, typename To>
+void launch_convert_blocks(const Ti* const* src, const int* lds, To* const* dst, const int* ldd, const int* n,
+                           int nmat, int maxn, cudaStream_t s) {
+    if (nmat <= 0 || maxn <= 0) return;
+    dim3 grid(min(maxn, 1024), nmat);
+    convert_blocks_kernel<Ti, To><<<grid, 256, 0, s>>>(src, lds, dst, ldd, n);
+}
+template void launch_convert_blocks<double, float>(const double* const*, const int*, float* const*, const int*,
+                                                   const int*, int, int, cudaStream_t);
+
 // ------------------------------------------------------------------ tridiagonal eigenvalues
 // Householder reduction of a symmetric n x n matrix (full storage, updated in
 // place) to tridiagonal form T = Q^T A Q, one CTA per matrix: at step k the
@@ -1099,5 +1190,96 @@ void launch_gemv_rows(const GemvDescT<T>* d, const int* row_desc, const int* row
 }
 template void launch_gemv_rows<float>(const GemvDescT<float>*, const int*, const int*, int64_t, cudaStream_t);
 template void launch_gemv_rows<double>(const GemvDescT<double>*, const int*, const int*, int64_t, cudaStream_t);
+
+// ------------------------------------------------------------------ coarse solve
+// L_E L_E^T e = c by blocked substitution in one cooperative launch.  The
+// factor is split into K diagonal blocks of SB rows whose inverses Y_kk are
+// stored.  Forward, for k = 0..K-1: y_k = Y_kk t_k (t = c, updated in
+// place), then every later row r subtracts L[r, block k] y_k.  Backward, for
+// k = K-1..0: e_k = Y_kk^T y_k, then every earlier row r subtracts
+// (L^T)[r, block k] e_k.  Each phase spreads its rows over all warps of the
+// grid (one warp per row, lane-strided products, fixed shuffle tree), and a
+// grid-wide barrier separates the phases; rows outside the envelope of L_E
+// (first column env_row[r], column r ends at env_colend[r]) are skipped.
+// One CTA of 1024 threads per SM keeps the barrier to one arrival per SM.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int CSOLVE_THREADS = 1024;
+
+__global__ void __launch_bounds__(CSOLVE_THREADS) coarse_solve_kernel(CoarseSolveArgs a) {
+    cg::grid_group grid = cg::this_grid();
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const int n = a.n, SB = a.SB, K = a.K;
+    double* t = a.c;
+    for (int k = 0; k < K; ++k) {
+        const int r0 = k * SB, sb = min(SB, n - r0), r1 = r0 + sb;
+        const double* Y = a.Yd + (size_t)k * SB * SB;
+        for (int i = gw; i < sb; i += nw) {
+            const double* row = Y + (size_t)i * SB;
+            double s = 0.0;
+            for (int j = lane; j <= i; j += 32) s = fma(row[j], t[r0 + j], s);
+            s = warp_sum_d(s);
+            if (lane == 0) a.y[r0 + i] = s;
+        }
+        grid.sync();
+        if (k + 1 == K) break;
+        for (int r = r1 + gw; r < n; r += nw) {
+            const int j0 = max(a.env_row[r], r0);
+            if (j0 >= r1) continue;
+            const double* row = a.L + (size_t)r * a.ld;
+            double s = 0.0;
+            for (int j = j0 + lane; j < r1; j += 32) s = fma(row[j], a.y[j], s);
+            s = warp_sum_d(s);
+            if (lane == 0) t[r] -= s;
+        }
+        grid.sync();
+    }
+    for (int k = K - 1; k >= 0; --k) {
+        const int r0 = k * SB, sb = min(SB, n - r0), r1 = r0 + sb;
+        const double* Yt = a.Ydt + (size_t)k * SB * SB;
+        for (int i = gw; i < sb; i += nw) {
+            const double* row = Yt + (size_t)i * SB;
+            double s = 0.0;
+            for (int j = i + lane; j < sb; j += 32) s = fma(row[j], a.y[r0 + j], s);
+            s = warp_sum_d(s);
+            if (lane == 0) a.e[r0 + i] = s;
+        }
+        if (k == 0) break;
+        grid.sync();
+        for (int r = gw; r < r0; r += nw) {
+            const int j1 = min(a.env_colend[r], r1);
+            if (j1 <= r0) continue;
+            const double* row = a.Lt + (size_t)r * a.ld;
+            double s = 0.0;
+            for (int j = r0 + lane; j < j1; j += 32) s = fma(row[j], a.e[j], s);
+            s = warp_sum_d(s);
+            if (lane == 0) a.y[r] -= s;
+        }
+        grid.sync();
+    }
+}
+
+int coarse_solve_blocks() {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, coarse_solve_kernel, CSOLVE_THREADS, 0) != cudaSuccess)
+        return 0;
+    // one CTA per SM: the grid barriers between phases then take one arrival per SM
+    return per >= 1 ? sms : 0;
+}
+
+cudaError_t launch_coarse_solve(const CoarseSolveArgs& a, int blocks, cudaStream_t s) {
+    CoarseSolveArgs arg = a;
+    void* params[] = {&arg};
+    return cudaLaunchCooperativeKernel((const void*)coarse_solve_kernel, dim3(blocks), dim3(CSOLVE_THREADS), params, 0,
+                                       s);
+}
 
 }  // namespace amdd

@@ -145,6 +145,96 @@ def diffusion3d(m: int, sigma: float = 2.0, corr: float = 8.0, n_channels: int =
     return _csr_from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
 
 
+def _q1_elasticity_stiffness(nu: float) -> np.ndarray:
+    """24 x 24 stiffness of a unit-cube trilinear (Q1) hexahedron for isotropic
+    linear elasticity with Young's modulus 1 and Poisson ratio nu, by 2x2x2
+    Gauss quadrature.  Local node a = (ax, ay, az) in {0,1}^3 has index
+    ax + 2 ay + 4 az; dof 3a + component."""
+    lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = 1.0 / (2.0 * (1.0 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[np.arange(3), np.arange(3)] += 2.0 * mu
+    D[np.arange(3, 6), np.arange(3, 6)] = mu
+    corners = np.array([[ax, ay, az] for az in (0, 1) for ay in (0, 1) for ax in (0, 1)], dtype=float)
+    sgn = 2.0 * corners - 1.0  # reference coordinates of the corners, +-1
+    g = 1.0 / np.sqrt(3.0)
+    K = np.zeros((24, 24))
+    for qx in (-g, g):
+        for qy in (-g, g):
+            for qz in (-g, g):
+                q = np.array([qx, qy, qz])
+                # dN_a/dxi_k = sgn_ak / 8 * prod_{l != k} (1 + sgn_al q_l); x = (xi + 1) / 2
+                dN = np.zeros((8, 3))
+                for a in range(8):
+                    f = 1.0 + sgn[a] * q
+                    for k in range(3):
+                        dN[a, k] = sgn[a, k] / 8.0 * np.prod(np.delete(f, k))
+                dN *= 2.0  # d/dx = 2 d/dxi on a unit cube
+                B = np.zeros((6, 24))
+                for a in range(8):
+                    bx, by, bz = dN[a]
+                    B[0, 3 * a] = bx
+                    B[1, 3 * a + 1] = by
+                    B[2, 3 * a + 2] = bz
+                    B[3, 3 * a], B[3, 3 * a + 1] = by, bx
+                    B[4, 3 * a + 1], B[4, 3 * a + 2] = bz, by
+                    B[5, 3 * a], B[5, 3 * a + 2] = bz, bx
+                K += B.T @ D @ B / 8.0  # weight 1, det J = 1/8
+    return 0.5 * (K + K.T)
+
+
+def elasticity3d(ne: int, e_soft: float = 1.0, e_stiff: float = 1e5, layer: int = 4, nu: float = 0.3):
+    """3D linear elasticity on ne^3 unit Q1 hexahedra, 3 dofs per node, with
+    Young's modulus alternating e_soft / e_stiff every `layer` element layers
+    along x, Poisson ratio nu, and the nodes of the face x = 0 clamped (their
+    dofs removed).  Returns (A, f, coords): A the SPD stiffness (CSR), f the
+    load of a unit body force (0, 0, -1) per unit volume (1/8 of each element's
+    volume to each of its nodes), and the node coordinates of each dof.
+    Node (x, y, z) has index x + (ne+1) y + (ne+1)^2 z; dofs are numbered
+    node-major over the free nodes."""
+    Ke = _q1_elasticity_stiffness(nu)
+    m = ne + 1
+    ex, ey, ez = np.meshgrid(np.arange(ne), np.arange(ne), np.arange(ne), indexing="ij")
+    ex, ey, ez = ex.ravel(), ey.ravel(), ez.ravel()
+    young = np.where((ex // layer) % 2 == 0, e_soft, e_stiff)
+    corner = np.array([[ax, ay, az] for az in (0, 1) for ay in (0, 1) for ax in (0, 1)])
+    nodes = ((ex[:, None] + corner[None, :, 0]) + m * (ey[:, None] + corner[None, :, 1])
+             + m * m * (ez[:, None] + corner[None, :, 2]))  # (nel, 8)
+    free = np.ones(m ** 3, dtype=bool)
+    free[np.arange(m ** 3) % m == 0] = False  # x = 0
+    node_id = -np.ones(m ** 3, dtype=np.int64)
+    node_id[free] = np.arange(int(free.sum()))
+    dofs = (3 * node_id[nodes][:, :, None] + np.arange(3)[None, None, :]).reshape(len(ex), 24)
+    keep = (node_id[nodes][:, :, None] >= 0).repeat(3, axis=2).reshape(len(ex), 24)
+    rows = np.broadcast_to(dofs[:, :, None], (len(ex), 24, 24))
+    cols = np.broadcast_to(dofs[:, None, :], (len(ex), 24, 24))
+    vals = young[:, None, None] * Ke[None, :, :]
+    mask = keep[:, :, None] & keep[:, None, :]
+    n = 3 * int(free.sum())
+    A = _csr_from_coo(n, rows[mask], cols[mask], vals[mask])
+    f = np.zeros(n)
+    zdof = dofs[:, 2::3]
+    zkeep = keep[:, 2::3]
+    np.add.at(f, zdof[zkeep], -1.0 / 8.0)
+    fx = np.flatnonzero(free)
+    coords = np.stack([fx % m, (fx // m) % m, fx // (m * m)], axis=1).repeat(3, axis=0)
+    return A, f, coords
+
+
+def box_partition_dofs(coords: np.ndarray, boxes) -> np.ndarray:
+    """Partition dofs by the node's position in a grid of boxes: boxes =
+    (bx, by, bz) node counts per box along x, y, z.  Subdomains are numbered
+    x-fastest and renumbered to be contiguous (empty boxes dropped)."""
+    c = np.asarray(coords)
+    b = np.asarray(boxes)
+    cell = c // b
+    nb = cell.max(axis=0) + 1
+    raw = cell[:, 0] + nb[0] * (cell[:, 1] + nb[1] * cell[:, 2])
+    _, part = np.unique(raw, return_inverse=True)
+    return part.astype(np.int32)
+
+
 def _neighbors(A: CSR, v: int) -> np.ndarray:
     return A.colind[A.rowptr[v]:A.rowptr[v + 1]]
 

@@ -1,20 +1,21 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Bars (FP64 throughout):
-  * singular values of X_i: 1e-10 relative;
+Every bar has a fixed part and a part that scales with the FP64 rounding
+envelope of the oracle itself on the same problem: the largest change of the
+oracle's result when the unknowns are relabelled (three seeded permutations;
+exact arithmetic is invariant to the order of Omega_i).  On well-conditioned
+problems the envelope is ~1e-15 and the fixed part decides; on the layered
+elasticity problems (modulus contrast 1e5, sigma_1 / sigma_min of X_i ~ 4e6)
+FP64 itself fixes the small singular directions, the spans of near-degenerate
+eigenvectors and the apply only to the envelope.
+  * singular values of X_i: |dsigma_j| <= 1e-10 sigma_j + 20 eta_sigma;
   * eigenvalues of eq. (Zi), compared as mu = 1/lambda (ascending, mu = 0 for
-    lambda = +inf): |mu_gpu - mu_oracle| <= 1e-8 mu_oracle + 20 eta_i, where
-    eta_i is the FP64 rounding envelope of the oracle itself on subdomain i:
-    the largest change of its mu when the unknowns are relabelled (two random
-    permutations; exact arithmetic is invariant to the order of Omega_i).  On
-    well-conditioned problems eta ~ 1e-15, so the bar is 1e-8 relative; on
-    high-contrast ones it widens only where FP64 cannot fix mu (the range
-    between the finite modes and the eps-cluster);
-  * selected count p_i exactly; selected span to 1e-8 (sine of the largest
-    principal angle);
-  * one apply z = M^{-1} r: 1e-10 relative (2-norm);
+    lambda = +inf): |dmu| <= 1e-8 mu + 20 eta_mu;
+  * selected count p_i exactly; selected span: sine of the largest principal
+    angle <= max(1e-8, 20 eta_span);
+  * one apply z = M^{-1} r: 1e-10 relative, or 20 eta_apply if larger;
   * PCG iterations to 1e-8: equal within +-1; PCG solutions at rtol 1e-12:
-    1e-10 relative;
+    1e-10 relative (plus 20 eta_apply);
   * bitwise run-to-run reproducibility of apply and PCG (deterministic
     reductions).
 """
@@ -46,6 +47,12 @@ def _diff(m, N, seed, ov, tau, lo, hi, cv=1e3, sigma=1.0):
     return M, part, int(part.max()) + 1, ov, tau
 
 
+def _elas(ne, box, layer, ov, tau):
+    M, _, xyz = synth.elasticity3d(ne, layer=layer)
+    part = synth.box_partition_dofs(xyz, (box, box, box))
+    return M, part, int(part.max()) + 1, ov, tau
+
+
 CASES = {
     "lap16_box4_tau50": lambda: _lap(16, 4, 1, 50.0),
     "lap16_box4_tau0.5": lambda: _lap(16, 4, 1, 0.5),
@@ -55,6 +62,8 @@ CASES = {
     "diff9_bfs_ov2_tau100": lambda: _diff(9, 5, 2, 2, 100.0, 60, 220),
     "diff10_bfs_ov1_tau0.1_contrast": lambda: _diff(10, 8, 4, 1, 0.1, 60, 200, cv=1e5, sigma=1.5),
     "single_subdomain": lambda: (synth.laplace2d(12), np.zeros(144, np.int32), 1, 1, 50.0),
+    "elas6_layer2_ov1_tau0.5": lambda: _elas(6, 4, 2, 1, 0.5),
+    "elas5_layer2_ov2_tau100": lambda: _elas(5, 3, 2, 2, 100.0),
 }
 
 _cache = {}
@@ -84,9 +93,11 @@ def test_sizes_match(name):
 @pytest.mark.parametrize("name", list(CASES))
 def test_singular_values(name):
     M, part, N, ov, tau, S, dA, dpart, P = _case(name)
+    eta = _envelope(name)["sigma"]
     for i, s in enumerate(S.subs):
         sg = A.get_singular_values(P.h, i)
-        assert np.allclose(sg, s.sigma, rtol=1e-10, atol=0)
+        so = np.sort(s.sigma)[::-1]
+        assert np.all(np.abs(sg - so) <= 1e-10 * so + 20 * eta[i]), f"subdomain {i}"
 
 
 def _mu(lam):
@@ -97,17 +108,38 @@ def _mu(lam):
 _env = {}
 
 
+def _span_sine(Za, Zb):
+    qa, _ = np.linalg.qr(Za)
+    qb, _ = np.linalg.qr(Zb)
+    return np.linalg.norm(qb - qa @ (qa.T @ qb), 2)
+
+
 def _envelope(name):
-    """eta_i: largest change of the oracle's mu on subdomain i over two random
-    relabellings of the unknowns (same sets, different FP64 rounding)."""
+    """FP64 rounding envelope of the oracle on each subdomain: the largest
+    change of mu, sigma (absolute), the selected span and one apply over three
+    random relabellings of the unknowns (same sets, different FP64 rounding)."""
     if name not in _env:
         M, part, N, ov, tau, S, dA, dpart, P = _case(name)
-        eta = np.zeros(N)
-        for seed in (101, 202):
+        eta = {"mu": np.zeros(N), "sigma": np.zeros(N), "span": np.zeros(N), "apply": 0.0}
+        r = np.random.default_rng(7).uniform(-1, 1, M.n)
+        zo = O.apply(S, r)
+        for seed in (101, 202, 303):
             perm = np.random.default_rng(seed).permutation(M.n)
+            inv = np.argsort(perm)
             Sp = O.setup(S.A[perm][:, perm].tocsr(), np.asarray(part)[perm], N, ov, tau)
+            zp = O.apply(Sp, r[perm])[inv]
+            eta["apply"] = max(eta["apply"], np.linalg.norm(zp - zo) / np.linalg.norm(zo))
             for i in range(N):
-                eta[i] = max(eta[i], np.abs(_mu(Sp.subs[i].lam) - _mu(S.subs[i].lam)).max())
+                s, t = S.subs[i], Sp.subs[i]
+                eta["mu"][i] = max(eta["mu"][i], np.abs(_mu(t.lam) - _mu(s.lam)).max())
+                eta["sigma"][i] = max(eta["sigma"][i],
+                                      np.abs(np.sort(t.sigma)[::-1] - np.sort(s.sigma)[::-1]).max())
+                if 0 < s.p < len(s.I) and t.p == s.p:
+                    Zo = np.zeros((M.n, s.p))
+                    Zo[s.I] = s.Z[: len(s.I)]
+                    Zq = np.zeros((M.n, s.p))
+                    Zq[perm[t.I]] = t.Z[: len(t.I)]
+                    eta["span"][i] = max(eta["span"][i], _span_sine(Zq, Zo))
         _env[name] = eta
     return _env[name]
 
@@ -115,7 +147,8 @@ def _envelope(name):
 @pytest.mark.parametrize("name", list(CASES))
 def test_eigenvalues_and_selection(name):
     M, part, N, ov, tau, S, dA, dpart, P = _case(name)
-    eta = _envelope(name)
+    env = _envelope(name)
+    eta = env["mu"]
     for i, s in enumerate(S.subs):
         lg = A.get_eigenvalues(P.h, i)
         assert len(lg) == len(s.lam)
@@ -126,9 +159,7 @@ def test_eigenvalues_and_selection(name):
         Zt = A.get_coarse_block(P.h, i)
         assert Zt.shape[0] == s.p
         if 0 < s.p < len(s.I):
-            q1, _ = np.linalg.qr(Zt.T)
-            q2, _ = np.linalg.qr(s.Z[: len(s.I)])
-            assert np.linalg.norm(q2 - q1 @ (q1.T @ q2), 2) < 1e-8
+            assert _span_sine(Zt.T, s.Z[: len(s.I)]) <= max(1e-8, 20 * env["span"][i])
         if s.p:
             # A_II-orthonormal columns on Omega_Ii
             AII = s.Aii[: len(s.I), : len(s.I)]
@@ -146,7 +177,8 @@ def test_apply_matches_oracle(name):
     zd = torch.empty_like(rd)
     P.apply(rd, zd)
     zg = zd.cpu().numpy()
-    assert np.linalg.norm(zg - zo) <= 1e-10 * np.linalg.norm(zo)
+    bar = max(1e-10, 20 * _envelope(name)["apply"])
+    assert np.linalg.norm(zg - zo) <= bar * np.linalg.norm(zo)
     z2 = torch.empty_like(rd)
     P.apply(rd, z2)
     assert torch.equal(zd, z2), "apply is not bitwise reproducible"
@@ -178,7 +210,8 @@ def test_pcg_matches_oracle(name):
     xo, _, _ = O.pcg(S.A, b, lambda r: O.apply(S, r), rtol=1e-12)
     xd2 = torch.zeros_like(bd)
     P.solve(bd, xd2, rtol=1e-12)
-    assert np.linalg.norm(xd2.cpu().numpy() - xo) <= 1e-10 * np.linalg.norm(xo)
+    bar = 1e-10 + 20 * _envelope(name)["apply"]
+    assert np.linalg.norm(xd2.cpu().numpy() - xo) <= bar * np.linalg.norm(xo)
     xd3 = torch.zeros_like(bd)
     P.solve(bd, xd3, rtol=1e-12)
     assert torch.equal(xd2, xd3), "PCG is not bitwise reproducible"
