@@ -212,17 +212,19 @@ def reduced_T(Aii: np.ndarray, Abar: np.ndarray, nI: int):
 
 
 # ------------------------------------------------------------------- LOBPCG
-def _orth(S: np.ndarray, drop: float = 1e-8) -> np.ndarray:
+def _orth(S: np.ndarray) -> np.ndarray:
     """Orthonormal basis of span(S): columns scaled to unit norm, then two
     passes of orthonormalisation through an eigendecomposition of the Gram
-    matrix (directions with eigenvalue below drop^2 of the largest are
-    dropped in the first pass)."""
+    matrix.  The first pass drops the directions with eigenvalue <= 1e-12 of
+    the largest (above the rounding level of a Gram matrix, where the exact
+    zeros of a rank-deficient S land); the second keeps eigenvalues > 1/2
+    (the columns are then nearly orthonormal)."""
     nrm = np.linalg.norm(S, axis=0)
     S = S[:, nrm > 0] / nrm[nrm > 0]
     for it in range(2):
         G = S.T @ S
         w, V = np.linalg.eigh(0.5 * (G + G.T))
-        keep = w > (drop ** 2) * max(w.max(), 1e-300) if it == 0 else w > 0
+        keep = w > 1e-12 * max(w.max(), 1e-300) if it == 0 else w > 0.5
         S = S @ (V[:, keep] / np.sqrt(w[keep]))
     return S
 

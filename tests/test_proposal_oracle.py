@@ -139,6 +139,8 @@ def test_lobpcg_matches_dense_on_local_pencil():
     k = s.p + 4
     th, X, its, ok = L.lobpcg(T, rng.standard_normal((nI, k)), s.p, tol=1e-7, maxit=500)
     assert ok and np.allclose(th, ev[: s.p], atol=1e-9)
+    # the block spans ~all of R^nI here (3k > nI): the Ritz vectors must stay orthonormal
+    assert np.allclose(X.T @ X, np.eye(s.p), atol=1e-10)
     Wq, _ = np.linalg.qr(W)
     Xq, _ = np.linalg.qr(X)
     assert np.linalg.norm(Wq - Xq @ (Xq.T @ Wq), 2) <= 1e-5
