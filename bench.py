@@ -136,8 +136,8 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20):
     eigenvalues above 1e12 enter the coarse space, so the apply is the
     bandwidth-bound part (restriction, the local triangular products with
     ~1.7 GB of FP32 factors, prolongation).  Each timed call is bracketed by
-    CUDA events on the library's stream, with L2 flushed before it; bytes are
-    the algorithmic counts of the library's profile."""
+    CUDA events on the library's stream, with L2 flushed (by a read) before it;
+    bytes are the algorithmic counts of the library's profile."""
     import synth
     from paper_2109_05908_gb300.device import DeviceMatrix
     c = APPLY_SCALE
@@ -156,12 +156,14 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20):
     stream = torch.cuda.current_stream(dev)
     r = torch.from_numpy(synth.rhs(M.n, 3)).to(dev)
     z = torch.empty_like(r)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    # L2 flush by a read of 256 MB (> L2): unlike a write, it leaves no dirty
+    # lines to drain to HBM during the timed call
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
     def timed(fn):
         out = []
         for k in range(reps + 3):
-            flush.zero_()
+            torch.sum(flush)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
@@ -171,7 +173,7 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20):
                 out.append(e0.elapsed_time(e1))
         return statistics.median(out)
 
-    spmv_ms = timed(lambda: A.spmv(dA.csr, r.data_ptr(), z.data_ptr(), sp))
+    spmv_call_ms = timed(lambda: A.spmv(dA.csr, r.data_ptr(), z.data_ptr(), sp))
     spmv_bytes = 12.0 * dA.nnz + 8.0 * (M.n + 1) + 16.0 * M.n
     A.apply(h, r.data_ptr(), z.data_ptr(), 1)
     A.reset_profile(h)
@@ -179,23 +181,33 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20):
     prof = {p["name"]: p for p in A.get_profile(h)}
     n_calls = reps + 3
     apply_bytes = sum(prof[k]["bytes"] for k in APPLY_CLASSES if k in prof) / n_calls
+    # per-launch kernel times from the library's events inside PCG: between two
+    # SpMVs the apply streams ~1.7 GB of factors through L2, so each launch
+    # starts cold
+    A.reset_profile(h)
+    x = torch.zeros_like(r)
+    A.pcg_solve(h, r.data_ptr(), x.data_ptr(), 1, 1e-30, 10, allow_noconv=True)
+    prof_pcg = {p["name"]: p for p in A.get_profile(h)}
     kernels = {}
-    for k in APPLY_CLASSES:
-        p = prof.get(k)
+    for k in APPLY_CLASSES + ("spmv",):
+        p = prof_pcg.get(k)
         if p and p["launches"] and p["ms"] > 0:
             gbs = p["bytes"] / (p["ms"] * 1e-3) / 1e9
-            kernels[k] = {"launches_per_apply": p["launches"] / n_calls, "ms_per_apply": p["ms"] / n_calls,
+            kernels[k] = {"launches": p["launches"], "ms_per_launch": p["ms"] / p["launches"],
                           "GB/s": gbs, "frac": gbs / hbm_gbs}
     A.destroy(h)
-    spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    spmv_gbs = kernels["spmv"]["GB/s"] if "spmv" in kernels else None
     apply_gbs = apply_bytes / (apply_ms * 1e-3) / 1e9
     return {
         "workload": f"laplace2d_{c['m']}x{c['m']}_{N}box_ov{c['overlap']}_tau{c['tau']:g}, mixed form",
-        "n": M.n, "N": N, "n_C": info.n_C, "setup_s": setup_s, "l2": "flushed before every timed call",
-        "spmv": {"ms": spmv_ms, "bytes": spmv_bytes, "GB/s": spmv_gbs, "frac": spmv_gbs / hbm_gbs},
+        "n": M.n, "N": N, "n_C": info.n_C, "setup_s": setup_s, "l2": "flushed by a 256 MB read before every timed call",
+        "spmv": {"ms_per_launch": kernels.get("spmv", {}).get("ms_per_launch"), "bytes": spmv_bytes,
+                 "GB/s": spmv_gbs, "frac": spmv_gbs / hbm_gbs if spmv_gbs else None,
+                 "call_ms": spmv_call_ms,
+                 "note": "kernel events inside PCG; call_ms is the whole amdd_spmv call (it synchronises)"},
         "apply": {"ms": apply_ms, "bytes": apply_bytes, "GB/s": apply_gbs, "frac": apply_gbs / hbm_gbs,
-                  "note": "whole amdd_apply call between events (launch gaps included)"},
-        "apply_kernels": kernels,
+                  "note": "whole amdd_apply call between events (launch gaps and its final synchronisation included)"},
+        "kernels_in_pcg": kernels,
     }
 
 

@@ -66,6 +66,26 @@ typedef struct {
     const double* val;
 } amdd_csr;
 
+/* A trained proposal network for the learned warm start of the local
+ * eigensolve (no counterpart in the paper: an accelerator of the eigensolve
+ * of eq. (Zi) whose results are accepted only if they pass the same checks
+ * as those of the plain eigensolver).  Device pointers, FP32, owned by the
+ * caller and read during amdd_setup only:
+ *   weights  AMDD_MLP_NPARAM values rounded to bfloat16 (amdd_mlp_train_step
+ *            keeps such a copy), layout W1 (32 x 256), b1 (256), W2
+ *            (256 x 256), b2, W3 (256 x 256), b3, matrices row-major;
+ *   mean, sd the 32 feature means and standard deviations (sd > 0) the
+ *            network was trained with. */
+typedef struct {
+    const float* weights;
+    const float* mean;
+    const float* sd;
+} amdd_proposal;
+
+#define AMDD_MLP_NPARAM 140032
+#define AMDD_PROP_NF 32
+#define AMDD_PROP_NB 16
+
 typedef struct {
     double eps;           /* shift of Remark 3.2 / Sec. 3.2: Abar += sigma_1*eps*I; default 2^-52 */
     int32_t max_sweeps;   /* sweep limit of the one-sided Jacobi solvers; default 60               */
@@ -82,7 +102,16 @@ typedef struct {
                              solves, T and the eigensolve of eq. (Zi) in FP32; E and PCG in FP64 */
     uint32_t profile_classes; /* with profile = 1: bit k set times kernel class k only (classes as
                              numbered by amdd_get_profile); 0 times every class; default 0         */
-    int32_t reserved[4];  /* must be zero                                                          */
+    int32_t eig_solver;   /* eigenvectors of eq. (Zi) when the selection is partial: 0 dense one-sided
+                             Jacobi on [T | I] (default); 1 block LOBPCG from counter-based random
+                             rows; 2 block LOBPCG from the learned proposal (needs `proposal`).
+                             A LOBPCG result is accepted only if every wanted residual is within
+                             the tolerance and its Ritz values match the bisection eigenvalues;
+                             otherwise that subdomain takes the dense path                          */
+    int32_t keep_proposal_data; /* 1: keep the features and Krylov bases of the partially selected
+                             subdomains for amdd_proposal_export                                     */
+    const amdd_proposal* proposal; /* the network of eig_solver = 2 (NULL otherwise)                */
+    int32_t reserved[2];  /* must be zero                                                          */
 } amdd_opts;
 
 typedef struct {
@@ -117,6 +146,11 @@ typedef struct {
     int32_t sweeps_eig32;  /* sweeps of the FP32 preconditioning stage (eq. (Zi)) */
     int32_t precision;     /* 0 plain FP64, 1 or 2 mixed (see amdd_opts)     */
     double eps;            /* the eps of the splitting actually used       */
+    int32_t n_partial;     /* subdomains whose selection is partial (0 < p_i < |Omega_Ii|) */
+    int32_t lobpcg_subdomains; /* of those, eigenvectors accepted from LOBPCG */
+    int32_t lobpcg_fallbacks;  /* LOBPCG results rejected (dense path taken)  */
+    int32_t lobpcg_iters_max;  /* largest LOBPCG iteration count             */
+    int64_t lobpcg_iters_total;/* sum of the LOBPCG iteration counts         */
 } amdd_info;
 
 /* Fill `o` with the defaults (eps = 2^-52, max_sweeps = 60). */
@@ -170,6 +204,48 @@ amdd_status amdd_apply(amdd_handle* h, const double* r, double* z, int32_t nrhs)
  * right-hand side. */
 amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t nrhs,
                            double rtol, int32_t maxit, amdd_stats* stats);
+
+/* Training data of the learned warm start (no counterpart in the paper)
+ * from a handle built with opts.keep_proposal_data = 1: for each partially
+ * selected subdomain, in subdomain order, its 32 features (feat, row-major
+ * count x 32), the target 16 x 16 projector B^T Q Q^T B (target, count x 256;
+ * B the orthonormal Krylov basis K_16(A_II, 1), Q an orthonormal basis of
+ * the selected eigenvectors on Omega_Ii) and its subdomain index (sub).  Host
+ * arrays of capacity cap (any may be NULL to query *count only).  Features
+ * (definitions in the library's source): sizes and their ratios, statistics
+ * of log diag(A_II), of log|off-diagonal entries|, of row degrees, of the
+ * coupling to Omega_Gi and of diagonal dominance, ||A_II||_F, trace, sign
+ * structure, p_i, tau.  AMDD_ERR_INVALID without the kept data. */
+amdd_status amdd_proposal_export(const amdd_handle* h, float* feat, float* target, int32_t* sub, int32_t cap,
+                                 int32_t* count);
+
+/* Per-subdomain LOBPCG iteration counts into the host array iters[cap]
+ * (cap >= N): >= 0 accepted from LOBPCG, -1 dense path, -2 selection not
+ * partial. */
+amdd_status amdd_get_eig_iterations(const amdd_handle* h, int32_t* iters, int32_t cap);
+
+/* The proposal network (no counterpart in the paper), trained on the GPU by
+ * these kernels; all pointers are device pointers, work runs on `stream`
+ * and is complete on return.  n = number of samples (rows).
+ *   amdd_mlp_sizes: *nparam = AMDD_MLP_NPARAM, *nwork = floats of the `work`
+ *     buffer amdd_mlp_forward / amdd_mlp_train_step need for n samples.
+ *   amdd_mlp_normalize: x = (feat - mean) / sd (n x 32).
+ *   amdd_mlp_forward: q (n x 256) = the symmetrised outputs, as 16 x 16
+ *     matrices, of the MLP 32 -> 256 -> 256 -> 256 (ReLU) with weights wb.
+ *   amdd_mlp_train_step: forward with wb, loss = mean over samples of
+ *     ||q - qt||_F^2 (written to *loss, a device float), its gradient in
+ *     grad (AMDD_MLP_NPARAM), then, when lr > 0, one Adam step (beta1 0.9,
+ *     beta2 0.999, eps 1e-8, step number t >= 1) on the FP32 master weights w
+ *     with moments m, v, and wb = w rounded to bfloat16 (nearest, ties to
+ *     even).  lr = 0 computes the gradient only.
+ *   amdd_mlp_round_bf16: wb = w rounded to bfloat16 (n values). */
+amdd_status amdd_mlp_sizes(int32_t n, int64_t* nparam, int64_t* nwork);
+amdd_status amdd_mlp_normalize(const float* feat, const float* mean, const float* sd, int32_t n, float* x,
+                               void* stream);
+amdd_status amdd_mlp_forward(const float* wb, const float* x, int32_t n, float* q, float* work, void* stream);
+amdd_status amdd_mlp_train_step(float* w, float* wb, float* m, float* v, int32_t t, float lr, const float* x,
+                                const float* qt, int32_t n, float* grad, float* work, float* loss, void* stream);
+amdd_status amdd_mlp_round_bf16(const float* w, float* wb, int64_t n, void* stream);
 
 /* Host-only, no GPU involved: the extreme eigenvalues of the Lanczos
  * tridiagonal of k PCG steps (the CG-Lanczos relation; Sec. 1 gives the CG

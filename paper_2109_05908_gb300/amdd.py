@@ -23,9 +23,20 @@ class amdd_csr(C.Structure):
                 ("val", C.c_void_p)]
 
 
+class amdd_proposal(C.Structure):
+    _fields_ = [("weights", C.c_void_p), ("mean", C.c_void_p), ("sd", C.c_void_p)]
+
+
 class amdd_opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("max_sweeps", C.c_int32), ("profile", C.c_int32),
-                ("precision", C.c_int32), ("profile_classes", C.c_uint32), ("reserved", C.c_int32 * 4)]
+                ("precision", C.c_int32), ("profile_classes", C.c_uint32), ("eig_solver", C.c_int32),
+                ("keep_proposal_data", C.c_int32), ("proposal", C.POINTER(amdd_proposal)),
+                ("reserved", C.c_int32 * 2)]
+
+
+MLP_NPARAM = 140032
+PROP_NF = 32
+PROP_NB = 16
 
 
 class amdd_stats(C.Structure):
@@ -40,7 +51,9 @@ class amdd_info(C.Structure):
                 ("max_nti", C.c_int32), ("sweeps_svd", C.c_int32), ("sweeps_eig", C.c_int32),
                 ("setup_ms", C.c_double), ("rotations_svd", C.c_int64), ("rotations_eig", C.c_int64),
                 ("sweeps_svd32", C.c_int32), ("sweeps_eig32", C.c_int32), ("precision", C.c_int32),
-                ("eps", C.c_double)]
+                ("eps", C.c_double), ("n_partial", C.c_int32), ("lobpcg_subdomains", C.c_int32),
+                ("lobpcg_fallbacks", C.c_int32), ("lobpcg_iters_max", C.c_int32),
+                ("lobpcg_iters_total", C.c_int64)]
 
 
 class AmddError(RuntimeError):
@@ -61,6 +74,16 @@ SIGNATURES = {
     "amdd_pcg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32,
                                  C.POINTER(amdd_stats)]),
     "amdd_get_info": (C.c_int, [C.c_void_p, C.POINTER(amdd_info)]),
+    "amdd_proposal_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                       C.POINTER(C.c_int32)]),
+    "amdd_get_eig_iterations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "amdd_mlp_sizes": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "amdd_mlp_normalize": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "amdd_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "amdd_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
+                                      C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
+    "amdd_mlp_round_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "amdd_lanczos_extremes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]),
     "amdd_get_subdomain": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -202,6 +225,53 @@ def overlap_sets(n, rowptr, colind, part, i: int, overlap: int):
     _check(lib().amdd_overlap_sets(*args, I.ctypes.data, a.value, G.ctypes.data, b.value, D.ctypes.data, c.value,
                                    C.byref(a), C.byref(b), C.byref(c)), "amdd_overlap_sets")
     return I, G, D
+
+
+def proposal_export(h: int):
+    """(features (count x 32), target projectors (count x 16 x 16), subdomain
+    indices) of a handle built with keep_proposal_data = 1 (host numpy)."""
+    import numpy as np
+    cnt = C.c_int32()
+    _check(lib().amdd_proposal_export(h, None, None, None, 0, C.byref(cnt)), "amdd_proposal_export")
+    n = cnt.value
+    feat = np.empty((n, PROP_NF), np.float32)
+    tgt = np.empty((n, PROP_NB, PROP_NB), np.float32)
+    sub = np.empty(n, np.int32)
+    if n:
+        _check(lib().amdd_proposal_export(h, feat.ctypes.data, tgt.ctypes.data, sub.ctypes.data, n, C.byref(cnt)),
+               "amdd_proposal_export")
+    return feat, tgt, sub
+
+
+def eig_iterations(h: int, N: int):
+    import numpy as np
+    out = np.empty(N, np.int32)
+    _check(lib().amdd_get_eig_iterations(h, out.ctypes.data, N), "amdd_get_eig_iterations")
+    return out
+
+
+def mlp_sizes(n: int):
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().amdd_mlp_sizes(n, C.byref(a), C.byref(b)), "amdd_mlp_sizes")
+    return a.value, b.value
+
+
+def mlp_normalize(feat_ptr: int, mean_ptr: int, sd_ptr: int, n: int, x_ptr: int, stream: int = 0) -> None:
+    _check(lib().amdd_mlp_normalize(feat_ptr, mean_ptr, sd_ptr, n, x_ptr, stream), "amdd_mlp_normalize")
+
+
+def mlp_forward(wb_ptr: int, x_ptr: int, n: int, q_ptr: int, work_ptr: int, stream: int = 0) -> None:
+    _check(lib().amdd_mlp_forward(wb_ptr, x_ptr, n, q_ptr, work_ptr, stream), "amdd_mlp_forward")
+
+
+def mlp_train_step(w_ptr, wb_ptr, m_ptr, v_ptr, t: int, lr: float, x_ptr, qt_ptr, n: int, grad_ptr, work_ptr,
+                   loss_ptr, stream: int = 0) -> None:
+    _check(lib().amdd_mlp_train_step(w_ptr, wb_ptr, m_ptr, v_ptr, t, float(lr), x_ptr, qt_ptr, n, grad_ptr,
+                                     work_ptr, loss_ptr, stream), "amdd_mlp_train_step")
+
+
+def mlp_round_bf16(w_ptr: int, wb_ptr: int, n: int, stream: int = 0) -> None:
+    _check(lib().amdd_mlp_round_bf16(w_ptr, wb_ptr, n, stream), "amdd_mlp_round_bf16")
 
 
 def lanczos_extremes(alpha, beta):

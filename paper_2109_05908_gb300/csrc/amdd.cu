@@ -146,7 +146,9 @@ struct amdd_handle {
     GemvDesc* d_gv_l1 = nullptr;
     GemvDesc* d_gv_l2 = nullptr;
     GemvDesc* d_gv_c = nullptr;
-    int32_t *d_rd_loc = nullptr, *d_rl_loc = nullptr, *d_rd_c = nullptr, *d_rl_c = nullptr;
+    int32_t *d_rd_c = nullptr, *d_rl_c = nullptr;
+    int32_t *d_g4_desc = nullptr, *d_g4_row = nullptr;  // row groups (one warp each) of the local products
+    int64_t n_g4 = 0;
     int32_t *d_order_g = nullptr, *d_own_sub = nullptr, *d_own_a = nullptr, *d_sc_idx = nullptr;
     int32_t *d_nI = nullptr, *d_p = nullptr;
     int64_t *d_sc_ptr = nullptr, *d_zt_off = nullptr, *d_coff = nullptr;
@@ -166,6 +168,19 @@ struct amdd_handle {
     std::vector<int> env_colend;  // one past the last non-zero row of each column of L_E
     int* d_env_row = nullptr;
     int* d_env_colend = nullptr;
+    // eigenvectors of partial selections: 0 dense Jacobi, 1 LOBPCG from random
+    // rows, 2 LOBPCG from the learned proposal
+    int eig_solver = 0, keep_prop = 0;
+    amdd_proposal prop{};
+    bool have_prop = false;
+    std::vector<int> eig_iters;  // per subdomain: LOBPCG iterations, -1 dense path, -2 not partial
+    int n_partial = 0, lob_subs = 0, lob_max = 0, lob_fallbacks = 0;
+    int64_t lob_total = 0;
+    // kept for amdd_proposal_export: features and Krylov bases of the partial subdomains
+    float* prop_feat = nullptr;
+    double* prop_bt = nullptr;
+    std::vector<int> prop_sub;
+    std::vector<int64_t> prop_off_b;
     // PCG work vectors
     double *d_r = nullptr, *d_z = nullptr, *d_pv = nullptr, *d_q = nullptr, *d_part = nullptr;
     PcgScal* d_sc = nullptr;
@@ -653,6 +668,681 @@ void overlap_layers(const int64_t* rp, const int32_t* ci, const std::vector<int3
 // FP64 form, float for the mixed form (local factors, local solves, the SVD
 // of X_i, the splitting and the eigensolve in FP32; E, its factor and PCG in
 // FP64).
+// ---------------------------------------------------------------------------
+// Learned warm start and block LOBPCG for the eigenvectors of eq. (Zi)
+// ---------------------------------------------------------------------------
+// Small symmetric positive semi-definite matrices G_q (m_q x m_q, row-major,
+// leading dimension ld_q, at base + off_q) are diagonalised by one-sided
+// Jacobi on the rows of [G_q | I]: the rotated rows of G_q become lambda_j
+// w_j^T, so the row norms are the eigenvalues and the right half holds the
+// eigenvectors w_j as rows.  Returns, per matrix, the eigenvalues ascending
+// (host) and the device offset of each eigenvector row in W.
+template <typename T>
+struct SmallEig {
+    T* W = nullptr;                          // [G | I] work, rows of eigenvectors in the right half
+    std::vector<int64_t> off;                // per matrix: offset of its m x 2m block in W
+    std::vector<std::vector<int>> row;       // per matrix: row of the j-th smallest eigenvalue
+    std::vector<std::vector<double>> val;    // per matrix: eigenvalues, ascending
+};
+
+template <typename T>
+SmallEig<T> small_eig(Ctx& C, const T* base, const std::vector<int64_t>& goff, const std::vector<int>& m,
+                      const std::vector<int>& ldg) {
+    amdd_handle* h = C.h;
+    const int nq = (int)m.size();
+    SmallEig<T> out;
+    out.off.assign(nq + 1, 0);
+    int maxm = 1;
+    for (int q = 0; q < nq; ++q) {
+        out.off[q + 1] = out.off[q] + (int64_t)m[q] * 2 * m[q];
+        maxm = std::max(maxm, m[q]);
+    }
+    out.W = C.tnew<T>(std::max<int64_t>(out.off[nq], 1));
+    std::vector<int64_t> src, dst;
+    std::vector<int32_t> len;
+    std::vector<TrtriDescT<T>> idd(nq);
+    std::vector<JacobiDescT<T>> jd(nq);
+    T* nrm = C.tnew<T>(std::max<int64_t>(out.off[nq], 1));
+    double* norms = C.tnew<double>(std::max<int64_t>(out.off[nq], 1));
+    std::vector<double*> np(nq);
+    int64_t nacc = 0;
+    for (int q = 0; q < nq; ++q) {
+        for (int r = 0; r < m[q]; ++r) {
+            src.push_back(goff[q] + (int64_t)r * ldg[q]);
+            dst.push_back(out.off[q] + (int64_t)r * 2 * m[q]);
+            len.push_back(m[q]);
+        }
+        idd[q] = {nullptr, out.W + out.off[q] + m[q], nullptr, m[q], 0, 2 * m[q]};
+        jd[q] = {out.W + out.off[q], m[q], 2 * m[q], m[q], 2 * m[q], nrm + nacc, nullptr};
+        np[q] = norms + nacc;
+        nacc += m[q];
+    }
+    {
+        auto a = C.up(src);
+        auto b = C.up(dst);
+        auto c = C.up(len);
+        auto di = C.up(idd);
+        PScope ps(h, PK_SMALL);
+        launch_gather_rows<T>(base, a, out.W, b, c, (int64_t)src.size(), h->s);
+        launch_set_identity<T>(di, nq, maxm, h->s);
+    }
+    const JacobiDescT<T>* djd = C.up(jd);
+    int* sw = C.tnew<int>(nq);
+    unsigned long long* rots = C.tnew<unsigned long long>(nq);
+    {
+        PScope ps(h, PK_JAC_EIG);
+        const T tol = (std::is_same<T, double>::value ? T(2) : T(8)) * std::sqrt((T)maxm) * std::numeric_limits<T>::epsilon();
+        run_jacobi<T>(h, jd, djd, h->max_sweeps, tol, sw, rots, 0);
+    }
+    {
+        auto dn = C.up(np);
+        PScope ps(h, PK_SMALL);
+        launch_rownorms<T>(djd, nq, dn, (T*)nullptr, 0.0, 0, h->s);
+    }
+    std::vector<double> hn(nacc);
+    ck(cudaMemcpyAsync(hn.data(), norms, nacc * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    ck(cudaStreamSynchronize(h->s));
+    out.row.resize(nq);
+    out.val.resize(nq);
+    nacc = 0;
+    for (int q = 0; q < nq; ++q) {
+        std::vector<int> o(m[q]);
+        std::iota(o.begin(), o.end(), 0);
+        const double* v = hn.data() + nacc;
+        std::stable_sort(o.begin(), o.end(), [&](int x, int y) { return v[x] < v[y]; });
+        out.row[q] = o;
+        out.val[q].resize(m[q]);
+        for (int j = 0; j < m[q]; ++j) out.val[q][j] = v[o[j]];
+        nacc += m[q];
+    }
+    return out;
+}
+
+// Orthonormal basis (rows) of the span of the rows of S_q (r_q rows of n_q
+// entries): rows scaled to unit norm, then two passes of S <- diag(w^{-1/2})
+// V^T S from the eigendecomposition G = S S^T = V diag(w) V^T.  The first
+// pass drops the directions with w <= 1e-12 w_max (well above the rounding
+// level ~ r u w_max of a Gram matrix, where the exact zeros of a rank-
+// deficient S land); the second, on rows that are already nearly
+// orthonormal, keeps only w > 1/2.  The result overwrites S_q; the new row
+// counts are returned.
+template <typename T>
+std::vector<int> orth_rows(Ctx& C, T* S, const std::vector<int64_t>& soff, const std::vector<int>& r,
+                           const std::vector<int>& n, int ld) {
+    amdd_handle* h = C.h;
+    const int nq = (int)r.size();
+    std::vector<int> rr = r;
+    {
+        std::vector<ScaleDesc<T>> sd(nq);
+        for (int q = 0; q < nq; ++q) sd[q] = {S + soff[q], ld, rr[q], n[q], nullptr};
+        auto d = C.up(sd);
+        PScope ps(h, PK_SMALL);
+        launch_scale_rows<T>(d, nq, 1, h->s);
+    }
+    int maxr = 1;
+    for (int q = 0; q < nq; ++q) maxr = std::max(maxr, rr[q]);
+    std::vector<int64_t> goff(nq + 1, 0), voff(nq + 1, 0);
+    for (int q = 0; q < nq; ++q) {
+        goff[q + 1] = goff[q] + (int64_t)maxr * maxr;
+        voff[q + 1] = voff[q] + (int64_t)maxr * ld;
+    }
+    T* G = C.tnew<T>(goff[nq]);
+    T* V = C.tnew<T>(goff[nq]);
+    T* tmp = C.tnew<T>(voff[nq]);
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<GemmDescT<T>> g(nq);
+        std::vector<int> ldg(nq, maxr);
+        for (int q = 0; q < nq; ++q)
+            g[q] = gd<T>(S + soff[q], ld, 0, S + soff[q], ld, 1, G + goff[q], maxr, rr[q], rr[q], n[q], 1.0, 0.0, 0);
+        gemm(C, g);
+        SmallEig<T> e = small_eig<T>(C, G, std::vector<int64_t>(goff.begin(), goff.end() - 1), rr, ldg);
+        // kept eigenvector rows, and the scale w^{-1/2} of each
+        std::vector<int64_t> src, dst;
+        std::vector<int32_t> len;
+        std::vector<T> f;
+        std::vector<int64_t> foff(nq + 1, 0);
+        std::vector<int> keep(nq);
+        for (int q = 0; q < nq; ++q) {
+            const double wmax = e.val[q].empty() ? 0.0 : e.val[q].back();
+            int k = 0;
+            for (int j = rr[q] - 1; j >= 0; --j) {  // largest first
+                const double w = e.val[q][j];
+                const bool ok = pass == 0 ? (w > 1e-12 * wmax) : (w > 0.5);
+                if (!ok) continue;
+                src.push_back(e.off[q] + (int64_t)e.row[q][j] * 2 * rr[q] + rr[q]);
+                dst.push_back(goff[q] + (int64_t)k * maxr);
+                len.push_back(rr[q]);
+                f.push_back((T)(1.0 / std::sqrt(w)));
+                ++k;
+            }
+            keep[q] = k;
+            foff[q + 1] = foff[q] + k;
+        }
+        {
+            auto a = C.up(src);
+            auto b = C.up(dst);
+            auto c = C.up(len);
+            PScope ps(h, PK_SMALL);
+            launch_gather_rows<T>(e.W, a, V, b, c, (int64_t)src.size(), h->s);
+        }
+        std::vector<GemmDescT<T>> g2(nq);
+        for (int q = 0; q < nq; ++q)
+            g2[q] = gd<T>(V + goff[q], maxr, 0, S + soff[q], ld, 0, tmp + voff[q], ld, keep[q], n[q], rr[q], 1.0, 0.0, 0);
+        gemm(C, g2);
+        const T* df = C.up(f);
+        std::vector<ScaleDesc<T>> sd(nq);
+        std::vector<int64_t> src2, dst2;
+        std::vector<int32_t> len2;
+        for (int q = 0; q < nq; ++q) {
+            sd[q] = {tmp + voff[q], ld, keep[q], n[q], df + foff[q]};
+            for (int j = 0; j < keep[q]; ++j) {
+                src2.push_back(voff[q] + (int64_t)j * ld);
+                dst2.push_back(soff[q] + (int64_t)j * ld);
+                len2.push_back(n[q]);
+            }
+        }
+        {
+            auto d = C.up(sd);
+            auto a = C.up(src2);
+            auto b = C.up(dst2);
+            auto c = C.up(len2);
+            PScope ps(h, PK_SMALL);
+            launch_scale_rows<T>(d, nq, 0, h->s);
+            launch_gather_rows<T>(tmp, a, S, b, c, (int64_t)src2.size(), h->s);
+        }
+        rr = keep;
+    }
+    return rr;
+}
+
+// Block LOBPCG (Knyazev 2001, no preconditioner) for the p_q smallest
+// eigenpairs of the symmetric T_q (n_q x n_q at Tm + toff[q], leading
+// dimension ldt_q), block size k_q, from the initial rows X0_q (k_q x n_q at
+// X0 + xoff[q], leading dimension n_q; overwritten).  Vectors are rows.  Per
+// iteration: residual rows R = T X - diag(theta) X; stop when every wanted
+// residual norm is <= tol; otherwise Rayleigh-Ritz on the orthonormalised
+// rows of [X; R; P] and P = X_new - (X_new X^T) X.  On return the first p_q
+// rows of X0_q are the Ritz vectors and theta_out[q] the Ritz values;
+// iters[q] counts the iterations and ok[q] the convergence.
+template <typename T>
+void lobpcg_rows(Ctx& C, const T* Tm, const std::vector<int64_t>& toff, const std::vector<int>& ldt, T* X0,
+                 const std::vector<int64_t>& xoff, const std::vector<int>& n, const std::vector<int>& k,
+                 const std::vector<int>& p, double tol, int maxit, std::vector<int>& iters, std::vector<char>& ok,
+                 std::vector<std::vector<double>>& theta_out) {
+    amdd_handle* h = C.h;
+    const int nq = (int)n.size();
+    iters.assign(nq, 0);
+    ok.assign(nq, 0);
+    theta_out.assign(nq, {});
+    if (nq == 0) return;
+    int maxn = 1, maxk = 1;
+    for (int q = 0; q < nq; ++q) {
+        maxn = std::max(maxn, n[q]);
+        maxk = std::max(maxk, k[q]);
+    }
+    const int ld = maxn;
+    const int64_t blk = (int64_t)maxk * ld, blk3 = 3 * blk;
+    T* X = C.tnew<T>(nq * blk);
+    T* TX = C.tnew<T>(nq * blk);
+    T* R = C.tnew<T>(nq * blk);
+    T* P = C.tnew<T>(nq * blk);
+    T* S = C.tnew<T>(nq * blk3);
+    T* TS = C.tnew<T>(nq * blk3);
+    T* G = C.tnew<T>((int64_t)nq * 9 * maxk * maxk);
+    T* Cm = C.tnew<T>((int64_t)nq * 9 * maxk * maxk);
+    T* M = C.tnew<T>((int64_t)nq * maxk * maxk);
+    T* theta = C.tnew<T>((int64_t)nq * maxk);
+    double* rn = C.tnew<double>((int64_t)nq * maxk);
+    auto boff = [&](int q, int64_t b) { return (int64_t)q * b; };
+    // rows of a small matrix (from SmallEig) -> dense rows at dst
+    auto take_rows = [&](const SmallEig<T>& e, const std::vector<int>& mm, const std::vector<int>& cnt, T* dst,
+                         int64_t dblk, int dld) {
+        std::vector<int64_t> src, dsto;
+        std::vector<int32_t> len;
+        for (int q = 0; q < (int)mm.size(); ++q)
+            for (int j = 0; j < cnt[q]; ++j) {
+                src.push_back(e.off[q] + (int64_t)e.row[q][j] * 2 * mm[q] + mm[q]);
+                dsto.push_back((int64_t)q * dblk + (int64_t)j * dld);
+                len.push_back(mm[q]);
+            }
+        auto a = C.up(src);
+        auto b = C.up(dsto);
+        auto c = C.up(len);
+        PScope ps(h, PK_SMALL);
+        launch_gather_rows<T>(e.W, a, dst, b, c, (int64_t)src.size(), h->s);
+    };
+    auto copy_rows = [&](const T* from, int64_t fblk, T* to, int64_t tblk, const std::vector<int>& rows, int rfrom,
+                         int rto) {
+        std::vector<int64_t> src, dsto;
+        std::vector<int32_t> len;
+        for (int q = 0; q < nq; ++q)
+            for (int j = 0; j < rows[q]; ++j) {
+                src.push_back(boff(q, fblk) + (int64_t)(rfrom + j) * ld);
+                dsto.push_back(boff(q, tblk) + (int64_t)(rto + j) * ld);
+                len.push_back(n[q]);
+            }
+        if (src.empty()) return;
+        auto a = C.up(src);
+        auto b = C.up(dsto);
+        auto c = C.up(len);
+        PScope ps(h, PK_SMALL);
+        launch_gather_rows<T>(from, a, to, b, c, (int64_t)src.size(), h->s);
+    };
+    // Rayleigh-Ritz on the orthonormal rows of S (rs rows): X <- first k Ritz rows
+    auto rayleigh_ritz = [&](const std::vector<int>& rs) {
+        std::vector<GemmDescT<T>> g1(nq), g2(nq);
+        const int ldg = 3 * maxk;
+        for (int q = 0; q < nq; ++q) {
+            g1[q] = gd<T>(S + boff(q, blk3), ld, 0, Tm + toff[q], ldt[q], 0, TS + boff(q, blk3), ld, rs[q], n[q], n[q],
+                          1.0, 0.0, 0);
+            g2[q] = gd<T>(S + boff(q, blk3), ld, 0, TS + boff(q, blk3), ld, 1, G + (int64_t)q * 9 * maxk * maxk, ldg,
+                          rs[q], rs[q], n[q], 1.0, 0.0, 0);
+        }
+        gemm(C, g1);
+        gemm(C, g2);
+        std::vector<int64_t> go(nq);
+        std::vector<int> lg(nq, ldg);
+        for (int q = 0; q < nq; ++q) go[q] = (int64_t)q * 9 * maxk * maxk;
+        SmallEig<T> e = small_eig<T>(C, G, go, rs, lg);
+        std::vector<int> kk(nq);
+        for (int q = 0; q < nq; ++q) kk[q] = std::min(k[q], rs[q]);
+        take_rows(e, rs, kk, Cm, 9 * maxk * maxk, ldg);
+        std::vector<GemmDescT<T>> g3(nq), g4(nq);
+        std::vector<T> th((size_t)nq * maxk, T(0));
+        for (int q = 0; q < nq; ++q) {
+            g3[q] = gd<T>(Cm + (int64_t)q * 9 * maxk * maxk, ldg, 0, S + boff(q, blk3), ld, 0, X + boff(q, blk), ld,
+                          kk[q], n[q], rs[q], 1.0, 0.0, 0);
+            g4[q] = gd<T>(Cm + (int64_t)q * 9 * maxk * maxk, ldg, 0, TS + boff(q, blk3), ld, 0, TX + boff(q, blk), ld,
+                          kk[q], n[q], rs[q], 1.0, 0.0, 0);
+            for (int j = 0; j < kk[q]; ++j) th[(size_t)q * maxk + j] = (T)e.val[q][j];
+            theta_out[q].assign(e.val[q].begin(), e.val[q].begin() + kk[q]);
+        }
+        gemm(C, g3);
+        gemm(C, g4);
+        ck(cudaMemcpyAsync(theta, th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice, h->s));
+        ck(cudaStreamSynchronize(h->s));
+        return kk;
+    };
+    // initial block: orthonormalise X0 and Rayleigh-Ritz on it
+    {
+        // the caller's X0 layout (xoff, leading dimension n_q) -> S
+        std::vector<int64_t> src, dsto;
+        std::vector<int32_t> len;
+        for (int q = 0; q < nq; ++q)
+            for (int j = 0; j < k[q]; ++j) {
+                src.push_back(xoff[q] + (int64_t)j * n[q]);
+                dsto.push_back(boff(q, blk3) + (int64_t)j * ld);
+                len.push_back(n[q]);
+            }
+        auto a = C.up(src);
+        auto b = C.up(dsto);
+        auto c = C.up(len);
+        PScope ps(h, PK_SMALL);
+        launch_gather_rows<T>(X0, a, S, b, c, (int64_t)src.size(), h->s);
+    }
+    std::vector<int64_t> soff(nq);
+    for (int q = 0; q < nq; ++q) soff[q] = boff(q, blk3);
+    std::vector<int> rs = orth_rows<T>(C, S, soff, k, n, ld);
+    std::vector<int> kx = rayleigh_ritz(rs);
+    std::vector<char> haveP(nq, 0), live(nq, 1);
+    for (int it = 0;; ++it) {
+        // residuals of the live matrices
+        std::vector<ResidDesc<T>> rd;
+        std::vector<int> qs;
+        for (int q = 0; q < nq; ++q)
+            if (live[q]) {
+                rd.push_back({X + boff(q, blk), TX + boff(q, blk), R + boff(q, blk), theta + (int64_t)q * maxk,
+                              rn + (int64_t)q * maxk, ld, n[q], kx[q], std::min(p[q], kx[q])});
+                qs.push_back(q);
+            }
+        if (qs.empty()) break;
+        {
+            auto d = C.up(rd);
+            PScope ps(h, PK_SMALL);
+            launch_residual_rows<T>(d, (int)rd.size(), h->s);
+        }
+        std::vector<double> hr((size_t)nq * maxk);
+        ck(cudaMemcpyAsync(hr.data(), rn, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        ck(cudaStreamSynchronize(h->s));
+        bool any = false;
+        for (int q : qs) {
+            double mx = 0.0;
+            for (int j = 0; j < std::min(p[q], kx[q]); ++j) mx = std::max(mx, hr[(size_t)q * maxk + j]);
+            if (mx <= tol && kx[q] >= p[q]) {
+                live[q] = 0;
+                ok[q] = 1;
+                iters[q] = it;
+            } else if (it >= maxit) {
+                live[q] = 0;
+                iters[q] = it;
+            } else {
+                any = true;
+            }
+        }
+        if (!any) break;
+        // S = [X; R; P] for the live matrices (frozen ones keep a copy of X)
+        std::vector<int> r3(nq);
+        for (int q = 0; q < nq; ++q) r3[q] = live[q] ? kx[q] * (haveP[q] ? 3 : 2) : kx[q];
+        {
+            std::vector<int64_t> src, dsto;
+            std::vector<int32_t> len;
+            auto add = [&](int q, int rfrom, int rto, int cnt) {
+                for (int j = 0; j < cnt; ++j) {
+                    src.push_back(boff(q, blk) + (int64_t)(rfrom + j) * ld);
+                    dsto.push_back(boff(q, blk3) + (int64_t)(rto + j) * ld);
+                    len.push_back(n[q]);
+                }
+            };
+            // three gathers (X, R, P) share the block layout of X
+            for (int pass = 0; pass < 3; ++pass) {
+                src.clear();
+                dsto.clear();
+                len.clear();
+                const T* from = pass == 0 ? X : (pass == 1 ? R : P);
+                for (int q = 0; q < nq; ++q) {
+                    if (pass == 0) add(q, 0, 0, kx[q]);
+                    if (pass == 1 && live[q]) add(q, 0, kx[q], kx[q]);
+                    if (pass == 2 && live[q] && haveP[q]) add(q, 0, 2 * kx[q], kx[q]);
+                }
+                if (src.empty()) continue;
+                auto a = C.up(src);
+                auto b = C.up(dsto);
+                auto c = C.up(len);
+                PScope ps(h, PK_SMALL);
+                launch_gather_rows<T>(from, a, S, b, c, (int64_t)src.size(), h->s);
+            }
+        }
+        // keep the old X for the search direction
+        copy_rows(X, blk, R, blk, kx, 0, 0);
+        const std::vector<int> kold = kx;
+        rs = orth_rows<T>(C, S, soff, r3, n, ld);
+        kx = rayleigh_ritz(rs);
+        // P = X_new - (X_new X_old^T) X_old (X_old in R)
+        std::vector<GemmDescT<T>> g1, g2;
+        for (int q = 0; q < nq; ++q) {
+            if (!live[q]) continue;
+            g1.push_back(gd<T>(X + boff(q, blk), ld, 0, R + boff(q, blk), ld, 1, M + (int64_t)q * maxk * maxk, maxk,
+                               kx[q], kold[q], n[q], 1.0, 0.0, 0));
+        }
+        gemm(C, g1);
+        copy_rows(X, blk, P, blk, kx, 0, 0);
+        for (int q = 0; q < nq; ++q) {
+            if (!live[q]) continue;
+            g2.push_back(gd<T>(M + (int64_t)q * maxk * maxk, maxk, 0, R + boff(q, blk), ld, 0, P + boff(q, blk), ld,
+                               kx[q], n[q], kold[q], -1.0, 1.0, 0));
+            haveP[q] = 1;
+        }
+        gemm(C, g2);
+    }
+    // Ritz vectors back to the caller's layout
+    std::vector<int64_t> src, dsto;
+    std::vector<int32_t> len;
+    for (int q = 0; q < nq; ++q)
+        for (int j = 0; j < std::min(p[q], kx[q]); ++j) {
+            src.push_back(boff(q, blk) + (int64_t)j * ld);
+            dsto.push_back(xoff[q] + (int64_t)j * n[q]);
+            len.push_back(n[q]);
+        }
+    auto a = C.up(src);
+    auto b = C.up(dsto);
+    auto c = C.up(len);
+    PScope ps(h, PK_SMALL);
+    launch_gather_rows<T>(X, a, X0, b, c, (int64_t)src.size(), h->s);
+}
+
+// MLP forward on n standardised feature rows X (n x 32): Q (n x 16 x 16,
+// symmetrised).  Work: Z1, H1, Z2, H2, Y (n x 256 each).
+void mlp_forward(Ctx& C, const float* Wb, const float* X, int n, float* work, float* Q) {
+    amdd_handle* h = C.h;
+    float* Z1 = work;
+    float* H1 = Z1 + (size_t)n * PROP_NH;
+    float* Z2 = H1 + (size_t)n * PROP_NH;
+    float* H2 = Z2 + (size_t)n * PROP_NH;
+    float* Y = H2 + (size_t)n * PROP_NH;
+    gemm(C, std::vector<GemmDescT<float>>{gd<float>(X, PROP_NF, 0, Wb + MLP_OFF_W1, PROP_NH, 0, Z1, PROP_NH, n, PROP_NH,
+                                                    PROP_NF, 1.0, 0.0, 0)});
+    launch_bias_act(Z1, Wb + MLP_OFF_B1, H1, n, PROP_NH, h->s);
+    gemm(C, std::vector<GemmDescT<float>>{gd<float>(H1, PROP_NH, 0, Wb + MLP_OFF_W2, PROP_NH, 0, Z2, PROP_NH, n, PROP_NH,
+                                                    PROP_NH, 1.0, 0.0, 0)});
+    launch_bias_act(Z2, Wb + MLP_OFF_B2, H2, n, PROP_NH, h->s);
+    gemm(C, std::vector<GemmDescT<float>>{gd<float>(H2, PROP_NH, 0, Wb + MLP_OFF_W3, PROP_NO, 0, Y, PROP_NO, n, PROP_NO,
+                                                    PROP_NH, 1.0, 0.0, 0)});
+    launch_bias_act(Y, Wb + MLP_OFF_B3, nullptr, n, PROP_NO, h->s);
+    launch_symmetrise(Y, Q, n, h->s);
+}
+
+// Gradient of the mean squared Frobenius error (forward with Wb, work as in
+// mlp_forward plus Q, dY, dH, dZ (n x 256) and n partial sums).
+void mlp_backward(Ctx& C, const float* Wb, const float* X, const float* Qt, int n, float* work, float* grad,
+                  float* loss) {
+    amdd_handle* h = C.h;
+    const size_t L = (size_t)n * PROP_NH;
+    float* Z1 = work;
+    float* H1 = Z1 + L;
+    float* Z2 = H1 + L;
+    float* H2 = Z2 + L;
+    float* Q = H2 + 2 * L;  // after Y
+    float* dY = Q + L;
+    float* dH = dY + L;
+    float* dZ = dH + L;
+    float* part = dZ + L;
+    mlp_forward(C, Wb, X, n, work, Q);
+    launch_loss_grad(Q, Qt, dY, part, loss, n, h->s);
+    // output layer
+    gemm(C, std::vector<GemmDescT<float>>{gd<float>(H2, PROP_NH, 1, dY, PROP_NO, 0, grad + MLP_OFF_W3, PROP_NO, PROP_NH,
+                                                    PROP_NO, n, 1.0, 0.0, 0)});
+    launch_colsum(dY, grad + MLP_OFF_B3, n, PROP_NO, h->s);
+    gemm(C, std::vector<GemmDescT<float>>{gd<float>(dY, PROP_NO, 0, Wb + MLP_OFF_W3, PROP_NO, 1, dH, PROP_NH, n, PROP_NH,
+                                                    PROP_NO, 1.0, 0.0, 0)});
+    launch_relu_back(dH, Z2, dZ, n * PROP_NH, h->s);
+    // second hidden layer
+    gemm(C, std::vector<GemmDescT<float>>{gd<float>(H1, PROP_NH, 1, dZ, PROP_NH, 0, grad + MLP_OFF_W2, PROP_NH, PROP_NH,
+                                                    PROP_NH, n, 1.0, 0.0, 0)});
+    launch_colsum(dZ, grad + MLP_OFF_B2, n, PROP_NH, h->s);
+    gemm(C, std::vector<GemmDescT<float>>{gd<float>(dZ, PROP_NH, 0, Wb + MLP_OFF_W2, PROP_NH, 1, dH, PROP_NH, n, PROP_NH,
+                                                    PROP_NH, 1.0, 0.0, 0)});
+    launch_relu_back(dH, Z1, dZ, n * PROP_NH, h->s);
+    // first layer
+    gemm(C, std::vector<GemmDescT<float>>{gd<float>(X, PROP_NF, 1, dZ, PROP_NH, 0, grad + MLP_OFF_W1, PROP_NH, PROP_NF,
+                                                    PROP_NH, n, 1.0, 0.0, 0)});
+    launch_colsum(dZ, grad + MLP_OFF_B1, n, PROP_NH, h->s);
+}
+
+// Eigenvectors of the partial selections without the dense Jacobi: the
+// features and Krylov bases of those subdomains (kept in the handle for
+// amdd_proposal_export when asked), then, with eig_solver >= 1, block LOBPCG
+// for the p_i eigenvectors of T_i with the smallest mu, started from random
+// rows (eig_solver = 1) or from the learned proposal (eig_solver = 2: the MLP
+// predicts the projector onto the selected space on the Krylov basis; its
+// leading eigenvectors B W give u, mapped to T's coordinates by w = L_A^T u,
+// and random rows fill the block).  A result is accepted when every wanted
+// residual is within the tolerance, the rows are orthonormal and the Ritz
+// values agree with the bisection eigenvalues (a missed mode would show as a
+// Ritz value above tau); its rows go to Wsel.  Returns the subdomains left to the dense path.
+template <typename T>
+std::vector<int> learned_eigvecs(Ctx& C, amdd_handle* h, const std::vector<int>& partial, const double* Araw, T* Lb,
+                                 const T* TI, const std::vector<int64_t>& off_ti, T* Wsel) {
+    constexpr bool f64 = std::is_same<T, double>::value;
+    cudaStream_t s = h->s;
+    const int np = (int)partial.size();
+    std::vector<int64_t> off_b(np + 1, 0), off_w(np + 1, 0);
+    for (int q = 0; q < np; ++q) {
+        const int nIi = h->nI[partial[q]];
+        off_b[q + 1] = off_b[q] + (int64_t)PROP_NB * nIi;
+        off_w[q + 1] = off_w[q] + nIi;
+    }
+    const bool warm = h->eig_solver == 2 && h->have_prop;
+    float* feat = nullptr;
+    double* bt = nullptr;
+    if (warm || h->keep_prop) {
+        feat = C.tnew<float>((int64_t)np * PROP_NF);
+        bt = C.tnew<double>(off_b[np]);
+        double* wscr = C.tnew<double>(off_w[np]);
+        std::vector<FeatDesc> fd(np);
+        std::vector<KrylovDesc> kd(np);
+        for (int q = 0; q < np; ++q) {
+            const int i = partial[q], ni = h->ni[i];
+            fd[q] = {Araw + h->off_sq[i], ni, ni, h->nI[i], h->nG[i], h->nD[i], h->p[i], h->tau, feat + (int64_t)q * PROP_NF};
+            kd[q] = {Araw + h->off_sq[i], ni, h->nI[i], bt + off_b[q], wscr + off_w[q]};
+        }
+        auto dfd = C.up(fd);
+        auto dkd = C.up(kd);
+        PScope ps(h, PK_SMALL);
+        launch_features(dfd, np, s);
+        launch_krylov(dkd, np, s);
+        if (h->keep_prop) {
+            h->prop_feat = dnew<float>(h, (int64_t)np * PROP_NF);
+            h->prop_bt = dnew<double>(h, off_b[np]);
+            ck(cudaMemcpyAsync(h->prop_feat, feat, (size_t)np * PROP_NF * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            ck(cudaMemcpyAsync(h->prop_bt, bt, off_b[np] * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            h->prop_sub = partial;
+            h->prop_off_b = off_b;
+        }
+    }
+    if (h->eig_solver < 1) return partial;
+    std::vector<int> n(np), k(np), p(np), m(np, 0), ldt(np);
+    std::vector<int64_t> xoff(np + 1, 0), toff(np);
+    int maxk = 1;
+    for (int q = 0; q < np; ++q) {
+        const int i = partial[q];
+        n[q] = h->nI[i];
+        p[q] = h->p[i];
+        k[q] = std::min(n[q], p[q] + std::max(4, p[q] / 8));
+        xoff[q + 1] = xoff[q] + (int64_t)k[q] * n[q];
+        toff[q] = off_ti[i];
+        ldt[q] = 2 * n[q];
+        maxk = std::max(maxk, k[q]);
+    }
+    T* X0 = C.tnew<T>(xoff[np]);
+    if (warm) {
+        float* Xn = C.tnew<float>((int64_t)np * PROP_NF);
+        launch_normalize_features(feat, h->prop.mean, h->prop.sd, Xn, np, s);
+        float* work = C.tnew<float>((int64_t)5 * np * PROP_NH);
+        float* Qh = C.tnew<float>((int64_t)np * PROP_NO);
+        mlp_forward(C, h->prop.weights, Xn, np, work, Qh);
+        std::vector<int64_t> go(np);
+        std::vector<int> mm(np, PROP_NB), lg(np, PROP_NB);
+        for (int q = 0; q < np; ++q) go[q] = (int64_t)q * PROP_NO;
+        SmallEig<float> e = small_eig<float>(C, Qh, go, mm, lg);
+        float* Wt = C.tnew<float>((int64_t)np * PROP_NO);
+        std::vector<int64_t> src, dst;
+        std::vector<int32_t> len;
+        for (int q = 0; q < np; ++q) {
+            m[q] = std::min(std::min(p[q], PROP_NB), k[q]);
+            for (int j = 0; j < m[q]; ++j) {  // leading eigenvectors first
+                src.push_back(e.off[q] + (int64_t)e.row[q][PROP_NB - 1 - j] * 2 * PROP_NB + PROP_NB);
+                dst.push_back((int64_t)q * PROP_NO + (int64_t)j * PROP_NB);
+                len.push_back(PROP_NB);
+            }
+        }
+        {
+            auto a = C.up(src);
+            auto b = C.up(dst);
+            auto c = C.up(len);
+            PScope ps(h, PK_SMALL);
+            launch_gather_rows<float>(e.W, a, Wt, b, c, (int64_t)src.size(), s);
+        }
+        const T* WtT;
+        const T* BtT;
+        if constexpr (f64) {
+            double* w2 = C.tnew<double>((int64_t)np * PROP_NO);
+            launch_convert<float, double>(Wt, w2, (int64_t)np * PROP_NO, s);
+            WtT = w2;
+            BtT = bt;
+        } else {
+            float* b2 = C.tnew<float>(off_b[np]);
+            launch_convert<double, float>(bt, b2, off_b[np], s);
+            WtT = Wt;
+            BtT = b2;
+        }
+        T* U0 = C.tnew<T>(xoff[np]);
+        std::vector<RowsDesc<T>> zu(np);
+        int maxn = 1;
+        std::vector<GemmDescT<T>> g1, g2;
+        for (int q = 0; q < np; ++q) {
+            const int i = partial[q], ni = h->ni[i];
+            zu[q] = {Lb + h->off_sq[i], ni, 0, n[q], n[q], i};
+            maxn = std::max(maxn, n[q]);
+            if (m[q] == 0) continue;
+            g1.push_back(gd<T>(WtT + (int64_t)q * PROP_NO, PROP_NB, 0, BtT + off_b[q], n[q], 0, U0 + xoff[q], n[q], m[q],
+                               n[q], PROP_NB, 1.0, 0.0, 0));
+            g2.push_back(gd<T>(U0 + xoff[q], n[q], 0, Lb + h->off_sq[i], ni, 0, X0 + xoff[q], n[q], m[q], n[q], n[q], 1.0,
+                               0.0, 0));
+        }
+        {
+            auto dz = C.up(zu);
+            PScope ps(h, PK_SMALL);
+            launch_zero_upper<T>(dz, np, maxn, s);
+        }
+        gemm(C, g1);
+        gemm(C, g2);
+    }
+    {
+        std::vector<RowsDesc<T>> rd(np);
+        for (int q = 0; q < np; ++q) rd[q] = {X0 + xoff[q], n[q], m[q], k[q], n[q], partial[q]};
+        auto d = C.up(rd);
+        PScope ps(h, PK_SMALL);
+        launch_rng_rows<T>(d, np, maxk, 0x5EEDull, s);
+    }
+    const double tol = f64 ? 1e-9 : 2e-4;
+    std::vector<int> iters;
+    std::vector<char> ok;
+    std::vector<std::vector<double>> th;
+    lobpcg_rows<T>(C, TI, toff, ldt, X0, xoff, n, k, p, tol, 60, iters, ok, th);
+    // orthonormality of the returned rows (a rank-deficient block would make E singular)
+    std::vector<int64_t> oo(np + 1, 0);
+    for (int q = 0; q < np; ++q) oo[q + 1] = oo[q] + (int64_t)p[q] * p[q];
+    T* Gx = C.tnew<T>(std::max<int64_t>(oo[np], 1));
+    {
+        std::vector<GemmDescT<T>> g;
+        for (int q = 0; q < np; ++q)
+            g.push_back(gd<T>(X0 + xoff[q], n[q], 0, X0 + xoff[q], n[q], 1, Gx + oo[q], p[q], p[q], p[q], n[q], 1.0, 0.0,
+                              0));
+        gemm(C, g);
+    }
+    std::vector<T> hg(oo[np]);
+    ck(cudaMemcpyAsync(hg.data(), Gx, oo[np] * sizeof(T), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    const double otol = f64 ? 1e-8 : 1e-3;
+    std::vector<int> dense;
+    std::vector<int64_t> src, dst;
+    std::vector<int32_t> len;
+    for (int q = 0; q < np; ++q) {
+        const int i = partial[q];
+        bool accept = ok[q] && (int)th[q].size() >= p[q];
+        for (int a = 0; accept && a < p[q]; ++a)
+            for (int b = 0; b < p[q]; ++b)
+                if (std::fabs((double)hg[oo[q] + (int64_t)a * p[q] + b] - (a == b ? 1.0 : 0.0)) > otol) accept = false;
+        for (int j = 0; accept && j < p[q]; ++j) {
+            const double lam = h->lam_h[h->off_I[i] + j];
+            const double mu = std::isinf(lam) ? 0.0 : 1.0 / lam;
+            if (std::fabs(th[q][j] - mu) > 1e-3 + 1e-3 * mu) accept = false;
+        }
+        if (!accept) {
+            dense.push_back(i);
+            ++h->lob_fallbacks;
+            continue;
+        }
+        h->eig_iters[i] = iters[q];
+        ++h->lob_subs;
+        h->lob_max = std::max(h->lob_max, iters[q]);
+        h->lob_total += iters[q];
+        for (int j = 0; j < p[q]; ++j) {
+            src.push_back(xoff[q] + (int64_t)j * n[q]);
+            dst.push_back(h->off_zt[i] + (int64_t)j * n[q]);
+            len.push_back(n[q]);
+        }
+    }
+    if (!src.empty()) {
+        auto a = C.up(src);
+        auto b = C.up(dst);
+        auto c = C.up(len);
+        PScope ps(h, PK_SMALL);
+        launch_gather_rows<T>(X0, a, Wsel, b, c, (int64_t)src.size(), s);
+    }
+    return dense;
+}
+
 // T: type of the local work (factors of A_ii, T = L_A^{-1} S L_A^{-T}, its
 // eigensolve, Z_i).  TS: type of the splitting (SVD of X_i, Abar_ii and its
 // Schur complement S).
@@ -690,7 +1380,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         Il[part[g]].push_back((int32_t)g);
     }
     for (int i = 0; i < N; ++i) require(!Il[i].empty());
-    h->spmv_group = (nnz / std::max<int64_t>(n, 1) <= 8) ? 4 : (nnz / std::max<int64_t>(n, 1) <= 24 ? 8 : 32);
+    h->spmv_group = (nnz / std::max<int64_t>(n, 1) <= 8) ? 1 : (nnz / std::max<int64_t>(n, 1) <= 24 ? 8 : 32);
 
     // ---- overlap Omega_Gi (distance 1..ov) and extension Omega_Di (ov+1)
     std::vector<std::vector<int32_t>> Gl(N), Dl(N);
@@ -1128,15 +1818,24 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             PScope ps(h, PK_SMALL);
             launch_gather_rows<T>(Yl, a, ZtT, b, c, (int64_t)ysrc.size(), s);
         }
-        if (!partial.empty()) {
-            const int np = (int)partial.size();
+        h->n_partial = (int)partial.size();
+        h->eig_iters.assign(N, -2);
+        T* Wsel = partial.empty() ? nullptr : C.tnew<T>(h->sum_zt);
+        std::vector<int> dense = partial;  // subdomains whose eigenvectors come from the dense Jacobi
+        if (!partial.empty() && (h->eig_solver >= 1 || h->keep_prop)) {
+            dense = learned_eigvecs<T>(C, h, partial, Araw, Lb, TI, off_ti, Wsel);
+        }
+        for (int i : dense) h->eig_iters[i] = -1;
+        if (!dense.empty()) {
+            const std::vector<int>& partial_d = dense;
+            const int np = (int)partial_d.size();
             std::vector<JacobiDescT<T>> jd(np);
             std::vector<double*> mp(np);
             double* mu_j = C.tnew<double>(h->sum_nI);
             T* nrmE = C.tnew<T>(h->sum_nI);  // row norms of the eigen-Jacobi
             int maxc = 1;
             for (int q = 0; q < np; ++q) {
-                const int i = partial[q], nIi = h->nI[i];
+                const int i = partial_d[q], nIi = h->nI[i];
                 jd[q] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrmE + h->off_I[i], nullptr};
                 mp[q] = mu_j + h->off_I[i];
                 maxc = std::max(maxc, nIi);
@@ -1163,7 +1862,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             std::vector<int64_t> wsrc, wdst;
             std::vector<int32_t> wlen;
             for (int q = 0; q < np; ++q) {
-                const int i = partial[q], nIi = h->nI[i];
+                const int i = partial_d[q], nIi = h->nI[i];
                 h->sweeps_eig = std::max(h->sweeps_eig, sw[N + q]);
                 h->rot_eig += (int64_t)rot_h[N + q];
                 if (h->prof.on)
@@ -1179,7 +1878,6 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                     wlen.push_back(nIi);
                 }
             }
-            T* Wsel = C.tnew<T>(h->sum_zt);
             {
                 auto a = C.up(wsrc);
                 auto b = C.up(wdst);
@@ -1187,6 +1885,8 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                 PScope ps(h, PK_SMALL);
                 launch_gather_rows<T>(TI, a, Wsel, b, c, (int64_t)wsrc.size(), s);
             }
+        }
+        if (!partial.empty()) {
             std::vector<GemmDescT<T>> g;
             for (int i : partial)
                 g.push_back(gd<T>(Wsel + h->off_zt[i], h->nI[i], 0, Yl + h->off_sq[i], h->ni[i], 0,
@@ -1305,8 +2005,10 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         chol_batched<double>(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}}, {&h->env_row});
         // Inverses of the diagonal blocks of L_E (block size cSB): the coarse
         // solve is then a blocked forward / backward substitution with L_E and
-        // L_E^T (row GEMVs), with no inverse of the whole factor.
-        const int SB = std::max<int>(CHOL_NB, cdiv(cdiv(nC, 8), CHOL_NB) * CHOL_NB);
+        // L_E^T, with no inverse of the whole factor.  About four blocks (each
+        // costs two grid-wide phases per coarse solve), at most 1024 wide (the
+        // inverses are stored dense).
+        const int SB = std::min<int>(1024, std::max<int>(CHOL_NB, cdiv(cdiv(nC, 4), CHOL_NB) * CHOL_NB));
         const int K = cdiv(nC, SB);
         h->cSB = SB;
         h->cK = K;
@@ -1353,16 +2055,14 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         }
         h->d_c = dnew<double>(h, nC);
         h->d_e = dnew<double>(h, nC);
-        std::vector<int32_t> rd, rl, rdc, rlc;
-        rd.reserve(h->sum_ni);
-        rl.reserve(h->sum_ni);
+        std::vector<int32_t> rd, rl, rdc, rlc;  // rd / rl: row groups of the local products (matrix, first row)
         for (int i = 0; i < N; ++i) {
             const int ni = h->ni[i];
             l1[i] = {Yl + h->off_sq[i], ni, ni, ni, 1, rlocT + h->off_om[i], tlocT + h->off_om[i]};
             l2[i] = {Ylt + h->off_sq[i], ni, ni, ni, 2, tlocT + h->off_om[i], ylocT + h->off_om[i]};
             cr[i] = {h->d_Zt + h->off_zt[i], h->p[i], h->nI[i], h->nI[i], 0, h->d_rloc + h->off_om[i],
                      h->d_c + h->coff[i]};
-            for (int a = 0; a < ni; ++a) {
+            for (int a = 0; a < ni; a += GEMV_ROWS_PER_WARP) {
                 rd.push_back(i);
                 rl.push_back(a);
             }
@@ -1379,8 +2079,9 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             h->d_gv_l2_32 = C.up(l2, true);
         }
         h->d_gv_c = C.up(cr, true);
-        h->d_rd_loc = C.up(rd, true);
-        h->d_rl_loc = C.up(rl, true);
+        h->d_g4_desc = C.up(rd, true);
+        h->d_g4_row = C.up(rl, true);
+        h->n_g4 = (int64_t)rd.size();
         h->d_rd_c = C.up(rdc, true);
         h->d_rl_c = C.up(rlc, true);
         // coarse solve L_E L_E^T e = c: blocked forward / backward substitution
@@ -1448,11 +2149,11 @@ void apply_one(amdd_handle* h, const double* r, double* z) {
     if (h->precision == 0) {
         {
             PScope ps(h, PK_GEMV, tri, 8.0 * tri / 2 + 24.0 * h->sum_ni);
-            launch_gemv_rows<double>(h->d_gv_l1, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+            launch_gemv_rows4<double>(h->d_gv_l1, h->d_g4_desc, h->d_g4_row, h->n_g4, s);
         }
         {
             PScope ps(h, PK_GEMV, tri, 8.0 * tri / 2 + 24.0 * h->sum_ni);
-            launch_gemv_rows<double>(h->d_gv_l2, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+            launch_gemv_rows4<double>(h->d_gv_l2, h->d_g4_desc, h->d_g4_row, h->n_g4, s);
         }
     } else {
         // mixed form: local solves in FP32 (FP32 factors, FP32 accumulation)
@@ -1462,11 +2163,11 @@ void apply_one(amdd_handle* h, const double* r, double* z) {
         }
         {
             PScope ps(h, PK_GEMV_F32, tri, 4.0 * tri / 2 + 12.0 * h->sum_ni);
-            launch_gemv_rows<float>(h->d_gv_l1_32, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+            launch_gemv_rows4<float>(h->d_gv_l1_32, h->d_g4_desc, h->d_g4_row, h->n_g4, s);
         }
         {
             PScope ps(h, PK_GEMV_F32, tri, 4.0 * tri / 2 + 12.0 * h->sum_ni);
-            launch_gemv_rows<float>(h->d_gv_l2_32, h->d_rd_loc, h->d_rl_loc, h->sum_ni, s);
+            launch_gemv_rows4<float>(h->d_gv_l2_32, h->d_g4_desc, h->d_g4_row, h->n_g4, s);
         }
     }
     if (h->nC > 0) {
@@ -1540,7 +2241,7 @@ amdd_status amdd_spmv(const amdd_csr* A, const double* x, double* y, void* strea
     if (A->n > INT32_MAX) return AMDD_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t per = A->n ? A->nnz / A->n : 0;
-    launch_spmv(A->n, A->rowptr, A->colind, A->val, x, y, per <= 8 ? 4 : (per <= 24 ? 8 : 32), s);
+    launch_spmv(A->n, A->rowptr, A->colind, A->val, x, y, per <= 8 ? 1 : (per <= 24 ? 8 : 32), s);
     if (cudaGetLastError() != cudaSuccess) return AMDD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return AMDD_ERR_CUDA;
     return AMDD_OK;
@@ -1588,9 +2289,13 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
     if (opts) {
         o = *opts;
         if (!(o.eps > 0.0) || o.max_sweeps < 1 || o.precision < 0 || o.precision > 2) return AMDD_ERR_INVALID;
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 2; ++k)
             if (o.reserved[k] != 0) return AMDD_ERR_INVALID;
         if (o.profile_classes >> PK_COUNT) return AMDD_ERR_INVALID;
+        if (o.eig_solver < 0 || o.eig_solver > 2) return AMDD_ERR_INVALID;
+        if (o.eig_solver == 2 &&
+            (!o.proposal || !o.proposal->weights || !o.proposal->mean || !o.proposal->sd))
+            return AMDD_ERR_INVALID;
     }
     const auto t0 = std::chrono::steady_clock::now();
     amdd_handle* h = nullptr;
@@ -1610,6 +2315,12 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         h->prof.on = o.profile != 0;
         h->prof.mask = o.profile_classes ? o.profile_classes : ~0u;
         h->precision = o.precision;
+        h->eig_solver = o.eig_solver;
+        h->keep_prop = o.keep_proposal_data != 0;
+        if (o.eig_solver == 2) {
+            h->prop = *o.proposal;
+            h->have_prop = true;
+        }
         if (o.precision == 0)
             do_setup<double, double>(h, A, part);
         else if (o.precision == 1)
@@ -1697,6 +2408,154 @@ void lanczos_extremes(const std::vector<double>& al, const std::vector<double>& 
 }
 
 }  // namespace
+
+amdd_status amdd_get_eig_iterations(const amdd_handle* h, int32_t* iters, int32_t cap) {
+    if (!h || !iters || cap < h->N) return AMDD_ERR_INVALID;
+    for (int i = 0; i < h->N; ++i) iters[i] = i < (int)h->eig_iters.size() ? h->eig_iters[i] : -2;
+    return AMDD_OK;
+}
+
+amdd_status amdd_proposal_export(const amdd_handle* hc, float* feat, float* target, int32_t* sub, int32_t cap,
+                                 int32_t* count) {
+    if (!hc || !count) return AMDD_ERR_INVALID;
+    amdd_handle* h = const_cast<amdd_handle*>(hc);
+    if (!h->keep_prop) return AMDD_ERR_INVALID;
+    const int np = (int)h->prop_sub.size();
+    *count = np;
+    if (!feat && !target && !sub) return AMDD_OK;
+    if (cap < np) return AMDD_ERR_INVALID;
+    if (np == 0) return AMDD_OK;
+    try {
+        cudaStream_t s = h->s;
+        if (feat)
+            ck(cudaMemcpyAsync(feat, h->prop_feat, (size_t)np * PROP_NF * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (sub)
+            for (int q = 0; q < np; ++q) sub[q] = h->prop_sub[q];
+        if (target) {
+            // B^T Q Q^T B = G M^{-1} G^T with G = Bt Zt^T (16 x p) and M = Zt Zt^T = L_M L_M^T:
+            // H = G L_M^{-T}, target = H H^T
+            Ctx C(h);
+            std::vector<int64_t> om(np + 1, 0), og(np + 1, 0);
+            for (int q = 0; q < np; ++q) {
+                const int pq = h->p[h->prop_sub[q]];
+                om[q + 1] = om[q] + (int64_t)pq * pq;
+                og[q + 1] = og[q] + (int64_t)PROP_NB * pq;
+            }
+            double* M = C.tnew<double>(om[np]);
+            double* Mi = C.tnew<double>(om[np]);
+            double* G = C.tnew<double>(og[np]);
+            double* H = C.tnew<double>(og[np]);
+            double* Q = C.tnew<double>((int64_t)np * PROP_NO);
+            int64_t lsz = 0;
+            for (int q = 0; q < np; ++q) lsz += (int64_t)cdiv(h->p[h->prop_sub[q]], CHOL_NB) * CHOL_NB * CHOL_NB;
+            double* linv = C.tnew<double>(lsz);
+            std::vector<GemmDesc> g1, g2;
+            std::vector<CholDesc> cd;
+            std::vector<TrtriDesc> td;
+            int64_t lo = 0;
+            for (int q = 0; q < np; ++q) {
+                const int i = h->prop_sub[q], pq = h->p[i], nIi = h->nI[i];
+                const double* Zt = h->d_Zt + h->off_zt[i];
+                g1.push_back(gd(Zt, nIi, 0, Zt, nIi, 1, M + om[q], pq, pq, pq, nIi, 1.0, 0.0, 0));
+                g2.push_back(gd(h->prop_bt + h->prop_off_b[q], nIi, 0, Zt, nIi, 1, G + og[q], pq, PROP_NB, pq, nIi, 1.0,
+                                0.0, 0));
+                cd.push_back({M + om[q], pq, pq, pq, nullptr, linv + lo});
+                td.push_back({M + om[q], Mi + om[q], linv + lo, pq, pq, pq});
+                lo += (int64_t)cdiv(pq, CHOL_NB) * CHOL_NB * CHOL_NB;
+            }
+            gemm(C, g1);
+            gemm(C, g2);
+            chol_batched<double>(C, cd);
+            trtri_batched<double>(C, td);
+            std::vector<GemmDesc> g3, g4;
+            for (int q = 0; q < np; ++q) {
+                const int pq = h->p[h->prop_sub[q]];
+                g3.push_back(gd(G + og[q], pq, 0, Mi + om[q], pq, 1, H + og[q], pq, PROP_NB, pq, pq, 1.0, 0.0, 0));
+                g4.push_back(gd(H + og[q], pq, 0, H + og[q], pq, 1, Q + (int64_t)q * PROP_NO, PROP_NB, PROP_NB, PROP_NB,
+                                pq, 1.0, 0.0, 0));
+            }
+            gemm(C, g3);
+            gemm(C, g4);
+            std::vector<double> hq((size_t)np * PROP_NO);
+            ck(cudaMemcpyAsync(hq.data(), Q, hq.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            ck(cudaStreamSynchronize(s));
+            {
+                const int e = read_err(h);
+                if (e) throw Fail{err_status(e)};
+            }
+            for (size_t t = 0; t < hq.size(); ++t) target[t] = (float)hq[t];
+        }
+        ck(cudaStreamSynchronize(s));
+    } catch (...) {
+        return guard_exc();
+    }
+    return AMDD_OK;
+}
+
+// The MLP entry points run on a transient handle that only carries the
+// stream (no profiling), so the batched GEMM and its uploads serve them too.
+amdd_status amdd_mlp_sizes(int32_t n, int64_t* nparam, int64_t* nwork) {
+    if (n < 1 || !nparam || !nwork) return AMDD_ERR_INVALID;
+    *nparam = MLP_NPARAM;
+    *nwork = (int64_t)9 * n * PROP_NH + n + 16;
+    return AMDD_OK;
+}
+
+amdd_status amdd_mlp_normalize(const float* feat, const float* mean, const float* sd, int32_t n, float* x,
+                               void* stream) {
+    if (n < 1 || !feat || !mean || !sd || !x) return AMDD_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    launch_normalize_features(feat, mean, sd, x, n, s);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return AMDD_ERR_CUDA;
+    return AMDD_OK;
+}
+
+amdd_status amdd_mlp_forward(const float* wb, const float* x, int32_t n, float* q, float* work, void* stream) {
+    if (n < 1 || !wb || !x || !q || !work) return AMDD_ERR_INVALID;
+    try {
+        amdd_handle tmp;
+        tmp.s = static_cast<cudaStream_t>(stream);
+        {
+            Ctx C(&tmp);
+            mlp_forward(C, wb, x, n, work, q);
+            ck(cudaGetLastError());
+            ck(cudaStreamSynchronize(tmp.s));
+        }
+        ck(cudaStreamSynchronize(tmp.s));
+    } catch (...) {
+        return guard_exc();
+    }
+    return AMDD_OK;
+}
+
+amdd_status amdd_mlp_train_step(float* w, float* wb, float* m, float* v, int32_t t, float lr, const float* x,
+                                const float* qt, int32_t n, float* grad, float* work, float* loss, void* stream) {
+    if (n < 1 || !wb || !x || !qt || !grad || !work || !loss || !(lr >= 0.0f)) return AMDD_ERR_INVALID;
+    if (lr > 0.0f && (!w || !m || !v || t < 1)) return AMDD_ERR_INVALID;
+    try {
+        amdd_handle tmp;
+        tmp.s = static_cast<cudaStream_t>(stream);
+        {
+            Ctx C(&tmp);
+            mlp_backward(C, wb, x, qt, n, work, grad, loss);
+            if (lr > 0.0f) launch_adam(w, wb, m, v, grad, (int)MLP_NPARAM, lr, t, tmp.s);
+            ck(cudaGetLastError());
+            ck(cudaStreamSynchronize(tmp.s));
+        }
+        ck(cudaStreamSynchronize(tmp.s));
+    } catch (...) {
+        return guard_exc();
+    }
+    return AMDD_OK;
+}
+
+amdd_status amdd_mlp_round_bf16(const float* w, float* wb, int64_t n, void* stream) {
+    if (n < 1 || n > INT32_MAX || !w || !wb) return AMDD_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    launch_bf16_round(w, wb, (int)n, s);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return AMDD_ERR_CUDA;
+    return AMDD_OK;
+}
 
 amdd_status amdd_lanczos_extremes(const double* alpha, const double* beta, int32_t k, double* lo, double* hi) {
     if (k < 0 || !lo || !hi || (k > 0 && !alpha) || (k > 1 && !beta)) return AMDD_ERR_INVALID;
@@ -1827,6 +2686,11 @@ amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
     info->sweeps_eig32 = h->sweeps_eig32;
     info->precision = h->precision;
     info->eps = h->eps;
+    info->n_partial = h->n_partial;
+    info->lobpcg_subdomains = h->lob_subs;
+    info->lobpcg_fallbacks = h->lob_fallbacks;
+    info->lobpcg_iters_max = h->lob_max;
+    info->lobpcg_iters_total = h->lob_total;
     return AMDD_OK;
 }
 

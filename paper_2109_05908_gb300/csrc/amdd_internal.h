@@ -20,6 +20,7 @@ enum : int {
 constexpr int CHOL_NB = 32;     // diagonal block of the blocked Cholesky / inverse
 constexpr int GEMM_T = 64;      // GEMM output tile
 constexpr int PANEL_ROWS = 16;  // rows per CTA of the Cholesky panel solve
+constexpr int GEMV_ROWS_PER_WARP = 4;  // rows per warp of the local triangular products
 constexpr int JAC_CLUSTER = 8;  // CTAs per matrix in the Jacobi solvers
 constexpr int JAC_MAX_PAIRS = 64;  // largest sub-round of the shared-memory block Jacobi
 
@@ -162,6 +163,9 @@ template <typename T>
 void launch_gemv_rows(const GemvDescT<T>* d, const int* row_desc, const int* row_local, int64_t nrows,
                       cudaStream_t s);
 template <typename T>
+void launch_gemv_rows4(const GemvDescT<T>* d, const int* grp_desc, const int* grp_row, int64_t ngroups,
+                       cudaStream_t s);
+template <typename T>
 void launch_tridiag(const TridiagDescT<T>* d, int nmat, int maxn, cudaStream_t s);
 template <typename T>
 void launch_bisect(const TridiagDescT<T>* d, int nmat, const int* eig_mat, const int* eig_idx, int64_t total,
@@ -201,6 +205,91 @@ void launch_e_offdiag(const EPairRef* tiles, int ntiles, const int32_t* la, cons
 // Deterministic dot products: fixed grid of DOT_BLOCKS partial sums reduced in
 // a fixed order by one block.
 constexpr int DOT_BLOCKS = 264;
+// ---------------------------------------------------------------------------
+// Learned warm start of the local eigensolve and block LOBPCG
+// ---------------------------------------------------------------------------
+constexpr int PROP_NF = 32;    // features per subdomain
+constexpr int PROP_NB = 16;    // Krylov basis vectors
+constexpr int PROP_NH = 256;   // hidden width
+constexpr int PROP_NO = 256;   // outputs: a 16 x 16 matrix
+// parameter layout: W1 (32 x 256), b1, W2 (256 x 256), b2, W3 (256 x 256), b3
+constexpr int64_t MLP_OFF_W1 = 0;
+constexpr int64_t MLP_OFF_B1 = MLP_OFF_W1 + PROP_NF * PROP_NH;
+constexpr int64_t MLP_OFF_W2 = MLP_OFF_B1 + PROP_NH;
+constexpr int64_t MLP_OFF_B2 = MLP_OFF_W2 + PROP_NH * PROP_NH;
+constexpr int64_t MLP_OFF_W3 = MLP_OFF_B2 + PROP_NH;
+constexpr int64_t MLP_OFF_B3 = MLP_OFF_W3 + PROP_NH * PROP_NO;
+constexpr int64_t MLP_NPARAM = MLP_OFF_B3 + PROP_NO;
+
+// Features of subdomain i from its dense local matrix A_ii (rows [I, G],
+// leading dimension ld, ncols = |Omega_i|):
+//  0 log nI, 1 log(1+nG), 2 log(1+nD), 3 nG/nI, 4 nD/nI,
+//  5-8 mean/std/min/max of log diag(A_II), 9-12 the same of log|off-diagonal
+//  non-zeros of A_II|, 13 max - min of log diag, 14-16 mean/std/max of the
+//  off-diagonal non-zeros per row, 17 fraction of rows coupled to Omega_G,
+//  18-19 mean/max of sum_G |a_rg| / a_rr, 20-23 mean/std/min/max of
+//  sum_{c != r} |a_rc| / a_rr, 24 log(||A_II||_F / nI), 25 log(trace / nI),
+//  26 fraction of positive off-diagonal non-zeros, 27 log(max(p,1)/nI),
+//  28 log max(p,1), 29 log tau, 30 mean log diag over coupled rows minus
+//  the mean over all rows, 31 the constant 1.
+struct FeatDesc {
+    const double* A;
+    int ld, ncols, nI, nG, nD, p;
+    double tau;
+    float* out;  // 32 entries
+};
+void launch_features(const FeatDesc* d, int nmat, cudaStream_t s);
+
+struct KrylovDesc {
+    const double* A;  // A_II is the leading nI x nI block (leading dimension ld)
+    int ld, nI;
+    double* Bt;  // PROP_NB x nI, rows = basis vectors
+    double* w;   // nI scratch
+};
+void launch_krylov(const KrylovDesc* d, int nmat, cudaStream_t s);
+
+void launch_normalize_features(const float* feat, const float* mean, const float* sd, float* X, int n,
+                               cudaStream_t s);
+void launch_bias_act(float* Z, const float* bias, float* H, int rows, int cols, cudaStream_t s);
+void launch_symmetrise(const float* Y, float* Q, int n, cudaStream_t s);
+void launch_loss_grad(const float* Q, const float* Qt, float* dY, float* part, float* loss, int n, cudaStream_t s);
+void launch_relu_back(const float* dH, const float* Z, float* dZ, int n, cudaStream_t s);
+void launch_colsum(const float* dZ, float* db, int rows, int cols, cudaStream_t s);
+void launch_adam(float* W, float* Wb, float* m, float* v, const float* g, int n, float lr, int t, cudaStream_t s);
+void launch_bf16_round(const float* W, float* Wb, int n, cudaStream_t s);
+
+template <typename T>
+struct RowsDesc {  // rows [r0, r1) of a row-major matrix (cols entries each)
+    T* A;
+    int ld, r0, r1, cols, id;
+};
+template <typename T>
+void launch_rng_rows(const RowsDesc<T>* d, int nmat, int maxrows, unsigned long long seed, cudaStream_t s);
+
+template <typename T>
+void launch_zero_upper(const RowsDesc<T>* d, int nmat, int maxrows, cudaStream_t s);
+
+template <typename T>
+struct ResidDesc {  // R = TX - diag(theta) X over k rows of n entries; norms of the first `want`
+    const T* X;
+    const T* TX;
+    T* R;
+    const T* theta;
+    double* norms;
+    int ld, n, k, want;
+};
+template <typename T>
+void launch_residual_rows(const ResidDesc<T>* d, int nmat, cudaStream_t s);
+
+template <typename T>
+struct ScaleDesc {  // A[r] *= f[r] (or 1 / ||A[r]|| with unit scaling)
+    T* A;
+    int ld, rows, cols;
+    const T* f;
+};
+template <typename T>
+void launch_scale_rows(const ScaleDesc<T>* d, int nmat, int unit, cudaStream_t s);
+
 // Coarse solve L_E L_E^T e = c (one cooperative launch; c is overwritten).
 struct CoarseSolveArgs {
     const double* L;       // factor, n x n row-major (lower), leading dimension ld

@@ -1191,6 +1191,80 @@ void launch_gemv_rows(const GemvDescT<T>* d, const int* row_desc, const int* row
 template void launch_gemv_rows<float>(const GemvDescT<float>*, const int*, const int*, int64_t, cudaStream_t);
 template void launch_gemv_rows<double>(const GemvDescT<double>*, const int*, const int*, int64_t, cudaStream_t);
 
+// Local triangular products of the apply: one warp per group of RW
+// consecutive rows of one matrix (mode 1: row r uses columns [0, r]; mode 2:
+// [r, ncols)).  The descriptor is read once per group; each loop iteration
+// issues 2 x RW independent coalesced row loads; x (one subdomain's vector)
+// stays in L1.  Per row: lane-strided partial sums (two interleaved
+// accumulators) and a fixed shuffle tree.
+constexpr int GEMV_RW = GEMV_ROWS_PER_WARP;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemv_rows4_kernel(const GemvDescT<T>* __restrict__ descs,
+                                                         const int* __restrict__ grp_desc,
+                                                         const int* __restrict__ grp_row, int64_t ngroups) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= ngroups) return;
+    const GemvDescT<T> d = descs[grp_desc[w]];
+    const int r0 = grp_row[w];
+    const int nr = min(GEMV_RW, d.rows - r0);
+    int lo[GEMV_RW], hi[GEMV_RW];
+    int cmin = d.ncols, cmax = 0;
+#pragma unroll
+    for (int k = 0; k < GEMV_RW; ++k) {
+        const int r = r0 + k;
+        lo[k] = (d.mode == 2) ? r : 0;
+        hi[k] = (d.mode == 1) ? min(r + 1, d.ncols) : d.ncols;
+        if (k >= nr) hi[k] = lo[k];
+        if (k < nr) {
+            cmin = min(cmin, lo[k]);
+            cmax = max(cmax, hi[k]);
+        }
+    }
+    const T* M0 = d.M + (size_t)r0 * d.ld;
+    T s[GEMV_RW], t[GEMV_RW];
+#pragma unroll
+    for (int k = 0; k < GEMV_RW; ++k) s[k] = t[k] = T(0);
+    int c = cmin + lane;
+    for (; c + 32 < cmax; c += 64) {
+        const T x0 = d.x[c], x1 = d.x[c + 32];
+#pragma unroll
+        for (int k = 0; k < GEMV_RW; ++k) {
+            if (c >= lo[k] && c < hi[k]) s[k] = fma(M0[(size_t)k * d.ld + c], x0, s[k]);
+            if (c + 32 >= lo[k] && c + 32 < hi[k]) t[k] = fma(M0[(size_t)k * d.ld + c + 32], x1, t[k]);
+        }
+    }
+    if (c < cmax) {
+        const T x0 = d.x[c];
+#pragma unroll
+        for (int k = 0; k < GEMV_RW; ++k)
+            if (c >= lo[k] && c < hi[k]) s[k] = fma(M0[(size_t)k * d.ld + c], x0, s[k]);
+    }
+    T mine = T(0);
+#pragma unroll
+    for (int k = 0; k < GEMV_RW; ++k) {
+        T v = s[k] + t[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == k) mine = v;
+    }
+    if (lane < nr) {
+        const int r = r0 + lane;
+        d.y[r] = d.b ? fma(d.alpha, mine, d.b[r]) : d.alpha * mine;
+    }
+}
+
+template <typename T>
+void launch_gemv_rows4(const GemvDescT<T>* d, const int* grp_desc, const int* grp_row, int64_t ngroups,
+                       cudaStream_t s) {
+    if (ngroups <= 0) return;
+    const int64_t blocks = (ngroups * 32 + 255) / 256;
+    gemv_rows4_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, grp_desc, grp_row, ngroups);
+}
+template void launch_gemv_rows4<float>(const GemvDescT<float>*, const int*, const int*, int64_t, cudaStream_t);
+template void launch_gemv_rows4<double>(const GemvDescT<double>*, const int*, const int*, int64_t, cudaStream_t);
+
 // ------------------------------------------------------------------ coarse solve
 // L_E L_E^T e = c by blocked substitution in one cooperative launch.  The
 // factor is split into K diagonal blocks of SB rows whose inverses Y_kk are

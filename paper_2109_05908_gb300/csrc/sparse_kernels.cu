@@ -7,8 +7,9 @@
 namespace amdd {
 
 // ------------------------------------------------------------------ SpMV
-// G lanes per row (G in {4, 8, 32}); rows are assigned to lane groups in a
-// grid-stride loop.
+// G lanes per row (G in {1, 8, 32}); rows are assigned to lane groups in a
+// grid-stride loop.  G = 1 (rows of at most 8 entries): the entries of a
+// row load in parallel and a warp covers 32 consecutive rows.
 template <int G>
 __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, const int64_t* __restrict__ rowptr,
                                                    const int32_t* __restrict__ col, const double* __restrict__ val,
@@ -35,8 +36,10 @@ void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
                  double* y, int group, cudaStream_t s) {
     if (n <= 0) return;
     const int64_t want = (n * group + 255) / 256;
-    const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
-    if (group <= 4)
+    const int blocks = (int)(want < 152 * 64 ? want : 152 * 64);
+    if (group <= 1)
+        spmv_kernel<1><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
+    else if (group <= 4)
         spmv_kernel<4><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
     else if (group <= 8)
         spmv_kernel<8><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
