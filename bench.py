@@ -130,7 +130,7 @@ APPLY_SCALE = {"m": 1024, "box": 16, "overlap": 1, "tau": 1e-12}
 APPLY_CLASSES = ("gemv_rows_f32", "gemv_rows", "gather_scatter", "coarse_solve")
 
 
-def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20):
+def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20, m=None):
     """SpMV and the two-level apply at scale: 2D Laplacian 1024 x 1024 (n = 1M),
     4096 boxes of 16 x 16, overlap 1, mixed form.  With tau = 1e-12 only
     eigenvalues above 1e12 enter the coarse space, so the apply is the
@@ -140,7 +140,9 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20):
     bytes are the algorithmic counts of the library's profile."""
     import synth
     from paper_2109_05908_gb300.device import DeviceMatrix
-    c = APPLY_SCALE
+    c = dict(APPLY_SCALE)
+    if m:
+        c["m"] = m
     M = synth.laplace2d(c["m"])
     part_h = synth.box_partition_2d(c["m"], c["box"])
     N = int(part_h.max()) + 1
@@ -181,6 +183,13 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20):
     prof = {p["name"]: p for p in A.get_profile(h)}
     n_calls = reps + 3
     apply_bytes = sum(prof[k]["bytes"] for k in APPLY_CLASSES if k in prof) / n_calls
+    # eight right-hand sides in one call: one pass over the factors for all
+    R8 = torch.from_numpy(synth.rhs(M.n, 4, nrhs=8)).to(dev)
+    Z8 = torch.empty_like(R8)
+    A.reset_profile(h)
+    apply8_ms = timed(lambda: A.apply(h, R8.data_ptr(), Z8.data_ptr(), 8))
+    prof8 = {p["name"]: p for p in A.get_profile(h)}
+    apply8_bytes = sum(prof8[k]["bytes"] for k in APPLY_CLASSES if k in prof8) / n_calls
     # per-launch kernel times from the library's events inside PCG: between two
     # SpMVs the apply streams ~1.7 GB of factors through L2, so each launch
     # starts cold
@@ -207,6 +216,9 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20):
                  "note": "kernel events inside PCG; call_ms is the whole amdd_spmv call (it synchronises)"},
         "apply": {"ms": apply_ms, "bytes": apply_bytes, "GB/s": apply_gbs, "frac": apply_gbs / hbm_gbs,
                   "note": "whole amdd_apply call between events (launch gaps and its final synchronisation included)"},
+        "apply_8rhs": {"ms": apply8_ms, "ms_per_rhs": apply8_ms / 8, "bytes": apply8_bytes,
+                       "GB/s": apply8_bytes / (apply8_ms * 1e-3) / 1e9,
+                       "note": "one amdd_apply call on 8 right-hand sides; factors read once for all"},
         "kernels_in_pcg": kernels,
     }
 
@@ -381,7 +393,7 @@ def run_amdd(args):
                 "launches_per_step": c["launches"] / args.steps, "ms_per_launch": per_launch_ms,
                 "peak_source": f"hbm_gbs ({peak_src})"}
     launches = int(sum(v["launches"] for v in prof.values()) / args.steps)
-    scale = apply_at_scale(A, torch, np, dev, sp, peaks["hbm_gbs"]) if not args.no_scale else None
+    scale = apply_at_scale(A, torch, np, dev, sp, peaks["hbm_gbs"], m=args.scale_m) if not args.no_scale else None
     base, base_its = cpu_baseline(w) if world == 1 or rank == 0 else (None, None)
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -435,6 +447,8 @@ def main():
     ap.add_argument("--impl", default="amdd", choices=["amdd", "reference"])
     ap.add_argument("--no-scale", action="store_true",
                     help="skip the SpMV / apply bandwidth measurement on the 1M-unknown problem")
+    ap.add_argument("--scale-m", type=int, default=None,
+                    help="grid side of the bandwidth problem (default 1024; 16 x 16 boxes)")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
                     help="0: plain FP64 form; 1: mixed form (FP32 local work, FP64 coarse and PCG); "
                          "2: mixed form with an FP64 splitting")

@@ -147,6 +147,13 @@ struct amdd_handle {
     GemvDesc* d_gv_l2 = nullptr;
     GemvDesc* d_gv_c = nullptr;
     int32_t *d_rd_c = nullptr, *d_rl_c = nullptr;
+    // coarse prolongation zc = Z e as row GEMVs over Z_i = Zt_i^T (nI x p_i)
+    double* d_Zr = nullptr;
+    double* d_zc = nullptr;
+    GemvDesc* d_gv_zp = nullptr;
+    int32_t *d_rd_zp = nullptr, *d_rl_zp = nullptr;
+    int64_t n_zp = 0;
+    std::vector<GemvDesc> gv_zp_h;  // host copy (the batched path rebinds x / y)
     int32_t *d_g4_desc = nullptr, *d_g4_row = nullptr;  // row groups (one warp each) of the local products
     int64_t n_g4 = 0;
     int32_t *d_order_g = nullptr, *d_own_sub = nullptr, *d_own_a = nullptr, *d_sc_idx = nullptr;
@@ -176,6 +183,18 @@ struct amdd_handle {
     std::vector<int> eig_iters;  // per subdomain: LOBPCG iterations, -1 dense path, -2 not partial
     int n_partial = 0, lob_subs = 0, lob_max = 0, lob_fallbacks = 0;
     int64_t lob_total = 0;
+    // batched right-hand sides (up to MAXB per pass), allocated on first use
+    int mb_cap = 0;
+    double *d_m_rloc = nullptr, *d_m_tloc = nullptr, *d_m_yloc = nullptr;
+    float *d_m_rloc32 = nullptr, *d_m_tloc32 = nullptr, *d_m_yloc32 = nullptr;
+    double *d_m_c = nullptr, *d_m_ctmp = nullptr, *d_m_e = nullptr, *d_m_zc = nullptr;
+    GemvDesc* d_m_gv_zp = nullptr;
+    double *d_m_q = nullptr, *d_m_r = nullptr, *d_m_z = nullptr, *d_m_p = nullptr, *d_m_part = nullptr;
+    PcgScal* d_m_sc = nullptr;
+    void* d_m_gv_l1 = nullptr;  // GemvDescT<double or float> per subdomain, on the batched buffers
+    void* d_m_gv_l2 = nullptr;
+    GemvDesc* d_m_gv_c = nullptr;
+    std::vector<const void*> lm1, lm2;  // per subdomain: L_i^{-1} and L_i^{-T} (FP64 or FP32)
     // kept for amdd_proposal_export: features and Krylov bases of the partial subdomains
     float* prop_feat = nullptr;
     double* prop_bt = nullptr;
@@ -2055,9 +2074,43 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         }
         h->d_c = dnew<double>(h, nC);
         h->d_e = dnew<double>(h, nC);
+        if (nC > 0) {
+            h->d_Zr = dnew<double>(h, h->sum_zt);
+            h->d_zc = dnew<double>(h, n);
+            ck(cudaMemsetAsync(h->d_zc, 0, n * sizeof(double), s));
+            std::vector<TransDesc> tdz;
+            std::vector<int32_t> rdz, rlz;
+            int maxd = 1;
+            h->gv_zp_h.clear();
+            for (int i = 0; i < N; ++i) {
+                if (h->p[i] == 0) continue;
+                const int pi = h->p[i], nIi = h->nI[i];
+                tdz.push_back({h->d_Zt + h->off_zt[i], h->d_Zr + h->off_zt[i], pi, nIi, nIi, pi});
+                maxd = std::max(maxd, std::max(pi, nIi));
+                GemvDesc g{h->d_Zr + h->off_zt[i], nIi, pi, pi, 0, h->d_e + h->coff[i], h->d_zc + h->off_I[i]};
+                for (int a = 0; a < nIi; ++a) {
+                    rdz.push_back((int32_t)h->gv_zp_h.size());
+                    rlz.push_back(a);
+                }
+                h->gv_zp_h.push_back(g);
+            }
+            auto dt = C.up(tdz);
+            {
+                PScope ps(h, PK_SMALL);
+                launch_transpose_rect(dt, (int)tdz.size(), maxd, s);
+            }
+            h->d_gv_zp = C.up(h->gv_zp_h, true);
+            h->d_rd_zp = C.up(rdz, true);
+            h->d_rl_zp = C.up(rlz, true);
+            h->n_zp = (int64_t)rdz.size();
+        }
         std::vector<int32_t> rd, rl, rdc, rlc;  // rd / rl: row groups of the local products (matrix, first row)
+        h->lm1.assign(N, nullptr);
+        h->lm2.assign(N, nullptr);
         for (int i = 0; i < N; ++i) {
             const int ni = h->ni[i];
+            h->lm1[i] = Yl + h->off_sq[i];
+            h->lm2[i] = Ylt + h->off_sq[i];
             l1[i] = {Yl + h->off_sq[i], ni, ni, ni, 1, rlocT + h->off_om[i], tlocT + h->off_om[i]};
             l2[i] = {Ylt + h->off_sq[i], ni, ni, ni, 2, tlocT + h->off_om[i], ylocT + h->off_om[i]};
             cr[i] = {h->d_Zt + h->off_zt[i], h->p[i], h->nI[i], h->nI[i], 0, h->d_rloc + h->off_om[i],
@@ -2182,16 +2235,17 @@ void apply_one(amdd_handle* h, const double* r, double* z) {
             PScope ps(h, PK_CSOLVE, h->csolve_flops, h->csolve_bytes);
             ck(launch_coarse_solve(a, h->coop_blocks, s));
         }
+        {
+            PScope ps(h, PK_GEMV, 2.0 * zt, 8.0 * zt + 8.0 * h->nC + 8.0 * h->n);
+            launch_gemv_rows<double>(h->d_gv_zp, h->d_rd_zp, h->d_rl_zp, h->n_zp, s);
+        }
     }
-    PScope ps(h, PK_GATHER_SCATTER, 2.0 * h->sum_zt, 8.0 * h->sum_zt + 12.0 * h->sum_ni + 24.0 * h->n);
+    PScope ps(h, PK_GATHER_SCATTER, 0.0, 12.0 * h->sum_ni + 24.0 * h->n);
+    const double* zc = h->nC > 0 ? h->d_zc : nullptr;
     if (h->precision == 0)
-        launch_scatter_prolong<double>(h->n, h->d_order_g, h->d_own_sub, h->d_own_a, h->d_sc_ptr, h->d_sc_idx,
-                                       h->d_yloc, h->d_zt_off, h->d_nI, h->d_p, h->d_coff, h->d_Zt,
-                                       h->nC > 0 ? h->d_e : nullptr, z, s);
+        launch_scatter_prolong<double>(h->n, h->d_order_g, h->d_sc_ptr, h->d_sc_idx, h->d_yloc, zc, z, s);
     else
-        launch_scatter_prolong<float>(h->n, h->d_order_g, h->d_own_sub, h->d_own_a, h->d_sc_ptr, h->d_sc_idx,
-                                      h->d_yloc32, h->d_zt_off, h->d_nI, h->d_p, h->d_coff, h->d_Zt,
-                                      h->nC > 0 ? h->d_e : nullptr, z, s);
+        launch_scatter_prolong<float>(h->n, h->d_order_g, h->d_sc_ptr, h->d_sc_idx, h->d_yloc32, zc, z, s);
 }
 
 // Launch wrappers of the PCG loop with their profile accounting.
@@ -2206,6 +2260,225 @@ void dot_h(amdd_handle* h, const double* x, const double* y, int which, double t
     }
     PScope ps(h, PK_PCG_VEC);
     launch_dot_finalize(h->d_part, h->d_sc, which, tol2, h->s);
+}
+
+// Buffers and descriptors of the batched path (MAXB right-hand sides), on first use.
+template <typename T>
+void* make_local_descs(amdd_handle* h, T* rloc, T* tloc, T* yloc, int which) {
+    const int N = h->N;
+    std::vector<GemvDescT<T>> g(N);
+    for (int i = 0; i < N; ++i) {
+        const int ni = h->ni[i];
+        if (which == 1)
+            g[i] = {static_cast<const T*>(h->lm1[i]), ni, ni, ni, 1, rloc + h->off_om[i], tloc + h->off_om[i]};
+        else
+            g[i] = {static_cast<const T*>(h->lm2[i]), ni, ni, ni, 2, tloc + h->off_om[i], yloc + h->off_om[i]};
+    }
+    GemvDescT<T>* d = dnew<GemvDescT<T>>(h, N);
+    ck(cudaMemcpyAsync(d, g.data(), N * sizeof(GemvDescT<T>), cudaMemcpyHostToDevice, h->s));
+    ck(cudaStreamSynchronize(h->s));
+    return d;
+}
+
+void ensure_multi(amdd_handle* h) {
+    if (h->mb_cap >= MAXB) return;
+    const int64_t L = (int64_t)MAXB * h->sum_ni, V = (int64_t)MAXB * h->n, CC = (int64_t)MAXB * std::max<int64_t>(h->nC, 1);
+    h->d_m_rloc = dnew<double>(h, L);
+    if (h->precision == 0) {
+        h->d_m_tloc = dnew<double>(h, L);
+        h->d_m_yloc = dnew<double>(h, L);
+        h->d_m_gv_l1 = make_local_descs<double>(h, h->d_m_rloc, h->d_m_tloc, h->d_m_yloc, 1);
+        h->d_m_gv_l2 = make_local_descs<double>(h, h->d_m_rloc, h->d_m_tloc, h->d_m_yloc, 2);
+    } else {
+        h->d_m_rloc32 = dnew<float>(h, L);
+        h->d_m_tloc32 = dnew<float>(h, L);
+        h->d_m_yloc32 = dnew<float>(h, L);
+        h->d_m_gv_l1 = make_local_descs<float>(h, h->d_m_rloc32, h->d_m_tloc32, h->d_m_yloc32, 1);
+        h->d_m_gv_l2 = make_local_descs<float>(h, h->d_m_rloc32, h->d_m_tloc32, h->d_m_yloc32, 2);
+    }
+    h->d_m_c = dnew<double>(h, CC);
+    h->d_m_ctmp = dnew<double>(h, CC);
+    h->d_m_e = dnew<double>(h, CC);
+    if (h->nC > 0) {
+        std::vector<GemvDesc> cr(h->N);
+        for (int i = 0; i < h->N; ++i)
+            cr[i] = {h->d_Zt + h->off_zt[i], h->p[i], h->nI[i], h->nI[i], 0, h->d_m_rloc + h->off_om[i],
+                     h->d_m_c + h->coff[i]};
+        h->d_m_gv_c = dnew<GemvDesc>(h, h->N);
+        ck(cudaMemcpyAsync(h->d_m_gv_c, cr.data(), h->N * sizeof(GemvDesc), cudaMemcpyHostToDevice, h->s));
+        h->d_m_zc = dnew<double>(h, (int64_t)MAXB * h->n);
+        ck(cudaMemsetAsync(h->d_m_zc, 0, (size_t)MAXB * h->n * sizeof(double), h->s));
+        std::vector<GemvDesc> zp = h->gv_zp_h;
+        int q = 0;
+        for (int i = 0; i < h->N; ++i) {
+            if (h->p[i] == 0) continue;
+            zp[q].x = h->d_m_e + h->coff[i];
+            zp[q].y = h->d_m_zc + h->off_I[i];
+            ++q;
+        }
+        h->d_m_gv_zp = dnew<GemvDesc>(h, std::max<int64_t>(q, 1));
+        ck(cudaMemcpyAsync(h->d_m_gv_zp, zp.data(), q * sizeof(GemvDesc), cudaMemcpyHostToDevice, h->s));
+    }
+    h->d_m_q = dnew<double>(h, V);
+    h->d_m_r = dnew<double>(h, V);
+    h->d_m_z = dnew<double>(h, V);
+    h->d_m_p = dnew<double>(h, V);
+    h->d_m_part = dnew<double>(h, (int64_t)MAXB * DOT_BLOCKS);
+    h->d_m_sc = dnew<PcgScal>(h, MAXB);
+    ck(cudaStreamSynchronize(h->s));
+    h->mb_cap = MAXB;
+}
+
+// z_k = M^{-1} r_k for nb <= MAXB right-hand sides (vectors n apart): every
+// factor, Z_i and L_E entry is read once per pass for all of them.
+void apply_multi(amdd_handle* h, const double* r, double* z, int nb) {
+    ensure_multi(h);
+    cudaStream_t s = h->s;
+    const int64_t L = h->sum_ni;
+    const double tri = (double)h->apply_tri_elems;
+    {
+        PScope ps(h, PK_GATHER_SCATTER, 0.0, 20.0 * L * nb);
+        launch_gather_vec_multi(h->d_omega, L, r, h->n, h->d_m_rloc, nb, s);
+    }
+    if (h->precision == 0) {
+        auto g1 = static_cast<const GemvDesc*>(h->d_m_gv_l1);
+        auto g2 = static_cast<const GemvDesc*>(h->d_m_gv_l2);
+        {
+            PScope ps(h, PK_GEMV, tri * nb, 8.0 * tri / 2 + 24.0 * L * nb);
+            launch_gemv_rows4_multi<double>(g1, h->d_g4_desc, h->d_g4_row, h->n_g4, nb, L, L, s);
+        }
+        {
+            PScope ps(h, PK_GEMV, tri * nb, 8.0 * tri / 2 + 24.0 * L * nb);
+            launch_gemv_rows4_multi<double>(g2, h->d_g4_desc, h->d_g4_row, h->n_g4, nb, L, L, s);
+        }
+    } else {
+        auto g1 = static_cast<const GemvDescT<float>*>(h->d_m_gv_l1);
+        auto g2 = static_cast<const GemvDescT<float>*>(h->d_m_gv_l2);
+        {
+            PScope ps(h, PK_GATHER_SCATTER, 0.0, 12.0 * L * nb);
+            launch_convert<double, float>(h->d_m_rloc, h->d_m_rloc32, L * nb, s);
+        }
+        {
+            PScope ps(h, PK_GEMV_F32, tri * nb, 4.0 * tri / 2 + 12.0 * L * nb);
+            launch_gemv_rows4_multi<float>(g1, h->d_g4_desc, h->d_g4_row, h->n_g4, nb, L, L, s);
+        }
+        {
+            PScope ps(h, PK_GEMV_F32, tri * nb, 4.0 * tri / 2 + 12.0 * L * nb);
+            launch_gemv_rows4_multi<float>(g2, h->d_g4_desc, h->d_g4_row, h->n_g4, nb, L, L, s);
+        }
+    }
+    if (h->nC > 0) {
+        const double zt = (double)h->sum_zt;
+        {
+            PScope ps(h, PK_GEMV, 2.0 * zt * nb, 8.0 * zt + (8.0 * L + 16.0 * h->nC) * nb);
+            launch_gemv_rows_multi<double>(h->d_m_gv_c, h->d_rd_c, h->d_rl_c, h->nC, nb, L, h->nC, s);
+        }
+        CoarseSolveArgs a{h->d_YE, h->d_YEt, h->d_Yd, h->d_Ydt, h->d_env_row, h->d_env_colend,
+                          h->d_m_c, h->d_m_ctmp, h->d_m_e, (int)h->nC, (int)h->nC, h->cSB, h->cK};
+        a.nb = nb;
+        a.ldv = h->nC;
+        {
+            PScope ps(h, PK_CSOLVE, h->csolve_flops * nb, h->csolve_bytes);
+            ck(launch_coarse_solve(a, h->coop_blocks, s));
+        }
+        PScope ps(h, PK_GEMV, 2.0 * zt * nb, 8.0 * zt + (8.0 * h->nC + 8.0 * h->n) * nb);
+        launch_gemv_rows_multi<double>(h->d_m_gv_zp, h->d_rd_zp, h->d_rl_zp, h->n_zp, nb, h->nC, h->n, s);
+    }
+    PScope ps(h, PK_GATHER_SCATTER, 0.0, (12.0 * L + 24.0 * h->n) * nb);
+    const double* zc = h->nC > 0 ? h->d_m_zc : nullptr;
+    if (h->precision == 0)
+        launch_scatter_prolong<double>(h->n, h->d_order_g, h->d_sc_ptr, h->d_sc_idx, h->d_m_yloc, zc, z, s, nb, L,
+                                       h->n, h->n);
+    else
+        launch_scatter_prolong<float>(h->n, h->d_order_g, h->d_sc_ptr, h->d_sc_idx, h->d_m_yloc32, zc, z, s, nb, L,
+                                      h->n, h->n);
+}
+
+void spmv_multi_h(amdd_handle* h, const double* x, double* y, int nb) {
+    PScope ps(h, PK_SPMV, 2.0 * h->nnz * nb, 12.0 * h->nnz + 8.0 * (h->n + 1) + 16.0 * h->n * nb);
+    launch_spmv_multi(h->n, h->rowptr, h->col, h->val, x, y, nb, h->n, h->s);
+}
+
+void dot_multi_h(amdd_handle* h, const double* x, const double* y, int which, double tol2, int nb, int skip) {
+    {
+        PScope ps(h, PK_PCG_VEC, 2.0 * h->n * nb, 16.0 * h->n * nb);
+        launch_dot_partials(h->n, x, y, h->d_m_part, h->s, nb, h->n);
+    }
+    PScope ps(h, PK_PCG_VEC);
+    launch_dot_finalize(h->d_m_part, h->d_m_sc, which, tol2, h->s, nb, skip);
+}
+
+// nb <= MAXB independent PCG solves advanced together (one SpMV and one
+// batched apply per iteration for all); a converged right-hand side keeps
+// its x, r, p.  Returns whether all converged; fills the iteration count and
+// the step lengths / ratios of the first right-hand side.
+bool pcg_multi(amdd_handle* h, const double* b, double* x, int nb, double rtol, int maxit, int* its0,
+               std::vector<double>& al, std::vector<double>& be, PcgScal* sc0) {
+    ensure_multi(h);
+    cudaStream_t s = h->s;
+    const int64_t n = h->n, V = n * nb;
+    const double tol2 = rtol * rtol;
+    ck(cudaMemsetAsync(h->d_m_sc, 0, nb * sizeof(PcgScal), s));
+    spmv_multi_h(h, x, h->d_m_q, nb);
+    {
+        PScope ps(h, PK_PCG_VEC, 2.0 * V, 24.0 * V);
+        launch_axpby(V, 1.0, b, -1.0, h->d_m_q, h->d_m_r, s);
+    }
+    dot_multi_h(h, b, b, 3, tol2, nb, 0);
+    dot_multi_h(h, h->d_m_r, h->d_m_r, 5, tol2, nb, 0);
+    std::vector<PcgScal> sc(nb);
+    ck(cudaMemcpyAsync(sc.data(), h->d_m_sc, nb * sizeof(PcgScal), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    bool all = true, zero = false;
+    for (int k = 0; k < nb; ++k) {
+        if (sc[k].bb == 0.0) {  // b_k = 0: x_k = 0, done
+            ck(cudaMemsetAsync(x + k * n, 0, n * sizeof(double), s));
+            sc[k].conv = 1;
+            sc[k].rr = 0.0;
+            zero = true;
+        }
+        if (!(sc[k].bb == 0.0 || sc[k].conv)) all = false;
+    }
+    if (zero) {
+        ck(cudaMemcpyAsync(h->d_m_sc, sc.data(), nb * sizeof(PcgScal), cudaMemcpyHostToDevice, s));
+        ck(cudaStreamSynchronize(s));
+    }
+    int its = 0;
+    if (!all) {
+        apply_multi(h, h->d_m_r, h->d_m_z, nb);
+        dot_multi_h(h, h->d_m_r, h->d_m_z, 4, tol2, nb, 0);
+        ck(cudaMemcpyAsync(h->d_m_p, h->d_m_z, V * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (its = 1; its <= maxit; ++its) {
+            spmv_multi_h(h, h->d_m_p, h->d_m_q, nb);
+            dot_multi_h(h, h->d_m_p, h->d_m_q, 0, tol2, nb, 1);
+            {
+                PScope ps(h, PK_PCG_VEC, 6.0 * V, 48.0 * V);
+                launch_pcg_update_xr(n, x, h->d_m_r, h->d_m_p, h->d_m_q, h->d_m_sc, h->d_m_part, s, nb, n, 1);
+            }
+            {
+                PScope ps(h, PK_PCG_VEC);
+                launch_dot_finalize(h->d_m_part, h->d_m_sc, 2, tol2, s, nb, 1);
+            }
+            ck(cudaMemcpyAsync(sc.data(), h->d_m_sc, nb * sizeof(PcgScal), cudaMemcpyDeviceToHost, s));
+            ck(cudaStreamSynchronize(s));
+            if ((int)al.size() < sc[0].iters) {  // a new step of the first right-hand side
+                if (sc[0].iters > 1) be.push_back(sc[0].beta);
+                al.push_back(sc[0].alpha);
+            }
+            all = true;
+            for (int k = 0; k < nb; ++k)
+                if (!(sc[k].bb == 0.0 || sc[k].conv)) all = false;
+            if (all || its == maxit) break;
+            apply_multi(h, h->d_m_r, h->d_m_z, nb);
+            dot_multi_h(h, h->d_m_r, h->d_m_z, 1, tol2, nb, 1);
+            PScope ps(h, PK_PCG_VEC, 2.0 * V, 24.0 * V);
+            launch_pcg_update_p(n, h->d_m_p, h->d_m_z, h->d_m_sc, s, nb, n, 1);
+        }
+        if (its > maxit) its = maxit;
+    }
+    *its0 = sc[0].bb == 0.0 ? 0 : sc[0].iters;
+    *sc0 = sc[0];
+    return all;
 }
 
 amdd_status guard_exc() {
@@ -2344,7 +2617,11 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
 amdd_status amdd_apply(amdd_handle* h, const double* r, double* z, int32_t nrhs) {
     if (!h || !r || !z || nrhs < 0 || r == z) return AMDD_ERR_INVALID;
     try {
-        for (int k = 0; k < nrhs; ++k) apply_one(h, r + (size_t)k * h->n, z + (size_t)k * h->n);
+        if (nrhs == 1)
+            apply_one(h, r, z);
+        else
+            for (int k = 0; k < nrhs; k += MAXB)
+                apply_multi(h, r + (size_t)k * h->n, z + (size_t)k * h->n, std::min(MAXB, nrhs - k));
         ck(cudaGetLastError());
         ck(cudaStreamSynchronize(h->s));
     } catch (...) {
@@ -2582,6 +2859,42 @@ amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t n
         cudaStream_t s = h->s;
         const int64_t n = h->n;
         const double tol2 = rtol * rtol;
+        if (nrhs > 1) {
+            // batched independent solves, MAXB right-hand sides per pass
+            std::vector<double> al, be;
+            PcgScal sc0{};
+            int its0 = 0;
+            bool conv0 = true;
+            for (int k = 0; k < nrhs; k += MAXB) {
+                const int nb = std::min(MAXB, nrhs - k);
+                std::vector<double> a2, b2;
+                PcgScal sck{};
+                int itk = 0;
+                const bool all = pcg_multi(h, b + (size_t)k * n, x + (size_t)k * n, nb, rtol, maxit, &itk,
+                                           k == 0 ? al : a2, k == 0 ? be : b2, &sck);
+                if (!all) result = AMDD_ERR_NOCONV;
+                if (k == 0) {
+                    its0 = itk;
+                    sc0 = sck;
+                    conv0 = sck.bb == 0.0 || sck.conv;
+                }
+            }
+            if (stats) {
+                spmv_h(h, x, h->d_q);
+                launch_axpby(n, 1.0, b, -1.0, h->d_q, h->d_z, s);
+                dot_h(h, h->d_z, h->d_z, 5, tol2);
+                PcgScal st{};
+                ck(cudaMemcpyAsync(&st, h->d_sc, sizeof(PcgScal), cudaMemcpyDeviceToHost, s));
+                ck(cudaStreamSynchronize(s));
+                stats->iterations = its0;
+                stats->converged = conv0 ? 1 : 0;
+                stats->rel_residual = sc0.bb > 0.0 ? std::sqrt(sc0.rr / sc0.bb) : 0.0;
+                stats->true_rel_residual = sc0.bb > 0.0 ? std::sqrt(st.rr / sc0.bb) : 0.0;
+                lanczos_extremes(al, be, &stats->ritz_min, &stats->ritz_max);
+                stats->cond_est = stats->ritz_max / stats->ritz_min;
+            }
+            nrhs = 0;  // done
+        }
         for (int k = 0; k < nrhs; ++k) {
             const double* bk = b + (size_t)k * n;
             double* xk = x + (size_t)k * n;

@@ -21,6 +21,7 @@ constexpr int CHOL_NB = 32;     // diagonal block of the blocked Cholesky / inve
 constexpr int GEMM_T = 64;      // GEMM output tile
 constexpr int PANEL_ROWS = 16;  // rows per CTA of the Cholesky panel solve
 constexpr int GEMV_ROWS_PER_WARP = 4;  // rows per warp of the local triangular products
+constexpr int MAXB = 8;                // right-hand sides per batched apply / PCG pass
 constexpr int JAC_CLUSTER = 8;  // CTAs per matrix in the Jacobi solvers
 constexpr int JAC_MAX_PAIRS = 64;  // largest sub-round of the shared-memory block Jacobi
 
@@ -166,6 +167,12 @@ template <typename T>
 void launch_gemv_rows4(const GemvDescT<T>* d, const int* grp_desc, const int* grp_row, int64_t ngroups,
                        cudaStream_t s);
 template <typename T>
+void launch_gemv_rows4_multi(const GemvDescT<T>* d, const int* grp_desc, const int* grp_row, int64_t ngroups, int nb,
+                             int64_t xs, int64_t ys, cudaStream_t s);
+template <typename T>
+void launch_gemv_rows_multi(const GemvDescT<T>* d, const int* row_desc, const int* row_local, int64_t nrows, int nb,
+                            int64_t xs, int64_t ys, cudaStream_t s);
+template <typename T>
 void launch_tridiag(const TridiagDescT<T>* d, int nmat, int maxn, cudaStream_t s);
 template <typename T>
 void launch_bisect(const TridiagDescT<T>* d, int nmat, const int* eig_mat, const int* eig_idx, int64_t total,
@@ -183,14 +190,24 @@ void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
 void launch_gather_values(const int64_t* src, const int64_t* dst, int64_t cnt, const double* val, double* out,
                           cudaStream_t s);
 void launch_gather_vec(const int32_t* idx, int64_t cnt, const double* x, double* out, cudaStream_t s);
+void launch_gather_vec_multi(const int32_t* idx, int64_t cnt, const double* x, int64_t ldx, double* out, int nb,
+                             cudaStream_t s);
+void launch_spmv_multi(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
+                       double* y, int nb, int64_t ld, cudaStream_t s);
 template <typename T>
 void launch_gather_rows(const T* src, const int64_t* src_off, T* dst, const int64_t* dst_off, const int32_t* len,
                         int64_t nrows, cudaStream_t s);
 template <typename TY>
-void launch_scatter_prolong(int64_t n, const int32_t* order_g, const int32_t* own_sub, const int32_t* own_a,
-                            const int64_t* sc_ptr, const int32_t* sc_idx, const TY* yloc,
-                            const int64_t* zt_off, const int32_t* nI, const int32_t* p, const int64_t* coff,
-                            const double* Zt, const double* e, double* z, cudaStream_t s);
+void launch_scatter_prolong(int64_t n, const int32_t* order_g, const int64_t* sc_ptr, const int32_t* sc_idx,
+                            const TY* yloc, const double* zc, double* z, cudaStream_t s, int nb = 1, int64_t ldy = 0,
+                            int64_t ldzc = 0, int64_t ldz = 0);
+// batched rectangular transposes: dst (cols x rows, leading dimension ldd) = src^T
+struct TransDesc {
+    const double* src;
+    double* dst;
+    int rows, cols, lds, ldd;
+};
+void launch_transpose_rect(const TransDesc* d, int nmat, int maxdim, cudaStream_t s);
 struct EPairRef {
     int i, j;          // block E_ij, i > j
     int64_t list_off;  // entries [list_off, list_off + list_len)
@@ -302,6 +319,8 @@ struct CoarseSolveArgs {
     double* y;             // work (n)
     double* e;             // solution (n)
     int n, ld, SB, K;
+    int nb = 1;            // right-hand sides (c, y, e hold nb vectors ldv apart)
+    int64_t ldv = 0;
 };
 int coarse_solve_blocks();  // cooperative grid size for this device (0 on error)
 cudaError_t launch_coarse_solve(const CoarseSolveArgs& a, int blocks, cudaStream_t s);
@@ -310,13 +329,19 @@ struct PcgScal {
     double rz, pq, rr, bb, alpha, beta, rz_new;
     int conv, iters;
 };
-void launch_dot_partials(int64_t n, const double* x, const double* y, double* partials, cudaStream_t s);
+// Vector operations of PCG on nb right-hand sides stored ld apart (scalars sc[k],
+// partial sums DOT_BLOCKS apart); with skip_done a converged right-hand side
+// (sc[k].conv) keeps x, r, p and its scalars.
+void launch_dot_partials(int64_t n, const double* x, const double* y, double* partials, cudaStream_t s, int nb = 1,
+                         int64_t ld = 0);
 // which: 0 -> pq (alpha = rz/pq), 1 -> rz_new (beta = rz_new/rz, rz = rz_new),
 // 2 -> rr (conv = rr <= tol2 * bb), 3 -> bb, 4 -> rz (initial)
-void launch_dot_finalize(const double* partials, PcgScal* sc, int which, double tol2, cudaStream_t s);
+void launch_dot_finalize(const double* partials, PcgScal* sc, int which, double tol2, cudaStream_t s, int nb = 1,
+                         int skip_done = 0);
 void launch_pcg_update_xr(int64_t n, double* x, double* r, const double* p, const double* q, const PcgScal* sc,
-                          double* partials, cudaStream_t s);
-void launch_pcg_update_p(int64_t n, double* p, const double* z, const PcgScal* sc, cudaStream_t s);
+                          double* partials, cudaStream_t s, int nb = 1, int64_t ld = 0, int skip_done = 0);
+void launch_pcg_update_p(int64_t n, double* p, const double* z, const PcgScal* sc, cudaStream_t s, int nb = 1,
+                         int64_t ld = 0, int skip_done = 0);
 void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
 
 }  // namespace amdd

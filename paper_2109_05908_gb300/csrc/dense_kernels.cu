@@ -864,6 +864,34 @@ template void launch_transpose<float>(const float* const*, float* const*, const 
 template void launch_transpose<double>(const double* const*, double* const*, const int*, const int*, const int*,
                                        int, int, cudaStream_t);
 
+// dst = src^T for a batch of rectangular FP64 matrices, 32 x 32 tiles through
+// shared memory (blockIdx.z = matrix)
+__global__ void transpose_rect_kernel(const TransDesc* __restrict__ descs) {
+    const TransDesc d = descs[blockIdx.z];
+    __shared__ double tile[32][33];
+    const int tr = (d.rows + 31) / 32, tc = (d.cols + 31) / 32;
+    for (int t = blockIdx.x; t < tr * tc; t += gridDim.x) {
+        const int r0 = (t / tc) * 32, c0 = (t % tc) * 32;
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+            const int r = e / 32, c = e % 32;
+            tile[r][c] = (r0 + r < d.rows && c0 + c < d.cols) ? d.src[(size_t)(r0 + r) * d.lds + c0 + c] : 0.0;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+            const int c = e / 32, r = e % 32;
+            if (r0 + r < d.rows && c0 + c < d.cols) d.dst[(size_t)(c0 + c) * d.ldd + r0 + r] = tile[r][c];
+        }
+        __syncthreads();
+    }
+}
+
+void launch_transpose_rect(const TransDesc* d, int nmat, int maxdim, cudaStream_t s) {
+    if (nmat <= 0 || maxdim <= 0) return;
+    const int t = (maxdim + 31) / 32;
+    dim3 grid(min(t * t, 4096), 1, nmat);
+    transpose_rect_kernel<<<grid, 256, 0, s>>>(d);
+}
+
 // dst[i] = (To) src[i]
 template <typename Ti, typename To>
 __global__ void convert_kernel(const Ti* __restrict__ src, To* __restrict__ dst, int64_t n) {
@@ -1265,6 +1293,120 @@ void launch_gemv_rows4(const GemvDescT<T>* d, const int* grp_desc, const int* gr
 template void launch_gemv_rows4<float>(const GemvDescT<float>*, const int*, const int*, int64_t, cudaStream_t);
 template void launch_gemv_rows4<double>(const GemvDescT<double>*, const int*, const int*, int64_t, cudaStream_t);
 
+// The same products for nb <= MAXB right-hand sides (x_k = x + k xs, y_k = y
+// + k ys; no b term): each factor entry is read once and applied to every
+// x_k.  With GEMV_RW x MAXB = 32 the reduced sum of (row r, rhs k) is
+// written by lane r MAXB + k.
+template <typename T>
+__global__ void __launch_bounds__(256) gemv_rows4_multi_kernel(const GemvDescT<T>* __restrict__ descs,
+                                                               const int* __restrict__ grp_desc,
+                                                               const int* __restrict__ grp_row, int64_t ngroups,
+                                                               int nb, int64_t xs, int64_t ys) {
+    static_assert(GEMV_RW * MAXB == 32, "one output per lane");
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= ngroups) return;
+    const GemvDescT<T> d = descs[grp_desc[w]];
+    const int r0 = grp_row[w];
+    const int nr = min(GEMV_RW, d.rows - r0);
+    int lo[GEMV_RW], hi[GEMV_RW];
+    int cmin = d.ncols, cmax = 0;
+#pragma unroll
+    for (int k = 0; k < GEMV_RW; ++k) {
+        const int r = r0 + k;
+        lo[k] = (d.mode == 2) ? r : 0;
+        hi[k] = (d.mode == 1) ? min(r + 1, d.ncols) : d.ncols;
+        if (k >= nr) hi[k] = lo[k];
+        if (k < nr) {
+            cmin = min(cmin, lo[k]);
+            cmax = max(cmax, hi[k]);
+        }
+    }
+    const T* M0 = d.M + (size_t)r0 * d.ld;
+    T s[GEMV_RW][MAXB];
+#pragma unroll
+    for (int r = 0; r < GEMV_RW; ++r)
+#pragma unroll
+        for (int k = 0; k < MAXB; ++k) s[r][k] = T(0);
+    for (int c = cmin + lane; c < cmax; c += 32) {
+        T xv[MAXB];
+#pragma unroll
+        for (int k = 0; k < MAXB; ++k) xv[k] = k < nb ? d.x[k * xs + c] : T(0);
+#pragma unroll
+        for (int r = 0; r < GEMV_RW; ++r)
+            if (c >= lo[r] && c < hi[r]) {
+                const T m = M0[(size_t)r * d.ld + c];
+#pragma unroll
+                for (int k = 0; k < MAXB; ++k) s[r][k] = fma(m, xv[k], s[r][k]);
+            }
+    }
+    T mine = T(0);
+#pragma unroll
+    for (int r = 0; r < GEMV_RW; ++r)
+#pragma unroll
+        for (int k = 0; k < MAXB; ++k) {
+            T v = s[r][k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == r * MAXB + k) mine = v;
+        }
+    const int rr = lane / MAXB, kk = lane % MAXB;
+    if (rr < nr && kk < nb) d.y[kk * ys + r0 + rr] = d.alpha * mine;
+}
+
+template <typename T>
+void launch_gemv_rows4_multi(const GemvDescT<T>* d, const int* grp_desc, const int* grp_row, int64_t ngroups, int nb,
+                             int64_t xs, int64_t ys, cudaStream_t s) {
+    if (ngroups <= 0) return;
+    const int64_t blocks = (ngroups * 32 + 255) / 256;
+    gemv_rows4_multi_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, grp_desc, grp_row, ngroups, nb, xs, ys);
+}
+template void launch_gemv_rows4_multi<float>(const GemvDescT<float>*, const int*, const int*, int64_t, int, int64_t,
+                                             int64_t, cudaStream_t);
+template void launch_gemv_rows4_multi<double>(const GemvDescT<double>*, const int*, const int*, int64_t, int, int64_t,
+                                              int64_t, cudaStream_t);
+
+// One warp per row of a batch of row-major matrices (mode 0: all columns),
+// nb right-hand sides: y_k[row] = alpha (M x_k)[row].
+template <typename T>
+__global__ void __launch_bounds__(256) gemv_rows_multi_kernel(const GemvDescT<T>* __restrict__ descs,
+                                                              const int* __restrict__ row_desc,
+                                                              const int* __restrict__ row_local, int64_t nrows, int nb,
+                                                              int64_t xs, int64_t ys) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nrows) return;
+    const GemvDescT<T> d = descs[row_desc[w]];
+    const int r = row_local[w];
+    const T* row = d.M + (size_t)r * d.ld;
+    T acc[MAXB];
+#pragma unroll
+    for (int k = 0; k < MAXB; ++k) acc[k] = T(0);
+    for (int c = lane; c < d.ncols; c += 32) {
+        const T m = row[c];
+#pragma unroll
+        for (int k = 0; k < MAXB; ++k)
+            if (k < nb) acc[k] = fma(m, d.x[k * xs + c], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < MAXB; ++k) {
+        T v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && k < nb) d.y[k * ys + r] = d.alpha * v;
+    }
+}
+
+template <typename T>
+void launch_gemv_rows_multi(const GemvDescT<T>* d, const int* row_desc, const int* row_local, int64_t nrows, int nb,
+                            int64_t xs, int64_t ys, cudaStream_t s) {
+    if (nrows <= 0) return;
+    const int64_t blocks = (nrows * 32 + 255) / 256;
+    gemv_rows_multi_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, row_desc, row_local, nrows, nb, xs, ys);
+}
+template void launch_gemv_rows_multi<double>(const GemvDescT<double>*, const int*, const int*, int64_t, int, int64_t,
+                                             int64_t, cudaStream_t);
+
 // ------------------------------------------------------------------ coarse solve
 // L_E L_E^T e = c by blocked substitution in one cooperative launch.  The
 // factor is split into K diagonal blocks of SB rows whose inverses Y_kk are
@@ -1276,6 +1418,8 @@ template void launch_gemv_rows4<double>(const GemvDescT<double>*, const int*, co
 // grid-wide barrier separates the phases; rows outside the envelope of L_E
 // (first column env_row[r], column r ends at env_colend[r]) are skipped.
 // One CTA of 1024 threads per SM keeps the barrier to one arrival per SM.
+// With nb right-hand sides (vectors ldv apart) each matrix entry is read once
+// and applied to all of them.
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1284,56 +1428,94 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 constexpr int CSOLVE_THREADS = 1024;
 
+// NB: the largest number of right-hand sides of the instantiation (1 for a
+// single solve: no per-entry loop over right-hand sides at all).
+template <int NB>
 __global__ void __launch_bounds__(CSOLVE_THREADS) coarse_solve_kernel(CoarseSolveArgs a) {
     cg::grid_group grid = cg::this_grid();
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-    const int n = a.n, SB = a.SB, K = a.K;
+    const int n = a.n, SB = a.SB, K = a.K, nb = NB == 1 ? 1 : a.nb;
+    const int64_t lv = a.ldv;
     double* t = a.c;
-    for (int k = 0; k < K; ++k) {
-        const int r0 = k * SB, sb = min(SB, n - r0), r1 = r0 + sb;
-        const double* Y = a.Yd + (size_t)k * SB * SB;
+    double s[NB];
+    auto reduce_store = [&](double* out, int idx, bool sub) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            if (k >= nb) break;
+            const double v = warp_sum_d(s[k]);
+            if (lane == 0) {
+                if (sub)
+                    out[k * lv + idx] -= v;
+                else
+                    out[k * lv + idx] = v;
+            }
+        }
+    };
+    for (int k0 = 0; k0 < K; ++k0) {
+        const int r0 = k0 * SB, sb = min(SB, n - r0), r1 = r0 + sb;
+        const double* Y = a.Yd + (size_t)k0 * SB * SB;
         for (int i = gw; i < sb; i += nw) {
             const double* row = Y + (size_t)i * SB;
-            double s = 0.0;
-            for (int j = lane; j <= i; j += 32) s = fma(row[j], t[r0 + j], s);
-            s = warp_sum_d(s);
-            if (lane == 0) a.y[r0 + i] = s;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) s[k] = 0.0;
+            for (int j = lane; j <= i; j += 32) {
+                const double m = row[j];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (NB == 1 || k < nb) s[k] = fma(m, t[k * lv + r0 + j], s[k]);
+            }
+            reduce_store(a.y, r0 + i, false);
         }
         grid.sync();
-        if (k + 1 == K) break;
+        if (k0 + 1 == K) break;
         for (int r = r1 + gw; r < n; r += nw) {
             const int j0 = max(a.env_row[r], r0);
             if (j0 >= r1) continue;
             const double* row = a.L + (size_t)r * a.ld;
-            double s = 0.0;
-            for (int j = j0 + lane; j < r1; j += 32) s = fma(row[j], a.y[j], s);
-            s = warp_sum_d(s);
-            if (lane == 0) t[r] -= s;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) s[k] = 0.0;
+            for (int j = j0 + lane; j < r1; j += 32) {
+                const double m = row[j];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (NB == 1 || k < nb) s[k] = fma(m, a.y[k * lv + j], s[k]);
+            }
+            reduce_store(t, r, true);
         }
         grid.sync();
     }
-    for (int k = K - 1; k >= 0; --k) {
-        const int r0 = k * SB, sb = min(SB, n - r0), r1 = r0 + sb;
-        const double* Yt = a.Ydt + (size_t)k * SB * SB;
+    for (int k0 = K - 1; k0 >= 0; --k0) {
+        const int r0 = k0 * SB, sb = min(SB, n - r0), r1 = r0 + sb;
+        const double* Yt = a.Ydt + (size_t)k0 * SB * SB;
         for (int i = gw; i < sb; i += nw) {
             const double* row = Yt + (size_t)i * SB;
-            double s = 0.0;
-            for (int j = i + lane; j < sb; j += 32) s = fma(row[j], a.y[r0 + j], s);
-            s = warp_sum_d(s);
-            if (lane == 0) a.e[r0 + i] = s;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) s[k] = 0.0;
+            for (int j = i + lane; j < sb; j += 32) {
+                const double m = row[j];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (NB == 1 || k < nb) s[k] = fma(m, a.y[k * lv + r0 + j], s[k]);
+            }
+            reduce_store(a.e, r0 + i, false);
         }
-        if (k == 0) break;
+        if (k0 == 0) break;
         grid.sync();
         for (int r = gw; r < r0; r += nw) {
             const int j1 = min(a.env_colend[r], r1);
             if (j1 <= r0) continue;
             const double* row = a.Lt + (size_t)r * a.ld;
-            double s = 0.0;
-            for (int j = r0 + lane; j < j1; j += 32) s = fma(row[j], a.e[j], s);
-            s = warp_sum_d(s);
-            if (lane == 0) a.y[r] -= s;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) s[k] = 0.0;
+            for (int j = r0 + lane; j < j1; j += 32) {
+                const double m = row[j];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (NB == 1 || k < nb) s[k] = fma(m, a.e[k * lv + j], s[k]);
+            }
+            reduce_store(a.y, r, true);
         }
         grid.sync();
     }
@@ -1343,8 +1525,11 @@ int coarse_solve_blocks() {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, coarse_solve_kernel, CSOLVE_THREADS, 0) != cudaSuccess)
+    int per8 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, coarse_solve_kernel<1>, CSOLVE_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per8, coarse_solve_kernel<MAXB>, CSOLVE_THREADS, 0) != cudaSuccess)
         return 0;
+    per = std::min(per, per8);
     // one CTA per SM: the grid barriers between phases then take one arrival per SM
     return per >= 1 ? sms : 0;
 }
@@ -1352,8 +1537,8 @@ int coarse_solve_blocks() {
 cudaError_t launch_coarse_solve(const CoarseSolveArgs& a, int blocks, cudaStream_t s) {
     CoarseSolveArgs arg = a;
     void* params[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void*)coarse_solve_kernel, dim3(blocks), dim3(CSOLVE_THREADS), params, 0,
-                                       s);
+    const void* fn = a.nb == 1 ? (const void*)coarse_solve_kernel<1> : (const void*)coarse_solve_kernel<MAXB>;
+    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(CSOLVE_THREADS), params, 0, s);
 }
 
 }  // namespace amdd

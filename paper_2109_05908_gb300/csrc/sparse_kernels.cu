@@ -47,6 +47,37 @@ void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
         spmv_kernel<32><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
 }
 
+// y_k = A x_k for nb <= MAXB right-hand sides stored ld apart: one thread per
+// row reads the row's entries once and applies them to every x_k.
+__global__ void __launch_bounds__(256) spmv_multi_kernel(int64_t n, const int64_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const double* __restrict__ val, const double* __restrict__ x,
+                                                         double* __restrict__ y, int nb, int64_t ld) {
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        double acc[MAXB];
+#pragma unroll
+        for (int k = 0; k < MAXB; ++k) acc[k] = 0.0;
+        for (int64_t e = rowptr[row]; e < rowptr[row + 1]; ++e) {
+            const double v = __ldg(val + e);
+            const int64_t c = __ldg(col + e);
+#pragma unroll
+            for (int k = 0; k < MAXB; ++k)
+                if (k < nb) acc[k] = fma(v, __ldg(x + k * ld + c), acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < MAXB; ++k)
+            if (k < nb) y[k * ld + row] = acc[k];
+    }
+}
+
+void launch_spmv_multi(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
+                       double* y, int nb, int64_t ld, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t want = (n + 255) / 256;
+    spmv_multi_kernel<<<(unsigned)(want < 152 * 64 ? want : 152 * 64), 256, 0, s>>>(n, rowptr, col, val, x, y, nb, ld);
+}
+
 // ------------------------------------------------------------------ gathers
 __global__ void gather_values_kernel(const int64_t* __restrict__ src, const int64_t* __restrict__ dst, int64_t cnt,
                                      const double* __restrict__ val, double* __restrict__ out) {
@@ -65,6 +96,22 @@ __global__ void gather_vec_kernel(const int32_t* __restrict__ idx, int64_t cnt, 
                                   double* __restrict__ out) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
         out[t] = x[idx[t]];
+}
+
+// out[k][t] = x[k][idx[t]] for nb right-hand sides (x stride ldx, out stride cnt)
+__global__ void gather_vec_multi_kernel(const int32_t* __restrict__ idx, int64_t cnt, const double* __restrict__ x,
+                                        int64_t ldx, double* __restrict__ out, int nb) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
+        const int g = idx[t];
+        for (int k = 0; k < nb; ++k) out[k * cnt + t] = x[k * ldx + g];
+    }
+}
+
+void launch_gather_vec_multi(const int32_t* idx, int64_t cnt, const double* x, int64_t ldx, double* out, int nb,
+                             cudaStream_t s) {
+    if (cnt <= 0) return;
+    const int64_t want = (cnt + 255) / 256;
+    gather_vec_multi_kernel<<<(unsigned)(want < 152 * 32 ? want : 152 * 32), 256, 0, s>>>(idx, cnt, x, ldx, out, nb);
 }
 
 void launch_gather_vec(const int32_t* idx, int64_t cnt, const double* x, double* out, cudaStream_t s) {
@@ -100,51 +147,39 @@ template void launch_gather_rows<double>(const double*, const int64_t*, double*,
 
 // ------------------------------------------------------------------ prolongation
 // z[g] = sum over the copies of g in the local vectors (fixed subdomain order)
-//      + sum_k Zt_i[k][a] e[coff_i + k]   (i owns g, a = position of g in Omega_Ii).
-// Threads run in owner order so that consecutive threads read consecutive
-// columns of Zt_i.
+//      + zc[t]   (the coarse prolongation (Z_i e_i)[a] of the owner i of g,
+//                 a = position of g in Omega_Ii, t = off_I[i] + a: thread t
+//                 runs in that owner order).  nb right-hand sides: yloc, zc
+//                 and z hold nb vectors ldy, ldzc and ldz apart.
 template <typename TY>
 __global__ void __launch_bounds__(256) scatter_prolong_kernel(
-    int64_t n, const int32_t* __restrict__ order_g, const int32_t* __restrict__ own_sub,
-    const int32_t* __restrict__ own_a, const int64_t* __restrict__ sc_ptr, const int32_t* __restrict__ sc_idx,
-    const TY* __restrict__ yloc, const int64_t* __restrict__ zt_off, const int32_t* __restrict__ nI,
-    const int32_t* __restrict__ p, const int64_t* __restrict__ coff, const double* __restrict__ Zt,
-    const double* __restrict__ e, double* __restrict__ z) {
+    int64_t n, const int32_t* __restrict__ order_g, const int64_t* __restrict__ sc_ptr,
+    const int32_t* __restrict__ sc_idx, const TY* __restrict__ yloc, const double* __restrict__ zc,
+    double* __restrict__ z, int nb, int64_t ldy, int64_t ldzc, int64_t ldz) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const int g = order_g[t];
-        double s = 0.0;
-        for (int64_t k = sc_ptr[g]; k < sc_ptr[g + 1]; ++k) s += (double)yloc[sc_idx[k]];
-        if (e) {
-            const int i = own_sub[t], a = own_a[t];
-            const int pi = p[i], ni = nI[i];
-            const double* zt = Zt + zt_off[i] + a;
-            const double* ei = e + coff[i];
-            double c = 0.0;
-            for (int k = 0; k < pi; ++k) c = fma(zt[(size_t)k * ni], ei[k], c);
-            s += c;
+        for (int r = 0; r < nb; ++r) {
+            double s = 0.0;
+            for (int64_t k = sc_ptr[g]; k < sc_ptr[g + 1]; ++k) s += (double)yloc[r * ldy + sc_idx[k]];
+            if (zc) s += zc[r * ldzc + t];
+            z[r * ldz + g] = s;
         }
-        z[g] = s;
     }
 }
 
 template <typename TY>
-void launch_scatter_prolong(int64_t n, const int32_t* order_g, const int32_t* own_sub, const int32_t* own_a,
-                            const int64_t* sc_ptr, const int32_t* sc_idx, const TY* yloc, const int64_t* zt_off,
-                            const int32_t* nI, const int32_t* p, const int64_t* coff, const double* Zt,
-                            const double* e, double* z, cudaStream_t s) {
+void launch_scatter_prolong(int64_t n, const int32_t* order_g, const int64_t* sc_ptr, const int32_t* sc_idx,
+                            const TY* yloc, const double* zc, double* z, cudaStream_t s, int nb, int64_t ldy,
+                            int64_t ldzc, int64_t ldz) {
     if (n <= 0) return;
     const int64_t want = (n + 255) / 256;
     scatter_prolong_kernel<TY><<<(unsigned)(want < 152 * 32 ? want : 152 * 32), 256, 0, s>>>(
-        n, order_g, own_sub, own_a, sc_ptr, sc_idx, yloc, zt_off, nI, p, coff, Zt, e, z);
+        n, order_g, sc_ptr, sc_idx, yloc, zc, z, nb, ldy, ldzc, ldz);
 }
-template void launch_scatter_prolong<float>(int64_t, const int32_t*, const int32_t*, const int32_t*, const int64_t*,
-                                            const int32_t*, const float*, const int64_t*, const int32_t*,
-                                            const int32_t*, const int64_t*, const double*, const double*, double*,
-                                            cudaStream_t);
-template void launch_scatter_prolong<double>(int64_t, const int32_t*, const int32_t*, const int32_t*, const int64_t*,
-                                             const int32_t*, const double*, const int64_t*, const int32_t*,
-                                             const int32_t*, const int64_t*, const double*, const double*, double*,
-                                             cudaStream_t);
+template void launch_scatter_prolong<float>(int64_t, const int32_t*, const int64_t*, const int32_t*, const float*,
+                                            const double*, double*, cudaStream_t, int, int64_t, int64_t, int64_t);
+template void launch_scatter_prolong<double>(int64_t, const int32_t*, const int64_t*, const int32_t*, const double*,
+                                             const double*, double*, cudaStream_t, int, int64_t, int64_t, int64_t);
 
 // ------------------------------------------------------------------ coarse blocks
 // E[coff_i + r][coff_j + c] = sum_l Zt_i[r][la[l]] * AZ_j[lpos[l]][c], 32 x 32
@@ -211,7 +246,10 @@ __device__ __forceinline__ double block_sum_256(double v) {
 
 __global__ void __launch_bounds__(256) dot_partials_kernel(int64_t n, const double* __restrict__ x,
                                                             const double* __restrict__ y,
-                                                            double* __restrict__ partials) {
+                                                            double* __restrict__ partials, int64_t ld) {
+    x += (int64_t)blockIdx.y * ld;
+    y += (int64_t)blockIdx.y * ld;
+    partials += (int64_t)blockIdx.y * DOT_BLOCKS;
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)DOT_BLOCKS * 256)
         s = fma(x[i], y[i], s);
@@ -219,12 +257,16 @@ __global__ void __launch_bounds__(256) dot_partials_kernel(int64_t n, const doub
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-void launch_dot_partials(int64_t n, const double* x, const double* y, double* partials, cudaStream_t s) {
-    dot_partials_kernel<<<DOT_BLOCKS, 256, 0, s>>>(n, x, y, partials);
+void launch_dot_partials(int64_t n, const double* x, const double* y, double* partials, cudaStream_t s, int nb,
+                         int64_t ld) {
+    dot_partials_kernel<<<dim3(DOT_BLOCKS, nb), 256, 0, s>>>(n, x, y, partials, ld);
 }
 
 __global__ void __launch_bounds__(256) dot_finalize_kernel(const double* __restrict__ partials, PcgScal* sc,
-                                                            int which, double tol2) {
+                                                            int which, double tol2, int skip_done) {
+    partials += (int64_t)blockIdx.x * DOT_BLOCKS;
+    sc += blockIdx.x;
+    if (skip_done && sc->conv) return;  // a converged right-hand side keeps its state
     double v = 0.0;
     for (int i = threadIdx.x; i < DOT_BLOCKS; i += 256) v += partials[i];
     v = block_sum_256(v);
@@ -258,8 +300,9 @@ __global__ void __launch_bounds__(256) dot_finalize_kernel(const double* __restr
     }
 }
 
-void launch_dot_finalize(const double* partials, PcgScal* sc, int which, double tol2, cudaStream_t s) {
-    dot_finalize_kernel<<<1, 256, 0, s>>>(partials, sc, which, tol2);
+void launch_dot_finalize(const double* partials, PcgScal* sc, int which, double tol2, cudaStream_t s, int nb,
+                         int skip_done) {
+    dot_finalize_kernel<<<nb, 256, 0, s>>>(partials, sc, which, tol2, skip_done);
 }
 
 // x += alpha p; r -= alpha q; partial sums of r.r
@@ -267,8 +310,16 @@ __global__ void __launch_bounds__(256) pcg_update_xr_kernel(int64_t n, double* _
                                                              double* __restrict__ r, const double* __restrict__ p,
                                                              const double* __restrict__ q,
                                                              const PcgScal* __restrict__ sc,
-                                                             double* __restrict__ partials) {
-    const double a = sc->alpha;
+                                                             double* __restrict__ partials, int64_t ld,
+                                                             int skip_done) {
+    const int k = blockIdx.y;
+    if (skip_done && sc[k].conv) return;
+    x += (int64_t)k * ld;
+    r += (int64_t)k * ld;
+    p += (int64_t)k * ld;
+    q += (int64_t)k * ld;
+    partials += (int64_t)k * DOT_BLOCKS;
+    const double a = sc[k].alpha;
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)DOT_BLOCKS * 256) {
         x[i] = fma(a, p[i], x[i]);
@@ -281,20 +332,25 @@ __global__ void __launch_bounds__(256) pcg_update_xr_kernel(int64_t n, double* _
 }
 
 void launch_pcg_update_xr(int64_t n, double* x, double* r, const double* p, const double* q, const PcgScal* sc,
-                          double* partials, cudaStream_t s) {
-    pcg_update_xr_kernel<<<DOT_BLOCKS, 256, 0, s>>>(n, x, r, p, q, sc, partials);
+                          double* partials, cudaStream_t s, int nb, int64_t ld, int skip_done) {
+    pcg_update_xr_kernel<<<dim3(DOT_BLOCKS, nb), 256, 0, s>>>(n, x, r, p, q, sc, partials, ld, skip_done);
 }
 
 // p = z + beta p
 __global__ void pcg_update_p_kernel(int64_t n, double* __restrict__ p, const double* __restrict__ z,
-                                    const PcgScal* __restrict__ sc) {
-    const double b = sc->beta;
+                                    const PcgScal* __restrict__ sc, int64_t ld, int skip_done) {
+    const int k = blockIdx.y;
+    if (skip_done && sc[k].conv) return;
+    p += (int64_t)k * ld;
+    z += (int64_t)k * ld;
+    const double b = sc[k].beta;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = fma(b, p[i], z[i]);
 }
 
-void launch_pcg_update_p(int64_t n, double* p, const double* z, const PcgScal* sc, cudaStream_t s) {
-    pcg_update_p_kernel<<<DOT_BLOCKS, 256, 0, s>>>(n, p, z, sc);
+void launch_pcg_update_p(int64_t n, double* p, const double* z, const PcgScal* sc, cudaStream_t s, int nb,
+                         int64_t ld, int skip_done) {
+    pcg_update_p_kernel<<<dim3(DOT_BLOCKS, nb), 256, 0, s>>>(n, p, z, sc, ld, skip_done);
 }
 
 // out = a x + b y

@@ -239,6 +239,36 @@ def test_condition_estimate(name):
     assert st.cond_est == pytest.approx(st.ritz_max / st.ritz_min) and st.cond_est <= bound
 
 
+@pytest.mark.parametrize("name,nrhs", [("diff8_bfs_ov1_tau0.5", 5), ("lap16_box4_tau0.5", 10)])
+def test_pcg_batched_rhs(name, nrhs):
+    """nrhs independent solves advanced together (batches of up to 8 share each
+    SpMV and apply): every solution matches the oracle's tight solve, the first
+    right-hand side's iteration count matches the oracle's, and a zero
+    right-hand side returns x = 0."""
+    M, part, N, ov, tau, S, dA, dpart, P = _case(name)
+    B = synth.rhs(M.n, 21, nrhs=nrhs)
+    B[3] = 0.0
+    bd = to_device(B)
+    xd = torch.zeros_like(bd)
+    st = P.solve(bd, xd, nrhs=nrhs, rtol=1e-12)
+    assert st.converged == 1
+    _, its_o, _ = O.pcg(S.A, B[0], lambda r: O.apply(S, r), rtol=1e-12)
+    assert abs(st.iterations - its_o) <= 1
+    X = xd.cpu().numpy()
+    for k in range(nrhs):
+        if k == 3:
+            assert np.all(X[k] == 0.0)
+            continue
+        xo, _, _ = O.pcg(S.A, B[k], lambda r: O.apply(S, r), rtol=1e-12)
+        assert np.linalg.norm(X[k] - xo) <= 1e-10 * np.linalg.norm(xo), k
+    # the batched apply (one pass over the factors for up to 8 right-hand sides)
+    zd = torch.empty_like(bd)
+    P.apply(bd, zd, nrhs=nrhs)
+    for k in (0, nrhs - 1):
+        zo = O.apply(S, B[k])
+        assert np.linalg.norm(zd[k].cpu().numpy() - zo) <= 1e-10 * np.linalg.norm(zo)
+
+
 def test_pcg_initial_guess_and_zero_rhs():
     M, part, N, ov, tau, S, dA, dpart, P = _case("lap16_box4_tau0.5")
     b = synth.rhs(M.n, 2)
