@@ -126,6 +126,18 @@ def cpu_baseline(w, max_seconds=30.0):
                       f"BLAS threading on {cores} host cores; {its} PCG iterations"}, its
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The job's time: the largest per-rank value (replicas run independent
+    copies of the workload; this reduction and a barrier are the only
+    cross-rank steps)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 APPLY_SCALE = {"m": 1024, "box": 16, "overlap": 1, "tau": 1e-12}
 APPLY_CLASSES = ("gemv_rows_f32", "gemv_rows", "gather_scatter", "coarse_solve")
 
@@ -330,10 +342,7 @@ def run_amdd(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(bb) for a, bb in ev]
     ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
 
     # ---- end to end from pinned host buffers through the C ABI
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
