@@ -19,6 +19,10 @@ notation, with numpy / scipy (LAPACK) primitives as single steps:
                 M^{-1} = R_0^T (R_0 A R_0^T)^{-1} R_0 + sum_i R_i^T A_ii^{-1} R_i,
                 R_0^T = [R_1^T D_1 Z_1, ..., R_N^T D_N Z_N]
   Sec. 1        preconditioned conjugate gradient (Hestenes-Stiefel), x0 = 0
+  Sec. 4.1      the deflated form used in the experiments,
+                M_deflated = R_0^T C_00^{-1} R_0 + M_RAS (I - A R_0^T C_00^{-1} R_0),
+                M_RAS = sum_i R_i^T D_i A_ii^{-1} R_i (restricted additive
+                Schwarz), inside right-preconditioned GMRES(m), x0 = 0
 
 Readings where the paper is silent (each listed in the design notes):
   * overlap > 1: Omega_Gi = all nodes at graph distance 1..overlap from
@@ -34,7 +38,10 @@ Readings where the paper is silent (each listed in the design notes):
     (S_i, A_II) with S_i the Schur complement of tilde A_ii onto Omega_Ii
     (= that of Abar_ii onto Omega_Ii, quotient property) and mu = 1/lambda;
   * stopping test ||r_k||_2 <= rtol ||b||_2 on the recursively updated
-    residual, x0 = 0.
+    residual, x0 = 0;
+  * GMRES stops on the least-squares residual |g_{j+1}| <= rtol ||b||_2
+    (equal to ||b - A x_j||_2 in exact arithmetic); the iteration count is
+    the number of Arnoldi steps over all restart cycles.
 """
 from __future__ import annotations
 
@@ -268,6 +275,84 @@ def apply_coarse(S: Setup, r: np.ndarray) -> np.ndarray:
 def apply(S: Setup, r: np.ndarray) -> np.ndarray:
     """z = M_additive^{-1} r (Eq. two_level_schwarz)."""
     return apply_coarse(S, r) + apply_one_level(S, r)
+
+
+def apply_ras(S: Setup, r: np.ndarray) -> np.ndarray:
+    """M_RAS r = sum_i R_i^T D_i A_ii^{-1} R_i r, the one-level restricted
+    additive Schwarz method of Cai and Sarkis (Sec. 4.1).  With Boolean D_i
+    every unknown takes the local solution of the one subdomain whose
+    Omega_Ii holds it."""
+    z = np.zeros_like(r)
+    for s in S.subs:
+        y = sla.cho_solve(s.chol, r[s.omega])
+        z[s.I] += y[: len(s.I)]
+    return z
+
+
+def apply_deflated(S: Setup, r: np.ndarray) -> np.ndarray:
+    """Sec. 4.1: M_deflated r = R_0^T C_00^{-1} R_0 r
+    + M_RAS (r - A R_0^T C_00^{-1} R_0 r), C = A, C_00 = E."""
+    zc = apply_coarse(S, r)
+    return zc + apply_ras(S, r - S.A @ zc)
+
+
+def gmres(As, b: np.ndarray, prec, restart: int = 30, rtol: float = 1e-8, maxit: int = 1000):
+    """Right-preconditioned GMRES(m) (Saad and Schultz), x0 = 0: Arnoldi on
+    A M with modified Gram-Schmidt, Givens rotations reducing the Hessenberg
+    matrix, x = x0 + M V_j y_j at the end of each cycle.  Stops when the
+    least-squares residual |g_{j+1}| <= rtol ||b||_2.  Returns (x, iterations,
+    relative residual estimates, one per Arnoldi step)."""
+    n = b.shape[0]
+    x = np.zeros_like(b)
+    nb = np.linalg.norm(b)
+    hist = [1.0 if nb else 0.0]
+    if nb == 0.0:
+        return x, 0, hist
+    its = 0
+    r = b.copy()
+    while its < maxit:
+        beta = np.linalg.norm(r)
+        m = restart
+        V = np.zeros((n, m + 1))
+        Zp = np.zeros((n, m))
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[:, 0] = r / beta
+        done = False
+        j = -1
+        for j in range(m):
+            Zp[:, j] = prec(V[:, j])
+            w = As @ Zp[:, j]
+            for i in range(j + 1):
+                H[i, j] = V[:, i] @ w
+                w = w - H[i, j] * V[:, i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0.0:
+                V[:, j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                a, c = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * a + sn[i] * c
+                H[i + 1, j] = -sn[i] * a + cs[i] * c
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            hist.append(abs(g[j + 1]) / nb)
+            if hist[-1] <= rtol or its >= maxit:
+                done = True
+                break
+        k = j + 1
+        y = sla.solve_triangular(H[:k, :k], g[:k])
+        x = x + Zp[:, :k] @ y
+        if done:
+            break
+        r = b - As @ x
+    return x, its, hist
 
 
 # --------------------------------------------------------------------------
