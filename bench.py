@@ -121,9 +121,12 @@ def cpu_baseline(w, max_seconds=30.0):
         if time.perf_counter() - t_all > max_seconds / 2 or len(times) >= 3:
             break
     cores = os.cpu_count()
+    # iteration count of the deflated GMRES(30) variant (Sec. 4.1), untimed
+    _, gits, _ = O.gmres(S.A, w["b"], lambda r: O.apply_deflated(S, r), restart=30, rtol=RTOL)
     return {"value": statistics.median(times), "unit": "ms", "cores": cores, "kind": "oracle",
             "sample": f"full workload ({WORKLOAD}), {len(times)} solve(s), numpy/scipy FP64 with the default "
-                      f"BLAS threading on {cores} host cores; {its} PCG iterations"}, its
+                      f"BLAS threading on {cores} host cores; {its} PCG iterations",
+            "deflated_gmres30_iterations": gits}, its
 
 
 def max_over_ranks(x: float, dist=None, device=None) -> float:
@@ -209,7 +212,20 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20, m=None):
     x = torch.zeros_like(r)
     A.pcg_solve(h, r.data_ptr(), x.data_ptr(), 1, 1e-30, 10, allow_noconv=True)
     prof_pcg = {p["name"]: p for p in A.get_profile(h)}
+    # GMRES(30) with the one-level restricted form (n_C = 0 here): one full
+    # cycle of 30 Arnoldi steps; the Gram-Schmidt passes stream the basis
+    A.reset_profile(h)
+    xg = torch.zeros_like(r)
+    A.gmres_solve(h, A.FORM_RAS, r.data_ptr(), xg.data_ptr(), 1, 30, 1e-30, 30, allow_noconv=True)
+    prof_gm = {p["name"]: p for p in A.get_profile(h)}
     kernels = {}
+    gp = prof_gm.get("gmres_vectors")
+    if gp and gp["launches"] and gp["ms"] > 0:
+        gbs = gp["bytes"] / (gp["ms"] * 1e-3) / 1e9
+        kernels["gmres_vectors"] = {"launches": gp["launches"], "ms_per_launch": gp["ms"] / gp["launches"],
+                                    "GB/s": gbs, "frac": gbs / hbm_gbs,
+                                    "note": "GMRES(30) cycle, restricted one-level form; includes the one-block "
+                                            "reductions and Givens updates (no bytes) in the time"}
     for k in APPLY_CLASSES + ("spmv",):
         p = prof_pcg.get(k)
         if p and p["launches"] and p["ms"] > 0:
@@ -233,6 +249,98 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20, m=None):
                        "note": "one amdd_apply call on 8 right-hand sides; factors read once for all"},
         "kernels_in_pcg": kernels,
     }
+
+
+def variants(A, torch, np, dev, sp, w, precision, steps=3):
+    """The Sec. 4.1 / Sec. 4.2 solver variants, device-timed like the main
+    step (CUDA events on the library's stream, L2 flushed before each step):
+      * deflated: setup + right-preconditioned GMRES(30) with the deflated
+        form on the main workload;
+      * three_level: Laplacian 64 x 64, 16 boxes, tau = 0.5; second level on
+        E with 2 x 2 groups of boxes, tau2 = 0.5; outer flexible GMRES(30) to
+        1e-8 with inner GMRES(30) to 1e-4, against the two-level deflated
+        solve of the same problem (exact coarse Cholesky)."""
+    import synth
+    from paper_2109_05908_gb300.device import DeviceMatrix
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {}
+
+    def timed(fn, k=steps, warm=2):
+        ts, res = [], None
+        for q in range(warm + k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if q >= warm:
+                ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts), res
+
+    M, part_h, b_h = w["A"], np.asarray(w["part"], np.int32), w["b"]
+    dA = DeviceMatrix(M, device=dev)
+    part = torch.from_numpy(part_h).to(dev)
+    b = torch.from_numpy(b_h).to(dev)
+    x = torch.zeros_like(b)
+    o = A.opts_default()
+    o.precision = precision
+
+    def deflated():
+        x.zero_()
+        h = A.setup(dA.csr, part.data_ptr(), w["N"], w["overlap"], w["tau"], o, sp)
+        st = A.gmres_solve(h, A.FORM_DEFLATED, b.data_ptr(), x.data_ptr(), 1, 30, RTOL, 1000)
+        A.destroy(h)
+        return st
+
+    ms, st = timed(deflated)
+    out["deflated_gmres30"] = {"workload": WORKLOAD, "form": "deflated (Sec. 4.1), right-preconditioned GMRES(30)",
+                               "ms": ms, "iterations": st.iterations, "true_rel_residual": st.true_rel_residual}
+    # three-level form
+    m, box, tau = 64, 16, 0.5
+    M3 = synth.laplace2d(m)
+    p3 = synth.box_partition_2d(m, box)
+    N3 = int(p3.max()) + 1
+    groups = synth.box_groups_2d(m // box, 2)
+    b3 = torch.from_numpy(synth.rhs(M3.n, 0)).to(dev)
+    x3 = torch.zeros_like(b3)
+    dA3 = DeviceMatrix(M3, device=dev)
+    dp3 = torch.from_numpy(p3).to(dev)
+    o3 = A.opts_default()
+    o3.precision = precision
+    o3.keep_coarse_matrix = 1
+    info = {}
+
+    def three():
+        x3.zero_()
+        h = A.setup(dA3.csr, dp3.data_ptr(), N3, 1, tau, o3, sp)
+        h2 = A.setup_next_level(h, groups, int(groups.max()) + 1, 1, 0.5, None, 30, 1e-4, 100)
+        st = A.gmres_solve(h, A.FORM_DEFLATED, b3.data_ptr(), x3.data_ptr(), 1, 30, RTOL, 1000)
+        info["l1"], info["l2"] = A.get_info(h), A.get_info(h2)
+        A.destroy(h)
+        return st
+
+    def two():
+        x3.zero_()
+        o2 = A.opts_default()
+        o2.precision = precision
+        h = A.setup(dA3.csr, dp3.data_ptr(), N3, 1, tau, o2, sp)
+        st = A.gmres_solve(h, A.FORM_DEFLATED, b3.data_ptr(), x3.data_ptr(), 1, 30, RTOL, 1000)
+        A.destroy(h)
+        return st
+
+    ms3, st3 = timed(three)
+    ms2, st2 = timed(two)
+    l1, l2 = info["l1"], info["l2"]
+    out["three_level"] = {
+        "workload": f"laplace2d_{m}x{m}_{N3}box_ov1_tau{tau:g}; level 2: {int(groups.max()) + 1} groups of 2x2 boxes, "
+                    f"ov 1, tau2 0.5; inner GMRES(30) to 1e-4; outer flexible GMRES(30) to 1e-8",
+        "ms": ms3, "outer_iterations": st3.iterations, "true_rel_residual": st3.true_rel_residual,
+        "n_C": l1.n_C, "n_C2": l2.n_C, "inner_solves": l1.inner_solves, "inner_iterations": l1.inner_iterations,
+        "inner_iterations_max": l1.inner_iterations_max,
+        "two_level_ms": ms2, "two_level_iterations": st2.iterations}
+    return out
 
 
 def run_reference(args):
@@ -403,7 +511,10 @@ def run_amdd(args):
                 "peak_source": f"hbm_gbs ({peak_src})"}
     launches = int(sum(v["launches"] for v in prof.values()) / args.steps)
     scale = apply_at_scale(A, torch, np, dev, sp, peaks["hbm_gbs"], m=args.scale_m) if not args.no_scale else None
+    var = variants(A, torch, np, dev, sp, w, args.precision) if not args.no_variants else None
     base, base_its = cpu_baseline(w) if world == 1 or rank == 0 else (None, None)
+    if var and base:
+        var["deflated_gmres30"]["oracle_iterations"] = base["deflated_gmres30_iterations"]
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -426,6 +537,7 @@ def run_amdd(args):
         "cpu_baseline": base,
         "clocks": clk,
         "apply_scale": scale,
+        "variants": var,
         "profile_ms_warmup_step": {k: round(v["ms"], 4) for k, v in
                                    sorted(warm_prof.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
     }
@@ -456,6 +568,8 @@ def main():
     ap.add_argument("--impl", default="amdd", choices=["amdd", "reference"])
     ap.add_argument("--no-scale", action="store_true",
                     help="skip the SpMV / apply bandwidth measurement on the 1M-unknown problem")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the deflated GMRES and three-level variant timings")
     ap.add_argument("--scale-m", type=int, default=None,
                     help="grid side of the bandwidth problem (default 1024; 16 x 16 boxes)")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],

@@ -111,7 +111,9 @@ typedef struct {
     int32_t keep_proposal_data; /* 1: keep the features and Krylov bases of the partially selected
                              subdomains for amdd_proposal_export                                     */
     const amdd_proposal* proposal; /* the network of eig_solver = 2 (NULL otherwise)                */
-    int32_t reserved[2];  /* must be zero                                                          */
+    int32_t keep_coarse_matrix; /* 1: keep a copy of the coarse matrix E (block pattern, see
+                             amdd_setup_next_level) for a next level; default 0                     */
+    int32_t reserved;     /* must be zero                                                          */
 } amdd_opts;
 
 typedef struct {
@@ -151,6 +153,13 @@ typedef struct {
     int32_t lobpcg_fallbacks;  /* LOBPCG results rejected (dense path taken)  */
     int32_t lobpcg_iters_max;  /* largest LOBPCG iteration count             */
     int64_t lobpcg_iters_total;/* sum of the LOBPCG iteration counts         */
+    int32_t robust_schur;      /* subdomains whose Schur complement of the splitting was
+                                  recomputed in the rounding-robust form (the Cholesky of
+                                  its [Omega_Gi, Omega_Di] block lost definiteness)   */
+    int32_t levels;            /* 1 + the levels attached by amdd_setup_next_level */
+    int32_t inner_iterations_max; /* largest inner GMRES iteration count of a coarse solve */
+    int64_t inner_solves;      /* coarse solves done by inner GMRES (since setup) */
+    int64_t inner_iterations;  /* their total iteration count                  */
 } amdd_info;
 
 /* Fill `o` with the defaults (eps = 2^-52, max_sweeps = 60). */
@@ -204,6 +213,89 @@ amdd_status amdd_apply(amdd_handle* h, const double* r, double* z, int32_t nrhs)
  * right-hand side. */
 amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t nrhs,
                            double rtol, int32_t maxit, amdd_stats* stats);
+
+/* Preconditioner forms of amdd_apply_form and amdd_gmres_solve.
+ *   AMDD_FORM_ADDITIVE  the additive two-level method, Eq. (two_level_schwarz):
+ *                       z = R_0^T E^{-1} R_0 r + sum_i R_i^T A_ii^{-1} R_i r.
+ *   AMDD_FORM_DEFLATED  the deflated two-level method of Sec. 4.1 with the
+ *                       restricted one-level method and C = A:
+ *                       zc = R_0^T E^{-1} R_0 r,  z = zc + M_RAS (r - A zc).
+ *   AMDD_FORM_RAS       the one-level restricted additive Schwarz method of
+ *                       Sec. 4.1: z = sum_i R_i^T D_i A_ii^{-1} R_i r (Boolean
+ *                       D_i: every unknown takes the local solution of the
+ *                       subdomain whose Omega_Ii holds it).
+ *   AMDD_FORM_ASM       the one-level additive method of Sec. 2.1:
+ *                       z = sum_i R_i^T A_ii^{-1} R_i r.
+ * DEFLATED and RAS are not symmetric: use them with GMRES. */
+typedef enum {
+    AMDD_FORM_ADDITIVE = 0,
+    AMDD_FORM_DEFLATED = 1,
+    AMDD_FORM_RAS = 2,
+    AMDD_FORM_ASM = 3
+} amdd_form;
+
+/* z = M^{-1} r for the preconditioner form `form` (amdd_form) of the
+ * handle's setup, for `nrhs` vectors.  r and z are device pointers to nrhs
+ * contiguous vectors of length n (vector k at offset k*n); z must not alias
+ * r.  The local and coarse solves are those of amdd_apply (same precision).
+ * AMDD_ERR_INVALID on a bad form or argument. */
+amdd_status amdd_apply_form(amdd_handle* h, int32_t form, const double* r, double* z, int32_t nrhs);
+
+/* Largest restart length of amdd_gmres_solve. */
+#define AMDD_GMRES_MAX_RESTART 64
+
+/* Right-preconditioned restarted GMRES(restart) (Saad and Schultz; the
+ * Krylov method of the experiments of Sec. 4.1, there with restart 30) on
+ * A x = b with the preconditioner form `form` (amdd_form), for `nrhs`
+ * right-hand sides solved one after the other.  b and x are device pointers
+ * (nrhs contiguous vectors of length n); x holds the initial guess on entry
+ * and the solution on return.  Each cycle starts from r = b - A x; the
+ * Arnoldi basis is orthogonalised by classical Gram-Schmidt applied twice.
+ * Stops when the least-squares residual estimate |g_{j+1}| <= rtol ||b||_2
+ * or after maxit Arnoldi steps in total (AMDD_ERR_NOCONV).  `stats` (host,
+ * may be NULL) describes the first right-hand side: iterations = Arnoldi
+ * steps, rel_residual = the estimate at exit, true_rel_residual recomputed;
+ * ritz_min, ritz_max and cond_est are NaN.  The handle allocates
+ * (restart + 1 + restart) n doubles of Krylov vectors on the first call (and
+ * again when a later call asks for a longer restart).  AMDD_ERR_INVALID for
+ * restart outside [1, AMDD_GMRES_MAX_RESTART], a bad form or argument. */
+amdd_status amdd_gmres_solve(amdd_handle* h, int32_t form, const double* b, double* x, int32_t nrhs,
+                             int32_t restart, double rtol, int32_t maxit, amdd_stats* stats);
+
+/* Multilevel form (Sec. 3.2, last paragraph; Sec. 4.2): the same fully
+ * algebraic construction applied to the coarse matrix E of handle h, whose
+ * exact coarse solve is then replaced by an inexact one.  h must have been
+ * set up with opts.keep_coarse_matrix = 1 and n_C > 0.
+ *   groups   HOST int32[N] (N = subdomains of h): the coarse unknowns of
+ *            subdomain i (its p_i selected eigenvectors) form part of
+ *            second-level subdomain groups[i], in [0, N2); every group must
+ *            hold at least one coarse unknown.
+ *   N2, overlap2, tau2, opts2   as in amdd_setup, for the second level.
+ *            The second level sees E as a sparse matrix with its block
+ *            pattern: every entry of the p_i x p_j block E_ij for i == j or
+ *            for subdomains whose non-overlapping sets are coupled in A
+ *            (A(Omega_Ii, Omega_Ij) has a structural non-zero).
+ *   inner_restart, inner_rtol, inner_maxit
+ *            every later coarse solve of h (in amdd_apply, amdd_apply_form,
+ *            amdd_pcg_solve, amdd_gmres_solve) is right-preconditioned
+ *            GMRES(inner_restart) on E e = c from e = 0 with the deflated
+ *            form of the second level, stopped at |g_{j+1}| <= inner_rtol
+ *            ||c||_2 or after inner_maxit steps (no error: an inexact solve;
+ *            the paper uses 30 and 1e-4).  The preconditioner of h then
+ *            changes from one application to the next: solve with
+ *            amdd_gmres_solve, which keeps the preconditioned vectors and so
+ *            is the flexible GMRES of Sec. 4.2.
+ * The second-level handle is owned by h (released by amdd_destroy(h)) and
+ * can be inspected through amdd_next_level; calling this function again
+ * replaces it.  h frees its copy of E afterwards.  Errors: AMDD_ERR_INVALID
+ * (no kept E, bad groups or parameters), and those of amdd_setup. */
+amdd_status amdd_setup_next_level(amdd_handle* h, const int32_t* groups, int32_t N2, int32_t overlap2,
+                                  double tau2, const amdd_opts* opts2, int32_t inner_restart, double inner_rtol,
+                                  int32_t inner_maxit);
+
+/* The second-level handle attached by amdd_setup_next_level (borrowed,
+ * owned by h), or NULL. */
+amdd_handle* amdd_next_level(const amdd_handle* h);
 
 /* Training data of the learned warm start (no counterpart in the paper)
  * from a handle built with opts.keep_proposal_data = 1: for each partially
@@ -295,7 +387,7 @@ amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, i
  * amdd_setup, amdd_apply and amdd_pcg_solve until amdd_reset_profile.
  * Synchronises the handle's stream.  AMDD_ERR_INVALID if profiling is off or
  * k is out of range. */
-#define AMDD_PROF_CLASSES 24
+#define AMDD_PROF_CLASSES 25
 amdd_status amdd_get_profile(amdd_handle* h, int32_t k, const char** name, int64_t* launches, double* ms,
                              double* flops, double* bytes);
 

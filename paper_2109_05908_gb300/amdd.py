@@ -31,7 +31,7 @@ class amdd_opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("max_sweeps", C.c_int32), ("profile", C.c_int32),
                 ("precision", C.c_int32), ("profile_classes", C.c_uint32), ("eig_solver", C.c_int32),
                 ("keep_proposal_data", C.c_int32), ("proposal", C.POINTER(amdd_proposal)),
-                ("reserved", C.c_int32 * 2)]
+                ("keep_coarse_matrix", C.c_int32), ("reserved", C.c_int32)]
 
 
 MLP_NPARAM = 140032
@@ -53,7 +53,9 @@ class amdd_info(C.Structure):
                 ("sweeps_svd32", C.c_int32), ("sweeps_eig32", C.c_int32), ("precision", C.c_int32),
                 ("eps", C.c_double), ("n_partial", C.c_int32), ("lobpcg_subdomains", C.c_int32),
                 ("lobpcg_fallbacks", C.c_int32), ("lobpcg_iters_max", C.c_int32),
-                ("lobpcg_iters_total", C.c_int64)]
+                ("lobpcg_iters_total", C.c_int64), ("robust_schur", C.c_int32), ("levels", C.c_int32),
+                ("inner_iterations_max", C.c_int32),
+                ("inner_solves", C.c_int64), ("inner_iterations", C.c_int64)]
 
 
 class AmddError(RuntimeError):
@@ -73,7 +75,13 @@ SIGNATURES = {
     "amdd_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "amdd_pcg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32,
                                  C.POINTER(amdd_stats)]),
+    "amdd_apply_form": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]),
+    "amdd_gmres_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                   C.c_double, C.c_int32, C.POINTER(amdd_stats)]),
     "amdd_get_info": (C.c_int, [C.c_void_p, C.POINTER(amdd_info)]),
+    "amdd_setup_next_level": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double,
+                                        C.POINTER(amdd_opts), C.c_int32, C.c_double, C.c_int32]),
+    "amdd_next_level": (C.c_void_p, [C.c_void_p]),
     "amdd_proposal_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                        C.POINTER(C.c_int32)]),
     "amdd_get_eig_iterations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
@@ -164,6 +172,38 @@ def pcg_solve(h: int, b_ptr: int, x_ptr: int, nrhs: int = 1, rtol: float = 1e-8,
     _check(lib().amdd_pcg_solve(h, b_ptr, x_ptr, nrhs, float(rtol), maxit, C.byref(s)), "amdd_pcg_solve",
            allow=(3,) if allow_noconv else ())
     return s
+
+
+FORM_ADDITIVE, FORM_DEFLATED, FORM_RAS, FORM_ASM = 0, 1, 2, 3
+GMRES_MAX_RESTART = 64
+
+
+def apply_form(h: int, form: int, r_ptr: int, z_ptr: int, nrhs: int = 1) -> None:
+    _check(lib().amdd_apply_form(h, form, r_ptr, z_ptr, nrhs), "amdd_apply_form")
+
+
+def gmres_solve(h: int, form: int, b_ptr: int, x_ptr: int, nrhs: int = 1, restart: int = 30, rtol: float = 1e-8,
+                maxit: int = 1000, allow_noconv: bool = False) -> amdd_stats:
+    s = amdd_stats()
+    _check(lib().amdd_gmres_solve(h, form, b_ptr, x_ptr, nrhs, restart, float(rtol), maxit, C.byref(s)),
+           "amdd_gmres_solve", allow=(3,) if allow_noconv else ())
+    return s
+
+
+def setup_next_level(h: int, groups, N2: int, overlap2: int, tau2: float, opts2: amdd_opts | None = None,
+                     inner_restart: int = 30, inner_rtol: float = 1e-4, inner_maxit: int = 100) -> int:
+    """Attach a second level built on the coarse matrix of h (host int32
+    groups[N]); returns the second-level handle (owned by h)."""
+    import numpy as np
+    g = np.ascontiguousarray(groups, dtype=np.int32)
+    _check(lib().amdd_setup_next_level(h, g.ctypes.data, N2, overlap2, float(tau2),
+                                       C.byref(opts2) if opts2 else None, inner_restart, float(inner_rtol),
+                                       inner_maxit), "amdd_setup_next_level")
+    return lib().amdd_next_level(h)
+
+
+def next_level(h: int):
+    return lib().amdd_next_level(h)
 
 
 def get_info(h: int) -> amdd_info:
@@ -286,7 +326,7 @@ def lanczos_extremes(alpha, beta):
     return lo.value, hi.value
 
 
-PROF_CLASSES = 24
+PROF_CLASSES = 25
 
 
 def get_profile(h: int):

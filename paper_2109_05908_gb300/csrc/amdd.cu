@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <type_traits>
 #include <chrono>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -66,6 +67,7 @@ enum ProfK {
     PK_BISECT_F32,
     PK_GEMV_F32,
     PK_CSOLVE,
+    PK_GMRES,
     PK_COUNT
 };
 static_assert(PK_COUNT == AMDD_PROF_CLASSES, "profile classes");
@@ -73,7 +75,7 @@ static const char* const kProfNames[PK_COUNT] = {
     "gather_values", "chol_diag", "chol_panel", "gemm_tiles", "trtri_diag", "jacobi_svd", "jacobi_eig", "jacobi_f32", "tridiag", "bisect",
     "small_dense", "e_offdiag", "spmv", "gemv_rows", "gather_scatter", "pcg_vectors",
     "gemm_tiles_f32", "chol_diag_f32", "chol_panel_f32", "trtri_diag_f32", "tridiag_f32", "bisect_f32",
-    "gemv_rows_f32", "coarse_solve"};
+    "gemv_rows_f32", "coarse_solve", "gmres_vectors"};
 
 // class of a kernel in element type T (FP32 variants have their own classes)
 template <typename T>
@@ -178,6 +180,7 @@ struct amdd_handle {
     // eigenvectors of partial selections: 0 dense Jacobi, 1 LOBPCG from random
     // rows, 2 LOBPCG from the learned proposal
     int eig_solver = 0, keep_prop = 0;
+    int n_robust = 0;  // subdomains whose Schur complement took the robust form (step 5b)
     amdd_proposal prop{};
     bool have_prop = false;
     std::vector<int> eig_iters;  // per subdomain: LOBPCG iterations, -1 dense path, -2 not partial
@@ -200,6 +203,27 @@ struct amdd_handle {
     double* prop_bt = nullptr;
     std::vector<int> prop_sub;
     std::vector<int64_t> prop_off_b;
+    // deflated / restricted forms (Sec. 4.1), allocated on first use: position
+    // in the local vectors of each unknown's own copy (owner order), and work
+    // vectors in global order
+    int32_t* d_own_idx = nullptr;
+    double *d_zg = nullptr, *d_t = nullptr;
+    // multilevel form: kept copy of E with its block pattern (CSR), the
+    // second level and the counters of its inner solves
+    int keep_E = 0;
+    int64_t* d_E_rowptr = nullptr;
+    int32_t* d_E_col = nullptr;
+    double* d_E_val = nullptr;
+    int64_t E_nnz = 0;
+    amdd_handle* next = nullptr;
+    int in_restart = 30, in_maxit = 100;
+    double in_rtol = 1e-4;
+    int64_t in_calls = 0, in_its = 0;
+    int in_max = 0;
+    // GMRES(m) work, allocated on first use for restart length gm_cap
+    int gm_cap = 0;
+    double *d_gm_V = nullptr, *d_gm_Zp = nullptr, *d_gm_wA = nullptr, *d_gm_wB = nullptr, *d_gm_part = nullptr;
+    GmState* d_gm_st = nullptr;
     // PCG work vectors
     double *d_r = nullptr, *d_z = nullptr, *d_pv = nullptr, *d_q = nullptr, *d_part = nullptr;
     PcgScal* d_sc = nullptr;
@@ -1650,11 +1674,14 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
 
     // ---- (4) Schur complement of Abar_ii onto Omega_Ii: Cholesky of the
     // leading [G, D] block (pivot floor sigma_1 eps, the shift of Remark 3.2).
+    constexpr bool f64s = std::is_same<TS, double>::value;
+    int* dbad = C.tnew<int>(N);
+    ck(cudaMemsetAsync(dbad, 0, N * sizeof(int), s));
     {
         std::vector<CholDescT<TS>> cd(N);
         for (int i = 0; i < N; ++i) {
             const int nt = h->nt[i], nR = h->nG[i] + h->nD[i];
-            cd[i] = {M + off_m[i], nt, nt, nR, delta + i, linvM + off_lm[i]};
+            cd[i] = {M + off_m[i], nt, nt, nR, delta + i, linvM + off_lm[i], dbad + i};
         }
         chol_batched(C, cd);
     }
@@ -1717,6 +1744,100 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         auto di = C.up(idd);
         PScope ps(h, PK_SMALL);
         launch_set_identity<T>(di, N, h->max_nt, s);
+    }
+
+    // ---- (5b) robust Schur complement for the subdomains whose clamped
+    // Cholesky was flagged.  With C = Sigma^{1/2} V^T = [C_R | C_I] (the scaled
+    // rows of step (2), columns [G, D | I]) and Abar = C^T C + delta I, the
+    // push-through identity gives the Schur complement onto Omega_Ii as
+    //   S = delta (I + C_I^T (C_R C_R^T + delta I)^{-1} C_I).
+    // C_R C_R^T + delta I = Q^T diag(s_k^2 + delta) Q comes from a one-sided
+    // Jacobi of the rows of C_R (no Gram matrix is formed, so the shift is
+    // never swamped by rounding), W = diag(1 / sqrt(s^2 + delta)) Q C_I and
+    //   T = L_A^{-1} S L_A^{-T} = delta (L_A^{-1} L_A^{-T} + P^T P),  P = W L_A^{-T},
+    // a sum of positive semidefinite terms.
+    {
+        std::vector<int> bad(N);
+        std::vector<TS> dl(N);
+        ck(cudaMemcpyAsync(bad.data(), dbad, N * sizeof(int), cudaMemcpyDeviceToHost, s));
+        ck(cudaMemcpyAsync(dl.data(), delta, N * sizeof(TS), cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        std::vector<int> F;
+        for (int i = 0; i < N; ++i)
+            if (bad[i] && h->nG[i] + h->nD[i] > 0) F.push_back(i);
+        h->n_robust = (int)F.size();
+        if (!F.empty()) {
+            const int nf = (int)F.size();
+            std::vector<int64_t> oj(nf + 1, 0), ow(nf + 1, 0);
+            for (int q = 0; q < nf; ++q) {
+                const int i = F[q];
+                oj[q + 1] = oj[q] + (int64_t)h->ni[i] * (h->nG[i] + h->nD[i] + h->ni[i]);
+                ow[q + 1] = ow[q] + (int64_t)h->ni[i] * h->nI[i];
+            }
+            TS* J = C.tnew<TS>(oj[nf]);
+            TS* W = C.tnew<TS>(ow[nf]);
+            TS* nrm = C.tnew<TS>(h->sum_ni);
+            std::vector<KjacDesc<TS>> kd(nf);
+            std::vector<JacobiDescT<TS>> jd(nf);
+            int maxr = 1, maxc = 1;
+            for (int q = 0; q < nf; ++q) {
+                const int i = F[q], ni = h->ni[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], lj = nR + ni;
+                kd[q] = {X1 + off_x[i], J + oj[q], ni, nR, nt, lj, delta + i};
+                jd[q] = {J + oj[q], ni, lj, nR, lj, nrm + h->off_om[i], nullptr};
+                maxr = std::max(maxr, ni);
+                maxc = std::max(maxc, nR);
+            }
+            // no rotation for |<p,q>| <= tol * delta: such rows are resolved to
+            // the accuracy of K = C_R C_R^T + delta I already
+            std::vector<TS> kfl(nf);
+            const TS tol = (f64s ? TS(2) : TS(8)) * std::sqrt((TS)maxc) * std::numeric_limits<TS>::epsilon();
+            for (int q = 0; q < nf; ++q) kfl[q] = tol * dl[F[q]];
+            TS* dkfl = C.up(kfl);
+            for (int q = 0; q < nf; ++q) jd[q].absfloor = dkfl + q;
+            auto dkd = C.up(kd);
+            JacobiDescT<TS>* djd = C.up(jd);
+            int* rsw = C.tnew<int>(nf);
+            unsigned long long* rrot = C.tnew<unsigned long long>(nf);
+            {
+                PScope ps(h, PK_SMALL);
+                launch_build_kjac<TS>(dkd, nf, maxr, s);
+            }
+            {
+                PScope ps(h, pk<TS>(PK_JAC_SVD, PK_JAC_F32));
+                run_jacobi<TS>(h, jd, djd, h->max_sweeps, tol, rsw, rrot, f64s ? 1 : 0);
+            }
+            {
+                PScope ps(h, PK_SMALL);
+                launch_kjac_scale<TS>(dkd, nf, s);
+            }
+            std::vector<GemmDescT<TS>> gw(nf);
+            for (int q = 0; q < nf; ++q) {
+                const int i = F[q], ni = h->ni[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], nIi = h->nI[i];
+                gw[q] = gd<TS>(J + oj[q] + nR, nR + ni, 0, X1 + off_x[i] + nR, nt, 0, W + ow[q], nIi, ni, nIi, ni,
+                               1.0, 0.0, 0);
+            }
+            gemm(C, gw);
+            T* WT = nullptr;
+            if constexpr (std::is_same<T, TS>::value) {
+                WT = W;
+            } else {
+                WT = C.tnew<T>(ow[nf]);
+                launch_convert<TS, T>(W, WT, ow[nf], s);
+            }
+            T* P = C.tnew<T>(ow[nf]);
+            std::vector<GemmDescT<T>> g1, g2;
+            for (int q = 0; q < nf; ++q) {
+                const int i = F[q], ni = h->ni[i], nIi = h->nI[i];
+                const T* Y = Yl + h->off_sq[i];  // L_A^{-1}: leading nI x nI block of L_i^{-1}
+                const double dv = (double)dl[i];
+                g1.push_back(gd<T>(WT + ow[q], nIi, 0, Y, ni, 1, P + ow[q], nIi, ni, nIi, nIi, 1.0, 0.0, 0));
+                g1.push_back(gd<T>(Y, ni, 0, Y, ni, 1, TI + off_ti[i], 2 * nIi, nIi, nIi, nIi, dv, 0.0, 0));
+                g2.push_back(gd<T>(P + ow[q], nIi, 1, P + ow[q], nIi, 0, TI + off_ti[i], 2 * nIi, nIi, nIi, ni, dv,
+                                   1.0, 0));
+            }
+            gemm(C, g1);
+            gemm(C, g2);
+        }
     }
 
     // ---- (6) eigenvalues mu = 1/lambda of eq. (Zi): Householder reduction of
@@ -2003,6 +2124,41 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             launch_e_offdiag(a, (int)et.size(), b, c, h->d_Zt, h->d_zt_off, h->d_nI, AZ, d, h->d_p, h->d_coff, E, nC,
                              s);
         }
+        if (h->keep_E) {
+            // a copy of E for a next level (multilevel form), as a sparse matrix
+            // with the block pattern: every entry of E_ij for i == j or for
+            // subdomains coupled in A (a structural non-zero in
+            // A(Omega_Ii, Omega_Ij)); E holds its lower triangle
+            std::vector<std::vector<int>> adj(N);
+            for (int64_t g = 0; g < n; ++g)
+                for (int64_t k = rp[g]; k < rp[g + 1]; ++k)
+                    if (part[g] != part[ci[k]]) adj[part[g]].push_back(part[ci[k]]);
+            for (int i = 0; i < N; ++i) {
+                adj[i].push_back(i);
+                std::sort(adj[i].begin(), adj[i].end());
+                adj[i].erase(std::unique(adj[i].begin(), adj[i].end()), adj[i].end());
+            }
+            std::vector<int64_t> erp(nC + 1, 0), esrc;
+            std::vector<int32_t> ecol;
+            for (int i = 0; i < N; ++i)
+                for (int k = 0; k < h->p[i]; ++k) {
+                    const int64_t r = h->coff[i] + k;
+                    for (int j : adj[i])
+                        for (int l = 0; l < h->p[j]; ++l) {
+                            const int64_t c = h->coff[j] + l;
+                            ecol.push_back((int32_t)c);
+                            esrc.push_back(std::max(r, c) * nC + std::min(r, c));
+                        }
+                    erp[r + 1] = (int64_t)ecol.size();
+                }
+            h->E_nnz = (int64_t)ecol.size();
+            h->d_E_rowptr = C.up(erp, true);
+            h->d_E_col = C.up(ecol, true);
+            h->d_E_val = dnew<double>(h, h->E_nnz);
+            auto dsrc = C.up(esrc);
+            PScope ps(h, PK_SMALL, 0.0, 16.0 * h->E_nnz);
+            launch_gather_idx64(dsrc, h->E_nnz, E, h->d_E_val, s);
+        }
         double* linvE = C.tnew<double>((size_t)cdiv(nC, CHOL_NB) * CHOL_NB * CHOL_NB);
         // envelope of E: block row i starts at the first subdomain j <= i coupled
         // to i.  The factor keeps that row envelope but fills it in, so column c
@@ -2192,7 +2348,10 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     if (e) throw Fail{err_status(e)};
 }
 
-void apply_one(amdd_handle* h, const double* r, double* z) {
+// Local solves of the Schwarz methods: rloc = R_i r for every subdomain,
+// then y_i = L_i^{-T} L_i^{-1} rloc_i (into d_yloc, or d_yloc32 in the mixed
+// form, whose local solves run in FP32).
+void local_solves(amdd_handle* h, const double* r) {
     cudaStream_t s = h->s;
     const double tri = (double)h->apply_tri_elems;  // elements of the lower + upper local factors
     {
@@ -2223,29 +2382,106 @@ void apply_one(amdd_handle* h, const double* r, double* z) {
             launch_gemv_rows4<float>(h->d_gv_l2_32, h->d_g4_desc, h->d_g4_row, h->n_g4, s);
         }
     }
-    if (h->nC > 0) {
-        const double zt = (double)h->sum_zt;
-        {
-            PScope ps(h, PK_GEMV, 2.0 * zt, 8.0 * zt + 8.0 * h->sum_ni + 16.0 * h->nC);
-            launch_gemv_rows<double>(h->d_gv_c, h->d_rd_c, h->d_rl_c, h->nC, s);
-        }
-        {
-            CoarseSolveArgs a{h->d_YE, h->d_YEt, h->d_Yd, h->d_Ydt, h->d_env_row, h->d_env_colend,
-                              h->d_c, h->d_ctmp, h->d_e, (int)h->nC, (int)h->nC, h->cSB, h->cK};
-            PScope ps(h, PK_CSOLVE, h->csolve_flops, h->csolve_bytes);
-            ck(launch_coarse_solve(a, h->coop_blocks, s));
-        }
-        {
-            PScope ps(h, PK_GEMV, 2.0 * zt, 8.0 * zt + 8.0 * h->nC + 8.0 * h->n);
-            launch_gemv_rows<double>(h->d_gv_zp, h->d_rd_zp, h->d_rl_zp, h->n_zp, s);
-        }
+}
+
+// Coarse correction R_0^T E^{-1} R_0 r of Eq. (two_level_schwarz) from the
+// gathered rloc (its Omega_Ii entries): c = Z^T r, the solve with L_E, and
+// zc = Z e in owner order (d_zc).  Needs nC > 0.
+void inner_coarse_solve(amdd_handle* h);
+
+void coarse_correction(amdd_handle* h) {
+    cudaStream_t s = h->s;
+    const double zt = (double)h->sum_zt;
+    {
+        PScope ps(h, PK_GEMV, 2.0 * zt, 8.0 * zt + 8.0 * h->sum_ni + 16.0 * h->nC);
+        launch_gemv_rows<double>(h->d_gv_c, h->d_rd_c, h->d_rl_c, h->nC, s);
     }
+    if (h->next) {
+        inner_coarse_solve(h);  // multilevel form: e ~ E^{-1} c by GMRES on the next level
+    } else {
+        CoarseSolveArgs a{h->d_YE, h->d_YEt, h->d_Yd, h->d_Ydt, h->d_env_row, h->d_env_colend,
+                          h->d_c, h->d_ctmp, h->d_e, (int)h->nC, (int)h->nC, h->cSB, h->cK};
+        PScope ps(h, PK_CSOLVE, h->csolve_flops, h->csolve_bytes);
+        ck(launch_coarse_solve(a, h->coop_blocks, s));
+    }
+    {
+        PScope ps(h, PK_GEMV, 2.0 * zt, 8.0 * zt + 8.0 * h->nC + 8.0 * h->n);
+        launch_gemv_rows<double>(h->d_gv_zp, h->d_rd_zp, h->d_rl_zp, h->n_zp, s);
+    }
+}
+
+// z = M^{-1} r, Eq. (two_level_schwarz): one-level sum plus the coarse term,
+// summed per unknown in a fixed order.
+void apply_one(amdd_handle* h, const double* r, double* z) {
+    cudaStream_t s = h->s;
+    local_solves(h, r);
+    if (h->nC > 0) coarse_correction(h);
     PScope ps(h, PK_GATHER_SCATTER, 0.0, 12.0 * h->sum_ni + 24.0 * h->n);
     const double* zc = h->nC > 0 ? h->d_zc : nullptr;
     if (h->precision == 0)
         launch_scatter_prolong<double>(h->n, h->d_order_g, h->d_sc_ptr, h->d_sc_idx, h->d_yloc, zc, z, s);
     else
         launch_scatter_prolong<float>(h->n, h->d_order_g, h->d_sc_ptr, h->d_sc_idx, h->d_yloc32, zc, z, s);
+}
+
+// Buffers of the deflated and restricted forms, on first use.
+void ensure_forms(amdd_handle* h) {
+    if (h->d_own_idx) return;
+    std::vector<int32_t> own(h->n);
+    for (int i = 0; i < h->N; ++i)
+        for (int a = 0; a < h->nI[i]; ++a) own[h->off_I[i] + a] = (int32_t)(h->off_om[i] + a);  // [I, G] order
+    h->d_own_idx = dnew<int32_t>(h, h->n);
+    ck(cudaMemcpyAsync(h->d_own_idx, own.data(), h->n * sizeof(int32_t), cudaMemcpyHostToDevice, h->s));
+    h->d_zg = dnew<double>(h, h->n);
+    h->d_t = dnew<double>(h, h->n);
+    ck(cudaStreamSynchronize(h->s));
+}
+
+// z = M^{-1} r for the forms of amdd_form:
+//   AMDD_FORM_ADDITIVE  Eq. (two_level_schwarz);
+//   AMDD_FORM_DEFLATED  Sec. 4.1: zc + M_RAS (r - A zc), zc = R_0^T E^{-1} R_0 r;
+//   AMDD_FORM_RAS       Sec. 4.1: sum_i R_i^T D_i A_ii^{-1} R_i r;
+//   AMDD_FORM_ASM       sum_i R_i^T A_ii^{-1} R_i r (one-level additive).
+void apply_form(amdd_handle* h, int form, const double* r, double* z) {
+    if (form == AMDD_FORM_ADDITIVE) {
+        apply_one(h, r, z);
+        return;
+    }
+    cudaStream_t s = h->s;
+    const bool coarse = form == AMDD_FORM_DEFLATED && h->nC > 0;
+    const double* x = r;
+    if (form != AMDD_FORM_ASM) ensure_forms(h);
+    if (coarse) {
+        {
+            PScope ps(h, PK_GATHER_SCATTER, 0.0, 20.0 * h->sum_ni);
+            launch_gather_vec(h->d_omega, h->sum_ni, r, h->d_rloc, s);
+        }
+        coarse_correction(h);
+        {
+            PScope ps(h, PK_GATHER_SCATTER, 0.0, 24.0 * h->n);
+            launch_owner_to_global(h->n, h->d_order_g, h->d_zc, h->d_zg, s);
+        }
+        {
+            PScope ps(h, PK_SPMV, 2.0 * h->nnz, 12.0 * h->nnz + 8.0 * (h->n + 1) + 24.0 * h->n);
+            launch_spmv_resid(h->n, h->rowptr, h->col, h->val, h->d_zg, r, h->d_t, h->spmv_group, s);
+        }
+        x = h->d_t;
+    }
+    local_solves(h, x);
+    const double* zc = coarse ? h->d_zc : nullptr;
+    if (form == AMDD_FORM_ASM) {
+        PScope ps(h, PK_GATHER_SCATTER, 0.0, 12.0 * h->sum_ni + 16.0 * h->n);
+        if (h->precision == 0)
+            launch_scatter_prolong<double>(h->n, h->d_order_g, h->d_sc_ptr, h->d_sc_idx, h->d_yloc, nullptr, z, s);
+        else
+            launch_scatter_prolong<float>(h->n, h->d_order_g, h->d_sc_ptr, h->d_sc_idx, h->d_yloc32, nullptr, z, s);
+        return;
+    }
+    PScope ps(h, PK_GATHER_SCATTER, 0.0, (h->precision == 0 ? 8.0 : 4.0) * h->n + (coarse ? 24.0 : 16.0) * h->n);
+    if (h->precision == 0)
+        launch_ras_prolong<double>(h->n, h->d_order_g, h->d_own_idx, h->d_yloc, zc, z, s);
+    else
+        launch_ras_prolong<float>(h->n, h->d_order_g, h->d_own_idx, h->d_yloc32, zc, z, s);
 }
 
 // Launch wrappers of the PCG loop with their profile accounting.
@@ -2332,6 +2568,10 @@ void ensure_multi(amdd_handle* h) {
 // z_k = M^{-1} r_k for nb <= MAXB right-hand sides (vectors n apart): every
 // factor, Z_i and L_E entry is read once per pass for all of them.
 void apply_multi(amdd_handle* h, const double* r, double* z, int nb) {
+    if (h->next) {  // inexact coarse solves run one right-hand side at a time
+        for (int k = 0; k < nb; ++k) apply_one(h, r + (size_t)k * h->n, z + (size_t)k * h->n);
+        return;
+    }
     ensure_multi(h);
     cudaStream_t s = h->s;
     const int64_t L = h->sum_ni;
@@ -2481,6 +2721,168 @@ bool pcg_multi(amdd_handle* h, const double* b, double* x, int nb, double rtol, 
     return all;
 }
 
+// GMRES(m) work buffers for restart length m, on first use (grown when a
+// later call asks for a longer restart).
+void ensure_gmres(amdd_handle* h, int m) {
+    if (h->gm_cap >= m) return;
+    auto drop = [h](void* p) {
+        if (!p) return;
+        ck(cudaFreeAsync(p, h->s));
+        h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
+    };
+    drop(h->d_gm_V);
+    drop(h->d_gm_Zp);
+    const int64_t n = h->n;
+    h->d_gm_V = dnew<double>(h, (int64_t)(m + 1) * n);
+    h->d_gm_Zp = dnew<double>(h, (int64_t)m * n);
+    if (!h->d_gm_st) {
+        h->d_gm_wA = dnew<double>(h, n);
+        h->d_gm_wB = dnew<double>(h, n);
+        h->d_gm_part = dnew<double>(h, (int64_t)(GM_MAXR + 1) * DOT_BLOCKS);
+        h->d_gm_st = dnew<GmState>(h, 1);
+    }
+    h->gm_cap = m;
+}
+
+struct GmTail {  // the trailing scalars of GmState, read back after each Arnoldi step
+    double bnorm2, beta, hnext, res;
+    int conv;
+};
+
+struct GmResult {
+    int its = 0;
+    bool conv = false;
+    double res = 0.0;  // |g_{j+1}| / ||b|| at exit
+    double bnorm2 = 0.0;
+};
+
+// Right-preconditioned GMRES(m) (Saad and Schultz) on A x = b with the
+// preconditioner of `form`: Arnoldi on A M with classical Gram-Schmidt
+// applied twice, Givens rotations on the Hessenberg matrix,
+// x += M V_k y_k at the end of each cycle (the preconditioned vectors
+// M v_j are kept), restart from r = b - A x.  Stops when the least-squares
+// residual |g_{j+1}| <= rtol ||b||_2 or after maxit Arnoldi steps.
+GmResult gmres_run(amdd_handle* h, int form, const double* b, double* x, int m, double rtol, int maxit) {
+    ensure_gmres(h, m);
+    cudaStream_t s = h->s;
+    const int64_t n = h->n;
+    double* V = h->d_gm_V;
+    double* Zp = h->d_gm_Zp;
+    double* part = h->d_gm_part;
+    GmState* st = h->d_gm_st;
+    double* hcol = reinterpret_cast<double*>(reinterpret_cast<char*>(st) + offsetof(GmState, hcol));
+    double* H = reinterpret_cast<double*>(reinterpret_cast<char*>(st) + offsetof(GmState, H));
+    const char* tail_src = reinterpret_cast<const char*>(st) + offsetof(GmState, bnorm2);
+    GmTail tail{};
+    GmResult out;
+    {
+        PScope ps(h, PK_GMRES, 2.0 * n, 8.0 * n);
+        launch_dot_partials(n, b, b, part, s);
+    }
+    {
+        PScope ps(h, PK_GMRES);
+        launch_gm_norm(part, st, 0, s);
+    }
+    ck(cudaMemcpyAsync(&tail, tail_src, sizeof(GmTail), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    out.bnorm2 = tail.bnorm2;
+    if (tail.bnorm2 == 0.0) {  // b = 0: x = 0
+        ck(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+        out.conv = true;
+        return out;
+    }
+    out.res = 1.0;
+    while (out.its < maxit) {
+        // r = b - A x, beta = ||r||, v_0 = r / beta, g = beta e_1
+        {
+            PScope ps(h, PK_SPMV, 2.0 * h->nnz, 12.0 * h->nnz + 8.0 * (n + 1) + 24.0 * n);
+            launch_spmv_resid(n, h->rowptr, h->col, h->val, x, b, V, h->spmv_group, s);
+        }
+        {
+            PScope ps(h, PK_GMRES, 2.0 * n, 8.0 * n);
+            launch_dot_partials(n, V, V, part, s);
+        }
+        {
+            PScope ps(h, PK_GMRES);
+            launch_gm_norm(part, st, 1, s);
+        }
+        {
+            PScope ps(h, PK_GMRES, (double)n, 16.0 * n);
+            launch_gm_scale(n, V, V, st, 0, s);
+        }
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            double* vj = V + (int64_t)j * n;
+            double* zj = Zp + (int64_t)j * n;
+            double* vn = V + (int64_t)(j + 1) * n;
+            double* Hc = H + (int64_t)j * (GM_MAXR + 1);
+            const int kk = j + 1;
+            apply_form(h, form, vj, zj);
+            {
+                PScope ps(h, PK_SPMV, 2.0 * h->nnz, 12.0 * h->nnz + 8.0 * (n + 1) + 16.0 * n);
+                launch_spmv(n, h->rowptr, h->col, h->val, zj, h->d_gm_wA, h->spmv_group, s);
+            }
+            // CGS2: h1 = V^T w; w1 = w - V h1, h2 = V^T w1; w2 = w1 - V h2, ||w2||
+            {
+                PScope ps(h, PK_GMRES, 2.0 * kk * n, 8.0 * (kk + 1) * n);
+                launch_gm_ortho(n, V, n, kk, nullptr, h->d_gm_wA, nullptr, part, 0, s);
+            }
+            {
+                PScope ps(h, PK_GMRES);
+                launch_gm_finalize(part, kk, hcol, Hc, 0, s);
+            }
+            {
+                PScope ps(h, PK_GMRES, 4.0 * kk * n, 8.0 * (kk + 2) * n);
+                launch_gm_ortho(n, V, n, kk, hcol, h->d_gm_wA, h->d_gm_wB, part, 1, s);
+            }
+            {
+                PScope ps(h, PK_GMRES);
+                launch_gm_finalize(part, kk, hcol, Hc, 1, s);
+            }
+            {
+                PScope ps(h, PK_GMRES, (2.0 * kk + 2.0) * n, 8.0 * (kk + 2) * n);
+                launch_gm_ortho(n, V, n, kk, hcol, h->d_gm_wB, vn, part, 2, s);
+            }
+            {
+                PScope ps(h, PK_GMRES);
+                launch_gm_givens(part, st, j, rtol, s);
+            }
+            {
+                PScope ps(h, PK_GMRES, (double)n, 16.0 * n);
+                launch_gm_scale(n, vn, vn, st, 1, s);
+            }
+            ++out.its;
+            k = kk;
+            ck(cudaMemcpyAsync(&tail, tail_src, sizeof(GmTail), cudaMemcpyDeviceToHost, s));
+            ck(cudaStreamSynchronize(s));
+            out.res = tail.res;
+            if (tail.conv) out.conv = true;
+            if (out.conv || out.its >= maxit) break;
+        }
+        {
+            PScope ps(h, PK_GMRES);
+            launch_gm_trisolve(st, k, s);
+        }
+        {
+            PScope ps(h, PK_GMRES, 2.0 * k * n, 8.0 * (k + 2) * n);
+            launch_gm_combine(n, Zp, n, k, st, x, s);
+        }
+        if (out.conv) break;
+    }
+    return out;
+}
+
+// Inexact coarse solve of the multilevel form: GMRES on E e = c (the next
+// level's operator) from e = 0, preconditioned by the next level's deflated
+// form.
+void inner_coarse_solve(amdd_handle* h) {
+    ck(cudaMemsetAsync(h->d_e, 0, h->nC * sizeof(double), h->s));
+    const GmResult g = gmres_run(h->next, AMDD_FORM_DEFLATED, h->d_c, h->d_e, h->in_restart, h->in_rtol, h->in_maxit);
+    h->in_calls += 1;
+    h->in_its += g.its;
+    h->in_max = std::max(h->in_max, g.its);
+}
+
 amdd_status guard_exc() {
     try {
         throw;
@@ -2562,8 +2964,7 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
     if (opts) {
         o = *opts;
         if (!(o.eps > 0.0) || o.max_sweeps < 1 || o.precision < 0 || o.precision > 2) return AMDD_ERR_INVALID;
-        for (int k = 0; k < 2; ++k)
-            if (o.reserved[k] != 0) return AMDD_ERR_INVALID;
+        if (o.reserved != 0 || o.keep_coarse_matrix < 0 || o.keep_coarse_matrix > 1) return AMDD_ERR_INVALID;
         if (o.profile_classes >> PK_COUNT) return AMDD_ERR_INVALID;
         if (o.eig_solver < 0 || o.eig_solver > 2) return AMDD_ERR_INVALID;
         if (o.eig_solver == 2 &&
@@ -2590,6 +2991,7 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         h->precision = o.precision;
         h->eig_solver = o.eig_solver;
         h->keep_prop = o.keep_proposal_data != 0;
+        h->keep_E = o.keep_coarse_matrix;
         if (o.eig_solver == 2) {
             h->prop = *o.proposal;
             h->have_prop = true;
@@ -2978,6 +3380,114 @@ amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t n
     return result;
 }
 
+amdd_status amdd_apply_form(amdd_handle* h, int32_t form, const double* r, double* z, int32_t nrhs) {
+    if (!h || !r || !z || nrhs < 0 || r == z || form < AMDD_FORM_ADDITIVE || form > AMDD_FORM_ASM)
+        return AMDD_ERR_INVALID;
+    if (form == AMDD_FORM_ADDITIVE) return amdd_apply(h, r, z, nrhs);
+    try {
+        for (int k = 0; k < nrhs; ++k) apply_form(h, form, r + (size_t)k * h->n, z + (size_t)k * h->n);
+        ck(cudaGetLastError());
+        ck(cudaStreamSynchronize(h->s));
+    } catch (...) {
+        return guard_exc();
+    }
+    return AMDD_OK;
+}
+
+amdd_status amdd_gmres_solve(amdd_handle* h, int32_t form, const double* b, double* x, int32_t nrhs,
+                             int32_t restart, double rtol, int32_t maxit, amdd_stats* stats) {
+    if (!h || !b || !x || nrhs < 0 || !(rtol >= 0.0) || maxit < 0 || restart < 1 || restart > AMDD_GMRES_MAX_RESTART ||
+        form < AMDD_FORM_ADDITIVE || form > AMDD_FORM_ASM)
+        return AMDD_ERR_INVALID;
+    const auto t0 = std::chrono::steady_clock::now();
+    amdd_status result = AMDD_OK;
+    try {
+        cudaStream_t s = h->s;
+        const int64_t n = h->n;
+        for (int k = 0; k < nrhs; ++k) {
+            const double* bk = b + (size_t)k * n;
+            double* xk = x + (size_t)k * n;
+            const GmResult g = gmres_run(h, form, bk, xk, restart, rtol, maxit);
+            if (!g.conv) result = AMDD_ERR_NOCONV;
+            if (k == 0 && stats) {
+                // true residual b - A x
+                launch_spmv_resid(n, h->rowptr, h->col, h->val, xk, bk, h->d_gm_wA, h->spmv_group, s);
+                launch_dot_partials(n, h->d_gm_wA, h->d_gm_wA, h->d_gm_part, s);
+                launch_gm_norm(h->d_gm_part, h->d_gm_st, 0, s);
+                double rr = 0.0;
+                ck(cudaMemcpyAsync(&rr, reinterpret_cast<const char*>(h->d_gm_st) + offsetof(GmState, bnorm2),
+                                   sizeof(double), cudaMemcpyDeviceToHost, s));
+                ck(cudaStreamSynchronize(s));
+                stats->iterations = g.its;
+                stats->converged = g.conv ? 1 : 0;
+                stats->rel_residual = g.bnorm2 > 0.0 ? g.res : 0.0;
+                stats->true_rel_residual = g.bnorm2 > 0.0 ? std::sqrt(rr / g.bnorm2) : 0.0;
+                stats->ritz_min = stats->ritz_max = stats->cond_est = std::numeric_limits<double>::quiet_NaN();
+            }
+        }
+        ck(cudaGetLastError());
+        ck(cudaStreamSynchronize(s));
+        const int e = read_err(h);
+        if (e) throw Fail{err_status(e)};
+    } catch (...) {
+        return guard_exc();
+    }
+    if (stats)
+        stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return result;
+}
+
+amdd_status amdd_setup_next_level(amdd_handle* h, const int32_t* groups, int32_t N2, int32_t overlap2,
+                                  double tau2, const amdd_opts* opts2, int32_t inner_restart, double inner_rtol,
+                                  int32_t inner_maxit) {
+    if (!h || !groups || !h->d_E_val || h->nC < 1 || N2 < 1 || inner_restart < 1 ||
+        inner_restart > AMDD_GMRES_MAX_RESTART || !(inner_rtol >= 0.0) || inner_maxit < 1)
+        return AMDD_ERR_INVALID;
+    std::vector<int32_t> part2(h->nC);
+    std::vector<int64_t> cnt(N2, 0);
+    for (int i = 0; i < h->N; ++i) {
+        if (groups[i] < 0 || groups[i] >= N2) return AMDD_ERR_INVALID;
+        for (int k = 0; k < h->p[i]; ++k) part2[h->coff[i] + k] = groups[i];
+        cnt[groups[i]] += h->p[i];
+    }
+    for (int g = 0; g < N2; ++g)
+        if (cnt[g] == 0) return AMDD_ERR_INVALID;
+    amdd_handle* h2 = nullptr;
+    int32_t* d_part2 = nullptr;
+    try {
+        ck(cudaMallocAsync(reinterpret_cast<void**>(&d_part2), h->nC * sizeof(int32_t), h->s));
+        ck(cudaMemcpyAsync(d_part2, part2.data(), h->nC * sizeof(int32_t), cudaMemcpyHostToDevice, h->s));
+        ck(cudaStreamSynchronize(h->s));
+    } catch (...) {
+        if (d_part2) cudaFreeAsync(d_part2, h->s);
+        return guard_exc();
+    }
+    const amdd_csr E{h->nC, h->E_nnz, h->d_E_rowptr, h->d_E_col, h->d_E_val};
+    const amdd_status st = amdd_setup(&E, d_part2, N2, overlap2, tau2, opts2, h->s, &h2);
+    cudaFreeAsync(d_part2, h->s);
+    cudaStreamSynchronize(h->s);
+    if (st != AMDD_OK) return st;
+    amdd_destroy(h->next);
+    h->next = h2;
+    h->in_restart = inner_restart;
+    h->in_rtol = inner_rtol;
+    h->in_maxit = inner_maxit;
+    h->in_calls = h->in_its = 0;
+    h->in_max = 0;
+    // the next level holds its own copy of E
+    for (void* p : {static_cast<void*>(h->d_E_rowptr), static_cast<void*>(h->d_E_col), static_cast<void*>(h->d_E_val)}) {
+        cudaFreeAsync(p, h->s);
+        h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
+    }
+    h->d_E_rowptr = nullptr;
+    h->d_E_col = nullptr;
+    h->d_E_val = nullptr;
+    cudaStreamSynchronize(h->s);
+    return AMDD_OK;
+}
+
+amdd_handle* amdd_next_level(const amdd_handle* h) { return h ? h->next : nullptr; }
+
 amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
     if (!h || !info) return AMDD_ERR_INVALID;
     std::memset(info, 0, sizeof(*info));
@@ -3004,6 +3514,12 @@ amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
     info->lobpcg_fallbacks = h->lob_fallbacks;
     info->lobpcg_iters_max = h->lob_max;
     info->lobpcg_iters_total = h->lob_total;
+    info->robust_schur = h->n_robust;
+    info->levels = 1;
+    for (const amdd_handle* q = h->next; q; q = q->next) info->levels += 1;
+    info->inner_iterations_max = h->in_max;
+    info->inner_solves = h->in_calls;
+    info->inner_iterations = h->in_its;
     return AMDD_OK;
 }
 
@@ -3081,6 +3597,7 @@ amdd_status amdd_reset_profile(amdd_handle* h) {
 
 void amdd_destroy(amdd_handle* h) {
     if (!h) return;
+    amdd_destroy(h->next);
     if (h->s2) cudaStreamSynchronize(h->s2);
     cudaStreamSynchronize(h->s);
     if (h->ev_panel) cudaEventDestroy(h->ev_panel);

@@ -57,6 +57,8 @@ struct CholDescT {
     int stop;        // factor columns [0, stop); stop < n leaves the Schur complement
     const T* clamp;  // per-matrix pivot floor (pivots below are raised to it); NULL = SPD check
     T* Linv;         // ceil(stop/NB) * NB*NB entries: inverses of the diagonal blocks
+    int* bad = nullptr;  // with clamp: set to 1 when a computed pivot falls below 0.9 x the floor
+                         // (or is not finite): the matrix is not numerically definite at that floor
 };
 using CholDesc = CholDescT<double>;
 
@@ -150,6 +152,24 @@ void launch_to_f32_with_identity(const CvtDesc* d, int nmat, int maxrows, cudaSt
 void launch_extract_q(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s);
 // sigma[j] = ||row j|| over ncols_dot (as double); delta[mat] = eps * max_j sigma[j];
 // optionally scale row j by 1/sqrt(sigma[j]).
+// Robust Schur complement of the splitting (fallback when the clamped
+// Cholesky of its [G, D] block is flagged): rows of C = Sigma^{1/2} V^T
+// (n_i x nt, columns [C_R | C_I], C_R the first nR) give
+//   J = [C_R | I_{n_i}]  (n_i x (nR + n_i), leading dimension ldj), and after
+//   the one-sided Jacobi of J's rows (inner products over the first nR
+//   columns) each row k of its right part is scaled by 1 / sqrt(s_k^2 + delta)
+//   with s_k^2 the squared norm of its left part.
+template <typename T>
+struct KjacDesc {
+    const T* C;  // n_i x nt (ldc)
+    T* J;        // n_i x (nR + n_i) (ldj)
+    int ni, nR, ldc, ldj;
+    const T* delta;
+};
+template <typename T>
+void launch_build_kjac(const KjacDesc<T>* d, int nmat, int maxrows, cudaStream_t s);
+template <typename T>
+void launch_kjac_scale(const KjacDesc<T>* d, int nmat, cudaStream_t s);
 template <typename T>
 void launch_rownorms(const JacobiDescT<T>* d, int nmat, double* const* sigma_ptrs, T* delta, double eps,
                      int scale_rows, cudaStream_t s);
@@ -343,5 +363,41 @@ void launch_pcg_update_xr(int64_t n, double* x, double* r, const double* p, cons
 void launch_pcg_update_p(int64_t n, double* p, const double* z, const PcgScal* sc, cudaStream_t s, int nb = 1,
                          int64_t ld = 0, int skip_done = 0);
 void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Deflated / restricted additive Schwarz forms and GMRES(m) (Sec. 4.1)
+// ---------------------------------------------------------------------------
+// z[order_g[t]] = yloc[own_idx[t]] (+ zc[t] when zc is given)
+template <typename TY>
+void launch_ras_prolong(int64_t n, const int32_t* order_g, const int32_t* own_idx, const TY* yloc, const double* zc,
+                        double* z, cudaStream_t s);
+// zg[order_g[t]] = zo[t]
+void launch_owner_to_global(int64_t n, const int32_t* order_g, const double* zo, double* zg, cudaStream_t s);
+// out[t] = val[src[t]] (64-bit indices)
+void launch_gather_idx64(const int64_t* src, int64_t cnt, const double* val, double* out, cudaStream_t s);
+// y = b - A x
+void launch_spmv_resid(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
+                       const double* b, double* y, int group, cudaStream_t s);
+
+constexpr int GM_MAXR = 64;   // largest GMRES restart length
+constexpr int GM_CHUNK = 32;  // basis vectors per block row of the fused Gram-Schmidt passes
+struct GmState {
+    double H[GM_MAXR * (GM_MAXR + 1)];  // Hessenberg matrix, column-major (column j: rows 0..j+1), rotated
+    double cs[GM_MAXR], sn[GM_MAXR];    // Givens rotations
+    double g[GM_MAXR + 1];              // rotated right-hand side beta e_1
+    double y[GM_MAXR];                  // least-squares solution of a cycle
+    double hcol[GM_MAXR + 1];           // projections of the current Gram-Schmidt pass
+    double bnorm2, beta, hnext, res;    // ||b||^2, ||r_0|| of the cycle, h_{j+1,j}, |g_{j+1}| / ||b||
+    int conv;
+};
+void launch_gm_ortho(int64_t n, const double* V, int64_t ldv, int k, const double* h, const double* w, double* out,
+                     double* part, int mode, cudaStream_t s);
+void launch_gm_finalize(const double* part, int k, double* hcol, double* Hcol, int add, cudaStream_t s);
+void launch_gm_norm(const double* part, GmState* st, int which, cudaStream_t s);
+void launch_gm_givens(const double* part, GmState* st, int j, double rtol, cudaStream_t s);
+void launch_gm_scale(int64_t n, const double* src, double* dst, const GmState* st, int which, cudaStream_t s);
+void launch_gm_trisolve(GmState* st, int k, cudaStream_t s);
+void launch_gm_combine(int64_t n, const double* Zp, int64_t ldv, int k, const GmState* st, double* x,
+                       cudaStream_t s);
 
 }  // namespace amdd

@@ -9,6 +9,8 @@
 
 #include "amdd_internal.h"
 
+#include <limits>
+
 namespace cg = cooperative_groups;
 
 namespace amdd {
@@ -156,6 +158,9 @@ __global__ void __launch_bounds__(DIAG_THREADS) chol_diag_kernel(const CholDescT
     auto take_pivot = [&](int j, T a) {
         T p = a;
         if (d.clamp) {
+            // exact pivots of a matrix >= floor * I are >= floor: one well below
+            // it means rounding has destroyed the definiteness
+            if (d.bad && !(p >= T(0.9) * floor_v && isfinite(p))) *d.bad = 1;
             if (!(p >= floor_v)) p = floor_v;
         } else if (!(p > T(0))) {
             atomicOr(err, DERR_NOT_SPD);
@@ -503,6 +508,7 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     const int hbe = hb + (hb & 1);
+    const T absf = d.absfloor ? *d.absfloor : T(0);
     unsigned long long my_rots = 0;
     int sweep = 0;
     bool done = false;
@@ -564,7 +570,7 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
                     jflag[k] = 0;
                     if (pair_of(k, sa, sb)) {
                         const T g = jg[k], a = nrm[sa], b = nrm[sb];
-                        if (g != T(0) && g * g > tol * tol * a * b) {
+                        if (g != T(0) && g * g > tol * tol * a * b && fabs(g) > absf) {
                             T cs, sn, t;
                             jac_rotation(a, b, g, cs, sn, t);
                             jcs[k] = cs;
@@ -785,6 +791,49 @@ template void launch_rownorms<float>(const JacobiDescT<float>*, int, double* con
                                      cudaStream_t);
 template void launch_rownorms<double>(const JacobiDescT<double>*, int, double* const*, double*, double, int,
                                       cudaStream_t);
+
+template <typename T>
+__global__ void __launch_bounds__(256) build_kjac_kernel(const KjacDesc<T>* __restrict__ descs) {
+    const KjacDesc<T> d = descs[blockIdx.y];
+    const int r = blockIdx.x;
+    if (r >= d.ni) return;
+    const T* c = d.C + (size_t)r * d.ldc;
+    T* j = d.J + (size_t)r * d.ldj;
+    for (int k = threadIdx.x; k < d.nR + d.ni; k += blockDim.x)
+        j[k] = k < d.nR ? c[k] : (k - d.nR == r ? T(1) : T(0));
+}
+
+template <typename T>
+void launch_build_kjac(const KjacDesc<T>* d, int nmat, int maxrows, cudaStream_t s) {
+    if (nmat > 0 && maxrows > 0) build_kjac_kernel<T><<<dim3(maxrows, nmat), 256, 0, s>>>(d);
+}
+template void launch_build_kjac<float>(const KjacDesc<float>*, int, int, cudaStream_t);
+template void launch_build_kjac<double>(const KjacDesc<double>*, int, int, cudaStream_t);
+
+// one warp per row: s^2 over the first nR entries, then the right part
+// scaled by 1 / sqrt(s^2 + delta)
+template <typename T>
+__global__ void __launch_bounds__(256) kjac_scale_kernel(const KjacDesc<T>* __restrict__ descs) {
+    const KjacDesc<T> d = descs[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T dl = *d.delta;
+    for (int r = warp; r < d.ni; r += 8) {
+        T* row = d.J + (size_t)r * d.ldj;
+        T s2 = T(0);
+        for (int k = lane; k < d.nR; k += 32) s2 = fma(row[k], row[k], s2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        const T f = T(1) / sqrt(s2 + dl);
+        for (int k = d.nR + lane; k < d.nR + d.ni; k += 32) row[k] *= f;
+    }
+}
+
+template <typename T>
+void launch_kjac_scale(const KjacDesc<T>* d, int nmat, cudaStream_t s) {
+    if (nmat > 0) kjac_scale_kernel<T><<<nmat, 256, 0, s>>>(d);
+}
+template void launch_kjac_scale<float>(const KjacDesc<float>*, int, cudaStream_t);
+template void launch_kjac_scale<double>(const KjacDesc<double>*, int, cudaStream_t);
 
 template <typename T>
 __global__ void add_diag_kernel(T* const* __restrict__ mats, const int* __restrict__ n, const int* __restrict__ ld,
@@ -1226,6 +1275,7 @@ template void launch_gemv_rows<double>(const GemvDescT<double>*, const int*, con
 // stays in L1.  Per row: lane-strided partial sums (two interleaved
 // accumulators) and a fixed shuffle tree.
 constexpr int GEMV_RW = GEMV_ROWS_PER_WARP;
+constexpr int GEMV_U = 4;  // column chunks per iteration (the final sum below is written for 4)
 
 template <typename T>
 __global__ void __launch_bounds__(256) gemv_rows4_kernel(const GemvDescT<T>* __restrict__ descs,
@@ -1251,28 +1301,36 @@ __global__ void __launch_bounds__(256) gemv_rows4_kernel(const GemvDescT<T>* __r
         }
     }
     const T* M0 = d.M + (size_t)r0 * d.ld;
-    T s[GEMV_RW], t[GEMV_RW];
+    // GEMV_U interleaved column chunks of 32: GEMV_RW x GEMV_U independent
+    // loads in flight per lane
+    T s[GEMV_RW][GEMV_U];
 #pragma unroll
-    for (int k = 0; k < GEMV_RW; ++k) s[k] = t[k] = T(0);
+    for (int k = 0; k < GEMV_RW; ++k)
+#pragma unroll
+        for (int u = 0; u < GEMV_U; ++u) s[k][u] = T(0);
     int c = cmin + lane;
-    for (; c + 32 < cmax; c += 64) {
-        const T x0 = d.x[c], x1 = d.x[c + 32];
+    for (; c + 32 * (GEMV_U - 1) < cmax; c += 32 * GEMV_U) {
+        T xv[GEMV_U];
 #pragma unroll
-        for (int k = 0; k < GEMV_RW; ++k) {
-            if (c >= lo[k] && c < hi[k]) s[k] = fma(M0[(size_t)k * d.ld + c], x0, s[k]);
-            if (c + 32 >= lo[k] && c + 32 < hi[k]) t[k] = fma(M0[(size_t)k * d.ld + c + 32], x1, t[k]);
-        }
+        for (int u = 0; u < GEMV_U; ++u) xv[u] = d.x[c + 32 * u];
+#pragma unroll
+        for (int k = 0; k < GEMV_RW; ++k)
+#pragma unroll
+            for (int u = 0; u < GEMV_U; ++u) {
+                const int cu = c + 32 * u;
+                if (cu >= lo[k] && cu < hi[k]) s[k][u] = fma(__ldcs(M0 + (size_t)k * d.ld + cu), xv[u], s[k][u]);
+            }
     }
-    if (c < cmax) {
+    for (; c < cmax; c += 32) {
         const T x0 = d.x[c];
 #pragma unroll
         for (int k = 0; k < GEMV_RW; ++k)
-            if (c >= lo[k] && c < hi[k]) s[k] = fma(M0[(size_t)k * d.ld + c], x0, s[k]);
+            if (c >= lo[k] && c < hi[k]) s[k][0] = fma(__ldcs(M0 + (size_t)k * d.ld + c), x0, s[k][0]);
     }
     T mine = T(0);
 #pragma unroll
     for (int k = 0; k < GEMV_RW; ++k) {
-        T v = s[k] + t[k];
+        T v = (s[k][0] + s[k][1]) + (s[k][2] + s[k][3]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == k) mine = v;

@@ -52,6 +52,13 @@ class Preconditioner:
               allow_noconv: bool = False):
         return _a.pcg_solve(self.h, b.data_ptr(), x.data_ptr(), nrhs, rtol, maxit, allow_noconv)
 
+    def apply_form(self, form: int, r: torch.Tensor, z: torch.Tensor, nrhs: int = 1):
+        _a.apply_form(self.h, form, r.data_ptr(), z.data_ptr(), nrhs)
+
+    def gmres(self, b: torch.Tensor, x: torch.Tensor, form: int = _a.FORM_DEFLATED, nrhs: int = 1, restart: int = 30,
+              rtol: float = 1e-8, maxit: int = 1000, allow_noconv: bool = False):
+        return _a.gmres_solve(self.h, form, b.data_ptr(), x.data_ptr(), nrhs, restart, rtol, maxit, allow_noconv)
+
     def info(self):
         return _a.get_info(self.h)
 

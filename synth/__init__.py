@@ -78,6 +78,15 @@ def box_partition_2d(m: int, box: int) -> np.ndarray:
     return ((ys // box) * nb + xs // box).ravel().astype(np.int32)
 
 
+def box_groups_2d(nb: int, g: int) -> np.ndarray:
+    """Groups of g x g neighbouring boxes of an nb x nb row-major box
+    partition (second-level subdomains of the multilevel form): box
+    i = by * nb + bx goes to group (by // g) * ceil(nb / g) + bx // g."""
+    ng = -(-nb // g)
+    by, bx = np.divmod(np.arange(nb * nb), nb)
+    return ((by // g) * ng + bx // g).astype(np.int32)
+
+
 def _gaussian_field(shape, corr: float, rng) -> np.ndarray:
     """Unit-variance Gaussian random field: white noise convolved with a
     separable Gaussian kernel of correlation length `corr` (truncated at
