@@ -368,12 +368,13 @@ amdd_status amdd_get_singular_values(const amdd_handle* h, int32_t i, double* si
                                      int32_t* count);
 
 /* The coarse block of subdomain i restricted to Omega_Ii (D_i Z_i on its
- * support) as a host row-major p x nI array: p A_II-orthonormal rows spanning
- * the selected eigenvectors of eq. (Zi), entries in ascending global order of
- * Omega_Ii.  When the selection is partial the rows are the eigenvectors, by
- * descending lambda; when every eigenvalue is selected the span is all of
- * R^nI and the rows are those of L_A^{-1} (A_II = L_A L_A^T).  Needs
- * cap >= p*nI. */
+ * support) as a host row-major p x nI array: p rows spanning the selected
+ * eigenvectors of eq. (Zi), entries in ascending global order of Omega_Ii.
+ * When the selection is partial the rows are the eigenvectors, A_II-
+ * orthonormal, by descending lambda; when every eigenvalue is selected the span is all of
+ * R^nI and the rows are those of diag(A_II)^{-1/2} (so E keeps the sparsity
+ * of A there), or, on a handle set up with keep_coarse_matrix = 1, those of
+ * L_A^{-1} (A_II = L_A L_A^T; A_II-orthonormal).  Needs cap >= p*nI. */
 amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, int64_t cap,
                                   int32_t* p, int32_t* nI);
 

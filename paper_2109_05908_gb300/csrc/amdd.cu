@@ -181,6 +181,7 @@ struct amdd_handle {
     // rows, 2 LOBPCG from the learned proposal
     int eig_solver = 0, keep_prop = 0;
     int n_robust = 0;  // subdomains whose Schur complement took the robust form (step 5b)
+    bool diag_basis = true;  // full selections use the basis diag(A_II)^{-1/2}
     amdd_proposal prop{};
     bool have_prop = false;
     std::vector<int> eig_iters;  // per subdomain: LOBPCG iterations, -1 dense path, -2 not partial
@@ -1940,11 +1941,18 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         ZtT = h->d_Zt;
     else
         ZtT = C.tnew<T>(h->sum_zt);
+    // full selections: the basis diag(A_II)^{-1/2} keeps every block of E that
+    // touches such a subdomain as sparse as A (its envelope-aware Cholesky and
+    // the coarse solve then skip most tiles); with a kept E (multilevel form)
+    // the A_II-orthonormal rows of L_A^{-1}, so that E is a block-orthogonal
+    // congruence of the one any other A_II-orthonormal basis gives
+    const bool diag_basis = !h->keep_E;
+    h->diag_basis = diag_basis;
     if (h->nC > 0) {
         std::vector<int64_t> ysrc, ydst;
         std::vector<int32_t> ylen;
         for (int i = 0; i < N; ++i) {
-            if (h->p[i] != h->nI[i] || h->p[i] == 0) continue;
+            if (h->p[i] != h->nI[i] || h->p[i] == 0 || diag_basis) continue;
             for (int k = 0; k < h->nI[i]; ++k) {
                 ysrc.push_back(h->off_sq[i] + (int64_t)k * h->ni[i]);
                 ydst.push_back(h->off_zt[i] + (int64_t)k * h->nI[i]);
@@ -2035,6 +2043,20 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         }
         // the coarse part is FP64: Z_i rounded to FP64 once, used for E and the apply
         if constexpr (!f64) launch_convert<float, double>(ZtT, h->d_Zt, h->sum_zt, s);
+        if (diag_basis) {
+            std::vector<DiagBasisDesc> db;
+            int maxn = 1;
+            for (int i = 0; i < N; ++i)
+                if (h->p[i] == h->nI[i] && h->p[i] > 0) {
+                    db.push_back({Araw + h->off_sq[i], h->ni[i], h->d_Zt + h->off_zt[i], h->nI[i]});
+                    maxn = std::max(maxn, h->nI[i]);
+                }
+            if (!db.empty()) {
+                auto d = C.up(db);
+                PScope ps(h, PK_SMALL);
+                launch_diag_basis(d, (int)db.size(), maxn, s);
+            }
+        }
     }
 
     // ---- (9) coarse matrix E = R_0 A R_0^T (Eq. (two_level_schwarz)), its
@@ -2171,11 +2193,38 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             for (int j = lowj[i]; j <= i; ++j) highi[j] = std::max(highi[j], i);
         h->env_row.assign(nC, 0);
         h->env_colend.assign(nC, 0);
-        for (int i = 0; i < N; ++i)
+        for (int i = 0; i < N; ++i) {
+            const bool full_diag = diag_basis && h->p[i] == h->nI[i];
             for (int k = 0; k < h->p[i]; ++k) {
-                h->env_row[h->coff[i] + k] = (int)h->coff[lowj[i]];
-                h->env_colend[h->coff[i] + k] = (int)h->coff[highi[i] + 1];
+                const int64_t r = h->coff[i] + k;
+                int64_t first = h->coff[lowj[i]];
+                if (full_diag) {
+                    // Z_i diagonal: row r of E is A's row of g scaled, so its
+                    // first column is that of g's coarsest-numbered neighbour
+                    const int32_t g = Il[i][k];
+                    first = r;
+                    for (int64_t q = rp[g]; q < rp[g + 1]; ++q) {
+                        const int32_t g2 = ci[q];
+                        const int j = part[g2];
+                        if (h->p[j] == 0) continue;
+                        const int64_t c = (h->p[j] == h->nI[j]) ? h->coff[j] + posI[g2] : h->coff[j];
+                        first = std::min(first, c);
+                    }
+                }
+                h->env_row[r] = (int)first;
             }
+        }
+        // the factor fills each row's envelope: column c of L_E reaches every
+        // row whose envelope starts at or before c
+        {
+            std::vector<int> mark(nC, 0);
+            for (int64_t r = 0; r < nC; ++r) mark[h->env_row[r]] = std::max(mark[h->env_row[r]], (int)r + 1);
+            int run = 0;
+            for (int64_t c = 0; c < nC; ++c) {
+                run = std::max(run, mark[c]);
+                h->env_colend[c] = std::max(run, (int)c + 1);
+            }
+        }
         h->d_YEt = dnew<double>(h, (size_t)nC * nC);
         chol_batched<double>(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}}, {&h->env_row});
         // Inverses of the diagonal blocks of L_E (block size cSB): the coarse

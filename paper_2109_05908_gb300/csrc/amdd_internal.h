@@ -166,6 +166,16 @@ struct KjacDesc {
     int ni, nR, ldc, ldj;
     const T* delta;
 };
+// Coarse block of a subdomain whose every eigenvalue is selected: the nI x nI
+// rows Zt[k][c] = (k == c) / sqrt(A_II[k][k]) (A_ii dense FP64, leading
+// dimension lda).
+struct DiagBasisDesc {
+    const double* A;
+    int lda;
+    double* Zt;
+    int nI;
+};
+void launch_diag_basis(const DiagBasisDesc* d, int nmat, int maxn, cudaStream_t s);
 template <typename T>
 void launch_build_kjac(const KjacDesc<T>* d, int nmat, int maxrows, cudaStream_t s);
 template <typename T>

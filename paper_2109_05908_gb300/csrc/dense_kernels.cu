@@ -792,6 +792,19 @@ template void launch_rownorms<float>(const JacobiDescT<float>*, int, double* con
 template void launch_rownorms<double>(const JacobiDescT<double>*, int, double* const*, double*, double, int,
                                       cudaStream_t);
 
+__global__ void __launch_bounds__(256) diag_basis_kernel(const DiagBasisDesc* __restrict__ descs) {
+    const DiagBasisDesc d = descs[blockIdx.y];
+    const int k = blockIdx.x;
+    if (k >= d.nI) return;
+    double* row = d.Zt + (size_t)k * d.nI;
+    for (int c = threadIdx.x; c < d.nI; c += blockDim.x)
+        row[c] = (c == k) ? 1.0 / sqrt(d.A[(size_t)k * d.lda + k]) : 0.0;
+}
+
+void launch_diag_basis(const DiagBasisDesc* d, int nmat, int maxn, cudaStream_t s) {
+    if (nmat > 0 && maxn > 0) diag_basis_kernel<<<dim3(maxn, nmat), 256, 0, s>>>(d);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) build_kjac_kernel(const KjacDesc<T>* __restrict__ descs) {
     const KjacDesc<T> d = descs[blockIdx.y];
@@ -1275,7 +1288,6 @@ template void launch_gemv_rows<double>(const GemvDescT<double>*, const int*, con
 // stays in L1.  Per row: lane-strided partial sums (two interleaved
 // accumulators) and a fixed shuffle tree.
 constexpr int GEMV_RW = GEMV_ROWS_PER_WARP;
-constexpr int GEMV_U = 4;  // column chunks per iteration (the final sum below is written for 4)
 
 template <typename T>
 __global__ void __launch_bounds__(256) gemv_rows4_kernel(const GemvDescT<T>* __restrict__ descs,
@@ -1301,36 +1313,28 @@ __global__ void __launch_bounds__(256) gemv_rows4_kernel(const GemvDescT<T>* __r
         }
     }
     const T* M0 = d.M + (size_t)r0 * d.ld;
-    // GEMV_U interleaved column chunks of 32: GEMV_RW x GEMV_U independent
-    // loads in flight per lane
-    T s[GEMV_RW][GEMV_U];
+    T s[GEMV_RW], t[GEMV_RW];
 #pragma unroll
-    for (int k = 0; k < GEMV_RW; ++k)
-#pragma unroll
-        for (int u = 0; u < GEMV_U; ++u) s[k][u] = T(0);
+    for (int k = 0; k < GEMV_RW; ++k) s[k] = t[k] = T(0);
     int c = cmin + lane;
-    for (; c + 32 * (GEMV_U - 1) < cmax; c += 32 * GEMV_U) {
-        T xv[GEMV_U];
+    for (; c + 32 < cmax; c += 64) {
+        const T x0 = d.x[c], x1 = d.x[c + 32];
 #pragma unroll
-        for (int u = 0; u < GEMV_U; ++u) xv[u] = d.x[c + 32 * u];
-#pragma unroll
-        for (int k = 0; k < GEMV_RW; ++k)
-#pragma unroll
-            for (int u = 0; u < GEMV_U; ++u) {
-                const int cu = c + 32 * u;
-                if (cu >= lo[k] && cu < hi[k]) s[k][u] = fma(__ldcs(M0 + (size_t)k * d.ld + cu), xv[u], s[k][u]);
-            }
+        for (int k = 0; k < GEMV_RW; ++k) {
+            if (c >= lo[k] && c < hi[k]) s[k] = fma(M0[(size_t)k * d.ld + c], x0, s[k]);
+            if (c + 32 >= lo[k] && c + 32 < hi[k]) t[k] = fma(M0[(size_t)k * d.ld + c + 32], x1, t[k]);
+        }
     }
-    for (; c < cmax; c += 32) {
+    if (c < cmax) {
         const T x0 = d.x[c];
 #pragma unroll
         for (int k = 0; k < GEMV_RW; ++k)
-            if (c >= lo[k] && c < hi[k]) s[k][0] = fma(__ldcs(M0 + (size_t)k * d.ld + c), x0, s[k][0]);
+            if (c >= lo[k] && c < hi[k]) s[k] = fma(M0[(size_t)k * d.ld + c], x0, s[k]);
     }
     T mine = T(0);
 #pragma unroll
     for (int k = 0; k < GEMV_RW; ++k) {
-        T v = (s[k][0] + s[k][1]) + (s[k][2] + s[k][3]);
+        T v = s[k] + t[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == k) mine = v;

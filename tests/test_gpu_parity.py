@@ -160,11 +160,15 @@ def test_eigenvalues_and_selection(name):
         assert Zt.shape[0] == s.p
         if 0 < s.p < len(s.I):
             assert _span_sine(Zt.T, s.Z[: len(s.I)]) <= max(1e-8, 20 * env["span"][i])
-        if s.p:
-            # A_II-orthonormal columns on Omega_Ii
-            AII = s.Aii[: len(s.I), : len(s.I)]
+        AII = s.Aii[: len(s.I), : len(s.I)]
+        if 0 < s.p < len(s.I):
+            # the selected eigenvectors: A_II-orthonormal rows on Omega_Ii
             G = Zt @ AII @ Zt.T
             assert np.allclose(G, np.eye(s.p), atol=1e-9)
+        elif s.p == len(s.I):
+            # every eigenvalue selected: the span is all of R^nI and the basis
+            # is diag(A_II)^{-1/2}
+            assert np.array_equal(Zt, np.diag(1.0 / np.sqrt(np.diag(AII))))
 
 
 @pytest.mark.parametrize("name", list(CASES))
