@@ -315,7 +315,9 @@ def variants(A, torch, np, dev, sp, w, precision, steps=3):
     def three():
         x3.zero_()
         h = A.setup(dA3.csr, dp3.data_ptr(), N3, 1, tau, o3, sp)
-        h2 = A.setup_next_level(h, groups, int(groups.max()) + 1, 1, 0.5, None, 30, 1e-4, 100)
+        o2 = A.opts_default()
+        o2.precision = precision  # the second level in the same form as the first
+        h2 = A.setup_next_level(h, groups, int(groups.max()) + 1, 1, 0.5, o2, 30, 1e-4, 100)
         st = A.gmres_solve(h, A.FORM_DEFLATED, b3.data_ptr(), x3.data_ptr(), 1, 30, RTOL, 1000)
         info["l1"], info["l2"] = A.get_info(h), A.get_info(h2)
         A.destroy(h)

@@ -176,6 +176,8 @@ struct amdd_handle {
     std::vector<int> env_row;     // first non-zero column of each row of E (and L_E)
     std::vector<int> env_colend;  // one past the last non-zero row of each column of L_E
     int* d_env_row = nullptr;
+    int32_t* d_cperm = nullptr;  // factorisation order of the coarse unknowns (NULL: subdomain order)
+    double *d_cp = nullptr, *d_ep = nullptr;  // coarse vectors in that order (MAXB vectors)
     int* d_env_colend = nullptr;
     // eigenvectors of partial selections: 0 dense Jacobi, 1 LOBPCG from random
     // rows, 2 LOBPCG from the learned proposal
@@ -223,6 +225,7 @@ struct amdd_handle {
     int in_max = 0;
     // GMRES(m) work, allocated on first use for restart length gm_cap
     int gm_cap = 0;
+    int64_t gm_ldv = 0;  // leading dimension of the Krylov vectors
     double *d_gm_V = nullptr, *d_gm_Zp = nullptr, *d_gm_wA = nullptr, *d_gm_wB = nullptr, *d_gm_part = nullptr;
     GmState* d_gm_st = nullptr;
     // PCG work vectors
@@ -566,13 +569,14 @@ void transpose_batched(Ctx& C, const std::vector<const T*>& src, const std::vect
 template <typename T>
 void run_jacobi(amdd_handle* h, const std::vector<JacobiDescT<T>>& jd, const JacobiDescT<T>* djd, int max_sweeps, T tol,
                 int* sweeps, unsigned long long* rots, int report_noconv) {
-    size_t smem = 0;
+    size_t smem8 = 0, smem16 = 0;
     int maxr = 0;
     for (const auto& j : jd) {
-        smem = std::max(smem, jacobi_block_smem<T>(j.rows, j.ncols_rot));
+        smem8 = std::max(smem8, jacobi_block_smem<T>(j.rows, j.ncols_rot, JAC_CLUSTER));
+        smem16 = std::max(smem16, jacobi_block_smem<T>(j.rows, j.ncols_rot, 2 * JAC_CLUSTER));
         maxr = std::max(maxr, j.rows);
     }
-    if (!launch_jacobi_block<T>(djd, (int)jd.size(), smem, maxr, max_sweeps, tol, sweeps, rots, h->d_err,
+    if (!launch_jacobi_block<T>(djd, (int)jd.size(), smem8, smem16, maxr, max_sweeps, tol, sweeps, rots, h->d_err,
                                 report_noconv, h->s))
         launch_jacobi_t<T>(djd, (int)jd.size(), max_sweeps, tol, sweeps, rots, h->d_err, report_noconv, h->s);
 }
@@ -1390,6 +1394,76 @@ std::vector<int> learned_eigvecs(Ctx& C, amdd_handle* h, const std::vector<int>&
 // T: type of the local work (factors of A_ii, T = L_A^{-1} S L_A^{-T}, its
 // eigensolve, Z_i).  TS: type of the splitting (SVD of X_i, Abar_ii and its
 // Schur complement S).
+// Reverse Cuthill-McKee order of a symmetric graph (adjacency lists): per
+// connected component a pseudo-peripheral start (George and Liu: repeated
+// breadth-first searches from a minimum-degree node of the deepest level),
+// then breadth-first numbering with the unnumbered neighbours of each node by
+// increasing degree; the whole sequence reversed.
+std::vector<int32_t> rcm_order(const std::vector<std::vector<int32_t>>& nbr) {
+    const int n = (int)nbr.size();
+    std::vector<int32_t> order;
+    order.reserve(n);
+    std::vector<char> numbered(n, 0);
+    std::vector<int> level(n, -1);
+    auto deg = [&](int v) { return (int)nbr[v].size(); };
+    // levels of the component of root among unnumbered nodes; returns the
+    // depth and leaves the visited nodes in comp (levels reset on exit)
+    std::vector<int32_t> comp, last;
+    auto bfs = [&](int root) {
+        comp.assign(1, root);
+        level[root] = 0;
+        int depth = 0;
+        for (size_t head = 0; head < comp.size(); ++head) {
+            const int v = comp[head];
+            for (int w : nbr[v])
+                if (level[w] < 0 && !numbered[w]) {
+                    level[w] = level[v] + 1;
+                    depth = std::max(depth, level[w]);
+                    comp.push_back(w);
+                }
+        }
+        last.clear();
+        for (int v : comp)
+            if (level[v] == depth) last.push_back(v);
+        for (int v : comp) level[v] = -1;
+        return depth;
+    };
+    for (int s0 = 0; s0 < n; ++s0) {
+        if (numbered[s0]) continue;
+        bfs(s0);
+        int root = s0;
+        for (int v : comp)
+            if (deg(v) < deg(root)) root = v;
+        int depth = bfs(root);
+        for (int it = 0; it < 8; ++it) {
+            int cand = last[0];
+            for (int v : last)
+                if (deg(v) < deg(cand)) cand = v;
+            const int d2 = bfs(cand);
+            if (d2 <= depth) break;
+            root = cand;
+            depth = d2;
+        }
+        const size_t start = order.size();
+        order.push_back(root);
+        numbered[root] = 1;
+        std::vector<int32_t> nb;
+        for (size_t head = start; head < order.size(); ++head) {
+            const int v = order[head];
+            nb.clear();
+            for (int w : nbr[v])
+                if (!numbered[w]) {
+                    numbered[w] = 1;
+                    nb.push_back(w);
+                }
+            std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg(a) < deg(b) || (deg(a) == deg(b) && a < b); });
+            order.insert(order.end(), nb.begin(), nb.end());
+        }
+    }
+    std::reverse(order.begin(), order.end());
+    return order;
+}
+
 template <typename T, typename TS>
 void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     constexpr bool f64 = std::is_same<T, double>::value;
@@ -2181,39 +2255,89 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             PScope ps(h, PK_SMALL, 0.0, 16.0 * h->E_nnz);
             launch_gather_idx64(dsrc, h->E_nnz, E, h->d_E_val, s);
         }
-        double* linvE = C.tnew<double>((size_t)cdiv(nC, CHOL_NB) * CHOL_NB * CHOL_NB);
-        // envelope of E: block row i starts at the first subdomain j <= i coupled
-        // to i.  The factor keeps that row envelope but fills it in, so column c
-        // of L_E reaches every row whose envelope starts at or before c: block
-        // column j ends after the last block row i with lowj[i] <= j.
-        std::vector<int> lowj(N), highi(N);
-        for (int i = 0; i < N; ++i) lowj[i] = highi[i] = i;
-        for (const auto& pr : pairs) lowj[pr.first] = std::min(lowj[pr.first], pr.second);
-        for (int i = 0; i < N; ++i)
-            for (int j = lowj[i]; j <= i; ++j) highi[j] = std::max(highi[j], i);
-        h->env_row.assign(nC, 0);
-        h->env_colend.assign(nC, 0);
+        // ---- sparsity graph of E (coarse unknowns in subdomain order): blocks
+        // of subdomains coupled in A (E_ij = Z_i^T A(Omega_Ii, Omega_Ij) Z_j is
+        // exactly zero otherwise); a diagonal-basis block contributes only the
+        // unknowns whose node touches the other subdomain
+        std::vector<std::vector<int>> adjB(N);
+        for (int64_t g = 0; g < n; ++g)
+            for (int64_t q = rp[g]; q < rp[g + 1]; ++q)
+                if (part[g] != part[ci[q]]) adjB[part[g]].push_back(part[ci[q]]);
         for (int i = 0; i < N; ++i) {
-            const bool full_diag = diag_basis && h->p[i] == h->nI[i];
-            for (int k = 0; k < h->p[i]; ++k) {
-                const int64_t r = h->coff[i] + k;
-                int64_t first = h->coff[lowj[i]];
-                if (full_diag) {
-                    // Z_i diagonal: row r of E is A's row of g scaled, so its
-                    // first column is that of g's coarsest-numbered neighbour
+            adjB[i].push_back(i);
+            std::sort(adjB[i].begin(), adjB[i].end());
+            adjB[i].erase(std::unique(adjB[i].begin(), adjB[i].end()), adjB[i].end());
+        }
+        auto full_diag = [&](int i) { return diag_basis && h->p[i] == h->nI[i] && h->p[i] > 0; };
+        std::vector<std::vector<int32_t>> nbr(nC);
+        for (int i = 0; i < N; ++i) {
+            if (h->p[i] == 0) continue;
+            if (full_diag(i)) {
+                for (int k = 0; k < h->p[i]; ++k) {
                     const int32_t g = Il[i][k];
-                    first = r;
+                    auto& L = nbr[h->coff[i] + k];
                     for (int64_t q = rp[g]; q < rp[g + 1]; ++q) {
                         const int32_t g2 = ci[q];
                         const int j = part[g2];
                         if (h->p[j] == 0) continue;
-                        const int64_t c = (h->p[j] == h->nI[j]) ? h->coff[j] + posI[g2] : h->coff[j];
-                        first = std::min(first, c);
+                        if (full_diag(j))
+                            L.push_back((int32_t)(h->coff[j] + posI[g2]));
+                        else
+                            for (int l = 0; l < h->p[j]; ++l) L.push_back((int32_t)(h->coff[j] + l));
                     }
                 }
-                h->env_row[r] = (int)first;
+            } else {
+                std::vector<int32_t> row;
+                for (int j : adjB[i]) {
+                    if (h->p[j] == 0) continue;
+                    if (!full_diag(j) || j == i) {
+                        for (int l = 0; l < h->p[j]; ++l) row.push_back((int32_t)(h->coff[j] + l));
+                    } else {
+                        for (int l = 0; l < h->nI[j]; ++l) {  // nodes of Omega_Ij touching Omega_Ii
+                            const int32_t g2 = Il[j][l];
+                            for (int64_t q = rp[g2]; q < rp[g2 + 1]; ++q)
+                                if (part[ci[q]] == i) {
+                                    row.push_back((int32_t)(h->coff[j] + l));
+                                    break;
+                                }
+                        }
+                    }
+                }
+                for (int k = 0; k < h->p[i]; ++k) nbr[h->coff[i] + k] = row;
             }
         }
+        for (auto& L : nbr) {
+            std::sort(L.begin(), L.end());
+            L.erase(std::unique(L.begin(), L.end()), L.end());
+        }
+        // ---- ordering of the coarse unknowns for the factorisation: reverse
+        // Cuthill-McKee when it cuts the factorisation work (the sum over rows
+        // of (r - first(r))^2) by a fifth or more, else the subdomain order.
+        // E is permuted on the device; the coarse solves gather and scatter
+        // through the order.
+        auto envelope = [&](const std::vector<int32_t>& iperm, const std::vector<int32_t>& perm,
+                            std::vector<int>& env) {
+            env.assign(nC, 0);
+            double work = 0.0;
+            for (int64_t rn = 0; rn < nC; ++rn) {
+                int first = (int)rn;
+                for (int32_t c : nbr[perm[rn]]) first = std::min(first, (int)iperm[c]);
+                env[rn] = first;
+                work += (double)(rn - first) * (double)(rn - first);
+            }
+            return work;
+        };
+        std::vector<int32_t> idp(nC);
+        std::iota(idp.begin(), idp.end(), 0);
+        std::vector<int> env_id, env_rcm;
+        const double prof_id = envelope(idp, idp, env_id);
+        std::vector<int32_t> rperm = rcm_order(nbr);
+        std::vector<int32_t> riperm(nC);
+        for (int64_t q = 0; q < nC; ++q) riperm[rperm[q]] = (int32_t)q;
+        const double prof_rcm = envelope(riperm, rperm, env_rcm);
+        const bool use_rcm = prof_rcm < 0.8 * prof_id;
+        h->env_row = use_rcm ? env_rcm : env_id;
+        h->env_colend.assign(nC, 0);
         // the factor fills each row's envelope: column c of L_E reaches every
         // row whose envelope starts at or before c
         {
@@ -2225,7 +2349,22 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                 h->env_colend[c] = std::max(run, (int)c + 1);
             }
         }
-        h->d_YEt = dnew<double>(h, (size_t)nC * nC);
+        double* linvE = C.tnew<double>((size_t)cdiv(nC, CHOL_NB) * CHOL_NB * CHOL_NB);
+        if (use_rcm) {
+            // E (lower triangle, subdomain order) -> Ep[r][c] = E[perm r][perm c]
+            // (lower triangle); the two nC x nC buffers swap roles
+            h->d_cperm = C.up(rperm, true);
+            h->d_cp = dnew<double>(h, (size_t)MAXB * nC);
+            h->d_ep = dnew<double>(h, (size_t)MAXB * nC);
+            h->d_YEt = dnew<double>(h, (size_t)nC * nC);
+            {
+                PScope ps(h, PK_SMALL, 0.0, 8.0 * (double)nC * nC);
+                launch_sym_permute(E, h->d_YEt, h->d_cperm, nC, s);
+            }
+            std::swap(h->d_YE, h->d_YEt);
+            E = h->d_YE;
+        }
+        if (!h->d_YEt) h->d_YEt = dnew<double>(h, (size_t)nC * nC);
         chol_batched<double>(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}}, {&h->env_row});
         // Inverses of the diagonal blocks of L_E (block size cSB): the coarse
         // solve is then a blocked forward / backward substitution with L_E and
@@ -2448,10 +2587,24 @@ void coarse_correction(amdd_handle* h) {
     if (h->next) {
         inner_coarse_solve(h);  // multilevel form: e ~ E^{-1} c by GMRES on the next level
     } else {
-        CoarseSolveArgs a{h->d_YE, h->d_YEt, h->d_Yd, h->d_Ydt, h->d_env_row, h->d_env_colend,
-                          h->d_c, h->d_ctmp, h->d_e, (int)h->nC, (int)h->nC, h->cSB, h->cK};
-        PScope ps(h, PK_CSOLVE, h->csolve_flops, h->csolve_bytes);
-        ck(launch_coarse_solve(a, h->coop_blocks, s));
+        double* cin = h->d_c;
+        double* eout = h->d_e;
+        if (h->d_cperm) {  // the factorisation order of the coarse unknowns
+            PScope ps(h, PK_GATHER_SCATTER, 0.0, 20.0 * h->nC);
+            launch_perm_gather(h->nC, h->d_cperm, h->d_c, h->d_cp, 1, h->nC, s);
+            cin = h->d_cp;
+            eout = h->d_ep;
+        }
+        {
+            CoarseSolveArgs a{h->d_YE, h->d_YEt, h->d_Yd, h->d_Ydt, h->d_env_row, h->d_env_colend,
+                              cin, h->d_ctmp, eout, (int)h->nC, (int)h->nC, h->cSB, h->cK};
+            PScope ps(h, PK_CSOLVE, h->csolve_flops, h->csolve_bytes);
+            ck(launch_coarse_solve(a, h->coop_blocks, s));
+        }
+        if (h->d_cperm) {
+            PScope ps(h, PK_GATHER_SCATTER, 0.0, 20.0 * h->nC);
+            launch_perm_scatter(h->nC, h->d_cperm, h->d_ep, h->d_e, 1, h->nC, s);
+        }
     }
     {
         PScope ps(h, PK_GEMV, 2.0 * zt, 8.0 * zt + 8.0 * h->nC + 8.0 * h->n);
@@ -2662,13 +2815,25 @@ void apply_multi(amdd_handle* h, const double* r, double* z, int nb) {
             PScope ps(h, PK_GEMV, 2.0 * zt * nb, 8.0 * zt + (8.0 * L + 16.0 * h->nC) * nb);
             launch_gemv_rows_multi<double>(h->d_m_gv_c, h->d_rd_c, h->d_rl_c, h->nC, nb, L, h->nC, s);
         }
+        double* cin = h->d_m_c;
+        double* eout = h->d_m_e;
+        if (h->d_cperm) {
+            PScope ps(h, PK_GATHER_SCATTER, 0.0, 20.0 * h->nC * nb);
+            launch_perm_gather(h->nC, h->d_cperm, h->d_m_c, h->d_cp, nb, h->nC, s);
+            cin = h->d_cp;
+            eout = h->d_ep;
+        }
         CoarseSolveArgs a{h->d_YE, h->d_YEt, h->d_Yd, h->d_Ydt, h->d_env_row, h->d_env_colend,
-                          h->d_m_c, h->d_m_ctmp, h->d_m_e, (int)h->nC, (int)h->nC, h->cSB, h->cK};
+                          cin, h->d_m_ctmp, eout, (int)h->nC, (int)h->nC, h->cSB, h->cK};
         a.nb = nb;
         a.ldv = h->nC;
         {
             PScope ps(h, PK_CSOLVE, h->csolve_flops * nb, h->csolve_bytes);
             ck(launch_coarse_solve(a, h->coop_blocks, s));
+        }
+        if (h->d_cperm) {
+            PScope ps(h, PK_GATHER_SCATTER, 0.0, 20.0 * h->nC * nb);
+            launch_perm_scatter(h->nC, h->d_cperm, h->d_ep, h->d_m_e, nb, h->nC, s);
         }
         PScope ps(h, PK_GEMV, 2.0 * zt * nb, 8.0 * zt + (8.0 * h->nC + 8.0 * h->n) * nb);
         launch_gemv_rows_multi<double>(h->d_m_gv_zp, h->d_rd_zp, h->d_rl_zp, h->n_zp, nb, h->nC, h->n, s);
@@ -2782,8 +2947,9 @@ void ensure_gmres(amdd_handle* h, int m) {
     drop(h->d_gm_V);
     drop(h->d_gm_Zp);
     const int64_t n = h->n;
-    h->d_gm_V = dnew<double>(h, (int64_t)(m + 1) * n);
-    h->d_gm_Zp = dnew<double>(h, (int64_t)m * n);
+    h->gm_ldv = n + (n & 1);  // even: 16-byte aligned vectors for the paired loads
+    h->d_gm_V = dnew<double>(h, (int64_t)(m + 1) * h->gm_ldv);
+    h->d_gm_Zp = dnew<double>(h, (int64_t)m * h->gm_ldv);
     if (!h->d_gm_st) {
         h->d_gm_wA = dnew<double>(h, n);
         h->d_gm_wB = dnew<double>(h, n);
@@ -2816,6 +2982,7 @@ GmResult gmres_run(amdd_handle* h, int form, const double* b, double* x, int m, 
     cudaStream_t s = h->s;
     const int64_t n = h->n;
     double* V = h->d_gm_V;
+    const int64_t ldv = h->gm_ldv;
     double* Zp = h->d_gm_Zp;
     double* part = h->d_gm_part;
     GmState* st = h->d_gm_st;
@@ -2861,9 +3028,9 @@ GmResult gmres_run(amdd_handle* h, int form, const double* b, double* x, int m, 
         }
         int k = 0;
         for (int j = 0; j < m; ++j) {
-            double* vj = V + (int64_t)j * n;
-            double* zj = Zp + (int64_t)j * n;
-            double* vn = V + (int64_t)(j + 1) * n;
+            double* vj = V + (int64_t)j * ldv;
+            double* zj = Zp + (int64_t)j * ldv;
+            double* vn = V + (int64_t)(j + 1) * ldv;
             double* Hc = H + (int64_t)j * (GM_MAXR + 1);
             const int kk = j + 1;
             apply_form(h, form, vj, zj);
@@ -2874,7 +3041,7 @@ GmResult gmres_run(amdd_handle* h, int form, const double* b, double* x, int m, 
             // CGS2: h1 = V^T w; w1 = w - V h1, h2 = V^T w1; w2 = w1 - V h2, ||w2||
             {
                 PScope ps(h, PK_GMRES, 2.0 * kk * n, 8.0 * (kk + 1) * n);
-                launch_gm_ortho(n, V, n, kk, nullptr, h->d_gm_wA, nullptr, part, 0, s);
+                launch_gm_ortho(n, V, ldv, kk, nullptr, h->d_gm_wA, nullptr, part, 0, s);
             }
             {
                 PScope ps(h, PK_GMRES);
@@ -2882,7 +3049,7 @@ GmResult gmres_run(amdd_handle* h, int form, const double* b, double* x, int m, 
             }
             {
                 PScope ps(h, PK_GMRES, 4.0 * kk * n, 8.0 * (kk + 2) * n);
-                launch_gm_ortho(n, V, n, kk, hcol, h->d_gm_wA, h->d_gm_wB, part, 1, s);
+                launch_gm_ortho(n, V, ldv, kk, hcol, h->d_gm_wA, h->d_gm_wB, part, 1, s);
             }
             {
                 PScope ps(h, PK_GMRES);
@@ -2890,7 +3057,7 @@ GmResult gmres_run(amdd_handle* h, int form, const double* b, double* x, int m, 
             }
             {
                 PScope ps(h, PK_GMRES, (2.0 * kk + 2.0) * n, 8.0 * (kk + 2) * n);
-                launch_gm_ortho(n, V, n, kk, hcol, h->d_gm_wB, vn, part, 2, s);
+                launch_gm_ortho(n, V, ldv, kk, hcol, h->d_gm_wB, vn, part, 2, s);
             }
             {
                 PScope ps(h, PK_GMRES);
@@ -2914,7 +3081,7 @@ GmResult gmres_run(amdd_handle* h, int form, const double* b, double* x, int m, 
         }
         {
             PScope ps(h, PK_GMRES, 2.0 * k * n, 8.0 * (k + 2) * n);
-            launch_gm_combine(n, Zp, n, k, st, x, s);
+            launch_gm_combine(n, Zp, ldv, k, st, x, s);
         }
         if (out.conv) break;
     }

@@ -142,10 +142,14 @@ void launch_jacobi_t(const JacobiDescT<T>* d, int nmat, int max_sweeps, T tol, i
 // the two row blocks of the largest matrix do not fit in shared memory.
 constexpr size_t JAC_BLOCK_SMEM_MAX = 220 * 1024;
 template <typename T>
-size_t jacobi_block_smem(int rows, int ncols_rot);
+size_t jacobi_block_smem(int rows, int ncols_rot, int cluster);
+// Shared-memory-resident block variant with a cluster of JAC_CLUSTER CTAs per
+// matrix, else (blocks too large) 2 * JAC_CLUSTER; returns false, with nothing
+// launched, when neither fits (smem8 / smem16: bytes per CTA for the two sizes).
 template <typename T>
-bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem, int max_rows, int max_sweeps, T tol,
-                         int* sweeps, unsigned long long* rots, int* err, int report_noconv, cudaStream_t s);
+bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem8, size_t smem16, int max_rows,
+                         int max_sweeps, T tol, int* sweeps, unsigned long long* rots, int* err, int report_noconv,
+                         cudaStream_t s);
 template <typename T>
 void launch_row_maxnorm2(const JacobiDescT<T>* d, int nmat, T eps, T* out, cudaStream_t s);
 void launch_to_f32_with_identity(const CvtDesc* d, int nmat, int maxrows, cudaStream_t s);
@@ -383,6 +387,14 @@ void launch_ras_prolong(int64_t n, const int32_t* order_g, const int32_t* own_id
                         double* z, cudaStream_t s);
 // zg[order_g[t]] = zo[t]
 void launch_owner_to_global(int64_t n, const int32_t* order_g, const double* zo, double* zg, cudaStream_t s);
+// Ep[r][c] = E[perm r][perm c] for c <= r (E and Ep lower triangles of n x n
+// row-major matrices; Ep's upper triangle is zeroed)
+void launch_sym_permute(const double* E, double* Ep, const int32_t* perm, int64_t n, cudaStream_t s);
+// dst[k*ld + r] = src[k*ld + perm[r]] / dst[k*ld + perm[r]] = src[k*ld + r], r < n, k < nb
+void launch_perm_gather(int64_t n, const int32_t* perm, const double* src, double* dst, int nb, int64_t ld,
+                        cudaStream_t s);
+void launch_perm_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, int nb, int64_t ld,
+                         cudaStream_t s);
 // out[t] = val[src[t]] (64-bit indices)
 void launch_gather_idx64(const int64_t* src, int64_t cnt, const double* val, double* out, cudaStream_t s);
 // y = b - A x

@@ -488,16 +488,16 @@ template void launch_jacobi_t<double>(const JacobiDescT<double>*, int, int, doub
 // visits every row pair once, with one cluster barrier per block round
 // (2 * JAC_CLUSTER - 1 per sweep).  Row norms^2 are recomputed when a block is
 // loaded and updated exactly after each rotation.
-template <typename T>
-__global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
+template <typename T, int CL>
+__global__ void __launch_bounds__(1024)
     jacobi_block_kernel(const JacobiDescT<T>* __restrict__ descs, int max_sweeps, T tol, int* __restrict__ sweeps,
                         unsigned long long* __restrict__ rots, int* __restrict__ err, int report_noconv) {
     extern __shared__ __align__(16) unsigned char jac_smem[];
     cg::cluster_group cluster = cg::this_cluster();
-    const int mat = blockIdx.x / JAC_CLUSTER;
+    const int mat = blockIdx.x / CL;
     const int crank = (int)cluster.block_rank();
     const JacobiDescT<T> d = descs[mat];
-    constexpr int NBLK = 2 * JAC_CLUSTER;
+    constexpr int NBLK = 2 * CL;
     const int hb = (d.rows + NBLK - 1) / NBLK;
     const int W = d.ncols_rot, D = d.ncols_dot;
     T* blk = reinterpret_cast<T*>(jac_smem);  // [2][hb][W]
@@ -636,7 +636,7 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
         }
         int any = 0;
 #pragma unroll
-        for (int rr = 0; rr < JAC_CLUSTER; ++rr) any |= *cluster.map_shared_rank(&rotated, rr);
+        for (int rr = 0; rr < CL; ++rr) any |= *cluster.map_shared_rank(&rotated, rr);
         cluster.sync();
         if (!any) {
             done = true;
@@ -651,34 +651,69 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(1024)
 }
 
 template <typename T>
-size_t jacobi_block_smem(int rows, int ncols_rot) {
-    const size_t hb = (size_t)(rows + 2 * JAC_CLUSTER - 1) / (2 * JAC_CLUSTER);
+size_t jacobi_block_smem(int rows, int ncols_rot, int cluster) {
+    const size_t hb = (size_t)(rows + 2 * cluster - 1) / (2 * cluster);
     return (2 * hb * (size_t)ncols_rot + 2 * hb) * sizeof(T);
 }
-template size_t jacobi_block_smem<float>(int, int);
-template size_t jacobi_block_smem<double>(int, int);
+template size_t jacobi_block_smem<float>(int, int, int);
+template size_t jacobi_block_smem<double>(int, int, int);
 
-template <typename T>
-bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem, int max_rows, int max_sweeps, T tol,
-                         int* sweeps, unsigned long long* rots, int* err, int report_noconv, cudaStream_t s) {
-    if (nmat <= 0) return true;
+// One launch of the block kernel with a cluster of CL CTAs per matrix
+// (cluster dimension given at launch; CL = 16 is the non-portable size).
+// Returns false, with nothing launched, when the blocks do not fit or the
+// device cannot co-schedule such a cluster.
+template <typename T, int CL>
+bool launch_jacobi_block_cl(const JacobiDescT<T>* d, int nmat, size_t smem, int max_rows, int max_sweeps, T tol,
+                            int* sweeps, unsigned long long* rots, int* err, int report_noconv, cudaStream_t s) {
     if (smem > JAC_BLOCK_SMEM_MAX) return false;
-    if (cudaFuncSetAttribute(jacobi_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
+    const int hb = (max_rows + 2 * CL - 1) / (2 * CL);
+    if (hb + 2 > JAC_MAX_PAIRS) return false;
+    auto kern = jacobi_block_kernel<T, CL>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (CL > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
         cudaGetLastError();
         return false;
     }
     // one warp per pair of a sub-round (hb pairs), 8 to 32 warps
-    const int hb = (max_rows + 2 * JAC_CLUSTER - 1) / (2 * JAC_CLUSTER);
-    if (hb + 2 > JAC_MAX_PAIRS) return false;
     const int warps = hb < 8 ? 8 : (hb > 32 ? 32 : hb);
-    jacobi_block_kernel<T><<<nmat * JAC_CLUSTER, 32 * warps, smem, s>>>(d, max_sweeps, tol, sweeps, rots, err,
-                                                                        report_noconv);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nmat * CL);
+    cfg.blockDim = dim3(32 * warps);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaLaunchKernelEx(&cfg, kern, d, max_sweeps, tol, sweeps, rots, err, report_noconv) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
     return true;
 }
-template bool launch_jacobi_block<float>(const JacobiDescT<float>*, int, size_t, int, int, float, int*,
+
+template <typename T>
+bool launch_jacobi_block(const JacobiDescT<T>* d, int nmat, size_t smem8, size_t smem16, int max_rows,
+                         int max_sweeps, T tol, int* sweeps, unsigned long long* rots, int* err, int report_noconv,
+                         cudaStream_t s) {
+    if (nmat <= 0) return true;
+    if (launch_jacobi_block_cl<T, JAC_CLUSTER>(d, nmat, smem8, max_rows, max_sweeps, tol, sweeps, rots, err,
+                                               report_noconv, s))
+        return true;
+    return launch_jacobi_block_cl<T, 2 * JAC_CLUSTER>(d, nmat, smem16, max_rows, max_sweeps, tol, sweeps, rots, err,
+                                                      report_noconv, s);
+}
+template bool launch_jacobi_block<float>(const JacobiDescT<float>*, int, size_t, size_t, int, int, float, int*,
                                          unsigned long long*, int*, int, cudaStream_t);
-template bool launch_jacobi_block<double>(const JacobiDescT<double>*, int, size_t, int, int, double, int*,
+template bool launch_jacobi_block<double>(const JacobiDescT<double>*, int, size_t, size_t, int, int, double, int*,
                                           unsigned long long*, int*, int, cudaStream_t);
 
 // absfloor[mat] = eps * max_r ||row r||^2 over ncols_dot (one CTA per matrix).
