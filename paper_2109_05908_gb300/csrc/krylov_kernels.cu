@@ -84,6 +84,51 @@ void launch_gather_idx64(const int64_t* src, int64_t cnt, const double* val, dou
     if (cnt > 0) gather_idx64_kernel<<<grid_for(cnt, 152 * 32), 256, 0, s>>>(src, cnt, val, out);
 }
 
+// ------------------------------------------------------------------ coarse ordering
+__global__ void __launch_bounds__(256) sym_permute_kernel(const double* __restrict__ E, double* __restrict__ Ep,
+                                                          const int32_t* __restrict__ perm, int64_t n) {
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const int64_t pr = perm[r];
+        double* out = Ep + r * n;
+        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+            double v = 0.0;
+            if (c <= r) {
+                const int64_t pc = perm[c];
+                v = pr >= pc ? E[pr * n + pc] : E[pc * n + pr];
+            }
+            out[c] = v;
+        }
+    }
+}
+
+void launch_sym_permute(const double* E, double* Ep, const int32_t* perm, int64_t n, cudaStream_t s) {
+    if (n > 0) sym_permute_kernel<<<(unsigned)(n < 152 * 64 ? n : 152 * 64), 256, 0, s>>>(E, Ep, perm, n);
+}
+
+__global__ void __launch_bounds__(256) perm_move_kernel(int64_t n, const int32_t* __restrict__ perm,
+                                                        const double* __restrict__ src, double* __restrict__ dst,
+                                                        int nb, int64_t ld, int scatter) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = perm[r];
+        for (int k = 0; k < nb; ++k) {
+            if (scatter)
+                dst[k * ld + q] = src[k * ld + r];
+            else
+                dst[k * ld + r] = src[k * ld + q];
+        }
+    }
+}
+
+void launch_perm_gather(int64_t n, const int32_t* perm, const double* src, double* dst, int nb, int64_t ld,
+                        cudaStream_t s) {
+    if (n > 0) perm_move_kernel<<<grid_for(n, 152 * 8), 256, 0, s>>>(n, perm, src, dst, nb, ld, 0);
+}
+
+void launch_perm_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, int nb, int64_t ld,
+                         cudaStream_t s) {
+    if (n > 0) perm_move_kernel<<<grid_for(n, 152 * 8), 256, 0, s>>>(n, perm, src, dst, nb, ld, 1);
+}
+
 // ------------------------------------------------------------------ residual SpMV
 // y = b - A x, G lanes per row as in the plain SpMV.
 template <int G>
@@ -124,44 +169,78 @@ void launch_spmv_resid(int64_t n, const int64_t* rowptr, const int32_t* col, con
 
 // ------------------------------------------------------------------ GMRES(m)
 // Classical Gram-Schmidt applied twice (CGS2) against the Arnoldi basis
-// V_0..V_{k-1} (rows ldv apart), in three fused passes:
-//   mode 0: partial sums of <V_j, w> for the GM_CHUNK vectors of chunk blockIdx.y;
+// V_0..V_{k-1} (rows ldv apart, ldv even, 16-byte aligned), in three fused
+// passes over the basis:
+//   mode 0: partial sums of <V_j, w> for the KC vectors of chunk blockIdx.y;
 //   mode 1: u = w - sum_j h_j V_j (written to out by chunk 0), partial sums of <V_j, u>;
-//   mode 2: u = w - sum_j h_j V_j (written to out), partial sums of <u, u> (one chunk).
+//   mode 2: u = w - sum_j h_j V_j (written to out), partial sums of <u, u> (KC = 1).
+// Each thread takes two consecutive elements per step (16-byte loads).
 // Partial sums go to part[j * DOT_BLOCKS + blockIdx.x] (mode 2: part[blockIdx.x]).
+template <int KC, int MODE>
 __global__ void __launch_bounds__(256) gm_ortho_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int k,
                                                        const double* __restrict__ h, const double* __restrict__ w,
-                                                       double* __restrict__ out, double* __restrict__ part,
-                                                       int mode) {
+                                                       double* __restrict__ out, double* __restrict__ part) {
     __shared__ double hs[GM_MAXR + 1];
-    __shared__ double wsum[8][GM_CHUNK];
-    const int c0 = blockIdx.y * GM_CHUNK;
-    const int kc = mode == 2 ? 1 : min(GM_CHUNK, k - c0);
-    if (mode != 0)
+    __shared__ double wsum[8][KC];
+    const int c0 = blockIdx.y * KC;
+    const int kc = MODE == 2 ? 1 : min(KC, k - c0);
+    if (MODE != 0)
         for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
     __syncthreads();
-    double acc[GM_CHUNK];
+    double acc[KC];
 #pragma unroll
-    for (int j = 0; j < GM_CHUNK; ++j) acc[j] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)DOT_BLOCKS * 256) {
+    for (int j = 0; j < KC; ++j) acc[j] = 0.0;
+    const int64_t npair = n >> 1;
+    for (int64_t q = (int64_t)blockIdx.x * 256 + threadIdx.x; q < npair; q += (int64_t)DOT_BLOCKS * 256) {
+        const int64_t i = 2 * q;
+        double2 u = *reinterpret_cast<const double2*>(w + i);
+        if (MODE != 0) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int j = 0; j < k; ++j) {
+                // pass 2 reads each vector once (streaming); pass 1 reads its
+                // block again for the dots below, so keeps it cached
+                const double2* vp = reinterpret_cast<const double2*>(V + (int64_t)j * ldv + i);
+                const double2 v = MODE == 2 ? __ldcs(vp) : *vp;
+                s0 = fma(hs[j], v.x, s0);
+                s1 = fma(hs[j], v.y, s1);
+            }
+            u.x -= s0;
+            u.y -= s1;
+            if (blockIdx.y == 0) *reinterpret_cast<double2*>(out + i) = u;
+        }
+        if (MODE == 2) {
+            acc[0] = fma(u.x, u.x, acc[0]);
+            acc[0] = fma(u.y, u.y, acc[0]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < KC; ++j)
+                if (j < kc) {
+                    const double2 v = *reinterpret_cast<const double2*>(V + (int64_t)(c0 + j) * ldv + i);
+                    acc[j] = fma(v.x, u.x, acc[j]);
+                    acc[j] = fma(v.y, u.y, acc[j]);
+                }
+        }
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd n: the last element
+        const int64_t i = n - 1;
         double u = w[i];
-        if (mode != 0) {
-            double s = 0.0;
-            for (int j = 0; j < k; ++j) s = fma(hs[j], V[(int64_t)j * ldv + i], s);
-            u -= s;
+        if (MODE != 0) {
+            double s0 = 0.0;
+            for (int j = 0; j < k; ++j) s0 = fma(hs[j], V[(int64_t)j * ldv + i], s0);
+            u -= s0;
             if (blockIdx.y == 0) out[i] = u;
         }
-        if (mode == 2) {
+        if (MODE == 2) {
             acc[0] = fma(u, u, acc[0]);
         } else {
 #pragma unroll
-            for (int j = 0; j < GM_CHUNK; ++j)
+            for (int j = 0; j < KC; ++j)
                 if (j < kc) acc[j] = fma(V[(int64_t)(c0 + j) * ldv + i], u, acc[j]);
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int j = 0; j < GM_CHUNK; ++j) {
+    for (int j = 0; j < KC; ++j) {
         if (j < kc) {
             double v = acc[j];
 #pragma unroll
@@ -180,8 +259,19 @@ __global__ void __launch_bounds__(256) gm_ortho_kernel(int64_t n, const double* 
 
 void launch_gm_ortho(int64_t n, const double* V, int64_t ldv, int k, const double* h, const double* w, double* out,
                      double* part, int mode, cudaStream_t s) {
-    const int chunks = mode == 2 ? 1 : (k + GM_CHUNK - 1) / GM_CHUNK;
-    gm_ortho_kernel<<<dim3(DOT_BLOCKS, chunks), 256, 0, s>>>(n, V, ldv, k, h, w, out, part, mode);
+    if (mode == 0) {  // dots only: blocks of 8 vectors
+        gm_ortho_kernel<8, 0><<<dim3(DOT_BLOCKS, (k + 7) / 8), 256, 0, s>>>(n, V, ldv, k, h, w, out, part);
+    } else if (mode == 1) {  // update + dots: the update reads every vector, so one block row holds them all
+        if (k <= 8)
+            gm_ortho_kernel<8, 1><<<dim3(DOT_BLOCKS, 1), 256, 0, s>>>(n, V, ldv, k, h, w, out, part);
+        else if (k <= 16)
+            gm_ortho_kernel<16, 1><<<dim3(DOT_BLOCKS, 1), 256, 0, s>>>(n, V, ldv, k, h, w, out, part);
+        else
+            gm_ortho_kernel<GM_CHUNK, 1><<<dim3(DOT_BLOCKS, (k + GM_CHUNK - 1) / GM_CHUNK), 256, 0, s>>>(
+                n, V, ldv, k, h, w, out, part);
+    } else {
+        gm_ortho_kernel<1, 2><<<dim3(DOT_BLOCKS, 1), 256, 0, s>>>(n, V, ldv, k, h, w, out, part);
+    }
 }
 
 // hcol[j] = sum of the DOT_BLOCKS partial sums of vector j (fixed order);
