@@ -2368,10 +2368,11 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         chol_batched<double>(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}}, {&h->env_row});
         // Inverses of the diagonal blocks of L_E (block size cSB): the coarse
         // solve is then a blocked forward / backward substitution with L_E and
-        // L_E^T, with no inverse of the whole factor.  About four blocks (each
-        // costs two grid-wide phases per coarse solve), at most 1024 wide (the
-        // inverses are stored dense).
-        const int SB = std::min<int>(1024, std::max<int>(CHOL_NB, cdiv(cdiv(nC, 4), CHOL_NB) * CHOL_NB));
+        // L_E^T, with no inverse of the whole factor.  About eight blocks, at
+        // most 512 wide: each block costs two grid-wide phases per coarse
+        // solve, and its inverse (stored dense) costs SB^3 / 3 FP64
+        // multiply-adds in the setup, so n_C SB^2 / 3 in all.
+        const int SB = std::min<int>(512, std::max<int>(CHOL_NB, cdiv(cdiv(nC, 8), CHOL_NB) * CHOL_NB));
         const int K = cdiv(nC, SB);
         h->cSB = SB;
         h->cK = K;
