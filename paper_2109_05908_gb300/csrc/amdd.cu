@@ -2144,9 +2144,19 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         double* E = h->d_YE;
         ck(cudaMemsetAsync(E, 0, (size_t)nC * nC * sizeof(double), s));
         std::vector<GemmDesc> g1, g2;
+        std::vector<DiagScaleDesc> dsd;
+        int max_ni_d = 1;
         for (int i = 0; i < N; ++i) {
             if (h->p[i] == 0) continue;
             const int ni = h->ni[i], nIi = h->nI[i], pi = h->p[i];
+            if (diag_basis && pi == nIi) {
+                // Z_i = diag(A_II)^{-1/2}: AZ_i and E_ii are scalings of A_ii
+                // (the same products as the GEMMs, whose other terms are zeros)
+                dsd.push_back({Araw + h->off_sq[i], ni, nIi, AZ + off_az[i], E + (size_t)h->coff[i] * nC + h->coff[i],
+                               (int64_t)nC});
+                max_ni_d = std::max(max_ni_d, ni);
+                continue;
+            }
             // AZ_i = A(Omega_i, Omega_Ii) Z_i   (ni x p_i)
             g1.push_back(gd(Araw + h->off_sq[i], ni, 0, h->d_Zt + h->off_zt[i], nIi, 1, AZ + off_az[i], pi, ni, pi,
                             nIi, 1.0, 0.0, 0));
@@ -2156,6 +2166,11 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         }
         gemm(C, g1);
         gemm(C, g2);
+        if (!dsd.empty()) {
+            auto d = C.up(dsd);
+            PScope ps(h, PK_SMALL, 0.0, 0.0);
+            launch_diag_scale(d, (int)dsd.size(), max_ni_d, s);
+        }
         // E_ij (i > j) = sum over g in Omega_Ii cap Omega_j of Z_i[g]^T (A Z_j)[g]
         std::vector<int32_t> posI(n, -1);
         for (int i = 0; i < N; ++i)

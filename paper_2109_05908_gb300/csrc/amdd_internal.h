@@ -180,6 +180,17 @@ struct DiagBasisDesc {
     int nI;
 };
 void launch_diag_basis(const DiagBasisDesc* d, int nmat, int maxn, cudaStream_t s);
+// With that basis: AZ[r][c] = A_ii[r][c] / sqrt(A_II[c][c]) (ni x nI, leading
+// dimension nI) and the lower triangle of E_ii[r][c] = AZ[r][c] / sqrt(A_II[r][r])
+// (leading dimension ldE).
+struct DiagScaleDesc {
+    const double* A;  // A_ii dense, ni x ni (leading dimension ni)
+    int ni, nI;
+    double* AZ;
+    double* Eii;
+    int64_t ldE;
+};
+void launch_diag_scale(const DiagScaleDesc* d, int nmat, int maxni, cudaStream_t s);
 template <typename T>
 void launch_build_kjac(const KjacDesc<T>* d, int nmat, int maxrows, cudaStream_t s);
 template <typename T>

@@ -840,6 +840,23 @@ void launch_diag_basis(const DiagBasisDesc* d, int nmat, int maxn, cudaStream_t 
     if (nmat > 0 && maxn > 0) diag_basis_kernel<<<dim3(maxn, nmat), 256, 0, s>>>(d);
 }
 
+__global__ void __launch_bounds__(256) diag_scale_kernel(const DiagScaleDesc* __restrict__ descs) {
+    const DiagScaleDesc d = descs[blockIdx.y];
+    const int r = blockIdx.x;
+    if (r >= d.ni) return;
+    const double* a = d.A + (size_t)r * d.ni;
+    const double fr = r < d.nI ? 1.0 / sqrt(d.A[(size_t)r * d.ni + r]) : 0.0;
+    for (int c = threadIdx.x; c < d.nI; c += blockDim.x) {
+        const double az = a[c] * (1.0 / sqrt(d.A[(size_t)c * d.ni + c]));
+        d.AZ[(size_t)r * d.nI + c] = az;
+        if (r < d.nI && c <= r) d.Eii[(size_t)r * d.ldE + c] = fr * az;
+    }
+}
+
+void launch_diag_scale(const DiagScaleDesc* d, int nmat, int maxni, cudaStream_t s) {
+    if (nmat > 0 && maxni > 0) diag_scale_kernel<<<dim3(maxni, nmat), 256, 0, s>>>(d);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) build_kjac_kernel(const KjacDesc<T>* __restrict__ descs) {
     const KjacDesc<T> d = descs[blockIdx.y];
