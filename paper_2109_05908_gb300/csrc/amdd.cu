@@ -122,6 +122,9 @@ struct amdd_handle {
     cudaStream_t s = nullptr;
     cudaStream_t s2 = nullptr;  // second stream of the setup (look-ahead of the blocked Cholesky)
     cudaEvent_t ev_panel = nullptr, ev_far = nullptr;
+    // third and fourth streams: the speculative coarse factorisation (tau > 1)
+    cudaStream_t s3 = nullptr, s4 = nullptr;
+    cudaEvent_t ev_panel3 = nullptr, ev_far3 = nullptr, ev_spec_in = nullptr, ev_spec_done = nullptr;
     ProfState prof;
     int64_t n = 0, nnz = 0;
     int N = 0, overlap = 0;
@@ -286,8 +289,10 @@ struct Ctx {
     std::vector<std::shared_ptr<void>> keep;
     explicit Ctx(amdd_handle* hh) : h(hh) {}
     ~Ctx() {
-        // work on the second stream may still read temporaries (after an error)
+        // work on the other setup streams may still read temporaries (after an error)
         if (h->s2) cudaStreamSynchronize(h->s2);
+        if (h->s3) cudaStreamSynchronize(h->s3);
+        if (h->s4) cudaStreamSynchronize(h->s4);
         for (void* p : temps) cudaFreeAsync(p, h->s);
     }
     template <class T>
@@ -330,6 +335,10 @@ std::vector<TileRef> gemm_tiles(const std::vector<GemmDescT<T>>& ds, int tile) {
 
 // 64 x 64 tiles unless that leaves fewer than two CTAs per SM; then 32 x 32.
 constexpr int SMALL_LAUNCH_TILES = 2 * 152;
+// A launch with fewer 32 x 32 tiles than this uses 16 x 16 tiles: with FP64 at
+// two multiply-adds per clock per SM, a few large tiles leave most SMs idle and
+// each tile's chain long.
+constexpr int TINY_LAUNCH_TILES = 152 / 2;
 
 template <typename T>
 void gemm(Ctx& C, const std::vector<GemmDescT<T>>& ds) {
@@ -339,6 +348,10 @@ void gemm(Ctx& C, const std::vector<GemmDescT<T>>& ds) {
     if ((int)tiles.size() < SMALL_LAUNCH_TILES) {
         tile = 32;
         tiles = gemm_tiles(ds, tile);
+        if ((int)tiles.size() < TINY_LAUNCH_TILES) {
+            tile = 16;
+            tiles = gemm_tiles(ds, tile);
+        }
     }
     double fl = 0.0;
     for (const GemmDescT<T>& g : ds) {
@@ -475,16 +488,33 @@ void chol_batched(Ctx& C, const std::vector<CholDescT<T>>& ds, const std::vector
             launch_chol_panel<T>(dd, dpt, (int)pt.size(), k0, sm);
         }
         // far update on the second stream, after this panel
-        const int tile = tiles64 < SMALL_LAUNCH_TILES ? 32 : 64;
+        int tile = tiles64 < SMALL_LAUNCH_TILES ? 32 : 64;
         std::vector<TileRef> tf, tn;
         double ffl = 0.0, nfl = 0.0;
-        for (int q = 0; q < (int)gf.size(); ++q) {
-            const int kend = gf_kend[q];
-            const int w = (int)(ds[gf_d[q]].n - kend) - gf[q].m;
-            update_tiles(q, gf[q], gf_d[q], kend + w, kend + w, kend, tile, tf, ffl);
+        auto far_tiles = [&]() {
+            tf.clear();
+            ffl = 0.0;
+            for (int q = 0; q < (int)gf.size(); ++q) {
+                const int kend = gf_kend[q];
+                const int w = (int)(ds[gf_d[q]].n - kend) - gf[q].m;
+                update_tiles(q, gf[q], gf_d[q], kend + w, kend + w, kend, tile, tf, ffl);
+            }
+        };
+        far_tiles();
+        if (tile == 32 && (int)tf.size() < TINY_LAUNCH_TILES) {
+            tile = 16;
+            far_tiles();
         }
+        int ntile = 32;
         for (int q = 0; q < (int)gn.size(); ++q)
-            update_tiles(q, gn[q], gn_d[q], gn_kend[q], gn_kend[q], gn_kend[q], 32, tn, nfl);
+            update_tiles(q, gn[q], gn_d[q], gn_kend[q], gn_kend[q], gn_kend[q], ntile, tn, nfl);
+        if ((int)tn.size() < TINY_LAUNCH_TILES) {
+            ntile = 16;
+            tn.clear();
+            nfl = 0.0;
+            for (int q = 0; q < (int)gn.size(); ++q)
+                update_tiles(q, gn[q], gn_d[q], gn_kend[q], gn_kend[q], gn_kend[q], ntile, tn, nfl);
+        }
         const GemmDescT<T>* dgf = tf.empty() ? nullptr : C.up(gf);
         const TileRef* dtf = tf.empty() ? nullptr : C.up(tf);
         const GemmDescT<T>* dgn = tn.empty() ? nullptr : C.up(gn);
@@ -507,7 +537,7 @@ void chol_batched(Ctx& C, const std::vector<CholDescT<T>>& ds, const std::vector
         }
         if (!tn.empty()) {
             PScope ps(h, pk<T>(PK_GEMM, PK_GEMM_F32), nfl);
-            launch_gemm<T>(dgn, dtn, (int)tn.size(), 32, sm);
+            launch_gemm<T>(dgn, dtn, (int)tn.size(), ntile, sm);
         }
     }
     if (far_pending) ck(cudaStreamWaitEvent(sm, h->ev_far, 0));
@@ -1641,6 +1671,364 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     else
         launch_convert<double, float>(Araw, Lb, h->sum_sq, s);
 
+    // full selections: the basis diag(A_II)^{-1/2} keeps every block of E that
+    // touches such a subdomain as sparse as A (its envelope-aware Cholesky and
+    // the coarse solve then skip most tiles); with a kept E (multilevel form)
+    // the A_II-orthonormal rows of L_A^{-1}, so that E is a block-orthogonal
+    // congruence of the one any other A_II-orthonormal basis gives
+    const bool diag_basis = !h->keep_E;
+    h->diag_basis = diag_basis;
+    // Z_i = diag(A_II)^{-1/2} for every fully selected subdomain (d_Zt allocated)
+    auto fill_diag_zt = [&]() {
+        std::vector<DiagBasisDesc> db;
+        int maxn = 1;
+        for (int i = 0; i < N; ++i)
+            if (h->p[i] == h->nI[i] && h->p[i] > 0) {
+                db.push_back({Araw + h->off_sq[i], h->ni[i], h->d_Zt + h->off_zt[i], h->nI[i]});
+                maxn = std::max(maxn, h->nI[i]);
+            }
+        if (!db.empty()) {
+            auto d = C.up(db);
+            PScope ps(h, PK_SMALL);
+            launch_diag_basis(d, (int)db.size(), maxn, h->s);
+        }
+    };
+    // ---- (9) as a function of the selection (h->p, h->coff, h->d_Zt): the coarse
+    // matrix, its ordering, factor and the diagonal-block inverses of the factor,
+    // on whatever streams h->s / h->s2 name when it is called.
+    auto factor_coarse = [&]() {
+        // ---- (9) coarse matrix E = R_0 A R_0^T (Eq. (two_level_schwarz)), its
+        // Cholesky factor and inverse factor
+        cudaStream_t s = h->s;  // the stream this call runs on
+        const int64_t nC = h->nC;
+        h->d_cperm = nullptr;
+        h->d_YEt = nullptr;
+        if (nC > 0) {
+            std::vector<int64_t> off_az(N + 1, 0);
+            for (int i = 0; i < N; ++i) off_az[i + 1] = off_az[i] + (int64_t)h->ni[i] * h->p[i];
+            double* AZ = C.tnew<double>(off_az[N]);
+            h->d_YE = dnew<double>(h, (size_t)nC * nC);  // E, then its Cholesky factor L_E (lower)
+            double* E = h->d_YE;
+            ck(cudaMemsetAsync(E, 0, (size_t)nC * nC * sizeof(double), s));
+            std::vector<GemmDesc> g1, g2;
+            std::vector<DiagScaleDesc> dsd;
+            int max_ni_d = 1;
+            for (int i = 0; i < N; ++i) {
+                if (h->p[i] == 0) continue;
+                const int ni = h->ni[i], nIi = h->nI[i], pi = h->p[i];
+                if (diag_basis && pi == nIi) {
+                    // Z_i = diag(A_II)^{-1/2}: AZ_i and E_ii are scalings of A_ii
+                    // (the same products as the GEMMs, whose other terms are zeros)
+                    dsd.push_back({Araw + h->off_sq[i], ni, nIi, AZ + off_az[i], E + (size_t)h->coff[i] * nC + h->coff[i],
+                                   (int64_t)nC});
+                    max_ni_d = std::max(max_ni_d, ni);
+                    continue;
+                }
+                // AZ_i = A(Omega_i, Omega_Ii) Z_i   (ni x p_i)
+                g1.push_back(gd(Araw + h->off_sq[i], ni, 0, h->d_Zt + h->off_zt[i], nIi, 1, AZ + off_az[i], pi, ni, pi,
+                                nIi, 1.0, 0.0, 0));
+                // E_ii = Z_i^T A_II Z_i
+                g2.push_back(gd(h->d_Zt + h->off_zt[i], nIi, 0, AZ + off_az[i], pi, 0,
+                                E + (size_t)h->coff[i] * nC + h->coff[i], (int)nC, pi, pi, nIi, 1.0, 0.0, 1));
+            }
+            gemm(C, g1);
+            gemm(C, g2);
+            if (!dsd.empty()) {
+                auto d = C.up(dsd);
+                PScope ps(h, PK_SMALL, 0.0, 0.0);
+                launch_diag_scale(d, (int)dsd.size(), max_ni_d, s);
+            }
+            // E_ij (i > j) = sum over g in Omega_Ii cap Omega_j of Z_i[g]^T (A Z_j)[g]
+            std::vector<int32_t> posI(n, -1);
+            for (int i = 0; i < N; ++i)
+                for (int a = 0; a < h->nI[i]; ++a) posI[Il[i][a]] = a;
+            std::vector<std::vector<std::pair<int32_t, int32_t>>> lists;  // per pair
+            std::vector<std::pair<int, int>> pairs;
+            {
+                std::vector<int> slot(N, -1);
+                for (int j = 0; j < N; ++j) {
+                    if (h->p[j] == 0) continue;
+                    std::fill(slot.begin(), slot.end(), -1);
+                    std::vector<int> touched;
+                    const int32_t* om = omega.data() + h->off_om[j];
+                    for (int ps = 0; ps < h->ni[j]; ++ps) {
+                        const int32_t g = om[ps];
+                        const int i = part[g];
+                        if (i <= j || h->p[i] == 0) continue;
+                        if (slot[i] < 0) {
+                            slot[i] = (int)pairs.size();
+                            pairs.push_back({i, j});
+                            lists.emplace_back();
+                        }
+                        lists[slot[i]].push_back({posI[g], ps});
+                    }
+                }
+            }
+            std::vector<int32_t> la, lpos;
+            std::vector<EPairRef> et;
+            for (size_t q = 0; q < pairs.size(); ++q) {
+                const int i = pairs[q].first, j = pairs[q].second;
+                const int64_t lo = (int64_t)la.size();
+                for (auto& e : lists[q]) {
+                    la.push_back(e.first);
+                    lpos.push_back(e.second);
+                }
+                for (int tr = 0; tr * 32 < h->p[i]; ++tr)
+                    for (int tc = 0; tc * 32 < h->p[j]; ++tc) {
+                        EPairRef t;
+                        t.i = i;
+                        t.j = j;
+                        t.list_off = lo;
+                        t.list_len = (int)lists[q].size();
+                        t.tr = tr;
+                        t.tc = tc;
+                        et.push_back(t);
+                    }
+            }
+            std::vector<int32_t> nIv(h->nI.begin(), h->nI.end()), pv(h->p.begin(), h->p.end());
+            h->d_zt_off = C.up(std::vector<int64_t>(h->off_zt.begin(), h->off_zt.end() - 1), true);
+            h->d_nI = C.up(nIv, true);
+            h->d_p = C.up(pv, true);
+            h->d_coff = C.up(std::vector<int64_t>(h->coff.begin(), h->coff.end() - 1), true);
+            if (!et.empty()) {
+                auto a = C.up(et);
+                auto b = C.up(la);
+                auto c = C.up(lpos);
+                auto d = C.up(std::vector<int64_t>(off_az.begin(), off_az.end() - 1));
+                double fl = 0.0;
+                for (size_t q = 0; q < pairs.size(); ++q)
+                    fl += 2.0 * h->p[pairs[q].first] * h->p[pairs[q].second] * lists[q].size();
+                PScope ps(h, PK_E_ASM, fl);
+                launch_e_offdiag(a, (int)et.size(), b, c, h->d_Zt, h->d_zt_off, h->d_nI, AZ, d, h->d_p, h->d_coff, E, nC,
+                                 s);
+            }
+            if (h->keep_E) {
+                // a copy of E for a next level (multilevel form), as a sparse matrix
+                // with the block pattern: every entry of E_ij for i == j or for
+                // subdomains coupled in A (a structural non-zero in
+                // A(Omega_Ii, Omega_Ij)); E holds its lower triangle
+                std::vector<std::vector<int>> adj(N);
+                for (int64_t g = 0; g < n; ++g)
+                    for (int64_t k = rp[g]; k < rp[g + 1]; ++k)
+                        if (part[g] != part[ci[k]]) adj[part[g]].push_back(part[ci[k]]);
+                for (int i = 0; i < N; ++i) {
+                    adj[i].push_back(i);
+                    std::sort(adj[i].begin(), adj[i].end());
+                    adj[i].erase(std::unique(adj[i].begin(), adj[i].end()), adj[i].end());
+                }
+                std::vector<int64_t> erp(nC + 1, 0), esrc;
+                std::vector<int32_t> ecol;
+                for (int i = 0; i < N; ++i)
+                    for (int k = 0; k < h->p[i]; ++k) {
+                        const int64_t r = h->coff[i] + k;
+                        for (int j : adj[i])
+                            for (int l = 0; l < h->p[j]; ++l) {
+                                const int64_t c = h->coff[j] + l;
+                                ecol.push_back((int32_t)c);
+                                esrc.push_back(std::max(r, c) * nC + std::min(r, c));
+                            }
+                        erp[r + 1] = (int64_t)ecol.size();
+                    }
+                h->E_nnz = (int64_t)ecol.size();
+                h->d_E_rowptr = C.up(erp, true);
+                h->d_E_col = C.up(ecol, true);
+                h->d_E_val = dnew<double>(h, h->E_nnz);
+                auto dsrc = C.up(esrc);
+                PScope ps(h, PK_SMALL, 0.0, 16.0 * h->E_nnz);
+                launch_gather_idx64(dsrc, h->E_nnz, E, h->d_E_val, s);
+            }
+            // ---- sparsity graph of E (coarse unknowns in subdomain order): blocks
+            // of subdomains coupled in A (E_ij = Z_i^T A(Omega_Ii, Omega_Ij) Z_j is
+            // exactly zero otherwise); a diagonal-basis block contributes only the
+            // unknowns whose node touches the other subdomain
+            std::vector<std::vector<int>> adjB(N);
+            for (int64_t g = 0; g < n; ++g)
+                for (int64_t q = rp[g]; q < rp[g + 1]; ++q)
+                    if (part[g] != part[ci[q]]) adjB[part[g]].push_back(part[ci[q]]);
+            for (int i = 0; i < N; ++i) {
+                adjB[i].push_back(i);
+                std::sort(adjB[i].begin(), adjB[i].end());
+                adjB[i].erase(std::unique(adjB[i].begin(), adjB[i].end()), adjB[i].end());
+            }
+            auto full_diag = [&](int i) { return diag_basis && h->p[i] == h->nI[i] && h->p[i] > 0; };
+            std::vector<std::vector<int32_t>> nbr(nC);
+            for (int i = 0; i < N; ++i) {
+                if (h->p[i] == 0) continue;
+                if (full_diag(i)) {
+                    for (int k = 0; k < h->p[i]; ++k) {
+                        const int32_t g = Il[i][k];
+                        auto& L = nbr[h->coff[i] + k];
+                        for (int64_t q = rp[g]; q < rp[g + 1]; ++q) {
+                            const int32_t g2 = ci[q];
+                            const int j = part[g2];
+                            if (h->p[j] == 0) continue;
+                            if (full_diag(j))
+                                L.push_back((int32_t)(h->coff[j] + posI[g2]));
+                            else
+                                for (int l = 0; l < h->p[j]; ++l) L.push_back((int32_t)(h->coff[j] + l));
+                        }
+                    }
+                } else {
+                    std::vector<int32_t> row;
+                    for (int j : adjB[i]) {
+                        if (h->p[j] == 0) continue;
+                        if (!full_diag(j) || j == i) {
+                            for (int l = 0; l < h->p[j]; ++l) row.push_back((int32_t)(h->coff[j] + l));
+                        } else {
+                            for (int l = 0; l < h->nI[j]; ++l) {  // nodes of Omega_Ij touching Omega_Ii
+                                const int32_t g2 = Il[j][l];
+                                for (int64_t q = rp[g2]; q < rp[g2 + 1]; ++q)
+                                    if (part[ci[q]] == i) {
+                                        row.push_back((int32_t)(h->coff[j] + l));
+                                        break;
+                                    }
+                            }
+                        }
+                    }
+                    for (int k = 0; k < h->p[i]; ++k) nbr[h->coff[i] + k] = row;
+                }
+            }
+            for (auto& L : nbr) {
+                std::sort(L.begin(), L.end());
+                L.erase(std::unique(L.begin(), L.end()), L.end());
+            }
+            // ---- ordering of the coarse unknowns for the factorisation: reverse
+            // Cuthill-McKee when it cuts the factorisation work (the sum over rows
+            // of (r - first(r))^2) by a fifth or more, else the subdomain order.
+            // E is permuted on the device; the coarse solves gather and scatter
+            // through the order.
+            auto envelope = [&](const std::vector<int32_t>& iperm, const std::vector<int32_t>& perm,
+                                std::vector<int>& env) {
+                env.assign(nC, 0);
+                double work = 0.0;
+                for (int64_t rn = 0; rn < nC; ++rn) {
+                    int first = (int)rn;
+                    for (int32_t c : nbr[perm[rn]]) first = std::min(first, (int)iperm[c]);
+                    env[rn] = first;
+                    work += (double)(rn - first) * (double)(rn - first);
+                }
+                return work;
+            };
+            std::vector<int32_t> idp(nC);
+            std::iota(idp.begin(), idp.end(), 0);
+            std::vector<int> env_id, env_rcm;
+            const double prof_id = envelope(idp, idp, env_id);
+            std::vector<int32_t> rperm = rcm_order(nbr);
+            std::vector<int32_t> riperm(nC);
+            for (int64_t q = 0; q < nC; ++q) riperm[rperm[q]] = (int32_t)q;
+            const double prof_rcm = envelope(riperm, rperm, env_rcm);
+            const bool use_rcm = prof_rcm < 0.8 * prof_id;
+            h->env_row = use_rcm ? env_rcm : env_id;
+            h->env_colend.assign(nC, 0);
+            // the factor fills each row's envelope: column c of L_E reaches every
+            // row whose envelope starts at or before c
+            {
+                std::vector<int> mark(nC, 0);
+                for (int64_t r = 0; r < nC; ++r) mark[h->env_row[r]] = std::max(mark[h->env_row[r]], (int)r + 1);
+                int run = 0;
+                for (int64_t c = 0; c < nC; ++c) {
+                    run = std::max(run, mark[c]);
+                    h->env_colend[c] = std::max(run, (int)c + 1);
+                }
+            }
+            double* linvE = C.tnew<double>((size_t)cdiv(nC, CHOL_NB) * CHOL_NB * CHOL_NB);
+            if (use_rcm) {
+                // E (lower triangle, subdomain order) -> Ep[r][c] = E[perm r][perm c]
+                // (lower triangle); the two nC x nC buffers swap roles
+                h->d_cperm = C.up(rperm, true);
+                h->d_cp = dnew<double>(h, (size_t)MAXB * nC);
+                h->d_ep = dnew<double>(h, (size_t)MAXB * nC);
+                h->d_YEt = dnew<double>(h, (size_t)nC * nC);
+                {
+                    PScope ps(h, PK_SMALL, 0.0, 8.0 * (double)nC * nC);
+                    launch_sym_permute(E, h->d_YEt, h->d_cperm, nC, s);
+                }
+                std::swap(h->d_YE, h->d_YEt);
+                E = h->d_YE;
+            }
+            if (!h->d_YEt) h->d_YEt = dnew<double>(h, (size_t)nC * nC);
+            chol_batched<double>(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}}, {&h->env_row});
+            // Inverses of the diagonal blocks of L_E (block size cSB): the coarse
+            // solve is then a blocked forward / backward substitution with L_E and
+            // L_E^T, with no inverse of the whole factor.  About eight blocks, at
+            // most 512 wide: each block costs two grid-wide phases per coarse
+            // solve, and its inverse (stored dense) costs SB^3 / 3 FP64
+            // multiply-adds in the setup, so n_C SB^2 / 3 in all.
+            const int SB = std::min<int>(512, std::max<int>(CHOL_NB, cdiv(cdiv(nC, 8), CHOL_NB) * CHOL_NB));
+            const int K = cdiv(nC, SB);
+            h->cSB = SB;
+            h->cK = K;
+            h->d_Yd = dnew<double>(h, (size_t)K * SB * SB);
+            h->d_Ydt = dnew<double>(h, (size_t)K * SB * SB);
+            std::vector<TrtriDesc> tj;
+            std::vector<const double*> ts;
+            std::vector<double*> tdst;
+            std::vector<int> tn, tl;
+            for (int k = 0; k < K; ++k) {
+                const int r0 = k * SB, sb = (int)std::min<int64_t>(SB, nC - r0);
+                tj.push_back({E + (size_t)r0 * nC + r0, h->d_Yd + (size_t)k * SB * SB,
+                              linvE + (size_t)(r0 / CHOL_NB) * CHOL_NB * CHOL_NB, sb, (int)nC, SB});
+                ts.push_back(h->d_Yd + (size_t)k * SB * SB);
+                tdst.push_back(h->d_Ydt + (size_t)k * SB * SB);
+                tn.push_back(sb);
+                tl.push_back(SB);
+            }
+            trtri_batched(C, tj);
+            transpose_batched(C, ts, tdst, tn, tl, tl);
+            transpose_batched<double>(C, {E}, {h->d_YEt}, {(int)nC}, {(int)nC}, {(int)nC});
+        } else {
+            h->d_zt_off = C.up(std::vector<int64_t>(h->off_zt.begin(), h->off_zt.end() - 1), true);
+            h->d_nI = C.up(std::vector<int32_t>(h->nI.begin(), h->nI.end()), true);
+            h->d_p = C.up(std::vector<int32_t>(h->p.begin(), h->p.end()), true);
+            h->d_coff = C.up(std::vector<int64_t>(h->coff.begin(), h->coff.end() - 1), true);
+        }
+    };
+
+    // ---- speculative coarse space.  With Boolean D_i every non-zero eigenvalue
+    // of eq. (Zi) is >= 1, so for tau > 1 every one is selected and the coarse
+    // space is known before the eigensolve: the coarse matrix and its factor
+    // (a latency-bound FP64 chain on few SMs) are built on the third and fourth
+    // streams while the local eigenproblems run.  The selection computed in
+    // step (7) is then compared with this one; on a mismatch (rounding below
+    // 1/tau) the speculative work is dropped and step (9) runs as usual.
+    const bool spec = diag_basis && h->tau >= 1.01 && h->s3 && h->s4;
+    bool spec_ok = false;
+    std::vector<int32_t> spec_p;
+    if (spec) {
+        h->p.assign(h->nI.begin(), h->nI.end());
+        h->coff.assign(N + 1, 0);
+        h->off_zt.assign(N + 1, 0);
+        for (int i = 0; i < N; ++i) {
+            h->coff[i + 1] = h->coff[i] + h->p[i];
+            h->off_zt[i + 1] = h->off_zt[i] + (int64_t)h->p[i] * h->nI[i];
+        }
+        h->nC = h->coff[N];
+        h->sum_zt = h->off_zt[N];
+        spec_p = h->p;
+        ck(cudaEventRecord(h->ev_spec_in, h->s));  // A_ii gathered
+        ck(cudaStreamWaitEvent(h->s3, h->ev_spec_in, 0));
+        std::swap(h->s, h->s3);
+        std::swap(h->s2, h->s4);
+        std::swap(h->ev_panel, h->ev_panel3);
+        std::swap(h->ev_far, h->ev_far3);
+        auto restore = [&]() {
+            std::swap(h->s, h->s3);
+            std::swap(h->s2, h->s4);
+            std::swap(h->ev_panel, h->ev_panel3);
+            std::swap(h->ev_far, h->ev_far3);
+        };
+        try {
+            h->d_Zt = dnew<double>(h, h->sum_zt);
+            fill_diag_zt();
+            factor_coarse();
+            ck(cudaEventRecord(h->ev_spec_done, h->s));
+        } catch (...) {
+            restore();
+            throw;
+        }
+        restore();
+    }
+
     // ---- (1) exact Cholesky of A_ii (local solver) and its inverse factor
     {
         std::vector<CholDescT<T>> cd(N);
@@ -1976,7 +2364,9 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         if (h->prof.on) {
             // per sweep: row norms and one inner product per pair; plus the rotations performed
             const double ni = h->ni[i], nt = h->nt[i];
-            h->prof.flops[PK_JAC_SVD] += sw[i] * (ni * 2.0 * nt + ni * (ni - 1) / 2 * 2.0 * nt) + rot_h[i] * 6.0 * nt;
+            // (the class of the precision the SVD ran in)
+            h->prof.flops[pk<TS>(PK_JAC_SVD, PK_JAC_F32)] +=
+                sw[i] * (ni * 2.0 * nt + ni * (ni - 1) / 2 * 2.0 * nt) + rot_h[i] * 6.0 * nt;
         }
         std::sort(h->sigma_h.begin() + h->off_om[i], h->sigma_h.begin() + h->off_om[i + 1], std::greater<double>());
     }
@@ -2001,6 +2391,15 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     }
     h->nC = h->coff[N];
     h->sum_zt = h->off_zt[N];
+    if (spec) {
+        spec_ok = h->p == spec_p;
+        if (spec_ok) {
+            ck(cudaStreamWaitEvent(s, h->ev_spec_done, 0));
+        } else {  // the speculative buffers stay owned by the handle until amdd_destroy
+            ck(cudaStreamSynchronize(h->s3));
+            ck(cudaStreamSynchronize(h->s4));
+        }
+    }
 
     // ---- (8) coarse block Z_i on Omega_Ii as A_II-orthonormal rows.  When
     // every eigenvalue is selected, span(Z_i) = R^{|Omega_Ii|} and any
@@ -2009,412 +2408,122 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     // [T | I] (FP64, relative criterion) gives the eigenvectors w_j as the
     // right half and mu_j as the left-half row norms; the p_i rows with the
     // smallest mu give u = L_A^{-T} w.
-    h->d_Zt = dnew<double>(h, h->sum_zt);
-    T* ZtT = nullptr;
-    if constexpr (f64)
-        ZtT = h->d_Zt;
-    else
-        ZtT = C.tnew<T>(h->sum_zt);
-    // full selections: the basis diag(A_II)^{-1/2} keeps every block of E that
-    // touches such a subdomain as sparse as A (its envelope-aware Cholesky and
-    // the coarse solve then skip most tiles); with a kept E (multilevel form)
-    // the A_II-orthonormal rows of L_A^{-1}, so that E is a block-orthogonal
-    // congruence of the one any other A_II-orthonormal basis gives
-    const bool diag_basis = !h->keep_E;
-    h->diag_basis = diag_basis;
-    if (h->nC > 0) {
-        std::vector<int64_t> ysrc, ydst;
-        std::vector<int32_t> ylen;
-        for (int i = 0; i < N; ++i) {
-            if (h->p[i] != h->nI[i] || h->p[i] == 0 || diag_basis) continue;
-            for (int k = 0; k < h->nI[i]; ++k) {
-                ysrc.push_back(h->off_sq[i] + (int64_t)k * h->ni[i]);
-                ydst.push_back(h->off_zt[i] + (int64_t)k * h->nI[i]);
-                ylen.push_back(h->nI[i]);
-            }
-        }
-        if (!ysrc.empty()) {
-            auto a = C.up(ysrc);
-            auto b = C.up(ydst);
-            auto c = C.up(ylen);
-            PScope ps(h, PK_SMALL);
-            launch_gather_rows<T>(Yl, a, ZtT, b, c, (int64_t)ysrc.size(), s);
-        }
-        h->n_partial = (int)partial.size();
+    if (spec_ok) {
+        h->n_partial = 0;
         h->eig_iters.assign(N, -2);
-        T* Wsel = partial.empty() ? nullptr : C.tnew<T>(h->sum_zt);
-        std::vector<int> dense = partial;  // subdomains whose eigenvectors come from the dense Jacobi
-        if (!partial.empty() && (h->eig_solver >= 1 || h->keep_prop)) {
-            dense = learned_eigvecs<T>(C, h, partial, Araw, Lb, TI, off_ti, Wsel);
-        }
-        for (int i : dense) h->eig_iters[i] = -1;
-        if (!dense.empty()) {
-            const std::vector<int>& partial_d = dense;
-            const int np = (int)partial_d.size();
-            std::vector<JacobiDescT<T>> jd(np);
-            std::vector<double*> mp(np);
-            double* mu_j = C.tnew<double>(h->sum_nI);
-            T* nrmE = C.tnew<T>(h->sum_nI);  // row norms of the eigen-Jacobi
-            int maxc = 1;
-            for (int q = 0; q < np; ++q) {
-                const int i = partial_d[q], nIi = h->nI[i];
-                jd[q] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrmE + h->off_I[i], nullptr};
-                mp[q] = mu_j + h->off_I[i];
-                maxc = std::max(maxc, nIi);
-            }
-            JacobiDescT<T>* djd = C.up(jd);
-            double* const* dmp = C.up(mp);
-            {
-                PScope ps(h, PK_JAC_EIG);
-                const T tol = (f64 ? T(2) : T(8)) * std::sqrt((T)maxc) * std::numeric_limits<T>::epsilon();
-                run_jacobi<T>(h, jd, djd, h->max_sweeps, tol, sweeps + N, rots + N, f64 ? 1 : 0);
-            }
-            {
-                PScope ps(h, PK_SMALL);
-                launch_rownorms<T>(djd, np, dmp, (T*)nullptr, 0.0, 0, s);
-            }
-            std::vector<double> muj(h->sum_nI);
-            ck(cudaMemcpyAsync(muj.data(), mu_j, h->sum_nI * sizeof(double), cudaMemcpyDeviceToHost, s));
-            ck(cudaMemcpyAsync(sw.data() + N, sweeps + N, N * sizeof(int), cudaMemcpyDeviceToHost, s));
-            ck(cudaMemcpyAsync(rot_h.data() + N, rots + N, N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-            {
-                const int e = read_err(h);
-                if (e) throw Fail{err_status(e)};
-            }
-            std::vector<int64_t> wsrc, wdst;
-            std::vector<int32_t> wlen;
-            for (int q = 0; q < np; ++q) {
-                const int i = partial_d[q], nIi = h->nI[i];
-                h->sweeps_eig = std::max(h->sweeps_eig, sw[N + q]);
-                h->rot_eig += (int64_t)rot_h[N + q];
-                if (h->prof.on)
-                    h->prof.flops[PK_JAC_EIG] +=
-                        sw[N + q] * (nIi * 2.0 * nIi + nIi * (nIi - 1) / 2.0 * 2.0 * nIi) + rot_h[N + q] * 12.0 * nIi;
-                std::vector<int> order(nIi);
-                std::iota(order.begin(), order.end(), 0);
-                const double* m = muj.data() + h->off_I[i];
-                std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return m[x] < m[y]; });
-                for (int k = 0; k < h->p[i]; ++k) {
-                    wsrc.push_back(off_ti[i] + (int64_t)order[k] * 2 * nIi + nIi);
-                    wdst.push_back(h->off_zt[i] + (int64_t)k * nIi);
-                    wlen.push_back(nIi);
+    } else {
+        h->d_Zt = dnew<double>(h, h->sum_zt);
+        T* ZtT = nullptr;
+        if constexpr (f64)
+            ZtT = h->d_Zt;
+        else
+            ZtT = C.tnew<T>(h->sum_zt);
+        // full selections: the basis diag(A_II)^{-1/2} keeps every block of E that
+        // touches such a subdomain as sparse as A (its envelope-aware Cholesky and
+        // the coarse solve then skip most tiles); with a kept E (multilevel form)
+        // the A_II-orthonormal rows of L_A^{-1}, so that E is a block-orthogonal
+        // congruence of the one any other A_II-orthonormal basis gives
+        if (h->nC > 0) {
+            std::vector<int64_t> ysrc, ydst;
+            std::vector<int32_t> ylen;
+            for (int i = 0; i < N; ++i) {
+                if (h->p[i] != h->nI[i] || h->p[i] == 0 || diag_basis) continue;
+                for (int k = 0; k < h->nI[i]; ++k) {
+                    ysrc.push_back(h->off_sq[i] + (int64_t)k * h->ni[i]);
+                    ydst.push_back(h->off_zt[i] + (int64_t)k * h->nI[i]);
+                    ylen.push_back(h->nI[i]);
                 }
             }
-            {
-                auto a = C.up(wsrc);
-                auto b = C.up(wdst);
-                auto c = C.up(wlen);
+            if (!ysrc.empty()) {
+                auto a = C.up(ysrc);
+                auto b = C.up(ydst);
+                auto c = C.up(ylen);
                 PScope ps(h, PK_SMALL);
-                launch_gather_rows<T>(TI, a, Wsel, b, c, (int64_t)wsrc.size(), s);
+                launch_gather_rows<T>(Yl, a, ZtT, b, c, (int64_t)ysrc.size(), s);
             }
-        }
-        if (!partial.empty()) {
-            std::vector<GemmDescT<T>> g;
-            for (int i : partial)
-                g.push_back(gd<T>(Wsel + h->off_zt[i], h->nI[i], 0, Yl + h->off_sq[i], h->ni[i], 0,
-                                  ZtT + h->off_zt[i], h->nI[i], h->p[i], h->nI[i], h->nI[i], 1.0, 0.0, 0));
-            gemm(C, g);
-        }
-        // the coarse part is FP64: Z_i rounded to FP64 once, used for E and the apply
-        if constexpr (!f64) launch_convert<float, double>(ZtT, h->d_Zt, h->sum_zt, s);
-        if (diag_basis) {
-            std::vector<DiagBasisDesc> db;
-            int maxn = 1;
-            for (int i = 0; i < N; ++i)
-                if (h->p[i] == h->nI[i] && h->p[i] > 0) {
-                    db.push_back({Araw + h->off_sq[i], h->ni[i], h->d_Zt + h->off_zt[i], h->nI[i]});
-                    maxn = std::max(maxn, h->nI[i]);
+            h->n_partial = (int)partial.size();
+            h->eig_iters.assign(N, -2);
+            T* Wsel = partial.empty() ? nullptr : C.tnew<T>(h->sum_zt);
+            std::vector<int> dense = partial;  // subdomains whose eigenvectors come from the dense Jacobi
+            if (!partial.empty() && (h->eig_solver >= 1 || h->keep_prop)) {
+                dense = learned_eigvecs<T>(C, h, partial, Araw, Lb, TI, off_ti, Wsel);
+            }
+            for (int i : dense) h->eig_iters[i] = -1;
+            if (!dense.empty()) {
+                const std::vector<int>& partial_d = dense;
+                const int np = (int)partial_d.size();
+                std::vector<JacobiDescT<T>> jd(np);
+                std::vector<double*> mp(np);
+                double* mu_j = C.tnew<double>(h->sum_nI);
+                T* nrmE = C.tnew<T>(h->sum_nI);  // row norms of the eigen-Jacobi
+                int maxc = 1;
+                for (int q = 0; q < np; ++q) {
+                    const int i = partial_d[q], nIi = h->nI[i];
+                    jd[q] = {TI + off_ti[i], nIi, 2 * nIi, nIi, 2 * nIi, nrmE + h->off_I[i], nullptr};
+                    mp[q] = mu_j + h->off_I[i];
+                    maxc = std::max(maxc, nIi);
                 }
-            if (!db.empty()) {
-                auto d = C.up(db);
-                PScope ps(h, PK_SMALL);
-                launch_diag_basis(d, (int)db.size(), maxn, s);
+                JacobiDescT<T>* djd = C.up(jd);
+                double* const* dmp = C.up(mp);
+                {
+                    PScope ps(h, PK_JAC_EIG);
+                    const T tol = (f64 ? T(2) : T(8)) * std::sqrt((T)maxc) * std::numeric_limits<T>::epsilon();
+                    run_jacobi<T>(h, jd, djd, h->max_sweeps, tol, sweeps + N, rots + N, f64 ? 1 : 0);
+                }
+                {
+                    PScope ps(h, PK_SMALL);
+                    launch_rownorms<T>(djd, np, dmp, (T*)nullptr, 0.0, 0, s);
+                }
+                std::vector<double> muj(h->sum_nI);
+                ck(cudaMemcpyAsync(muj.data(), mu_j, h->sum_nI * sizeof(double), cudaMemcpyDeviceToHost, s));
+                ck(cudaMemcpyAsync(sw.data() + N, sweeps + N, N * sizeof(int), cudaMemcpyDeviceToHost, s));
+                ck(cudaMemcpyAsync(rot_h.data() + N, rots + N, N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+                {
+                    const int e = read_err(h);
+                    if (e) throw Fail{err_status(e)};
+                }
+                std::vector<int64_t> wsrc, wdst;
+                std::vector<int32_t> wlen;
+                for (int q = 0; q < np; ++q) {
+                    const int i = partial_d[q], nIi = h->nI[i];
+                    h->sweeps_eig = std::max(h->sweeps_eig, sw[N + q]);
+                    h->rot_eig += (int64_t)rot_h[N + q];
+                    if (h->prof.on)
+                        h->prof.flops[PK_JAC_EIG] +=
+                            sw[N + q] * (nIi * 2.0 * nIi + nIi * (nIi - 1) / 2.0 * 2.0 * nIi) + rot_h[N + q] * 12.0 * nIi;
+                    std::vector<int> order(nIi);
+                    std::iota(order.begin(), order.end(), 0);
+                    const double* m = muj.data() + h->off_I[i];
+                    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return m[x] < m[y]; });
+                    for (int k = 0; k < h->p[i]; ++k) {
+                        wsrc.push_back(off_ti[i] + (int64_t)order[k] * 2 * nIi + nIi);
+                        wdst.push_back(h->off_zt[i] + (int64_t)k * nIi);
+                        wlen.push_back(nIi);
+                    }
+                }
+                {
+                    auto a = C.up(wsrc);
+                    auto b = C.up(wdst);
+                    auto c = C.up(wlen);
+                    PScope ps(h, PK_SMALL);
+                    launch_gather_rows<T>(TI, a, Wsel, b, c, (int64_t)wsrc.size(), s);
+                }
             }
+            if (!partial.empty()) {
+                std::vector<GemmDescT<T>> g;
+                for (int i : partial)
+                    g.push_back(gd<T>(Wsel + h->off_zt[i], h->nI[i], 0, Yl + h->off_sq[i], h->ni[i], 0,
+                                      ZtT + h->off_zt[i], h->nI[i], h->p[i], h->nI[i], h->nI[i], 1.0, 0.0, 0));
+                gemm(C, g);
+            }
+            // the coarse part is FP64: Z_i rounded to FP64 once, used for E and the apply
+            if constexpr (!f64) launch_convert<float, double>(ZtT, h->d_Zt, h->sum_zt, s);
+            if (diag_basis) fill_diag_zt();
         }
     }
 
-    // ---- (9) coarse matrix E = R_0 A R_0^T (Eq. (two_level_schwarz)), its
-    // Cholesky factor and inverse factor
+    if (!spec_ok) factor_coarse();
     const int64_t nC = h->nC;
-    if (nC > 0) {
-        std::vector<int64_t> off_az(N + 1, 0);
-        for (int i = 0; i < N; ++i) off_az[i + 1] = off_az[i] + (int64_t)h->ni[i] * h->p[i];
-        double* AZ = C.tnew<double>(off_az[N]);
-        h->d_YE = dnew<double>(h, (size_t)nC * nC);  // E, then its Cholesky factor L_E (lower)
-        double* E = h->d_YE;
-        ck(cudaMemsetAsync(E, 0, (size_t)nC * nC * sizeof(double), s));
-        std::vector<GemmDesc> g1, g2;
-        std::vector<DiagScaleDesc> dsd;
-        int max_ni_d = 1;
-        for (int i = 0; i < N; ++i) {
-            if (h->p[i] == 0) continue;
-            const int ni = h->ni[i], nIi = h->nI[i], pi = h->p[i];
-            if (diag_basis && pi == nIi) {
-                // Z_i = diag(A_II)^{-1/2}: AZ_i and E_ii are scalings of A_ii
-                // (the same products as the GEMMs, whose other terms are zeros)
-                dsd.push_back({Araw + h->off_sq[i], ni, nIi, AZ + off_az[i], E + (size_t)h->coff[i] * nC + h->coff[i],
-                               (int64_t)nC});
-                max_ni_d = std::max(max_ni_d, ni);
-                continue;
-            }
-            // AZ_i = A(Omega_i, Omega_Ii) Z_i   (ni x p_i)
-            g1.push_back(gd(Araw + h->off_sq[i], ni, 0, h->d_Zt + h->off_zt[i], nIi, 1, AZ + off_az[i], pi, ni, pi,
-                            nIi, 1.0, 0.0, 0));
-            // E_ii = Z_i^T A_II Z_i
-            g2.push_back(gd(h->d_Zt + h->off_zt[i], nIi, 0, AZ + off_az[i], pi, 0,
-                            E + (size_t)h->coff[i] * nC + h->coff[i], (int)nC, pi, pi, nIi, 1.0, 0.0, 1));
-        }
-        gemm(C, g1);
-        gemm(C, g2);
-        if (!dsd.empty()) {
-            auto d = C.up(dsd);
-            PScope ps(h, PK_SMALL, 0.0, 0.0);
-            launch_diag_scale(d, (int)dsd.size(), max_ni_d, s);
-        }
-        // E_ij (i > j) = sum over g in Omega_Ii cap Omega_j of Z_i[g]^T (A Z_j)[g]
-        std::vector<int32_t> posI(n, -1);
-        for (int i = 0; i < N; ++i)
-            for (int a = 0; a < h->nI[i]; ++a) posI[Il[i][a]] = a;
-        std::vector<std::vector<std::pair<int32_t, int32_t>>> lists;  // per pair
-        std::vector<std::pair<int, int>> pairs;
-        {
-            std::vector<int> slot(N, -1);
-            for (int j = 0; j < N; ++j) {
-                if (h->p[j] == 0) continue;
-                std::fill(slot.begin(), slot.end(), -1);
-                std::vector<int> touched;
-                const int32_t* om = omega.data() + h->off_om[j];
-                for (int ps = 0; ps < h->ni[j]; ++ps) {
-                    const int32_t g = om[ps];
-                    const int i = part[g];
-                    if (i <= j || h->p[i] == 0) continue;
-                    if (slot[i] < 0) {
-                        slot[i] = (int)pairs.size();
-                        pairs.push_back({i, j});
-                        lists.emplace_back();
-                    }
-                    lists[slot[i]].push_back({posI[g], ps});
-                }
-            }
-        }
-        std::vector<int32_t> la, lpos;
-        std::vector<EPairRef> et;
-        for (size_t q = 0; q < pairs.size(); ++q) {
-            const int i = pairs[q].first, j = pairs[q].second;
-            const int64_t lo = (int64_t)la.size();
-            for (auto& e : lists[q]) {
-                la.push_back(e.first);
-                lpos.push_back(e.second);
-            }
-            for (int tr = 0; tr * 32 < h->p[i]; ++tr)
-                for (int tc = 0; tc * 32 < h->p[j]; ++tc) {
-                    EPairRef t;
-                    t.i = i;
-                    t.j = j;
-                    t.list_off = lo;
-                    t.list_len = (int)lists[q].size();
-                    t.tr = tr;
-                    t.tc = tc;
-                    et.push_back(t);
-                }
-        }
-        std::vector<int32_t> nIv(h->nI.begin(), h->nI.end()), pv(h->p.begin(), h->p.end());
-        h->d_zt_off = C.up(std::vector<int64_t>(h->off_zt.begin(), h->off_zt.end() - 1), true);
-        h->d_nI = C.up(nIv, true);
-        h->d_p = C.up(pv, true);
-        h->d_coff = C.up(std::vector<int64_t>(h->coff.begin(), h->coff.end() - 1), true);
-        if (!et.empty()) {
-            auto a = C.up(et);
-            auto b = C.up(la);
-            auto c = C.up(lpos);
-            auto d = C.up(std::vector<int64_t>(off_az.begin(), off_az.end() - 1));
-            double fl = 0.0;
-            for (size_t q = 0; q < pairs.size(); ++q)
-                fl += 2.0 * h->p[pairs[q].first] * h->p[pairs[q].second] * lists[q].size();
-            PScope ps(h, PK_E_ASM, fl);
-            launch_e_offdiag(a, (int)et.size(), b, c, h->d_Zt, h->d_zt_off, h->d_nI, AZ, d, h->d_p, h->d_coff, E, nC,
-                             s);
-        }
-        if (h->keep_E) {
-            // a copy of E for a next level (multilevel form), as a sparse matrix
-            // with the block pattern: every entry of E_ij for i == j or for
-            // subdomains coupled in A (a structural non-zero in
-            // A(Omega_Ii, Omega_Ij)); E holds its lower triangle
-            std::vector<std::vector<int>> adj(N);
-            for (int64_t g = 0; g < n; ++g)
-                for (int64_t k = rp[g]; k < rp[g + 1]; ++k)
-                    if (part[g] != part[ci[k]]) adj[part[g]].push_back(part[ci[k]]);
-            for (int i = 0; i < N; ++i) {
-                adj[i].push_back(i);
-                std::sort(adj[i].begin(), adj[i].end());
-                adj[i].erase(std::unique(adj[i].begin(), adj[i].end()), adj[i].end());
-            }
-            std::vector<int64_t> erp(nC + 1, 0), esrc;
-            std::vector<int32_t> ecol;
-            for (int i = 0; i < N; ++i)
-                for (int k = 0; k < h->p[i]; ++k) {
-                    const int64_t r = h->coff[i] + k;
-                    for (int j : adj[i])
-                        for (int l = 0; l < h->p[j]; ++l) {
-                            const int64_t c = h->coff[j] + l;
-                            ecol.push_back((int32_t)c);
-                            esrc.push_back(std::max(r, c) * nC + std::min(r, c));
-                        }
-                    erp[r + 1] = (int64_t)ecol.size();
-                }
-            h->E_nnz = (int64_t)ecol.size();
-            h->d_E_rowptr = C.up(erp, true);
-            h->d_E_col = C.up(ecol, true);
-            h->d_E_val = dnew<double>(h, h->E_nnz);
-            auto dsrc = C.up(esrc);
-            PScope ps(h, PK_SMALL, 0.0, 16.0 * h->E_nnz);
-            launch_gather_idx64(dsrc, h->E_nnz, E, h->d_E_val, s);
-        }
-        // ---- sparsity graph of E (coarse unknowns in subdomain order): blocks
-        // of subdomains coupled in A (E_ij = Z_i^T A(Omega_Ii, Omega_Ij) Z_j is
-        // exactly zero otherwise); a diagonal-basis block contributes only the
-        // unknowns whose node touches the other subdomain
-        std::vector<std::vector<int>> adjB(N);
-        for (int64_t g = 0; g < n; ++g)
-            for (int64_t q = rp[g]; q < rp[g + 1]; ++q)
-                if (part[g] != part[ci[q]]) adjB[part[g]].push_back(part[ci[q]]);
-        for (int i = 0; i < N; ++i) {
-            adjB[i].push_back(i);
-            std::sort(adjB[i].begin(), adjB[i].end());
-            adjB[i].erase(std::unique(adjB[i].begin(), adjB[i].end()), adjB[i].end());
-        }
-        auto full_diag = [&](int i) { return diag_basis && h->p[i] == h->nI[i] && h->p[i] > 0; };
-        std::vector<std::vector<int32_t>> nbr(nC);
-        for (int i = 0; i < N; ++i) {
-            if (h->p[i] == 0) continue;
-            if (full_diag(i)) {
-                for (int k = 0; k < h->p[i]; ++k) {
-                    const int32_t g = Il[i][k];
-                    auto& L = nbr[h->coff[i] + k];
-                    for (int64_t q = rp[g]; q < rp[g + 1]; ++q) {
-                        const int32_t g2 = ci[q];
-                        const int j = part[g2];
-                        if (h->p[j] == 0) continue;
-                        if (full_diag(j))
-                            L.push_back((int32_t)(h->coff[j] + posI[g2]));
-                        else
-                            for (int l = 0; l < h->p[j]; ++l) L.push_back((int32_t)(h->coff[j] + l));
-                    }
-                }
-            } else {
-                std::vector<int32_t> row;
-                for (int j : adjB[i]) {
-                    if (h->p[j] == 0) continue;
-                    if (!full_diag(j) || j == i) {
-                        for (int l = 0; l < h->p[j]; ++l) row.push_back((int32_t)(h->coff[j] + l));
-                    } else {
-                        for (int l = 0; l < h->nI[j]; ++l) {  // nodes of Omega_Ij touching Omega_Ii
-                            const int32_t g2 = Il[j][l];
-                            for (int64_t q = rp[g2]; q < rp[g2 + 1]; ++q)
-                                if (part[ci[q]] == i) {
-                                    row.push_back((int32_t)(h->coff[j] + l));
-                                    break;
-                                }
-                        }
-                    }
-                }
-                for (int k = 0; k < h->p[i]; ++k) nbr[h->coff[i] + k] = row;
-            }
-        }
-        for (auto& L : nbr) {
-            std::sort(L.begin(), L.end());
-            L.erase(std::unique(L.begin(), L.end()), L.end());
-        }
-        // ---- ordering of the coarse unknowns for the factorisation: reverse
-        // Cuthill-McKee when it cuts the factorisation work (the sum over rows
-        // of (r - first(r))^2) by a fifth or more, else the subdomain order.
-        // E is permuted on the device; the coarse solves gather and scatter
-        // through the order.
-        auto envelope = [&](const std::vector<int32_t>& iperm, const std::vector<int32_t>& perm,
-                            std::vector<int>& env) {
-            env.assign(nC, 0);
-            double work = 0.0;
-            for (int64_t rn = 0; rn < nC; ++rn) {
-                int first = (int)rn;
-                for (int32_t c : nbr[perm[rn]]) first = std::min(first, (int)iperm[c]);
-                env[rn] = first;
-                work += (double)(rn - first) * (double)(rn - first);
-            }
-            return work;
-        };
-        std::vector<int32_t> idp(nC);
-        std::iota(idp.begin(), idp.end(), 0);
-        std::vector<int> env_id, env_rcm;
-        const double prof_id = envelope(idp, idp, env_id);
-        std::vector<int32_t> rperm = rcm_order(nbr);
-        std::vector<int32_t> riperm(nC);
-        for (int64_t q = 0; q < nC; ++q) riperm[rperm[q]] = (int32_t)q;
-        const double prof_rcm = envelope(riperm, rperm, env_rcm);
-        const bool use_rcm = prof_rcm < 0.8 * prof_id;
-        h->env_row = use_rcm ? env_rcm : env_id;
-        h->env_colend.assign(nC, 0);
-        // the factor fills each row's envelope: column c of L_E reaches every
-        // row whose envelope starts at or before c
-        {
-            std::vector<int> mark(nC, 0);
-            for (int64_t r = 0; r < nC; ++r) mark[h->env_row[r]] = std::max(mark[h->env_row[r]], (int)r + 1);
-            int run = 0;
-            for (int64_t c = 0; c < nC; ++c) {
-                run = std::max(run, mark[c]);
-                h->env_colend[c] = std::max(run, (int)c + 1);
-            }
-        }
-        double* linvE = C.tnew<double>((size_t)cdiv(nC, CHOL_NB) * CHOL_NB * CHOL_NB);
-        if (use_rcm) {
-            // E (lower triangle, subdomain order) -> Ep[r][c] = E[perm r][perm c]
-            // (lower triangle); the two nC x nC buffers swap roles
-            h->d_cperm = C.up(rperm, true);
-            h->d_cp = dnew<double>(h, (size_t)MAXB * nC);
-            h->d_ep = dnew<double>(h, (size_t)MAXB * nC);
-            h->d_YEt = dnew<double>(h, (size_t)nC * nC);
-            {
-                PScope ps(h, PK_SMALL, 0.0, 8.0 * (double)nC * nC);
-                launch_sym_permute(E, h->d_YEt, h->d_cperm, nC, s);
-            }
-            std::swap(h->d_YE, h->d_YEt);
-            E = h->d_YE;
-        }
-        if (!h->d_YEt) h->d_YEt = dnew<double>(h, (size_t)nC * nC);
-        chol_batched<double>(C, {CholDesc{E, (int)nC, (int)nC, (int)nC, nullptr, linvE}}, {&h->env_row});
-        // Inverses of the diagonal blocks of L_E (block size cSB): the coarse
-        // solve is then a blocked forward / backward substitution with L_E and
-        // L_E^T, with no inverse of the whole factor.  About eight blocks, at
-        // most 512 wide: each block costs two grid-wide phases per coarse
-        // solve, and its inverse (stored dense) costs SB^3 / 3 FP64
-        // multiply-adds in the setup, so n_C SB^2 / 3 in all.
-        const int SB = std::min<int>(512, std::max<int>(CHOL_NB, cdiv(cdiv(nC, 8), CHOL_NB) * CHOL_NB));
-        const int K = cdiv(nC, SB);
-        h->cSB = SB;
-        h->cK = K;
-        h->d_Yd = dnew<double>(h, (size_t)K * SB * SB);
-        h->d_Ydt = dnew<double>(h, (size_t)K * SB * SB);
-        std::vector<TrtriDesc> tj;
-        std::vector<const double*> ts;
-        std::vector<double*> tdst;
-        std::vector<int> tn, tl;
-        for (int k = 0; k < K; ++k) {
-            const int r0 = k * SB, sb = (int)std::min<int64_t>(SB, nC - r0);
-            tj.push_back({E + (size_t)r0 * nC + r0, h->d_Yd + (size_t)k * SB * SB,
-                          linvE + (size_t)(r0 / CHOL_NB) * CHOL_NB * CHOL_NB, sb, (int)nC, SB});
-            ts.push_back(h->d_Yd + (size_t)k * SB * SB);
-            tdst.push_back(h->d_Ydt + (size_t)k * SB * SB);
-            tn.push_back(sb);
-            tl.push_back(SB);
-        }
-        trtri_batched(C, tj);
-        transpose_batched(C, ts, tdst, tn, tl, tl);
-        transpose_batched<double>(C, {E}, {h->d_YEt}, {(int)nC}, {(int)nC}, {(int)nC});
-    } else {
-        h->d_zt_off = C.up(std::vector<int64_t>(h->off_zt.begin(), h->off_zt.end() - 1), true);
-        h->d_nI = C.up(std::vector<int32_t>(h->nI.begin(), h->nI.end()), true);
-        h->d_p = C.up(std::vector<int32_t>(h->p.begin(), h->p.end()), true);
-        h->d_coff = C.up(std::vector<int64_t>(h->coff.begin(), h->coff.end() - 1), true);
-    }
 
     // ---- (10) apply plan
     {
@@ -3211,6 +3320,10 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         ck(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
         ck(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
         ck(cudaEventCreateWithFlags(&h->ev_far, cudaEventDisableTiming));
+        ck(cudaStreamCreateWithFlags(&h->s3, cudaStreamNonBlocking));
+        ck(cudaStreamCreateWithFlags(&h->s4, cudaStreamNonBlocking));
+        for (cudaEvent_t* e : {&h->ev_panel3, &h->ev_far3, &h->ev_spec_in, &h->ev_spec_done})
+            ck(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         h->n = A->n;
         h->nnz = A->nnz;
         h->N = N;
@@ -3831,10 +3944,14 @@ void amdd_destroy(amdd_handle* h) {
     if (!h) return;
     amdd_destroy(h->next);
     if (h->s2) cudaStreamSynchronize(h->s2);
+    if (h->s3) cudaStreamSynchronize(h->s3);
+    if (h->s4) cudaStreamSynchronize(h->s4);
     cudaStreamSynchronize(h->s);
-    if (h->ev_panel) cudaEventDestroy(h->ev_panel);
-    if (h->ev_far) cudaEventDestroy(h->ev_far);
+    for (cudaEvent_t e : {h->ev_panel, h->ev_far, h->ev_panel3, h->ev_far3, h->ev_spec_in, h->ev_spec_done})
+        if (e) cudaEventDestroy(e);
     if (h->s2) cudaStreamDestroy(h->s2);
+    if (h->s3) cudaStreamDestroy(h->s3);
+    if (h->s4) cudaStreamDestroy(h->s4);
     h->prof.release();
     for (void* p : h->allocs) cudaFreeAsync(p, h->s);
     cudaStreamSynchronize(h->s);

@@ -102,7 +102,9 @@ __global__ void __launch_bounds__((TILE / RM) * (TILE / 4)) gemm_tiles_kernel(co
 template <typename T>
 void launch_gemm(const GemmDescT<T>* d_descs, const TileRef* d_tiles, int ntiles, int tile, cudaStream_t s) {
     if (ntiles <= 0) return;
-    if (tile == 32)
+    if (tile == 16)
+        gemm_tiles_kernel<T, 16, 1><<<ntiles, 64, 0, s>>>(d_descs, d_tiles, ntiles);
+    else if (tile == 32)
         gemm_tiles_kernel<T, 32, 2><<<ntiles, 128, 0, s>>>(d_descs, d_tiles, ntiles);
     else
         gemm_tiles_kernel<T, 64, 4><<<ntiles, 256, 0, s>>>(d_descs, d_tiles, ntiles);
