@@ -438,7 +438,7 @@ def run_amdd(args):
     prof = {}
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
-    its, cond = [], []
+    its, cond, setup_ms, solve_ms = [], [], [], []
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -446,6 +446,8 @@ def run_amdd(args):
         ev[k][1].record(stream)
         its.append(st.iterations)
         cond.append(st.cond_est)
+        setup_ms.append(info.setup_ms)
+        solve_ms.append(st.solve_ms)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -529,6 +531,8 @@ def run_amdd(args):
                               "sweeps_svd_fp32": info.sweeps_svd32, "sweeps_eig_fp32": info.sweeps_eig32,
                               "rotations_svd": info.rotations_svd, "rotations_eig": info.rotations_eig},
                    "oracle_pcg_iterations": base_its, "l2": "flushed (256 MB write) before every timed step",
+                   "setup_ms": statistics.median(setup_ms), "solve_ms": statistics.median(solve_ms),
+                   "setup_solve_note": "wall time of the amdd_setup and amdd_pcg_solve calls (each synchronises)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "form": FORMS[args.precision],
                    "profiling_events_in_timed_region": "dominant kernel class only"},
