@@ -180,6 +180,9 @@ struct amdd_handle {
     std::vector<int> env_colend;  // one past the last non-zero row of each column of L_E
     int* d_env_row = nullptr;
     int32_t* d_cperm = nullptr;  // factorisation order of the coarse unknowns (NULL: subdomain order)
+    double *d_cF = nullptr, *d_cG = nullptr;  // folded coarse solve (CoarseSolveArgs::F, G), NULL: not folded
+    int *d_cfw0 = nullptr, *d_cgw1 = nullptr;
+    int cFW = 0;
     double *d_cp = nullptr, *d_ep = nullptr;  // coarse vectors in that order (MAXB vectors)
     int* d_env_colend = nullptr;
     // eigenvectors of partial selections: 0 dense Jacobi, 1 LOBPCG from random
@@ -1703,6 +1706,9 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         const int64_t nC = h->nC;
         h->d_cperm = nullptr;
         h->d_YEt = nullptr;
+        h->d_cF = h->d_cG = nullptr;
+        h->d_cfw0 = h->d_cgw1 = nullptr;
+        h->cFW = 0;
         if (nC > 0) {
             std::vector<int64_t> off_az(N + 1, 0);
             for (int i = 0; i < N; ++i) off_az[i + 1] = off_az[i] + (int64_t)h->ni[i] * h->p[i];
@@ -1976,6 +1982,44 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             trtri_batched(C, tj);
             transpose_batched(C, ts, tdst, tn, tl, tl);
             transpose_batched<double>(C, {E}, {h->d_YEt}, {(int)nC}, {(int)nC}, {(int)nC});
+            // folded coarse solve: when every block's rows reach back (and its
+            // columns forward) at most SB entries beyond the block, F_k = Yd_k
+            // L(block k, window) and G_k = Ydt_k L^T(block k, window) let each
+            // block be solved in one grid-wide phase per direction
+            {
+                std::vector<int> fw0(K), gw1(K);
+                int FW = 0;
+                for (int k = 0; k < K; ++k) {
+                    const int r0 = k * SB, r1 = (int)std::min<int64_t>(nC, (int64_t)r0 + SB);
+                    int w0 = r0, w1 = r1;
+                    for (int r = r0; r < r1; ++r) {
+                        w0 = std::min(w0, h->env_row[r]);
+                        w1 = std::max(w1, h->env_colend[r]);
+                    }
+                    fw0[k] = w0;
+                    gw1[k] = w1;
+                    FW = std::max(FW, std::max(r0 - w0, w1 - r1));
+                }
+                if (FW > 0 && FW <= SB) {
+                    h->cFW = FW;
+                    h->d_cF = dnew<double>(h, (size_t)K * SB * FW);
+                    h->d_cG = dnew<double>(h, (size_t)K * SB * FW);
+                    std::vector<GemmDesc> gfg;
+                    for (int k = 0; k < K; ++k) {
+                        const int r0 = k * SB, sb = (int)std::min<int64_t>(SB, nC - r0), r1 = r0 + sb;
+                        const int W = r0 - fw0[k], V = gw1[k] - r1;
+                        if (W > 0)
+                            gfg.push_back(gd(h->d_Yd + (size_t)k * SB * SB, SB, 0, h->d_YE + (size_t)r0 * nC + fw0[k],
+                                             (int)nC, 0, h->d_cF + (size_t)k * SB * FW, FW, sb, W, sb, 1.0, 0.0, 0));
+                        if (V > 0)
+                            gfg.push_back(gd(h->d_Ydt + (size_t)k * SB * SB, SB, 0, h->d_YEt + (size_t)r0 * nC + r1,
+                                             (int)nC, 0, h->d_cG + (size_t)k * SB * FW, FW, sb, V, sb, 1.0, 0.0, 0));
+                    }
+                    gemm(C, gfg);
+                    h->d_cfw0 = C.up(fw0, true);
+                    h->d_cgw1 = C.up(gw1, true);
+                }
+            }
         } else {
             h->d_zt_off = C.up(std::vector<int64_t>(h->off_zt.begin(), h->off_zt.end() - 1), true);
             h->d_nI = C.up(std::vector<int32_t>(h->nI.begin(), h->nI.end()), true);
@@ -2618,10 +2662,20 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             if (h->coop_blocks <= 0) throw Fail{AMDD_ERR_CUDA};
             const int SB = h->cSB, K = h->cK;
             double el = 0.0, dl = 0.0;
-            for (int64_t r = 0; r < nC; ++r) el += (double)(r - h->env_row[r]) + (double)(h->env_colend[r] - 1 - r);
+            if (h->cFW == 0)
+                for (int64_t r = 0; r < nC; ++r) el += (double)(r - h->env_row[r]) + (double)(h->env_colend[r] - 1 - r);
             for (int k = 0; k < K; ++k) {
-                const double sb = (double)std::min<int64_t>(SB, nC - (int64_t)k * SB);
+                const int r0 = k * SB, r1 = (int)std::min<int64_t>(nC, (int64_t)r0 + SB);
+                const double sb = (double)(r1 - r0);
                 dl += sb * (sb + 1);
+                if (h->cFW > 0) {  // folded: the dense sb x W and sb x V window blocks F_k, G_k
+                    int w0 = r0, w1 = r1;
+                    for (int r = r0; r < r1; ++r) {
+                        w0 = std::min(w0, h->env_row[r]);
+                        w1 = std::max(w1, h->env_colend[r]);
+                    }
+                    el += sb * (double)((r0 - w0) + (w1 - r1));
+                }
             }
             h->csolve_flops = 2.0 * el + 2.0 * dl;
             h->csolve_bytes = 8.0 * el + 8.0 * dl + 8.0 * 6.0 * nC;
@@ -2702,6 +2756,15 @@ void local_solves(amdd_handle* h, const double* r) {
 // zc = Z e in owner order (d_zc).  Needs nC > 0.
 void inner_coarse_solve(amdd_handle* h);
 
+// the folded form of the coarse solve when the setup built it
+void fold_args(const amdd_handle* h, CoarseSolveArgs& a) {
+    a.F = h->d_cF;
+    a.G = h->d_cG;
+    a.fw0 = h->d_cfw0;
+    a.gw1 = h->d_cgw1;
+    a.FW = h->cFW;
+}
+
 void coarse_correction(amdd_handle* h) {
     cudaStream_t s = h->s;
     const double zt = (double)h->sum_zt;
@@ -2723,6 +2786,7 @@ void coarse_correction(amdd_handle* h) {
         {
             CoarseSolveArgs a{h->d_YE, h->d_YEt, h->d_Yd, h->d_Ydt, h->d_env_row, h->d_env_colend,
                               cin, h->d_ctmp, eout, (int)h->nC, (int)h->nC, h->cSB, h->cK};
+            fold_args(h, a);
             PScope ps(h, PK_CSOLVE, h->csolve_flops, h->csolve_bytes);
             ck(launch_coarse_solve(a, h->coop_blocks, s));
         }
@@ -2950,6 +3014,7 @@ void apply_multi(amdd_handle* h, const double* r, double* z, int nb) {
         }
         CoarseSolveArgs a{h->d_YE, h->d_YEt, h->d_Yd, h->d_Ydt, h->d_env_row, h->d_env_colend,
                           cin, h->d_m_ctmp, eout, (int)h->nC, (int)h->nC, h->cSB, h->cK};
+        fold_args(h, a);
         a.nb = nb;
         a.ldv = h->nC;
         {

@@ -366,6 +366,15 @@ struct CoarseSolveArgs {
     int n, ld, SB, K;
     int nb = 1;            // right-hand sides (c, y, e hold nb vectors ldv apart)
     int64_t ldv = 0;
+    // Folded form (F != NULL), one grid-wide phase per block and direction:
+    //   y_k = Yd_k c_k - F_k y[fw0_k, r0_k),   F_k = Yd_k L(block k, [fw0_k, r0_k))
+    //   e_k = Ydt_k y_k - G_k e[r1_k, gw1_k),  G_k = Ydt_k L^T(block k, [r1_k, gw1_k))
+    // F_k and G_k are SB x FW row-major blocks (K of each); c is not overwritten.
+    const double* F = nullptr;
+    const double* G = nullptr;
+    const int* fw0 = nullptr;
+    const int* gw1 = nullptr;
+    int FW = 0;
 };
 int coarse_solve_blocks();  // cooperative grid size for this device (0 on error)
 cudaError_t launch_coarse_solve(const CoarseSolveArgs& a, int blocks, cudaStream_t s);

@@ -1637,15 +1637,93 @@ __global__ void __launch_bounds__(CSOLVE_THREADS) coarse_solve_kernel(CoarseSolv
     }
 }
 
+template <int NB>
+__global__ void __launch_bounds__(CSOLVE_THREADS) coarse_solve_folded_kernel(CoarseSolveArgs a) {
+    cg::grid_group grid = cg::this_grid();
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const int n = a.n, SB = a.SB, K = a.K, FW = a.FW, nb = NB == 1 ? 1 : a.nb;
+    const int64_t lv = a.ldv;
+    double s[NB];
+    auto store = [&](double* out, int idx) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            if (k >= nb) break;
+            const double v = warp_sum_d(s[k]);
+            if (lane == 0) out[k * lv + idx] = v;
+        }
+    };
+    // forward: y_k = Yd_k c_k - F_k y(window), windows of earlier blocks complete
+    for (int k0 = 0; k0 < K; ++k0) {
+        const int r0 = k0 * SB, sb = min(SB, n - r0);
+        const double* Y = a.Yd + (size_t)k0 * SB * SB;
+        const double* F = a.F + (size_t)k0 * SB * FW;
+        const int w0 = a.fw0[k0], W = r0 - w0;
+        for (int i = gw; i < sb; i += nw) {
+#pragma unroll
+            for (int k = 0; k < NB; ++k) s[k] = 0.0;
+            const double* row = Y + (size_t)i * SB;
+            for (int j = lane; j <= i; j += 32) {
+                const double m = row[j];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (NB == 1 || k < nb) s[k] = fma(m, a.c[k * lv + r0 + j], s[k]);
+            }
+            const double* frow = F + (size_t)i * FW;
+            for (int j = lane; j < W; j += 32) {
+                const double m = frow[j];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (NB == 1 || k < nb) s[k] = fma(-m, a.y[k * lv + w0 + j], s[k]);
+            }
+            store(a.y, r0 + i);
+        }
+        grid.sync();
+    }
+    // backward: e_k = Ydt_k y_k - G_k e(window), windows of later blocks complete
+    for (int k0 = K - 1; k0 >= 0; --k0) {
+        const int r0 = k0 * SB, sb = min(SB, n - r0), r1 = r0 + sb;
+        const double* Yt = a.Ydt + (size_t)k0 * SB * SB;
+        const double* G = a.G + (size_t)k0 * SB * FW;
+        const int V = a.gw1[k0] - r1;
+        for (int i = gw; i < sb; i += nw) {
+#pragma unroll
+            for (int k = 0; k < NB; ++k) s[k] = 0.0;
+            const double* row = Yt + (size_t)i * SB;
+            for (int j = i + lane; j < sb; j += 32) {
+                const double m = row[j];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (NB == 1 || k < nb) s[k] = fma(m, a.y[k * lv + r0 + j], s[k]);
+            }
+            const double* grow = G + (size_t)i * FW;
+            for (int j = lane; j < V; j += 32) {
+                const double m = grow[j];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (NB == 1 || k < nb) s[k] = fma(-m, a.e[k * lv + r1 + j], s[k]);
+            }
+            store(a.e, r0 + i);
+        }
+        if (k0 > 0) grid.sync();
+    }
+}
+
 int coarse_solve_blocks() {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     int per8 = 0;
+    int pf = 0, pf8 = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, coarse_solve_kernel<1>, CSOLVE_THREADS, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per8, coarse_solve_kernel<MAXB>, CSOLVE_THREADS, 0) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per8, coarse_solve_kernel<MAXB>, CSOLVE_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, coarse_solve_folded_kernel<1>, CSOLVE_THREADS, 0) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf8, coarse_solve_folded_kernel<MAXB>, CSOLVE_THREADS, 0) !=
+            cudaSuccess)
         return 0;
-    per = std::min(per, per8);
+    per = std::min(std::min(per, per8), std::min(pf, pf8));
     // one CTA per SM: the grid barriers between phases then take one arrival per SM
     return per >= 1 ? sms : 0;
 }
@@ -1653,7 +1731,9 @@ int coarse_solve_blocks() {
 cudaError_t launch_coarse_solve(const CoarseSolveArgs& a, int blocks, cudaStream_t s) {
     CoarseSolveArgs arg = a;
     void* params[] = {&arg};
-    const void* fn = a.nb == 1 ? (const void*)coarse_solve_kernel<1> : (const void*)coarse_solve_kernel<MAXB>;
+    const void* fn = a.F ? (a.nb == 1 ? (const void*)coarse_solve_folded_kernel<1>
+                                      : (const void*)coarse_solve_folded_kernel<MAXB>)
+                         : (a.nb == 1 ? (const void*)coarse_solve_kernel<1> : (const void*)coarse_solve_kernel<MAXB>);
     return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(CSOLVE_THREADS), params, 0, s);
 }
 
