@@ -69,6 +69,21 @@ def laplace2d(m: int) -> CSR:
     return _csr_from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
 
 
+def disjoint_blocks(m: int, nblocks: int):
+    """nblocks uncoupled copies of the m x m 2D Laplacian, copy b scaled by
+    b + 1, and the partition with one subdomain per copy (returns (A, part)).
+    Every subdomain then has empty overlap and extension sets."""
+    L = laplace2d(m)
+    rows = np.repeat(np.arange(L.n, dtype=np.int64), np.diff(L.rowptr))
+    R, Cc, V = [], [], []
+    for b in range(nblocks):
+        R.append(rows + b * L.n)
+        Cc.append(L.colind.astype(np.int64) + b * L.n)
+        V.append(L.val * (b + 1))
+    A = _csr_from_coo(nblocks * L.n, np.concatenate(R), np.concatenate(Cc), np.concatenate(V))
+    return A, np.repeat(np.arange(nblocks, dtype=np.int32), L.n)
+
+
 def box_partition_2d(m: int, box: int) -> np.ndarray:
     """Partition of the m x m grid of laplace2d into (m/box)^2 square boxes,
     numbered row-major; returns part[node] in [0, N)."""
