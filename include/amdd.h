@@ -107,7 +107,15 @@ typedef struct {
                              rows; 2 block LOBPCG from the learned proposal (needs `proposal`).
                              A LOBPCG result is accepted only if every wanted residual is within
                              the tolerance and its Ritz values match the bisection eigenvalues;
-                             otherwise that subdomain takes the dense path                          */
+                             otherwise that subdomain takes the dense path.
+                             3: matrix-free eigensolve (Sec. 3.2, eq. (invAii)): neither Abar_ii,
+                             its Schur complement nor T_i is formed; block LOBPCG finds the largest
+                             eigenpairs of K_i = L_A^T (Abar_ii^{-1})_II L_A with (Abar_ii^{-1})_II
+                             applied from the SVD of X_i, the block doubling until its last
+                             converged eigenvalue is at most 1/tau.  Needs precision = 0,
+                             eps >= 2^-30 (below that the two terms of eq. (invAii) cancel in FP64
+                             and the eigenvalues near 1/tau lose all accuracy) and
+                             keep_proposal_data = 0; otherwise AMDD_ERR_INVALID                   */
     int32_t keep_proposal_data; /* 1: keep the features and Krylov bases of the partially selected
                              subdomains for amdd_proposal_export                                     */
     const amdd_proposal* proposal; /* the network of eig_solver = 2 (NULL otherwise)                */
@@ -358,7 +366,10 @@ amdd_status amdd_get_subdomain(const amdd_handle* h, int32_t i, int32_t* nI, int
 
 /* The |Omega_Ii| non-zero eigenvalues of eq. (Zi) of subdomain i, descending,
  * into the host array lam[cap]; +inf marks an eps-cluster eigenvalue whose
- * computed reciprocal was not positive.  *count receives |Omega_Ii|. */
+ * computed reciprocal was not positive.  With the matrix-free eigensolve
+ * (eig_solver 3) only the leading eigenvalues it computed are given (every
+ * selected one and at least one at or below 1/tau, unless all were
+ * computed); the rest are NaN.  *count receives |Omega_Ii|. */
 amdd_status amdd_get_eigenvalues(const amdd_handle* h, int32_t i, double* lam, int32_t cap,
                                  int32_t* count);
 

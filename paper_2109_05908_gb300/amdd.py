@@ -175,6 +175,8 @@ def pcg_solve(h: int, b_ptr: int, x_ptr: int, nrhs: int = 1, rtol: float = 1e-8,
 
 
 FORM_ADDITIVE, FORM_DEFLATED, FORM_RAS, FORM_ASM = 0, 1, 2, 3
+# amdd_opts.eig_solver values
+EIG_DENSE, EIG_LOBPCG, EIG_LEARNED, EIG_MATRIX_FREE = 0, 1, 2, 3
 GMRES_MAX_RESTART = 64
 
 

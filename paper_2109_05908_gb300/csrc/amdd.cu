@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <limits>
 #include <memory>
 #include <new>
@@ -752,11 +753,12 @@ void overlap_layers(const int64_t* rp, const int32_t* ci, const std::vector<int3
 // ---------------------------------------------------------------------------
 // Learned warm start and block LOBPCG for the eigenvectors of eq. (Zi)
 // ---------------------------------------------------------------------------
-// Small symmetric positive semi-definite matrices G_q (m_q x m_q, row-major,
-// leading dimension ld_q, at base + off_q) are diagonalised by one-sided
-// Jacobi on the rows of [G_q | I]: the rotated rows of G_q become lambda_j
-// w_j^T, so the row norms are the eigenvalues and the right half holds the
-// eigenvectors w_j as rows.  Returns, per matrix, the eigenvalues ascending
+// Small symmetric semi-definite matrices G_q (of either sign; m_q x m_q,
+// row-major, leading dimension ld_q, at base + off_q) are diagonalised by
+// one-sided Jacobi on the rows of [G_q | I]: the rotated rows of G_q become
+// lambda_j w_j^T, so the row norms are |lambda_j|, the right half holds the
+// eigenvectors w_j as rows and the dot product of the two halves gives the
+// sign.  Returns, per matrix, the eigenvalues ascending
 // (host) and the device offset of each eigenvector row in W.
 template <typename T>
 struct SmallEig {
@@ -820,9 +822,29 @@ SmallEig<T> small_eig(Ctx& C, const T* base, const std::vector<int64_t>& goff, c
         PScope ps(h, PK_SMALL);
         launch_rownorms<T>(djd, nq, dn, (T*)nullptr, 0.0, 0, h->s);
     }
-    std::vector<double> hn(nacc);
+    // signs: at convergence row j of the left half is lambda_j times row j of
+    // the right half (a unit vector), so sign(lambda_j) is that of their dot
+    // product (the row norm alone gives |lambda_j|)
+    double* dots = C.tnew<double>(std::max<int64_t>(nacc, 1));
+    {
+        std::vector<int64_t> ro;
+        std::vector<int32_t> rl;
+        for (int q = 0; q < nq; ++q)
+            for (int r = 0; r < m[q]; ++r) {
+                ro.push_back(out.off[q] + (int64_t)r * 2 * m[q]);
+                rl.push_back(m[q]);
+            }
+        auto a = C.up(ro);
+        auto b = C.up(rl);
+        PScope ps(h, PK_SMALL);
+        launch_half_dots<T>(out.W, a, b, (int64_t)ro.size(), dots, h->s);
+    }
+    std::vector<double> hn(nacc), hd(nacc);
     ck(cudaMemcpyAsync(hn.data(), norms, nacc * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    ck(cudaMemcpyAsync(hd.data(), dots, nacc * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     ck(cudaStreamSynchronize(h->s));
+    for (int64_t t = 0; t < nacc; ++t)
+        if (hd[t] < 0.0) hn[t] = -hn[t];
     out.row.resize(nq);
     out.val.resize(nq);
     nacc = 0;
@@ -936,20 +958,30 @@ std::vector<int> orth_rows(Ctx& C, T* S, const std::vector<int64_t>& soff, const
     return rr;
 }
 
+// An operator applied to blocks of rows: out_q = in_q T_q^T for every matrix
+// q with rows[q] > 0 (in_q, out_q at q * stride, leading dimension ld).
+template <typename T>
+using RowsOp = std::function<void(const T* in, T* out, int ld, int64_t stride, const std::vector<int>& rows)>;
+
 // Block LOBPCG (Knyazev 2001, no preconditioner) for the p_q smallest
 // eigenpairs of the symmetric T_q (n_q x n_q at Tm + toff[q], leading
-// dimension ldt_q), block size k_q, from the initial rows X0_q (k_q x n_q at
-// X0 + xoff[q], leading dimension n_q; overwritten).  Vectors are rows.  Per
-// iteration: residual rows R = T X - diag(theta) X; stop when every wanted
-// residual norm is <= tol; otherwise Rayleigh-Ritz on the orthonormalised
-// rows of [X; R; P] and P = X_new - (X_new X^T) X.  On return the first p_q
-// rows of X0_q are the Ritz vectors and theta_out[q] the Ritz values;
-// iters[q] counts the iterations and ok[q] the convergence.
+// dimension ldt_q, or applied by op when op is given), block size k_q, from
+// the initial rows X0_q (k_q x n_q at X0 + xoff[q], leading dimension n_q;
+// overwritten).  Vectors are rows.  Per iteration: residual rows
+// R = T X - diag(theta) X; stop when every wanted residual norm is
+// <= tol + tol_rel |theta_j| + tol_max max_j |theta_j|; otherwise
+// Rayleigh-Ritz on the orthonormalised rows of [X; R; P] and
+// P = X_new - (X_new X^T) X.  With a threshold sel (not NaN) only the pairs
+// with theta < sel are wanted: see the selection mode below.  On return the
+// first p_q rows of X0_q are the Ritz vectors and theta_out[q] the Ritz
+// values; iters[q] counts the iterations and ok[q] the convergence (2: the
+// block holds fewer than all wanted pairs).
 template <typename T>
 void lobpcg_rows(Ctx& C, const T* Tm, const std::vector<int64_t>& toff, const std::vector<int>& ldt, T* X0,
                  const std::vector<int64_t>& xoff, const std::vector<int>& n, const std::vector<int>& k,
                  const std::vector<int>& p, double tol, int maxit, std::vector<int>& iters, std::vector<char>& ok,
-                 std::vector<std::vector<double>>& theta_out) {
+                 std::vector<std::vector<double>>& theta_out, const RowsOp<T>* op = nullptr, double tol_rel = 0.0,
+                 double tol_max = 0.0, double sel = std::numeric_limits<double>::quiet_NaN()) {
     amdd_handle* h = C.h;
     const int nq = (int)n.size();
     iters.assign(nq, 0);
@@ -1014,12 +1046,16 @@ void lobpcg_rows(Ctx& C, const T* Tm, const std::vector<int64_t>& toff, const st
         std::vector<GemmDescT<T>> g1(nq), g2(nq);
         const int ldg = 3 * maxk;
         for (int q = 0; q < nq; ++q) {
-            g1[q] = gd<T>(S + boff(q, blk3), ld, 0, Tm + toff[q], ldt[q], 0, TS + boff(q, blk3), ld, rs[q], n[q], n[q],
-                          1.0, 0.0, 0);
+            if (!op)
+                g1[q] = gd<T>(S + boff(q, blk3), ld, 0, Tm + toff[q], ldt[q], 0, TS + boff(q, blk3), ld, rs[q], n[q],
+                              n[q], 1.0, 0.0, 0);
             g2[q] = gd<T>(S + boff(q, blk3), ld, 0, TS + boff(q, blk3), ld, 1, G + (int64_t)q * 9 * maxk * maxk, ldg,
                           rs[q], rs[q], n[q], 1.0, 0.0, 0);
         }
-        gemm(C, g1);
+        if (op)
+            (*op)(S, TS, ld, blk3, rs);
+        else
+            gemm(C, g1);
         gemm(C, g2);
         std::vector<int64_t> go(nq);
         std::vector<int> lg(nq, ldg);
@@ -1087,9 +1123,34 @@ void lobpcg_rows(Ctx& C, const T* Tm, const std::vector<int64_t>& toff, const st
         ck(cudaStreamSynchronize(h->s));
         bool any = false;
         for (int q : qs) {
-            double mx = 0.0;
-            for (int j = 0; j < std::min(p[q], kx[q]); ++j) mx = std::max(mx, hr[(size_t)q * maxk + j]);
-            if (mx <= tol && kx[q] >= p[q]) {
+            double thmax = 0.0;
+            for (double t : theta_out[q]) thmax = std::max(thmax, std::fabs(t));
+            const double* rq = hr.data() + (size_t)q * maxk;
+            const std::vector<double>& t = theta_out[q];
+            const int w = std::min(p[q], kx[q]);
+            auto small = [&](int j) { return rq[j] <= tol + tol_rel * std::fabs(t[j]) + tol_max * thmax; };
+            bool conv = kx[q] >= p[q];
+            if (!std::isnan(sel) && w > 0) {
+                // selection mode: the wanted pairs are those with theta < sel.
+                // Ritz values bound the smallest eigenvalues from above, so
+                // theta_{w-1} < sel proves at least w of them: stop, the block is
+                // too small (ok = 2).  Otherwise converge the pairs below sel and
+                // require the first one above it to stay there within its
+                // residual.
+                if (t[w - 1] < sel) {
+                    live[q] = 0;
+                    ok[q] = 2;
+                    iters[q] = it;
+                    continue;
+                }
+                int js = 0;
+                while (t[js] < sel) ++js;
+                conv = t[js] - rq[js] >= sel;
+                for (int j = 0; conv && j < js; ++j) conv = small(j);
+            } else {
+                for (int j = 0; conv && j < w; ++j) conv = small(j);
+            }
+            if (conv) {
                 live[q] = 0;
                 ok[q] = 1;
                 iters[q] = it;
@@ -1169,6 +1230,179 @@ void lobpcg_rows(Ctx& C, const T* Tm, const std::vector<int64_t>& toff, const st
     auto c = C.up(len);
     PScope ps(h, PK_SMALL);
     launch_gather_rows<T>(X, a, X0, b, c, (int64_t)src.size(), h->s);
+}
+
+// Matrix-free eigensolve of eq. (Zi) (Sec. 3.2, eq. (invAii)), FP64.  With
+// C = Sigma^{1/2} V^T the scaled rows of the SVD of X_i (step (2)) and
+// C_I its Omega_Ii columns, eq. (invAii) restricted to Omega_Ii reads
+//   (Abar_ii^{-1})_II = (1/delta) (I - C_I^T diag(1/(sigma + delta)) C_I),
+// the inverse of the Schur complement S of Abar_ii onto Omega_Ii, so the
+// wanted eigenpairs A_II u = lambda S u are the largest of the symmetric
+//   K_i = L_A^T (Abar_ii^{-1})_II L_A,   u = L_A^{-T} y.
+// Block LOBPCG on -K_i applies K_i to a block of rows X as four products,
+// never forming Abar_ii, S or K_i:
+//   Y = X L_A^T;  W = Y C_I^T;  Y -= W diag(1/(sigma+delta)) C_I;  X K_i = (1/delta) Y L_A.
+// The two terms cancel to the working precision over delta, so the caller
+// allows this path only for eps >= 2^-30.  The number of eigenvalues above
+// 1/tau is not known in advance: LOBPCG runs in its selection mode (it
+// converges the pairs above 1/tau and checks that the next one stays below),
+// on a block that starts at max(16, nI/4) rows and doubles, restarted from
+// its best rows, while a Ritz value proves the block too small (Ritz values
+// are lower bounds of the largest eigenvalues) or the block did not
+// converge; a block of nI rows spans everything (its Rayleigh-Ritz step is a
+// dense eigensolve) and ends the search.  Returns per subdomain the computed
+// lambda (descending: the selected ones and the first unselected one, or all)
+// and their Ritz rows y (count x nI at rows[i]).
+void mf_local_eigs(Ctx& C, amdd_handle* h, const double* X1, const std::vector<int64_t>& off_x, const double* sig,
+                   const double* delta, double* Lb, std::vector<std::vector<double>>& lam,
+                   std::vector<double*>& rows, std::vector<int>& its) {
+    cudaStream_t s = h->s;
+    const int N = h->N;
+    lam.assign(N, {});
+    rows.assign(N, nullptr);
+    its.assign(N, -2);
+    std::vector<double> dl(N);
+    ck(cudaMemcpyAsync(dl.data(), delta, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    std::vector<int64_t> oc(N + 1, 0);
+    int maxni = 1;
+    for (int i = 0; i < N; ++i) {
+        oc[i + 1] = oc[i] + (int64_t)h->ni[i] * h->nI[i];
+        maxni = std::max(maxni, h->ni[i]);
+    }
+    double* Cc = C.tnew<double>(std::max<int64_t>(oc[N], 1));
+    double* Bm = C.tnew<double>(std::max<int64_t>(oc[N], 1));
+    {
+        std::vector<MfPrepDesc> pd;
+        std::vector<RowsDesc<double>> zu;
+        for (int i = 0; i < N; ++i) {
+            if (h->nI[i] == 0) continue;
+            pd.push_back({X1 + off_x[i], h->nt[i], h->nG[i] + h->nD[i], h->ni[i], h->nI[i], sig + h->off_om[i],
+                          delta + i, Cc + oc[i], Bm + oc[i]});
+            // L_A (leading nI x nI block of the Cholesky factor of A_ii) enters
+            // full GEMMs: clear the rest of its rows
+            zu.push_back({Lb + h->off_sq[i], h->ni[i], 0, h->nI[i], h->nI[i], i});
+        }
+        if (pd.empty()) return;
+        auto a = C.up(pd);
+        auto b = C.up(zu);
+        PScope ps(h, PK_SMALL);
+        launch_mf_prepare(a, (int)pd.size(), maxni, s);
+        launch_zero_upper<double>(b, (int)zu.size(), h->max_ni, s);
+    }
+    ck(cudaStreamSynchronize(s));
+    std::vector<int> todo, kq(N, 0);
+    double* pbase = nullptr;             // the previous round's block rows
+    std::vector<int64_t> poff(N, 0);     // a subdomain's rows in it
+    std::vector<int> prevn(N, 0);        // of which converged
+    for (int i = 0; i < N; ++i)
+        if (h->nI[i] > 0) {
+            todo.push_back(i);
+            kq[i] = std::min(h->nI[i], std::max(16, h->nI[i] / 4));
+        }
+    const double thr = 1.0 / h->tau;
+    for (int round = 0; !todo.empty(); ++round) {
+        const int nq = (int)todo.size();
+        std::vector<int> n(nq), k(nq), want(nq), m(nq);
+        std::vector<int64_t> xoff(nq + 1, 0), toff(nq, 0);
+        std::vector<int> ldt(nq, 1);
+        int maxk = 1;
+        for (int q = 0; q < nq; ++q) {
+            const int i = todo[q];
+            n[q] = h->nI[i];
+            k[q] = kq[i];
+            want[q] = k[q] == n[q] ? n[q] : k[q] - std::max(2, k[q] / 8);
+            m[q] = std::min(prevn[i], k[q]);
+            xoff[q + 1] = xoff[q] + (int64_t)k[q] * n[q];
+            maxk = std::max(maxk, k[q]);
+        }
+        double* X0 = C.tnew<double>(xoff[nq]);
+        {
+            std::vector<int64_t> src, dst;
+            std::vector<int32_t> len;
+            std::vector<RowsDesc<double>> rd(nq);
+            for (int q = 0; q < nq; ++q) {
+                const int i = todo[q];
+                for (int j = 0; j < m[q]; ++j) {
+                    src.push_back(poff[i] + (int64_t)j * n[q]);
+                    dst.push_back(xoff[q] + (int64_t)j * n[q]);
+                    len.push_back(n[q]);
+                }
+                rd[q] = {X0 + xoff[q], n[q], m[q], k[q], n[q], i};
+            }
+            if (!src.empty()) {
+                auto a = C.up(src);
+                auto b = C.up(dst);
+                auto c = C.up(len);
+                PScope ps(h, PK_SMALL);
+                launch_gather_rows<double>(pbase, a, X0, b, c, (int64_t)src.size(), s);
+            }
+            auto d = C.up(rd);
+            PScope ps(h, PK_SMALL);
+            launch_rng_rows<double>(d, nq, maxk, 0x3A7Full + 0x1000ull * (unsigned long long)round, s);
+        }
+        double* Ybuf = nullptr;
+        double* Wbuf = nullptr;
+        RowsOp<double> op = [&](const double* in, double* out, int ld, int64_t stride, const std::vector<int>& r) {
+            const int64_t wstride = stride / ld * maxni;
+            if (!Ybuf) {
+                Ybuf = C.tnew<double>(nq * stride);
+                Wbuf = C.tnew<double>(nq * wstride);
+            }
+            std::vector<GemmDesc> g1, g2, g3, g4;
+            for (int q = 0; q < nq; ++q) {
+                if (r[q] == 0) continue;
+                const int i = todo[q], ni = h->ni[i], nI = n[q];
+                const double* LA = Lb + h->off_sq[i];
+                double* Y = Ybuf + q * stride;
+                double* W = Wbuf + q * wstride;
+                g1.push_back(gd(in + q * stride, ld, 0, LA, ni, 1, Y, ld, r[q], nI, nI, 1.0, 0.0, 0));
+                g2.push_back(gd(Y, ld, 0, Cc + oc[i], nI, 1, W, maxni, r[q], ni, nI, 1.0, 0.0, 0));
+                g3.push_back(gd(W, maxni, 0, Bm + oc[i], nI, 0, Y, ld, r[q], nI, ni, -1.0, 1.0, 0));
+                g4.push_back(gd(Y, ld, 0, LA, ni, 0, out + q * stride, ld, r[q], nI, nI, -1.0 / dl[i], 0.0, 0));
+            }
+            gemm(C, g1);
+            gemm(C, g2);
+            gemm(C, g3);
+            gemm(C, g4);
+        };
+        std::vector<int> iters;
+        std::vector<char> ok;
+        std::vector<std::vector<double>> th;
+        // residuals to a floor set by the operator's own rounding: the
+        // cancellation in eq. (invAii) leaves about u / eps per product
+        // (K_i is invariant under a scaling of A, and sigma_1 / delta = 1 / eps)
+        const double floor_abs = 1000.0 * 0x1p-53 / h->eps;
+        lobpcg_rows<double>(C, nullptr, toff, ldt, X0, xoff, n, k, want, floor_abs, 100, iters, ok, th, &op, 1e-9, 0.0,
+                            -thr);
+        std::vector<int> next;
+        for (int q = 0; q < nq; ++q) {
+            const int i = todo[q];
+            int got = std::min<int>(want[q], (int)th[q].size());
+            const bool full = k[q] == n[q];
+            const bool enough = ok[q] == 1;
+            h->lob_max = std::max(h->lob_max, iters[q]);
+            h->lob_total += iters[q];
+            if (enough) {  // the selected pairs and the first unselected one
+                int js = 0;
+                while (js < got - 1 && -th[q][js] > thr) ++js;
+                got = js + 1;
+            }
+            if (full || enough) {
+                lam[i].resize(got);
+                for (int j = 0; j < got; ++j) lam[i][j] = -th[q][j];
+                rows[i] = X0 + xoff[q];
+                its[i] = iters[q];
+                ++h->lob_subs;
+            } else {
+                kq[i] = std::min(n[q], 2 * k[q]);
+                poff[i] = xoff[q];
+                prevn[i] = got;  // converged or not, the best rows found so far
+                next.push_back(i);
+            }
+        }
+        pbase = X0;
+        todo = next;
+    }
 }
 
 // MLP forward on n standardised feature rows X (n x 32): Q (n x 16 x 16,
@@ -1631,14 +1865,17 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     double* Araw = C.tnew<double>(h->sum_sq);
     T* Lb = C.tnew<T>(h->sum_sq);
     double* Xp = C.tnew<double>(off_x[N]);
-    TS* M = C.tnew<TS>(off_m[N]);
-    T* TI = C.tnew<T>(off_ti[N]);
-    T* Pb = C.tnew<T>(off_P[N]);
+    // the matrix-free eigensolve (eig_solver 3) forms none of Abar_ii, its
+    // Schur complement or T_i
+    const bool mf = h->eig_solver == 3;
+    TS* M = C.tnew<TS>(mf ? 1 : off_m[N]);
+    T* TI = C.tnew<T>(mf ? 1 : off_ti[N]);
+    T* Pb = C.tnew<T>(mf ? 1 : off_P[N]);
     double* sig = C.tnew<double>(h->sum_ni);
     double* mu = C.tnew<double>(h->sum_nI);
     TS* delta = C.tnew<TS>(N);
     T* linvA = C.tnew<T>(off_la[N]);
-    TS* linvM = C.tnew<TS>(off_lm[N]);
+    TS* linvM = C.tnew<TS>(mf ? 1 : off_lm[N]);
     // sweeps / rotations: [FP64 SVD, FP64 eig, FP32 SVD, FP32 eig] x N
     int* sweeps = C.tnew<int>(4 * N);
     unsigned long long* rots = C.tnew<unsigned long long>(4 * N);
@@ -2158,234 +2395,245 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         launch_rownorms<float>(djd, N, dsp, delta, eps, 1, s);
     }
 
-    // ---- (3) Abar_ii = C^T diag(1/sigma) C + sigma_1 eps I, ordered [G, D, I]
-    {
-        std::vector<GemmDescT<TS>> g(N);
-        std::vector<TS*> mats(N);
-        std::vector<int> nn(N), ld(N);
-        for (int i = 0; i < N; ++i) {
-            const int ni = h->ni[i], nt = h->nt[i];
-            TS* Xi = X1 + off_x[i];
-            g[i] = gd(Xi, nt, 1, Xi, nt, 0, M + off_m[i], nt, nt, nt, ni, 1.0, 0.0, 1);
-            mats[i] = M + off_m[i];
-            nn[i] = nt;
-            ld[i] = nt;
-        }
-        gemm(C, g);
-        auto a = C.up(mats);
-        auto b = C.up(nn);
-        auto c = C.up(ld);
-        PScope ps(h, PK_SMALL);
-        launch_add_diag<TS>(a, b, c, delta, N, h->max_nt, s);
-    }
-
-    // ---- (4) Schur complement of Abar_ii onto Omega_Ii: Cholesky of the
-    // leading [G, D] block (pivot floor sigma_1 eps, the shift of Remark 3.2).
-    constexpr bool f64s = std::is_same<TS, double>::value;
-    int* dbad = C.tnew<int>(N);
-    ck(cudaMemsetAsync(dbad, 0, N * sizeof(int), s));
-    {
-        std::vector<CholDescT<TS>> cd(N);
-        for (int i = 0; i < N; ++i) {
-            const int nt = h->nt[i], nR = h->nG[i] + h->nD[i];
-            cd[i] = {M + off_m[i], nt, nt, nR, delta + i, linvM + off_lm[i], dbad + i};
-        }
-        chol_batched(C, cd);
-    }
-
-    // ---- (5) T = L_A^{-1} S L_A^{-T} (L_A = Cholesky factor of A_II, the
-    // leading block of that of A_ii), appended identity for the rotations.
-    // With an FP64 splitting and FP32 local work, S is rounded to FP32 first.
-    {
-        std::vector<TS*> mats(N);
-        std::vector<int> nn(N), ld(N);
-        std::vector<GemmDescT<T>> g1(N), g2(N);
-        std::vector<TrtriDescT<T>> idd(N);
-        T* Sc = nullptr;
-        if constexpr (!std::is_same<T, TS>::value) Sc = C.tnew<T>(off_P[N]);
-        std::vector<const TS*> csrc(N);
-        std::vector<T*> cdst(N);
-        std::vector<int> cls(N), cld(N);
-        for (int i = 0; i < N; ++i) {
-            const int nIi = h->nI[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], ni = h->ni[i];
-            TS* S = M + off_m[i] + (size_t)nR * nt + nR;
-            mats[i] = S;
-            nn[i] = nIi;
-            ld[i] = nt;
-            const T* Y = Yl + h->off_sq[i];
-            const T* Sl;
-            int lds;
-            if constexpr (std::is_same<T, TS>::value) {
-                Sl = S;
-                lds = nt;
-            } else {
-                Sl = Sc + off_P[i];
-                lds = nIi;
-            }
-            csrc[i] = S;
-            cdst[i] = Sc ? Sc + off_P[i] : nullptr;
-            cls[i] = nt;
-            cld[i] = nIi;
-            g1[i] = gd(Y, ni, 0, Sl, lds, 0, Pb + off_P[i], nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
-            g2[i] = gd(Pb + off_P[i], nIi, 0, Y, ni, 1, TI + off_ti[i], 2 * nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
-            idd[i] = {nullptr, TI + off_ti[i] + nIi, nullptr, nIi, 0, 2 * nIi};
-        }
+    // steps (3)-(6): the splitting, its Schur complement, T_i and its eigenvalues
+    if (!mf) {
+        // ---- (3) Abar_ii = C^T diag(1/sigma) C + sigma_1 eps I, ordered [G, D, I]
         {
+            std::vector<GemmDescT<TS>> g(N);
+            std::vector<TS*> mats(N);
+            std::vector<int> nn(N), ld(N);
+            for (int i = 0; i < N; ++i) {
+                const int ni = h->ni[i], nt = h->nt[i];
+                TS* Xi = X1 + off_x[i];
+                g[i] = gd(Xi, nt, 1, Xi, nt, 0, M + off_m[i], nt, nt, nt, ni, 1.0, 0.0, 1);
+                mats[i] = M + off_m[i];
+                nn[i] = nt;
+                ld[i] = nt;
+            }
+            gemm(C, g);
             auto a = C.up(mats);
             auto b = C.up(nn);
             auto c = C.up(ld);
             PScope ps(h, PK_SMALL);
-            launch_mirror_lower<TS>(a, b, c, N, h->max_nt, s);
+            launch_add_diag<TS>(a, b, c, delta, N, h->max_nt, s);
         }
-        if constexpr (!std::is_same<T, TS>::value) {
-            auto a = C.up(csrc);
-            auto b = C.up(cls);
-            auto c = C.up(cdst);
-            auto d = C.up(cld);
-            auto e = C.up(nn);
-            PScope ps(h, PK_SMALL);
-            launch_convert_blocks<TS, T>(a, b, c, d, e, N, h->max_nt, s);
-        }
-        gemm(C, g1);
-        gemm(C, g2);
-        auto di = C.up(idd);
-        PScope ps(h, PK_SMALL);
-        launch_set_identity<T>(di, N, h->max_nt, s);
-    }
 
-    // ---- (5b) robust Schur complement for the subdomains whose clamped
-    // Cholesky was flagged.  With C = Sigma^{1/2} V^T = [C_R | C_I] (the scaled
-    // rows of step (2), columns [G, D | I]) and Abar = C^T C + delta I, the
-    // push-through identity gives the Schur complement onto Omega_Ii as
-    //   S = delta (I + C_I^T (C_R C_R^T + delta I)^{-1} C_I).
-    // C_R C_R^T + delta I = Q^T diag(s_k^2 + delta) Q comes from a one-sided
-    // Jacobi of the rows of C_R (no Gram matrix is formed, so the shift is
-    // never swamped by rounding), W = diag(1 / sqrt(s^2 + delta)) Q C_I and
-    //   T = L_A^{-1} S L_A^{-T} = delta (L_A^{-1} L_A^{-T} + P^T P),  P = W L_A^{-T},
-    // a sum of positive semidefinite terms.
-    {
-        std::vector<int> bad(N);
-        std::vector<TS> dl(N);
-        ck(cudaMemcpyAsync(bad.data(), dbad, N * sizeof(int), cudaMemcpyDeviceToHost, s));
-        ck(cudaMemcpyAsync(dl.data(), delta, N * sizeof(TS), cudaMemcpyDeviceToHost, s));
-        ck(cudaStreamSynchronize(s));
-        std::vector<int> F;
-        for (int i = 0; i < N; ++i)
-            if (bad[i] && h->nG[i] + h->nD[i] > 0) F.push_back(i);
-        h->n_robust = (int)F.size();
-        if (!F.empty()) {
-            const int nf = (int)F.size();
-            std::vector<int64_t> oj(nf + 1, 0), ow(nf + 1, 0);
-            for (int q = 0; q < nf; ++q) {
-                const int i = F[q];
-                oj[q + 1] = oj[q] + (int64_t)h->ni[i] * (h->nG[i] + h->nD[i] + h->ni[i]);
-                ow[q + 1] = ow[q] + (int64_t)h->ni[i] * h->nI[i];
+        // ---- (4) Schur complement of Abar_ii onto Omega_Ii: Cholesky of the
+        // leading [G, D] block (pivot floor sigma_1 eps, the shift of Remark 3.2).
+        constexpr bool f64s = std::is_same<TS, double>::value;
+        int* dbad = C.tnew<int>(N);
+        ck(cudaMemsetAsync(dbad, 0, N * sizeof(int), s));
+        {
+            std::vector<CholDescT<TS>> cd(N);
+            for (int i = 0; i < N; ++i) {
+                const int nt = h->nt[i], nR = h->nG[i] + h->nD[i];
+                cd[i] = {M + off_m[i], nt, nt, nR, delta + i, linvM + off_lm[i], dbad + i};
             }
-            TS* J = C.tnew<TS>(oj[nf]);
-            TS* W = C.tnew<TS>(ow[nf]);
-            TS* nrm = C.tnew<TS>(h->sum_ni);
-            std::vector<KjacDesc<TS>> kd(nf);
-            std::vector<JacobiDescT<TS>> jd(nf);
-            int maxr = 1, maxc = 1;
-            for (int q = 0; q < nf; ++q) {
-                const int i = F[q], ni = h->ni[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], lj = nR + ni;
-                kd[q] = {X1 + off_x[i], J + oj[q], ni, nR, nt, lj, delta + i};
-                jd[q] = {J + oj[q], ni, lj, nR, lj, nrm + h->off_om[i], nullptr};
-                maxr = std::max(maxr, ni);
-                maxc = std::max(maxc, nR);
+            chol_batched(C, cd);
+        }
+
+        // ---- (5) T = L_A^{-1} S L_A^{-T} (L_A = Cholesky factor of A_II, the
+        // leading block of that of A_ii), appended identity for the rotations.
+        // With an FP64 splitting and FP32 local work, S is rounded to FP32 first.
+        {
+            std::vector<TS*> mats(N);
+            std::vector<int> nn(N), ld(N);
+            std::vector<GemmDescT<T>> g1(N), g2(N);
+            std::vector<TrtriDescT<T>> idd(N);
+            T* Sc = nullptr;
+            if constexpr (!std::is_same<T, TS>::value) Sc = C.tnew<T>(off_P[N]);
+            std::vector<const TS*> csrc(N);
+            std::vector<T*> cdst(N);
+            std::vector<int> cls(N), cld(N);
+            for (int i = 0; i < N; ++i) {
+                const int nIi = h->nI[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], ni = h->ni[i];
+                TS* S = M + off_m[i] + (size_t)nR * nt + nR;
+                mats[i] = S;
+                nn[i] = nIi;
+                ld[i] = nt;
+                const T* Y = Yl + h->off_sq[i];
+                const T* Sl;
+                int lds;
+                if constexpr (std::is_same<T, TS>::value) {
+                    Sl = S;
+                    lds = nt;
+                } else {
+                    Sl = Sc + off_P[i];
+                    lds = nIi;
+                }
+                csrc[i] = S;
+                cdst[i] = Sc ? Sc + off_P[i] : nullptr;
+                cls[i] = nt;
+                cld[i] = nIi;
+                g1[i] = gd(Y, ni, 0, Sl, lds, 0, Pb + off_P[i], nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
+                g2[i] = gd(Pb + off_P[i], nIi, 0, Y, ni, 1, TI + off_ti[i], 2 * nIi, nIi, nIi, nIi, 1.0, 0.0, 0);
+                idd[i] = {nullptr, TI + off_ti[i] + nIi, nullptr, nIi, 0, 2 * nIi};
             }
-            // no rotation for |<p,q>| <= tol * delta: such rows are resolved to
-            // the accuracy of K = C_R C_R^T + delta I already
-            std::vector<TS> kfl(nf);
-            const TS tol = (f64s ? TS(2) : TS(8)) * std::sqrt((TS)maxc) * std::numeric_limits<TS>::epsilon();
-            for (int q = 0; q < nf; ++q) kfl[q] = tol * dl[F[q]];
-            TS* dkfl = C.up(kfl);
-            for (int q = 0; q < nf; ++q) jd[q].absfloor = dkfl + q;
-            auto dkd = C.up(kd);
-            JacobiDescT<TS>* djd = C.up(jd);
-            int* rsw = C.tnew<int>(nf);
-            unsigned long long* rrot = C.tnew<unsigned long long>(nf);
             {
+                auto a = C.up(mats);
+                auto b = C.up(nn);
+                auto c = C.up(ld);
                 PScope ps(h, PK_SMALL);
-                launch_build_kjac<TS>(dkd, nf, maxr, s);
+                launch_mirror_lower<TS>(a, b, c, N, h->max_nt, s);
             }
-            {
-                PScope ps(h, pk<TS>(PK_JAC_SVD, PK_JAC_F32));
-                run_jacobi<TS>(h, jd, djd, h->max_sweeps, tol, rsw, rrot, f64s ? 1 : 0);
-            }
-            {
+            if constexpr (!std::is_same<T, TS>::value) {
+                auto a = C.up(csrc);
+                auto b = C.up(cls);
+                auto c = C.up(cdst);
+                auto d = C.up(cld);
+                auto e = C.up(nn);
                 PScope ps(h, PK_SMALL);
-                launch_kjac_scale<TS>(dkd, nf, s);
-            }
-            std::vector<GemmDescT<TS>> gw(nf);
-            for (int q = 0; q < nf; ++q) {
-                const int i = F[q], ni = h->ni[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], nIi = h->nI[i];
-                gw[q] = gd<TS>(J + oj[q] + nR, nR + ni, 0, X1 + off_x[i] + nR, nt, 0, W + ow[q], nIi, ni, nIi, ni,
-                               1.0, 0.0, 0);
-            }
-            gemm(C, gw);
-            T* WT = nullptr;
-            if constexpr (std::is_same<T, TS>::value) {
-                WT = W;
-            } else {
-                WT = C.tnew<T>(ow[nf]);
-                launch_convert<TS, T>(W, WT, ow[nf], s);
-            }
-            T* P = C.tnew<T>(ow[nf]);
-            std::vector<GemmDescT<T>> g1, g2;
-            for (int q = 0; q < nf; ++q) {
-                const int i = F[q], ni = h->ni[i], nIi = h->nI[i];
-                const T* Y = Yl + h->off_sq[i];  // L_A^{-1}: leading nI x nI block of L_i^{-1}
-                const double dv = (double)dl[i];
-                g1.push_back(gd<T>(WT + ow[q], nIi, 0, Y, ni, 1, P + ow[q], nIi, ni, nIi, nIi, 1.0, 0.0, 0));
-                g1.push_back(gd<T>(Y, ni, 0, Y, ni, 1, TI + off_ti[i], 2 * nIi, nIi, nIi, nIi, dv, 0.0, 0));
-                g2.push_back(gd<T>(P + ow[q], nIi, 1, P + ow[q], nIi, 0, TI + off_ti[i], 2 * nIi, nIi, nIi, ni, dv,
-                                   1.0, 0));
+                launch_convert_blocks<TS, T>(a, b, c, d, e, N, h->max_nt, s);
             }
             gemm(C, g1);
             gemm(C, g2);
+            auto di = C.up(idd);
+            PScope ps(h, PK_SMALL);
+            launch_set_identity<T>(di, N, h->max_nt, s);
         }
-    }
 
-    // ---- (6) eigenvalues mu = 1/lambda of eq. (Zi): Householder reduction of
-    // each T_i to tridiagonal form and bisection with Sturm counts (absolute
-    // accuracy O(eps ||T||), like a dense symmetric eigensolver).
-    {
-        T* TD = C.tnew<T>(off_P[N]);
-        T* dd = C.tnew<T>(h->sum_nI);
-        T* ee = C.tnew<T>(h->sum_nI);
-        T* pp = C.tnew<T>(h->sum_nI);
-        std::vector<TridiagDescT<T>> td(N);
-        std::vector<double*> outp(N);
-        std::vector<int> em, ej;
-        em.reserve(h->sum_nI);
-        ej.reserve(h->sum_nI);
-        int maxn = 1;
-        for (int i = 0; i < N; ++i) {
-            const int nIi = h->nI[i];
-            if (nIi > 0)
-                ck(cudaMemcpy2DAsync(TD + off_P[i], nIi * sizeof(T), TI + off_ti[i], 2 * nIi * sizeof(T),
-                                     nIi * sizeof(T), nIi, cudaMemcpyDeviceToDevice, s));
-            td[i] = {TD + off_P[i], nIi, nIi, dd + h->off_I[i], ee + h->off_I[i], pp + h->off_I[i]};
-            outp[i] = mu + h->off_I[i];
-            for (int j = 0; j < nIi; ++j) {
-                em.push_back(i);
-                ej.push_back(j);
-            }
-            maxn = std::max(maxn, nIi);
-        }
-        const TridiagDescT<T>* dtd = C.up(td);
-        auto dem = C.up(em);
-        auto dej = C.up(ej);
-        auto dout = C.up(outp);
+        // ---- (5b) robust Schur complement for the subdomains whose clamped
+        // Cholesky was flagged.  With C = Sigma^{1/2} V^T = [C_R | C_I] (the scaled
+        // rows of step (2), columns [G, D | I]) and Abar = C^T C + delta I, the
+        // push-through identity gives the Schur complement onto Omega_Ii as
+        //   S = delta (I + C_I^T (C_R C_R^T + delta I)^{-1} C_I).
+        // C_R C_R^T + delta I = Q^T diag(s_k^2 + delta) Q comes from a one-sided
+        // Jacobi of the rows of C_R (no Gram matrix is formed, so the shift is
+        // never swamped by rounding), W = diag(1 / sqrt(s^2 + delta)) Q C_I and
+        //   T = L_A^{-1} S L_A^{-T} = delta (L_A^{-1} L_A^{-T} + P^T P),  P = W L_A^{-T},
+        // a sum of positive semidefinite terms.
         {
-            double fl = 0.0;
-            for (int i = 0; i < N; ++i) fl += 8.0 / 3.0 * std::pow((double)h->nI[i], 3);
-            PScope ps(h, pk<T>(PK_TRIDIAG, PK_TRIDIAG_F32), fl);
-            launch_tridiag<T>(dtd, N, maxn, s);
+            std::vector<int> bad(N);
+            std::vector<TS> dl(N);
+            ck(cudaMemcpyAsync(bad.data(), dbad, N * sizeof(int), cudaMemcpyDeviceToHost, s));
+            ck(cudaMemcpyAsync(dl.data(), delta, N * sizeof(TS), cudaMemcpyDeviceToHost, s));
+            ck(cudaStreamSynchronize(s));
+            std::vector<int> F;
+            for (int i = 0; i < N; ++i)
+                if (bad[i] && h->nG[i] + h->nD[i] > 0) F.push_back(i);
+            h->n_robust = (int)F.size();
+            if (!F.empty()) {
+                const int nf = (int)F.size();
+                std::vector<int64_t> oj(nf + 1, 0), ow(nf + 1, 0);
+                for (int q = 0; q < nf; ++q) {
+                    const int i = F[q];
+                    oj[q + 1] = oj[q] + (int64_t)h->ni[i] * (h->nG[i] + h->nD[i] + h->ni[i]);
+                    ow[q + 1] = ow[q] + (int64_t)h->ni[i] * h->nI[i];
+                }
+                TS* J = C.tnew<TS>(oj[nf]);
+                TS* W = C.tnew<TS>(ow[nf]);
+                TS* nrm = C.tnew<TS>(h->sum_ni);
+                std::vector<KjacDesc<TS>> kd(nf);
+                std::vector<JacobiDescT<TS>> jd(nf);
+                int maxr = 1, maxc = 1;
+                for (int q = 0; q < nf; ++q) {
+                    const int i = F[q], ni = h->ni[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], lj = nR + ni;
+                    kd[q] = {X1 + off_x[i], J + oj[q], ni, nR, nt, lj, delta + i};
+                    jd[q] = {J + oj[q], ni, lj, nR, lj, nrm + h->off_om[i], nullptr};
+                    maxr = std::max(maxr, ni);
+                    maxc = std::max(maxc, nR);
+                }
+                // no rotation for |<p,q>| <= tol * delta: such rows are resolved to
+                // the accuracy of K = C_R C_R^T + delta I already
+                std::vector<TS> kfl(nf);
+                const TS tol = (f64s ? TS(2) : TS(8)) * std::sqrt((TS)maxc) * std::numeric_limits<TS>::epsilon();
+                for (int q = 0; q < nf; ++q) kfl[q] = tol * dl[F[q]];
+                TS* dkfl = C.up(kfl);
+                for (int q = 0; q < nf; ++q) jd[q].absfloor = dkfl + q;
+                auto dkd = C.up(kd);
+                JacobiDescT<TS>* djd = C.up(jd);
+                int* rsw = C.tnew<int>(nf);
+                unsigned long long* rrot = C.tnew<unsigned long long>(nf);
+                {
+                    PScope ps(h, PK_SMALL);
+                    launch_build_kjac<TS>(dkd, nf, maxr, s);
+                }
+                {
+                    PScope ps(h, pk<TS>(PK_JAC_SVD, PK_JAC_F32));
+                    run_jacobi<TS>(h, jd, djd, h->max_sweeps, tol, rsw, rrot, f64s ? 1 : 0);
+                }
+                {
+                    PScope ps(h, PK_SMALL);
+                    launch_kjac_scale<TS>(dkd, nf, s);
+                }
+                std::vector<GemmDescT<TS>> gw(nf);
+                for (int q = 0; q < nf; ++q) {
+                    const int i = F[q], ni = h->ni[i], nt = h->nt[i], nR = h->nG[i] + h->nD[i], nIi = h->nI[i];
+                    gw[q] = gd<TS>(J + oj[q] + nR, nR + ni, 0, X1 + off_x[i] + nR, nt, 0, W + ow[q], nIi, ni, nIi, ni,
+                                   1.0, 0.0, 0);
+                }
+                gemm(C, gw);
+                T* WT = nullptr;
+                if constexpr (std::is_same<T, TS>::value) {
+                    WT = W;
+                } else {
+                    WT = C.tnew<T>(ow[nf]);
+                    launch_convert<TS, T>(W, WT, ow[nf], s);
+                }
+                T* P = C.tnew<T>(ow[nf]);
+                std::vector<GemmDescT<T>> g1, g2;
+                for (int q = 0; q < nf; ++q) {
+                    const int i = F[q], ni = h->ni[i], nIi = h->nI[i];
+                    const T* Y = Yl + h->off_sq[i];  // L_A^{-1}: leading nI x nI block of L_i^{-1}
+                    const double dv = (double)dl[i];
+                    g1.push_back(gd<T>(WT + ow[q], nIi, 0, Y, ni, 1, P + ow[q], nIi, ni, nIi, nIi, 1.0, 0.0, 0));
+                    g1.push_back(gd<T>(Y, ni, 0, Y, ni, 1, TI + off_ti[i], 2 * nIi, nIi, nIi, nIi, dv, 0.0, 0));
+                    g2.push_back(gd<T>(P + ow[q], nIi, 1, P + ow[q], nIi, 0, TI + off_ti[i], 2 * nIi, nIi, nIi, ni, dv,
+                                       1.0, 0));
+                }
+                gemm(C, g1);
+                gemm(C, g2);
+            }
         }
-        PScope ps(h, pk<T>(PK_BISECT, PK_BISECT_F32));
-        launch_bisect<T>(dtd, N, dem, dej, (int64_t)em.size(), dout, s);
+
+        // ---- (6) eigenvalues mu = 1/lambda of eq. (Zi): Householder reduction of
+        // each T_i to tridiagonal form and bisection with Sturm counts (absolute
+        // accuracy O(eps ||T||), like a dense symmetric eigensolver).
+        {
+            T* TD = C.tnew<T>(off_P[N]);
+            T* dd = C.tnew<T>(h->sum_nI);
+            T* ee = C.tnew<T>(h->sum_nI);
+            T* pp = C.tnew<T>(h->sum_nI);
+            std::vector<TridiagDescT<T>> td(N);
+            std::vector<double*> outp(N);
+            std::vector<int> em, ej;
+            em.reserve(h->sum_nI);
+            ej.reserve(h->sum_nI);
+            int maxn = 1;
+            for (int i = 0; i < N; ++i) {
+                const int nIi = h->nI[i];
+                if (nIi > 0)
+                    ck(cudaMemcpy2DAsync(TD + off_P[i], nIi * sizeof(T), TI + off_ti[i], 2 * nIi * sizeof(T),
+                                         nIi * sizeof(T), nIi, cudaMemcpyDeviceToDevice, s));
+                td[i] = {TD + off_P[i], nIi, nIi, dd + h->off_I[i], ee + h->off_I[i], pp + h->off_I[i]};
+                outp[i] = mu + h->off_I[i];
+                for (int j = 0; j < nIi; ++j) {
+                    em.push_back(i);
+                    ej.push_back(j);
+                }
+                maxn = std::max(maxn, nIi);
+            }
+            const TridiagDescT<T>* dtd = C.up(td);
+            auto dem = C.up(em);
+            auto dej = C.up(ej);
+            auto dout = C.up(outp);
+            {
+                double fl = 0.0;
+                for (int i = 0; i < N; ++i) fl += 8.0 / 3.0 * std::pow((double)h->nI[i], 3);
+                PScope ps(h, pk<T>(PK_TRIDIAG, PK_TRIDIAG_F32), fl);
+                launch_tridiag<T>(dtd, N, maxn, s);
+            }
+            PScope ps(h, pk<T>(PK_BISECT, PK_BISECT_F32));
+            launch_bisect<T>(dtd, N, dem, dej, (int64_t)em.size(), dout, s);
+        }
+    }  // !mf
+
+    // ---- (6mf) the matrix-free eigensolve of eq. (Zi) through eq. (invAii)
+    std::vector<std::vector<double>> mf_lam;
+    std::vector<double*> mf_rows;
+    std::vector<int> mf_its;
+    if constexpr (f64 && s64) {
+        if (mf) mf_local_eigs(C, h, X1, off_x, sig, delta, Lb, mf_lam, mf_rows, mf_its);
     }
 
     // ---- (7) selection lambda > 1/tau on the host
@@ -2394,7 +2642,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     std::vector<unsigned long long> rot_h(4 * N);
     h->sigma_h.resize(h->sum_ni);
     ck(cudaMemcpyAsync(rot_h.data(), rots, 4 * N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    ck(cudaMemcpyAsync(mu_h.data(), mu, h->sum_nI * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (!mf) ck(cudaMemcpyAsync(mu_h.data(), mu, h->sum_nI * sizeof(double), cudaMemcpyDeviceToHost, s));
     ck(cudaMemcpyAsync(h->sigma_h.data(), sig, h->sum_ni * sizeof(double), cudaMemcpyDeviceToHost, s));
     ck(cudaMemcpyAsync(sw.data(), sweeps, 4 * N * sizeof(int), cudaMemcpyDeviceToHost, s));
     {
@@ -2423,8 +2671,13 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         const int nIi = h->nI[i];
         int pi = 0;
         for (int j = 0; j < nIi; ++j) {  // mu ascending -> lambda descending
-            const double m = mu_h[h->off_I[i] + j];
-            const double lam = (m > 0.0) ? 1.0 / m : std::numeric_limits<double>::infinity();
+            double lam;
+            if (mf) {  // the computed ones (descending), NaN for the rest
+                lam = j < (int)mf_lam[i].size() ? mf_lam[i][j] : std::numeric_limits<double>::quiet_NaN();
+            } else {
+                const double m = mu_h[h->off_I[i] + j];
+                lam = (m > 0.0) ? 1.0 / m : std::numeric_limits<double>::infinity();
+            }
             h->lam_h[h->off_I[i] + j] = lam;
             if (lam > 1.0 / h->tau) ++pi;
         }
@@ -2455,6 +2708,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     if (spec_ok) {
         h->n_partial = 0;
         h->eig_iters.assign(N, -2);
+        if (mf) h->eig_iters = mf_its;
     } else {
         h->d_Zt = dnew<double>(h, h->sum_zt);
         T* ZtT = nullptr;
@@ -2487,9 +2741,18 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             }
             h->n_partial = (int)partial.size();
             h->eig_iters.assign(N, -2);
+            if (mf) h->eig_iters = mf_its;
             T* Wsel = partial.empty() ? nullptr : C.tnew<T>(h->sum_zt);
             std::vector<int> dense = partial;  // subdomains whose eigenvectors come from the dense Jacobi
-            if (!partial.empty() && (h->eig_solver >= 1 || h->keep_prop)) {
+            if (mf) {
+                // the leading p_i Ritz rows of the matrix-free eigensolve
+                // (descending lambda, contiguous p_i x nI blocks)
+                if constexpr (f64)
+                    for (int i : partial)
+                        ck(cudaMemcpyAsync(Wsel + h->off_zt[i], mf_rows[i], (size_t)h->p[i] * h->nI[i] * sizeof(T),
+                                           cudaMemcpyDeviceToDevice, s));
+                dense.clear();
+            } else if (!partial.empty() && (h->eig_solver >= 1 || h->keep_prop)) {
                 dense = learned_eigvecs<T>(C, h, partial, Araw, Lb, TI, off_ti, Wsel);
             }
             for (int i : dense) h->eig_iters[i] = -1;
@@ -2564,6 +2827,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             if constexpr (!f64) launch_convert<float, double>(ZtT, h->d_Zt, h->sum_zt, s);
             if (diag_basis) fill_diag_zt();
         }
+        if (mf) h->eig_iters = mf_its;
     }
 
     if (!spec_ok) factor_coarse();
@@ -3372,7 +3636,11 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         if (!(o.eps > 0.0) || o.max_sweeps < 1 || o.precision < 0 || o.precision > 2) return AMDD_ERR_INVALID;
         if (o.reserved != 0 || o.keep_coarse_matrix < 0 || o.keep_coarse_matrix > 1) return AMDD_ERR_INVALID;
         if (o.profile_classes >> PK_COUNT) return AMDD_ERR_INVALID;
-        if (o.eig_solver < 0 || o.eig_solver > 2) return AMDD_ERR_INVALID;
+        if (o.eig_solver < 0 || o.eig_solver > 3) return AMDD_ERR_INVALID;
+        // the matrix-free eigensolve: FP64 only, with the shift far enough above
+        // the FP64 rounding for eq. (invAii) not to cancel
+        if (o.eig_solver == 3 && (o.precision != 0 || o.eps < 0x1p-30 || o.keep_proposal_data))
+            return AMDD_ERR_INVALID;
         if (o.eig_solver == 2 &&
             (!o.proposal || !o.proposal->weights || !o.proposal->mean || !o.proposal->sd))
             return AMDD_ERR_INVALID;

@@ -191,6 +191,19 @@ struct DiagScaleDesc {
     int64_t ldE;
 };
 void launch_diag_scale(const DiagScaleDesc* d, int nmat, int maxni, cudaStream_t s);
+// Matrix-free local eigensolve (eq. (invAii)): from the scaled rows C =
+// Sigma^{1/2} V^T of the SVD of X_i (ni x nt, leading dimension ld, the
+// Omega_Ii columns from nR on) and the row norms sigma, Cc = C(:, I) and
+// Bm = diag(1 / (sigma + delta)) C(:, I), both ni x nI contiguous.
+struct MfPrepDesc {
+    const double* X1;
+    int ld, nR, ni, nI;
+    const double* sig;    // sigma_j of row j
+    const double* delta;  // sigma_1 eps (one value)
+    double* Cc;
+    double* Bm;
+};
+void launch_mf_prepare(const MfPrepDesc* d, int nmat, int maxni, cudaStream_t s);
 template <typename T>
 void launch_build_kjac(const KjacDesc<T>* d, int nmat, int maxrows, cudaStream_t s);
 template <typename T>
@@ -330,6 +343,9 @@ void launch_rng_rows(const RowsDesc<T>* d, int nmat, int maxrows, unsigned long 
 
 template <typename T>
 void launch_zero_upper(const RowsDesc<T>* d, int nmat, int maxrows, cudaStream_t s);
+// out[t] = dot of the two halves (len[t] entries each) of the row at W + off[t]
+template <typename T>
+void launch_half_dots(const T* W, const int64_t* off, const int32_t* len, int64_t rows, double* out, cudaStream_t s);
 
 template <typename T>
 struct ResidDesc {  // R = TX - diag(theta) X over k rows of n entries; norms of the first `want`

@@ -859,6 +859,23 @@ void launch_diag_scale(const DiagScaleDesc* d, int nmat, int maxni, cudaStream_t
     if (nmat > 0 && maxni > 0) diag_scale_kernel<<<dim3(maxni, nmat), 256, 0, s>>>(d);
 }
 
+__global__ void __launch_bounds__(256) mf_prepare_kernel(const MfPrepDesc* __restrict__ descs) {
+    const MfPrepDesc d = descs[blockIdx.y];
+    const int r = blockIdx.x;
+    if (r >= d.ni) return;
+    const double f = 1.0 / (d.sig[r] + *d.delta);
+    const double* x = d.X1 + (size_t)r * d.ld + d.nR;
+    for (int c = threadIdx.x; c < d.nI; c += blockDim.x) {
+        const double v = x[c];
+        d.Cc[(size_t)r * d.nI + c] = v;
+        d.Bm[(size_t)r * d.nI + c] = v * f;
+    }
+}
+
+void launch_mf_prepare(const MfPrepDesc* d, int nmat, int maxni, cudaStream_t s) {
+    if (nmat > 0 && maxni > 0) mf_prepare_kernel<<<dim3(maxni, nmat), 256, 0, s>>>(d);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) build_kjac_kernel(const KjacDesc<T>* __restrict__ descs) {
     const KjacDesc<T> d = descs[blockIdx.y];

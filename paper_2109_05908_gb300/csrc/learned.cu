@@ -455,6 +455,31 @@ template void launch_scale_rows<double>(const ScaleDesc<double>*, int, int, cuda
 
 // entries above the diagonal of rows [r0, r1) set to zero (a lower factor
 // stored in a matrix whose upper triangle still holds the input)
+// out[t] = sum_c W[off[t] + c] W[off[t] + len[t] + c]: the dot product of the
+// two halves of a row, one warp per row
+template <typename T>
+__global__ void __launch_bounds__(256) half_dots_kernel(const T* __restrict__ W, const int64_t* __restrict__ off,
+                                                        const int32_t* __restrict__ len, int64_t rows,
+                                                        double* __restrict__ out) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= rows) return;  // whole warps
+    const T* a = W + off[t];
+    const int L = len[t];
+    double s = 0.0;
+    for (int c = lane; c < L; c += 32) s = fma((double)a[c], (double)a[L + c], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[t] = s;
+}
+
+template <typename T>
+void launch_half_dots(const T* W, const int64_t* off, const int32_t* len, int64_t rows, double* out, cudaStream_t s) {
+    if (rows > 0) half_dots_kernel<T><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(W, off, len, rows, out);
+}
+template void launch_half_dots<float>(const float*, const int64_t*, const int32_t*, int64_t, double*, cudaStream_t);
+template void launch_half_dots<double>(const double*, const int64_t*, const int32_t*, int64_t, double*, cudaStream_t);
+
 template <typename T>
 __global__ void zero_upper_kernel(const RowsDesc<T>* __restrict__ descs) {
     const RowsDesc<T> d = descs[blockIdx.y];
