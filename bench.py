@@ -259,7 +259,10 @@ def variants(A, torch, np, dev, sp, w, precision, steps=3):
       * three_level: Laplacian 64 x 64, 16 boxes, tau = 0.5; second level on
         E with 2 x 2 groups of boxes, tau2 = 0.5; outer flexible GMRES(30) to
         1e-8 with inner GMRES(30) to 1e-4, against the two-level deflated
-        solve of the same problem (exact coarse Cholesky)."""
+        solve of the same problem (exact coarse Cholesky);
+      * matrix_free_eigensolve: the same Laplacian, setup + PCG with the
+        local eigenproblems solved matrix-free through eq. (invAii), against
+        the dense eigensolve (FP64, eps = 2^-23 for both)."""
     import synth
     from paper_2109_05908_gb300.device import DeviceMatrix
     stream = torch.cuda.current_stream(dev)
@@ -342,6 +345,38 @@ def variants(A, torch, np, dev, sp, w, precision, steps=3):
         "n_C": l1.n_C, "n_C2": l2.n_C, "inner_solves": l1.inner_solves, "inner_iterations": l1.inner_iterations,
         "inner_iterations_max": l1.inner_iterations_max,
         "two_level_ms": ms2, "two_level_iterations": st2.iterations}
+    # matrix-free local eigensolve (Sec. 3.2, eq. (invAii)) against the dense
+    # eigensolve on the same problem, both FP64 with the shift eps = 2^-23
+    try:
+        bm = torch.from_numpy(synth.rhs(M3.n, 0)).to(dev)
+        xm = torch.zeros_like(bm)
+        mf_info = {}
+
+        def mf_solve(solver):
+            def run():
+                xm.zero_()
+                om = A.opts_default()
+                om.precision = 0
+                om.eps = 2.0 ** -23
+                om.eig_solver = solver
+                h = A.setup(dA3.csr, dp3.data_ptr(), N3, 1, tau, om, sp)
+                st = A.pcg_solve(h, bm.data_ptr(), xm.data_ptr(), 1, RTOL, 1000)
+                mf_info[solver] = A.get_info(h)
+                A.destroy(h)
+                return st
+            return run
+
+        msm, stm = timed(mf_solve(A.EIG_MATRIX_FREE))
+        msd, std_ = timed(mf_solve(A.EIG_DENSE))
+        im = mf_info[A.EIG_MATRIX_FREE]
+        out["matrix_free_eigensolve"] = {
+            "workload": f"laplace2d_{m}x{m}_{N3}box_ov1_tau{tau:g}, FP64, eps 2^-23; setup + PCG to 1e-8",
+            "ms": msm, "pcg_iterations": stm.iterations, "true_rel_residual": stm.true_rel_residual,
+            "n_C": im.n_C, "lobpcg_iters_max": im.lobpcg_iters_max, "lobpcg_iters_total": im.lobpcg_iters_total,
+            "dense_eigensolve_ms": msd, "dense_pcg_iterations": std_.iterations,
+            "dense_n_C": mf_info[A.EIG_DENSE].n_C}
+    except Exception as e:  # a variant never costs the main line
+        out["matrix_free_eigensolve"] = {"error": str(e)}
     return out
 
 
