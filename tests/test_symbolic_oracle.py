@@ -3,9 +3,9 @@ forms and a numerical factorisation (CPU):
   * a path (tridiagonal) in natural order: no fill, parent k+1;
   * a star (arrow matrix): hub first fills everything (colcount n - k), hub
     last fills nothing;
-  * the m x m five-point grid in natural order: every row of the factor
-    fills its envelope, nnz(L) = sum_i 1 + min(i, m), and the elimination
-    tree is a chain;
+  * the m x m five-point grid in natural order: every row past the first
+    grid line fills its envelope, nnz(L) = 1 + 2 (m - 1) + (n - m)(m + 1),
+    and the elimination tree is a chain;
   * random sparse SPD matrices: the non-zeros of numpy's Cholesky factor of
     P A P^T (random values, so no cancellation) are the predicted ones."""
 import numpy as np
@@ -39,15 +39,15 @@ def test_star_hub_first_and_last():
 
 
 def test_grid_natural_order_fills_the_row_envelopes():
-    """Row i of the factor fills its envelope [i - m, i] (the fill path
-    through the previous grid line), so nnz(L) = sum_i 1 + min(i, m), and
-    the elimination tree is the chain k -> k + 1."""
+    """A row i >= m of the factor fills its envelope [i - m, i] (through the
+    previous grid line); a row 0 < i < m of the first line keeps only
+    (i, i - 1).  So nnz(L) = 1 + 2 (m - 1) + (n - m)(m + 1), and the
+    elimination tree is the chain k -> k + 1."""
     m = 6
     A = synth.laplace2d(m)
     n = A.n
     parent, cc = SY.eliminate(n, A.rowptr, A.colind, np.arange(n))
-    i = np.arange(n)
-    assert cc.sum() == np.sum(1 + np.minimum(i, m))
+    assert cc.sum() == 1 + 2 * (m - 1) + (n - m) * (m + 1)
     assert np.array_equal(parent, np.r_[np.arange(1, n), -1])
 
 
