@@ -170,6 +170,24 @@ typedef struct {
     int64_t inner_iterations;  /* their total iteration count                  */
 } amdd_info;
 
+/* Symbolic phase of a sparse local Cholesky factorisation, on the host (no
+ * GPU involved): a nested-dissection fill-reducing order of the symmetric
+ * pattern of a HOST CSR graph (n, rowptr[n+1], colind[rowptr[n]]; the
+ * pattern is symmetrised, the diagonal ignored) and the structure of the
+ * Cholesky factor of P A P^T in that order.  Sec. 4.1 uses exact Cholesky
+ * factorisations of the local matrices; a sparse factor in this order is
+ * the same factor of the permuted matrix with far fewer entries than the
+ * dense one.  Sets of at most `leaf` (>= 1) unknowns are not cut further.
+ * Outputs (host arrays of n entries, the last three may be NULL):
+ *   perm[k]      the unknown eliminated k-th (row k of P A P^T is row perm[k]);
+ *   parent[k]    the elimination tree in the new numbering (-1 for a root);
+ *   colcount[k]  entries of column k of the factor, the diagonal included;
+ *   *nnzL        their sum.
+ * AMDD_ERR_INVALID for a malformed graph or leaf < 1; AMDD_ERR_OOM if the
+ * host allocation fails. */
+amdd_status amdd_nd_order(int64_t n, const int64_t* rowptr, const int32_t* colind, int32_t leaf, int32_t* perm,
+                          int32_t* parent, int64_t* colcount, int64_t* nnzL);
+
 /* Fill `o` with the defaults (eps = 2^-52, max_sweeps = 60). */
 amdd_status amdd_opts_default(amdd_opts* o);
 

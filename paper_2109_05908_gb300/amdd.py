@@ -101,6 +101,8 @@ SIGNATURES = {
                                            C.POINTER(C.c_int32)]),
     "amdd_get_coarse_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.POINTER(C.c_int32),
                                         C.POINTER(C.c_int32)]),
+    "amdd_nd_order": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.POINTER(C.c_int64)]),
     "amdd_overlap_sets": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                     C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -248,6 +250,21 @@ def get_coarse_block(h: int, i: int):
         _check(lib().amdd_get_coarse_block(h, i, out.ctypes.data, out.size, C.byref(p), C.byref(nI)),
                "amdd_get_coarse_block")
     return out
+
+
+def nd_order(n, rowptr, colind, leaf: int = 64):
+    """Host-only nested-dissection order and symbolic Cholesky factor of a
+    host CSR pattern; returns (perm, parent, colcount, nnzL)."""
+    import numpy as np
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    perm = np.empty(n, np.int32)
+    parent = np.empty(n, np.int32)
+    cc = np.empty(n, np.int64)
+    nnz = C.c_int64()
+    _check(lib().amdd_nd_order(n, rowptr.ctypes.data, colind.ctypes.data, leaf, perm.ctypes.data, parent.ctypes.data,
+                               cc.ctypes.data, C.byref(nnz)), "amdd_nd_order")
+    return perm, parent, cc, nnz.value
 
 
 def overlap_sets(n, rowptr, colind, part, i: int, overlap: int):
