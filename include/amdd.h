@@ -157,9 +157,10 @@ typedef struct {
     int32_t precision;     /* 0 plain FP64, 1 or 2 mixed (see amdd_opts)     */
     double eps;            /* the eps of the splitting actually used       */
     int32_t n_partial;     /* subdomains whose selection is partial (0 < p_i < |Omega_Ii|) */
-    int32_t lobpcg_subdomains; /* of those, eigenvectors accepted from LOBPCG */
+    int32_t lobpcg_subdomains; /* of those, eigenvectors accepted from LOBPCG (eig_solver 3:
+                                  every subdomain, all solved by the matrix-free LOBPCG) */
     int32_t lobpcg_fallbacks;  /* LOBPCG results rejected (dense path taken)  */
-    int32_t lobpcg_iters_max;  /* largest LOBPCG iteration count             */
+    int32_t lobpcg_iters_max;  /* largest LOBPCG iteration count (eig_solver 3: of one block) */
     int64_t lobpcg_iters_total;/* sum of the LOBPCG iteration counts         */
     int32_t robust_schur;      /* subdomains whose Schur complement of the splitting was
                                   recomputed in the rounding-robust form (the Cholesky of
@@ -339,7 +340,8 @@ amdd_status amdd_proposal_export(const amdd_handle* h, float* feat, float* targe
 
 /* Per-subdomain LOBPCG iteration counts into the host array iters[cap]
  * (cap >= N): >= 0 accepted from LOBPCG, -1 dense path, -2 selection not
- * partial. */
+ * partial.  With eig_solver 3 every subdomain with |Omega_Ii| > 0 has the
+ * iteration count of its last (accepted) block; -2 for an empty one. */
 amdd_status amdd_get_eig_iterations(const amdd_handle* h, int32_t* iters, int32_t cap);
 
 /* The proposal network (no counterpart in the paper), trained on the GPU by
