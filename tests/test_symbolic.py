@@ -8,7 +8,9 @@ on the CPU (no GPU involved):
     natural order's (closed form 1 + 2 (m - 1) + (n - m)(m + 1));
   * on the local matrix of an interior 64 x 64 box with one overlap layer
     (4352 unknowns, the subdomains of the 1M-unknown apply workload) the
-    factor holds under 4 % of the entries of the dense triangle;
+    factor holds under 4 % of the entries of the dense triangle (under 1 %
+    with leaf 16, with under 1e-3 of the dense factorisation work and an
+    elimination tree under 250 levels high);
   * malformed input is rejected."""
 import os
 
@@ -87,6 +89,15 @@ def test_local_matrix_of_the_apply_workload(A):
     _, _, _, nnz = A.nd_order(ni, L.indptr.astype(np.int64), L.indices.astype(np.int32), 64)
     dense = ni * (ni + 1) // 2
     assert nnz < 0.04 * dense, (nnz, dense)
+    # leaf 16: factor entries, factorisation work sum_k colcount_k^2 and the
+    # height of the elimination tree (the depth of a level-scheduled solve)
+    _, parent, cc, nnz16 = A.nd_order(ni, L.indptr.astype(np.int64), L.indices.astype(np.int32), 16)
+    assert nnz16 < 0.01 * dense
+    assert (cc.astype(float) ** 2).sum() < 1e-3 * ni ** 3 / 3
+    depth = np.zeros(ni, np.int64)
+    for k in range(ni - 1, -1, -1):
+        depth[k] = 0 if parent[k] < 0 else depth[parent[k]] + 1
+    assert depth.max() + 1 < 250
 
 
 def test_rejects_malformed(A):
