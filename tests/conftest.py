@@ -8,3 +8,15 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
+
+
+def pytest_collection_modifyitems(config, items):
+    """Every GPU test gets a per-test time limit (thread method: the process
+    ends and releases the device) when pytest-timeout is installed, unless the
+    test sets its own."""
+    if not config.pluginmanager.hasplugin("timeout"):
+        return
+    import pytest
+    for item in items:
+        if item.get_closest_marker("gpu") and not item.get_closest_marker("timeout"):
+            item.add_marker(pytest.mark.timeout(600, method="thread"))
