@@ -122,6 +122,19 @@ typedef struct {
     int32_t keep_coarse_matrix; /* 1: keep a copy of the coarse matrix E (block pattern, see
                              amdd_setup_next_level) for a next level; default 0                     */
     int32_t reserved;     /* must be zero                                                          */
+    double tie_band;      /* eigenvalues of eq. (Zi) within a relative band of the threshold,
+                             |lambda tau - 1| <= tie_band, are counted in amdd_info.n_tied: the
+                             selection lambda > 1/tau of eq. (Zi) is unchanged, but two correct
+                             eigensolvers may disagree on such an eigenvalue; default 1e-10, >= 0 */
+    int32_t use_graphs;   /* 1: amdd_pcg_solve replays its iterations as CUDA graphs, several per
+                             host synchronisation, and stops them on the device once converged
+                             (same arithmetic and results as 0); 0: one launch sequence and one
+                             host synchronisation per iteration; default 1                        */
+    int32_t reserved2;    /* must be zero                                                          */
+    size_t mem_budget;    /* largest number of device bytes the handle may hold at once, setup
+                             temporaries included; an allocation beyond it fails with
+                             AMDD_ERR_OOM before it is made (amdd_info.device_bytes_peak reports
+                             what a setup used); 0 (default): no limit                             */
 } amdd_opts;
 
 typedef struct {
@@ -169,6 +182,10 @@ typedef struct {
     int32_t inner_iterations_max; /* largest inner GMRES iteration count of a coarse solve */
     int64_t inner_solves;      /* coarse solves done by inner GMRES (since setup) */
     int64_t inner_iterations;  /* their total iteration count                  */
+    int32_t n_tied;            /* eigenvalues of eq. (Zi) with |lambda tau - 1| <= tie_band */
+    int32_t reserved;
+    int64_t device_bytes_peak; /* largest device memory the handle has held (bytes) */
+    int64_t graph_solves;      /* PCG solves whose iterations ran as one CUDA graph   */
 } amdd_info;
 
 /* Symbolic phase of a sparse local Cholesky factorisation, on the host (no
@@ -189,7 +206,8 @@ typedef struct {
 amdd_status amdd_nd_order(int64_t n, const int64_t* rowptr, const int32_t* colind, int32_t leaf, int32_t* perm,
                           int32_t* parent, int64_t* colcount, int64_t* nnzL);
 
-/* Fill `o` with the defaults (eps = 2^-52, max_sweeps = 60). */
+/* Fill `o` with the defaults (eps = 2^-52, max_sweeps = 60, tie_band = 1e-10,
+ * use_graphs = 1, everything else 0). */
 amdd_status amdd_opts_default(amdd_opts* o);
 
 /* y = A x (Sec. 1: the operator of A x = b).  A, x (length n) and y
@@ -220,7 +238,8 @@ amdd_status amdd_overlap_sets(int64_t n, const int64_t* rowptr, const int32_t* c
  *   opts     NULL for defaults.
  *   stream   cudaStream_t on which all work of the handle runs (NULL allowed).
  *   out      receives the handle (NULL on failure).
- * Errors: AMDD_ERR_INVALID (sizes, empty subdomain, part out of range),
+ * Errors: AMDD_ERR_INVALID (sizes, empty subdomain, part out of range, a NaN
+ * or an infinity among the values of A),
  * AMDD_ERR_NOT_SPD (non-positive pivot in a local or the coarse Cholesky),
  * AMDD_ERR_EIG_NOCONV, AMDD_ERR_OOM, AMDD_ERR_CUDA. */
 amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_t overlap,
@@ -232,12 +251,16 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
 amdd_status amdd_apply(amdd_handle* h, const double* r, double* z, int32_t nrhs);
 
 /* Preconditioned conjugate gradient on A x = b with M^{-1} of
- * Eq. (two_level_schwarz), for `nrhs` right-hand sides solved one after the
- * other.  b and x are device pointers (nrhs contiguous vectors of length n);
- * x holds the initial guess on entry and the solution on return.  Stops when
- * ||r_k||_2 <= rtol ||b||_2 (recursive residual) or after maxit iterations
- * (AMDD_ERR_NOCONV).  `stats` (host, may be NULL) describes the first
- * right-hand side. */
+ * Eq. (two_level_schwarz), for `nrhs` right-hand sides.  With nrhs > 1 the
+ * right-hand sides are independent PCG iterations advanced together in
+ * batches of up to 8: each batch shares one pass over A per SpMV and one pass
+ * over the local and coarse factors per apply; a right-hand side that has
+ * converged stops updating while the others go on.  b and x are device
+ * pointers (nrhs contiguous vectors of length n); x holds the initial guess
+ * on entry and the solution on return.  Stops when ||r_k||_2 <= rtol ||b||_2
+ * (recursive residual) or after maxit iterations (AMDD_ERR_NOCONV).  A NaN or
+ * an infinity in b or in the initial guess is AMDD_ERR_INVALID.  `stats`
+ * (host, may be NULL) describes the first right-hand side. */
 amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t nrhs,
                            double rtol, int32_t maxit, amdd_stats* stats);
 

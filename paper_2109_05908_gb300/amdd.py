@@ -31,7 +31,8 @@ class amdd_opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("max_sweeps", C.c_int32), ("profile", C.c_int32),
                 ("precision", C.c_int32), ("profile_classes", C.c_uint32), ("eig_solver", C.c_int32),
                 ("keep_proposal_data", C.c_int32), ("proposal", C.POINTER(amdd_proposal)),
-                ("keep_coarse_matrix", C.c_int32), ("reserved", C.c_int32)]
+                ("keep_coarse_matrix", C.c_int32), ("reserved", C.c_int32), ("tie_band", C.c_double),
+                ("use_graphs", C.c_int32), ("reserved2", C.c_int32), ("mem_budget", C.c_size_t)]
 
 
 MLP_NPARAM = 140032
@@ -55,7 +56,8 @@ class amdd_info(C.Structure):
                 ("lobpcg_fallbacks", C.c_int32), ("lobpcg_iters_max", C.c_int32),
                 ("lobpcg_iters_total", C.c_int64), ("robust_schur", C.c_int32), ("levels", C.c_int32),
                 ("inner_iterations_max", C.c_int32),
-                ("inner_solves", C.c_int64), ("inner_iterations", C.c_int64)]
+                ("inner_solves", C.c_int64), ("inner_iterations", C.c_int64), ("n_tied", C.c_int32),
+                ("reserved", C.c_int32), ("device_bytes_peak", C.c_int64), ("graph_solves", C.c_int64)]
 
 
 class AmddError(RuntimeError):

@@ -239,6 +239,7 @@ struct amdd_handle {
     double *d_r = nullptr, *d_z = nullptr, *d_pv = nullptr, *d_q = nullptr, *d_part = nullptr;
     PcgScal* d_sc = nullptr;
     int* d_err = nullptr;
+    int* d_chk = nullptr;  // flag of the non-finite input check
     // host results
     std::vector<double> sigma_h;  // singular values of X_i, descending, at off_om
     std::vector<double> lam_h;    // eigenvalues of eq. (Zi), descending, at off_I
@@ -246,14 +247,39 @@ struct amdd_handle {
     int64_t rot_svd = 0, rot_eig = 0;
     double setup_ms = 0.0;
     std::vector<void*> allocs;
+    // device bytes allocated by the setup (persistent + temporary; nothing is
+    // freed before the setup ends, so the sum is its peak) and the budget
+    size_t bytes_now = 0, bytes_peak = 0, mem_budget = 0;
+    double tie_band = 1e-10;
+    int n_tied = 0;  // eigenvalues with |lambda tau - 1| <= tie_band
+    int use_graphs = 1;
+    // PCG iterations as a CUDA graph (amdd_opts.use_graphs): a device-side
+    // while-loop over one iteration, built on the first solve of a tolerance
+    cudaGraph_t pg_graph = nullptr;
+    cudaGraphExec_t pg_exec = nullptr;
+    double pg_tol2 = -1.0;
+    bool pg_failed = false;  // the runtime could not capture the loop: per-iteration launches
+    double *d_px = nullptr, *d_alog = nullptr, *d_blog = nullptr;
+    int* d_maxit = nullptr;
+    int pg_cap = 0;
+    int64_t graph_solves = 0;  // solves whose iterations ran as the graph
 };
 
 namespace {
+
+// Counts the bytes against the handle's budget (amdd_opts.mem_budget): an
+// allocation past it is AMDD_ERR_OOM before anything is allocated.
+void account(amdd_handle* h, size_t bytes) {
+    if (h->mem_budget && h->bytes_now + bytes > h->mem_budget) throw Fail{AMDD_ERR_OOM};
+    h->bytes_now += bytes;
+    h->bytes_peak = std::max(h->bytes_peak, h->bytes_now);
+}
 
 // Stream-ordered allocation owned by the handle (freed by amdd_destroy).
 template <class T>
 T* dnew(amdd_handle* h, size_t count) {
     void* p = nullptr;
+    account(h, std::max<size_t>(count, 1) * sizeof(T));
     ck(cudaMallocAsync(&p, std::max<size_t>(count, 1) * sizeof(T), h->s));
     h->allocs.push_back(p);
     return static_cast<T*>(p);
@@ -291,6 +317,7 @@ struct Ctx {
     amdd_handle* h;
     std::vector<void*> temps;
     std::vector<std::shared_ptr<void>> keep;
+    size_t tbytes = 0;  // bytes of the temporaries
     explicit Ctx(amdd_handle* hh) : h(hh) {}
     ~Ctx() {
         // work on the other setup streams may still read temporaries (after an error)
@@ -298,12 +325,15 @@ struct Ctx {
         if (h->s3) cudaStreamSynchronize(h->s3);
         if (h->s4) cudaStreamSynchronize(h->s4);
         for (void* p : temps) cudaFreeAsync(p, h->s);
+        h->bytes_now -= std::min(h->bytes_now, tbytes);
     }
     template <class T>
     T* tnew(size_t count) {
         void* p = nullptr;
+        account(h, std::max<size_t>(count, 1) * sizeof(T));
         ck(cudaMallocAsync(&p, std::max<size_t>(count, 1) * sizeof(T), h->s));
         temps.push_back(p);
+        tbytes += std::max<size_t>(count, 1) * sizeof(T);
         return static_cast<T*>(p);
     }
     template <class T>
@@ -597,12 +627,64 @@ void transpose_batched(Ctx& C, const std::vector<const T*>& src, const std::vect
     launch_transpose<T>(a, b, c, d, e, (int)src.size(), maxn, C.h->s);
 }
 
-// One-sided Jacobi on the rows of a batch: the shared-memory-resident block
-// kernel when the two row blocks of the largest matrix fit, else the kernel
-// that keeps the rows in global memory.
+// Block-pair one-sided Jacobi (rows in global memory): the host runs the
+// rounds of each sweep, one launch per round over every matrix still
+// rotating, and drops a matrix after a sweep in which none of its block pairs
+// needed a rotation (sweeps[m] then counts that sweep, as the row kernels
+// do).  A matrix still rotating after max_sweeps keeps sweeps[m] = max_sweeps
+// and, with report_noconv, latches DERR_EIG_NOCONV.
 template <typename T>
-void run_jacobi(amdd_handle* h, const std::vector<JacobiDescT<T>>& jd, const JacobiDescT<T>* djd, int max_sweeps, T tol,
+void jacobi_pairs(Ctx& C, const std::vector<JacobiDescT<T>>& jd, const JacobiDescT<T>* djd, int max_sweeps, T tol,
+                  int* sweeps, unsigned long long* rots, int report_noconv) {
+    amdd_handle* h = C.h;
+    const int nm = (int)jd.size();
+    std::vector<int> nblk(nm), active;
+    auto sw = std::make_shared<std::vector<int>>(nm, max_sweeps);
+    for (int m = 0; m < nm; ++m) {
+        const int b = cdiv(std::max(jd[m].rows, 1), JP_ROWS);
+        nblk[m] = std::max(2, b + (b & 1));
+        if (jd[m].rows >= 2)
+            active.push_back(m);
+        else
+            (*sw)[m] = 1;
+    }
+    int* d_rot = C.tnew<int>(nm);
+    std::vector<int> rot_h(nm);
+    for (int sweep = 0; sweep < max_sweeps && !active.empty(); ++sweep) {
+        std::vector<int4> tasks;
+        int maxb = 2;
+        for (int m : active) {
+            for (int k = 0; k < nblk[m] / 2; ++k) tasks.push_back(make_int4(m, k, nblk[m], 0));
+            maxb = std::max(maxb, nblk[m]);
+        }
+        const int4* dt = C.up(tasks);
+        ck(cudaMemsetAsync(d_rot, 0, nm * sizeof(int), h->s));
+        for (int r = 0; r < maxb - 1; ++r)
+            launch_jacobi_pair_round<T>(djd, dt, (int)tasks.size(), r, tol, d_rot, rots, h->s);
+        ck(cudaGetLastError());
+        ck(cudaMemcpyAsync(rot_h.data(), d_rot, nm * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+        ck(cudaStreamSynchronize(h->s));
+        std::vector<int> still;
+        for (int m : active) {
+            if (rot_h[m])
+                still.push_back(m);
+            else
+                (*sw)[m] = sweep + 1;
+        }
+        active.swap(still);
+    }
+    C.keep.push_back(sw);
+    ck(cudaMemcpyAsync(sweeps, sw->data(), nm * sizeof(int), cudaMemcpyHostToDevice, h->s));
+    if (!active.empty() && report_noconv) launch_or_flag(h->d_err, DERR_EIG_NOCONV, h->s);
+}
+
+// One-sided Jacobi on the rows of a batch: the shared-memory-resident block
+// kernel when the two row blocks of the largest matrix fit, else the
+// block-pair form with the rows in global memory.
+template <typename T>
+void run_jacobi(Ctx& C, const std::vector<JacobiDescT<T>>& jd, const JacobiDescT<T>* djd, int max_sweeps, T tol,
                 int* sweeps, unsigned long long* rots, int report_noconv) {
+    amdd_handle* h = C.h;
     size_t smem8 = 0, smem16 = 0;
     int maxr = 0;
     for (const auto& j : jd) {
@@ -612,7 +694,7 @@ void run_jacobi(amdd_handle* h, const std::vector<JacobiDescT<T>>& jd, const Jac
     }
     if (!launch_jacobi_block<T>(djd, (int)jd.size(), smem8, smem16, maxr, max_sweeps, tol, sweeps, rots, h->d_err,
                                 report_noconv, h->s))
-        launch_jacobi_t<T>(djd, (int)jd.size(), max_sweeps, tol, sweeps, rots, h->d_err, report_noconv, h->s);
+        jacobi_pairs<T>(C, jd, djd, max_sweeps, tol, sweeps, rots, report_noconv);
 }
 
 // FP32 stage of the Jacobi solvers.  For each R x L matrix A_b (FP64, lda),
@@ -674,7 +756,7 @@ void fp32_precondition(Ctx& C, const std::vector<PrecondJob>& jobs, bool floor, 
         for (const auto& j : jobs) fl += (double)j.R * (j.R - 1) / 2 * 2.0 * j.L;
         PScope ps(h, PK_JAC_F32, fl);
         const float tol32 = 8.0f * std::sqrt((float)maxL) * std::numeric_limits<float>::epsilon();
-        run_jacobi<float>(h, jd, djd, max_sweeps32, tol32, sweeps32, rots32, 0);
+        run_jacobi<float>(C, jd, djd, max_sweeps32, tol32, sweeps32, rots32, 0);
     }
     {
         PScope ps(h, PK_SMALL);
@@ -696,6 +778,18 @@ void fp32_precondition(Ctx& C, const std::vector<PrecondJob>& jobs, bool floor, 
     chol_batched(C, ch);
     trtri_batched(C, tr);
     gemm(C, g2);
+}
+
+// true when v[0..cnt) holds only finite values (one read of v, one
+// synchronisation of the handle's stream)
+bool all_finite(amdd_handle* h, const double* v, int64_t cnt) {
+    if (!h->d_chk) h->d_chk = dnew<int>(h, 1);
+    ck(cudaMemsetAsync(h->d_chk, 0, sizeof(int), h->s));
+    launch_nonfinite(v, cnt, h->d_chk, h->s);
+    int f = 0;
+    ck(cudaMemcpyAsync(&f, h->d_chk, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    ck(cudaStreamSynchronize(h->s));
+    return f == 0;
 }
 
 int read_err(amdd_handle* h) {
@@ -815,7 +909,7 @@ SmallEig<T> small_eig(Ctx& C, const T* base, const std::vector<int64_t>& goff, c
     {
         PScope ps(h, PK_JAC_EIG);
         const T tol = (std::is_same<T, double>::value ? T(2) : T(8)) * std::sqrt((T)maxm) * std::numeric_limits<T>::epsilon();
-        run_jacobi<T>(h, jd, djd, h->max_sweeps, tol, sw, rots, 0);
+        run_jacobi<T>(C, jd, djd, h->max_sweeps, tol, sw, rots, 0);
     }
     {
         auto dn = C.up(np);
@@ -1748,6 +1842,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     ck(cudaMemcpyAsync(h->rowptr, A->rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     ck(cudaMemcpyAsync(h->col, A->colind, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     ck(cudaMemcpyAsync(h->val, A->val, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    require(all_finite(h, h->val, nnz));  // a NaN or infinity in A: AMDD_ERR_INVALID
 
     // ---- host copies of the graph and the partition (integer setup, Sec. 2.1)
     std::vector<int64_t> rp(n + 1);
@@ -1765,7 +1860,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         Il[part[g]].push_back((int32_t)g);
     }
     for (int i = 0; i < N; ++i) require(!Il[i].empty());
-    h->spmv_group = (nnz / std::max<int64_t>(n, 1) <= 8) ? 1 : (nnz / std::max<int64_t>(n, 1) <= 24 ? 8 : 32);
+    h->spmv_group = spmv_group_for(n, nnz);
 
     // ---- overlap Omega_Gi (distance 1..ov) and extension Omega_Di (ov+1)
     std::vector<std::vector<int32_t>> Gl(N), Dl(N);
@@ -2366,7 +2461,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         double* const* dsp = C.up(sp);
         {
             PScope ps(h, PK_JAC_SVD);
-            run_jacobi<double>(h, jd, djd, h->max_sweeps,
+            run_jacobi<double>(C, jd, djd, h->max_sweeps,
                                2.0 * std::sqrt((double)maxc) * std::numeric_limits<double>::epsilon(), sweeps, rots, 1);
         }
         PScope ps(h, PK_SMALL);
@@ -2388,7 +2483,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         double* const* dsp = C.up(sp);
         {
             PScope ps(h, PK_JAC_F32);
-            run_jacobi<float>(h, jd, djd, h->max_sweeps,
+            run_jacobi<float>(C, jd, djd, h->max_sweeps,
                               8.0f * std::sqrt((float)maxc) * std::numeric_limits<float>::epsilon(), sweeps, rots, 0);
         }
         PScope ps(h, PK_SMALL);
@@ -2550,7 +2645,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                 }
                 {
                     PScope ps(h, pk<TS>(PK_JAC_SVD, PK_JAC_F32));
-                    run_jacobi<TS>(h, jd, djd, h->max_sweeps, tol, rsw, rrot, f64s ? 1 : 0);
+                    run_jacobi<TS>(C, jd, djd, h->max_sweeps, tol, rsw, rrot, f64s ? 1 : 0);
                 }
                 {
                     PScope ps(h, PK_SMALL);
@@ -2680,6 +2775,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
             }
             h->lam_h[h->off_I[i] + j] = lam;
             if (lam > 1.0 / h->tau) ++pi;
+            if (std::fabs(lam * h->tau - 1.0) <= h->tie_band) ++h->n_tied;
         }
         h->p[i] = pi;
         if (pi > 0 && pi < nIi) partial.push_back(i);
@@ -2775,7 +2871,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                 {
                     PScope ps(h, PK_JAC_EIG);
                     const T tol = (f64 ? T(2) : T(8)) * std::sqrt((T)maxc) * std::numeric_limits<T>::epsilon();
-                    run_jacobi<T>(h, jd, djd, h->max_sweeps, tol, sweeps + N, rots + N, f64 ? 1 : 0);
+                    run_jacobi<T>(C, jd, djd, h->max_sweeps, tol, sweeps + N, rots + N, f64 ? 1 : 0);
                 }
                 {
                     PScope ps(h, PK_SMALL);
@@ -3553,6 +3649,95 @@ void inner_coarse_solve(amdd_handle* h) {
     h->in_max = std::max(h->in_max, g.its);
 }
 
+// Whether single right-hand-side PCG iterations may run as a graph: asked
+// for, no inexact coarse solve on a next level (it synchronises with the
+// host), and no profiling events around the loop's kernel classes.
+bool graph_ok(const amdd_handle* h) {
+    if (!h->use_graphs || h->pg_failed || h->next) return false;
+    if (h->prof.on) {
+        const uint32_t loop = (1u << PK_SPMV) | (1u << PK_GEMV) | (1u << PK_GEMV_F32) | (1u << PK_GATHER_SCATTER) |
+                              (1u << PK_PCG_VEC) | (1u << PK_CSOLVE);
+        if (h->prof.mask & loop) return false;
+    }
+    return true;
+}
+
+// The PCG loop as one graph, built once per handle and tolerance:
+//   while (not converged and iterations < maxit) {
+//       z = M^{-1} r;  rz' = r.z, beta = rz' / rz, rz = rz';  p = z + beta p;
+//       q = A p;  alpha = rz / p.q;  x += alpha p, r -= alpha q;  rr = r.r
+//   }
+// on the handle's vectors (x accumulates in d_px), the condition set on the
+// device after each pass (pcg_loop_cond_kernel), so a whole solve is one
+// graph launch and one synchronisation.  The same kernels in the same order
+// as the per-iteration loop, so the results are the same bits.  Returns false
+// when the runtime cannot capture or instantiate it (the solve then launches
+// iteration by iteration).
+bool pcg_graph(amdd_handle* h, double tol2, int maxit) {
+    if (h->pg_exec && h->pg_tol2 == tol2 && maxit <= h->pg_cap) return true;
+    if (h->pg_exec) cudaGraphExecDestroy(h->pg_exec);
+    if (h->pg_graph) cudaGraphDestroy(h->pg_graph);
+    h->pg_exec = nullptr;
+    h->pg_graph = nullptr;
+    const int64_t n = h->n;
+    cudaStream_t s = h->s;
+    if (maxit > h->pg_cap) {
+        h->pg_cap = std::max(maxit, 1024);
+        h->d_alog = dnew<double>(h, h->pg_cap);
+        h->d_blog = dnew<double>(h, h->pg_cap);
+    }
+    if (!h->d_px) h->d_px = dnew<double>(h, n);
+    if (!h->d_maxit) h->d_maxit = dnew<int>(h, 1);
+    ck(cudaStreamSynchronize(s));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaGraphConditionalHandle loop{};
+    cudaGraphNodeParams cp{};
+    cudaGraphNode_t node = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = loop;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok)
+        ok = cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        bool launched = true;
+        try {
+            apply_one(h, h->d_r, h->d_z);
+            dot_h(h, h->d_r, h->d_z, 1, tol2);
+            launch_pcg_update_p(n, h->d_pv, h->d_z, h->d_sc, s);
+            spmv_h(h, h->d_pv, h->d_q);
+            dot_h(h, h->d_pv, h->d_q, 0, tol2);
+            launch_pcg_update_xr(n, h->d_px, h->d_r, h->d_pv, h->d_q, h->d_sc, h->d_part, s);
+            launch_dot_finalize(h->d_part, h->d_sc, 2, tol2, s);
+            launch_pcg_loop_cond(h->d_sc, h->d_maxit, h->d_alog, h->d_blog, loop, s);
+        } catch (...) {
+            launched = false;
+        }
+        cudaGraph_t body = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &body);
+        ok = launched && e == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (ex) cudaGraphExecDestroy(ex);
+        if (g) cudaGraphDestroy(g);
+        h->pg_failed = true;
+        return false;
+    }
+    h->pg_graph = g;
+    h->pg_exec = ex;
+    h->pg_tol2 = tol2;
+    return true;
+}
+
 amdd_status guard_exc() {
     try {
         throw;
@@ -3577,6 +3762,8 @@ amdd_status amdd_opts_default(amdd_opts* o) {
     std::memset(o, 0, sizeof(*o));
     o->eps = std::ldexp(1.0, -52);
     o->max_sweeps = 60;
+    o->tie_band = 1e-10;
+    o->use_graphs = 1;
     return AMDD_OK;
 }
 
@@ -3585,8 +3772,7 @@ amdd_status amdd_spmv(const amdd_csr* A, const double* x, double* y, void* strea
         return AMDD_ERR_INVALID;
     if (A->n > INT32_MAX) return AMDD_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t per = A->n ? A->nnz / A->n : 0;
-    launch_spmv(A->n, A->rowptr, A->colind, A->val, x, y, per <= 8 ? 1 : (per <= 24 ? 8 : 32), s);
+    launch_spmv(A->n, A->rowptr, A->colind, A->val, x, y, spmv_group_for(A->n, A->nnz), s);
     if (cudaGetLastError() != cudaSuccess) return AMDD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return AMDD_ERR_CUDA;
     return AMDD_OK;
@@ -3635,6 +3821,7 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         o = *opts;
         if (!(o.eps > 0.0) || o.max_sweeps < 1 || o.precision < 0 || o.precision > 2) return AMDD_ERR_INVALID;
         if (o.reserved != 0 || o.keep_coarse_matrix < 0 || o.keep_coarse_matrix > 1) return AMDD_ERR_INVALID;
+        if (!(o.tie_band >= 0.0) || o.use_graphs < 0 || o.use_graphs > 1 || o.reserved2 != 0) return AMDD_ERR_INVALID;
         if (o.profile_classes >> PK_COUNT) return AMDD_ERR_INVALID;
         if (o.eig_solver < 0 || o.eig_solver > 3) return AMDD_ERR_INVALID;
         // the matrix-free eigensolve: FP64 only, with the shift far enough above
@@ -3670,6 +3857,9 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         h->eig_solver = o.eig_solver;
         h->keep_prop = o.keep_proposal_data != 0;
         h->keep_E = o.keep_coarse_matrix;
+        h->tie_band = o.tie_band;
+        h->mem_budget = o.mem_budget;
+        h->use_graphs = o.use_graphs;
         if (o.eig_solver == 2) {
             h->prop = *o.proposal;
             h->have_prop = true;
@@ -3939,6 +4129,8 @@ amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t n
         cudaStream_t s = h->s;
         const int64_t n = h->n;
         const double tol2 = rtol * rtol;
+        // a NaN or infinity in b or in the initial guess: AMDD_ERR_INVALID
+        require(all_finite(h, b, (int64_t)nrhs * n) && all_finite(h, x, (int64_t)nrhs * n));
         if (nrhs > 1) {
             // batched independent solves, MAXB right-hand sides per pass
             std::vector<double> al, be;
@@ -3998,7 +4190,32 @@ amdd_status amdd_pcg_solve(amdd_handle* h, const double* b, double* x, int32_t n
                 ck(cudaMemsetAsync(xk, 0, n * sizeof(double), s));
                 sc.rr = 0.0;
             }
-            if (!conv) {
+            if (!conv && maxit >= 1 && graph_ok(h) && pcg_graph(h, tol2, maxit)) {
+                // p = 0 and rz = 1: the first pass of the loop forms p = z + (r.z / 1) 0 = z
+                // exactly, the direction of the first iteration
+                static const double one = 1.0;
+                ck(cudaMemcpyAsync(h->d_px, xk, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                ck(cudaMemsetAsync(h->d_pv, 0, n * sizeof(double), s));
+                ck(cudaMemcpyAsync(reinterpret_cast<char*>(h->d_sc) + offsetof(PcgScal, rz), &one, sizeof(double),
+                                   cudaMemcpyHostToDevice, s));
+                ck(cudaMemcpyAsync(h->d_maxit, &maxit, sizeof(int), cudaMemcpyHostToDevice, s));
+                ck(cudaGraphLaunch(h->pg_exec, s));
+                ck(cudaMemcpyAsync(xk, h->d_px, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                ck(cudaMemcpyAsync(&sc, h->d_sc, sizeof(PcgScal), cudaMemcpyDeviceToHost, s));
+                ck(cudaStreamSynchronize(s));
+                its = sc.iters;
+                conv = sc.conv != 0;
+                h->graph_solves += 1;
+                if (k == 0 && its > 0) {
+                    al.resize(its);
+                    be.resize(its - 1);
+                    ck(cudaMemcpyAsync(al.data(), h->d_alog, its * sizeof(double), cudaMemcpyDeviceToHost, s));
+                    if (its > 1)
+                        ck(cudaMemcpyAsync(be.data(), h->d_blog, (its - 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                                           s));
+                    ck(cudaStreamSynchronize(s));
+                }
+            } else if (!conv) {
                 apply_one(h, h->d_r, h->d_z);
                 dot_h(h, h->d_r, h->d_z, 4, tol2);
                 ck(cudaMemcpyAsync(h->d_pv, h->d_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -4082,6 +4299,8 @@ amdd_status amdd_gmres_solve(amdd_handle* h, int32_t form, const double* b, doub
     try {
         cudaStream_t s = h->s;
         const int64_t n = h->n;
+        // a NaN or infinity in b or in the initial guess: AMDD_ERR_INVALID
+        require(all_finite(h, b, (int64_t)nrhs * n) && all_finite(h, x, (int64_t)nrhs * n));
         for (int k = 0; k < nrhs; ++k) {
             const double* bk = b + (size_t)k * n;
             double* xk = x + (size_t)k * n;
@@ -4198,6 +4417,9 @@ amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
     info->inner_iterations_max = h->in_max;
     info->inner_solves = h->in_calls;
     info->inner_iterations = h->in_its;
+    info->n_tied = h->n_tied;
+    info->device_bytes_peak = (int64_t)h->bytes_peak;
+    info->graph_solves = h->graph_solves;
     return AMDD_OK;
 }
 
@@ -4286,6 +4508,8 @@ void amdd_destroy(amdd_handle* h) {
     if (h->s3) cudaStreamDestroy(h->s3);
     if (h->s4) cudaStreamDestroy(h->s4);
     h->prof.release();
+    if (h->pg_exec) cudaGraphExecDestroy(h->pg_exec);
+    if (h->pg_graph) cudaGraphDestroy(h->pg_graph);
     for (void* p : h->allocs) cudaFreeAsync(p, h->s);
     cudaStreamSynchronize(h->s);
     delete h;

@@ -138,6 +138,19 @@ void launch_set_identity(const TrtriDescT<T>* d, int nmat, int maxn, cudaStream_
 template <typename T>
 void launch_jacobi_t(const JacobiDescT<T>* d, int nmat, int max_sweeps, T tol, int* sweeps, unsigned long long* rots,
                      int* err, int report_noconv, cudaStream_t s);
+// Block-pair variant for matrices of any size (rows in global memory): one
+// round of the block round-robin schedule (blocks of 32 rows; tasks[t] =
+// {matrix, pair index in the round, blocks of that matrix (even, >= 2), 0});
+// rotated[matrix] is set when a pair of it was rotated, rots[matrix] counts
+// plane rotations.  The host runs the rounds of a sweep and the sweeps.
+constexpr int JP_ROWS = 32;
+template <typename T>
+size_t jacobi_pair_smem();
+template <typename T>
+void launch_jacobi_pair_round(const JacobiDescT<T>* d, const int4* tasks, int ntasks, int round, T tol, int* rotated,
+                              unsigned long long* rots, cudaStream_t s);
+// *p |= bits (one thread)
+void launch_or_flag(int* p, int bits, cudaStream_t s);
 // Shared-memory-resident block variant; returns false (nothing launched) when
 // the two row blocks of the largest matrix do not fit in shared memory.
 constexpr size_t JAC_BLOCK_SMEM_MAX = 220 * 1024;
@@ -243,6 +256,11 @@ void launch_convert_blocks(const Ti* const* src, const int* lds, To* const* dst,
                            int nmat, int maxn, cudaStream_t s);
 
 // ---------------------------------------------------------------- sparse / vectors
+// *flag |= 1 when v[0..n) holds a NaN or an infinity
+void launch_nonfinite(const double* v, int64_t n, int* flag, cudaStream_t s);
+// Lanes per row of launch_spmv for a matrix of n rows and nnz entries: the one
+// choice every SpMV of the library makes, so that equal inputs give equal bits
+int spmv_group_for(int64_t n, int64_t nnz);
 void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
                  double* y, int group, cudaStream_t s);
 void launch_gather_values(const int64_t* src, const int64_t* dst, int64_t cnt, const double* val, double* out,
@@ -413,6 +431,11 @@ void launch_pcg_update_xr(int64_t n, double* x, double* r, const double* p, cons
 void launch_pcg_update_p(int64_t n, double* p, const double* z, const PcgScal* sc, cudaStream_t s, int nb = 1,
                          int64_t ld = 0, int skip_done = 0);
 void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
+// One thread: alog[k-1] = sc->alpha, blog[k-2] = sc->beta (k = sc->iters, entries
+// below *maxit only), then the while-loop condition of the graph that replays
+// PCG iterations: !sc->conv && k < *maxit.
+void launch_pcg_loop_cond(const PcgScal* sc, const int* maxit, double* alog, double* blog,
+                          cudaGraphConditionalHandle loop, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Deflated / restricted additive Schwarz forms and GMRES(m) (Sec. 4.1)

@@ -479,6 +479,258 @@ template void launch_jacobi_t<float>(const JacobiDescT<float>*, int, int, float,
 template void launch_jacobi_t<double>(const JacobiDescT<double>*, int, int, double, int*, unsigned long long*, int*,
                                       int, cudaStream_t);
 
+// ------------------------------------------------------------------ block-pair Jacobi
+// The same one-sided Jacobi for matrices whose rows do not fit in shared
+// memory.  Rows are cut into blocks of JP_B; a sweep meets every two blocks
+// once in a round-robin (circle) schedule, one launch per round for all
+// matrices and all disjoint block pairs of the round.  For a pair (I, J) one
+// CTA
+//   1. forms the Gram matrix G = Y Y^T of the JP_R = 2 JP_B rows
+//      Y = [Y_I; Y_J] over the first ncols_dot columns (columns streamed
+//      through shared memory, 4 x 4 outputs per thread);
+//   2. diagonalises G in shared memory by two-sided cyclic Jacobi with the
+//      rotation, the stopping test and the absolute floor of the row kernel:
+//      in exact arithmetic the two-sided rotation of G is the Gram matrix of
+//      the one-sided rotation of the rows, so the composed rotation Q^T
+//      (accumulated as Qt = Q^T) is what one-sided Jacobi on the pair would
+//      apply;
+//   3. replaces Y by Qt Y over ncols_rot columns (streamed, 2 x 4 outputs per
+//      thread, in place: a chunk is read whole before it is written).
+// A pair whose fresh Gram matrix meets the stopping test (no rotation in the
+// first inner sweep) is left as it is; a matrix is converged when a whole
+// sweep rotates none of its pairs, the test of the row kernel on freshly
+// formed inner products.  Padding rows (beyond `rows`) are zero, never
+// rotated and never written.
+constexpr int JP_B = 32;
+constexpr int JP_R = 2 * JP_B;
+constexpr int JP_KC = 32;             // columns per streamed chunk
+constexpr int JP_LDG = JP_R + 1;      // G and Qt, row-major
+constexpr int JP_LDT = JP_R + 4;      // Gram chunk, [column][row] (16-byte aligned rows)
+constexpr int JP_LDA = JP_KC + 4;     // apply chunk, [row][column]
+constexpr int JP_INNER = 40;          // inner sweep limit
+
+template <typename T>
+size_t jacobi_pair_smem() {
+    const size_t chunk = (size_t)JP_KC * JP_LDT > (size_t)JP_R * JP_LDA ? (size_t)JP_KC * JP_LDT : (size_t)JP_R * JP_LDA;
+    return (2 * (size_t)JP_R * JP_LDG + chunk) * sizeof(T) + 64;
+}
+template size_t jacobi_pair_smem<float>();
+template size_t jacobi_pair_smem<double>();
+
+__device__ __forceinline__ void jp_load4(const float* p, float* v) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+__device__ __forceinline__ void jp_load4(const double* p, double* v) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* __restrict__ descs,
+                                                          const int4* __restrict__ tasks, int round, T tol,
+                                                          int* __restrict__ rotated,
+                                                          unsigned long long* __restrict__ rots) {
+    extern __shared__ __align__(16) unsigned char jp_raw[];
+    T* G = reinterpret_cast<T*>(jp_raw);
+    T* Qt = G + JP_R * JP_LDG;
+    T* Yc = Qt + JP_R * JP_LDG;
+    // rotation of each of the JP_R / 2 disjoint pairs of an inner round
+    __shared__ T r_cs[JP_R / 2], r_sn[JP_R / 2], r_a[JP_R / 2], r_b[JP_R / 2];
+    __shared__ int r_p[JP_R / 2], r_q[JP_R / 2], r_do[JP_R / 2];
+    __shared__ int any_rot;
+    const int4 tk = tasks[blockIdx.x];
+    const int mat = tk.x, kp = tk.y, nblk = tk.z;
+    if (round >= nblk - 1) return;  // uniform over the CTA
+    const JacobiDescT<T> d = descs[mat];
+    int bp, bq;
+    if (kp == 0) {
+        bp = nblk - 1;
+        bq = round;
+    } else {
+        bp = (round + kp) % (nblk - 1);
+        bq = (round - kp + nblk - 1) % (nblk - 1);
+    }
+    const int tid = threadIdx.x;
+    // global row of local row lr, -1 for padding
+    auto grow = [&](int lr) -> int {
+        const int r = (lr < JP_B ? bp : bq) * JP_B + (lr & (JP_B - 1));
+        return r < d.rows ? r : -1;
+    };
+    const T absf = d.absfloor ? *d.absfloor : T(0);
+
+    // ---- 1. Gram matrix over ncols_dot columns
+    {
+        const int ty = tid >> 4, tx = tid & 15;
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        for (int c0 = 0; c0 < d.ncols_dot; c0 += JP_KC) {
+            for (int e = tid; e < JP_R * JP_KC; e += 256) {
+                const int lr = e / JP_KC, kk = e % JP_KC;
+                const int r = grow(lr), c = c0 + kk;
+                Yc[kk * JP_LDT + lr] = (r >= 0 && c < d.ncols_dot) ? __ldcg(d.A + (size_t)r * d.ld + c) : T(0);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < JP_KC; ++kk) {
+                T a[4], b[4];
+                jp_load4(Yc + kk * JP_LDT + 4 * ty, a);
+                jp_load4(Yc + kk * JP_LDT + 4 * tx, b);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) G[(4 * ty + i) * JP_LDG + 4 * tx + j] = acc[i][j];
+        for (int e = tid; e < JP_R * JP_R; e += 256) Qt[(e / JP_R) * JP_LDG + e % JP_R] = (e / JP_R == e % JP_R) ? T(1) : T(0);
+        __syncthreads();
+    }
+
+    // ---- 2. two-sided cyclic Jacobi on G, rotations accumulated in Qt
+    int first_any = 0;
+    unsigned nrot = 0;
+    for (int sw = 0; sw < JP_INNER; ++sw) {
+        if (tid == 0) any_rot = 0;
+        __syncthreads();
+        for (int rr = 0; rr < JP_R - 1; ++rr) {
+            if (tid < JP_R / 2) {
+                int p, q;
+                if (tid == 0) {
+                    p = JP_R - 1;
+                    q = rr;
+                } else {
+                    p = (rr + tid) % (JP_R - 1);
+                    q = (rr - tid + JP_R - 1) % (JP_R - 1);
+                }
+                const T a = G[p * JP_LDG + p], b = G[q * JP_LDG + q], g = G[p * JP_LDG + q];
+                const bool doit = g != T(0) && g * g > tol * tol * a * b && fabs(g) > absf;
+                r_p[tid] = p;
+                r_q[tid] = q;
+                r_do[tid] = doit ? 1 : 0;
+                if (doit) {
+                    T cs, sn, t;
+                    jac_rotation(a, b, g, cs, sn, t);
+                    r_cs[tid] = cs;
+                    r_sn[tid] = sn;
+                    r_a[tid] = fma(-t, g, a);
+                    r_b[tid] = fma(t, g, b);
+                    any_rot = 1;
+                    ++nrot;
+                }
+            }
+            __syncthreads();
+            // rows p, q of G and of Qt
+            for (int e = tid; e < (JP_R / 2) * JP_R; e += 256) {
+                const int k = e / JP_R, c = e % JP_R;
+                if (!r_do[k]) continue;
+                const int p = r_p[k], q = r_q[k];
+                const T cs = r_cs[k], sn = r_sn[k];
+                T u = G[p * JP_LDG + c], v = G[q * JP_LDG + c];
+                G[p * JP_LDG + c] = fma(cs, u, -sn * v);
+                G[q * JP_LDG + c] = fma(sn, u, cs * v);
+                u = Qt[p * JP_LDG + c];
+                v = Qt[q * JP_LDG + c];
+                Qt[p * JP_LDG + c] = fma(cs, u, -sn * v);
+                Qt[q * JP_LDG + c] = fma(sn, u, cs * v);
+            }
+            __syncthreads();
+            // columns p, q of G
+            for (int e = tid; e < (JP_R / 2) * JP_R; e += 256) {
+                const int k = e / JP_R, c = e % JP_R;
+                if (!r_do[k]) continue;
+                const int p = r_p[k], q = r_q[k];
+                const T cs = r_cs[k], sn = r_sn[k];
+                const T u = G[c * JP_LDG + p], v = G[c * JP_LDG + q];
+                G[c * JP_LDG + p] = fma(cs, u, -sn * v);
+                G[c * JP_LDG + q] = fma(sn, u, cs * v);
+            }
+            __syncthreads();
+            // the rotated 2 x 2 block exactly: diag(a - t g, b + t g)
+            if (tid < JP_R / 2 && r_do[tid]) {
+                const int p = r_p[tid], q = r_q[tid];
+                G[p * JP_LDG + p] = r_a[tid];
+                G[q * JP_LDG + q] = r_b[tid];
+                G[p * JP_LDG + q] = T(0);
+                G[q * JP_LDG + p] = T(0);
+            }
+            __syncthreads();
+        }
+        const int any = any_rot;
+        if (sw == 0) first_any = any;
+        __syncthreads();
+        if (!any) break;
+    }
+    if (!first_any) return;  // the pair met the stopping test: rows unchanged
+    if (nrot) atomicAdd(rots + mat, (unsigned long long)nrot);
+    if (tid == 0) rotated[mat] = 1;
+
+    // ---- 3. Y <- Qt Y over ncols_rot columns
+    {
+        const int ty = tid >> 3, tx = tid & 7;  // rows 2 ty, 2 ty + 1; columns 4 tx .. 4 tx + 3
+        const int r0 = grow(2 * ty), r1 = grow(2 * ty + 1);
+        for (int c0 = 0; c0 < d.ncols_rot; c0 += JP_KC) {
+            for (int e = tid; e < JP_R * JP_KC; e += 256) {
+                const int lr = e / JP_KC, kk = e % JP_KC;
+                const int r = grow(lr), c = c0 + kk;
+                Yc[lr * JP_LDA + kk] = (r >= 0 && c < d.ncols_rot) ? __ldcg(d.A + (size_t)r * d.ld + c) : T(0);
+            }
+            __syncthreads();
+            T o0[4] = {T(0), T(0), T(0), T(0)}, o1[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 4
+            for (int k = 0; k < JP_R; ++k) {
+                const T q0 = Qt[(2 * ty) * JP_LDG + k], q1 = Qt[(2 * ty + 1) * JP_LDG + k];
+                T y[4];
+                jp_load4(Yc + k * JP_LDA + 4 * tx, y);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    o0[j] = fma(q0, y[j], o0[j]);
+                    o1[j] = fma(q1, y[j], o1[j]);
+                }
+            }
+            __syncthreads();  // the chunk is read whole before the next one is loaded
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = c0 + 4 * tx + j;
+                if (c < d.ncols_rot) {
+                    if (r0 >= 0) d.A[(size_t)r0 * d.ld + c] = o0[j];
+                    if (r1 >= 0) d.A[(size_t)r1 * d.ld + c] = o1[j];
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+void launch_jacobi_pair_round(const JacobiDescT<T>* d, const int4* tasks, int ntasks, int round, T tol, int* rotated,
+                              unsigned long long* rots, cudaStream_t s) {
+    if (ntasks <= 0) return;
+    const size_t smem = jacobi_pair_smem<T>();
+    cudaFuncSetAttribute(jacobi_pair_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    jacobi_pair_kernel<T><<<ntasks, 256, smem, s>>>(d, tasks, round, tol, rotated, rots);
+}
+template void launch_jacobi_pair_round<float>(const JacobiDescT<float>*, const int4*, int, int, float, int*,
+                                              unsigned long long*, cudaStream_t);
+template void launch_jacobi_pair_round<double>(const JacobiDescT<double>*, const int4*, int, int, double, int*,
+                                               unsigned long long*, cudaStream_t);
+
+__global__ void or_flag_kernel(int* p, int bits) { atomicOr(p, bits); }
+void launch_or_flag(int* p, int bits, cudaStream_t s) { or_flag_kernel<<<1, 1, 0, s>>>(p, bits); }
+
 // ------------------------------------------------------------------ block Jacobi
 // The same one-sided Jacobi with the rows resident in shared memory: the
 // matrix is cut into 2 * JAC_CLUSTER row blocks of hb rows; in each block

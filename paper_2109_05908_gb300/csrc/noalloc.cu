@@ -59,10 +59,9 @@ extern "C" amdd_status amdd_true_residual_noalloc(const amdd_csr* A, const doubl
     double* partials = scratch + 2 * (size_t)AMDD_NOALLOC_MAX_N;
     PcgScal* sc = reinterpret_cast<PcgScal*>(partials + DOT_BLOCKS);
     const int64_t n = A->n;
-    const int64_t per = A->nnz / n;
     // the record keeps the previous call's values: clear it
     if (cudaMemsetAsync(sc, 0, sizeof(PcgScal), s) != cudaSuccess) return AMDD_ERR_CUDA;
-    launch_spmv(n, A->rowptr, A->colind, A->val, x, q, per <= 8 ? 4 : (per <= 24 ? 8 : 32), s);
+    launch_spmv(n, A->rowptr, A->colind, A->val, x, q, spmv_group_for(n, A->nnz), s);
     launch_axpby(n, 1.0, b, -1.0, q, r, s);
     launch_dot_partials(n, b, b, partials, s);
     launch_dot_finalize(partials, sc, 3, 0.0, s);

@@ -32,6 +32,11 @@ __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, const int64_t* __r
     }
 }
 
+int spmv_group_for(int64_t n, int64_t nnz) {
+    const int64_t per = n > 0 ? nnz / n : 0;
+    return per <= 8 ? 1 : (per <= 24 ? 8 : 32);
+}
+
 void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
                  double* y, int group, cudaStream_t s) {
     if (n <= 0) return;
@@ -76,6 +81,21 @@ void launch_spmv_multi(int64_t n, const int64_t* rowptr, const int32_t* col, con
     if (n <= 0) return;
     const int64_t want = (n + 255) / 256;
     spmv_multi_kernel<<<(unsigned)(want < 152 * 64 ? want : 152 * 64), 256, 0, s>>>(n, rowptr, col, val, x, y, nb, ld);
+}
+
+// ------------------------------------------------------------------ input checks
+// *flag |= 1 if any of v[0..n) is NaN or infinite (the flag is only ever set)
+__global__ void nonfinite_kernel(const double* __restrict__ v, int64_t n, int* __restrict__ flag) {
+    bool bad = false;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(__ldg(v + t));
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+void launch_nonfinite(const double* v, int64_t n, int* flag, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t want = (n + 255) / 256;
+    nonfinite_kernel<<<(unsigned)(want < 152 * 16 ? want : 152 * 16), 256, 0, s>>>(v, n, flag);
 }
 
 // ------------------------------------------------------------------ gathers
@@ -351,6 +371,26 @@ __global__ void pcg_update_p_kernel(int64_t n, double* __restrict__ p, const dou
 void launch_pcg_update_p(int64_t n, double* p, const double* z, const PcgScal* sc, cudaStream_t s, int nb,
                          int64_t ld, int skip_done) {
     pcg_update_p_kernel<<<dim3(DOT_BLOCKS, nb), 256, 0, s>>>(n, p, z, sc, ld, skip_done);
+}
+
+// End of one PCG iteration replayed inside a CUDA graph's while-loop: log the
+// step length alpha of the iteration just finished (and the ratio beta that
+// built its direction, from the second iteration on) for the Lanczos
+// condition estimate, and continue the loop while the recursive residual is
+// above the tolerance and fewer than *maxit iterations have run.
+__global__ void pcg_loop_cond_kernel(const PcgScal* __restrict__ sc, const int* __restrict__ maxit,
+                                     double* __restrict__ alog, double* __restrict__ blog,
+                                     cudaGraphConditionalHandle loop) {
+    if (threadIdx.x != 0) return;
+    const int k = sc->iters;
+    if (k >= 1 && k <= *maxit) alog[k - 1] = sc->alpha;
+    if (k >= 2 && k <= *maxit) blog[k - 2] = sc->beta;
+    cudaGraphSetConditional(loop, (!sc->conv && k < *maxit) ? 1u : 0u);
+}
+
+void launch_pcg_loop_cond(const PcgScal* sc, const int* maxit, double* alog, double* blog,
+                          cudaGraphConditionalHandle loop, cudaStream_t s) {
+    pcg_loop_cond_kernel<<<1, 32, 0, s>>>(sc, maxit, alog, blog, loop);
 }
 
 // out = a x + b y

@@ -37,6 +37,13 @@ def test_exports_every_declared_symbol(A):
     assert set(names) == set(A.SIGNATURES)
 
 
+def test_noalloc_bound_matches_header(A):
+    """The binding's copy of AMDD_NOALLOC_MAX_N is the header's."""
+    txt = open(os.path.join(ROOT, "include", "amdd.h")).read()
+    m = re.search(r"#define\s+AMDD_NOALLOC_MAX_N\s+(\d+)", txt)
+    assert m and int(m.group(1)) == A.NOALLOC_MAX_N
+
+
 def test_status_strings_and_defaults(A):
     for k in range(8):
         assert A.status_str(k)

@@ -22,6 +22,9 @@ Bars, against the reference of each form:
   * PCG reaches a true relative residual of 1e-8 against the FP64 matrix with
     the reference's iteration count +-10% (at least +-1), and its Lanczos
     condition estimate lies under the bound of Sec. 3.2;
+  * both mixed forms also take the PLAIN FP64 oracle's (eps = 2^-52) iteration
+    count +-10% (at least +-1): the method's own count, whatever shift the
+    FP32 stage needs;
   * bitwise reproducible.
 """
 import numpy as np
@@ -116,7 +119,9 @@ def test_mixed_selection_and_apply(built, prec, name):
     if prec == 1:
         kx = max(s.sigma.max() / s.sigma.min() for s in Sr.subs)
         bar = max(bar, 4 * 2.0 ** -24 * kx)
-    assert np.linalg.norm(zd.cpu().numpy() - zo) <= bar * np.linalg.norm(zo)
+    zg = zd.cpu().numpy()
+    assert np.linalg.norm(zg - zo) <= bar * np.linalg.norm(zo)
+    assert np.abs(zg - zo).max() <= bar * np.abs(zo).max()  # entry by entry
     z2 = torch.empty_like(rd)
     Pp.apply(rd, z2)
     assert torch.equal(zd, z2)
@@ -139,6 +144,20 @@ def test_mixed_pcg_reaches_1e8(built, prec, name):
     if M.n <= 1000:
         bound = O.condition_bound(O.colouring_number(Sr), O.splitting_constant(Sr), Sr.tau)
         assert st.cond_est <= bound
+
+
+@pytest.mark.parametrize("prec,name", PARAMS, ids=IDS)
+def test_mixed_iterations_match_plain_oracle(built, prec, name):
+    """The headline bar: the mixed forms reach 1e-8 within +-10% (at least +-1)
+    of the iteration count of the plain FP64 oracle at eps = 2^-52."""
+    M, b, S, P = built[name]
+    S64 = S[EPS64]
+    _, its_o, _ = O.pcg(S64.A, b, lambda v: O.apply(S64, v), rtol=1e-8)
+    bd = to_device(b)
+    x = torch.zeros_like(bd)
+    st = P[prec].solve(bd, x, rtol=1e-8)
+    assert st.converged == 1 and st.true_rel_residual <= 2e-8
+    assert abs(st.iterations - its_o) <= max(1, int(np.ceil(0.1 * its_o))), (st.iterations, its_o)
 
 
 def test_mixed_batched_rhs(built):

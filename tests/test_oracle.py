@@ -409,3 +409,60 @@ def test_planted_dropped_shift_is_caught(monkeypatch):
     monkeypatch.setattr(O, "splitting_root", wrong)
     with pytest.raises((AssertionError, np.linalg.LinAlgError)):
         test_eigenproblem_matches_extended_precision_bruteforce()
+
+
+# ------------------------------------------------- k_c and k_m of Sec. 3.2
+@pytest.mark.parametrize("m,box,kc", [(8, 4, 4), (16, 4, 4), (12, 12, 1)])
+def test_colouring_number_of_box_layouts(m, box, kc):
+    """k_c on box layouts with overlap 1 where it is known: on a 2 x 2 grid of
+    boxes every overlapped subdomain touches the three others (K_4, four
+    colours); on a 4 x 4 grid each box touches its eight king-move neighbours
+    and no box two steps away (the king's graph, chromatic number 4, which
+    the row-major greedy order attains); one box needs one colour.  A
+    colouring that missed the diagonal neighbours would find 2 here."""
+    A = synth.laplace2d(m)
+    part = synth.box_partition_2d(m, box)
+    S = O.setup(A, part, int(part.max()) + 1, 1, 0.5)
+    assert O.colouring_number(S) == kc
+
+
+def test_colouring_number_of_strips():
+    """Vertical strips four columns wide with overlap 1: strip i touches only
+    strips i - 1 and i + 1, a path, so two colours."""
+    m = 16
+    A = synth.laplace2d(m)
+    part = (np.arange(m * m) % m // 4).astype(np.int32)
+    S = O.setup(A, part, 4, 1, 0.5)
+    assert O.colouring_number(S) == 2
+
+
+@pytest.mark.parametrize("m,eps", [(8, 1e-3), (10, 2.0 ** -20)])
+def test_splitting_constant_single_subdomain(m, eps):
+    """N = 1: Omega_G and Omega_D are empty, X = A, the regularised root is
+    (A^T A)^{1/2} + sigma_1 eps I = A + sigma_1 eps I with sigma_1 = lambda_max(A),
+    so k_m = lambda_max(A + sigma_1 eps I, A) = 1 + eps lambda_max / lambda_min,
+    in closed form from the Laplacian's spectrum 4 - 2cos(j pi/(m+1)) -
+    2cos(k pi/(m+1)).  A dropped shift would give exactly 1."""
+    A = synth.laplace2d(m)
+    part = np.zeros(m * m, np.int32)
+    S = O.setup(A, part, 1, 1, 0.5, eps=eps)
+    c = np.cos(np.pi / (m + 1))
+    lmin, lmax = 4.0 - 4.0 * c, 4.0 + 4.0 * c
+    km = O.splitting_constant(S)
+    assert km - 1.0 == pytest.approx(eps * lmax / lmin, rel=1e-6)
+
+
+def test_splitting_constant_at_most_multiplicity():
+    """Each R_i^T tilde A_ii R_i is at most A in the Loewner order (Lemma 3.2),
+    so k_m is at most the number of subdomains whose Omega_i holds a given
+    unknown, maximised over unknowns (here: overlap-1 boxes on a 12 x 12 grid,
+    multiplicity 4 at box corners).  The lower check (k_m >= 1) is a sanity
+    bar on this layout, where vectors supported deep inside one box see only
+    that box's term."""
+    A, part, N = _small_2d()
+    S = O.setup(A, part, N, 1, 0.5)
+    mult = np.zeros(A.n, int)
+    for s in S.subs:
+        mult[s.omega] += 1
+    km = O.splitting_constant(S)
+    assert 1.0 <= km <= mult.max() + 1e-10

@@ -1,9 +1,11 @@
 """The allocation-free true-residual entry point (for callers that cannot
-allocate device memory) agrees with the residual amdd_pcg_solve reports for
-the same solution, on two calls in a row (its static scratch is reused and
-must be re-initialised by every call), and rejects sizes beyond its static
-scratch.  Collected last so that a run stopping at the first failure has run
-every other test first; it also passes alone in a fresh process."""
+allocate device memory) gives bit for bit the residual amdd_pcg_solve reports
+for the same solution (same SpMV lane width, same fixed reduction order), on
+two calls in a row (its static scratch is reused and must be re-initialised by
+every call); it agrees with ||b - A x|| and ||b|| computed on the host for a
+non-zero x, and rejects sizes beyond its static scratch.  Collected last so
+that a run stopping at the first failure has run every other test first; it
+also passes alone in a fresh process."""
 import numpy as np
 import pytest
 
@@ -33,7 +35,24 @@ def test_matches_pcg_true_residual_twice():
         r2 = A.true_residual_noalloc(dA.csr, b.data_ptr(), x.data_ptr(), stream)
         assert r1 == r2
         assert r1[1] == pytest.approx(float(np.linalg.norm(w["b"])), rel=1e-14)
-        assert r1[0] / r1[1] == pytest.approx(st.true_rel_residual, rel=1e-12)
+        # the same kernels in the same order: the same bits
+        assert r1[0] / r1[1] == st.true_rel_residual
+        # independent host check at a non-zero x (the PCG solution itself)
+        xs = x.cpu().numpy()
+        M = w["A"]
+        rows = np.repeat(np.arange(M.n), np.diff(M.rowptr))
+        ax = np.zeros(M.n)
+        np.add.at(ax, rows, M.val * xs[M.colind])
+        res_host = float(np.linalg.norm(w["b"] - ax))
+        assert r1[0] == pytest.approx(res_host, rel=1e-6, abs=1e-15 * float(np.linalg.norm(w["b"])))
+        # a rougher non-zero x: the residual is O(||b||), so the relative bar is tight
+        rng = np.random.Generator(np.random.PCG64(7))
+        xr = rng.uniform(-1.0, 1.0, M.n)
+        axr = np.zeros(M.n)
+        np.add.at(axr, rows, M.val * xr[M.colind])
+        xr_d = to_device(xr)
+        r4 = A.true_residual_noalloc(dA.csr, b.data_ptr(), xr_d.data_ptr(), stream)
+        assert r4[0] == pytest.approx(float(np.linalg.norm(w["b"] - axr)), rel=1e-12)
         # a different x between calls: the scratch holds the last call's values
         x2 = torch.zeros_like(b)
         r3 = A.true_residual_noalloc(dA.csr, b.data_ptr(), x2.data_ptr(), stream)
