@@ -1,19 +1,26 @@
 """Benchmark: time to a 1e-8 relative residual (setup + PCG solve) of the
-two-level algebraic Schwarz preconditioner on one GB300.
+two-level algebraic Schwarz preconditioner on one GB300, mixed form against
+the plain FP64 form on the same GPU.
 
-Workload: 2D 5-point Laplacian on 64 x 64 interior nodes (n = 4096), 16 boxes
-of 16 x 16, overlap 1, tau = 50, b uniform[-1, 1] (seed 0): the
-configuration of the paper-shaped suite that fits one GPU (see the design
-notes for why the 2M-unknown diffusion configurations do not).
+Workload: 3D 7-point channelled diffusion (lognormal coefficient, sigma 2,
+correlation length 8 cells, 16 one-cell channels of 1e6 along x) on a 24^3
+grid, 16 seeded BFS subdomains of 256..2048 cells, overlap 2, tau = 100, b
+uniform[-1, 1] (seed 0): the shape of the 128^3 diffusion configuration
+(high-contrast channels, BFS subdomains, overlap 2; here 1.3k..2.4k unknowns
+per subdomain with their overlap) at the size whose plain FP64 arm one GPU
+sets up in seconds; see the design notes for what excludes the full size.
 
 One step = amdd_setup + amdd_pcg_solve (rtol 1e-8) on device-resident inputs,
 timed with CUDA events on the library's stream; L2 is flushed before each
-step.  `e2e` repeats the step through the C ABI from pinned host buffers with
-the host->device copies of A, the partition and b and the device->host copy of
-x inside the timed region.  `roofline` describes the kernel class with the
-largest device time, measured with CUDA events around each of its launches
-(the library's profiling mode) during the timed steps.  `cpu_baseline` is the
-FP64 CPU oracle on the same workload.
+step.  `value` is the mixed form (FP32 local work, FP64 coarse and PCG);
+`config.arms` holds both forms' setup and solve times and their ratio.  `e2e`
+repeats the mixed step through the C ABI from pinned host buffers with the
+host->device copies of A, the partition and b and the device->host copy of x
+inside the timed region.  `roofline` describes the kernel class with the
+largest device time, measured with CUDA events around its launches (the
+library's profiling mode) during the timed steps, against the algorithmic
+work of that step of the method.  `cpu_baseline` is the FP64 CPU oracle on a
+bounded, extrapolated sample of the same workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amdd|reference]
 """
@@ -32,21 +39,45 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-8 residual (setup+solve), learned/mixed vs plain FP64, same GB300"
-WORKLOAD = "laplace2d_64x64_16box_ov1_tau50"
+WORKLOAD_3D = dict(m=24, N=16, lo=256, hi=2048, overlap=2, tau=100.0)
 RTOL = 1e-8
 # GB300 FP64: 152 SMs x 2 FMA/clock/SM x 2 flops x 2.07 GHz = 1.26 TFLOP/s (the recipe's 1.25 TFLOP/s;
 # a DFMA throughput probe measured 1.20 TFLOP/s at 1.98 GHz).  FP32: 152 x 128 lanes x 2 x 2.07 GHz.
 FP64_PEAK_GFLOPS = 1250.0
 FP32_PEAK_GFLOPS = 80550.0
+SVD_CLASSES = {"jacobi_f32": True, "jacobi_svd": False}
+TRIDIAG_CLASSES = {"tridiag_f32": True, "tridiag": False}
 F32_CLASSES = {"jacobi_f32", "gemm_tiles_f32", "chol_diag_f32", "chol_panel_f32", "trtri_diag_f32", "tridiag_f32",
                "bisect_f32"}
 ALU_CLASSES = F32_CLASSES | {"jacobi_svd", "jacobi_eig", "tridiag", "bisect", "gemm_tiles", "chol_diag", "chol_panel", "trtri_diag", "e_offdiag"}
 
 
-def _workload():
+def _workload(**over):
     import synth
-    w = synth.workload_c1()
-    return w
+    kw = dict(WORKLOAD_3D)
+    kw.update(over)
+    return synth.workload_diffusion3d(**kw)
+
+
+def _sizes(A, h, N):
+    """(|Omega_Ii|, n_i = |Omega_i|, tilde n_i) of every subdomain."""
+    out = []
+    for i in range(N):
+        nI, nG, nD, _ = A.get_subdomain(h, i)
+        out.append((nI, nI + nG, nI + nG + nD))
+    return out
+
+
+def svd_flops(sizes):
+    """Algorithmic work of the SVD of the X_i: 4 n_i^2 tilde n_i each (the
+    count of a dense SVD, not of the Jacobi sweeps that compute it)."""
+    return sum(4.0 * ni * ni * nt for _, ni, nt in sizes)
+
+
+def eig_flops(sizes):
+    """Algorithmic work of the symmetric reduction of eq. (Zi) on Omega_Ii:
+    (8/3) |Omega_Ii|^3 (Householder tridiagonalisation)."""
+    return sum(8.0 / 3.0 * nI ** 3 for nI, _, _ in sizes)
 
 
 def _peaks():
@@ -108,25 +139,90 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, max_seconds=30.0):
-    """The FP64 CPU oracle, as it stands, on the same workload (setup + PCG)."""
+def _oracle_local(w, i):
+    """The oracle's local setup of subdomain i (Sec. 2.1 sets, eq. (Xi), the
+    splitting of Sec. 3.2, eq. (Zi), the local Cholesky factor): seconds, its
+    n_i^2 tilde n_i and n_i."""
+    import scipy.linalg as sla
+
     from oracle import amdd_oracle as O
-    times, its = [], None
-    t_all = time.perf_counter()
-    while True:
-        t0 = time.perf_counter()
-        S = O.setup(w["A"], w["part"], w["N"], w["overlap"], w["tau"])
-        _, its, _ = O.pcg(S.A, w["b"], lambda r: O.apply(S, r), rtol=RTOL)
-        times.append((time.perf_counter() - t0) * 1e3)
-        if time.perf_counter() - t_all > max_seconds / 2 or len(times) >= 3:
+    As = O.to_scipy(w["A"])
+    t0 = time.perf_counter()
+    I, G, D = O.subdomain_sets(As, w["part"], i, w["overlap"])
+    Aii, X = O.local_matrices(As, I, G, D)
+    Abar, _ = O.splitting_root(X, O.EPS)
+    O.local_eigenproblem(Aii, Abar, len(I), w["tau"])
+    sla.cho_factor(Aii, lower=True)
+    dt = time.perf_counter() - t0
+    ni = len(I) + len(G)
+    return dt, float(ni) * ni * (ni + len(D)), ni
+
+
+def _oracle_dense_rates(ns=2048):
+    """Seconds of the oracle's dense coarse steps at order ns (LAPACK Cholesky
+    of an SPD matrix and one solve with it), for extrapolation by (n_C/ns)^3
+    and (n_C/ns)^2."""
+    import numpy as np
+    import scipy.linalg as sla
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((ns, ns))
+    E = B @ B.T + ns * np.eye(ns)
+    t0 = time.perf_counter()
+    c = sla.cho_factor(E, lower=True)
+    t1 = time.perf_counter()
+    sla.cho_solve(c, rng.standard_normal(ns))
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, ns
+
+
+def cpu_baseline(w, sizes, n_c, its, max_seconds=25.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload,
+    extrapolated to the whole setup + solve:
+      * local setup of seeded sample subdomains, scaled by sum n_i^2 tilde n_i
+        (the order of its dense SVD) over all subdomains;
+      * dense Cholesky of E and one solve with it, timed at order 2048 and
+        scaled by (n_C / 2048)^3 and (n_C / 2048)^2;
+      * per PCG iteration: the local solves of the sample scaled by sum n_i^2
+        plus the coarse solve, times the iteration count of the GPU's plain
+        FP64 form (equal to the oracle's within one, tested)."""
+    import numpy as np
+    import scipy.linalg as sla
+    rng = np.random.default_rng(1)
+    order = rng.permutation(len(sizes))
+    t_loc = w_loc = 0.0
+    n_sub = 0
+    t_start = time.perf_counter()
+    for i in order:
+        dt, wk, _ = _oracle_local(w, int(i))
+        t_loc += dt
+        w_loc += wk
+        n_sub += 1
+        if time.perf_counter() - t_start > max_seconds * 0.6:
             break
+    total_w = sum(float(ni) * ni * nt for _, ni, nt in sizes)
+    setup_local = t_loc * total_w / w_loc
+    tf, ts, ns = _oracle_dense_rates()
+    coarse_factor = tf * (n_c / ns) ** 3
+    coarse_solve = ts * (n_c / ns) ** 2
+    # local solves per iteration: cho_solve on the sampled subdomains' factors
+    t_ls, w_ls = 0.0, 0.0
+    for _, ni, _ in [sizes[int(i)] for i in order[:n_sub]]:
+        M = np.eye(ni) * 4.0 + 0.1
+        c = sla.cho_factor(M, lower=True)
+        t0 = time.perf_counter()
+        sla.cho_solve(c, np.ones(ni))
+        t_ls += time.perf_counter() - t0
+        w_ls += float(ni) * ni
+    local_solve = t_ls * sum(float(ni) * ni for _, ni, _ in sizes) / max(w_ls, 1.0)
+    total_s = setup_local + coarse_factor + its * (local_solve + coarse_solve)
     cores = os.cpu_count()
-    # iteration count of the deflated GMRES(30) variant (Sec. 4.1), untimed
-    _, gits, _ = O.gmres(S.A, w["b"], lambda r: O.apply_deflated(S, r), restart=30, rtol=RTOL)
-    return {"value": statistics.median(times), "unit": "ms", "cores": cores, "kind": "oracle",
-            "sample": f"full workload ({WORKLOAD}), {len(times)} solve(s), numpy/scipy FP64 with the default "
-                      f"BLAS threading on {cores} host cores; {its} PCG iterations",
-            "deflated_gmres30_iterations": gits}, its
+    return {"value": total_s * 1e3, "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": f"extrapolated: local setup of {n_sub} of {len(sizes)} subdomains timed "
+                      f"({t_loc:.1f} s) and scaled by sum n_i^2 tilde n_i; dense coarse Cholesky and solve timed "
+                      f"at order {ns} and scaled to n_C = {n_c}; {its} PCG iterations (the GPU plain FP64 "
+                      f"count); numpy/scipy FP64 with the default BLAS threading on {cores} host cores",
+            "parts_s": {"local_setup": setup_local, "coarse_factor": coarse_factor,
+                        "per_iteration": local_solve + coarse_solve}}
 
 
 def max_over_ranks(x: float, dist=None, device=None) -> float:
@@ -146,11 +242,12 @@ APPLY_CLASSES = ("gemv_rows_f32", "gemv_rows", "gather_scatter", "coarse_solve")
 
 
 def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20, m=None):
-    """SpMV and the two-level apply at scale: 2D Laplacian 1024 x 1024 (n = 1M),
-    4096 boxes of 16 x 16, overlap 1, mixed form.  With tau = 1e-12 only
-    eigenvalues above 1e12 enter the coarse space, so the apply is the
-    bandwidth-bound part (restriction, the local triangular products with
-    ~1.7 GB of FP32 factors, prolongation).  Each timed call is bracketed by
+    """SpMV and the one-level apply at scale: 2D Laplacian 1024 x 1024 (n = 1M),
+    4096 boxes of 16 x 16, overlap 1, mixed form.  With tau = 1e-12 no
+    eigenvalue of eq. (Zi) exceeds 1/tau = 1e12 in the FP32 splitting, so n_C
+    = 0 and the apply is the one-level sum of Sec. 2.1 (restriction, the local
+    triangular products with ~1.7 GB of FP32 factors, prolongation): its
+    bandwidth-bound part.  Each timed call is bracketed by
     CUDA events on the library's stream, with L2 flushed (by a read) before it;
     bytes are the algorithmic counts of the library's profile."""
     import synth
@@ -242,7 +339,7 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20, m=None):
                  "GB/s": spmv_gbs, "frac": spmv_gbs / hbm_gbs if spmv_gbs else None,
                  "call_ms": spmv_call_ms,
                  "note": "kernel events inside PCG; call_ms is the whole amdd_spmv call (it synchronises)"},
-        "apply": {"ms": apply_ms, "bytes": apply_bytes, "GB/s": apply_gbs, "frac": apply_gbs / hbm_gbs,
+        "one_level_apply": {"ms": apply_ms, "bytes": apply_bytes, "GB/s": apply_gbs, "frac": apply_gbs / hbm_gbs,
                   "note": "whole amdd_apply call between events (launch gaps and its final synchronisation included)"},
         "apply_8rhs": {"ms": apply8_ms, "ms_per_rhs": apply8_ms / 8, "bytes": apply8_bytes,
                        "GB/s": apply8_bytes / (apply8_ms * 1e-3) / 1e9,
@@ -251,11 +348,50 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20, m=None):
     }
 
 
-def variants(A, torch, np, dev, sp, w, precision, steps=3):
-    """The Sec. 4.1 / Sec. 4.2 solver variants, device-timed like the main
-    step (CUDA events on the library's stream, L2 flushed before each step):
+def _arm_ms(A, torch, dev, sp, w, precision, steps=2, warm=1):
+    """Setup + PCG to 1e-8 of one workload in one precision form, device-timed
+    like the main step (L2 flushed before each step): (ms, iterations, n_C,
+    setup_ms, solve_ms)."""
+    import numpy as np
+
+    from paper_2109_05908_gb300.device import DeviceMatrix
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    dA = DeviceMatrix(w["A"], device=dev)
+    part = torch.from_numpy(np.asarray(w["part"], np.int32)).to(dev)
+    b = torch.from_numpy(w["b"]).to(dev)
+    x = torch.zeros_like(b)
+    o = A.opts_default()
+    o.precision = precision
+    ts, out = [], None
+    for q in range(warm + steps):
+        flush.zero_()
+        x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = A.setup(dA.csr, part.data_ptr(), w["N"], w["overlap"], w["tau"], o, sp)
+        st = A.pcg_solve(h, b.data_ptr(), x.data_ptr(), 1, RTOL, 1000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        info = A.get_info(h)
+        A.destroy(h)
+        if q >= warm:
+            ts.append(e0.elapsed_time(e1))
+            out = (st.iterations, info.n_C, info.setup_ms, st.solve_ms)
+    return {"ms": sum(ts) / len(ts), "pcg_iterations": out[0], "n_C": out[1], "setup_ms": out[2],
+            "solve_ms": out[3]}
+
+
+def variants(A, torch, np, dev, sp, precision, steps=3):
+    """Other workloads and the Sec. 4.1 / Sec. 4.2 solver variants,
+    device-timed like the main step (CUDA events on the library's stream, L2
+    flushed before each step):
+      * c1: the 2D Laplacian 64 x 64, 16 boxes, tau = 50, both forms;
+      * partial_selection_3d: the main 3D workload with tau = 0.5, both forms:
+        only part of each local spectrum enters the coarse space, so the
+        eigenvectors of eq. (Zi) are computed;
       * deflated: setup + right-preconditioned GMRES(30) with the deflated
-        form on the main workload;
+        form on c1;
       * three_level: Laplacian 64 x 64, 16 boxes, tau = 0.5; second level on
         E with 2 x 2 groups of boxes, tau2 = 0.5; outer flexible GMRES(30) to
         1e-8 with inner GMRES(30) to 1e-4, against the two-level deflated
@@ -282,6 +418,19 @@ def variants(A, torch, np, dev, sp, w, precision, steps=3):
                 ts.append(e0.elapsed_time(e1))
         return sum(ts) / len(ts), res
 
+    w = synth.workload_c1()
+    out["c1"] = {"workload": w["name"], "mixed": _arm_ms(A, torch, dev, sp, w, precision, steps=5, warm=2),
+                 "plain_fp64": _arm_ms(A, torch, dev, sp, w, 0, steps=5, warm=2)}
+    out["c1"]["plain_over_mixed"] = out["c1"]["plain_fp64"]["ms"] / out["c1"]["mixed"]["ms"]
+    w3 = _workload(tau=0.5)
+    out["partial_selection_3d"] = {"workload": w3["name"], "mixed": _arm_ms(A, torch, dev, sp, w3, precision),
+                                   "mixed_fp64_splitting": _arm_ms(A, torch, dev, sp, w3, 2),
+                                   "plain_fp64": _arm_ms(A, torch, dev, sp, w3, 0),
+                                   "note": "precision 1 splits in FP32 with eps = 2^-23, which selects a different "
+                                           "eps-cluster for tau < 1; precision 2 keeps the FP64 splitting and the "
+                                           "plain selection"}
+    out["partial_selection_3d"]["plain_over_mixed"] = (out["partial_selection_3d"]["plain_fp64"]["ms"] /
+                                                       out["partial_selection_3d"]["mixed"]["ms"])
     M, part_h, b_h = w["A"], np.asarray(w["part"], np.int32), w["b"]
     dA = DeviceMatrix(M, device=dev)
     part = torch.from_numpy(part_h).to(dev)
@@ -298,7 +447,7 @@ def variants(A, torch, np, dev, sp, w, precision, steps=3):
         return st
 
     ms, st = timed(deflated)
-    out["deflated_gmres30"] = {"workload": WORKLOAD, "form": "deflated (Sec. 4.1), right-preconditioned GMRES(30)",
+    out["deflated_gmres30"] = {"workload": w["name"], "form": "deflated (Sec. 4.1), right-preconditioned GMRES(30)",
                                "ms": ms, "iterations": st.iterations, "true_rel_residual": st.true_rel_residual}
     # three-level form
     m, box, tau = 64, 16, 0.5
@@ -381,34 +530,56 @@ def variants(A, torch, np, dev, sp, w, precision, steps=3):
 
 
 def run_reference(args):
+    """The oracle arm: each step times the oracle's local setup of one sampled
+    subdomain (seeded order) and the whole setup + solve is extrapolated as in
+    cpu_baseline; bounded to about 150 s of host time in total."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import numpy as np
     w = _workload()
     from oracle import amdd_oracle as O
+    As = O.to_scipy(w["A"])
+    sizes = []
+    for i in range(w["N"]):
+        I, G, D = O.subdomain_sets(As, w["part"], i, w["overlap"])
+        sizes.append((len(I), len(I) + len(G), len(I) + len(G) + len(D)))
+    n_c = w["A"].n  # tau >= 1: every eigenvalue of eq. (Zi) is selected
+    its = int(os.environ.get("AMDD_REF_ITS", "26"))
+    tf, ts, ns = _oracle_dense_rates()
+    total_w = sum(float(ni) * ni * nt for _, ni, nt in sizes)
+    order = np.random.default_rng(1).permutation(w["N"])
     budget = 150.0
     t_start = time.perf_counter()
-    for _ in range(min(args.warmup, 1)):
-        S = O.setup(w["A"], w["part"], w["N"], w["overlap"], w["tau"])
-        O.pcg(S.A, w["b"], lambda r: O.apply(S, r), rtol=RTOL)
-    times, its = [], 0
-    for _ in range(args.steps):
+    times = []
+    total_sq = sum(float(ni) * ni for _, ni, _ in sizes)
+    import scipy.linalg as sla
+    for k in range(args.warmup + args.steps):
+        dt, wk, ni = _oracle_local(w, int(order[k % len(order)]))
+        # one local solve with a factor of this order, scaled by sum n_i^2, plus the coarse solve
+        c = sla.cho_factor(np.eye(ni) * 4.0 + 0.1, lower=True)
         t0 = time.perf_counter()
-        S = O.setup(w["A"], w["part"], w["N"], w["overlap"], w["tau"])
-        _, its, _ = O.pcg(S.A, w["b"], lambda r: O.apply(S, r), rtol=RTOL)
-        times.append((time.perf_counter() - t0) * 1e3)
+        sla.cho_solve(c, np.ones(ni))
+        t_ls = time.perf_counter() - t0
+        per_it = t_ls * total_sq / (float(ni) * ni) + ts * (n_c / ns) ** 2
+        est = dt * total_w / wk + tf * (n_c / ns) ** 3 + its * per_it
+        if k >= args.warmup:
+            times.append(est * 1e3)
         if time.perf_counter() - t_start > budget:
             break
-    v = sum(times) / len(times)
+    v = sum(times) / len(times) if times else float("nan")
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": w["A"].n, "N": w["N"], "overlap": w["overlap"],
+            "config": {"workload": w["name"], "n": w["A"].n, "N": w["N"], "overlap": w["overlap"],
                        "tau": w["tau"], "rtol": RTOL},
             "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
-                             "sample": f"full workload per step, {len(times)} of {args.steps} steps run "
-                                       f"(bounded to {budget:.0f} s), {its} PCG iterations"},
+                             "sample": f"extrapolated per step from the oracle's local setup of one sampled "
+                                       f"subdomain (scaled by sum n_i^2 tilde n_i), the dense coarse Cholesky and "
+                                       f"solve timed at order {ns} (scaled to n_C = {n_c}) and {its} PCG "
+                                       f"iterations; {len(times)} of {args.steps} steps run (bounded to "
+                                       f"{budget:.0f} s); {cores} host cores"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -440,58 +611,105 @@ def run_amdd(args):
     b = torch.from_numpy(b_h).to(dev)
     x = torch.zeros_like(b)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
-    opts = A.opts_default()
-    opts.profile = 1
-    opts.precision = args.precision
 
-    def one_step(profile_acc=None):
-        x.zero_()
-        h = A.setup(dA.csr, part.data_ptr(), w["N"], w["overlap"], w["tau"], opts, sp)
-        st = A.pcg_solve(h, b.data_ptr(), x.data_ptr(), 1, RTOL, 1000)
-        if profile_acc is not None:
-            for c in A.get_profile(h):
-                a = profile_acc.setdefault(c["name"], {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
-                for k in ("launches", "ms", "flops", "bytes"):
-                    a[k] += c[k]
-        info = A.get_info(h)
-        A.destroy(h)
-        return st, info
+    def make_step(precision, profile_classes=0, profile=1):
+        o = A.opts_default()
+        o.profile = profile
+        o.precision = precision
+        o.profile_classes = profile_classes
 
-    # warm-up: the first step times every kernel class (the per-class table);
-    # the timed steps record events around the dominant class only, so the
-    # event records cost little inside the timed region
-    warm_prof = {}
+        def one_step(profile_acc=None, keep=None):
+            x.zero_()
+            h = A.setup(dA.csr, part.data_ptr(), w["N"], w["overlap"], w["tau"], o, sp)
+            st = A.pcg_solve(h, b.data_ptr(), x.data_ptr(), 1, RTOL, 1000)
+            if profile_acc is not None:
+                for c in A.get_profile(h):
+                    a = profile_acc.setdefault(c["name"], {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+                    for kk in ("launches", "ms", "flops", "bytes"):
+                        a[kk] += c[kk]
+            info = A.get_info(h)
+            if keep is not None:
+                keep.append(_sizes(A, h, w["N"]))
+            A.destroy(h)
+            return st, info
+        return one_step, o
+
+    def timed_steps(one_step, k_steps, prof=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_steps)]
+        torch.cuda.synchronize()
+        its, cond, setup_ms, solve_ms, info = [], [], [], [], None
+        for k in range(k_steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            st, info = one_step(prof)
+            ev[k][1].record(stream)
+            its.append(st.iterations)
+            cond.append(st.cond_est)
+            setup_ms.append(info.setup_ms)
+            solve_ms.append(st.solve_ms)
+        torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(bb) for a, bb in ev]
+        return {"ms": sum(step_ms) / len(step_ms), "setup_ms": statistics.median(setup_ms),
+                "solve_ms": statistics.median(solve_ms), "pcg_iterations": its[-1], "cond_est": cond[-1],
+                "n_C": info.n_C, "eps": info.eps, "steps": k_steps, "step_ms": step_ms}, info
+
+    # ---- mixed arm (the value): warm-up, the first warm-up step times every kernel
+    # class; the timed steps record events around the dominant class only
+    step_mixed, o_mixed = make_step(args.precision)
+    warm_prof, keep = {}, []
     for k in range(args.warmup):
-        one_step(warm_prof if k == 0 else None)
+        step_mixed(warm_prof if k == 0 else None, keep if k == 0 else None)
+    sizes = keep[0]
     torch.cuda.synchronize()
     top_name = max(warm_prof.items(), key=lambda kv: kv[1]["ms"])[0] if warm_prof else None
     if top_name is not None:
-        opts.profile_classes = 1 << list(warm_prof).index(top_name)  # classes in amdd_get_profile order
+        o_mixed.profile_classes = 1 << list(warm_prof).index(top_name)  # classes in amdd_get_profile order
     if dist:
         dist.barrier()
     clocks = ClockSampler(local)
     prof = {}
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    its, cond, setup_ms, solve_ms = [], [], [], []
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        st, info = one_step(prof)
-        ev[k][1].record(stream)
-        its.append(st.iterations)
-        cond.append(st.cond_est)
-        setup_ms.append(info.setup_ms)
-        solve_ms.append(st.solve_ms)
-    torch.cuda.synchronize()
+    mixed, info = timed_steps(step_mixed, args.steps, prof)
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(bb) for a, bb in ev]
-    ms = sum(step_ms) / len(step_ms)
-    ms = max_over_ranks(ms, dist, dev)
+    ms = max_over_ranks(mixed["ms"], dist, dev)
 
-    # ---- end to end from pinned host buffers through the C ABI
+    # ---- plain FP64 arm on the same box (fewer steps: it is the slow form)
+    step_plain, _ = make_step(0, profile=0)
+    step_plain()
+    plain, _ = timed_steps(step_plain, max(1, min(args.steps, args.plain_steps)))
+
+    # ---- the same solve with and without the PCG graph (one handle each)
+    graphs = None
+    try:
+        hs = {}
+        for g in (1, 0):
+            o = A.opts_default()
+            o.precision = args.precision
+            o.use_graphs = g
+            hs[g] = A.setup(dA.csr, part.data_ptr(), w["N"], w["overlap"], w["tau"], o, sp)
+        res = {}
+        for g in (1, 0):
+            tt = []
+            for k in range(4):
+                x.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = A.pcg_solve(hs[g], b.data_ptr(), x.data_ptr(), 1, RTOL, 1000)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if k:
+                    tt.append(e0.elapsed_time(e1))
+            res[g] = (statistics.median(tt), st.iterations, A.get_info(hs[g]).graph_solves)
+        for h in hs.values():
+            A.destroy(h)
+        graphs = {"solve_ms_graph": res[1][0], "solve_ms_launches": res[0][0], "iterations_graph": res[1][1],
+                  "iterations_launches": res[0][1], "graph_solves": res[1][2],
+                  "note": "PCG solve on a set-up handle, CUDA events around the call, median of 3 after one"}
+    except Exception as e:  # never costs the main line
+        graphs = {"error": str(e)}
+
+    # ---- end to end from pinned host buffers through the C ABI (mixed arm)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     h_rowptr, h_col, h_val = pin(M.rowptr.astype(np.int64)), pin(M.colind.astype(np.int32)), pin(M.val)
     h_part, h_b = pin(part_h), pin(b_h)
@@ -502,7 +720,7 @@ def run_amdd(args):
     h2d = sum(t.numel() * t.element_size() for t in (h_rowptr, h_col, h_val, h_part, h_b))
     d2h = h_x.numel() * h_x.element_size()
     e2e_ms = []
-    for k in range(args.warmup + args.steps):
+    for k in range(1 + args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -517,7 +735,7 @@ def run_amdd(args):
         e1.record(stream)
         torch.cuda.synchronize()
         A.destroy(h)
-        if k >= args.warmup:
+        if k >= 1:
             e2e_ms.append(e0.elapsed_time(e1))
     e2e = sum(e2e_ms) / len(e2e_ms)
     xs = h_x.numpy()
@@ -531,43 +749,58 @@ def run_amdd(args):
     peaks, peak_src = _peaks()
     top = max(prof.items(), key=lambda kv: kv[1]["ms"])
     name, c = top
-    assert top_name is None or name == top_name
+    per_step_ms = c["ms"] / args.steps
     per_launch_ms = c["ms"] / max(c["launches"], 1)
-    if name in ALU_CLASSES:
-        achieved = c["flops"] / (c["ms"] * 1e-3) / 1e12
-        f32 = name in F32_CLASSES
+    executed = c["flops"] / (c["ms"] * 1e-3) / 1e12 if c["ms"] > 0 else None
+    if name in SVD_CLASSES or name in TRIDIAG_CLASSES:
+        f32 = SVD_CLASSES.get(name, TRIDIAG_CLASSES.get(name))
+        alg = svd_flops(sizes) if name in SVD_CLASSES else eig_flops(sizes)
+        achieved = alg / (per_step_ms * 1e-3) / 1e12
         peak = (FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS) / 1e3
         roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "launches_per_step": c["launches"] / args.steps, "ms_per_launch": per_launch_ms,
-                "peak_source": ("FP32 FFMA peak from SM count, lanes and max clock" if f32 else
+                "algorithmic_flops_per_step": alg,
+                "algorithmic_count": ("sum_i 4 n_i^2 tilde n_i (dense SVD of the X_i)" if name in SVD_CLASSES
+                                      else "sum_i (8/3) |Omega_Ii|^3 (Householder reduction)"),
+                "executed_tflops": executed,
+                "launches_per_step": c["launches"] / args.steps, "ms_per_step": per_step_ms,
+                "peak_source": ("FP32 FFMA peak from SM count, lanes and max clock (no tensor cores)" if f32 else
                                 "FP64 1.25 TFLOP/s (recipe table; 2 DFMA/clk/SM x 152 SMs x 2.07 GHz)")}
+    elif name in ALU_CLASSES:
+        f32 = name in F32_CLASSES
+        peak = (FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS) / 1e3
+        roof = {"bound": "alu", "kernel": name, "achieved": executed, "peak": peak, "unit": "TFLOP/s",
+                "frac": executed / peak if executed else None, "traffic": None,
+                "launches_per_step": c["launches"] / args.steps, "ms_per_launch": per_launch_ms}
     else:
         achieved = c["bytes"] / (c["ms"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "launches_per_step": c["launches"] / args.steps, "ms_per_launch": per_launch_ms,
                 "peak_source": f"hbm_gbs ({peak_src})"}
-    launches = int(sum(v["launches"] for v in prof.values()) / args.steps)
+    launches = int(sum(v["launches"] for v in warm_prof.values()))
     scale = apply_at_scale(A, torch, np, dev, sp, peaks["hbm_gbs"], m=args.scale_m) if not args.no_scale else None
-    var = variants(A, torch, np, dev, sp, w, args.precision) if not args.no_variants else None
-    base, base_its = cpu_baseline(w) if world == 1 or rank == 0 else (None, None)
-    if var and base:
-        var["deflated_gmres30"]["oracle_iterations"] = base["deflated_gmres30_iterations"]
+    var = variants(A, torch, np, dev, sp, args.precision) if not args.no_variants else None
+    base = cpu_baseline(w, sizes, info.n_C, plain["pcg_iterations"]) if (world == 1 or rank == 0) else None
     line = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == 0 else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": M.n, "nnz": int(M.rowptr[-1]), "N": w["N"], "overlap": w["overlap"],
-                   "tau": w["tau"], "rtol": RTOL, "n_C": info.n_C, "eps": info.eps, "pcg_iterations": its[-1],
-                   "cond_est": cond[-1],
-                   "jacobi": {"sweeps_svd": info.sweeps_svd, "sweeps_eig": info.sweeps_eig,
-                              "sweeps_svd_fp32": info.sweeps_svd32, "sweeps_eig_fp32": info.sweeps_eig32,
-                              "rotations_svd": info.rotations_svd, "rotations_eig": info.rotations_eig},
-                   "oracle_pcg_iterations": base_its, "l2": "flushed (256 MB write) before every timed step",
-                   "setup_ms": statistics.median(setup_ms), "solve_ms": statistics.median(solve_ms),
-                   "setup_solve_note": "wall time of the amdd_setup and amdd_pcg_solve calls (each synchronises)",
+        "config": {"workload": w["name"], "n": M.n, "nnz": int(M.rowptr[-1]), "N": w["N"], "overlap": w["overlap"],
+                   "tau": w["tau"], "rtol": RTOL, "n_C": info.n_C, "eps": info.eps,
+                   "subdomain_sizes": {"n_i_min": min(t[1] for t in sizes), "n_i_max": max(t[1] for t in sizes),
+                                       "tilde_n_i_max": max(t[2] for t in sizes),
+                                       "Omega_Ii_min": min(t[0] for t in sizes),
+                                       "Omega_Ii_max": max(t[0] for t in sizes)},
+                   "arms": {"mixed": {k: v for k, v in mixed.items() if k != "step_ms"},
+                            "plain_fp64": {k: v for k, v in plain.items() if k != "step_ms"},
+                            "plain_over_mixed": plain["ms"] / mixed["ms"],
+                            "note": "each arm's ms is setup + PCG device-timed per step; setup_ms and solve_ms are "
+                                    "the wall times of the amdd_setup and amdd_pcg_solve calls (each synchronises)"},
+                   "pcg_graphs": graphs,
+                   "device_bytes_peak": info.device_bytes_peak,
+                   "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "form": FORMS[args.precision],
                    "profiling_events_in_timed_region": "dominant kernel class only"},
@@ -613,6 +846,8 @@ def main():
                     help="skip the deflated GMRES and three-level variant timings")
     ap.add_argument("--scale-m", type=int, default=None,
                     help="grid side of the bandwidth problem (default 1024; 16 x 16 boxes)")
+    ap.add_argument("--plain-steps", type=int, default=3,
+                    help="timed steps of the plain FP64 arm (at most --steps)")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
                     help="0: plain FP64 form; 1: mixed form (FP32 local work, FP64 coarse and PCG); "
                          "2: mixed form with an FP64 splitting")

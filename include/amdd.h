@@ -49,7 +49,7 @@ typedef enum {
     AMDD_ERR_NOT_SPD = 2,     /* a Cholesky pivot <= 0 (A_ii or E not SPD)         */
     AMDD_ERR_NOCONV = 3,      /* PCG reached maxit before the tolerance            */
     AMDD_ERR_OOM = 4,         /* a device or host allocation failed                */
-    AMDD_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up           */
+    AMDD_ERR_TIMEOUT = 5,     /* a bounded device wait (tensor-core GEMM) gave up   */
     AMDD_ERR_CUDA = 6,        /* any other CUDA runtime error                      */
     AMDD_ERR_EIG_NOCONV = 7   /* a Jacobi eigensolver hit its sweep limit          */
 } amdd_status;
@@ -130,11 +130,20 @@ typedef struct {
                              host synchronisation, and stops them on the device once converged
                              (same arithmetic and results as 0); 0: one launch sequence and one
                              host synchronisation per iteration; default 1                        */
-    int32_t reserved2;    /* must be zero                                                          */
+    int32_t autotune;     /* 1: the batched GEMM tile (16, 32 or 64) is measured once per size
+                             bucket and process on the first batch that can be rerun, and the
+                             fastest kept (the tile size never changes a result, only its time);
+                             0: a fixed rule on the launch size; default 1                          */
     size_t mem_budget;    /* largest number of device bytes the handle may hold at once, setup
                              temporaries included; an allocation beyond it fails with
                              AMDD_ERR_OOM before it is made (amdd_info.device_bytes_peak reports
                              what a setup used); 0 (default): no limit                             */
+    int32_t tensor_cores; /* 1: FP32 batched GEMMs of at least 16 output tiles of 128 x 128 (the
+                             mixed form's local products) run on the tcgen05 tensor cores in TF32
+                             with the 3xTF32 split (hi*hi + hi*lo + lo*hi, FP32 accumulation), whose
+                             error is of the order of an FP32 multiply-add loop's; 0: CUDA-core FMA;
+                             default 0                                                              */
+    int32_t reserved3;    /* must be zero                                                          */
 } amdd_opts;
 
 typedef struct {
@@ -183,9 +192,13 @@ typedef struct {
     int64_t inner_solves;      /* coarse solves done by inner GMRES (since setup) */
     int64_t inner_iterations;  /* their total iteration count                  */
     int32_t n_tied;            /* eigenvalues of eq. (Zi) with |lambda tau - 1| <= tie_band */
-    int32_t reserved;
+    int32_t n_below_one;       /* computed eigenvalues of eq. (Zi) below 1 - 1e-6: every
+                                  non-zero one is >= 1 with Boolean D_i, so these are rounding
+                                  (of an FP32 splitting); for tau >= 1.01 they are selected
+                                  like the others                                          */
     int64_t device_bytes_peak; /* largest device memory the handle has held (bytes) */
     int64_t graph_solves;      /* PCG solves whose iterations ran as one CUDA graph   */
+    int64_t tuned_buckets;     /* GEMM size buckets measured by the autotuner in this process */
 } amdd_info;
 
 /* Symbolic phase of a sparse local Cholesky factorisation, on the host (no
@@ -207,8 +220,22 @@ amdd_status amdd_nd_order(int64_t n, const int64_t* rowptr, const int32_t* colin
                           int32_t* parent, int64_t* colcount, int64_t* nnzL);
 
 /* Fill `o` with the defaults (eps = 2^-52, max_sweeps = 60, tie_band = 1e-10,
- * use_graphs = 1, everything else 0). */
+ * use_graphs = 1, autotune = 1, everything else 0). */
 amdd_status amdd_opts_default(amdd_opts* o);
+
+/* C = alpha op(A) op(B) + beta C in FP32 (row-major; op(A) = A if ta = 0,
+ * A^T if ta = 1; op(A) is m x k, op(B) is k x n), the dense block product the
+ * setup's FP32 stage uses (Sec. 3.2: the splitting, the local Cholesky
+ * factors and eq. (Zi)).  tensor_cores = 1: the tcgen05 kernel with the
+ * 3xTF32 split (TF32 units, FP32 accumulation, error of the order of an FP32
+ * multiply-add loop's); 0: CUDA-core FMA.  A, B, C are device pointers with
+ * leading dimensions lda, ldb, ldc (>= the stored row length); work runs on
+ * `stream` and is complete on return.  The call makes one small stream-ordered
+ * allocation for its descriptors.  AMDD_ERR_INVALID on bad sizes or flags;
+ * AMDD_ERR_TIMEOUT if a bounded wait of the tensor-core kernel gave up. */
+amdd_status amdd_gemm_f32(int32_t m, int32_t n, int32_t k, float alpha, const float* A, int32_t lda, int32_t ta,
+                          const float* B, int32_t ldb, int32_t tb, float beta, float* C, int32_t ldc,
+                          int32_t tensor_cores, void* stream);
 
 /* y = A x (Sec. 1: the operator of A x = b).  A, x (length n) and y
  * (length n) are device pointers; y must not alias x.  Work is issued on
@@ -442,7 +469,7 @@ amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, i
  * amdd_setup, amdd_apply and amdd_pcg_solve until amdd_reset_profile.
  * Synchronises the handle's stream.  AMDD_ERR_INVALID if profiling is off or
  * k is out of range. */
-#define AMDD_PROF_CLASSES 25
+#define AMDD_PROF_CLASSES 26
 amdd_status amdd_get_profile(amdd_handle* h, int32_t k, const char** name, int64_t* launches, double* ms,
                              double* flops, double* bytes);
 

@@ -32,7 +32,8 @@ class amdd_opts(C.Structure):
                 ("precision", C.c_int32), ("profile_classes", C.c_uint32), ("eig_solver", C.c_int32),
                 ("keep_proposal_data", C.c_int32), ("proposal", C.POINTER(amdd_proposal)),
                 ("keep_coarse_matrix", C.c_int32), ("reserved", C.c_int32), ("tie_band", C.c_double),
-                ("use_graphs", C.c_int32), ("reserved2", C.c_int32), ("mem_budget", C.c_size_t)]
+                ("use_graphs", C.c_int32), ("autotune", C.c_int32), ("mem_budget", C.c_size_t),
+                ("tensor_cores", C.c_int32), ("reserved3", C.c_int32)]
 
 
 MLP_NPARAM = 140032
@@ -57,7 +58,8 @@ class amdd_info(C.Structure):
                 ("lobpcg_iters_total", C.c_int64), ("robust_schur", C.c_int32), ("levels", C.c_int32),
                 ("inner_iterations_max", C.c_int32),
                 ("inner_solves", C.c_int64), ("inner_iterations", C.c_int64), ("n_tied", C.c_int32),
-                ("reserved", C.c_int32), ("device_bytes_peak", C.c_int64), ("graph_solves", C.c_int64)]
+                ("n_below_one", C.c_int32), ("device_bytes_peak", C.c_int64), ("graph_solves", C.c_int64),
+                ("tuned_buckets", C.c_int64)]
 
 
 class AmddError(RuntimeError):
@@ -72,6 +74,9 @@ _lib = None
 SIGNATURES = {
     "amdd_opts_default": (C.c_int, [C.POINTER(amdd_opts)]),
     "amdd_spmv": (C.c_int, [C.POINTER(amdd_csr), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "amdd_gemm_f32": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_void_p, C.c_int32, C.c_int32,
+                                C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_void_p, C.c_int32, C.c_int32,
+                                C.c_void_p]),
     "amdd_setup": (C.c_int, [C.POINTER(amdd_csr), C.c_void_p, C.c_int32, C.c_int32, C.c_double,
                              C.POINTER(amdd_opts), C.c_void_p, C.POINTER(C.c_void_p)]),
     "amdd_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
@@ -151,6 +156,13 @@ def opts_default() -> amdd_opts:
 
 def make_csr(n: int, nnz: int, rowptr_ptr: int, colind_ptr: int, val_ptr: int) -> amdd_csr:
     return amdd_csr(n, nnz, rowptr_ptr, colind_ptr, val_ptr)
+
+
+def gemm_f32(m: int, n: int, k: int, alpha: float, a_ptr: int, lda: int, ta: int, b_ptr: int, ldb: int, tb: int,
+             beta: float, c_ptr: int, ldc: int, tensor_cores: int = 1, stream: int = 0) -> None:
+    """C = alpha op(A) op(B) + beta C in FP32 through amdd_gemm_f32."""
+    _check(lib().amdd_gemm_f32(m, n, k, alpha, a_ptr, lda, ta, b_ptr, ldb, tb, beta, c_ptr, ldc, tensor_cores,
+                               stream), "amdd_gemm_f32")
 
 
 def spmv(A: amdd_csr, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
@@ -347,7 +359,7 @@ def lanczos_extremes(alpha, beta):
     return lo.value, hi.value
 
 
-PROF_CLASSES = 25
+PROF_CLASSES = 26
 
 
 def get_profile(h: int):

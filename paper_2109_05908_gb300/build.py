@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libamdd.so")
 SOURCES = ["amdd.cu", "dense_kernels.cu", "sparse_kernels.cu", "learned.cu", "noalloc.cu", "krylov_kernels.cu",
-           "symbolic.cu"]
+           "symbolic.cu", "tc_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-Xcompiler", "-Wno-free-nonheap-object",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

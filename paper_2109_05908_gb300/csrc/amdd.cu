@@ -17,6 +17,10 @@
 #include <numeric>
 #include <vector>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "amdd.h"
 #include "amdd_internal.h"
 
@@ -69,6 +73,7 @@ enum ProfK {
     PK_GEMV_F32,
     PK_CSOLVE,
     PK_GMRES,
+    PK_GEMM_TC,
     PK_COUNT
 };
 static_assert(PK_COUNT == AMDD_PROF_CLASSES, "profile classes");
@@ -76,7 +81,7 @@ static const char* const kProfNames[PK_COUNT] = {
     "gather_values", "chol_diag", "chol_panel", "gemm_tiles", "trtri_diag", "jacobi_svd", "jacobi_eig", "jacobi_f32", "tridiag", "bisect",
     "small_dense", "e_offdiag", "spmv", "gemv_rows", "gather_scatter", "pcg_vectors",
     "gemm_tiles_f32", "chol_diag_f32", "chol_panel_f32", "trtri_diag_f32", "tridiag_f32", "bisect_f32",
-    "gemv_rows_f32", "coarse_solve", "gmres_vectors"};
+    "gemv_rows_f32", "coarse_solve", "gmres_vectors", "gemm_tc_f32"};
 
 // class of a kernel in element type T (FP32 variants have their own classes)
 template <typename T>
@@ -252,11 +257,15 @@ struct amdd_handle {
     size_t bytes_now = 0, bytes_peak = 0, mem_budget = 0;
     double tie_band = 1e-10;
     int n_tied = 0;  // eigenvalues with |lambda tau - 1| <= tie_band
+    int n_below_one = 0;  // computed eigenvalues below the bound 1 (rounding)
     int use_graphs = 1;
+    int autotune = 1;  // GEMM tile autotuner (process-wide table)
+    int tensor_cores = 0;  // FP32 GEMMs on tcgen05 (3xTF32)
     // PCG iterations as a CUDA graph (amdd_opts.use_graphs): a device-side
     // while-loop over one iteration, built on the first solve of a tolerance
     cudaGraph_t pg_graph = nullptr;
     cudaGraphExec_t pg_exec = nullptr;
+    cudaStream_t s_cap = nullptr;  // private stream the loop is captured on (the legacy stream cannot be)
     double pg_tol2 = -1.0;
     bool pg_failed = false;  // the runtime could not capture the loop: per-iteration launches
     double *d_px = nullptr, *d_alog = nullptr, *d_blog = nullptr;
@@ -373,18 +382,123 @@ constexpr int SMALL_LAUNCH_TILES = 2 * 152;
 // two multiply-adds per clock per SM, a few large tiles leave most SMs idle and
 // each tile's chain long.
 constexpr int TINY_LAUNCH_TILES = 152 / 2;
+// Smallest batch (in 128 x 128 output tiles) that takes the tensor-core GEMM.
+constexpr int TC_MIN_TILES = 16;
+
+// Process-wide autotuner of the GEMM tile (amdd_opts.autotune): per element
+// type and size bucket (the batch's count of 64 x 64 output tiles and its
+// largest k, each rounded up to a power of two) the tile size, 16, 32 or 64,
+// that ran a batch of that bucket fastest.  It is measured once per bucket,
+// with CUDA events on the handle's stream, on the first batch whose outputs
+// may be written more than once (beta = 0 and no output overlapping an
+// input); until then the launch-size rule decides.  Every tile size sums each
+// output over k in the same order, so the choice changes the time and never
+// the result.
+struct TileTuner {
+    std::mutex mu;
+    std::map<std::tuple<int, int, int>, int> best;
+    int64_t measured = 0;  // buckets measured in this process
+};
+TileTuner& tile_tuner() {
+    static TileTuner t;
+    return t;
+}
+
+inline int ceil_log2(int64_t v) {
+    int b = 0;
+    while ((int64_t{1} << b) < v) ++b;
+    return b;
+}
+
+template <typename T>
+bool rewritable(const std::vector<GemmDescT<T>>& ds) {
+    for (const GemmDescT<T>& g : ds) {
+        if (g.m <= 0 || g.n <= 0) continue;
+        if (g.beta != T(0)) return false;
+        const char* c0 = reinterpret_cast<const char*>(g.C);
+        const char* c1 = reinterpret_cast<const char*>(g.C + (size_t)(g.m - 1) * g.ldc + g.n);
+        const int64_t ar = g.ta ? g.k : g.m, ac = g.ta ? g.m : g.k;
+        const int64_t br = g.tb ? g.n : g.k, bc = g.tb ? g.k : g.n;
+        const char* a0 = reinterpret_cast<const char*>(g.A);
+        const char* a1 = reinterpret_cast<const char*>(g.A + (size_t)(ar - 1) * g.lda + ac);
+        const char* b0 = reinterpret_cast<const char*>(g.B);
+        const char* b1 = reinterpret_cast<const char*>(g.B + (size_t)(br - 1) * g.ldb + bc);
+        if ((c0 < a1 && a0 < c1) || (c0 < b1 && b0 < c1)) return false;
+    }
+    return true;
+}
 
 template <typename T>
 void gemm(Ctx& C, const std::vector<GemmDescT<T>>& ds) {
     int tile = GEMM_T;
     std::vector<TileRef> tiles = gemm_tiles(ds, tile);
     if (tiles.empty()) return;
-    if ((int)tiles.size() < SMALL_LAUNCH_TILES) {
-        tile = 32;
-        tiles = gemm_tiles(ds, tile);
-        if ((int)tiles.size() < TINY_LAUNCH_TILES) {
-            tile = 16;
-            tiles = gemm_tiles(ds, tile);
+    const int heuristic = (int)tiles.size() >= SMALL_LAUNCH_TILES
+                              ? 64
+                              : ((int)gemm_tiles(ds, 32).size() >= TINY_LAUNCH_TILES ? 32 : 16);
+    tile = heuristic;
+    const GemmDescT<T>* dd = C.up(ds);
+    if (C.h->autotune) {
+        int kmax = 1;
+        for (const GemmDescT<T>& g : ds) kmax = std::max(kmax, g.k);
+        const auto key = std::make_tuple((int)sizeof(T), ceil_log2((int64_t)tiles.size()), ceil_log2(kmax));
+        TileTuner& tt = tile_tuner();
+        int found = 0;
+        {
+            std::lock_guard<std::mutex> lock(tt.mu);
+            auto it = tt.best.find(key);
+            if (it != tt.best.end()) found = it->second;
+        }
+        if (found) {
+            tile = found;
+        } else if (rewritable(ds)) {
+            float best_ms = 0.0f;
+            int best_tile = heuristic;
+            cudaEvent_t e0, e1;
+            ck(cudaEventCreate(&e0));
+            ck(cudaEventCreate(&e1));
+            for (int cand : {64, 32, 16}) {
+                const std::vector<TileRef> tc = gemm_tiles(ds, cand);
+                const TileRef* dtc = C.up(tc);
+                launch_gemm<T>(dd, dtc, (int)tc.size(), cand, C.h->s);  // warm (first-launch costs)
+                ck(cudaEventRecord(e0, C.h->s));
+                launch_gemm<T>(dd, dtc, (int)tc.size(), cand, C.h->s);
+                ck(cudaEventRecord(e1, C.h->s));
+                ck(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                ck(cudaEventElapsedTime(&ms, e0, e1));
+                if (cand == 64 || ms < best_ms) {
+                    best_ms = ms;
+                    best_tile = cand;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            tile = best_tile;
+            std::lock_guard<std::mutex> lock(tt.mu);
+            tt.best[key] = best_tile;
+            tt.measured += 1;
+        }
+    }
+    if (tile != GEMM_T) tiles = gemm_tiles(ds, tile);
+    if constexpr (std::is_same<T, float>::value) {
+        // the tensor-core path (amdd_opts.tensor_cores) for batches of at least
+        // TC_MIN_TILES 128 x 128 output tiles
+        if (C.h->tensor_cores) {
+            std::vector<TileRef> tt = gemm_tiles(ds, TC_GEMM_TILE);
+            if ((int)tt.size() >= TC_MIN_TILES) {
+                double fl = 0.0;
+                for (const GemmDescT<T>& g : ds) {
+                    if (g.m <= 0 || g.n <= 0) continue;
+                    const double m = g.m, n = g.n;
+                    const double outs = g.lower ? (n <= m ? m * n - n * (n - 1) / 2 : m * (m + 1) / 2) : m * n;
+                    fl += 2.0 * outs * g.k;
+                }
+                const TileRef* dtt = C.up(tt);
+                PScope ps(C.h, PK_GEMM_TC, fl);
+                launch_gemm_tc(dd, dtt, (int)tt.size(), C.h->d_err, C.h->s);
+                return;
+            }
         }
     }
     double fl = 0.0;
@@ -394,7 +508,6 @@ void gemm(Ctx& C, const std::vector<GemmDescT<T>>& ds) {
         const double outs = g.lower ? (n <= m ? m * n - n * (n - 1) / 2 : m * (m + 1) / 2) : m * n;
         fl += 2.0 * outs * g.k;
     }
-    const GemmDescT<T>* dd = C.up(ds);
     const TileRef* dt = C.up(tiles);
     PScope ps(C.h, pk<T>(PK_GEMM, PK_GEMM_F32), fl);
     launch_gemm<T>(dd, dt, (int)tiles.size(), tile, C.h->s);
@@ -802,6 +915,7 @@ int read_err(amdd_handle* h) {
 amdd_status err_status(int e) {
     if (e & DERR_NOT_SPD) return AMDD_ERR_NOT_SPD;
     if (e & DERR_EIG_NOCONV) return AMDD_ERR_EIG_NOCONV;
+    if (e & DERR_TIMEOUT) return AMDD_ERR_TIMEOUT;
     if (e) return AMDD_ERR_CUDA;
     return AMDD_OK;
 }
@@ -2762,6 +2876,7 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     h->coff.assign(N + 1, 0);
     h->off_zt.assign(N + 1, 0);
     std::vector<int> partial;  // subdomains whose selection is neither empty nor everything
+    const bool full_by_bound = h->tau >= 1.01;
     for (int i = 0; i < N; ++i) {
         const int nIi = h->nI[i];
         int pi = 0;
@@ -2774,7 +2889,12 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                 lam = (m > 0.0) ? 1.0 / m : std::numeric_limits<double>::infinity();
             }
             h->lam_h[h->off_I[i] + j] = lam;
-            if (lam > 1.0 / h->tau) ++pi;
+            // with Boolean D_i every non-zero eigenvalue of eq. (Zi) is at least 1
+            // (Lemma 3.2 and Courant-Fischer), so for tau >= 1.01 each one is
+            // selected whatever rounding did to its computed value (an FP32
+            // splitting can leave one far below the bound); such values are counted
+            if (lam > 1.0 / h->tau || full_by_bound) ++pi;
+            if (lam < 1.0 - 1e-6) ++h->n_below_one;
             if (std::fabs(lam * h->tau - 1.0) <= h->tie_band) ++h->n_tied;
         }
         h->p[i] = pi;
@@ -3681,6 +3801,7 @@ bool pcg_graph(amdd_handle* h, double tol2, int maxit) {
     h->pg_graph = nullptr;
     const int64_t n = h->n;
     cudaStream_t s = h->s;
+    cudaStream_t s_main = h->s;
     if (maxit > h->pg_cap) {
         h->pg_cap = std::max(maxit, 1024);
         h->d_alog = dnew<double>(h, h->pg_cap);
@@ -3703,11 +3824,17 @@ bool pcg_graph(amdd_handle* h, double tol2, int maxit) {
         cp.conditional.size = 1;
         ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
     }
+    // capture on a private non-blocking stream: the handle's stream may be the
+    // legacy default stream, which cannot be captured; every launch of the
+    // loop goes to h->s, so h->s names the capture stream meanwhile
+    if (ok && !h->s_cap) ok = cudaStreamCreateWithFlags(&h->s_cap, cudaStreamNonBlocking) == cudaSuccess;
     if (ok)
-        ok = cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+        ok = cudaStreamBeginCaptureToGraph(h->s_cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                            cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
         bool launched = true;
+        h->s = h->s_cap;
+        s = h->s_cap;
         try {
             apply_one(h, h->d_r, h->d_z);
             dot_h(h, h->d_r, h->d_z, 1, tol2);
@@ -3721,7 +3848,9 @@ bool pcg_graph(amdd_handle* h, double tol2, int maxit) {
             launched = false;
         }
         cudaGraph_t body = nullptr;
-        const cudaError_t e = cudaStreamEndCapture(s, &body);
+        const cudaError_t e = cudaStreamEndCapture(h->s_cap, &body);
+        h->s = s_main;
+        s = s_main;
         ok = launched && e == cudaSuccess;
     }
     if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
@@ -3764,7 +3893,70 @@ amdd_status amdd_opts_default(amdd_opts* o) {
     o->max_sweeps = 60;
     o->tie_band = 1e-10;
     o->use_graphs = 1;
+    o->autotune = 1;
     return AMDD_OK;
+}
+
+amdd_status amdd_gemm_f32(int32_t m, int32_t n, int32_t k, float alpha, const float* A, int32_t lda, int32_t ta,
+                          const float* B, int32_t ldb, int32_t tb, float beta, float* C, int32_t ldc,
+                          int32_t tensor_cores, void* stream) {
+    if (m < 0 || n < 0 || k < 0 || (ta != 0 && ta != 1) || (tb != 0 && tb != 1) ||
+        (tensor_cores != 0 && tensor_cores != 1))
+        return AMDD_ERR_INVALID;
+    if (m == 0 || n == 0) return AMDD_OK;
+    if (!C || (k > 0 && (!A || !B)) || ldc < n || (k > 0 && lda < (ta ? m : k)) || (k > 0 && ldb < (tb ? k : n)))
+        return AMDD_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GemmDescT<float> g;
+    g.A = A;
+    g.B = B;
+    g.C = C;
+    g.m = m;
+    g.n = n;
+    g.k = k;
+    g.lda = lda;
+    g.ldb = ldb;
+    g.ldc = ldc;
+    g.ta = ta;
+    g.tb = tb;
+    g.lower = 0;
+    g.kfrom_row = 0;
+    g.alpha = alpha;
+    g.beta = beta;
+    const int tile = tensor_cores ? TC_GEMM_TILE : GEMM_T;
+    std::vector<TileRef> tiles;
+    for (int a = 0; a < cdiv(m, tile); ++a)
+        for (int b = 0; b < cdiv(n, tile); ++b) tiles.push_back({0, a, b});
+    void* buf = nullptr;
+    const size_t bytes = sizeof(g) + tiles.size() * sizeof(TileRef) + sizeof(int);
+    if (cudaMallocAsync(&buf, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return AMDD_ERR_OOM;
+    }
+    std::vector<unsigned char> host(bytes, 0);
+    std::memcpy(host.data(), &g, sizeof(g));
+    std::memcpy(host.data() + sizeof(g), tiles.data(), tiles.size() * sizeof(TileRef));
+    auto* dg = static_cast<GemmDescT<float>*>(buf);
+    auto* dt = reinterpret_cast<TileRef*>(static_cast<unsigned char*>(buf) + sizeof(g));
+    auto* derr = reinterpret_cast<int*>(static_cast<unsigned char*>(buf) + sizeof(g) + tiles.size() * sizeof(TileRef));
+    amdd_status st = AMDD_OK;
+    if (cudaMemcpyAsync(buf, host.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) st = AMDD_ERR_CUDA;
+    if (st == AMDD_OK) {
+        if (tensor_cores)
+            launch_gemm_tc(dg, dt, (int)tiles.size(), derr, s);
+        else
+            launch_gemm<float>(dg, dt, (int)tiles.size(), tile, s);
+        int e = 0;
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&e, derr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            st = AMDD_ERR_CUDA;
+        else if (e)
+            st = err_status(e);
+    }
+    cudaFreeAsync(buf, s);
+    cudaStreamSynchronize(s);
+    return st;
 }
 
 amdd_status amdd_spmv(const amdd_csr* A, const double* x, double* y, void* stream) {
@@ -3821,7 +4013,9 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         o = *opts;
         if (!(o.eps > 0.0) || o.max_sweeps < 1 || o.precision < 0 || o.precision > 2) return AMDD_ERR_INVALID;
         if (o.reserved != 0 || o.keep_coarse_matrix < 0 || o.keep_coarse_matrix > 1) return AMDD_ERR_INVALID;
-        if (!(o.tie_band >= 0.0) || o.use_graphs < 0 || o.use_graphs > 1 || o.reserved2 != 0) return AMDD_ERR_INVALID;
+        if (!(o.tie_band >= 0.0) || o.use_graphs < 0 || o.use_graphs > 1 || o.autotune < 0 || o.autotune > 1)
+            return AMDD_ERR_INVALID;
+        if (o.tensor_cores < 0 || o.tensor_cores > 1 || o.reserved3 != 0) return AMDD_ERR_INVALID;
         if (o.profile_classes >> PK_COUNT) return AMDD_ERR_INVALID;
         if (o.eig_solver < 0 || o.eig_solver > 3) return AMDD_ERR_INVALID;
         // the matrix-free eigensolve: FP64 only, with the shift far enough above
@@ -3860,6 +4054,8 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         h->tie_band = o.tie_band;
         h->mem_budget = o.mem_budget;
         h->use_graphs = o.use_graphs;
+        h->autotune = o.autotune;
+        h->tensor_cores = o.tensor_cores;
         if (o.eig_solver == 2) {
             h->prop = *o.proposal;
             h->have_prop = true;
@@ -4418,8 +4614,13 @@ amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
     info->inner_solves = h->in_calls;
     info->inner_iterations = h->in_its;
     info->n_tied = h->n_tied;
+    info->n_below_one = h->n_below_one;
     info->device_bytes_peak = (int64_t)h->bytes_peak;
     info->graph_solves = h->graph_solves;
+    {
+        std::lock_guard<std::mutex> lock(tile_tuner().mu);
+        info->tuned_buckets = tile_tuner().measured;
+    }
     return AMDD_OK;
 }
 
@@ -4510,6 +4711,7 @@ void amdd_destroy(amdd_handle* h) {
     h->prof.release();
     if (h->pg_exec) cudaGraphExecDestroy(h->pg_exec);
     if (h->pg_graph) cudaGraphDestroy(h->pg_graph);
+    if (h->s_cap) cudaStreamDestroy(h->s_cap);
     for (void* p : h->allocs) cudaFreeAsync(p, h->s);
     cudaStreamSynchronize(h->s);
     delete h;

@@ -15,6 +15,7 @@ enum : int {
     DERR_NOT_SPD = 1,        // Cholesky pivot <= 0 (or NaN) without clamping
     DERR_EIG_NOCONV = 2,     // Jacobi sweep limit reached
     DERR_BOUNDS = 4,         // an index check failed
+    DERR_TIMEOUT = 8,        // a bounded device wait (mbarrier) gave up
 };
 
 constexpr int CHOL_NB = 32;     // diagonal block of the blocked Cholesky / inverse
@@ -149,6 +150,12 @@ size_t jacobi_pair_smem();
 template <typename T>
 void launch_jacobi_pair_round(const JacobiDescT<T>* d, const int4* tasks, int ntasks, int round, T tol, int* rotated,
                               unsigned long long* rots, cudaStream_t s);
+// Batched FP32 GEMM on the tensor cores (tcgen05, TF32 with the 3xTF32 split
+// for FP32 accuracy), 128 x 128 output tiles (TileRef tm, tn in units of 128);
+// a wait that gives up latches DERR_TIMEOUT in *err.
+constexpr int TC_GEMM_TILE = 128;
+size_t gemm_tc_smem();
+void launch_gemm_tc(const GemmDescT<float>* d_descs, const TileRef* d_tiles, int ntiles, int* err, cudaStream_t s);
 // *p |= bits (one thread)
 void launch_or_flag(int* p, int bits, cudaStream_t s);
 // Shared-memory-resident block variant; returns false (nothing launched) when

@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
     // rotation of each of the JP_R / 2 disjoint pairs of an inner round
     __shared__ T r_cs[JP_R / 2], r_sn[JP_R / 2], r_a[JP_R / 2], r_b[JP_R / 2];
     __shared__ int r_p[JP_R / 2], r_q[JP_R / 2], r_do[JP_R / 2];
-    __shared__ int any_rot;
+    __shared__ int any_rot, any_outer;
     const int4 tk = tasks[blockIdx.x];
     const int mat = tk.x, kp = tk.y, nblk = tk.z;
     if (round >= nblk - 1) return;  // uniform over the CTA
@@ -601,11 +601,19 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
         __syncthreads();
     }
 
-    // ---- 2. two-sided cyclic Jacobi on G, rotations accumulated in Qt
+    // ---- 2. two-sided cyclic Jacobi on G, rotations accumulated in Qt.  The
+    // stopping test of the sweep (tol) decides whether the pair is rotated at
+    // all; once it is, the pair is orthogonalised to a tighter inner test (tin,
+    // still well above the rounding of G), so that one visit leaves it
+    // converged and the outer sweeps do not revisit rounding-level couplings.
+    const T tin = fmax(tol * T(1.0 / 64.0), T(16) * (sizeof(T) == 4 ? T(1.1920928955078125e-7) : T(2.220446049250313e-16)));
     int first_any = 0;
     unsigned nrot = 0;
     for (int sw = 0; sw < JP_INNER; ++sw) {
-        if (tid == 0) any_rot = 0;
+        if (tid == 0) {
+            any_rot = 0;
+            any_outer = 0;
+        }
         __syncthreads();
         for (int rr = 0; rr < JP_R - 1; ++rr) {
             if (tid < JP_R / 2) {
@@ -618,7 +626,8 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
                     q = (rr - tid + JP_R - 1) % (JP_R - 1);
                 }
                 const T a = G[p * JP_LDG + p], b = G[q * JP_LDG + q], g = G[p * JP_LDG + q];
-                const bool doit = g != T(0) && g * g > tol * tol * a * b && fabs(g) > absf;
+                const bool doit = g != T(0) && g * g > tin * tin * a * b && fabs(g) > absf;
+                if (g != T(0) && g * g > tol * tol * a * b && fabs(g) > absf) any_outer = 1;
                 r_p[tid] = p;
                 r_q[tid] = q;
                 r_do[tid] = doit ? 1 : 0;
@@ -671,9 +680,9 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
             __syncthreads();
         }
         const int any = any_rot;
-        if (sw == 0) first_any = any;
+        if (sw == 0) first_any = any_outer;
         __syncthreads();
-        if (!any) break;
+        if (!any || !first_any) break;
     }
     if (!first_any) return;  // the pair met the stopping test: rows unchanged
     if (nrot) atomicAdd(rots + mat, (unsigned long long)nrot);

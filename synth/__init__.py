@@ -391,3 +391,18 @@ def workload_c1():
     m = 64
     return dict(A=laplace2d(m), part=box_partition_2d(m, 16), N=16, overlap=1, tau=50.0,
                 b=rhs(m * m, 0), name="laplace2d_64x64_16box_ov1_tau50")
+
+
+def workload_diffusion3d(m: int = 32, N: int = 16, lo: int = 1024, hi: int = 4096, overlap: int = 2,
+                         tau: float = 100.0, sigma: float = 2.0, corr: float = 8.0, n_channels: int = 16,
+                         seed: int = 0):
+    """3D 7-point channelled diffusion on an m^3 grid (lognormal coefficient,
+    correlation length corr, n_channels one-cell channels of 1e6 along x),
+    N seeded BFS subdomains of lo..hi cells, overlap layers, tau, b uniform
+    [-1, 1] (seed 0): the shape of the paper-scale diffusion configuration at
+    a size one GPU sets up in seconds in both precision forms."""
+    A = diffusion3d(m, sigma=sigma, corr=corr, n_channels=n_channels, seed=seed)
+    part = bfs_partition(A, N, seed, lo, hi)
+    Nn = int(part.max()) + 1
+    name = f"diffusion3d_{m}^3_sigma{sigma:g}_ch{n_channels}_bfs{Nn}_{lo}-{hi}_ov{overlap}_tau{tau:g}"
+    return dict(A=A, part=part, N=Nn, overlap=overlap, tau=tau, b=rhs(A.n, 0), name=name)
