@@ -143,13 +143,15 @@ void launch_jacobi_t(const JacobiDescT<T>* d, int nmat, int max_sweeps, T tol, i
 // round of the block round-robin schedule (blocks of 32 rows; tasks[t] =
 // {matrix, pair index in the round, blocks of that matrix (even, >= 2), 0});
 // rotated[matrix] is set when a pair of it was rotated, rots[matrix] counts
-// plane rotations.  The host runs the rounds of a sweep and the sweeps.
+// plane rotations, stats[5] accumulates pair tasks, rotated pairs and the SM
+// cycles of the three phases (Gram matrix, small eigensolve, rotation of the
+// rows).  The host runs the rounds of a sweep and the sweeps.
 constexpr int JP_ROWS = 32;
 template <typename T>
 size_t jacobi_pair_smem();
 template <typename T>
 void launch_jacobi_pair_round(const JacobiDescT<T>* d, const int4* tasks, int ntasks, int round, T tol, int* rotated,
-                              unsigned long long* rots, cudaStream_t s);
+                              unsigned long long* rots, unsigned long long* stats, cudaStream_t s);
 // Batched FP32 GEMM on the tensor cores (tcgen05, TF32 with the 3xTF32 split
 // for FP32 accuracy), 128 x 128 output tiles (TileRef tm, tn in units of 128);
 // a wait that gives up latches DERR_TIMEOUT in *err.

@@ -537,7 +537,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* __restrict__ descs,
                                                           const int4* __restrict__ tasks, int round, T tol,
                                                           int* __restrict__ rotated,
-                                                          unsigned long long* __restrict__ rots) {
+                                                          unsigned long long* __restrict__ rots,
+                                                          unsigned long long* __restrict__ stats) {
     extern __shared__ __align__(16) unsigned char jp_raw[];
     T* G = reinterpret_cast<T*>(jp_raw);
     T* Qt = G + JP_R * JP_LDG;
@@ -545,7 +546,6 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
     // rotation of each of the JP_R / 2 disjoint pairs of an inner round
     __shared__ T r_cs[JP_R / 2], r_sn[JP_R / 2], r_a[JP_R / 2], r_b[JP_R / 2];
     __shared__ int r_p[JP_R / 2], r_q[JP_R / 2], r_do[JP_R / 2];
-    __shared__ int any_rot, any_outer;
     const int4 tk = tasks[blockIdx.x];
     const int mat = tk.x, kp = tk.y, nblk = tk.z;
     if (round >= nblk - 1) return;  // uniform over the CTA
@@ -565,6 +565,9 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
         return r < d.rows ? r : -1;
     };
     const T absf = d.absfloor ? *d.absfloor : T(0);
+    // stats: [0] pair tasks, [1] pairs rotated, [2..4] SM clock cycles of the
+    // Gram matrix, the small eigensolve and the rotation of the rows (thread 0)
+    const long long t0 = clock64();
 
     // ---- 1. Gram matrix over ncols_dot columns
     {
@@ -602,20 +605,32 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
     }
 
     // ---- 2. two-sided cyclic Jacobi on G, rotations accumulated in Qt.  The
-    // stopping test of the sweep (tol) decides whether the pair is rotated at
-    // all; once it is, the pair is orthogonalised to a tighter inner test (tin,
-    // still well above the rounding of G), so that one visit leaves it
-    // converged and the outer sweeps do not revisit rounding-level couplings.
+    // stopping test of the sweep (tol) on the fresh Gram matrix decides
+    // whether the pair is rotated at all; once it is, the pair is
+    // orthogonalised to a tighter inner test (tin, still well above the
+    // rounding of G), so that one visit leaves it converged and the outer
+    // sweeps do not revisit rounding-level couplings.
     const T tin = fmax(tol * T(1.0 / 64.0), T(16) * (sizeof(T) == 4 ? T(1.1920928955078125e-7) : T(2.220446049250313e-16)));
-    int first_any = 0;
+    const long long t1 = clock64();
+    if (tid == 0) {
+        atomicAdd(stats + 0, 1ull);
+        atomicAdd(stats + 2, (unsigned long long)(t1 - t0));
+    }
+    {
+        int mine = 0;
+        for (int e = tid; e < JP_R * JP_R; e += 256) {
+            const int p = e / JP_R, q = e % JP_R;
+            if (q <= p) continue;
+            const T a = G[p * JP_LDG + p], b = G[q * JP_LDG + q], g = G[p * JP_LDG + q];
+            if (g != T(0) && g * g > tol * tol * a * b && fabs(g) > absf) mine = 1;
+        }
+        if (!__syncthreads_or(mine)) return;  // the pair met the stopping test: rows unchanged
+    }
     unsigned nrot = 0;
     for (int sw = 0; sw < JP_INNER; ++sw) {
-        if (tid == 0) {
-            any_rot = 0;
-            any_outer = 0;
-        }
-        __syncthreads();
+        int rot_mine = 0;
         for (int rr = 0; rr < JP_R - 1; ++rr) {
+            // the rotations of the round's JP_R / 2 disjoint pairs (identity where none)
             if (tid < JP_R / 2) {
                 int p, q;
                 if (tid == 0) {
@@ -627,10 +642,11 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
                 }
                 const T a = G[p * JP_LDG + p], b = G[q * JP_LDG + q], g = G[p * JP_LDG + q];
                 const bool doit = g != T(0) && g * g > tin * tin * a * b && fabs(g) > absf;
-                if (g != T(0) && g * g > tol * tol * a * b && fabs(g) > absf) any_outer = 1;
                 r_p[tid] = p;
                 r_q[tid] = q;
                 r_do[tid] = doit ? 1 : 0;
+                r_cs[tid] = T(1);
+                r_sn[tid] = T(0);
                 if (doit) {
                     T cs, sn, t;
                     jac_rotation(a, b, g, cs, sn, t);
@@ -638,55 +654,57 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
                     r_sn[tid] = sn;
                     r_a[tid] = fma(-t, g, a);
                     r_b[tid] = fma(t, g, b);
-                    any_rot = 1;
+                    rot_mine = 1;
                     ++nrot;
                 }
             }
             __syncthreads();
-            // rows p, q of G and of Qt
+            // G <- R G R^T by 2 x 2 blocks: rows {p, q} of pair P times columns
+            // {p', q'} of pair Q go to R_P B R_Q^T (each entry of G is in exactly one
+            // block); a rotated diagonal block becomes diag(a - t g, b + t g) exactly
+            for (int e = tid; e < (JP_R / 2) * (JP_R / 2); e += 256) {
+                const int P = e / (JP_R / 2), Q = e % (JP_R / 2);
+                if (!r_do[P] && !r_do[Q]) continue;
+                const int p = r_p[P], q = r_q[P];
+                if (P == Q) {
+                    G[p * JP_LDG + p] = r_a[P];
+                    G[q * JP_LDG + q] = r_b[P];
+                    G[p * JP_LDG + q] = T(0);
+                    G[q * JP_LDG + p] = T(0);
+                    continue;
+                }
+                const int p2 = r_p[Q], q2 = r_q[Q];
+                const T c1 = r_cs[P], s1 = r_sn[P], c2 = r_cs[Q], s2 = r_sn[Q];
+                const T b00 = G[p * JP_LDG + p2], b01 = G[p * JP_LDG + q2];
+                const T b10 = G[q * JP_LDG + p2], b11 = G[q * JP_LDG + q2];
+                const T u00 = fma(c1, b00, -s1 * b10), u01 = fma(c1, b01, -s1 * b11);
+                const T u10 = fma(s1, b00, c1 * b10), u11 = fma(s1, b01, c1 * b11);
+                G[p * JP_LDG + p2] = fma(c2, u00, -s2 * u01);
+                G[p * JP_LDG + q2] = fma(s2, u00, c2 * u01);
+                G[q * JP_LDG + p2] = fma(c2, u10, -s2 * u11);
+                G[q * JP_LDG + q2] = fma(s2, u10, c2 * u11);
+            }
+            // rows p, q of Qt
             for (int e = tid; e < (JP_R / 2) * JP_R; e += 256) {
                 const int k = e / JP_R, c = e % JP_R;
                 if (!r_do[k]) continue;
                 const int p = r_p[k], q = r_q[k];
                 const T cs = r_cs[k], sn = r_sn[k];
-                T u = G[p * JP_LDG + c], v = G[q * JP_LDG + c];
-                G[p * JP_LDG + c] = fma(cs, u, -sn * v);
-                G[q * JP_LDG + c] = fma(sn, u, cs * v);
-                u = Qt[p * JP_LDG + c];
-                v = Qt[q * JP_LDG + c];
+                const T u = Qt[p * JP_LDG + c], v = Qt[q * JP_LDG + c];
                 Qt[p * JP_LDG + c] = fma(cs, u, -sn * v);
                 Qt[q * JP_LDG + c] = fma(sn, u, cs * v);
             }
             __syncthreads();
-            // columns p, q of G
-            for (int e = tid; e < (JP_R / 2) * JP_R; e += 256) {
-                const int k = e / JP_R, c = e % JP_R;
-                if (!r_do[k]) continue;
-                const int p = r_p[k], q = r_q[k];
-                const T cs = r_cs[k], sn = r_sn[k];
-                const T u = G[c * JP_LDG + p], v = G[c * JP_LDG + q];
-                G[c * JP_LDG + p] = fma(cs, u, -sn * v);
-                G[c * JP_LDG + q] = fma(sn, u, cs * v);
-            }
-            __syncthreads();
-            // the rotated 2 x 2 block exactly: diag(a - t g, b + t g)
-            if (tid < JP_R / 2 && r_do[tid]) {
-                const int p = r_p[tid], q = r_q[tid];
-                G[p * JP_LDG + p] = r_a[tid];
-                G[q * JP_LDG + q] = r_b[tid];
-                G[p * JP_LDG + q] = T(0);
-                G[q * JP_LDG + p] = T(0);
-            }
-            __syncthreads();
         }
-        const int any = any_rot;
-        if (sw == 0) first_any = any_outer;
-        __syncthreads();
-        if (!any || !first_any) break;
+        if (!__syncthreads_or(rot_mine)) break;
     }
-    if (!first_any) return;  // the pair met the stopping test: rows unchanged
     if (nrot) atomicAdd(rots + mat, (unsigned long long)nrot);
-    if (tid == 0) rotated[mat] = 1;
+    const long long t2 = clock64();
+    if (tid == 0) {
+        rotated[mat] = 1;
+        atomicAdd(stats + 1, 1ull);
+        atomicAdd(stats + 3, (unsigned long long)(t2 - t1));
+    }
 
     // ---- 3. Y <- Qt Y over ncols_rot columns
     {
@@ -722,20 +740,21 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
             }
         }
     }
+    if (tid == 0) atomicAdd(stats + 4, (unsigned long long)(clock64() - t2));
 }
 
 template <typename T>
 void launch_jacobi_pair_round(const JacobiDescT<T>* d, const int4* tasks, int ntasks, int round, T tol, int* rotated,
-                              unsigned long long* rots, cudaStream_t s) {
+                              unsigned long long* rots, unsigned long long* stats, cudaStream_t s) {
     if (ntasks <= 0) return;
     const size_t smem = jacobi_pair_smem<T>();
     cudaFuncSetAttribute(jacobi_pair_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    jacobi_pair_kernel<T><<<ntasks, 256, smem, s>>>(d, tasks, round, tol, rotated, rots);
+    jacobi_pair_kernel<T><<<ntasks, 256, smem, s>>>(d, tasks, round, tol, rotated, rots, stats);
 }
 template void launch_jacobi_pair_round<float>(const JacobiDescT<float>*, const int4*, int, int, float, int*,
-                                              unsigned long long*, cudaStream_t);
+                                              unsigned long long*, unsigned long long*, cudaStream_t);
 template void launch_jacobi_pair_round<double>(const JacobiDescT<double>*, const int4*, int, int, double, int*,
-                                               unsigned long long*, cudaStream_t);
+                                               unsigned long long*, unsigned long long*, cudaStream_t);
 
 __global__ void or_flag_kernel(int* p, int bits) { atomicOr(p, bits); }
 void launch_or_flag(int* p, int bits, cudaStream_t s) { or_flag_kernel<<<1, 1, 0, s>>>(p, bits); }
@@ -1677,12 +1696,100 @@ __global__ void __launch_bounds__(256) gemv_rows4_kernel(const GemvDescT<T>* __r
     }
 }
 
+// The same products with 16-byte loads of the factor rows.  The four rows of
+// a warp start at arbitrary alignment: each gets a scalar head up to its first
+// 16-byte boundary, a vector body and a scalar tail; the bodies of the four
+// rows are streamed together (one 16-byte load per row and lane in flight per
+// step), x by scalar loads (it stays in L1).  Per row: lane-strided partial
+// sums and the fixed shuffle tree, so the result is reproducible run to run.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int V = 4;
+    __device__ static float dot(const float4& a, const float* x, float s) {
+        s = fmaf(a.x, __ldg(x), s);
+        s = fmaf(a.y, __ldg(x + 1), s);
+        s = fmaf(a.z, __ldg(x + 2), s);
+        return fmaf(a.w, __ldg(x + 3), s);
+    }
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int V = 2;
+    __device__ static double dot(const double2& a, const double* x, double s) {
+        s = fma(a.x, __ldg(x), s);
+        return fma(a.y, __ldg(x + 1), s);
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemv_rows4v_kernel(const GemvDescT<T>* __restrict__ descs,
+                                                          const int* __restrict__ grp_desc,
+                                                          const int* __restrict__ grp_row, int64_t ngroups) {
+    using VT = typename Vec16<T>::type;
+    constexpr int V = Vec16<T>::V;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= ngroups) return;
+    const GemvDescT<T> d = descs[grp_desc[w]];
+    const int r0 = grp_row[w];
+    const int nr = min(GEMV_RW, d.rows - r0);
+    int vs[GEMV_RW], nv[GEMV_RW];
+    T s[GEMV_RW];
+    int nvmax = 0;
+#pragma unroll
+    for (int k = 0; k < GEMV_RW; ++k) {
+        s[k] = T(0);
+        vs[k] = 0;
+        nv[k] = 0;
+        if (k < nr) {
+            const int r = r0 + k;
+            const int lo = (d.mode == 2) ? r : 0;
+            const int hi = (d.mode == 1) ? min(r + 1, d.ncols) : d.ncols;
+            const T* Mr = d.M + (size_t)r * d.ld;
+            const int mis = (int)((reinterpret_cast<uintptr_t>(Mr + lo) / sizeof(T)) % V);
+            const int v0 = min(hi, lo + (V - mis) % V);
+            if (lane < v0 - lo) s[k] = fma(Mr[lo + lane], d.x[lo + lane], s[k]);  // head
+            const int n = (hi - v0) / V;
+            const int ve = v0 + n * V;
+            if (lane < hi - ve) s[k] = fma(Mr[ve + lane], d.x[ve + lane], s[k]);  // tail
+            vs[k] = v0;
+            nv[k] = n;
+            nvmax = max(nvmax, n);
+        }
+    }
+    for (int j = lane; j < nvmax; j += 32) {
+        VT a[GEMV_RW];
+#pragma unroll
+        for (int k = 0; k < GEMV_RW; ++k)
+            if (j < nv[k]) a[k] = __ldg(reinterpret_cast<const VT*>(d.M + (size_t)(r0 + k) * d.ld + vs[k]) + j);
+#pragma unroll
+        for (int k = 0; k < GEMV_RW; ++k)
+            if (j < nv[k]) s[k] = Vec16<T>::dot(a[k], d.x + vs[k] + j * V, s[k]);
+    }
+    T mine = T(0);
+#pragma unroll
+    for (int k = 0; k < GEMV_RW; ++k) {
+        T v = s[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == k) mine = v;
+    }
+    if (lane < nr) {
+        const int r = r0 + lane;
+        d.y[r] = d.b ? fma(d.alpha, mine, d.b[r]) : d.alpha * mine;
+    }
+}
+
 template <typename T>
 void launch_gemv_rows4(const GemvDescT<T>* d, const int* grp_desc, const int* grp_row, int64_t ngroups,
                        cudaStream_t s) {
     if (ngroups <= 0) return;
     const int64_t blocks = (ngroups * 32 + 255) / 256;
-    gemv_rows4_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, grp_desc, grp_row, ngroups);
+    gemv_rows4v_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, grp_desc, grp_row, ngroups);
 }
 template void launch_gemv_rows4<float>(const GemvDescT<float>*, const int*, const int*, int64_t, cudaStream_t);
 template void launch_gemv_rows4<double>(const GemvDescT<double>*, const int*, const int*, int64_t, cudaStream_t);

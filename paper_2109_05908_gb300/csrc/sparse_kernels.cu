@@ -37,52 +37,13 @@ int spmv_group_for(int64_t n, int64_t nnz) {
     return per <= 8 ? 1 : (per <= 24 ? 8 : 32);
 }
 
-// Short rows (group 1): a warp takes 32 consecutive rows, whose entries are
-// one contiguous range of the CSR arrays.  The warp streams that range with
-// coalesced loads (lane k of a pass reads entry base + k), staging each
-// value and its x[col] in shared memory, then every lane accumulates its own
-// row from shared memory in ascending order with one fma per entry: the
-// arithmetic of a thread-per-row loop, with the memory traffic of a stream.
-// Ranges longer than SPMV_CAP entries are taken in passes.
-constexpr int SPMV_CAP = 256;
-__global__ void __launch_bounds__(256) spmv_stream_kernel(int64_t n, const int64_t* __restrict__ rowptr,
-                                                          const int32_t* __restrict__ col,
-                                                          const double* __restrict__ val,
-                                                          const double* __restrict__ x, double* __restrict__ y) {
-    __shared__ double sv[8][SPMV_CAP], sx[8][SPMV_CAP];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    for (int64_t r0 = gw * 32; r0 < n; r0 += nwarps * 32) {
-        const int64_t row = r0 + lane;
-        const int64_t b = row < n ? __ldg(rowptr + row) : 0;
-        const int64_t e = row < n ? __ldg(rowptr + row + 1) : 0;
-        const int64_t last = (r0 + 32 < n ? r0 + 32 : n);
-        const int64_t base = __shfl_sync(0xffffffffu, b, 0);
-        const int64_t end = __ldg(rowptr + last);
-        double acc = 0.0;
-        for (int64_t c0 = base; c0 < end; c0 += SPMV_CAP) {
-            const int64_t c1 = (c0 + SPMV_CAP < end) ? c0 + SPMV_CAP : end;
-            for (int64_t k = c0 + lane; k < c1; k += 32) {
-                sv[warp][k - c0] = __ldg(val + k);
-                sx[warp][k - c0] = __ldg(x + __ldg(col + k));
-            }
-            __syncwarp();
-            const int64_t lo = b > c0 ? b : c0, hi = e < c1 ? e : c1;
-            for (int64_t k = lo; k < hi; ++k) acc = fma(sv[warp][k - c0], sx[warp][k - c0], acc);
-            __syncwarp();
-        }
-        if (row < n) y[row] = acc;
-    }
-}
-
 void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, const double* x,
                  double* y, int group, cudaStream_t s) {
     if (n <= 0) return;
     const int64_t want = (n * group + 255) / 256;
     const int blocks = (int)(want < 152 * 64 ? want : 152 * 64);
     if (group <= 1)
-        spmv_stream_kernel<<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
+        spmv_kernel<1><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
     else if (group <= 4)
         spmv_kernel<4><<<blocks, 256, 0, s>>>(n, rowptr, col, val, x, y);
     else if (group <= 8)

@@ -1,24 +1,27 @@
 // Batched FP32 GEMM on the fifth-generation tensor cores (tcgen05, sm_103a):
 // C = alpha op(A) op(B) + beta C for every descriptor of a batch, one CTA per
-// 128 x 128 output tile, accumulator in tensor memory.
+// 128 x 128 output tile.
 //
 // FP32 accuracy from TF32 units ("3xTF32"): each operand value v is split as
 // v = hi + lo with hi = tf32(v) (round to nearest) and lo = tf32(v - hi), and
 // the product is accumulated as hi_a hi_b + hi_a lo_b + lo_a hi_b; the
-// dropped lo_a lo_b term is below 2^-21 of |a b|.  TF32 products are exact
-// in FP32, so the result differs from an FP32 FMA loop by accumulation
-// rounding of the same order.
+// dropped lo_a lo_b term is below 2^-21 of |a b|.  The tensor core's own
+// accumulation over long k is less accurate than IEEE FP32 (measured: 5 to
+// 10 times the error of an FP32 multiply-add loop at k = 1000 to 2048), so
+// the tensor memory holds the product of one 32-wide k chunk at a time, and
+// the chunks are summed in FP32 registers, one output row per thread.
 //
-// Per 32-wide k chunk the 128 threads load op(A) and op(B) (coalesced for
-// either storage order), split them, and store hi and lo into shared memory
-// in the 128-byte-swizzled K-major layout of the tensor core's shared-memory
-// descriptors (8-row atoms of 1024 bytes; the 16-byte chunk c of row r sits
-// at chunk position c ^ (r mod 8)).  One elected thread issues the 4 x 3
-// tcgen05.mma (M = 128, N = 128, K = 8 each) and commits them to an mbarrier
-// that every thread waits on, with an iteration limit, before the tiles are
-// rewritten.  The epilogue reads the accumulator with tcgen05.ld (warp w owns
-// tensor-memory lanes 32 w .. 32 w + 31, i.e. output rows) and applies alpha,
-// beta and the lower-triangle mask.
+// Per chunk the 128 threads load op(A) and op(B) (coalesced for either
+// storage order), split them, and store hi and lo into shared memory in the
+// 128-byte-swizzled K-major layout of the tensor core's shared-memory
+// descriptors (8-row atoms of 1024 bytes; the 16-byte chunk c of row r sits at
+// chunk position c ^ (r mod 8)).  One elected thread issues the 4 x 3
+// tcgen05.mma (M = 128, N = 128, K = 8 each) into one of two tensor-memory
+// buffers and commits them to an mbarrier that every thread waits on, with an
+// iteration limit, before the tiles are rewritten; while the chunk runs the
+// threads add the previous chunk's buffer (tcgen05.ld: warp w owns lanes
+// 32 w .. 32 w + 31, i.e. output rows) into their registers.  The epilogue
+// applies alpha, beta and the lower-triangle mask.
 #include "amdd_internal.h"
 
 namespace amdd {
@@ -76,6 +79,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 
 }  // namespace
 
+// acc[j] += the 32-bit values of columns c0 .. c0 + 15 of this warp's lanes of
+// tensor memory at taddr
+__device__ __forceinline__ void tmem_add16(uint32_t taddr, float* acc) {
+    uint32_t v[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(v[j]);
+}
+
 __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmDescT<float>* __restrict__ descs,
                                                       const TileRef* __restrict__ tiles, int ntiles,
                                                       int* __restrict__ err) {
@@ -97,7 +114,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmDescT<float>* __
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(TC_N));
+                     "r"(2 * TC_N));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -109,15 +126,28 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmDescT<float>* __
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
     // D f32, A and B tf32, both K-major, N = 128, M = 128
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                            ((uint32_t)(TC_M >> 4) << 24);
     const uint32_t mb = smem_u32(&mbar);
 
+    float acc[TC_N];
+#pragma unroll
+    for (int j = 0; j < TC_N; ++j) acc[j] = 0.0f;
     int kbeg = 0;
     if (d.kfrom_row) kbeg = (row0 / TC_KC) * TC_KC;
     uint32_t chunk = 0;
     for (int k0 = kbeg; k0 < d.k; k0 += TC_KC, ++chunk) {
+        if (chunk > 0) {
+            // the previous chunk's MMAs are done before its tiles are rewritten
+            const bool mine = mbar_wait(mb, (chunk - 1) & 1u);
+            if (!__syncthreads_and(mine ? 1 : 0)) {
+                if (tid == 0) failed = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+        }
         // op(A)[row0 + r][k0 + kk] and op(B)^T[col0 + c][k0 + kk]
         for (int e = tid; e < TC_M * TC_KC; e += 128) {
             int r, kk;
@@ -157,70 +187,56 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmDescT<float>* __
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t dbuf = tmem + (chunk & 1u) * TC_N;
         if (tid == 0) {
             for (int ks = 0; ks < TC_KC / 8; ++ks) {
                 const uint32_t koff = (uint32_t)ks * 32;
                 const uint64_t ah = sw128_desc(smem_u32(Ahi) + koff), al = sw128_desc(smem_u32(Alo) + koff);
                 const uint64_t bh = sw128_desc(smem_u32(Bhi) + koff), bl = sw128_desc(smem_u32(Blo) + koff);
-                const uint32_t acc0 = (chunk > 0 || ks > 0) ? 1u : 0u;
-                mma_tf32(tmem, ah, bh, idesc, acc0);
-                mma_tf32(tmem, ah, bl, idesc, 1u);
-                mma_tf32(tmem, al, bh, idesc, 1u);
+                mma_tf32(dbuf, ah, bh, idesc, ks > 0 ? 1u : 0u);
+                mma_tf32(dbuf, ah, bl, idesc, 1u);
+                mma_tf32(dbuf, al, bh, idesc, 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb));
         }
-        // the tiles are rewritten by the next chunk only after the MMAs that read them
-        // are done; the vote keeps the decision uniform over the CTA
-        const bool mine = mbar_wait(mb, chunk & 1u);
+        if (chunk > 0) {
+            // sum the previous chunk's product (done: waited above) while this one runs
+            const uint32_t prev = tmem + ((chunk - 1) & 1u) * TC_N + lane_off;
+#pragma unroll
+            for (int q = 0; q < TC_N / 16; ++q) tmem_add16(prev + 16 * q, acc + 16 * q);
+        }
+    }
+    if (!failed && chunk > 0) {
+        const bool mine = mbar_wait(mb, (chunk - 1) & 1u);
         if (!__syncthreads_and(mine ? 1 : 0)) {
             if (tid == 0) failed = 1;
-            break;
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t last = tmem + ((chunk - 1) & 1u) * TC_N + lane_off;
+#pragma unroll
+            for (int q = 0; q < TC_N / 16; ++q) tmem_add16(last + 16 * q, acc + 16 * q);
         }
-        asm volatile("tcgen05.fence::after_thread_sync;");
     }
     __syncthreads();
     if (failed) {
         if (tid == 0) atomicOr(err, DERR_TIMEOUT);
-    } else if (chunk > 0) {
-        // epilogue: row = 32 warp + lane, 32 columns per tcgen05.ld
+    } else {
+        // epilogue (k = 0 leaves acc = 0: C = beta C)
         const int r = row0 + 32 * warp + lane;
-        for (int cb = 0; cb < TC_N; cb += 32) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (r < d.m) {
+        if (r < d.m) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int c = col0 + cb + j;
-                    if (c >= d.n || (d.lower && c > r)) continue;
-                    float* cp = d.C + (size_t)r * d.ldc + c;
-                    const float val = d.alpha * __uint_as_float(v[j]);
-                    *cp = (d.beta != 0.0f) ? fmaf(d.beta, *cp, val) : val;
-                }
+            for (int j = 0; j < TC_N; ++j) {
+                const int c = col0 + j;
+                if (c >= d.n || (d.lower && c > r)) continue;
+                float* cp = d.C + (size_t)r * d.ldc + c;
+                const float val = d.alpha * acc[j];
+                *cp = (d.beta != 0.0f) ? fmaf(d.beta, *cp, val) : val;
             }
         }
-    } else if (d.beta != 1.0f) {
-        // k = 0: C = beta C on the tile (the product is empty)
-        const int r = row0 + 32 * warp + lane;
-        if (r < d.m)
-            for (int c = col0; c < col0 + TC_N && c < d.n; ++c) {
-                if (d.lower && c > r) continue;
-                float* cp = d.C + (size_t)r * d.ldc + c;
-                *cp = d.beta != 0.0f ? d.beta * *cp : 0.0f;
-            }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_N));
 }
 
 size_t gemm_tc_smem() { return 4 * (size_t)TC_TILE_BYTES + 1024; }

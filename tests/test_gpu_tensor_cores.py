@@ -38,7 +38,9 @@ def _gemm(m, n, k, ta, tb, alpha, beta, tc, seed):
     opA = (Ah.T if ta else Ah).double()
     opB = (Bh.T if tb else Bh).double()
     ref = alpha * (opA @ opB) + beta * Ch.double()
-    bound = 8 * max(k, 1) * U32 * float(Ah.abs().max()) * float(Bh.abs().max()) * abs(alpha) + 4 * U32 * abs(beta) * float(Ch.abs().max())
+    amax = float(Ah.abs().max()) if Ah.numel() else 0.0
+    bmax = float(Bh.abs().max()) if Bh.numel() else 0.0
+    bound = 8 * max(k, 1) * U32 * amax * bmax * abs(alpha) + 4 * U32 * abs(beta) * float(Ch.abs().max())
     return (Cd.cpu().double() - ref).abs().max().item(), bound
 
 
