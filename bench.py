@@ -617,6 +617,7 @@ def run_amdd(args):
         o.profile = profile
         o.precision = precision
         o.profile_classes = profile_classes
+        o.tensor_cores = args.tensor_cores
 
         def one_step(profile_acc=None, keep=None):
             x.zero_()
@@ -846,12 +847,21 @@ def main():
                     help="skip the deflated GMRES and three-level variant timings")
     ap.add_argument("--scale-m", type=int, default=None,
                     help="grid side of the bandwidth problem (default 1024; 16 x 16 boxes)")
+    ap.add_argument("--m", type=int, default=None, help="grid side of the 3D workload (default 24)")
+    ap.add_argument("--N", type=int, default=None, help="BFS subdomains of the 3D workload (default 16)")
+    ap.add_argument("--lo", type=int, default=None, help="smallest BFS subdomain (cells, default 256)")
+    ap.add_argument("--hi", type=int, default=None, help="largest BFS subdomain (cells, default 2048)")
+    ap.add_argument("--tensor-cores", type=int, default=1, choices=[0, 1],
+                    help="FP32 batched GEMMs of the mixed form on the tcgen05 tensor cores")
     ap.add_argument("--plain-steps", type=int, default=3,
                     help="timed steps of the plain FP64 arm (at most --steps)")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
                     help="0: plain FP64 form; 1: mixed form (FP32 local work, FP64 coarse and PCG); "
                          "2: mixed form with an FP64 splitting")
     args = ap.parse_args()
+    for key in ("m", "N", "lo", "hi"):
+        if getattr(args, key) is not None:
+            WORKLOAD_3D[key] = getattr(args, key)
     if args.impl == "reference":
         return run_reference(args)
     return run_amdd(args)

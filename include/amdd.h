@@ -192,10 +192,10 @@ typedef struct {
     int64_t inner_solves;      /* coarse solves done by inner GMRES (since setup) */
     int64_t inner_iterations;  /* their total iteration count                  */
     int32_t n_tied;            /* eigenvalues of eq. (Zi) with |lambda tau - 1| <= tie_band */
-    int32_t n_below_one;       /* computed eigenvalues of eq. (Zi) below 1 - 1e-6: every
-                                  non-zero one is >= 1 with Boolean D_i, so these are rounding
-                                  (of an FP32 splitting); for tau >= 1.01 they are selected
-                                  like the others                                          */
+    int32_t n_below_one;       /* eigenvalues of eq. (Zi) below 1 - 1e-6: without the shift
+                                  sigma_1 eps every non-zero one is >= 1 with Boolean D_i; the
+                                  shift lowers the bound to 1 / (1 + sigma_1 eps / lambda_min(A_II)),
+                                  far below 1 for the FP32 splitting on high-contrast matrices */
     int64_t device_bytes_peak; /* largest device memory the handle has held (bytes) */
     int64_t graph_solves;      /* PCG solves whose iterations ran as one CUDA graph   */
     int64_t tuned_buckets;     /* GEMM size buckets measured by the autotuner in this process */
@@ -224,7 +224,7 @@ amdd_status amdd_nd_order(int64_t n, const int64_t* rowptr, const int32_t* colin
                           int32_t* parent, int64_t* colcount, int64_t* nnzL);
 
 /* Fill `o` with the defaults (eps = 2^-52, max_sweeps = 60, tie_band = 1e-10,
- * use_graphs = 1, autotune = 1, everything else 0). */
+ * use_graphs = 1, autotune = 1, tensor_cores = 1, everything else 0). */
 amdd_status amdd_opts_default(amdd_opts* o);
 
 /* C = alpha op(A) op(B) + beta C in FP32 (row-major; op(A) = A if ta = 0,
@@ -403,6 +403,9 @@ amdd_status amdd_get_eig_iterations(const amdd_handle* h, int32_t* iters, int32_
  * and is complete on return.  n = number of samples (rows).
  *   amdd_mlp_sizes: *nparam = AMDD_MLP_NPARAM, *nwork = floats of the `work`
  *     buffer amdd_mlp_forward / amdd_mlp_train_step need for n samples.
+ *   amdd_mlp_feature_stats: mean[32] and sd[32] (population standard
+ *     deviation, 1 where below 1e-6) of the columns of feat (n x 32), the
+ *     standardisation the network is trained with.
  *   amdd_mlp_normalize: x = (feat - mean) / sd (n x 32).
  *   amdd_mlp_forward: q (n x 256) = the symmetrised outputs, as 16 x 16
  *     matrices, of the MLP 32 -> 256 -> 256 -> 256 (ReLU) with weights wb.
@@ -414,6 +417,7 @@ amdd_status amdd_get_eig_iterations(const amdd_handle* h, int32_t* iters, int32_
  *     even).  lr = 0 computes the gradient only.
  *   amdd_mlp_round_bf16: wb = w rounded to bfloat16 (n values). */
 amdd_status amdd_mlp_sizes(int32_t n, int64_t* nparam, int64_t* nwork);
+amdd_status amdd_mlp_feature_stats(const float* feat, int32_t n, float* mean, float* sd, void* stream);
 amdd_status amdd_mlp_normalize(const float* feat, const float* mean, const float* sd, int32_t n, float* x,
                                void* stream);
 amdd_status amdd_mlp_forward(const float* wb, const float* x, int32_t n, float* q, float* work, void* stream);

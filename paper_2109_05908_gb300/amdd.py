@@ -93,6 +93,7 @@ SIGNATURES = {
                                        C.POINTER(C.c_int32)]),
     "amdd_get_eig_iterations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "amdd_mlp_sizes": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "amdd_mlp_feature_stats": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "amdd_mlp_normalize": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "amdd_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "amdd_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
@@ -327,6 +328,10 @@ def mlp_sizes(n: int):
     a, b = C.c_int64(), C.c_int64()
     _check(lib().amdd_mlp_sizes(n, C.byref(a), C.byref(b)), "amdd_mlp_sizes")
     return a.value, b.value
+
+
+def mlp_feature_stats(feat_ptr: int, n: int, mean_ptr: int, sd_ptr: int, stream: int = 0) -> None:
+    _check(lib().amdd_mlp_feature_stats(feat_ptr, n, mean_ptr, sd_ptr, stream), "amdd_mlp_feature_stats")
 
 
 def mlp_normalize(feat_ptr: int, mean_ptr: int, sd_ptr: int, n: int, x_ptr: int, stream: int = 0) -> None:

@@ -257,7 +257,7 @@ struct amdd_handle {
     size_t bytes_now = 0, bytes_peak = 0, mem_budget = 0;
     double tie_band = 1e-10;
     int n_tied = 0;  // eigenvalues with |lambda tau - 1| <= tie_band
-    int n_below_one = 0;  // computed eigenvalues below the bound 1 (rounding)
+    int n_below_one = 0;  // computed eigenvalues below 1 (the shift of the splitting)
     int64_t pair_stats[5] = {0, 0, 0, 0, 0};  // block-pair Jacobi: tasks, rotated, cycles of 3 phases
     int use_graphs = 1;
     int autotune = 1;  // GEMM tile autotuner (process-wide table)
@@ -2883,7 +2883,6 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     h->coff.assign(N + 1, 0);
     h->off_zt.assign(N + 1, 0);
     std::vector<int> partial;  // subdomains whose selection is neither empty nor everything
-    const bool full_by_bound = h->tau >= 1.01;
     for (int i = 0; i < N; ++i) {
         const int nIi = h->nI[i];
         int pi = 0;
@@ -2896,11 +2895,9 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
                 lam = (m > 0.0) ? 1.0 / m : std::numeric_limits<double>::infinity();
             }
             h->lam_h[h->off_I[i] + j] = lam;
-            // with Boolean D_i every non-zero eigenvalue of eq. (Zi) is at least 1
-            // (Lemma 3.2 and Courant-Fischer), so for tau >= 1.01 each one is
-            // selected whatever rounding did to its computed value (an FP32
-            // splitting can leave one far below the bound); such values are counted
-            if (lam > 1.0 / h->tau || full_by_bound) ++pi;
+            if (lam > 1.0 / h->tau) ++pi;
+            // below 1: possible only through the shift sigma_1 eps of the splitting
+            // (diagnostic count)
             if (lam < 1.0 - 1e-6) ++h->n_below_one;
             if (std::fabs(lam * h->tau - 1.0) <= h->tie_band) ++h->n_tied;
         }
@@ -3901,6 +3898,7 @@ amdd_status amdd_opts_default(amdd_opts* o) {
     o->tie_band = 1e-10;
     o->use_graphs = 1;
     o->autotune = 1;
+    o->tensor_cores = 1;
     return AMDD_OK;
 }
 
@@ -4248,6 +4246,14 @@ amdd_status amdd_mlp_sizes(int32_t n, int64_t* nparam, int64_t* nwork) {
     if (n < 1 || !nparam || !nwork) return AMDD_ERR_INVALID;
     *nparam = MLP_NPARAM;
     *nwork = (int64_t)9 * n * PROP_NH + n + 16;
+    return AMDD_OK;
+}
+
+amdd_status amdd_mlp_feature_stats(const float* feat, int32_t n, float* mean, float* sd, void* stream) {
+    if (n < 1 || !feat || !mean || !sd) return AMDD_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    launch_feature_stats(feat, n, mean, sd, s);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return AMDD_ERR_CUDA;
     return AMDD_OK;
 }
 

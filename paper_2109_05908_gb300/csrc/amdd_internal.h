@@ -350,6 +350,8 @@ struct KrylovDesc {
 };
 void launch_krylov(const KrylovDesc* d, int nmat, cudaStream_t s);
 
+// mean[f], sd[f] (population; < 1e-6 -> 1) of the columns of an n x PROP_NF matrix
+void launch_feature_stats(const float* feat, int n, float* mean, float* sd, cudaStream_t s);
 void launch_normalize_features(const float* feat, const float* mean, const float* sd, float* X, int n,
                                cudaStream_t s);
 void launch_bias_act(float* Z, const float* bias, float* H, int rows, int cols, cudaStream_t s);

@@ -577,13 +577,25 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        // software pipeline: the next chunk's values are loaded into registers
+        // while the current chunk is multiplied out of shared memory
+        constexpr int PER = JP_R * JP_KC / 256;  // values per thread and chunk
+        const int kk_t = tid % JP_KC;
+        int rows_t[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) rows_t[q] = grow((tid + 256 * q) / JP_KC);
+        T pre[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            pre[q] = (rows_t[q] >= 0 && kk_t < d.ncols_dot) ? __ldcg(d.A + (size_t)rows_t[q] * d.ld + kk_t) : T(0);
         for (int c0 = 0; c0 < d.ncols_dot; c0 += JP_KC) {
-            for (int e = tid; e < JP_R * JP_KC; e += 256) {
-                const int lr = e / JP_KC, kk = e % JP_KC;
-                const int r = grow(lr), c = c0 + kk;
-                Yc[kk * JP_LDT + lr] = (r >= 0 && c < d.ncols_dot) ? __ldcg(d.A + (size_t)r * d.ld + c) : T(0);
-            }
+#pragma unroll
+            for (int q = 0; q < PER; ++q) Yc[kk_t * JP_LDT + (tid + 256 * q) / JP_KC] = pre[q];
             __syncthreads();
+            const int cn = c0 + JP_KC + kk_t;
+#pragma unroll
+            for (int q = 0; q < PER; ++q)
+                pre[q] = (rows_t[q] >= 0 && cn < d.ncols_dot) ? __ldcg(d.A + (size_t)rows_t[q] * d.ld + cn) : T(0);
 #pragma unroll 4
             for (int kk = 0; kk < JP_KC; ++kk) {
                 T a[4], b[4];
@@ -710,13 +722,25 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
     {
         const int ty = tid >> 3, tx = tid & 7;  // rows 2 ty, 2 ty + 1; columns 4 tx .. 4 tx + 3
         const int r0 = grow(2 * ty), r1 = grow(2 * ty + 1);
+        constexpr int PER = JP_R * JP_KC / 256;
+        const int kk_t = tid % JP_KC;
+        int rows_t[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) rows_t[q] = grow((tid + 256 * q) / JP_KC);
+        T pre[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            pre[q] = (rows_t[q] >= 0 && kk_t < d.ncols_rot) ? __ldcg(d.A + (size_t)rows_t[q] * d.ld + kk_t) : T(0);
         for (int c0 = 0; c0 < d.ncols_rot; c0 += JP_KC) {
-            for (int e = tid; e < JP_R * JP_KC; e += 256) {
-                const int lr = e / JP_KC, kk = e % JP_KC;
-                const int r = grow(lr), c = c0 + kk;
-                Yc[lr * JP_LDA + kk] = (r >= 0 && c < d.ncols_rot) ? __ldcg(d.A + (size_t)r * d.ld + c) : T(0);
-            }
+#pragma unroll
+            for (int q = 0; q < PER; ++q) Yc[((tid + 256 * q) / JP_KC) * JP_LDA + kk_t] = pre[q];
             __syncthreads();
+            // the next chunk is read before this one is written back: different
+            // columns, so the in-place update stays safe
+            const int cn = c0 + JP_KC + kk_t;
+#pragma unroll
+            for (int q = 0; q < PER; ++q)
+                pre[q] = (rows_t[q] >= 0 && cn < d.ncols_rot) ? __ldcg(d.A + (size_t)rows_t[q] * d.ld + cn) : T(0);
             T o0[4] = {T(0), T(0), T(0), T(0)}, o1[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll 4
             for (int k = 0; k < JP_R; ++k) {
@@ -1696,100 +1720,12 @@ __global__ void __launch_bounds__(256) gemv_rows4_kernel(const GemvDescT<T>* __r
     }
 }
 
-// The same products with 16-byte loads of the factor rows.  The four rows of
-// a warp start at arbitrary alignment: each gets a scalar head up to its first
-// 16-byte boundary, a vector body and a scalar tail; the bodies of the four
-// rows are streamed together (one 16-byte load per row and lane in flight per
-// step), x by scalar loads (it stays in L1).  Per row: lane-strided partial
-// sums and the fixed shuffle tree, so the result is reproducible run to run.
-template <typename T>
-struct Vec16;
-template <>
-struct Vec16<float> {
-    using type = float4;
-    static constexpr int V = 4;
-    __device__ static float dot(const float4& a, const float* x, float s) {
-        s = fmaf(a.x, __ldg(x), s);
-        s = fmaf(a.y, __ldg(x + 1), s);
-        s = fmaf(a.z, __ldg(x + 2), s);
-        return fmaf(a.w, __ldg(x + 3), s);
-    }
-};
-template <>
-struct Vec16<double> {
-    using type = double2;
-    static constexpr int V = 2;
-    __device__ static double dot(const double2& a, const double* x, double s) {
-        s = fma(a.x, __ldg(x), s);
-        return fma(a.y, __ldg(x + 1), s);
-    }
-};
-
-template <typename T>
-__global__ void __launch_bounds__(256) gemv_rows4v_kernel(const GemvDescT<T>* __restrict__ descs,
-                                                          const int* __restrict__ grp_desc,
-                                                          const int* __restrict__ grp_row, int64_t ngroups) {
-    using VT = typename Vec16<T>::type;
-    constexpr int V = Vec16<T>::V;
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= ngroups) return;
-    const GemvDescT<T> d = descs[grp_desc[w]];
-    const int r0 = grp_row[w];
-    const int nr = min(GEMV_RW, d.rows - r0);
-    int vs[GEMV_RW], nv[GEMV_RW];
-    T s[GEMV_RW];
-    int nvmax = 0;
-#pragma unroll
-    for (int k = 0; k < GEMV_RW; ++k) {
-        s[k] = T(0);
-        vs[k] = 0;
-        nv[k] = 0;
-        if (k < nr) {
-            const int r = r0 + k;
-            const int lo = (d.mode == 2) ? r : 0;
-            const int hi = (d.mode == 1) ? min(r + 1, d.ncols) : d.ncols;
-            const T* Mr = d.M + (size_t)r * d.ld;
-            const int mis = (int)((reinterpret_cast<uintptr_t>(Mr + lo) / sizeof(T)) % V);
-            const int v0 = min(hi, lo + (V - mis) % V);
-            if (lane < v0 - lo) s[k] = fma(Mr[lo + lane], d.x[lo + lane], s[k]);  // head
-            const int n = (hi - v0) / V;
-            const int ve = v0 + n * V;
-            if (lane < hi - ve) s[k] = fma(Mr[ve + lane], d.x[ve + lane], s[k]);  // tail
-            vs[k] = v0;
-            nv[k] = n;
-            nvmax = max(nvmax, n);
-        }
-    }
-    for (int j = lane; j < nvmax; j += 32) {
-        VT a[GEMV_RW];
-#pragma unroll
-        for (int k = 0; k < GEMV_RW; ++k)
-            if (j < nv[k]) a[k] = __ldg(reinterpret_cast<const VT*>(d.M + (size_t)(r0 + k) * d.ld + vs[k]) + j);
-#pragma unroll
-        for (int k = 0; k < GEMV_RW; ++k)
-            if (j < nv[k]) s[k] = Vec16<T>::dot(a[k], d.x + vs[k] + j * V, s[k]);
-    }
-    T mine = T(0);
-#pragma unroll
-    for (int k = 0; k < GEMV_RW; ++k) {
-        T v = s[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == k) mine = v;
-    }
-    if (lane < nr) {
-        const int r = r0 + lane;
-        d.y[r] = d.b ? fma(d.alpha, mine, d.b[r]) : d.alpha * mine;
-    }
-}
-
 template <typename T>
 void launch_gemv_rows4(const GemvDescT<T>* d, const int* grp_desc, const int* grp_row, int64_t ngroups,
                        cudaStream_t s) {
     if (ngroups <= 0) return;
     const int64_t blocks = (ngroups * 32 + 255) / 256;
-    gemv_rows4v_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, grp_desc, grp_row, ngroups);
+    gemv_rows4_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, grp_desc, grp_row, ngroups);
 }
 template void launch_gemv_rows4<float>(const GemvDescT<float>*, const int*, const int*, int64_t, cudaStream_t);
 template void launch_gemv_rows4<double>(const GemvDescT<double>*, const int*, const int*, int64_t, cudaStream_t);

@@ -233,6 +233,48 @@ __global__ void normalize_features_kernel(const float* __restrict__ feat, const 
     }
 }
 
+// Standardisation of the features: per column f of the n x PROP_NF matrix,
+// mean and population standard deviation (two passes, FP64 sums in a fixed
+// order: one thread per column strides the rows, then a fixed tree over the
+// 8 threads of the column); sd below 1e-6 becomes 1 so that a constant
+// feature passes unchanged.
+__global__ void __launch_bounds__(256) feature_stats_kernel(const float* __restrict__ feat, int n,
+                                                            float* __restrict__ mean, float* __restrict__ sd) {
+    __shared__ double red[8][PROP_NF];
+    __shared__ double mu_s[PROP_NF];
+    const int f = threadIdx.x % PROP_NF, part = threadIdx.x / PROP_NF;  // 8 parts x 32 columns
+    double s = 0.0;
+    for (int r = part; r < n; r += 8) s += feat[(size_t)r * PROP_NF + f];
+    red[part][f] = s;
+    __syncthreads();
+    if (part == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[q][f];
+        mu_s[f] = t / n;
+    }
+    __syncthreads();
+    const double mu = mu_s[f];
+    double v = 0.0;
+    for (int r = part; r < n; r += 8) {
+        const double d = feat[(size_t)r * PROP_NF + f] - mu;
+        v += d * d;
+    }
+    __syncthreads();
+    red[part][f] = v;
+    __syncthreads();
+    if (part == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[q][f];
+        const double sdv = sqrt(t / n);
+        mean[f] = (float)mu;
+        sd[f] = sdv > 1e-6 ? (float)sdv : 1.0f;
+    }
+}
+
+void launch_feature_stats(const float* feat, int n, float* mean, float* sd, cudaStream_t s) {
+    feature_stats_kernel<<<1, 8 * PROP_NF, 0, s>>>(feat, n, mean, sd);
+}
+
 void launch_normalize_features(const float* feat, const float* mean, const float* sd, float* X, int n,
                                cudaStream_t s) {
     if (n > 0) normalize_features_kernel<<<(n * PROP_NF + 255) / 256, 256, 0, s>>>(feat, mean, sd, X, n);

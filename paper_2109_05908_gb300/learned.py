@@ -74,11 +74,11 @@ class ProposalModel:
         self._prop = None
 
     def set_normalisation(self, feats: np.ndarray):
-        mu = feats.mean(axis=0)
-        sd = feats.std(axis=0)
-        sd = np.where(sd > 1e-6, sd, 1.0)
-        self.mean = torch.from_numpy(mu.astype(np.float32)).to(self.device)
-        self.sd = torch.from_numpy(sd.astype(np.float32)).to(self.device)
+        """Feature means and standard deviations, computed by the library's kernel."""
+        f = torch.from_numpy(np.ascontiguousarray(feats, np.float32)).to(self.device)
+        self.mean = torch.empty(NF, dtype=torch.float32, device=self.device)
+        self.sd = torch.empty(NF, dtype=torch.float32, device=self.device)
+        A.mlp_feature_stats(f.data_ptr(), f.shape[0], self.mean.data_ptr(), self.sd.data_ptr(), stream_ptr())
 
     def _inputs(self, feats: np.ndarray) -> torch.Tensor:
         f = torch.from_numpy(np.ascontiguousarray(feats, np.float32)).to(self.device)

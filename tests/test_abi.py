@@ -50,6 +50,7 @@ def test_status_strings_and_defaults(A):
     o = A.opts_default()
     assert o.eps == 2.0 ** -52 and o.max_sweeps == 60
     assert o.tie_band == 1e-10 and o.use_graphs == 1 and o.autotune == 1 and o.mem_budget == 0
+    assert o.tensor_cores == 1
 
 
 @pytest.mark.parametrize("ov", [1, 2, 3])

@@ -219,3 +219,22 @@ def test_learned_start_trains_and_is_accepted(capsys):
         print(f"\n[learned start] training loss {hist[0]:.3f} -> {hist[-1]:.3f}; LOBPCG iterations on unseen "
               f"subdomains: cold {cold_total}, learned {warm_total}")
     assert warm_total <= cold_total + 2
+
+
+def test_feature_standardisation_kernel():
+    """Column means and population standard deviations of the features come
+    from the library's kernel (FP64 sums): equal to numpy's to 1e-6, and a
+    constant column gets sd = 1."""
+    rng = np.random.default_rng(5)
+    f = (rng.standard_normal((257, A.PROP_NF)) * rng.uniform(0.1, 50, A.PROP_NF) + rng.uniform(-3, 3, A.PROP_NF))
+    f[:, 7] = 2.5
+    f = f.astype(np.float32)
+    fd = torch.from_numpy(f).cuda()
+    mean = torch.empty(A.PROP_NF, dtype=torch.float32, device="cuda")
+    sd = torch.empty_like(mean)
+    A.mlp_feature_stats(fd.data_ptr(), f.shape[0], mean.data_ptr(), sd.data_ptr(), stream_ptr())
+    f64 = f.astype(np.float64)
+    mu, s = f64.mean(axis=0), f64.std(axis=0)
+    s[7] = 1.0
+    assert np.allclose(mean.cpu().numpy(), mu, rtol=1e-6, atol=1e-6)
+    assert np.allclose(sd.cpu().numpy(), s, rtol=1e-6, atol=1e-7)
