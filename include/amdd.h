@@ -199,10 +199,10 @@ typedef struct {
     int64_t device_bytes_peak; /* largest device memory the handle has held (bytes) */
     int64_t graph_solves;      /* PCG solves whose iterations ran as one CUDA graph   */
     int64_t tuned_buckets;     /* GEMM size buckets measured by the autotuner in this process */
-    int64_t pair_stats[5];     /* block-pair one-sided Jacobi (matrices whose rows exceed shared
-                                  memory): pair tasks run, pairs rotated, and SM clock cycles
+    int64_t pair_stats[6];     /* block-pair one-sided Jacobi (matrices whose rows exceed shared
+                                  memory): pair tasks run, pairs rotated, SM clock cycles
                                   summed over CTAs of its three phases (Gram matrices, small
-                                  eigensolves, rotation of the rows)                        */
+                                  eigensolves, rotation of the rows), inner sweeps            */
 } amdd_info;
 
 /* Symbolic phase of a sparse local Cholesky factorisation, on the host (no

@@ -258,7 +258,7 @@ struct amdd_handle {
     double tie_band = 1e-10;
     int n_tied = 0;  // eigenvalues with |lambda tau - 1| <= tie_band
     int n_below_one = 0;  // computed eigenvalues below 1 (the shift of the splitting)
-    int64_t pair_stats[5] = {0, 0, 0, 0, 0};  // block-pair Jacobi: tasks, rotated, cycles of 3 phases
+    int64_t pair_stats[6] = {0, 0, 0, 0, 0, 0};  // block-pair Jacobi: tasks, rotated, cycles of 3 phases, inner sweeps
     int use_graphs = 1;
     int autotune = 1;  // GEMM tile autotuner (process-wide table)
     int tensor_cores = 0;  // FP32 GEMMs on tcgen05 (3xTF32)
@@ -764,8 +764,8 @@ void jacobi_pairs(Ctx& C, const std::vector<JacobiDescT<T>>& jd, const JacobiDes
     }
     int* d_rot = C.tnew<int>(nm);
     std::vector<int> rot_h(nm);
-    unsigned long long* d_st = C.tnew<unsigned long long>(5);
-    ck(cudaMemsetAsync(d_st, 0, 5 * sizeof(unsigned long long), h->s));
+    unsigned long long* d_st = C.tnew<unsigned long long>(6);
+    ck(cudaMemsetAsync(d_st, 0, 6 * sizeof(unsigned long long), h->s));
     for (int sweep = 0; sweep < max_sweeps && !active.empty(); ++sweep) {
         std::vector<int4> tasks;
         int maxb = 2;
@@ -791,10 +791,10 @@ void jacobi_pairs(Ctx& C, const std::vector<JacobiDescT<T>>& jd, const JacobiDes
     }
     C.keep.push_back(sw);
     ck(cudaMemcpyAsync(sweeps, sw->data(), nm * sizeof(int), cudaMemcpyHostToDevice, h->s));
-    unsigned long long st[5];
+    unsigned long long st[6];
     ck(cudaMemcpyAsync(st, d_st, sizeof(st), cudaMemcpyDeviceToHost, h->s));
     ck(cudaStreamSynchronize(h->s));
-    for (int k = 0; k < 5; ++k) h->pair_stats[k] += (int64_t)st[k];
+    for (int k = 0; k < 6; ++k) h->pair_stats[k] += (int64_t)st[k];
     if (!active.empty() && report_noconv) launch_or_flag(h->d_err, DERR_EIG_NOCONV, h->s);
 }
 
@@ -4628,7 +4628,7 @@ amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
     info->inner_iterations = h->in_its;
     info->n_tied = h->n_tied;
     info->n_below_one = h->n_below_one;
-    for (int k = 0; k < 5; ++k) info->pair_stats[k] = h->pair_stats[k];
+    for (int k = 0; k < 6; ++k) info->pair_stats[k] = h->pair_stats[k];
     info->device_bytes_peak = (int64_t)h->bytes_peak;
     info->graph_solves = h->graph_solves;
     {

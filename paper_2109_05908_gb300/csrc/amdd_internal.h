@@ -143,9 +143,9 @@ void launch_jacobi_t(const JacobiDescT<T>* d, int nmat, int max_sweeps, T tol, i
 // round of the block round-robin schedule (blocks of 32 rows; tasks[t] =
 // {matrix, pair index in the round, blocks of that matrix (even, >= 2), 0});
 // rotated[matrix] is set when a pair of it was rotated, rots[matrix] counts
-// plane rotations, stats[5] accumulates pair tasks, rotated pairs and the SM
+// plane rotations, stats[6] accumulates pair tasks, rotated pairs, the SM
 // cycles of the three phases (Gram matrix, small eigensolve, rotation of the
-// rows).  The host runs the rounds of a sweep and the sweeps.
+// rows) and the inner sweeps.  The host runs the rounds of a sweep and the sweeps.
 constexpr int JP_ROWS = 32;
 template <typename T>
 size_t jacobi_pair_smem();

@@ -507,7 +507,7 @@ constexpr int JP_KC = 32;             // columns per streamed chunk
 constexpr int JP_LDG = JP_R + 1;      // G and Qt, row-major
 constexpr int JP_LDT = JP_R + 4;      // Gram chunk, [column][row] (16-byte aligned rows)
 constexpr int JP_LDA = JP_KC + 4;     // apply chunk, [row][column]
-constexpr int JP_INNER = 40;          // inner sweep limit
+constexpr int JP_INNER = 20;          // inner sweep limit
 
 template <typename T>
 size_t jacobi_pair_smem() {
@@ -566,7 +566,8 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
     };
     const T absf = d.absfloor ? *d.absfloor : T(0);
     // stats: [0] pair tasks, [1] pairs rotated, [2..4] SM clock cycles of the
-    // Gram matrix, the small eigensolve and the rotation of the rows (thread 0)
+    // Gram matrix, the small eigensolve and the rotation of the rows (thread 0),
+    // [5] inner sweeps
     const long long t0 = clock64();
 
     // ---- 1. Gram matrix over ncols_dot columns
@@ -622,7 +623,8 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
     // orthogonalised to a tighter inner test (tin, still well above the
     // rounding of G), so that one visit leaves it converged and the outer
     // sweeps do not revisit rounding-level couplings.
-    const T tin = fmax(tol * T(1.0 / 64.0), T(16) * (sizeof(T) == 4 ? T(1.1920928955078125e-7) : T(2.220446049250313e-16)));
+    const T ueps = sizeof(T) == 4 ? T(1.1920928955078125e-7) : T(2.220446049250313e-16);
+    const T tin = fmax(tol * T(1.0 / 64.0), T(16) * ueps);
     const long long t1 = clock64();
     if (tid == 0) {
         atomicAdd(stats + 0, 1ull);
@@ -653,7 +655,11 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
                     q = (rr - tid + JP_R - 1) % (JP_R - 1);
                 }
                 const T a = G[p * JP_LDG + p], b = G[q * JP_LDG + q], g = G[p * JP_LDG + q];
-                const bool doit = g != T(0) && g * g > tin * tin * a * b && fabs(g) > absf;
+                // after the first inner sweep, G's off-diagonal entries carry the rounding
+                // of earlier rotations, of the order of u max(a, b): couplings below that
+                // floor are left to the next outer sweep's fresh Gram matrix
+                const bool doit = g != T(0) && g * g > tin * tin * a * b && fabs(g) > absf &&
+                                  (sw == 0 || fabs(g) > T(8) * ueps * fmax(a, b));
                 r_p[tid] = p;
                 r_q[tid] = q;
                 r_do[tid] = doit ? 1 : 0;
@@ -708,6 +714,7 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
             }
             __syncthreads();
         }
+        if (tid == 0) atomicAdd(stats + 5, 1ull);
         if (!__syncthreads_or(rot_mine)) break;
     }
     if (nrot) atomicAdd(rots + mat, (unsigned long long)nrot);

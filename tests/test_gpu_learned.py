@@ -238,3 +238,59 @@ def test_feature_standardisation_kernel():
     s[7] = 1.0
     assert np.allclose(mean.cpu().numpy(), mu, rtol=1e-6, atol=1e-6)
     assert np.allclose(sd.cpu().numpy(), s, rtol=1e-6, atol=1e-7)
+
+
+def _c2_shaped(seed, m=24, N=16, tau=0.5):
+    """The 3D channelled diffusion of the paper-scale configuration (sigma 2,
+    correlation length 8, 16 channels of 1e6), 16 BFS subdomains of
+    256..2048 cells, overlap 2, tau = 0.5 (partial selections)."""
+    w = synth.workload_diffusion3d(m=m, N=N, lo=256, hi=2048, tau=tau, seed=seed)
+    return w["A"], w["part"], w["N"], w["overlap"], w["tau"]
+
+
+def test_learned_start_at_scale(capsys):
+    """The learned warm start on subdomains of 740..980 owned unknowns (1.3k..2.4k
+    with the overlap), mixed form: trained on 8 seeded problems (128
+    subdomains), evaluated on 2 unseen seeds.  Every learned result must be
+    accepted or fall back, and keep the preconditioner (PCG iterations +-1
+    against the dense eigenvector path); the LOBPCG iteration counts and setup
+    times with and without the network are reported, and the learned start
+    may not cost more than 10% over the cold start in iterations."""
+    import time
+    train = [_c2_shaped(1000 + s) for s in range(8)]
+    feats, tgts = Lg.collect(train, precision=1)
+    assert len(feats) >= 32
+    model = Lg.ProposalModel(seed=0)
+    hist = model.fit(feats, tgts, steps=400, lr=1e-3)
+    assert hist[-1] < hist[0]
+    tot = {"cold": 0, "learned": 0}
+    ms = {"cold": 0.0, "learned": 0.0, "dense": 0.0}
+    for seed in (5000, 5001):
+        prob = _c2_shaped(seed)
+        M = prob[0]
+        t0 = time.perf_counter()
+        hd, kd = _setup(prob, precision=1, eig_solver=0)
+        ms["dense"] += (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        hc, kc = _setup(prob, precision=1, eig_solver=1)
+        ms["cold"] += (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        hw, kw = _setup(prob, opts=model.opts(precision=1), precision=1)
+        ms["learned"] += (time.perf_counter() - t0) * 1e3
+        try:
+            idn, ic, iw = A.get_info(hd), A.get_info(hc), A.get_info(hw)
+            assert ic.n_partial > 0 and iw.n_partial == ic.n_partial
+            assert iw.lobpcg_subdomains + iw.lobpcg_fallbacks == iw.n_partial
+            tot["cold"] += ic.lobpcg_iters_total
+            tot["learned"] += iw.lobpcg_iters_total
+            sd, sw = _pcg_its(hd, M), _pcg_its(hw, M)
+            assert sw.converged == 1 and abs(sw.iterations - sd.iterations) <= 1
+            assert idn.n_C == iw.n_C
+        finally:
+            for h in (hd, hc, hw):
+                A.destroy(h)
+    with capsys.disabled():
+        print(f"\n[learned start at scale] {len(feats)} training subdomains, loss {hist[0]:.3f} -> {hist[-1]:.3f}; "
+              f"LOBPCG iterations on unseen seeds: cold {tot['cold']}, learned {tot['learned']}; setup ms: dense "
+              f"eigenvectors {ms['dense']:.0f}, cold LOBPCG {ms['cold']:.0f}, learned {ms['learned']:.0f}")
+    assert tot["learned"] <= 1.1 * tot["cold"] + 2
