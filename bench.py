@@ -46,6 +46,11 @@ RTOL = 1e-8
 FP64_PEAK_GFLOPS = 1250.0
 FP32_PEAK_GFLOPS = 80550.0
 SVD_CLASSES = {"jacobi_f32": True, "jacobi_svd": False}
+# DRAM bytes (read + write) per step of a kernel class on the default workload, from one ncu capture of
+# `bench.py --steps 1 --warmup 1 --plain-steps 1 --no-scale --no-variants` (dram__bytes_read.sum +
+# dram__bytes_write.sum summed over the class's launches of one step); reported as roofline.traffic only for the
+# workload it was taken on
+TRAFFIC_PER_STEP = {("jacobi_f32", "diffusion3d_24^3_sigma2_ch16_bfs16_256-2048_ov2_tau100"): 3.5211e11}
 TRIDIAG_CLASSES = {"tridiag_f32": True, "tridiag": False}
 F32_CLASSES = {"jacobi_f32", "gemm_tiles_f32", "chol_diag_f32", "chol_panel_f32", "trtri_diag_f32", "tridiag_f32",
                "bisect_f32"}
@@ -330,6 +335,35 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20, m=None):
             kernels[k] = {"launches": p["launches"], "ms_per_launch": p["ms"] / p["launches"],
                           "GB/s": gbs, "frac": gbs / hbm_gbs}
     A.destroy(h)
+    # the same one-level apply with sparse local Cholesky factors in a
+    # nested-dissection order (local_solver = 2 keeps them on these boxes)
+    sparse = None
+    o2 = A.opts_default()
+    o2.precision = 1
+    o2.profile = 1
+    o2.local_solver = 2
+    h2 = A.setup(dA.csr, part.data_ptr(), N, c["overlap"], c["tau"], o2, sp)
+    try:
+        i2 = A.get_info(h2)
+        if i2.sparse_local_nnz > 0:
+            A.apply(h2, r.data_ptr(), z.data_ptr(), 1)
+            A.reset_profile(h2)
+            sp_ms = timed(lambda: A.apply(h2, r.data_ptr(), z.data_ptr(), 1))
+            prof2 = {p["name"]: p for p in A.get_profile(h2)}
+            sl = prof2.get("sparse_local")
+            sp8_ms = timed(lambda: A.apply(h2, R8.data_ptr(), Z8.data_ptr(), 8))
+            dense_tri = sum(float(ni) * (ni + 1) for ni in _box_ni(A, h2, N))
+            sparse = {"ms": sp_ms, "ms_8rhs": sp8_ms, "factor_entries": i2.sparse_local_nnz,
+                      "dense_triangle_entries": dense_tri,
+                      "kernel_ms_per_launch": sl["ms"] / sl["launches"] if sl and sl["launches"] else None,
+                      "kernel_bytes": sl["bytes"] / sl["launches"] if sl and sl["launches"] else None,
+                      "speedup_vs_dense_apply": apply_ms / sp_ms,
+                      "note": "whole amdd_apply call; the factors (FP32 values, 16-bit row indices) are staged "
+                              "in shared memory, one warp per subdomain; bytes = factor + local vectors"}
+            if sparse["kernel_bytes"] and sparse["kernel_ms_per_launch"]:
+                sparse["kernel_GB/s"] = sparse["kernel_bytes"] / (sparse["kernel_ms_per_launch"] * 1e-3) / 1e9
+    finally:
+        A.destroy(h2)
     spmv_gbs = kernels["spmv"]["GB/s"] if "spmv" in kernels else None
     apply_gbs = apply_bytes / (apply_ms * 1e-3) / 1e9
     return {
@@ -345,6 +379,7 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20, m=None):
                        "GB/s": apply8_bytes / (apply8_ms * 1e-3) / 1e9,
                        "note": "one amdd_apply call on 8 right-hand sides; factors read once for all"},
         "kernels_in_pcg": kernels,
+        "one_level_apply_sparse_factors": sparse,
     }
 
 
@@ -380,6 +415,15 @@ def _arm_ms(A, torch, dev, sp, w, precision, steps=2, warm=1):
             out = (st.iterations, info.n_C, info.setup_ms, st.solve_ms)
     return {"ms": sum(ts) / len(ts), "pcg_iterations": out[0], "n_C": out[1], "setup_ms": out[2],
             "solve_ms": out[3]}
+
+
+def _box_ni(A, h, N):
+    """|Omega_i| of every subdomain of a handle."""
+    out = []
+    for i in range(N):
+        nI, nG, _, _ = A.get_subdomain(h, i)
+        out.append(nI + nG)
+    return out
 
 
 def variants(A, torch, np, dev, sp, precision, steps=3):
@@ -758,8 +802,11 @@ def run_amdd(args):
         alg = svd_flops(sizes) if name in SVD_CLASSES else eig_flops(sizes)
         achieved = alg / (per_step_ms * 1e-3) / 1e12
         peak = (FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS) / 1e3
+        traffic = TRAFFIC_PER_STEP.get((name, w["name"]))
         roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": ("DRAM bytes per step of this class (all its launches in one step), from an ncu "
+                                 "capture of the same workload" if traffic else None),
                 "algorithmic_flops_per_step": alg,
                 "algorithmic_count": ("sum_i 4 n_i^2 tilde n_i (dense SVD of the X_i)" if name in SVD_CLASSES
                                       else "sum_i (8/3) |Omega_Ii|^3 (Householder reduction)"),

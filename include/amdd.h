@@ -143,7 +143,14 @@ typedef struct {
                              with the 3xTF32 split (hi*hi + hi*lo + lo*hi, FP32 accumulation), whose
                              error is of the order of an FP32 multiply-add loop's; 0: CUDA-core FMA;
                              default 0                                                              */
-    int32_t reserved3;    /* must be zero                                                          */
+    int32_t local_solver; /* local solves of the Schwarz methods (Sec. 4.1: exact local Cholesky):
+                             0: the explicit inverse factors L_i^{-1}, L_i^{-T} (dense triangles);
+                             1: sparse Cholesky factors in a nested-dissection order (the same exact
+                             factor of the permuted A_ii, with the symbolic fill only), solved by
+                             forward and backward substitution with each factor staged in shared
+                             memory; AMDD_ERR_INVALID if a factor does not fit (about 200 KB);
+                             2: 1 where every factor fits and holds at most a quarter of its dense
+                             triangle, else 0; default 0                                           */
 } amdd_opts;
 
 typedef struct {
@@ -199,6 +206,8 @@ typedef struct {
     int64_t device_bytes_peak; /* largest device memory the handle has held (bytes) */
     int64_t graph_solves;      /* PCG solves whose iterations ran as one CUDA graph   */
     int64_t tuned_buckets;     /* GEMM size buckets measured by the autotuner in this process */
+    int64_t sparse_local_nnz;  /* entries of the sparse local factors in use (0: dense inverse
+                                  factors, see amdd_opts.local_solver)                      */
     int64_t pair_stats[6];     /* block-pair one-sided Jacobi (matrices whose rows exceed shared
                                   memory): pair tasks run, pairs rotated, SM clock cycles
                                   summed over CTAs of its three phases (Gram matrices, small
@@ -477,7 +486,7 @@ amdd_status amdd_get_coarse_block(const amdd_handle* h, int32_t i, double* Zt, i
  * amdd_setup, amdd_apply and amdd_pcg_solve until amdd_reset_profile.
  * Synchronises the handle's stream.  AMDD_ERR_INVALID if profiling is off or
  * k is out of range. */
-#define AMDD_PROF_CLASSES 26
+#define AMDD_PROF_CLASSES 27
 amdd_status amdd_get_profile(amdd_handle* h, int32_t k, const char** name, int64_t* launches, double* ms,
                              double* flops, double* bytes);
 

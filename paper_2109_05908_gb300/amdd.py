@@ -33,7 +33,7 @@ class amdd_opts(C.Structure):
                 ("keep_proposal_data", C.c_int32), ("proposal", C.POINTER(amdd_proposal)),
                 ("keep_coarse_matrix", C.c_int32), ("reserved", C.c_int32), ("tie_band", C.c_double),
                 ("use_graphs", C.c_int32), ("autotune", C.c_int32), ("mem_budget", C.c_size_t),
-                ("tensor_cores", C.c_int32), ("reserved3", C.c_int32)]
+                ("tensor_cores", C.c_int32), ("local_solver", C.c_int32)]
 
 
 MLP_NPARAM = 140032
@@ -59,7 +59,8 @@ class amdd_info(C.Structure):
                 ("inner_iterations_max", C.c_int32),
                 ("inner_solves", C.c_int64), ("inner_iterations", C.c_int64), ("n_tied", C.c_int32),
                 ("n_below_one", C.c_int32), ("device_bytes_peak", C.c_int64), ("graph_solves", C.c_int64),
-                ("tuned_buckets", C.c_int64), ("pair_stats", C.c_int64 * 6)]
+                ("tuned_buckets", C.c_int64), ("sparse_local_nnz", C.c_int64),
+                ("pair_stats", C.c_int64 * 6)]
 
 
 class AmddError(RuntimeError):
@@ -364,7 +365,7 @@ def lanczos_extremes(alpha, beta):
     return lo.value, hi.value
 
 
-PROF_CLASSES = 26
+PROF_CLASSES = 27
 
 
 def get_profile(h: int):

@@ -74,6 +74,7 @@ enum ProfK {
     PK_CSOLVE,
     PK_GMRES,
     PK_GEMM_TC,
+    PK_SPLOCAL,
     PK_COUNT
 };
 static_assert(PK_COUNT == AMDD_PROF_CLASSES, "profile classes");
@@ -81,7 +82,7 @@ static const char* const kProfNames[PK_COUNT] = {
     "gather_values", "chol_diag", "chol_panel", "gemm_tiles", "trtri_diag", "jacobi_svd", "jacobi_eig", "jacobi_f32", "tridiag", "bisect",
     "small_dense", "e_offdiag", "spmv", "gemv_rows", "gather_scatter", "pcg_vectors",
     "gemm_tiles_f32", "chol_diag_f32", "chol_panel_f32", "trtri_diag_f32", "tridiag_f32", "bisect_f32",
-    "gemv_rows_f32", "coarse_solve", "gmres_vectors", "gemm_tc_f32"};
+    "gemv_rows_f32", "coarse_solve", "gmres_vectors", "gemm_tc_f32", "sparse_local"};
 
 // class of a kernel in element type T (FP32 variants have their own classes)
 template <typename T>
@@ -262,6 +263,17 @@ struct amdd_handle {
     int use_graphs = 1;
     int autotune = 1;  // GEMM tile autotuner (process-wide table)
     int tensor_cores = 0;  // FP32 GEMMs on tcgen05 (3xTF32)
+    // sparse local Cholesky factors (amdd_opts.local_solver): columns of each
+    // factor in a nested-dissection order, used by the local solves when kept
+    int local_solver = 0;
+    bool sparse_local = false;
+    void* d_sl_val = nullptr;  // FP64 or FP32 as the local solves
+    uint16_t* d_sl_row = nullptr;
+    int32_t* d_sl_colptr = nullptr;
+    int32_t* d_sl_perm = nullptr;
+    SparseLocalDesc* d_sl_desc = nullptr;
+    size_t sl_smem = 0;
+    int64_t sl_nnz = 0;
     // PCG iterations as a CUDA graph (amdd_opts.use_graphs): a device-side
     // while-loop over one iteration, built on the first solve of a tolerance
     cudaGraph_t pg_graph = nullptr;
@@ -385,6 +397,9 @@ constexpr int SMALL_LAUNCH_TILES = 2 * 152;
 constexpr int TINY_LAUNCH_TILES = 152 / 2;
 // Smallest batch (in 128 x 128 output tiles) that takes the tensor-core GEMM.
 constexpr int TC_MIN_TILES = 16;
+// Largest dynamic shared memory of a sparse local solve (one subdomain's factor
+// and one vector).
+constexpr size_t SPARSE_LOCAL_SMEM_MAX = 200 * 1024;
 
 // Process-wide autotuner of the GEMM tile (amdd_opts.autotune): per element
 // type and size bucket (the batch's count of 64 x 64 output tiles and its
@@ -1946,6 +1961,117 @@ std::vector<int32_t> rcm_order(const std::vector<std::vector<int32_t>>& nbr) {
     return order;
 }
 
+// Sparse local factors (amdd_opts.local_solver): per subdomain the
+// nested-dissection order of the local pattern and the column structure of its
+// Cholesky factor (host, nd_factor_pattern); the permuted A_ii gathered dense on
+// the device, factored by the batched dense Cholesky (entries outside the
+// symbolic structure are rounding residues of exact zeros and are dropped), and
+// its entries compacted into columns.  With local_solver = 2 (automatic) the
+// factors are kept only when every subdomain's factor fits in shared memory and
+// holds at most a quarter of its dense triangle; otherwise the dense inverse
+// factors serve and nothing is kept.
+template <typename T>
+void build_sparse_local(Ctx& C, amdd_handle* h, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                        const std::vector<int32_t>& omega) {
+    const int N = h->N;
+    cudaStream_t s = h->s;
+    std::vector<int32_t> perm_all(h->sum_ni), colptr_all;
+    std::vector<uint16_t> rows_all;
+    std::vector<int64_t> src_k, dst_p, ent_idx;
+    std::vector<SparseLocalDesc> desc(N);
+    std::vector<int32_t> stamp(h->n, -1), pos(h->n, -1);
+    size_t smem_max = 0;
+    int64_t nnz_tot = 0, dense_tot = 0;
+    bool fits = true;
+    for (int i = 0; i < N; ++i) {
+        const int ni = h->ni[i];
+        if (ni > 65535) {
+            fits = false;
+            break;
+        }
+        const int32_t* om = omega.data() + h->off_om[i];
+        for (int a = 0; a < ni; ++a) {
+            stamp[om[a]] = i;
+            pos[om[a]] = a;
+        }
+        std::vector<int64_t> lrp(ni + 1, 0);
+        std::vector<int32_t> lci;
+        std::vector<int64_t> lk;  // global entry of each local entry
+        for (int a = 0; a < ni; ++a) {
+            const int32_t g = om[a];
+            for (int64_t k = rp[g]; k < rp[g + 1]; ++k)
+                if (stamp[ci[k]] == i) {
+                    lci.push_back(pos[ci[k]]);
+                    lk.push_back(k);
+                }
+            lrp[a + 1] = (int64_t)lci.size();
+        }
+        std::vector<int32_t> perm, colptr, rows;
+        require(nd_factor_pattern(ni, lrp.data(), lci.data(), 16, perm, colptr, rows));
+        std::vector<int32_t> iperm(ni);
+        for (int k = 0; k < ni; ++k) iperm[perm[k]] = k;
+        // the permuted matrix: local (a, b) goes to (iperm a, iperm b)
+        for (int a = 0; a < ni; ++a)
+            for (int64_t q = lrp[a]; q < lrp[a + 1]; ++q) {
+                src_k.push_back(lk[q]);
+                dst_p.push_back(h->off_sq[i] + (int64_t)iperm[a] * ni + iperm[lci[q]]);
+            }
+        const int nnz = colptr[ni];
+        desc[i] = {ni, nnz, (int64_t)colptr_all.size(), nnz_tot, h->off_om[i]};
+        colptr_all.insert(colptr_all.end(), colptr.begin(), colptr.end());
+        for (int j = 0; j < ni; ++j)
+            for (int q = colptr[j]; q < colptr[j + 1]; ++q) {
+                const int r = rows[q];
+                rows_all.push_back((uint16_t)r);
+                const int64_t at = h->off_sq[i] + (int64_t)r * ni + j;  // lower triangle, row-major
+                ent_idx.push_back(q == colptr[j] ? -at - 1 : at);        // diagonal: its reciprocal
+            }
+        std::copy(perm.begin(), perm.end(), perm_all.begin() + h->off_om[i]);
+        nnz_tot += nnz;
+        dense_tot += (int64_t)ni * (ni + 1) / 2;
+        smem_max = std::max(smem_max, sparse_local_smem<T>(ni, nnz));
+    }
+    if (fits) fits = smem_max <= SPARSE_LOCAL_SMEM_MAX;
+    if (h->local_solver == 2 && (!fits || 4 * nnz_tot > dense_tot)) return;  // automatic: dense
+    require(fits);  // local_solver = 1 needs every factor in shared memory
+    // numeric factorisation of the permuted matrices
+    double* Ap = C.tnew<double>(h->sum_sq);
+    ck(cudaMemsetAsync(Ap, 0, h->sum_sq * sizeof(double), s));
+    {
+        const int64_t* sk = C.up(src_k);
+        const int64_t* dp = C.up(dst_p);
+        PScope ps(h, PK_GATHER, 0.0, 32.0 * src_k.size());
+        launch_gather_values(sk, dp, (int64_t)src_k.size(), h->val, Ap, s);
+    }
+    T* At = nullptr;
+    if constexpr (std::is_same<T, double>::value) {
+        At = Ap;
+    } else {
+        At = C.tnew<T>(h->sum_sq);
+        launch_convert<double, T>(Ap, At, h->sum_sq, s);
+    }
+    std::vector<int64_t> off_lv(N + 1, 0);
+    for (int i = 0; i < N; ++i) off_lv[i + 1] = off_lv[i] + (int64_t)cdiv(h->ni[i], CHOL_NB) * CHOL_NB * CHOL_NB;
+    T* linv = C.tnew<T>(off_lv[N]);
+    std::vector<CholDescT<T>> cd(N);
+    for (int i = 0; i < N; ++i) cd[i] = {At + h->off_sq[i], h->ni[i], h->ni[i], h->ni[i], nullptr, linv + off_lv[i]};
+    chol_batched(C, cd);
+    // the factor's entries by column
+    h->d_sl_val = dnew<T>(h, nnz_tot);
+    {
+        const int64_t* ei = C.up(ent_idx);
+        PScope ps(h, PK_GATHER, 0.0, (8.0 + 2.0 * sizeof(T)) * nnz_tot);
+        launch_gather_entries<T>(At, ei, static_cast<T*>(h->d_sl_val), nnz_tot, s);
+    }
+    h->d_sl_row = C.up(rows_all, true);
+    h->d_sl_colptr = C.up(colptr_all, true);
+    h->d_sl_perm = C.up(perm_all, true);
+    h->d_sl_desc = C.up(desc, true);
+    h->sl_smem = smem_max;
+    h->sl_nnz = nnz_tot;
+    h->sparse_local = true;
+}
+
 template <typename T, typename TS>
 void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
     constexpr bool f64 = std::is_same<T, double>::value;
@@ -2546,6 +2672,12 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
         trtri_batched(C, td);
         transpose_batched(C, src, dst, nn, ld, ld);
     }
+
+    // ---- (1b) sparse Cholesky factors of the A_ii in a nested-dissection order
+    // (Sec. 4.1: exact local Cholesky; the same factor of the permuted matrix,
+    // with the fill of the symbolic factorisation only): local solves then read
+    // the factor's entries instead of the dense triangles of L_i^{-1}.
+    if (h->local_solver != 0) build_sparse_local<T>(C, h, rp, ci, omega);
 
     // ---- (2) SVD of X_i (Sec. 3.2) by one-sided Jacobi on its rows: an
     // FP32-preconditioned rotation Q_i (orthogonal to FP64 accuracy) is applied
@@ -3202,12 +3334,34 @@ void do_setup(amdd_handle* h, const amdd_csr* A, const int32_t* d_part) {
 // Local solves of the Schwarz methods: rloc = R_i r for every subdomain,
 // then y_i = L_i^{-T} L_i^{-1} rloc_i (into d_yloc, or d_yloc32 in the mixed
 // form, whose local solves run in FP32).
+// The sparse local solves on nb gathered vectors (ld apart) of precision T.
+template <typename T>
+void sparse_local_solves(amdd_handle* h, const T* rloc, T* yloc, int nb, int64_t ld) {
+    const double nnz = (double)h->sl_nnz;
+    PScope ps(h, PK_SPLOCAL, 4.0 * nnz * nb,
+              nnz * (sizeof(T) + 2.0) + (4.0 + 2.0 * sizeof(T)) * h->sum_ni * nb);
+    launch_sparse_local_solve<T>(h->d_sl_desc, h->N, h->sl_smem, h->d_sl_colptr, h->d_sl_row,
+                                 static_cast<const T*>(h->d_sl_val), h->d_sl_perm, rloc, yloc, nb, ld, h->s);
+}
+
 void local_solves(amdd_handle* h, const double* r) {
     cudaStream_t s = h->s;
     const double tri = (double)h->apply_tri_elems;  // elements of the lower + upper local factors
     {
         PScope ps(h, PK_GATHER_SCATTER, 0.0, 20.0 * h->sum_ni);
         launch_gather_vec(h->d_omega, h->sum_ni, r, h->d_rloc, s);
+    }
+    if (h->sparse_local) {
+        if (h->precision == 0) {
+            sparse_local_solves<double>(h, h->d_rloc, h->d_yloc, 1, h->sum_ni);
+        } else {
+            {
+                PScope ps(h, PK_GATHER_SCATTER, 0.0, 12.0 * h->sum_ni);
+                launch_convert<double, float>(h->d_rloc, h->d_rloc32, h->sum_ni, s);
+            }
+            sparse_local_solves<float>(h, h->d_rloc32, h->d_yloc32, 1, h->sum_ni);
+        }
+        return;
     }
     if (h->precision == 0) {
         {
@@ -3455,7 +3609,17 @@ void apply_multi(amdd_handle* h, const double* r, double* z, int nb) {
         PScope ps(h, PK_GATHER_SCATTER, 0.0, 20.0 * L * nb);
         launch_gather_vec_multi(h->d_omega, L, r, h->n, h->d_m_rloc, nb, s);
     }
-    if (h->precision == 0) {
+    if (h->sparse_local) {
+        if (h->precision == 0) {
+            sparse_local_solves<double>(h, h->d_m_rloc, h->d_m_yloc, nb, L);
+        } else {
+            {
+                PScope ps(h, PK_GATHER_SCATTER, 0.0, 12.0 * L * nb);
+                launch_convert<double, float>(h->d_m_rloc, h->d_m_rloc32, L * nb, s);
+            }
+            sparse_local_solves<float>(h, h->d_m_rloc32, h->d_m_yloc32, nb, L);
+        }
+    } else if (h->precision == 0) {
         auto g1 = static_cast<const GemvDesc*>(h->d_m_gv_l1);
         auto g2 = static_cast<const GemvDesc*>(h->d_m_gv_l2);
         {
@@ -4020,7 +4184,8 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         if (o.reserved != 0 || o.keep_coarse_matrix < 0 || o.keep_coarse_matrix > 1) return AMDD_ERR_INVALID;
         if (!(o.tie_band >= 0.0) || o.use_graphs < 0 || o.use_graphs > 1 || o.autotune < 0 || o.autotune > 1)
             return AMDD_ERR_INVALID;
-        if (o.tensor_cores < 0 || o.tensor_cores > 1 || o.reserved3 != 0) return AMDD_ERR_INVALID;
+        if (o.tensor_cores < 0 || o.tensor_cores > 1) return AMDD_ERR_INVALID;
+        if (o.local_solver < 0 || o.local_solver > 2) return AMDD_ERR_INVALID;
         if (o.profile_classes >> PK_COUNT) return AMDD_ERR_INVALID;
         if (o.eig_solver < 0 || o.eig_solver > 3) return AMDD_ERR_INVALID;
         // the matrix-free eigensolve: FP64 only, with the shift far enough above
@@ -4061,6 +4226,7 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         h->use_graphs = o.use_graphs;
         h->autotune = o.autotune;
         h->tensor_cores = o.tensor_cores;
+        h->local_solver = o.local_solver;
         if (o.eig_solver == 2) {
             h->prop = *o.proposal;
             h->have_prop = true;
@@ -4631,6 +4797,7 @@ amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
     for (int k = 0; k < 6; ++k) info->pair_stats[k] = h->pair_stats[k];
     info->device_bytes_peak = (int64_t)h->bytes_peak;
     info->graph_solves = h->graph_solves;
+    info->sparse_local_nnz = h->sparse_local ? h->sl_nnz : 0;
     {
         std::lock_guard<std::mutex> lock(tile_tuner().mu);
         info->tuned_buckets = tile_tuner().measured;

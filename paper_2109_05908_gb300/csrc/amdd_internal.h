@@ -265,6 +265,33 @@ void launch_convert_blocks(const Ti* const* src, const int* lds, To* const* dst,
                            int nmat, int maxn, cudaStream_t s);
 
 // ---------------------------------------------------------------- sparse / vectors
+// Sparse local Cholesky factors: per subdomain its order n, factor entries
+// nnz, the offset of its column pointers (n + 1 local offsets), of its entries
+// and of its rows in the local vectors.
+struct SparseLocalDesc {
+    int n, nnz;
+    int64_t poff, eoff, xoff;
+};
+// dst[t] = src[idx[t]] (idx >= 0) or 1 / src[-idx[t] - 1]
+template <typename T>
+void launch_gather_entries(const T* src, const int64_t* idx, T* dst, int64_t cnt, cudaStream_t s);
+// y_i = P^T L^{-T} L^{-1} P r_i with the factors staged in shared memory (smem:
+// the largest sparse_local_smem of the batch), nb vectors ld apart
+template <typename T>
+size_t sparse_local_smem(int n, int nnz);
+template <typename T>
+void launch_sparse_local_solve(const SparseLocalDesc* d, int nmat, size_t smem, const int32_t* colptr,
+                               const uint16_t* rowidx, const T* val, const int32_t* perm, const T* r, T* y, int nb,
+                               int64_t ld, cudaStream_t s);
+
+// Host: nested-dissection order of the symmetric pattern of an n x n CSR graph
+// (sets of at most `leaf` unknowns not cut) and the column structure of the
+// Cholesky factor of P A P^T in that order: perm[k] = old index of new k,
+// column j holds rows[colptr[j] .. colptr[j+1]), the diagonal j first, then
+// ascending.  False on a malformed graph.
+bool nd_factor_pattern(int n, const int64_t* rowptr, const int32_t* colind, int leaf, std::vector<int32_t>& perm,
+                       std::vector<int32_t>& colptr, std::vector<int32_t>& rows);
+
 // *flag |= 1 when v[0..n) holds a NaN or an infinity
 void launch_nonfinite(const double* v, int64_t n, int* flag, cudaStream_t s);
 // Lanes per row of launch_spmv for a matrix of n rows and nnz entries: the one

@@ -83,6 +83,109 @@ void launch_spmv_multi(int64_t n, const int64_t* rowptr, const int32_t* col, con
     spmv_multi_kernel<<<(unsigned)(want < 152 * 64 ? want : 152 * 64), 256, 0, s>>>(n, rowptr, col, val, x, y, nb, ld);
 }
 
+// ------------------------------------------------------------------ sparse local factors
+// dst[t] = src[idx[t]] for idx[t] >= 0, and 1 / src[-idx[t] - 1] otherwise
+// (the diagonal of a factor column is stored as its reciprocal)
+template <typename T>
+__global__ void gather_entries_kernel(const T* __restrict__ src, const int64_t* __restrict__ idx,
+                                      T* __restrict__ dst, int64_t cnt) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx[t];
+        dst[t] = k >= 0 ? src[k] : T(1) / src[-k - 1];
+    }
+}
+
+template <typename T>
+void launch_gather_entries(const T* src, const int64_t* idx, T* dst, int64_t cnt, cudaStream_t s) {
+    if (cnt <= 0) return;
+    const int64_t want = (cnt + 255) / 256;
+    gather_entries_kernel<T><<<(unsigned)(want < 152 * 32 ? want : 152 * 32), 256, 0, s>>>(src, idx, dst, cnt);
+}
+template void launch_gather_entries<float>(const float*, const int64_t*, float*, int64_t, cudaStream_t);
+template void launch_gather_entries<double>(const double*, const int64_t*, double*, int64_t, cudaStream_t);
+
+// The local solves of the Schwarz methods with sparse Cholesky factors in a
+// nested-dissection order: y_i = P^T L^{-T} L^{-1} P r_i for every subdomain,
+// one warp (one CTA) per subdomain.  The factor's columns (CSC, the diagonal
+// first and stored as its reciprocal, 16-bit row indices) are staged in shared
+// memory, then for each of nb right-hand sides
+//   forward  (column j ascending):  w_j = x_j / l_jj,  x_i -= l_ij w_j (i > j);
+//   backward (column j descending): z_j = (w_j - sum_{i>j} l_ij z_i) / l_jj,
+// the sum over the column's entries lane-strided with a fixed shuffle tree, so
+// the result is reproducible run to run.  r and y hold nb vectors, ld apart.
+template <typename T>
+__global__ void __launch_bounds__(32) sparse_local_solve_kernel(const SparseLocalDesc* __restrict__ descs,
+                                                                const int32_t* __restrict__ colptr,
+                                                                const uint16_t* __restrict__ rowidx,
+                                                                const T* __restrict__ val,
+                                                                const int32_t* __restrict__ perm,
+                                                                const T* __restrict__ r, T* __restrict__ y, int nb,
+                                                                int64_t ld) {
+    extern __shared__ __align__(16) unsigned char sl_raw[];
+    const SparseLocalDesc d = descs[blockIdx.x];
+    const int n = d.n, lane = threadIdx.x;
+    const int nnz = d.nnz;
+    T* x = reinterpret_cast<T*>(sl_raw);
+    T* v = x + n;
+    int32_t* cp = reinterpret_cast<int32_t*>(v + nnz);
+    uint16_t* rw = reinterpret_cast<uint16_t*>(cp + n + 1);
+    const int32_t* gcp = colptr + d.poff;
+    for (int k = lane; k <= n; k += 32) cp[k] = gcp[k];
+    for (int k = lane; k < nnz; k += 32) {
+        v[k] = val[d.eoff + k];
+        rw[k] = rowidx[d.eoff + k];
+    }
+    const int32_t* pm = perm + d.xoff;
+    __syncwarp();
+    for (int vec = 0; vec < nb; ++vec) {
+        const T* rv = r + (size_t)vec * ld + d.xoff;
+        T* yv = y + (size_t)vec * ld + d.xoff;
+        for (int a = lane; a < n; a += 32) x[a] = rv[pm[a]];
+        __syncwarp();
+        for (int j = 0; j < n; ++j) {
+            const int b = cp[j], e = cp[j + 1];
+            const T wj = x[j] * v[b];
+            __syncwarp();
+            for (int k = b + 1 + lane; k < e; k += 32) x[rw[k]] = fma(-v[k], wj, x[rw[k]]);
+            if (lane == 0) x[j] = wj;
+            __syncwarp();
+        }
+        for (int j = n - 1; j >= 0; --j) {
+            const int b = cp[j], e = cp[j + 1];
+            T sum = T(0);
+            for (int k = b + 1 + lane; k < e; k += 32) sum = fma(v[k], x[rw[k]], sum);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) x[j] = (x[j] - sum) * v[b];
+            __syncwarp();
+        }
+        for (int a = lane; a < n; a += 32) yv[pm[a]] = x[a];
+        __syncwarp();
+    }
+}
+
+template <typename T>
+size_t sparse_local_smem(int n, int nnz) {
+    return (size_t)(n + nnz) * sizeof(T) + (size_t)(n + 1) * sizeof(int32_t) + (size_t)nnz * sizeof(uint16_t) + 16;
+}
+template size_t sparse_local_smem<float>(int, int);
+template size_t sparse_local_smem<double>(int, int);
+
+template <typename T>
+void launch_sparse_local_solve(const SparseLocalDesc* d, int nmat, size_t smem, const int32_t* colptr,
+                               const uint16_t* rowidx, const T* val, const int32_t* perm, const T* r, T* y, int nb,
+                               int64_t ld, cudaStream_t s) {
+    if (nmat <= 0) return;
+    cudaFuncSetAttribute(sparse_local_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sparse_local_solve_kernel<T><<<nmat, 32, smem, s>>>(d, colptr, rowidx, val, perm, r, y, nb, ld);
+}
+template void launch_sparse_local_solve<float>(const SparseLocalDesc*, int, size_t, const int32_t*, const uint16_t*,
+                                               const float*, const int32_t*, const float*, float*, int, int64_t,
+                                               cudaStream_t);
+template void launch_sparse_local_solve<double>(const SparseLocalDesc*, int, size_t, const int32_t*,
+                                                const uint16_t*, const double*, const int32_t*, const double*,
+                                                double*, int, int64_t, cudaStream_t);
+
 // ------------------------------------------------------------------ input checks
 // *flag |= 1 if any of v[0..n) is NaN or infinite (the flag is only ever set)
 __global__ void nonfinite_kernel(const double* __restrict__ v, int64_t n, int* __restrict__ flag) {

@@ -178,6 +178,75 @@ struct Dissect {
 
 }  // namespace
 
+namespace amdd {
+
+bool nd_factor_pattern(int n, const int64_t* rowptr, const int32_t* colind, int leaf, std::vector<int32_t>& perm,
+                       std::vector<int32_t>& colptr, std::vector<int32_t>& rows) {
+    if (n < 0 || leaf < 1 || (n > 0 && (!rowptr || !colind)) || (n > 0 && rowptr[0] != 0)) return false;
+    for (int r = 0; r < n; ++r)
+        if (rowptr[r + 1] < rowptr[r]) return false;
+    for (int64_t k = 0; n > 0 && k < rowptr[n]; ++k)
+        if (colind[k] < 0 || colind[k] >= n) return false;
+    perm.assign(n, 0);
+    colptr.assign(n + 1, 0);
+    rows.clear();
+    if (n == 0) return true;
+    const Graph g = symmetrise(n, rowptr, colind);
+    Dissect d(g, leaf);
+    std::vector<int32_t> all(n);
+    for (int v = 0; v < n; ++v) all[v] = v;
+    d.run(all, 0);
+    if ((int)d.order.size() != n) return false;
+    std::vector<int32_t> iperm(n);
+    for (int k = 0; k < n; ++k) {
+        perm[k] = d.order[k];
+        iperm[d.order[k]] = k;
+    }
+    // elimination tree of P A P^T (ancestor path compression)
+    std::vector<int32_t> par(n, -1), anc(n, -1);
+    for (int k = 0; k < n; ++k) {
+        const int32_t v = perm[k];
+        for (int64_t q = g.ptr[v]; q < g.ptr[v + 1]; ++q) {
+            int32_t j = iperm[g.adj[q]];
+            if (j >= k) continue;
+            while (anc[j] != -1 && anc[j] != k) {
+                const int32_t nx = anc[j];
+                anc[j] = k;
+                j = nx;
+            }
+            if (anc[j] == -1) {
+                anc[j] = k;
+                par[j] = k;
+            }
+        }
+    }
+    // row i of the factor holds the columns of its row subtree: the paths from
+    // each j < i with a_ij != 0 up the tree to i; collected column by column,
+    // so each column lists its rows in ascending order after the diagonal
+    std::vector<std::vector<int32_t>> col(n);
+    for (int j = 0; j < n; ++j) col[j].push_back(j);
+    std::vector<int32_t> mark(n, -1);
+    for (int i = 0; i < n; ++i) {
+        mark[i] = i;
+        const int32_t v = perm[i];
+        for (int64_t q = g.ptr[v]; q < g.ptr[v + 1]; ++q) {
+            int32_t j = iperm[g.adj[q]];
+            if (j >= i) continue;
+            while (mark[j] != i) {
+                col[j].push_back(i);
+                mark[j] = i;
+                j = par[j];
+            }
+        }
+    }
+    for (int j = 0; j < n; ++j) colptr[j + 1] = colptr[j] + (int32_t)col[j].size();
+    rows.reserve(colptr[n]);
+    for (int j = 0; j < n; ++j) rows.insert(rows.end(), col[j].begin(), col[j].end());
+    return true;
+}
+
+}  // namespace amdd
+
 extern "C" amdd_status amdd_nd_order(int64_t n, const int64_t* rowptr, const int32_t* colind, int32_t leaf,
                                      int32_t* perm, int32_t* parent, int64_t* colcount, int64_t* nnzL) {
     if (n < 0 || n > INT32_MAX || leaf < 1 || (n > 0 && (!rowptr || !colind || !perm))) return AMDD_ERR_INVALID;

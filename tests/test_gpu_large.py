@@ -127,3 +127,21 @@ def test_large_subdomains_mixed(name, prec):
         assert abs(st.iterations - its_o) <= max(1, int(np.ceil(0.1 * its_o))), (st.iterations, its_o)
     finally:
         Q.close()
+
+
+def test_sparse_local_factors_beyond_shared_memory():
+    """On subdomains of 1.5k to 2k unknowns (3D, overlap 2) a sparse factor does
+    not fit in shared memory: local_solver = 1 is AMDD_ERR_INVALID and
+    local_solver = 2 keeps the dense inverse factors."""
+    M, part, N, ov, tau, S, eta, r, zo, dA, dpart, P = _case("diff16_bfs4_ov2_tau100")
+    o = A.opts_default()
+    o.local_solver = 1
+    with pytest.raises(A.AmddError) as e:
+        Preconditioner(dA, dpart, N, ov, tau, o)
+    assert e.value.status == 1
+    o.local_solver = 2
+    Q = Preconditioner(dA, dpart, N, ov, tau, o)
+    try:
+        assert Q.info().sparse_local_nnz == 0
+    finally:
+        Q.close()
