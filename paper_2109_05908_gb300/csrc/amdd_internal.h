@@ -276,7 +276,8 @@ struct SparseLocalDesc {
 template <typename T>
 void launch_gather_entries(const T* src, const int64_t* idx, T* dst, int64_t cnt, cudaStream_t s);
 // y_i = P^T L^{-T} L^{-1} P r_i with the factors staged in shared memory (smem:
-// the largest sparse_local_smem of the batch), nb vectors ld apart
+// the largest sparse_local_smem of the batch, which has room for MAXB
+// vectors), nb <= MAXB vectors ld apart
 template <typename T>
 size_t sparse_local_smem(int n, int nnz);
 template <typename T>

@@ -534,7 +534,7 @@ __device__ __forceinline__ void jp_load4(const double* p, double* v) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* __restrict__ descs,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) jacobi_pair_kernel(const JacobiDescT<T>* __restrict__ descs,
                                                           const int4* __restrict__ tasks, int round, T tol,
                                                           int* __restrict__ rotated,
                                                           unsigned long long* __restrict__ rots,

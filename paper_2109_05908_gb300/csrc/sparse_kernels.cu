@@ -106,13 +106,16 @@ template void launch_gather_entries<double>(const double*, const int64_t*, doubl
 
 // The local solves of the Schwarz methods with sparse Cholesky factors in a
 // nested-dissection order: y_i = P^T L^{-T} L^{-1} P r_i for every subdomain,
-// one warp (one CTA) per subdomain.  The factor's columns (CSC, the diagonal
-// first and stored as its reciprocal, 16-bit row indices) are staged in shared
-// memory, then for each of nb right-hand sides
+// one warp (one CTA) per subdomain and up to 8 right-hand sides at once.  The
+// factor's columns (CSC, the diagonal first and stored as its reciprocal,
+// 16-bit row indices) and the nb vectors are staged in shared memory; the warp
+// splits into nb groups of gs lanes (gs = 32 / nb rounded down to a power of
+// two), group v working on vector v:
 //   forward  (column j ascending):  w_j = x_j / l_jj,  x_i -= l_ij w_j (i > j);
 //   backward (column j descending): z_j = (w_j - sum_{i>j} l_ij z_i) / l_jj,
-// the sum over the column's entries lane-strided with a fixed shuffle tree, so
-// the result is reproducible run to run.  r and y hold nb vectors, ld apart.
+// the sum lane-strided over the column's entries with a fixed shuffle tree
+// inside the group, so the result is reproducible run to run.  r and y hold nb
+// vectors, ld apart.
 template <typename T>
 __global__ void __launch_bounds__(32) sparse_local_solve_kernel(const SparseLocalDesc* __restrict__ descs,
                                                                 const int32_t* __restrict__ colptr,
@@ -125,9 +128,9 @@ __global__ void __launch_bounds__(32) sparse_local_solve_kernel(const SparseLoca
     const SparseLocalDesc d = descs[blockIdx.x];
     const int n = d.n, lane = threadIdx.x;
     const int nnz = d.nnz;
-    T* x = reinterpret_cast<T*>(sl_raw);
-    T* v = x + n;
-    int32_t* cp = reinterpret_cast<int32_t*>(v + nnz);
+    T* v = reinterpret_cast<T*>(sl_raw);
+    T* x = v + nnz;  // nb vectors of n
+    int32_t* cp = reinterpret_cast<int32_t*>(x + (size_t)nb * n);
     uint16_t* rw = reinterpret_cast<uint16_t*>(cp + n + 1);
     const int32_t* gcp = colptr + d.poff;
     for (int k = lane; k <= n; k += 32) cp[k] = gcp[k];
@@ -136,37 +139,46 @@ __global__ void __launch_bounds__(32) sparse_local_solve_kernel(const SparseLoca
         rw[k] = rowidx[d.eoff + k];
     }
     const int32_t* pm = perm + d.xoff;
+    for (int e = lane; e < nb * n; e += 32) {
+        const int vec = e / n, a = e - vec * n;
+        x[e] = r[(size_t)vec * ld + d.xoff + pm[a]];
+    }
+    int gs = 32;
+    while (gs > 1 && gs * nb > 32) gs >>= 1;
+    const int vec = lane / gs, sub = lane % gs;
+    const bool act = vec < nb;
+    T* xv = x + (size_t)(act ? vec : 0) * n;
     __syncwarp();
-    for (int vec = 0; vec < nb; ++vec) {
-        const T* rv = r + (size_t)vec * ld + d.xoff;
-        T* yv = y + (size_t)vec * ld + d.xoff;
-        for (int a = lane; a < n; a += 32) x[a] = rv[pm[a]];
-        __syncwarp();
-        for (int j = 0; j < n; ++j) {
-            const int b = cp[j], e = cp[j + 1];
-            const T wj = x[j] * v[b];
-            __syncwarp();
-            for (int k = b + 1 + lane; k < e; k += 32) x[rw[k]] = fma(-v[k], wj, x[rw[k]]);
-            if (lane == 0) x[j] = wj;
-            __syncwarp();
+    for (int j = 0; j < n; ++j) {
+        const int b = cp[j], e = cp[j + 1];
+        const T dinv = v[b];
+        if (act) {
+            const T wj = xv[j] * dinv;
+            for (int k = b + 1 + sub; k < e; k += gs) xv[rw[k]] = fma(-v[k], wj, xv[rw[k]]);
         }
-        for (int j = n - 1; j >= 0; --j) {
-            const int b = cp[j], e = cp[j + 1];
-            T sum = T(0);
-            for (int k = b + 1 + lane; k < e; k += 32) sum = fma(v[k], x[rw[k]], sum);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if (lane == 0) x[j] = (x[j] - sum) * v[b];
-            __syncwarp();
-        }
-        for (int a = lane; a < n; a += 32) yv[pm[a]] = x[a];
         __syncwarp();
+        if (act && sub == 0) xv[j] *= dinv;
+        __syncwarp();
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        const int b = cp[j], e = cp[j + 1];
+        T sum = T(0);
+        if (act)
+            for (int k = b + 1 + sub; k < e; k += gs) sum = fma(v[k], xv[rw[k]], sum);
+        for (int o = gs / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (act && sub == 0) xv[j] = (xv[j] - sum) * v[b];
+        __syncwarp();
+    }
+    for (int e = lane; e < nb * n; e += 32) {
+        const int vv = e / n, a = e - vv * n;
+        y[(size_t)vv * ld + d.xoff + pm[a]] = x[e];
     }
 }
 
 template <typename T>
 size_t sparse_local_smem(int n, int nnz) {
-    return (size_t)(n + nnz) * sizeof(T) + (size_t)(n + 1) * sizeof(int32_t) + (size_t)nnz * sizeof(uint16_t) + 16;
+    return (size_t)((size_t)MAXB * n + nnz) * sizeof(T) + (size_t)(n + 1) * sizeof(int32_t) +
+           (size_t)nnz * sizeof(uint16_t) + 16;
 }
 template size_t sparse_local_smem<float>(int, int);
 template size_t sparse_local_smem<double>(int, int);
