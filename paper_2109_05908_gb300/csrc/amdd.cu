@@ -272,7 +272,8 @@ struct amdd_handle {
     int32_t* d_sl_colptr = nullptr;
     int32_t* d_sl_perm = nullptr;
     SparseLocalDesc* d_sl_desc = nullptr;
-    size_t sl_smem = 0;
+    size_t sl_smem = 0;  // shared memory of the largest factor without its vectors
+    int sl_nmax = 0;     // largest subdomain (vectors: nb x sl_nmax entries)
     int64_t sl_nnz = 0;
     // PCG iterations as a CUDA graph (amdd_opts.use_graphs): a device-side
     // while-loop over one iteration, built on the first solve of a tolerance
@@ -1980,7 +1981,8 @@ void build_sparse_local(Ctx& C, amdd_handle* h, const std::vector<int64_t>& rp, 
     std::vector<int64_t> src_k, dst_p, ent_idx;
     std::vector<SparseLocalDesc> desc(N);
     std::vector<int32_t> stamp(h->n, -1), pos(h->n, -1);
-    size_t smem_max = 0;
+    size_t smem_max = 0, smem_fixed = 0;
+    int n_max = 0;
     int64_t nnz_tot = 0, dense_tot = 0;
     bool fits = true;
     for (int i = 0; i < N; ++i) {
@@ -2029,8 +2031,12 @@ void build_sparse_local(Ctx& C, amdd_handle* h, const std::vector<int64_t>& rp, 
         std::copy(perm.begin(), perm.end(), perm_all.begin() + h->off_om[i]);
         nnz_tot += nnz;
         dense_tot += (int64_t)ni * (ni + 1) / 2;
-        smem_max = std::max(smem_max, sparse_local_smem<T>(ni, nnz));
+        smem_fixed = std::max(smem_fixed, sparse_local_smem<T>(ni, nnz, 0));
+        n_max = std::max(n_max, ni);
     }
+    // a launch reserves the largest factor plus nb vectors of the largest
+    // subdomain for every CTA, so the bound takes both maxima together
+    smem_max = smem_fixed + (size_t)MAXB * n_max * sizeof(T);
     if (fits) fits = smem_max <= SPARSE_LOCAL_SMEM_MAX;
     if (h->local_solver == 2 && (!fits || 4 * nnz_tot > dense_tot)) return;  // automatic: dense
     require(fits);  // local_solver = 1 needs every factor in shared memory
@@ -2067,7 +2073,8 @@ void build_sparse_local(Ctx& C, amdd_handle* h, const std::vector<int64_t>& rp, 
     h->d_sl_colptr = C.up(colptr_all, true);
     h->d_sl_perm = C.up(perm_all, true);
     h->d_sl_desc = C.up(desc, true);
-    h->sl_smem = smem_max;
+    h->sl_smem = smem_fixed;
+    h->sl_nmax = n_max;
     h->sl_nnz = nnz_tot;
     h->sparse_local = true;
 }
@@ -3340,7 +3347,8 @@ void sparse_local_solves(amdd_handle* h, const T* rloc, T* yloc, int nb, int64_t
     const double nnz = (double)h->sl_nnz;
     PScope ps(h, PK_SPLOCAL, 4.0 * nnz * nb,
               nnz * (sizeof(T) + 2.0) + (4.0 + 2.0 * sizeof(T)) * h->sum_ni * nb);
-    launch_sparse_local_solve<T>(h->d_sl_desc, h->N, h->sl_smem, h->d_sl_colptr, h->d_sl_row,
+    const size_t smem = h->sl_smem + (size_t)nb * h->sl_nmax * sizeof(T);
+    launch_sparse_local_solve<T>(h->d_sl_desc, h->N, smem, h->d_sl_colptr, h->d_sl_row,
                                  static_cast<const T*>(h->d_sl_val), h->d_sl_perm, rloc, yloc, nb, ld, h->s);
 }
 

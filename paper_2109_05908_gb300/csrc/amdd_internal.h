@@ -136,9 +136,6 @@ template <typename T>
 void launch_trtri_diag(const TrtriDescT<T>* d, const ChunkRef* tiles, int ntiles, int k0, cudaStream_t s);
 template <typename T>
 void launch_set_identity(const TrtriDescT<T>* d, int nmat, int maxn, cudaStream_t s);
-template <typename T>
-void launch_jacobi_t(const JacobiDescT<T>* d, int nmat, int max_sweeps, T tol, int* sweeps, unsigned long long* rots,
-                     int* err, int report_noconv, cudaStream_t s);
 // Block-pair variant for matrices of any size (rows in global memory): one
 // round of the block round-robin schedule (blocks of 32 rows; tasks[t] =
 // {matrix, pair index in the round, blocks of that matrix (even, >= 2), 0});
@@ -276,10 +273,10 @@ struct SparseLocalDesc {
 template <typename T>
 void launch_gather_entries(const T* src, const int64_t* idx, T* dst, int64_t cnt, cudaStream_t s);
 // y_i = P^T L^{-T} L^{-1} P r_i with the factors staged in shared memory (smem:
-// the largest sparse_local_smem of the batch, which has room for MAXB
-// vectors), nb <= MAXB vectors ld apart
+// the largest sparse_local_smem of the batch for nb vectors), nb <= MAXB
+// vectors ld apart
 template <typename T>
-size_t sparse_local_smem(int n, int nnz);
+size_t sparse_local_smem(int n, int nnz, int nb);
 template <typename T>
 void launch_sparse_local_solve(const SparseLocalDesc* d, int nmat, size_t smem, const int32_t* colptr,
                                const uint16_t* rowidx, const T* val, const int32_t* perm, const T* r, T* y, int nb,

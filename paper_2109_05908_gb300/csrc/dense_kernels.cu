@@ -347,20 +347,8 @@ template void launch_set_identity<double>(const TrtriDescT<double>*, int, int, c
 // ncols_dot columns to tol relative to the row norms (and, when a floor is
 // given, above that absolute floor on |<p,q>|); rotations are applied to
 // ncols_rot columns (so an identity appended on the right accumulates them).
-// Row norms^2 are recomputed at the start of each sweep and updated exactly
-// after each rotation (a' = a - t g, b' = b + t g), so a pair that needs no
-// rotation costs one inner product.  A cluster of JAC_CLUSTER CTAs works on
-// one matrix; each round of the round-robin (circle) schedule holds rows/2
-// disjoint pairs, one warp per pair, and the cluster barrier separates
-// rounds.  Every thread of the cluster runs the same number of barriers: the
-// sweep loop ends on a value all threads compute identically from the CTAs'
-// shared flags (read through distributed shared memory), and is bounded by
-// max_sweeps.
-template <typename T>
-__device__ __forceinline__ T ldcg_t(const T* p) {
-    return __ldcg(p);
-}
-
+// Two forms below: the rows resident in the shared memory of a cluster (block
+// kernel) when they fit, else block pairs with the rows in global memory.
 // Rotation that makes rows p, q (Gram [[a, g], [g, b]]) orthogonal:
 // t = tan(theta) is the smaller root of t^2 + 2 zeta t - 1 = 0, zeta =
 // (b - a) / (2 g), written as t = sign(b - a) 2 g / (|b - a| + sqrt((b - a)^2 +
@@ -375,109 +363,6 @@ __device__ __forceinline__ void jac_rotation(T a, T b, T g, T& cs, T& sn, T& t) 
     cs = rsqrt_t(fma(t, t, T(1)));
     sn = cs * t;
 }
-
-template <typename T>
-__global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
-    jacobi_rows_kernel(const JacobiDescT<T>* __restrict__ descs, int max_sweeps, T tol, int* __restrict__ sweeps,
-                       unsigned long long* __restrict__ rots, int* __restrict__ err, int report_noconv) {
-    cg::cluster_group cluster = cg::this_cluster();
-    const int mat = blockIdx.x / JAC_CLUSTER;
-    const int crank = (int)cluster.block_rank();
-    const JacobiDescT<T> d = descs[mat];
-    __shared__ int rotated;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wpc = blockDim.x >> 5;
-    const int gw = crank * wpc + warp, nw = JAC_CLUSTER * wpc;
-    const int m = d.rows + (d.rows & 1);
-    const int npairs = m / 2;
-    const int nrounds = m - 1;
-    const T absf = d.absfloor ? *d.absfloor : T(0);
-    int sweep = 0;
-    bool done = false;
-    for (; sweep < max_sweeps; ++sweep) {
-        if (threadIdx.x == 0) rotated = 0;
-        // row norms^2 at the start of the sweep
-        for (int r = gw; r < d.rows; r += nw) {
-            const T* x = d.A + (size_t)r * d.ld;
-            T a = T(0);
-            for (int c = lane; c < d.ncols_dot; c += 32) {
-                const T u = ldcg_t(x + c);
-                a = fma(u, u, a);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) d.nrm2[r] = a;
-        }
-        __threadfence();
-        cluster.sync();
-        for (int r = 0; r < nrounds; ++r) {
-            for (int k = gw; k < npairs; k += nw) {
-                int p, q;
-                if (k == 0) {
-                    p = m - 1;
-                    q = r;
-                } else {
-                    p = (r + k) % (m - 1);
-                    q = (r - k + (m - 1)) % (m - 1);
-                }
-                if (p >= d.rows || q >= d.rows) continue;
-                T* xp = d.A + (size_t)p * d.ld;
-                T* xq = d.A + (size_t)q * d.ld;
-                T g0 = T(0), g1 = T(0);
-                int c = lane;
-                for (; c + 32 < d.ncols_dot; c += 64) {
-                    g0 = fma(ldcg_t(xp + c), ldcg_t(xq + c), g0);
-                    g1 = fma(ldcg_t(xp + c + 32), ldcg_t(xq + c + 32), g1);
-                }
-                if (c < d.ncols_dot) g0 = fma(ldcg_t(xp + c), ldcg_t(xq + c), g0);
-                T g = g0 + g1;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-                const T a = ldcg_t(d.nrm2 + p), b = ldcg_t(d.nrm2 + q);
-                if (g != T(0) && g * g > tol * tol * a * b && fabs(g) > absf) {
-                    T cs, sn, t;
-                    jac_rotation(a, b, g, cs, sn, t);
-                    for (int c = lane; c < d.ncols_rot; c += 32) {
-                        const T u = ldcg_t(xp + c), v = ldcg_t(xq + c);
-                        xp[c] = fma(cs, u, -sn * v);
-                        xq[c] = fma(sn, u, cs * v);
-                    }
-                    if (lane == 0) {
-                        d.nrm2[p] = fma(-t, g, a);
-                        d.nrm2[q] = fma(t, g, b);
-                        rotated = 1;
-                        atomicAdd(rots + mat, 1ull);
-                    }
-                }
-            }
-            __threadfence();
-            cluster.sync();
-        }
-        int any = 0;
-#pragma unroll
-        for (int rr = 0; rr < JAC_CLUSTER; ++rr) any |= *cluster.map_shared_rank(&rotated, rr);
-        cluster.sync();
-        if (!any) {
-            done = true;
-            break;
-        }
-    }
-    if (crank == 0 && threadIdx.x == 0) {
-        sweeps[mat] = done ? sweep + 1 : sweep;
-        if (!done && report_noconv) atomicOr(err, DERR_EIG_NOCONV);
-    }
-}
-
-template <typename T>
-void launch_jacobi_t(const JacobiDescT<T>* d, int nmat, int max_sweeps, T tol, int* sweeps, unsigned long long* rots,
-                     int* err, int report_noconv, cudaStream_t s) {
-    if (nmat > 0)
-        jacobi_rows_kernel<T><<<nmat * JAC_CLUSTER, 256, 0, s>>>(d, max_sweeps, tol, sweeps, rots, err, report_noconv);
-}
-template void launch_jacobi_t<float>(const JacobiDescT<float>*, int, int, float, int*, unsigned long long*, int*, int,
-                                     cudaStream_t);
-template void launch_jacobi_t<double>(const JacobiDescT<double>*, int, int, double, int*, unsigned long long*, int*,
-                                      int, cudaStream_t);
 
 // ------------------------------------------------------------------ block-pair Jacobi
 // The same one-sided Jacobi for matrices whose rows do not fit in shared
@@ -534,7 +419,7 @@ __device__ __forceinline__ void jp_load4(const double* p, double* v) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) jacobi_pair_kernel(const JacobiDescT<T>* __restrict__ descs,
+__global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* __restrict__ descs,
                                                           const int4* __restrict__ tasks, int round, T tol,
                                                           int* __restrict__ rotated,
                                                           unsigned long long* __restrict__ rots,

@@ -149,17 +149,22 @@ __global__ void __launch_bounds__(32) sparse_local_solve_kernel(const SparseLoca
     const bool act = vec < nb;
     T* xv = x + (size_t)(act ? vec : 0) * n;
     __syncwarp();
+    // forward: column j reads x_j (final once the earlier columns are done) and
+    // updates rows > j only, so x_j itself is scaled by 1 / l_jj in one pass
+    // after the loop
     for (int j = 0; j < n; ++j) {
         const int b = cp[j], e = cp[j + 1];
-        const T dinv = v[b];
         if (act) {
-            const T wj = xv[j] * dinv;
+            const T wj = xv[j] * v[b];
             for (int k = b + 1 + sub; k < e; k += gs) xv[rw[k]] = fma(-v[k], wj, xv[rw[k]]);
         }
         __syncwarp();
-        if (act && sub == 0) xv[j] *= dinv;
-        __syncwarp();
     }
+    for (int e = lane; e < nb * n; e += 32) {
+        const int a = e % n;
+        x[e] *= v[cp[a]];
+    }
+    __syncwarp();
     for (int j = n - 1; j >= 0; --j) {
         const int b = cp[j], e = cp[j + 1];
         T sum = T(0);
@@ -176,12 +181,12 @@ __global__ void __launch_bounds__(32) sparse_local_solve_kernel(const SparseLoca
 }
 
 template <typename T>
-size_t sparse_local_smem(int n, int nnz) {
-    return (size_t)((size_t)MAXB * n + nnz) * sizeof(T) + (size_t)(n + 1) * sizeof(int32_t) +
+size_t sparse_local_smem(int n, int nnz, int nb) {
+    return (size_t)((size_t)nb * n + nnz) * sizeof(T) + (size_t)(n + 1) * sizeof(int32_t) +
            (size_t)nnz * sizeof(uint16_t) + 16;
 }
-template size_t sparse_local_smem<float>(int, int);
-template size_t sparse_local_smem<double>(int, int);
+template size_t sparse_local_smem<float>(int, int, int);
+template size_t sparse_local_smem<double>(int, int, int);
 
 template <typename T>
 void launch_sparse_local_solve(const SparseLocalDesc* d, int nmat, size_t smem, const int32_t* colptr,
