@@ -139,10 +139,11 @@ typedef struct {
                              AMDD_ERR_OOM before it is made (amdd_info.device_bytes_peak reports
                              what a setup used); 0 (default): no limit                             */
     int32_t tensor_cores; /* 1: FP32 batched GEMMs of at least 16 output tiles of 128 x 128 (the
-                             mixed form's local products) run on the tcgen05 tensor cores in TF32
+                             mixed form's local products), and the Gram matrices and rotations of
+                             the FP32 block-pair Jacobi, run on the tcgen05 tensor cores in TF32
                              with the 3xTF32 split (hi*hi + hi*lo + lo*hi, FP32 accumulation), whose
                              error is of the order of an FP32 multiply-add loop's; 0: CUDA-core FMA;
-                             default 0                                                              */
+                             default 1                                                              */
     int32_t local_solver; /* local solves of the Schwarz methods (Sec. 4.1: exact local Cholesky):
                              0: the explicit inverse factors L_i^{-1}, L_i^{-T} (dense triangles);
                              1: sparse Cholesky factors in a nested-dissection order (the same exact
@@ -151,6 +152,12 @@ typedef struct {
                              memory; AMDD_ERR_INVALID if a factor does not fit (about 200 KB);
                              2: 1 where every factor fits and holds at most a quarter of its dense
                              triangle, else 0; default 0                                           */
+    int32_t jacobi_inner_sweeps; /* block-pair Jacobi (matrices whose rows exceed shared memory):
+                             at most this many sweeps of the 64 x 64 eigensolve per visit of a
+                             block pair (the outer sweeps repeat until every pair passes the
+                             stopping test, so the result meets the same test); 0 (default): 1
+                             (one inner sweep, measured fastest: the outer sweep count did not
+                             grow); AMDD_ERR_INVALID above 64                                      */
 } amdd_opts;
 
 typedef struct {

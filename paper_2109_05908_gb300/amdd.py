@@ -33,7 +33,8 @@ class amdd_opts(C.Structure):
                 ("keep_proposal_data", C.c_int32), ("proposal", C.POINTER(amdd_proposal)),
                 ("keep_coarse_matrix", C.c_int32), ("reserved", C.c_int32), ("tie_band", C.c_double),
                 ("use_graphs", C.c_int32), ("autotune", C.c_int32), ("mem_budget", C.c_size_t),
-                ("tensor_cores", C.c_int32), ("local_solver", C.c_int32)]
+                ("tensor_cores", C.c_int32), ("local_solver", C.c_int32),
+                ("jacobi_inner_sweeps", C.c_int32)]
 
 
 MLP_NPARAM = 140032

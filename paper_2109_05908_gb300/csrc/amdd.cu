@@ -266,6 +266,7 @@ struct amdd_handle {
     // sparse local Cholesky factors (amdd_opts.local_solver): columns of each
     // factor in a nested-dissection order, used by the local solves when kept
     int local_solver = 0;
+    int jacobi_inner = 1;  // inner sweeps per block-pair visit
     bool sparse_local = false;
     void* d_sl_val = nullptr;  // FP64 or FP32 as the local solves
     uint16_t* d_sl_row = nullptr;
@@ -759,7 +760,8 @@ void transpose_batched(Ctx& C, const std::vector<const T*>& src, const std::vect
 
 // Block-pair one-sided Jacobi (rows in global memory): the host runs the
 // rounds of each sweep, one launch per round over every matrix still
-// rotating, and drops a matrix after a sweep in which none of its block pairs
+// rotating (in FP32 with amdd_opts.tensor_cores, the kernel whose Gram
+// matrices and rotations run on the tensor cores), and drops a matrix after a sweep in which none of its block pairs
 // needed a rotation (sweeps[m] then counts that sweep, as the row kernels
 // do).  A matrix still rotating after max_sweeps keeps sweeps[m] = max_sweeps
 // and, with report_noconv, latches DERR_EIG_NOCONV.
@@ -791,8 +793,16 @@ void jacobi_pairs(Ctx& C, const std::vector<JacobiDescT<T>>& jd, const JacobiDes
         }
         const int4* dt = C.up(tasks);
         ck(cudaMemsetAsync(d_rot, 0, nm * sizeof(int), h->s));
-        for (int r = 0; r < maxb - 1; ++r)
-            launch_jacobi_pair_round<T>(djd, dt, (int)tasks.size(), r, tol, d_rot, rots, d_st, h->s);
+        for (int r = 0; r < maxb - 1; ++r) {
+            if constexpr (std::is_same<T, float>::value) {
+                if (h->tensor_cores) {
+                    launch_jacobi_pair_tc_round(djd, dt, (int)tasks.size(), r, tol, h->jacobi_inner, d_rot, rots, d_st,
+                                                h->d_err, h->s);
+                    continue;
+                }
+            }
+            launch_jacobi_pair_round<T>(djd, dt, (int)tasks.size(), r, tol, h->jacobi_inner, d_rot, rots, d_st, h->s);
+        }
         ck(cudaGetLastError());
         ck(cudaMemcpyAsync(rot_h.data(), d_rot, nm * sizeof(int), cudaMemcpyDeviceToHost, h->s));
         ck(cudaStreamSynchronize(h->s));
@@ -4194,6 +4204,7 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
             return AMDD_ERR_INVALID;
         if (o.tensor_cores < 0 || o.tensor_cores > 1) return AMDD_ERR_INVALID;
         if (o.local_solver < 0 || o.local_solver > 2) return AMDD_ERR_INVALID;
+        if (o.jacobi_inner_sweeps < 0 || o.jacobi_inner_sweeps > 64) return AMDD_ERR_INVALID;
         if (o.profile_classes >> PK_COUNT) return AMDD_ERR_INVALID;
         if (o.eig_solver < 0 || o.eig_solver > 3) return AMDD_ERR_INVALID;
         // the matrix-free eigensolve: FP64 only, with the shift far enough above
@@ -4235,6 +4246,7 @@ amdd_status amdd_setup(const amdd_csr* A, const int32_t* part, int32_t N, int32_
         h->autotune = o.autotune;
         h->tensor_cores = o.tensor_cores;
         h->local_solver = o.local_solver;
+        h->jacobi_inner = o.jacobi_inner_sweeps ? o.jacobi_inner_sweeps : 1;
         if (o.eig_solver == 2) {
             h->prop = *o.proposal;
             h->have_prop = true;

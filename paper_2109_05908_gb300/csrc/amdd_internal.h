@@ -147,13 +147,20 @@ constexpr int JP_ROWS = 32;
 template <typename T>
 size_t jacobi_pair_smem();
 template <typename T>
-void launch_jacobi_pair_round(const JacobiDescT<T>* d, const int4* tasks, int ntasks, int round, T tol, int* rotated,
-                              unsigned long long* rots, unsigned long long* stats, cudaStream_t s);
+void launch_jacobi_pair_round(const JacobiDescT<T>* d, const int4* tasks, int ntasks, int round, T tol, int inner,
+                              int* rotated, unsigned long long* rots, unsigned long long* stats, cudaStream_t s);
 // Batched FP32 GEMM on the tensor cores (tcgen05, TF32 with the 3xTF32 split
 // for FP32 accuracy), 128 x 128 output tiles (TileRef tm, tn in units of 128);
 // a wait that gives up latches DERR_TIMEOUT in *err.
 constexpr int TC_GEMM_TILE = 128;
 size_t gemm_tc_smem();
+// one round of the block-pair Jacobi in FP32 with the Gram matrices and the
+// rotations on the tensor cores (3xTF32); DERR_TIMEOUT into *err when a wait
+// on the tensor core gives up
+size_t jacobi_pair_tc_smem();
+void launch_jacobi_pair_tc_round(const JacobiDescT<float>* d, const int4* tasks, int ntasks, int round, float tol,
+                                 int inner, int* rotated, unsigned long long* rots, unsigned long long* stats, int* err,
+                                 cudaStream_t s);
 void launch_gemm_tc(const GemmDescT<float>* d_descs, const TileRef* d_tiles, int ntiles, int* err, cudaStream_t s);
 // *p |= bits (one thread)
 void launch_or_flag(int* p, int bits, cudaStream_t s);

@@ -8,6 +8,7 @@
 #include <cooperative_groups.h>
 
 #include "amdd_internal.h"
+#include "jacobi_pair_inner.cuh"
 
 #include <limits>
 
@@ -389,15 +390,17 @@ __device__ __forceinline__ void jac_rotation(T a, T b, T g, T& cs, T& sn, T& t) 
 constexpr int JP_B = 32;
 constexpr int JP_R = 2 * JP_B;
 constexpr int JP_KC = 32;             // columns per streamed chunk
-constexpr int JP_LDG = JP_R + 1;      // G and Qt, row-major
 constexpr int JP_LDT = JP_R + 4;      // Gram chunk, [column][row] (16-byte aligned rows)
 constexpr int JP_LDA = JP_KC + 4;     // apply chunk, [row][column]
-constexpr int JP_INNER = 20;          // inner sweep limit
+static_assert(JP_R == JPI_N, "the inner eigensolve is written for 64 x 64 Gram matrices");
+static_assert((size_t)JP_KC * JP_LDT <= (size_t)JP_R * JPI_LDG && (size_t)JP_R * JP_LDA <= (size_t)JP_R * JPI_LDG,
+              "the streamed chunks share the second Gram buffer");
 
+// G0, G1 (the inner eigensolve's two Gram buffers; the streamed chunks of the
+// Gram matrix and of the rotation reuse G1) and Qt
 template <typename T>
 size_t jacobi_pair_smem() {
-    const size_t chunk = (size_t)JP_KC * JP_LDT > (size_t)JP_R * JP_LDA ? (size_t)JP_KC * JP_LDT : (size_t)JP_R * JP_LDA;
-    return (2 * (size_t)JP_R * JP_LDG + chunk) * sizeof(T) + 64;
+    return (2 * (size_t)JP_R * JPI_LDG + (size_t)JP_R * JPI_LDQ) * sizeof(T) + 64;
 }
 template size_t jacobi_pair_smem<float>();
 template size_t jacobi_pair_smem<double>();
@@ -421,16 +424,15 @@ __device__ __forceinline__ void jp_load4(const double* p, double* v) {
 template <typename T>
 __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* __restrict__ descs,
                                                           const int4* __restrict__ tasks, int round, T tol,
-                                                          int* __restrict__ rotated,
+                                                          int inner_max, int* __restrict__ rotated,
                                                           unsigned long long* __restrict__ rots,
                                                           unsigned long long* __restrict__ stats) {
     extern __shared__ __align__(16) unsigned char jp_raw[];
     T* G = reinterpret_cast<T*>(jp_raw);
-    T* Qt = G + JP_R * JP_LDG;
-    T* Yc = Qt + JP_R * JP_LDG;
-    // rotation of each of the JP_R / 2 disjoint pairs of an inner round
-    __shared__ T r_cs[JP_R / 2], r_sn[JP_R / 2], r_a[JP_R / 2], r_b[JP_R / 2];
-    __shared__ int r_p[JP_R / 2], r_q[JP_R / 2], r_do[JP_R / 2];
+    T* G1 = G + JP_R * JPI_LDG;
+    T* Qt = G1 + JP_R * JPI_LDG;
+    T* Yc = G1;  // streamed chunks (the inner eigensolve's second buffer is free then)
+    __shared__ JpRound<T> jr[2];
     const int4 tk = tasks[blockIdx.x];
     const int mat = tk.x, kp = tk.y, nblk = tk.z;
     if (round >= nblk - 1) return;  // uniform over the CTA
@@ -497,17 +499,17 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) G[(4 * ty + i) * JP_LDG + 4 * tx + j] = acc[i][j];
-        for (int e = tid; e < JP_R * JP_R; e += 256) Qt[(e / JP_R) * JP_LDG + e % JP_R] = (e / JP_R == e % JP_R) ? T(1) : T(0);
+            for (int j = 0; j < 4; ++j) G[(4 * ty + i) * JPI_LDG + 4 * tx + j] = acc[i][j];
+        for (int e = tid; e < JP_R * JP_R; e += 256) Qt[(e / JP_R) * JPI_LDQ + e % JP_R] = (e / JP_R == e % JP_R) ? T(1) : T(0);
         __syncthreads();
     }
 
     // ---- 2. two-sided cyclic Jacobi on G, rotations accumulated in Qt.  The
     // stopping test of the sweep (tol) on the fresh Gram matrix decides
-    // whether the pair is rotated at all; once it is, the pair is
-    // orthogonalised to a tighter inner test (tin, still well above the
-    // rounding of G), so that one visit leaves it converged and the outer
-    // sweeps do not revisit rounding-level couplings.
+    // whether the pair is rotated at all; once it is, up to inner_max inner
+    // sweeps rotate couplings above a tighter inner test (tin, still well
+    // above the rounding of G).  Whatever a visit leaves is met again by the
+    // outer sweeps' test on fresh Gram matrices.
     const T ueps = sizeof(T) == 4 ? T(1.1920928955078125e-7) : T(2.220446049250313e-16);
     const T tin = fmax(tol * T(1.0 / 64.0), T(16) * ueps);
     const long long t1 = clock64();
@@ -520,94 +522,20 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
         for (int e = tid; e < JP_R * JP_R; e += 256) {
             const int p = e / JP_R, q = e % JP_R;
             if (q <= p) continue;
-            const T a = G[p * JP_LDG + p], b = G[q * JP_LDG + q], g = G[p * JP_LDG + q];
+            const T a = G[p * JPI_LDG + p], b = G[q * JPI_LDG + q], g = G[p * JPI_LDG + q];
             if (g != T(0) && g * g > tol * tol * a * b && fabs(g) > absf) mine = 1;
         }
         if (!__syncthreads_or(mine)) return;  // the pair met the stopping test: rows unchanged
     }
     unsigned nrot = 0;
-    for (int sw = 0; sw < JP_INNER; ++sw) {
-        int rot_mine = 0;
-        for (int rr = 0; rr < JP_R - 1; ++rr) {
-            // the rotations of the round's JP_R / 2 disjoint pairs (identity where none)
-            if (tid < JP_R / 2) {
-                int p, q;
-                if (tid == 0) {
-                    p = JP_R - 1;
-                    q = rr;
-                } else {
-                    p = (rr + tid) % (JP_R - 1);
-                    q = (rr - tid + JP_R - 1) % (JP_R - 1);
-                }
-                const T a = G[p * JP_LDG + p], b = G[q * JP_LDG + q], g = G[p * JP_LDG + q];
-                // after the first inner sweep, G's off-diagonal entries carry the rounding
-                // of earlier rotations, of the order of u max(a, b): couplings below that
-                // floor are left to the next outer sweep's fresh Gram matrix
-                const bool doit = g != T(0) && g * g > tin * tin * a * b && fabs(g) > absf &&
-                                  (sw == 0 || fabs(g) > T(8) * ueps * fmax(a, b));
-                r_p[tid] = p;
-                r_q[tid] = q;
-                r_do[tid] = doit ? 1 : 0;
-                r_cs[tid] = T(1);
-                r_sn[tid] = T(0);
-                if (doit) {
-                    T cs, sn, t;
-                    jac_rotation(a, b, g, cs, sn, t);
-                    r_cs[tid] = cs;
-                    r_sn[tid] = sn;
-                    r_a[tid] = fma(-t, g, a);
-                    r_b[tid] = fma(t, g, b);
-                    rot_mine = 1;
-                    ++nrot;
-                }
-            }
-            __syncthreads();
-            // G <- R G R^T by 2 x 2 blocks: rows {p, q} of pair P times columns
-            // {p', q'} of pair Q go to R_P B R_Q^T (each entry of G is in exactly one
-            // block); a rotated diagonal block becomes diag(a - t g, b + t g) exactly
-            for (int e = tid; e < (JP_R / 2) * (JP_R / 2); e += 256) {
-                const int P = e / (JP_R / 2), Q = e % (JP_R / 2);
-                if (!r_do[P] && !r_do[Q]) continue;
-                const int p = r_p[P], q = r_q[P];
-                if (P == Q) {
-                    G[p * JP_LDG + p] = r_a[P];
-                    G[q * JP_LDG + q] = r_b[P];
-                    G[p * JP_LDG + q] = T(0);
-                    G[q * JP_LDG + p] = T(0);
-                    continue;
-                }
-                const int p2 = r_p[Q], q2 = r_q[Q];
-                const T c1 = r_cs[P], s1 = r_sn[P], c2 = r_cs[Q], s2 = r_sn[Q];
-                const T b00 = G[p * JP_LDG + p2], b01 = G[p * JP_LDG + q2];
-                const T b10 = G[q * JP_LDG + p2], b11 = G[q * JP_LDG + q2];
-                const T u00 = fma(c1, b00, -s1 * b10), u01 = fma(c1, b01, -s1 * b11);
-                const T u10 = fma(s1, b00, c1 * b10), u11 = fma(s1, b01, c1 * b11);
-                G[p * JP_LDG + p2] = fma(c2, u00, -s2 * u01);
-                G[p * JP_LDG + q2] = fma(s2, u00, c2 * u01);
-                G[q * JP_LDG + p2] = fma(c2, u10, -s2 * u11);
-                G[q * JP_LDG + q2] = fma(s2, u10, c2 * u11);
-            }
-            // rows p, q of Qt
-            for (int e = tid; e < (JP_R / 2) * JP_R; e += 256) {
-                const int k = e / JP_R, c = e % JP_R;
-                if (!r_do[k]) continue;
-                const int p = r_p[k], q = r_q[k];
-                const T cs = r_cs[k], sn = r_sn[k];
-                const T u = Qt[p * JP_LDG + c], v = Qt[q * JP_LDG + c];
-                Qt[p * JP_LDG + c] = fma(cs, u, -sn * v);
-                Qt[q * JP_LDG + c] = fma(sn, u, cs * v);
-            }
-            __syncthreads();
-        }
-        if (tid == 0) atomicAdd(stats + 5, 1ull);
-        if (!__syncthreads_or(rot_mine)) break;
-    }
+    const int inner = jpi_solve<T>(G, G1, Qt, jr, tin, absf, inner_max, nrot);
     if (nrot) atomicAdd(rots + mat, (unsigned long long)nrot);
     const long long t2 = clock64();
     if (tid == 0) {
         rotated[mat] = 1;
         atomicAdd(stats + 1, 1ull);
         atomicAdd(stats + 3, (unsigned long long)(t2 - t1));
+        atomicAdd(stats + 5, (unsigned long long)inner);
     }
 
     // ---- 3. Y <- Qt Y over ncols_rot columns
@@ -636,7 +564,7 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
             T o0[4] = {T(0), T(0), T(0), T(0)}, o1[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll 4
             for (int k = 0; k < JP_R; ++k) {
-                const T q0 = Qt[(2 * ty) * JP_LDG + k], q1 = Qt[(2 * ty + 1) * JP_LDG + k];
+                const T q0 = Qt[(2 * ty) * JPI_LDQ + k], q1 = Qt[(2 * ty + 1) * JPI_LDQ + k];
                 T y[4];
                 jp_load4(Yc + k * JP_LDA + 4 * tx, y);
 #pragma unroll
@@ -660,16 +588,16 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(const JacobiDescT<T>* 
 }
 
 template <typename T>
-void launch_jacobi_pair_round(const JacobiDescT<T>* d, const int4* tasks, int ntasks, int round, T tol, int* rotated,
-                              unsigned long long* rots, unsigned long long* stats, cudaStream_t s) {
+void launch_jacobi_pair_round(const JacobiDescT<T>* d, const int4* tasks, int ntasks, int round, T tol, int inner,
+                              int* rotated, unsigned long long* rots, unsigned long long* stats, cudaStream_t s) {
     if (ntasks <= 0) return;
     const size_t smem = jacobi_pair_smem<T>();
     cudaFuncSetAttribute(jacobi_pair_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    jacobi_pair_kernel<T><<<ntasks, 256, smem, s>>>(d, tasks, round, tol, rotated, rots, stats);
+    jacobi_pair_kernel<T><<<ntasks, 256, smem, s>>>(d, tasks, round, tol, inner, rotated, rots, stats);
 }
-template void launch_jacobi_pair_round<float>(const JacobiDescT<float>*, const int4*, int, int, float, int*,
+template void launch_jacobi_pair_round<float>(const JacobiDescT<float>*, const int4*, int, int, float, int, int*,
                                               unsigned long long*, unsigned long long*, cudaStream_t);
-template void launch_jacobi_pair_round<double>(const JacobiDescT<double>*, const int4*, int, int, double, int*,
+template void launch_jacobi_pair_round<double>(const JacobiDescT<double>*, const int4*, int, int, double, int, int*,
                                                unsigned long long*, unsigned long long*, cudaStream_t);
 
 __global__ void or_flag_kernel(int* p, int bits) { atomicOr(p, bits); }

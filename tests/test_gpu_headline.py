@@ -8,8 +8,13 @@ one subdomain at a time, and a closed form that holds at this tau:
   * sampled subdomains (three, seeded): singular values of X_i, eigenvalues of
     eq. (Zi) as mu = 1/lambda and the selection p_i, against the oracle's local
     steps (Sec. 2.1 sets, eq. (Xi), Sec. 3.2 splitting, eq. (Zi)) in FP64.  The
-    bars take the oracle's own FP64 envelope on the subdomain (one seeded
-    relabelling of its sets);
+    bars take the oracle's own FP64 envelope on the subdomain: the spread of
+    its results under one seeded relabelling of the sets and, for mu, also
+    under a normwise backward perturbation of X_i of size sqrt(n_i) u sigma_1.
+    That is the probabilistic rounding bound of the length-n_i products by
+    which the FP64 splitting rotates X_i. The Schur complement onto Omega_Ii
+    amplifies such perturbations through the shifted Abar_RR (Sec. 3.2), so
+    mu carries far more than u of them;
   * with tau = 100 every eigenvalue of eq. (Zi) is selected in FP64 (n_C = n),
     so R_0^T E^{-1} R_0 = A^{-1} for any basis, and one apply is
         z = A^{-1} r + sum_i R_i^T A_ii^{-1} R_i r,
@@ -97,6 +102,11 @@ def test_headline_sampled_subdomains(headline):
         assert np.all(np.abs(sg - so) <= 1e-10 * so + 20 * eta_s), f"sigma, subdomain {i}"
         mo = _mu(lam)
         eta_m = np.abs(_mu(lam2) - mo).max()
+        n, nt = X.shape
+        E = rng.standard_normal((n, nt)) * (np.sqrt(n) * 2.0**-53 * so[0] / (np.sqrt(n) + np.sqrt(nt)))
+        Abar3, _ = O.splitting_root(X + E, O.EPS)
+        lam3, _, _ = O.local_eigenproblem(Aii, Abar3, len(I), w["tau"])
+        eta_m = max(eta_m, np.abs(_mu(lam3) - mo).max())
         mg = _mu(A.get_eigenvalues(Pp.h, int(i)))
         worst = np.max(np.abs(mg - mo) / (1e-8 * mo + 20 * eta_m + 1e-300))
         assert worst <= 1.0, f"mu, subdomain {i}: {worst:.2f}"
