@@ -847,6 +847,16 @@ def run_amdd(args):
                             "note": "each arm's ms is setup + PCG device-timed per step; setup_ms and solve_ms are "
                                     "the wall times of the amdd_setup and amdd_pcg_solve calls (each synchronises)"},
                    "pcg_graphs": graphs,
+                   "svd_jacobi": {"sweeps_max": info.sweeps_svd, "pair_visits": int(info.pair_stats[0]),
+                                  "rotating_visits": int(info.pair_stats[1]),
+                                  "cta_cycles": {"gram": int(info.pair_stats[2]), "inner": int(info.pair_stats[3]),
+                                                 "rotation": int(info.pair_stats[4])},
+                                  "inner_sweeps": int(info.pair_stats[5]),
+                                  "flag_wait_cycles": int(info.pair_stats[6]),
+                                  "cta_lifetime_cycles": int(info.pair_stats[7]),
+                                  "ctas_with_work": int(info.pair_stats[8]),
+                                  "ctas_launched": int(info.pair_stats[9]),
+                                  "note": "block-pair one-sided Jacobi of the X_i, last timed mixed step"},
                    "device_bytes_peak": info.device_bytes_peak,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -890,6 +900,8 @@ def main():
     ap.add_argument("--impl", default="amdd", choices=["amdd", "reference"])
     ap.add_argument("--no-scale", action="store_true",
                     help="skip the SpMV / apply bandwidth measurement on the 1M-unknown problem")
+    ap.add_argument("--only-scale", action="store_true",
+                    help="run only the 1M-unknown SpMV / apply measurement and print it")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the deflated GMRES and three-level variant timings")
     ap.add_argument("--scale-m", type=int, default=None,
@@ -911,7 +923,24 @@ def main():
             WORKLOAD_3D[key] = getattr(args, key)
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_scale:
+        return run_scale_only(args)
     return run_amdd(args)
+
+
+def run_scale_only(args):
+    """The 1M-unknown SpMV / apply measurement alone (a small command for
+    profiling its kernels)."""
+    import numpy as np
+    import torch
+
+    from paper_2109_05908_gb300 import amdd as A
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sp = torch.cuda.current_stream(dev).cuda_stream
+    peaks, _ = _peaks()
+    print(json.dumps(apply_at_scale(A, torch, np, dev, sp, peaks["hbm_gbs"], m=args.scale_m)), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -215,10 +215,14 @@ typedef struct {
     int64_t tuned_buckets;     /* GEMM size buckets measured by the autotuner in this process */
     int64_t sparse_local_nnz;  /* entries of the sparse local factors in use (0: dense inverse
                                   factors, see amdd_opts.local_solver)                      */
-    int64_t pair_stats[6];     /* block-pair one-sided Jacobi (matrices whose rows exceed shared
+    int64_t pair_stats[10];     /* block-pair one-sided Jacobi (matrices whose rows exceed shared
                                   memory): pair tasks run, pairs rotated, SM clock cycles
                                   summed over CTAs of its three phases (Gram matrices, small
-                                  eigensolves, rotation of the rows), inner sweeps            */
+                                  eigensolves, rotation of the rows), inner sweeps; with the
+                                  tensor-core sweep kernel also the cycles spent waiting for
+                                  the previous round of a pair's row blocks, the summed
+                                  lifetimes of its CTAs (cycles), the CTAs that ran at least one
+                                  pair, and the CTAs launched                                  */
 } amdd_info;
 
 /* Symbolic phase of a sparse local Cholesky factorisation, on the host (no

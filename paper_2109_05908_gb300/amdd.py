@@ -61,7 +61,7 @@ class amdd_info(C.Structure):
                 ("inner_solves", C.c_int64), ("inner_iterations", C.c_int64), ("n_tied", C.c_int32),
                 ("n_below_one", C.c_int32), ("device_bytes_peak", C.c_int64), ("graph_solves", C.c_int64),
                 ("tuned_buckets", C.c_int64), ("sparse_local_nnz", C.c_int64),
-                ("pair_stats", C.c_int64 * 6)]
+                ("pair_stats", C.c_int64 * 10)]
 
 
 class AmddError(RuntimeError):

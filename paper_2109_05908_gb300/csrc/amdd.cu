@@ -259,7 +259,7 @@ struct amdd_handle {
     double tie_band = 1e-10;
     int n_tied = 0;  // eigenvalues with |lambda tau - 1| <= tie_band
     int n_below_one = 0;  // computed eigenvalues below 1 (the shift of the splitting)
-    int64_t pair_stats[6] = {0, 0, 0, 0, 0, 0};  // block-pair Jacobi: tasks, rotated, cycles of 3 phases, inner sweeps
+    int64_t pair_stats[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // block-pair Jacobi: tasks, rotated, cycles of 3 phases, inner sweeps
     int use_graphs = 1;
     int autotune = 1;  // GEMM tile autotuner (process-wide table)
     int tensor_cores = 0;  // FP32 GEMMs on tcgen05 (3xTF32)
@@ -759,10 +759,13 @@ void transpose_batched(Ctx& C, const std::vector<const T*>& src, const std::vect
 }
 
 // Block-pair one-sided Jacobi (rows in global memory): the host runs the
-// rounds of each sweep, one launch per round over every matrix still
-// rotating (in FP32 with amdd_opts.tensor_cores, the kernel whose Gram
-// matrices and rotations run on the tensor cores), and drops a matrix after a sweep in which none of its block pairs
-// needed a rotation (sweeps[m] then counts that sweep, as the row kernels
+// sweeps, each either as one launch per round over every matrix still
+// rotating or, in FP32 with amdd_opts.tensor_cores, as one persistent launch
+// of the kernel whose Gram matrices and rotations run on the tensor cores
+// (its CTAs take the pairs in round order and start a pair once both of its
+// row blocks have finished the previous round, so matrices of different
+// sizes and consecutive rounds overlap), and drops a matrix after a sweep in
+// which none of its block pairs needed a rotation (sweeps[m] then counts that sweep, as the row kernels
 // do).  A matrix still rotating after max_sweeps keeps sweeps[m] = max_sweeps
 // and, with report_noconv, latches DERR_EIG_NOCONV.
 template <typename T>
@@ -782,27 +785,46 @@ void jacobi_pairs(Ctx& C, const std::vector<JacobiDescT<T>>& jd, const JacobiDes
     }
     int* d_rot = C.tnew<int>(nm);
     std::vector<int> rot_h(nm);
-    unsigned long long* d_st = C.tnew<unsigned long long>(6);
-    ck(cudaMemsetAsync(d_st, 0, 6 * sizeof(unsigned long long), h->s));
+    unsigned long long* d_st = C.tnew<unsigned long long>(9);
+    ck(cudaMemsetAsync(d_st, 0, 9 * sizeof(unsigned long long), h->s));
+    // FP32 on the tensor cores: one persistent launch per sweep, tasks in round
+    // order, per-block round counters
+    const bool tc_sweep = std::is_same<T, float>::value && h->tensor_cores;
+    std::vector<int> bofs(nm + 1, 0);
+    for (int m = 0; m < nm; ++m) bofs[m + 1] = bofs[m] + nblk[m];
+    const int* d_bofs = tc_sweep ? C.up(bofs) : nullptr;
+    int* d_flags = tc_sweep ? C.tnew<int>(bofs[nm] + 1) : nullptr;  // block counters, then the task counter
     for (int sweep = 0; sweep < max_sweeps && !active.empty(); ++sweep) {
         std::vector<int4> tasks;
         int maxb = 2;
-        for (int m : active) {
-            for (int k = 0; k < nblk[m] / 2; ++k) tasks.push_back(make_int4(m, k, nblk[m], 0));
-            maxb = std::max(maxb, nblk[m]);
+        for (int m : active) maxb = std::max(maxb, nblk[m]);
+        if (tc_sweep) {
+            // within a round the largest matrices first: their chains of rounds are
+            // the longest, the smaller matrices fill in behind them
+            std::vector<int> order(active);
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nblk[a] > nblk[b]; });
+            for (int r = 0; r < maxb - 1; ++r)
+                for (int m : order)
+                    if (r < nblk[m] - 1)
+                        for (int k = 0; k < nblk[m] / 2; ++k) tasks.push_back(make_int4(m, k, nblk[m], r));
+        } else {
+            for (int m : active)
+                for (int k = 0; k < nblk[m] / 2; ++k) tasks.push_back(make_int4(m, k, nblk[m], 0));
         }
         const int4* dt = C.up(tasks);
         ck(cudaMemsetAsync(d_rot, 0, nm * sizeof(int), h->s));
-        for (int r = 0; r < maxb - 1; ++r) {
-            if constexpr (std::is_same<T, float>::value) {
-                if (h->tensor_cores) {
-                    launch_jacobi_pair_tc_round(djd, dt, (int)tasks.size(), r, tol, h->jacobi_inner, d_rot, rots, d_st,
-                                                h->d_err, h->s);
-                    continue;
-                }
+        if constexpr (std::is_same<T, float>::value) {
+            if (tc_sweep) {
+                ck(cudaMemsetAsync(d_flags, 0, (bofs[nm] + 1) * sizeof(int), h->s));
+                h->pair_stats[9] += launch_jacobi_pair_tc_sweep(djd, dt, (int)tasks.size(), d_flags + bofs[nm], d_flags,
+                                                                d_bofs, tol, h->jacobi_inner, d_rot, rots, d_st, h->d_err,
+                                                                h->s);
             }
-            launch_jacobi_pair_round<T>(djd, dt, (int)tasks.size(), r, tol, h->jacobi_inner, d_rot, rots, d_st, h->s);
         }
+        if (!tc_sweep)
+            for (int r = 0; r < maxb - 1; ++r)
+                launch_jacobi_pair_round<T>(djd, dt, (int)tasks.size(), r, tol, h->jacobi_inner, d_rot, rots, d_st,
+                                            h->s);
         ck(cudaGetLastError());
         ck(cudaMemcpyAsync(rot_h.data(), d_rot, nm * sizeof(int), cudaMemcpyDeviceToHost, h->s));
         ck(cudaStreamSynchronize(h->s));
@@ -817,10 +839,10 @@ void jacobi_pairs(Ctx& C, const std::vector<JacobiDescT<T>>& jd, const JacobiDes
     }
     C.keep.push_back(sw);
     ck(cudaMemcpyAsync(sweeps, sw->data(), nm * sizeof(int), cudaMemcpyHostToDevice, h->s));
-    unsigned long long st[6];
+    unsigned long long st[9];
     ck(cudaMemcpyAsync(st, d_st, sizeof(st), cudaMemcpyDeviceToHost, h->s));
     ck(cudaStreamSynchronize(h->s));
-    for (int k = 0; k < 6; ++k) h->pair_stats[k] += (int64_t)st[k];
+    for (int k = 0; k < 9; ++k) h->pair_stats[k] += (int64_t)st[k];
     if (!active.empty() && report_noconv) launch_or_flag(h->d_err, DERR_EIG_NOCONV, h->s);
 }
 
@@ -4814,7 +4836,7 @@ amdd_status amdd_get_info(const amdd_handle* h, amdd_info* info) {
     info->inner_iterations = h->in_its;
     info->n_tied = h->n_tied;
     info->n_below_one = h->n_below_one;
-    for (int k = 0; k < 6; ++k) info->pair_stats[k] = h->pair_stats[k];
+    for (int k = 0; k < 10; ++k) info->pair_stats[k] = h->pair_stats[k];
     info->device_bytes_peak = (int64_t)h->bytes_peak;
     info->graph_solves = h->graph_solves;
     info->sparse_local_nnz = h->sparse_local ? h->sl_nnz : 0;

@@ -154,13 +154,18 @@ void launch_jacobi_pair_round(const JacobiDescT<T>* d, const int4* tasks, int nt
 // a wait that gives up latches DERR_TIMEOUT in *err.
 constexpr int TC_GEMM_TILE = 128;
 size_t gemm_tc_smem();
-// one round of the block-pair Jacobi in FP32 with the Gram matrices and the
-// rotations on the tensor cores (3xTF32); DERR_TIMEOUT into *err when a wait
-// on the tensor core gives up
+// one sweep of the block-pair Jacobi in FP32 with the Gram matrices and the
+// rotations on the tensor cores (3xTF32), as one persistent launch: tasks[t] =
+// {matrix, pair index in its round, blocks of that matrix, round}, ordered by
+// round; CTAs claim tasks through *counter (zero before the launch) and wait
+// (bounded) until bdone[bofs[matrix] + block] (zero before the launch) shows
+// that both row blocks of the pair have finished the previous round; results
+// are those of the round-by-round launches.  DERR_TIMEOUT into *err when a
+// wait gives up.  Returns the CTAs launched.
 size_t jacobi_pair_tc_smem();
-void launch_jacobi_pair_tc_round(const JacobiDescT<float>* d, const int4* tasks, int ntasks, int round, float tol,
-                                 int inner, int* rotated, unsigned long long* rots, unsigned long long* stats, int* err,
-                                 cudaStream_t s);
+int launch_jacobi_pair_tc_sweep(const JacobiDescT<float>* d, const int4* tasks, int ntasks, int* counter, int* bdone,
+                                 const int* bofs, float tol, int inner, int* rotated, unsigned long long* rots,
+                                 unsigned long long* stats, int* err, cudaStream_t s);
 void launch_gemm_tc(const GemmDescT<float>* d_descs, const TileRef* d_tiles, int ntiles, int* err, cudaStream_t s);
 // *p |= bits (one thread)
 void launch_or_flag(int* p, int bits, cudaStream_t s);

@@ -1307,9 +1307,244 @@ __global__ void __cluster_dims__(JAC_CLUSTER, 1, 1) __launch_bounds__(256)
     }
 }
 
+// The same reduction with the matrix held in distributed shared memory: a
+// cluster of TD_CL CTAs per matrix, CTA c keeping the lower-triangle part
+// (columns 0..r) of the rows r = c mod TD_CL, packed row after row.  Per step
+// k (m = n - k - 1 trailing rows):
+//   A. the owned entries of column k go to colk and their squares to a partial
+//      sum; the owner of row k writes d[k];                 (cluster barrier 1)
+//   B. the norm, alpha and beta from the TD_CL partials in rank order; v
+//      gathered from the owners' colk; for every owned row r (one warp) the
+//      row part sum_{j <= r} A_rj v_j of (A22 v)_r and, for j < r, the column
+//      part A_rj v_r, accumulated per warp (in row order) and then summed over
+//      the warps into pcs;                                  (cluster barrier 2)
+//   C. p_r = beta (row part + the TD_CL column parts of r in rank order) for
+//      the owned rows, and a partial sum of p^T v;          (cluster barrier 3)
+//   D. K = beta/2 p^T v, w = p - K v gathered from the owners, and the rank-2
+//      update A_rj -= v_r w_j + w_r v_j of the owned rows.
+// colk, pcs, pv and the partials are double-buffered by step parity, so the
+// three barriers of a step also order it against the next one.  Every
+// reduction has a fixed order: the result does not depend on the schedule.
+constexpr int TD_CL = 16;
+
+__host__ __device__ inline int64_t td_rows_entries(int c, int n, int* nown_out = nullptr) {
+    const int nown = c < n ? (n - c + TD_CL - 1) / TD_CL : 0;
+    if (nown_out) *nown_out = nown;
+    return (int64_t)nown * (c + 1) + (int64_t)(TD_CL / 2) * nown * (nown - 1);
+}
+
+// Entries of the packed-row region, the same in every CTA of the cluster (the
+// largest share, rounded up to even), so that the vectors after it, which
+// other CTAs read, sit at the same offset in every CTA.
+__host__ __device__ inline int64_t td_region(int n) {
+    int64_t mx = 0;
+    for (int c = 0; c < TD_CL; ++c) {
+        const int64_t e = td_rows_entries(c, n);
+        mx = e > mx ? e : mx;
+    }
+    return (mx + 1) / 2 * 2;
+}
+// the packed rows, then colk, pcs, pv (2n each), v, w (n each), pcw (8n)
+constexpr int TD_VECS = 16;
+
+template <typename T>
+size_t tridiag_dsm_smem(int n) {
+    return (size_t)(td_region(n) + TD_VECS * (int64_t)n) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) tridiag_dsm_kernel(const TridiagDescT<T>* __restrict__ descs) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int mat = blockIdx.x / TD_CL;
+    const int c = (int)cluster.block_rank();
+    const TridiagDescT<T> t = descs[mat];
+    const int n = t.n;
+    extern __shared__ __align__(16) unsigned char td_raw[];
+    int nown = 0;
+    (void)td_rows_entries(c, n, &nown);
+    T* L = reinterpret_cast<T*>(td_raw);
+    T* colk = L + td_region(n);  // 2n, by global row
+    T* pcs = colk + 2 * n;            // 2n, by global row
+    T* pv = pcs + 2 * n;              // 2n, by global row
+    T* v = pv + 2 * n;                // n, by trailing index
+    T* w = v + n;                     // n
+    T* pcw = w + n;                   // 8n: column parts per warp
+    __shared__ T part[2][2];
+    __shared__ T red[8];
+    __shared__ T scal[4];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    auto off = [&](int l) -> int64_t { return (int64_t)l * (c + 1) + (int64_t)(TD_CL / 2) * l * (l - 1); };
+    // sum of the TD_CL partials part[b][q] in rank order, by warp 0, into scal[slot]
+    auto cluster_sum = [&](int b, int q, int slot) {
+        if (warp == 0) {
+            T x = T(0);
+            if (lane < TD_CL) x = *cluster.map_shared_rank(&part[b][q], lane);
+            T acc = T(0);
+            for (int i = 0; i < TD_CL; ++i) acc += __shfl_sync(0xffffffffu, x, i);
+            if (lane == 0) scal[slot] = acc;
+        }
+        __syncthreads();
+    };
+    auto block_sum = [&](T x, int b, int q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp] = x;
+        __syncthreads();
+        if (tid == 0) {
+            T acc = T(0);
+            for (int ww = 0; ww < 8; ++ww) acc += red[ww];
+            part[b][q] = acc;
+        }
+    };
+
+    for (int l = 0; l < nown; ++l) {
+        const int r = c + TD_CL * l;
+        T* dst = L + off(l);
+        for (int j = tid; j <= r; j += blockDim.x) dst[j] = t.A[(size_t)r * t.ld + j];
+    }
+    if (c == 0 && tid == 0) t.e[0] = T(0);
+    __syncthreads();
+
+    for (int k = 0; k + 2 < n; ++k) {
+        const int b = k & 1, m = n - k - 1;
+        const int l0 = (k + 1 - c) > 0 ? (k + 1 - c + TD_CL - 1) / TD_CL : 0;
+        T* colb = colk + (size_t)b * n;
+        T* pcb = pcs + (size_t)b * n;
+        T* pvb = pv + (size_t)b * n;
+        // A
+        T sl = T(0);
+        for (int l = l0 + tid; l < nown; l += blockDim.x) {
+            const int r = c + TD_CL * l;
+            const T x = L[off(l) + k];
+            colb[r] = x;
+            sl = fma(x, x, sl);
+        }
+        if (c == k % TD_CL && tid == 0) t.d[k] = L[off((k - c) / TD_CL) + k];
+        block_sum(sl, b, 0);
+        cluster.sync();  // 1
+        // B
+        cluster_sum(b, 0, 0);
+        const T s2 = scal[0];
+        const T x0 = *cluster.map_shared_rank(colb + (k + 1), (k + 1) % TD_CL);
+        const T tail = s2 - x0 * x0;
+        if (!(tail > T(0))) {
+            if (c == 0 && tid == 0) t.e[k + 1] = x0;
+            __syncthreads();
+            continue;
+        }
+        const T alpha = -copysign(sqrt(s2), x0);
+        const T v0 = x0 - alpha;
+        const T beta = T(2) / fma(v0, v0, tail);
+        for (int i = tid; i < m; i += blockDim.x) {
+            const int r = k + 1 + i;
+            v[i] = i == 0 ? v0 : *cluster.map_shared_rank(colb + r, r % TD_CL);
+        }
+        T* pw = pcw + (size_t)warp * n;
+        for (int j = lane; j < m; j += 32) pw[j] = T(0);
+        __syncthreads();
+        for (int l = l0 + warp; l < nown; l += 8) {
+            const int r = c + TD_CL * l, i = r - k - 1;
+            const T* row = L + off(l) + (k + 1);
+            const T vi = v[i];
+            T acc = T(0);
+            for (int j = lane; j <= i; j += 32) {
+                const T a = row[j];
+                acc = fma(a, v[j], acc);
+                if (j < i) pw[j] = fma(a, vi, pw[j]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) pvb[r] = acc;
+        }
+        __syncthreads();
+        for (int j = tid; j < m; j += blockDim.x) {
+            T acc = T(0);
+#pragma unroll
+            for (int ww = 0; ww < 8; ++ww) acc += pcw[(size_t)ww * n + j];
+            pcb[k + 1 + j] = acc;
+        }
+        cluster.sync();  // 2
+        // C
+        T kl = T(0);
+        for (int l = l0 + tid; l < nown; l += blockDim.x) {
+            const int r = c + TD_CL * l;
+            T acc = pvb[r];
+            for (int cc = 0; cc < TD_CL; ++cc) acc += *cluster.map_shared_rank(pcb + r, cc);
+            const T pr = beta * acc;
+            pvb[r] = pr;
+            kl = fma(pr, v[r - k - 1], kl);
+        }
+        block_sum(kl, b, 1);
+        cluster.sync();  // 3
+        // D
+        cluster_sum(b, 1, 1);
+        const T K = T(0.5) * beta * scal[1];
+        for (int i = tid; i < m; i += blockDim.x) {
+            const int r = k + 1 + i;
+            w[i] = fma(-K, v[i], *cluster.map_shared_rank(pvb + r, r % TD_CL));
+        }
+        __syncthreads();
+        for (int l = l0 + warp; l < nown; l += 8) {
+            const int r = c + TD_CL * l, i = r - k - 1;
+            T* row = L + off(l) + (k + 1);
+            const T vi = v[i], wi = w[i];
+            for (int j = lane; j <= i; j += 32) row[j] = fma(-vi, w[j], fma(-wi, v[j], row[j]));
+        }
+        if (c == 0 && tid == 0) t.e[k + 1] = alpha;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (n >= 2) {
+            if (c == (n - 2) % TD_CL) t.d[n - 2] = L[off((n - 2 - c) / TD_CL) + (n - 2)];
+            if (c == (n - 1) % TD_CL) {
+                t.e[n - 1] = L[off((n - 1 - c) / TD_CL) + (n - 2)];
+                t.d[n - 1] = L[off((n - 1 - c) / TD_CL) + (n - 1)];
+            }
+        } else if (n == 1 && c == 0) {
+            t.d[0] = L[0];
+        }
+    }
+    cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+template <typename T>
+bool launch_tridiag_dsm(const TridiagDescT<T>* d, int nmat, int maxn, cudaStream_t s) {
+    const size_t smem = tridiag_dsm_smem<T>(maxn);
+    if (smem > JAC_BLOCK_SMEM_MAX) return false;
+    auto kern = tridiag_dsm_kernel<T>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nmat * TD_CL);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = TD_CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaLaunchKernelEx(&cfg, kern, d) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 template <typename T>
 void launch_tridiag(const TridiagDescT<T>* d, int nmat, int maxn, cudaStream_t s) {
     if (nmat <= 0 || maxn <= 0) return;
+    if (launch_tridiag_dsm<T>(d, nmat, maxn, s)) return;
     const size_t smem = 2 * (size_t)maxn * sizeof(T);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(tridiag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
