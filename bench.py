@@ -50,7 +50,11 @@ SVD_CLASSES = {"jacobi_f32": True, "jacobi_svd": False}
 # `bench.py --steps 1 --warmup 1 --plain-steps 1 --no-scale --no-variants` (dram__bytes_read.sum +
 # dram__bytes_write.sum summed over the class's launches of one step); reported as roofline.traffic only for the
 # workload it was taken on
-TRAFFIC_PER_STEP = {("jacobi_f32", "diffusion3d_24^3_sigma2_ch16_bfs16_256-2048_ov2_tau100"): 3.5211e11}
+TRAFFIC_PER_STEP = {("jacobi_f32", "diffusion3d_24^3_sigma2_ch16_bfs16_256-2048_ov2_tau100"): 3.894e11}
+# TF32 / bf16 dense tensor rates (nominal 1.1 and 2.25 PFLOP/s); an FP32 product by the 3xTF32 split costs three
+# TF32 MMAs
+TF32_OVER_BF16 = 1.1 / 2.25
+SPLIT3 = 3.0
 TRIDIAG_CLASSES = {"tridiag_f32": True, "tridiag": False}
 F32_CLASSES = {"jacobi_f32", "gemm_tiles_f32", "chol_diag_f32", "chol_panel_f32", "trtri_diag_f32", "tridiag_f32",
                "bisect_f32"}
@@ -243,6 +247,7 @@ def max_over_ranks(x: float, dist=None, device=None) -> float:
 
 
 APPLY_SCALE = {"m": 1024, "box": 16, "overlap": 1, "tau": 1e-12}
+TWO_LEVEL_SCALE_TAU = 5e-6
 APPLY_CLASSES = ("gemv_rows_f32", "gemv_rows", "gather_scatter", "coarse_solve")
 
 
@@ -364,6 +369,52 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20, m=None):
                 sparse["kernel_GB/s"] = sparse["kernel_bytes"] / (sparse["kernel_ms_per_launch"] * 1e-3) / 1e9
     finally:
         A.destroy(h2)
+    # two-level apply and PCG at the same size with a partial coarse space: in the
+    # FP32 splitting the eps-cluster eigenvalues of eq. (Zi) on these boxes lie
+    # between about 5e3 and 3e5, so tau = 5e-6 (select lambda > 2e5) keeps a few
+    # modes per box and the dense coarse factor stays a few GB; one-level PCG
+    # (the handle above, n_C = 0) alongside for the iteration counts
+    two = None
+    o3 = A.opts_default()
+    o3.precision = 1
+    o3.profile = 1
+    t0 = time.perf_counter()
+    h3 = A.setup(dA.csr, part.data_ptr(), N, c["overlap"], TWO_LEVEL_SCALE_TAU, o3, sp)
+    setup3_s = time.perf_counter() - t0
+    try:
+        i3 = A.get_info(h3)
+        A.apply(h3, r.data_ptr(), z.data_ptr(), 1)
+        A.reset_profile(h3)
+        ms3 = timed(lambda: A.apply(h3, r.data_ptr(), z.data_ptr(), 1))
+        prof3 = {p["name"]: p for p in A.get_profile(h3)}
+        bytes3 = sum(prof3[k]["bytes"] for k in APPLY_CLASSES if k in prof3) / n_calls
+        cs = prof3.get("coarse_solve")
+        its = {}
+        for nm_, hh in (("one_level", None), ("two_level", h3)):
+            if hh is None:
+                o1 = A.opts_default()
+                o1.precision = 1
+                hh = A.setup(dA.csr, part.data_ptr(), N, c["overlap"], c["tau"], o1, sp)
+            try:
+                xx = torch.zeros_like(r)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = A.pcg_solve(hh, r.data_ptr(), xx.data_ptr(), 1, RTOL, 3000, allow_noconv=True)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                its[nm_] = {"iterations": st.iterations, "converged": int(st.converged),
+                            "true_rel_residual": st.true_rel_residual, "solve_ms": e0.elapsed_time(e1)}
+            finally:
+                if nm_ == "one_level":
+                    A.destroy(hh)
+        two = {"tau": TWO_LEVEL_SCALE_TAU, "n_C": i3.n_C, "setup_s": setup3_s, "apply_ms": ms3, "bytes": bytes3,
+               "GB/s": bytes3 / (ms3 * 1e-3) / 1e9, "frac": bytes3 / (ms3 * 1e-3) / 1e9 / hbm_gbs,
+               "coarse_solve_ms_per_apply": cs["ms"] / cs["launches"] if cs and cs["launches"] else None,
+               "pcg_to_1e-8": its,
+               "note": "whole amdd_apply call; bytes = local factors, gathers, Z rows and the coarse-solve "
+                       "blocks (library profile counts)"}
+    finally:
+        A.destroy(h3)
     spmv_gbs = kernels["spmv"]["GB/s"] if "spmv" in kernels else None
     apply_gbs = apply_bytes / (apply_ms * 1e-3) / 1e9
     return {
@@ -380,6 +431,7 @@ def apply_at_scale(A, torch, np, dev, sp, hbm_gbs, reps=20, m=None):
                        "note": "one amdd_apply call on 8 right-hand sides; factors read once for all"},
         "kernels_in_pcg": kernels,
         "one_level_apply_sparse_factors": sparse,
+        "two_level_apply": two,
     }
 
 
@@ -803,7 +855,15 @@ def run_amdd(args):
         achieved = alg / (per_step_ms * 1e-3) / 1e12
         peak = (FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS) / 1e3
         traffic = TRAFFIC_PER_STEP.get((name, w["name"]))
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+        bound = "alu"
+        tc = f32 and name in SVD_CLASSES and args.tensor_cores
+        if tc:
+            # the pair kernel's contractions run on tcgen05 in 3xTF32: FP32-accurate tensor rate from the
+            # measured bf16 burst
+            alu_peak = peak
+            peak = peaks["bf16_tflops"] * TF32_OVER_BF16 / SPLIT3
+            bound = "tensor"
+        roof = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_note": ("DRAM bytes per step of this class (all its launches in one step), from an ncu "
                                  "capture of the same workload" if traffic else None),
@@ -814,6 +874,10 @@ def run_amdd(args):
                 "launches_per_step": c["launches"] / args.steps, "ms_per_step": per_step_ms,
                 "peak_source": ("FP32 FFMA peak from SM count, lanes and max clock (no tensor cores)" if f32 else
                                 "FP64 1.25 TFLOP/s (recipe table; 2 DFMA/clk/SM x 152 SMs x 2.07 GHz)")}
+        if tc:
+            roof["peak_source"] = (f"3xTF32 on tcgen05: bf16_tflops ({peak_src}) x 1.1/2.25 (nominal TF32/bf16) / 3 "
+                                   "(three TF32 MMAs per FP32 product)")
+            roof["frac_of_fp32_ffma_peak"] = achieved / alu_peak
     elif name in ALU_CLASSES:
         f32 = name in F32_CLASSES
         peak = (FP32_PEAK_GFLOPS if f32 else FP64_PEAK_GFLOPS) / 1e3
