@@ -6,7 +6,9 @@ CPU-baseline leg may import this module.  It shares no code with the CUDA
 library: it reads the same seeded inputs (module `synth`) and nothing else.
 
 Every function follows the paper's definitions in the paper's order and
-notation, with numpy / scipy (LAPACK) primitives as single steps:
+notation, with numpy / scipy (LAPACK) primitives as single steps (the module
+own_linalg.py restates the SVD, Cholesky and symmetric eigensolver steps
+without LAPACK, and the tests check the two against each other):
 
   Sec. 2.1      non-overlapping sets Omega_Ii, overlap Omega_Gi, extension
                 Omega_Di, restrictions R_i, tilde R_i
