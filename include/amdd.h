@@ -49,7 +49,7 @@ typedef enum {
     AMDD_ERR_NOT_SPD = 2,     /* a Cholesky pivot <= 0 (A_ii or E not SPD)         */
     AMDD_ERR_NOCONV = 3,      /* PCG reached maxit before the tolerance            */
     AMDD_ERR_OOM = 4,         /* a device or host allocation failed                */
-    AMDD_ERR_TIMEOUT = 5,     /* a bounded device wait (tensor-core GEMM) gave up   */
+    AMDD_ERR_TIMEOUT = 5,     /* a bounded device wait (tensor cores, Jacobi sweep) gave up */
     AMDD_ERR_CUDA = 6,        /* any other CUDA runtime error                      */
     AMDD_ERR_EIG_NOCONV = 7   /* a Jacobi eigensolver hit its sweep limit          */
 } amdd_status;
@@ -260,6 +260,15 @@ amdd_status amdd_opts_default(amdd_opts* o);
 amdd_status amdd_gemm_f32(int32_t m, int32_t n, int32_t k, float alpha, const float* A, int32_t lda, int32_t ta,
                           const float* B, int32_t ldb, int32_t tb, float beta, float* C, int32_t ldc,
                           int32_t tensor_cores, void* stream);
+
+/* Check of the failure status of the library's bounded device waits (no
+ * counterpart in the paper): the wait of the persistent block-pair Jacobi
+ * sweep, run on its own for about 2 ms of SM clock on a device flag that is
+ * 1 when `set_flag` is non-zero and stays 0 otherwise.  AMDD_OK when the flag
+ * was set; AMDD_ERR_TIMEOUT when the wait gave up (the kernel returns normally
+ * and the context stays usable); AMDD_ERR_OOM / AMDD_ERR_CUDA on allocation or
+ * launch failure.  Allocates 8 bytes stream-ordered and synchronises `stream`. */
+amdd_status amdd_wait_selftest(int32_t set_flag, void* stream);
 
 /* y = A x (Sec. 1: the operator of A x = b).  A, x (length n) and y
  * (length n) are device pointers; y must not alias x.  Work is issued on

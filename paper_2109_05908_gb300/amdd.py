@@ -76,6 +76,7 @@ _lib = None
 SIGNATURES = {
     "amdd_opts_default": (C.c_int, [C.POINTER(amdd_opts)]),
     "amdd_spmv": (C.c_int, [C.POINTER(amdd_csr), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "amdd_wait_selftest": (C.c_int, [C.c_int32, C.c_void_p]),
     "amdd_gemm_f32": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_void_p, C.c_int32, C.c_int32,
                                 C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_void_p, C.c_int32, C.c_int32,
                                 C.c_void_p]),
@@ -166,6 +167,12 @@ def gemm_f32(m: int, n: int, k: int, alpha: float, a_ptr: int, lda: int, ta: int
     """C = alpha op(A) op(B) + beta C in FP32 through amdd_gemm_f32."""
     _check(lib().amdd_gemm_f32(m, n, k, alpha, a_ptr, lda, ta, b_ptr, ldb, tb, beta, c_ptr, ldc, tensor_cores,
                                stream), "amdd_gemm_f32")
+
+
+def wait_selftest(set_flag: bool, stream: int = 0) -> None:
+    """Bounded device wait on a flag that is set (returns) or never set
+    (raises AmddError with AMDD_ERR_TIMEOUT)."""
+    _check(lib().amdd_wait_selftest(1 if set_flag else 0, stream), "amdd_wait_selftest")
 
 
 def spmv(A: amdd_csr, x_ptr: int, y_ptr: int, stream: int = 0) -> None:

@@ -4168,6 +4168,20 @@ amdd_status amdd_gemm_f32(int32_t m, int32_t n, int32_t k, float alpha, const fl
     return st;
 }
 
+amdd_status amdd_wait_selftest(int32_t set_flag, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* buf = nullptr;  // flag, error word
+    if (cudaMallocAsync((void**)&buf, 2 * sizeof(int), s) != cudaSuccess) return AMDD_ERR_OOM;
+    const int init[2] = {set_flag ? 1 : 0, 0};
+    int err = 0;
+    cudaMemcpyAsync(buf, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    launch_wait_selftest(buf, 4000000ll, buf + 1, s);  // about 2 ms at 2 GHz
+    cudaMemcpyAsync(&err, buf + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(buf, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return AMDD_ERR_CUDA;
+    return err & DERR_TIMEOUT ? AMDD_ERR_TIMEOUT : AMDD_OK;
+}
+
 amdd_status amdd_spmv(const amdd_csr* A, const double* x, double* y, void* stream) {
     if (!A || A->n < 0 || A->nnz < 0 || (A->n > 0 && (!A->rowptr || !x || !y)) || (A->nnz > 0 && (!A->colind || !A->val)))
         return AMDD_ERR_INVALID;

@@ -166,6 +166,9 @@ size_t jacobi_pair_tc_smem();
 int launch_jacobi_pair_tc_sweep(const JacobiDescT<float>* d, const int4* tasks, int ntasks, int* counter, int* bdone,
                                  const int* bofs, float tol, int inner, int* rotated, unsigned long long* rots,
                                  unsigned long long* stats, int* err, cudaStream_t s);
+// one thread waits (bounded, `limit` SM cycles) for *flag >= 1; DERR_TIMEOUT
+// into *err when the wait gives up
+void launch_wait_selftest(const int* flag, long long limit, int* err, cudaStream_t s);
 void launch_gemm_tc(const GemmDescT<float>* d_descs, const TileRef* d_tiles, int ntiles, int* err, cudaStream_t s);
 // *p |= bits (one thread)
 void launch_or_flag(int* p, int bits, cudaStream_t s);

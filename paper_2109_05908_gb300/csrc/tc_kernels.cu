@@ -80,13 +80,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 
 // Block flags of the persistent block-pair sweep: bounded acquire wait until
 // *f >= v (about a second of polling), and a release store.
-__device__ __forceinline__ bool flag_wait_geq(const int* f, int v) {
+__device__ __forceinline__ bool flag_wait_geq(const int* f, int v, long long limit = 2000000000ll) {
     const long long start = clock64();
     for (;;) {
         int x;
         asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(x) : "l"(f) : "memory");
         if (x >= v) return true;
-        if (clock64() - start > 2000000000ll) return false;
+        if (clock64() - start > limit) return false;
         __nanosleep(64);
     }
 }
@@ -661,6 +661,17 @@ void launch_gemm_tc(const GemmDescT<float>* d_descs, const TileRef* d_tiles, int
     const size_t smem = gemm_tc_smem();
     cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     gemm_tc_kernel<<<ntiles, 128, smem, s>>>(d_descs, d_tiles, ntiles, err);
+}
+
+// The persistent sweep's bounded flag wait on its own: one thread waits until
+// *flag >= 1 for at most `limit` SM cycles and latches DERR_TIMEOUT in *err
+// when it gives up.
+__global__ void wait_selftest_kernel(const int* flag, long long limit, int* err) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && !flag_wait_geq(flag, 1, limit)) atomicOr(err, DERR_TIMEOUT);
+}
+
+void launch_wait_selftest(const int* flag, long long limit, int* err, cudaStream_t s) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(flag, limit, err);
 }
 
 }  // namespace amdd
